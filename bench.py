@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Throughput of the sCMRH hot path on GB300 (one JSON line on rank 0).
+
+One step = one whole solve through the C ABI: initialisation (pivot of b,
+v_1, sketches), k Hessenberg steps (operator, pivot-block solve, update +
+argmax, normalise + sketch) and the sketched projected solve with x = V_k y.
+
+Default workload: 2048 x 2048 deblurring with a 31 x 31 Moffat PSF
+(beta 2.5, alpha 4), ellipse phantom, 1% noise, k = 200, m_s = 800, zeta 8,
+basis stored in BF16 with FP32 accumulation (FP64 pivot-block and projected
+solves).  The FP32-storage form of the same workload is timed beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica (the method
+does not shard across GPUs here); value = all ranks' iterations / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "iters/s & solves/s, BF16 vs FP32 GPU at rel-err<=1e-3 vs FP64; p50/p99 latency"
+WORKLOAD = ("deblur 2048x2048, Moffat 31x31 PSF (beta 2.5, alpha 4), ellipse phantom, 1% noise; "
+            "k=200, m_s=800, zeta=8; basis BF16 storage, FP32 accumulate; x = V_k y per solve")
+K_ITERS = 200
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu_id, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _gpu_id(torch, dev):
+    try:
+        props = torch.cuda.get_device_properties(dev)
+        bus = getattr(props, "pci_bus_id", None)
+        dom = getattr(props, "pci_domain_id", 0)
+        devid = getattr(props, "pci_device_id", 0)
+        if bus is not None:
+            return f"{dom:08X}:{bus:02X}:{devid:02X}.0"
+    except Exception:
+        pass
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        return vis.split(",")[dev]
+    return str(dev)
+
+
+# ---------------------------------------------------------------------------
+# the FP64 oracle on a bounded sample (CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+ORACLE_SAMPLE = ("oracle (numpy float64) on the full 2048x2048 problem: initialisation plus Hessenberg "
+                 "steps 1..{s} (each: one 31x31 convolution, the sequential elimination, the max pivot, "
+                 "two sketches), single thread")
+
+
+def oracle_sample_child(steps: int, out_path: str):
+    """Runs in a fresh interpreter with BLAS limited to one thread."""
+    from gen import problems as P
+    from oracle import operators as ops, scmrh, sketch as sk
+    p = P.make("deblur2048")
+    A = ops.make_apply(p)
+    S = sk.SparseSignSketch(p.sketch_seed, p.n, p.m_s, p.zeta)
+    t0 = time.perf_counter()
+    times = []
+    st = None
+    for j, st in scmrh.iterate(A, p.b[0], S, steps):
+        times.append(time.perf_counter() - t0)
+    xs = {f"x{k}": scmrh.solve(st, k).astype(np.float32) for k in range(1, st.k_done + 1)}
+    np.savez(out_path, times=np.array(times), piv=np.array(st.piv), **xs)
+
+
+def run_oracle_sample(steps: int) -> dict:
+    import tempfile
+    out = os.path.join(tempfile.mkdtemp(prefix="ipf_oracle_"), "o.npz")
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = (f"import sys; sys.path.insert(0, {ROOT!r}); import bench; "
+            f"bench.oracle_sample_child({steps}, {out!r})")
+    subprocess.run([sys.executable, "-c", code], env=env, check=True)
+    d = np.load(out)
+    times = d["times"]
+    res = {"init_s": float(times[0]), "step_s": [float(times[i] - times[i - 1]) for i in range(1, len(times))],
+           "piv": d["piv"].tolist(), "x": {int(k[1:]): d[k] for k in d.files if k.startswith("x")}}
+    return res
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, torch, dist):
+    from gen import problems as P
+    from paper_2502_02721_gb300 import binding as bd, build as bl
+    if not os.path.exists(bl.lib_path()):
+        bl.build()
+    bd.load()
+    dev = torch.cuda.current_device()
+    p = P.make("deblur2048")
+    n = p.n
+    k = K_ITERS
+    stream = torch.cuda.current_stream()
+    keep = []
+    op = bd.operator_from_problem(p, keep)
+    b_dev = torch.from_numpy(p.b.copy()).to(f"cuda:{dev}")
+
+    def make_ctx(storage, profile):
+        cfg = bd.default_config(k_max=k, m_s=p.m_s, zeta=p.zeta, seed=p.sketch_seed, storage=storage,
+                                profile=profile, use_graphs=0 if profile else 1, stream=stream.cuda_stream)
+        return bd.Context(op, b_dev, cfg, keep)
+
+    def timed_solves(ctx, x_out, steps, warmup, lam=(0.0,)):
+        for _ in range(warmup):
+            ctx.reset(b_dev)
+            ctx.step(k)
+            ctx.solve(k, lam, out=x_out, wait=False)
+        torch.cuda.synchronize()
+        ctx.profile_read()                       # drop warm-up kernel times
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        evs[0].record(stream)
+        for s in range(steps):
+            ctx.reset(b_dev)
+            ctx.step(k)
+            ctx.solve(k, lam, out=x_out, wait=False)
+            evs[s + 1].record(stream)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        per = [evs[s].elapsed_time(evs[s + 1]) for s in range(steps)]
+        total = evs[0].elapsed_time(evs[-1])
+        prof = ctx.profile_read()
+        st, kd = ctx.sync()
+        return total, per, prof, kd
+
+    # --- BF16 (headline) --------------------------------------------------
+    clocks = ClockSampler(_gpu_id(torch, dev))
+    ctx16 = make_ctx("bf16", 1)
+    x16 = torch.zeros((1, 1, n), dtype=torch.float32, device=f"cuda:{dev}")
+    clocks.start()
+    t16, per16, prof16, kd16 = timed_solves(ctx16, x16, args.steps, args.warmup)
+    clk = clocks.stop()
+    t_max = t16
+    if dist is not None:
+        tt = torch.tensor([t16], dtype=torch.float64, device=f"cuda:{dev}")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+
+    # --- FP32 storage, same workload -----------------------------------------
+    ctx32 = make_ctx("f32", 1)
+    x32 = torch.zeros((1, 1, n), dtype=torch.float32, device=f"cuda:{dev}")
+    steps32 = max(1, min(args.steps, 5))
+    t32, per32, prof32, kd32 = timed_solves(ctx32, x32, steps32, 1)
+
+    # --- accuracy: BF16 and FP32 against each other, x_true, and the FP64 oracle
+    acc = {}
+    xb = x16[0, 0].double().cpu().numpy()
+    xf = x32[0, 0].double().cpu().numpy()
+    nrm = lambda a: float(np.linalg.norm(a))
+    acc["k200_relerr_bf16_vs_fp32"] = nrm(xb - xf) / nrm(xf)
+    acc["k200_err_vs_xtrue"] = {"bf16": nrm(xb - p.x_true) / nrm(p.x_true), "fp32": nrm(xf - p.x_true) / nrm(p.x_true)}
+    # small-k iterates (before semi-convergence) for the comparison with the oracle
+    small = {}
+    for name, ctx in (("bf16", ctx16), ("fp32", ctx32)):
+        ctx.reset(b_dev)
+        ctx.step(5)
+        xs, _ = ctx.solve(5, [0.0])
+        small[name] = xs[0, 0].astype(np.float64)
+        xs1 = None
+    for name, ctx in (("bf16", ctx16), ("fp32", ctx32)):
+        ctx.reset(b_dev)
+        ctx.step(2)
+        small[name + "_k1"] = ctx.solve(1, [0.0])[0][0, 0].astype(np.float64)
+        small[name + "_k2"] = ctx.solve(2, [0.0])[0][0, 0].astype(np.float64)
+    acc["k5_err_vs_xtrue"] = {nm: nrm(small[nm] - p.x_true) / nrm(p.x_true) for nm in ("bf16", "fp32")}
+    acc["k5_relerr_bf16_vs_fp32"] = nrm(small["bf16"] - small["fp32"]) / nrm(small["fp32"])
+
+    # --- end to end: pinned host b in, host x out, through the C ABI ------
+    b_host = torch.from_numpy(p.b.copy()).pin_memory()
+    x_host = torch.zeros((1, 1, n), dtype=torch.float32).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    ctx16.reset(b_host)
+    ctx16.step(k)
+    ctx16.solve(k, [0.0], out=x_host)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx16.reset(b_host)
+        ctx16.step(k)
+        ctx16.solve(k, [0.0], out=x_host)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    ctx16.profile_read()
+
+    # --- CPU baseline (rank 0 only, bounded oracle sample) -----------------
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        o = run_oracle_sample(1)
+        step_s = o["step_s"][0]
+        cpu = {"value": 1.0 / step_s, "unit": "iters/s", "cores": 1, "kind": "oracle",
+               "sample": ORACLE_SAMPLE.format(s=1) + f"; init {o['init_s']:.1f} s, step 1 {step_s:.1f} s"}
+        acc["k1_relerr_vs_fp64_oracle"] = {
+            "bf16": nrm(small["bf16_k1"] - o["x"][1]) / nrm(o["x"][1]),
+            "fp32": nrm(small["fp32_k1"] - o["x"][1]) / nrm(o["x"][1])}
+
+    # --- roofline of the dominant kernel ------------------------------------
+    ms, cnt, byts = prof16
+    names = ["operator", "pivot_solve", "update_argmax", "normalize_sketch", "init", "solve_qr", "solve_x"]
+    kern = {names[i]: {"ms_total": ms[i], "launches": int(cnt[i]),
+                       "share": ms[i] / max(sum(ms[:7]), 1e-9),
+                       "GBps": (byts[i] / (ms[i] * 1e-3) / 1e9) if ms[i] > 0 and byts[i] > 0 else None}
+            for i in range(7)}
+    peak, peak_kind = _peaks()
+    upd = kern["update_argmax"]
+    roof = {"kernel": "k_update_f (u -= V_j h, zero pivots, argmax)", "bound": "hbm",
+            "achieved": upd["GBps"], "peak": peak, "unit": "GB/s",
+            "frac": (upd["GBps"] / peak) if upd["GBps"] else None, "traffic": None,
+            "peak_source": f"{peak_kind} hbm_gbs", "bytes_per_launch": byts[2] / max(cnt[2], 1),
+            "algorithmic_bytes": "per launch at step j: (j+1)*n*2 (read V_j, BF16) + 8n (read+write u, FP32) + n/8 (pivot bitmap)"}
+    # FP32 FMA peak for the convolution (152 SMs x 128 lanes x 2 flop x clock)
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    conv_flops = 2.0 * 961 * n * cnt[0]
+    conv_tf = conv_flops / (ms[0] * 1e-3) / 1e12 if ms[0] > 0 else None
+    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    roof_conv = {"kernel": "k_conv2d<bf16,31> (w = P * v)", "bound": "alu", "achieved": conv_tf,
+                 "peak": alu_peak, "unit": "TFLOP/s", "frac": (conv_tf / alu_peak) if conv_tf else None,
+                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock under load"}
+    dominant = max(range(7), key=lambda i: ms[i])
+    launches = int(cnt[0] + cnt[1] + cnt[2] + cnt[3] + 4 * cnt[4] + 2 * cnt[5] + 2 * cnt[6])
+
+    iters = world * args.steps * k
+    value = iters / (t_max * 1e-3)
+    out = {
+        "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "k": k, "m_s": p.m_s, "zeta": p.zeta, "storage": "bf16",
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2: the BF16 basis is 1.69 GB (L2 129 MB)",
+                   "launch": "eager launches with CUDA events around each kernel (profile mode)"},
+        "solves_per_s": world * args.steps / (t_max * 1e-3),
+        "latency_ms": {"p50": float(np.percentile(per16, 50)), "p99": float(np.percentile(per16, 99))},
+        "fp32": {"iters_per_s": steps32 * k / (t32 * 1e-3), "solves_per_s": steps32 / (t32 * 1e-3),
+                 "ms_per_solve": t32 / steps32},
+        "bf16_speedup_over_fp32": (args.steps / t16) / (steps32 / t32),
+        "accuracy": acc,
+        "roofline": roof if dominant in (2, 3, 6) else roof_conv,
+        "roofline_other": roof_conv if dominant in (2, 3, 6) else roof,
+        "kernels": kern,
+        "gpu_launches": launches * world,
+        "e2e": {"value": e2e_steps * k / t_e2e, "unit": "iters/s", "h2d_bytes_per_step": int(4 * n),
+                "d2h_bytes_per_step": int(4 * n)},
+        "clocks": {k2: clk[k2] for k2 in ("sm_mhz", "sm_max_mhz", "reasons")},
+        "k_done": kd16,
+    }
+    if cpu is not None:
+        out["cpu_baseline"] = cpu
+    ctx16.close()
+    ctx32.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle as it stands, on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    from gen import problems as P
+    from oracle import operators as ops, scmrh, sketch as sk
+    p = P.make("deblur2048")
+    A = ops.make_apply(p)
+    S = sk.SparseSignSketch(p.sketch_seed, p.n, p.m_s, p.zeta)
+    total = args.warmup + args.steps
+    it = scmrh.iterate(A, p.b[0], S, total)
+    next(it)                                   # initialisation (not a step)
+    times = []
+    for s in range(total):
+        t0 = time.perf_counter()
+        next(it)
+        times.append(time.perf_counter() - t0)
+    timed = times[args.warmup:]
+    t = sum(timed)
+    value = args.steps / t
+    sample = (f"each step = one Hessenberg step of the float64 oracle on the full 2048x2048 problem "
+              f"(steps {args.warmup + 1}..{total} of one run after {args.warmup} warm-up steps), one thread")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "n": p.n, "k": K_ITERS, "m_s": p.m_s},
+            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args)), flush=True)
+        return
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    else:
+        torch.cuda.set_device(0)
+    out = run_ours(args, rank, world, torch, dist)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

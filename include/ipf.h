@@ -1,0 +1,234 @@
+/*
+ * ipf.h -- C ABI of libipf, a GB300 (sm_103a) implementation of the sketched
+ * inner-product-free Krylov method sCMRH of arXiv 2502.02721
+ * ("Randomized and inner-product free Krylov methods for large-scale inverse
+ * problems").
+ *
+ * Problem (Sec. 1, Eq. 1-3):  b = A x_true + e.  The library builds, with no
+ * inner products, the pivoted Hessenberg basis V_{k+1} = L_{k+1} of
+ * K_k(A, b) with A V_k = V_{k+1} H_{k+1,k} (Sec. 3.1, Eq. Hessenberg_s),
+ * sketches it with a sparse-sign embedding S (Sec. 2), and solves the
+ * sketched projected problem (Sec. 3.2 Eq. sketched_LSLU; Sec. 3.3
+ * Eq. sketched_LSLU_hybrid)
+ *      y = argmin || S (A V_k y - b) ||^2 + lambda^2 || S V_k y ||^2,
+ *      x_k = V_k y                                      (x_0 = 0).
+ * A is reached only through products A v (Sec. 1).
+ *
+ * Conventions for every entry point
+ *  - Pointers are plain host or device addresses; which one is stated per
+ *    argument (an *_mem flag selects where caller arrays live).
+ *  - No exception crosses the ABI.  Every call returns an ipf_status.
+ *  - Errors on a context are sticky: once a call fails with an IPF_ERR_*
+ *    code, later calls on that context return the same code.
+ *    ipf_last_error() gives a one-line message.
+ *  - Work is enqueued on the context's own CUDA stream, ordered after all
+ *    work already on the caller's stream (config.stream) at call time, and
+ *    the caller's stream is made to wait for it before the call returns.
+ *  - All device memory of a context is allocated at ipf_create (through the
+ *    config's alloc/free callbacks when given, else cudaMalloc) and freed by
+ *    ipf_destroy.
+ */
+#ifndef IPF_H
+#define IPF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ipf_status {
+    IPF_OK = 0,
+    IPF_BREAKDOWN = 1,        /* H(k+1,k) = 0 (Algorithm 1): not an error; the iterate at
+                                 k_done is exact in K_{k_done}(A, b)                   */
+    IPF_PENDING = 2,          /* serving: request not finished yet                    */
+    IPF_ERR_ARG = -1,         /* invalid argument; nothing was enqueued               */
+    IPF_ERR_OOM = -2,         /* device allocation failed                             */
+    IPF_ERR_CUDA = -3,        /* a CUDA call failed (message in ipf_last_error)       */
+    IPF_ERR_NONFINITE = -4,   /* a pivot value was NaN or Inf                         */
+    IPF_ERR_TIMEOUT = -5,     /* a bounded device-side wait gave up                   */
+    IPF_ERR_STATE = -6,       /* call not valid in the current state (e.g. k > steps) */
+    IPF_ERR_UNSUPPORTED = -7, /* combination of options not implemented               */
+    IPF_ERR_REJECTED = -8     /* serving: request can never fit the memory budget     */
+} ipf_status;
+
+enum ipf_op_kind {
+    IPF_OP_PSF2D = 1,            /* w = P * v, odd ph x pw PSF, zero boundary          */
+    IPF_OP_PSF2D_SEP_MOTION = 2, /* w = M * (g_col (x) g_row * v), both passes zero
+                                    boundary, cropped to the image in between          */
+    IPF_OP_CSR = 3               /* w = A v, CSR (int64 rowptr, int32 colind, f32 vals) */
+};
+
+enum ipf_mem { IPF_MEM_HOST = 0, IPF_MEM_DEVICE = 1 };
+
+/* storage precision of the basis V; arithmetic is FP32-accumulate for
+ * F32/BF16/F16 and FP64 for F64; the pivot-block solve and the projected
+ * least-squares solve are FP64 in every mode.                              */
+enum ipf_storage { IPF_STORE_F64 = 0, IPF_STORE_F32 = 1, IPF_STORE_BF16 = 2, IPF_STORE_F16 = 3 };
+
+/* Tikhonov penalty: lambda^2 ||S V_k y||^2 (Eq. sketched_LSLU_hybrid with
+ * S_1 = S) or lambda^2 ||y||^2 (the penalty of Eq. TSP).                   */
+enum ipf_penalty { IPF_PEN_SKETCHED_X = 0, IPF_PEN_Y = 1 };
+
+/* How S A V_k is assembled: DIRECT uses the sketch of each product A v_j
+ * (Algorithm 1 line 11, z_k = S u, before the elimination), HESSENBERG uses
+ * S V_{k+1} H_k.  They agree in exact arithmetic; with BF16/FP16 storage
+ * DIRECT is the sketch of the products of the stored basis.               */
+enum ipf_zform { IPF_Z_DIRECT = 0, IPF_Z_HESSENBERG = 1 };
+
+/* Forward operator.  For PSF kinds n = rows*cols and images are row-major.
+ * For CSR, rows x cols is m x n and the method needs m == n (square A).
+ * mem says where psf/sep_row/sep_col/motion/rowptr/colind/vals live:
+ *   IPF_MEM_HOST    the library copies them at ipf_create / ipf_op_create;
+ *   IPF_MEM_DEVICE  PSF arrays are copied; CSR arrays are referenced, not
+ *                   copied: the caller keeps them alive and unchanged for
+ *                   the lifetime of every context or handle using them.
+ * Host CSR arrays are validated (rowptr monotone from 0 to nnz, column
+ * indices in [0, cols)); device CSR arrays must satisfy the same and are
+ * not checked.                                                            */
+typedef struct ipf_operator {
+    int kind;
+    int rows, cols;
+    const float* psf;            int ph, pw;        /* IPF_OP_PSF2D, ph, pw odd <= 63   */
+    const float* sep_row;        const float* sep_col; int slen;   /* odd <= 63        */
+    const float* motion;         int mlen;          /* mlen x mlen, odd <= 15          */
+    const long long* rowptr;     const int* colind; const float* vals; long long nnz;
+    int mem;
+} ipf_operator;
+
+typedef void* (*ipf_alloc_fn)(size_t bytes, void* user);
+typedef void (*ipf_free_fn)(void* ptr, void* user);
+
+typedef struct ipf_config {
+    int k_max;                   /* maximum Hessenberg steps (basis has k_max+1 vectors)   */
+    int m_s;                     /* sketch rows (l in Sec. 2); m_s >= zeta                  */
+    int zeta;                    /* nonzeros per sketch column, 1..16                       */
+    unsigned long long seed;     /* sketch seed (SplitMix64 state)                          */
+    int storage;                 /* enum ipf_storage                                        */
+    int penalty;                 /* enum ipf_penalty                                        */
+    int zform;                   /* enum ipf_zform                                          */
+    int nrhs;                    /* independent right-hand sides sharing A: 1, 2, 4 .. 32;
+                                    PSF operators and F64 storage need nrhs == 1            */
+    int use_graphs;              /* capture each Hessenberg step in a CUDA graph            */
+    int profile;                 /* bracket every kernel with CUDA events on the context's
+                                    stream (launches eagerly; read with ipf_profile_read)   */
+    void* stream;                /* cudaStream_t of the caller (NULL: legacy default)      */
+    ipf_alloc_fn alloc;          /* optional device allocator (e.g. a framework's pool)    */
+    ipf_free_fn free;
+    void* alloc_user;
+} ipf_config;
+
+typedef struct ipf_solve_info {
+    int k_used;                  /* iterations used for this right-hand side              */
+    int k_done;                  /* completed Hessenberg steps                            */
+    int status;                  /* IPF_OK, IPF_BREAKDOWN or an error                      */
+    int pad;
+} ipf_solve_info;
+
+typedef struct ipf_ctx ipf_ctx;
+typedef struct ipf_op ipf_op;
+
+/* Fill *cfg with defaults: k_max 50, m_s 200, zeta 8, seed 1, F32 storage,
+ * sketched-x penalty, direct Z, nrhs 1, graphs on, default stream, cudaMalloc. */
+void ipf_config_default(ipf_config* cfg);
+
+/* Bytes of device memory ipf_create would allocate for this problem
+ * (the serving loop admits requests by this number).                      */
+size_t ipf_footprint(const ipf_operator* op, const ipf_config* cfg);
+
+/* Create a solve context and enqueue the initialisation of Algorithm 1
+ * (r_0 = b, pivot p_1 = argmax |b| with the lowest index on ties,
+ * beta = b(p_1), v_1 = b / beta, c = S b).
+ *   op    operator (see ipf_operator for ownership of its arrays)
+ *   b     nrhs x n float32, right-hand side r stored at b + r*n; b_mem says
+ *         whether it is host or device memory; copied, not retained.
+ *   cfg   options; copied.
+ *   out   receives the context (NULL on failure).
+ * Errors: IPF_ERR_ARG (bad sizes or options), IPF_ERR_UNSUPPORTED,
+ * IPF_ERR_OOM, IPF_ERR_CUDA.  A zero right-hand side is not an error: that
+ * RHS reports IPF_BREAKDOWN with k_done 0 and solves to x = 0.             */
+ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem,
+                      const ipf_config* cfg, ipf_ctx** out);
+
+/* Start a new solve on an existing context with a new right-hand side b
+ * (same layout and ownership as in ipf_create), reusing all of its device
+ * memory: clears the state and enqueues the initialisation.  Allocates
+ * nothing.  Clears a sticky error only if it was IPF_ERR_NONFINITE.        */
+ipf_status ipf_reset(ipf_ctx* ctx, const float* b, int b_mem);
+
+/* Enqueue nsteps Hessenberg steps (Algorithm 1 lines 10-19, square form):
+ * u = A v_j; h = L_p^{-1} u(p) (the sequential elimination of lines 12-14
+ * as a unit-lower forward substitution on the pivot rows, FP64);
+ * u -= V_j h with the pivot rows set to 0; p_{j+1} = argmax |u| over
+ * non-pivot rows (lowest index on ties); H(j+1, j) = u(p_{j+1});
+ * v_{j+1} = u / H(j+1, j) rounded to the storage type; S v_{j+1}.
+ * Asynchronous.  A right-hand side that breaks down stops there; the
+ * others continue.  nsteps is clipped to k_max minus the steps already
+ * enqueued; *k_enqueued (may be NULL) receives the total enqueued.        */
+ipf_status ipf_step(ipf_ctx* ctx, int nsteps, int* k_enqueued);
+
+/* Wait for the context's work; k_done (nrhs entries, host, may be NULL)
+ * receives the completed steps per RHS.  Returns the worst RHS status.    */
+ipf_status ipf_sync(ipf_ctx* ctx, int* k_done);
+
+/* Solve the sketched projected problem at k for each lambda and form
+ * x = V_k y (Sec. 3.2, 3.3).  For RHS r, k_r = min(k, k_done_r).
+ *   lambdas  nl >= 1 host doubles (0 gives the plain sketched LS problem)
+ *   x_out    nl x nrhs x n float32, x for lambda l and RHS r at
+ *            x_out + (l*nrhs + r)*n; host or device per x_mem.
+ *   info     nrhs host entries, may be NULL.
+ * Synchronises with the context's stream.  IPF_ERR_STATE if k exceeds the
+ * steps enqueued.                                                          */
+ipf_status ipf_solve(ipf_ctx* ctx, int k, const double* lambdas, int nl,
+                     float* x_out, int x_mem, ipf_solve_info* info);
+/* With x_mem == IPF_MEM_DEVICE and info == NULL, ipf_solve does not wait
+ * for the GPU: it returns once the work is enqueued, and a device-side
+ * failure of the solve is reported by the next ipf_sync.                  */
+
+/* Kernel timings of a context created with config.profile = 1: for each
+ * kind (0 operator, 1 pivot-block solve, 2 update+argmax, 3 normalise+sketch,
+ * 4 initialisation, 5 projected-solve QR, 6 per-lambda solve + x = V_k y)
+ * the summed milliseconds, launch counts and the summed algorithmic bytes
+ * of the launches (0 where not defined), since the previous read.
+ * Arrays of 8 entries, host; synchronises.                                */
+ipf_status ipf_profile_read(ipf_ctx* ctx, double* ms, long long* launches, double* bytes);
+
+/* Copy the method's state for RHS r to host memory (any pointer may be
+ * NULL): pivots (k_done+1 ints, 0-based rows), H ((k_max+1) x k_max FP64,
+ * column-major, column j holds H(0..j+1, j)), SV (m_s x (k_max+1) FP64,
+ * column-major, the sketch of the stored basis), SW (same shape, sketch of
+ * each normalised vector before rounding to storage), beta (1 double).
+ * Synchronises.                                                           */
+ipf_status ipf_export(ipf_ctx* ctx, int r, int* pivots, double* H, double* SV, double* SW,
+                      double* beta);
+
+/* Copy basis vector j (0-based, j <= k_done) of RHS r as float32 (host). */
+ipf_status ipf_export_basis(ipf_ctx* ctx, int r, int j, float* v_out);
+
+void ipf_destroy(ipf_ctx* ctx);
+const char* ipf_status_str(ipf_status s);
+const char* ipf_last_error(const ipf_ctx* ctx);
+
+/* ---- operator and sketch kernels as standalone calls (device pointers) ---- */
+
+/* Upload an operator (see ipf_operator for ownership) and apply it:
+ * w = A v for nrhs vectors, v and w device float32 nrhs x n, vector r at
+ * offset r*n.  Runs on `stream` (cudaStream_t, may be NULL).              */
+ipf_status ipf_op_create(const ipf_operator* op, ipf_op** out);
+ipf_status ipf_op_apply(ipf_op* h, const float* v_dev, float* w_dev, int nrhs, void* stream);
+void ipf_op_destroy(ipf_op* h);
+
+/* y = S x for the block sparse-sign sketch S (m_s x n, zeta nonzeros
+ * +-1/sqrt(zeta) per column, drawn from a SplitMix64 counter hash of seed;
+ * Sec. 2 names sparse sign embeddings among the subspace embeddings).
+ * x: device float32 (n); y: device float64 (m_s).  Sums are accumulated
+ * exactly in 64-bit fixed point scaled to max|x|, so the result does not
+ * depend on thread order.  Allocates its scratch with cudaMallocAsync on
+ * `stream` and frees it before returning.                                  */
+ipf_status ipf_sketch_apply(const float* x_dev, long long n, int m_s, int zeta,
+                            unsigned long long seed, double* y_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IPF_H */

@@ -58,13 +58,10 @@ def _argmax_abs_excluding(u: np.ndarray, is_piv: np.ndarray):
     return i, float(top), gap
 
 
-def run(apply_A, b, sketch, k_max: int, forced_pivots=None) -> HessenbergState:
-    """k_max steps of the pivoted Hessenberg process with sketch S.
-
-    forced_pivots: optional sequence of rows to use as p_1, p_2, ... instead
-    of the max-|.| choice (replays another run's pivot order when two
-    candidates are within rounding of each other).
-    """
+def iterate(apply_A, b, sketch, k_max: int, forced_pivots=None):
+    """Generator form of run(): yields (j, state) after the initialisation
+    (j = 0) and after each Hessenberg step j = 1..k_done.  Each state holds
+    views of the working arrays trimmed to the j completed steps."""
     b = np.asarray(b, dtype=np.float64).reshape(-1)
     n = b.size
     m = sketch.m
@@ -76,6 +73,10 @@ def run(apply_A, b, sketch, k_max: int, forced_pivots=None) -> HessenbergState:
     c = sketch.apply(b)
     gaps = []
 
+    def state(k, beta, piv, breakdown):
+        return HessenbergState(V[:, :k + 1], H[:k + 1, :k], list(piv), SV[:, :k + 1], Zd[:, :k], c,
+                               beta, k, breakdown, list(gaps))
+
     # init: r0 = b - A x0 with x0 = 0
     if forced_pivots is not None:
         i = int(forced_pivots[0])
@@ -84,13 +85,14 @@ def run(apply_A, b, sketch, k_max: int, forced_pivots=None) -> HessenbergState:
         gaps.append(g)
     beta = float(b[i])
     if beta == 0.0:
-        return HessenbergState(V[:, :1], H[:1, :0], [], SV[:, :1], Zd[:, :0], c, 0.0, 0, True, gaps)
+        yield 0, state(0, 0.0, [], True)
+        return
     V[:, 0] = b / beta
     piv = [i]
     is_piv[i] = True
     SV[:, 0] = sketch.apply(V[:, 0])
+    yield 0, state(0, beta, piv, False)
 
-    k_done, breakdown = 0, False
     for j in range(k_max):
         u = apply_A(V[:, j])
         Zd[:, j] = sketch.apply(u)
@@ -98,11 +100,10 @@ def run(apply_A, b, sketch, k_max: int, forced_pivots=None) -> HessenbergState:
             H[ii, j] = u[piv[ii]]
             u = u - H[ii, j] * V[:, ii]
         assert not np.any(u[is_piv]), "elimination left a nonzero on a pivot row"
-        k_done = j + 1
         if j + 1 >= n or not np.any(u):
             H[j + 1, j] = 0.0
-            breakdown = True
-            break
+            yield j + 1, state(j + 1, beta, piv, True)
+            return
         if forced_pivots is not None and j + 1 < len(forced_pivots):
             p = int(forced_pivots[j + 1])
         else:
@@ -113,9 +114,20 @@ def run(apply_A, b, sketch, k_max: int, forced_pivots=None) -> HessenbergState:
         piv.append(p)
         is_piv[p] = True
         SV[:, j + 1] = sketch.apply(V[:, j + 1])
-    k = k_done
-    return HessenbergState(V[:, :k + 1], H[:k + 1, :k], piv, SV[:, :k + 1], Zd[:, :k], c,
-                           beta, k, breakdown, gaps)
+        yield j + 1, state(j + 1, beta, piv, False)
+
+
+def run(apply_A, b, sketch, k_max: int, forced_pivots=None) -> HessenbergState:
+    """k_max steps of the pivoted Hessenberg process with sketch S.
+
+    forced_pivots: optional sequence of rows to use as p_1, p_2, ... instead
+    of the max-|.| choice (replays another run's pivot order when two
+    candidates are within rounding of each other).
+    """
+    st = None
+    for _, st in iterate(apply_A, b, sketch, k_max, forced_pivots):
+        pass
+    return st
 
 
 def _lstsq_qr(M: np.ndarray, rhs: np.ndarray) -> np.ndarray:

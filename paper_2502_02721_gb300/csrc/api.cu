@@ -1,0 +1,764 @@
+// Host side of the C ABI declared in include/ipf.h: contexts, device memory,
+// the per-step launch sequence (captured once in a CUDA graph and replayed),
+// the projected solve, state export, and the standalone operator and sketch
+// calls.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ipf_internal.cuh"
+
+using namespace ipf;
+
+namespace {
+
+constexpr int kLamChunk = 16;
+
+size_t storage_bytes(int storage) {
+    switch (storage) {
+        case IPF_STORE_F64: return 8;
+        case IPF_STORE_F32: return 4;
+        default: return 2;
+    }
+}
+
+int device_sms() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+    return sms > 0 ? sms : 1;
+}
+
+bool pow2_le32(int b) { return b >= 1 && b <= 32 && (b & (b - 1)) == 0; }
+
+long long op_n(const ipf_operator* op) {
+    if (op->kind == IPF_OP_CSR) return op->cols;
+    return (long long)op->rows * op->cols;
+}
+
+struct Alloc {
+    ipf_alloc_fn fa = nullptr;
+    ipf_free_fn ff = nullptr;
+    void* user = nullptr;
+    std::vector<void*> live;
+    cudaError_t get(void** p, size_t bytes) {
+        bytes = (bytes + 255) & ~(size_t)255;
+        if (bytes == 0) bytes = 256;
+        if (fa) {
+            *p = fa(bytes, user);
+            if (!*p) return cudaErrorMemoryAllocation;
+        } else {
+            cudaError_t e = cudaMalloc(p, bytes);
+            if (e != cudaSuccess) return e;
+        }
+        live.push_back(*p);
+        return cudaSuccess;
+    }
+    void release() {
+        for (void* p : live) {
+            if (ff) ff(p, user);
+            else cudaFree(p);
+        }
+        live.clear();
+    }
+};
+
+std::string fmt_cuda(const char* what, cudaError_t e) {
+    return std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+}
+
+// operator validation shared by ipf_create and ipf_op_create
+ipf_status check_op(const ipf_operator* op, int nrhs, std::string* why) {
+    if (!op) { *why = "operator is NULL"; return IPF_ERR_ARG; }
+    if (op->rows <= 0 || op->cols <= 0) { *why = "operator rows/cols must be positive"; return IPF_ERR_ARG; }
+    if (op->mem != IPF_MEM_HOST && op->mem != IPF_MEM_DEVICE) { *why = "operator mem flag"; return IPF_ERR_ARG; }
+    switch (op->kind) {
+        case IPF_OP_PSF2D:
+            if (!op->psf || op->ph <= 0 || op->pw <= 0 || !(op->ph & 1) || !(op->pw & 1) || op->ph > 63 || op->pw > 63) {
+                *why = "PSF2D needs an odd ph x pw PSF, sizes <= 63"; return IPF_ERR_ARG;
+            }
+            if (nrhs != 1) { *why = "PSF operators take one right-hand side per context"; return IPF_ERR_UNSUPPORTED; }
+            return IPF_OK;
+        case IPF_OP_PSF2D_SEP_MOTION:
+            if (!op->sep_row || !op->sep_col || !op->motion || op->slen <= 0 || !(op->slen & 1) || op->slen > 63 ||
+                op->mlen <= 0 || !(op->mlen & 1) || op->mlen > 15) {
+                *why = "separable+motion needs odd slen <= 63 and odd mlen <= 15"; return IPF_ERR_ARG;
+            }
+            if (nrhs != 1) { *why = "PSF operators take one right-hand side per context"; return IPF_ERR_UNSUPPORTED; }
+            return IPF_OK;
+        case IPF_OP_CSR:
+            if (!op->rowptr || (op->nnz > 0 && (!op->colind || !op->vals)) || op->nnz < 0) {
+                *why = "CSR needs rowptr, colind, vals"; return IPF_ERR_ARG;
+            }
+            if (op->mem == IPF_MEM_HOST) {
+                // host arrays are checked here so no kernel can index out of bounds;
+                // device arrays are the caller's responsibility (documented in ipf.h)
+                if (op->rowptr[0] != 0 || op->rowptr[op->rows] != op->nnz) {
+                    *why = "CSR rowptr must start at 0 and end at nnz"; return IPF_ERR_ARG;
+                }
+                for (int r = 0; r < op->rows; ++r)
+                    if (op->rowptr[r + 1] < op->rowptr[r]) { *why = "CSR rowptr must be non-decreasing"; return IPF_ERR_ARG; }
+                for (long long t = 0; t < op->nnz; ++t)
+                    if (op->colind[t] < 0 || op->colind[t] >= op->cols) { *why = "CSR column index out of range"; return IPF_ERR_ARG; }
+            }
+            return IPF_OK;
+        default:
+            *why = "unknown operator kind"; return IPF_ERR_ARG;
+    }
+}
+
+// copy an operator to the device; CSR arrays already on the device are referenced
+cudaError_t upload_op(const ipf_operator* op, Alloc& al, OpDev* d, cudaStream_t s) {
+    memset(d, 0, sizeof(*d));
+    d->kind = op->kind;
+    d->rows = op->rows;
+    d->cols = op->cols;
+    const cudaMemcpyKind kind = op->mem == IPF_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    auto dup = [&](const void* src, size_t bytes, const void** dst) -> cudaError_t {
+        void* p = nullptr;
+        cudaError_t e = al.get(&p, bytes);
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpyAsync(p, src, bytes, kind, s);
+        *dst = p;
+        return e;
+    };
+    cudaError_t e = cudaSuccess;
+    if (op->kind == IPF_OP_PSF2D) {
+        d->ph = op->ph; d->pw = op->pw;
+        e = dup(op->psf, sizeof(float) * op->ph * op->pw, (const void**)&d->psf);
+    } else if (op->kind == IPF_OP_PSF2D_SEP_MOTION) {
+        d->slen = op->slen; d->mlen = op->mlen;
+        if ((e = dup(op->sep_row, sizeof(float) * op->slen, (const void**)&d->sep_row)) != cudaSuccess) return e;
+        if ((e = dup(op->sep_col, sizeof(float) * op->slen, (const void**)&d->sep_col)) != cudaSuccess) return e;
+        e = dup(op->motion, sizeof(float) * op->mlen * op->mlen, (const void**)&d->motion);
+    } else {
+        d->nnz = op->nnz;
+        if (op->mem == IPF_MEM_DEVICE) {
+            d->rowptr = op->rowptr; d->colind = op->colind; d->vals = op->vals;
+        } else {
+            if ((e = dup(op->rowptr, sizeof(long long) * (op->rows + 1), (const void**)&d->rowptr)) != cudaSuccess) return e;
+            if ((e = dup(op->colind, sizeof(int) * (op->nnz > 0 ? op->nnz : 1), (const void**)&d->colind)) != cudaSuccess) return e;
+            e = dup(op->vals, sizeof(float) * (op->nnz > 0 ? op->nnz : 1), (const void**)&d->vals);
+        }
+    }
+    return e;
+}
+
+}  // namespace
+
+struct ipf_ctx {
+    ipf_config cfg;
+    OpDev op;
+    Alloc al;
+    int storage = IPF_STORE_F32;
+    int B = 1;
+    Geom g;
+    Bufs bf;
+    SketchParams sp;
+    int num_sms = 1;
+    cudaStream_t s = nullptr;
+    cudaStream_t user = nullptr;
+    cudaEvent_t ev = nullptr;
+    int j_host = 0;                    // Hessenberg steps enqueued
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    ipf_status sticky = IPF_OK;
+    std::string err;
+    void* solve_ws = nullptr;
+    size_t solve_ws_bytes = 0;
+    double* lam_dev = nullptr;
+    float* x_stage = nullptr;          // B*n floats (host output path)
+    float* b_stage = nullptr;          // B*n floats (host b)
+    bool want_sw = false;
+    // profile mode: event pairs recorded around each kernel
+    struct Mark { int kind; double bytes; cudaEvent_t a, b; };
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> spare;
+    double prof_ms[8] = {0};
+    long long prof_n[8] = {0};
+    double prof_bytes[8] = {0};
+};
+
+struct ipf_op {
+    OpDev op;
+    Alloc al;
+};
+
+namespace {
+
+ipf_status fail(ipf_ctx* c, ipf_status st, const std::string& msg) {
+    if (c) {
+        if (c->sticky == IPF_OK) {
+            c->sticky = st;
+            c->err = msg;
+        }
+    }
+    return st;
+}
+
+ipf_status cuda_fail(ipf_ctx* c, const char* what, cudaError_t e) {
+    return fail(c, e == cudaErrorMemoryAllocation ? IPF_ERR_OOM : IPF_ERR_CUDA, fmt_cuda(what, e));
+}
+
+// user stream -> ctx stream ordering
+cudaError_t enter(ipf_ctx* c) {
+    cudaError_t e = cudaEventRecord(c->ev, c->user);
+    if (e != cudaSuccess) return e;
+    return cudaStreamWaitEvent(c->s, c->ev, 0);
+}
+cudaError_t leave(ipf_ctx* c) {
+    cudaError_t e = cudaEventRecord(c->ev, c->s);
+    if (e != cudaSuccess) return e;
+    return cudaStreamWaitEvent(c->user, c->ev, 0);
+}
+
+}  // namespace
+
+namespace {
+
+cudaEvent_t take_event(ipf_ctx* c) {
+    if (!c->spare.empty()) {
+        cudaEvent_t e = c->spare.back();
+        c->spare.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// run one launch, bracketed by events in profile mode
+template <class F>
+cudaError_t timed(ipf_ctx* c, int kind, double bytes, F&& launch) {
+    if (!c->cfg.profile) return launch();
+    ipf_ctx::Mark m{kind, bytes, take_event(c), take_event(c)};
+    cudaError_t e = cudaEventRecord(m.a, c->s);
+    if (e != cudaSuccess) return e;
+    e = launch();
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(m.b, c->s);
+    c->marks.push_back(m);
+    return e;
+}
+
+size_t acc_bytes(const ipf_ctx* c) { return c->storage == IPF_STORE_F64 ? 8 : 4; }
+
+double op_bytes(const ipf_ctx* c) {
+    const double N = (double)c->g.N, sv = (double)storage_bytes(c->storage), ab = (double)acc_bytes(c);
+    double b = N * sv + N * ab;
+    if (c->op.kind == IPF_OP_CSR) b += (double)c->op.nnz * 8.0 + (double)(c->op.rows + 1) * 8.0;
+    return b;
+}
+
+// one Hessenberg step; every kernel takes j from device memory, so the same
+// sequence serves every step and can be captured once.  `j` (host count) is
+// only used to label profile bytes.
+cudaError_t one_step(ipf_ctx* c, int j) {
+    cudaError_t e;
+    const double N = (double)c->g.N, sv = (double)storage_bytes(c->storage), ab = (double)acc_bytes(c);
+    if ((e = timed(c, 0, op_bytes(c), [&] {
+             return launch_op_apply(c->op, c->storage, c->bf.V, c->g.ldv, &c->bf.st->j, c->B, c->bf.w, c->s);
+         })) != cudaSuccess)
+        return e;
+    if ((e = timed(c, 1, 0.0, [&] { return launch_pivot_solve(c->storage, c->g, c->bf, c->s); })) != cudaSuccess)
+        return e;
+    if ((e = timed(c, 2, (double)(j + 1) * N * sv + 2.0 * N * ab + N / 8.0,
+                   [&] { return launch_update(c->storage, c->g, c->bf, c->num_sms, c->s); })) != cudaSuccess)
+        return e;
+    return timed(c, 3, N * ab + N * sv,
+                 [&] { return launch_normalize(c->storage, c->g, c->bf, c->sp, c->want_sw, c->num_sms, c->s); });
+}
+
+// clear the state and enqueue Algorithm 1's initialisation for b
+cudaError_t init_solve(ipf_ctx* c, const float* bdev) {
+    const Geom& g = c->g;
+    const size_t K1 = (size_t)g.k_max + 1;
+    const int B = c->B;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(c->bf.H, 0, B * K1 * g.k_max * sizeof(double), c->s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->bf.ispiv, 0, (g.ldv / 32 + 1) * sizeof(unsigned), c->s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->bf.accSV, 0, B * K1 * g.m_s * sizeof(long long), c->s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->bf.accSW, 0, B * K1 * g.m_s * sizeof(long long), c->s)) != cudaSuccess) return e;
+    return timed(c, 4, 0.0, [&] {
+        cudaError_t ee = launch_reset_state(c->bf.st, c->s);
+        if (ee != cudaSuccess) return ee;
+        if ((ee = launch_load_rhs(c->storage, bdev, g, c->bf, c->s)) != cudaSuccess) return ee;
+        if ((ee = launch_update(c->storage, g, c->bf, c->num_sms, c->s)) != cudaSuccess) return ee;
+        return launch_normalize(c->storage, g, c->bf, c->sp, true, c->num_sms, c->s);
+    });
+}
+
+}  // namespace
+
+extern "C" {
+
+void ipf_config_default(ipf_config* cfg) {
+    if (!cfg) return;
+    memset(cfg, 0, sizeof(*cfg));
+    cfg->k_max = 50;
+    cfg->m_s = 200;
+    cfg->zeta = 8;
+    cfg->seed = 1;
+    cfg->storage = IPF_STORE_F32;
+    cfg->penalty = IPF_PEN_SKETCHED_X;
+    cfg->zform = IPF_Z_DIRECT;
+    cfg->nrhs = 1;
+    cfg->use_graphs = 1;
+}
+
+static size_t ldv_for(long long N) { return (size_t)((N + 63) / 64 * 64); }
+
+static int lam_chunk(int B) { return B >= kLamChunk ? 1 : kLamChunk / B; }
+static size_t solve_ws_for(const Geom& g) { return solve_workspace_bytes(g, lam_chunk(g.B)); }
+
+size_t ipf_footprint(const ipf_operator* op, const ipf_config* cfg) {
+    if (!op || !cfg) return 0;
+    const long long n = op_n(op);
+    const int B = cfg->nrhs > 0 ? cfg->nrhs : 1;
+    const size_t sb = storage_bytes(cfg->storage);
+    const size_t acc = cfg->storage == IPF_STORE_F64 ? 8 : 4;
+    const size_t ldv = ldv_for(n * B);
+    const size_t K1 = (size_t)cfg->k_max + 1;
+    size_t bytes = K1 * ldv * sb + ldv * acc + ldv / 8 + 4096;
+    bytes += B * K1 * (sizeof(int) + sizeof(double) * cfg->k_max + acc * K1) + K1 * B * acc;
+    bytes += 2 * (size_t)B * K1 * cfg->m_s * 8;
+    Geom g; g.n = n; g.B = B; g.N = n * B; g.ldv = (long long)ldv; g.k_max = cfg->k_max; g.m_s = cfg->m_s; g.F = 0;
+    bytes += solve_ws_for(g) + 2 * (size_t)B * n * 4 + 256;
+    if (op->kind == IPF_OP_CSR && op->mem == IPF_MEM_HOST)
+        bytes += (size_t)(op->rows + 1) * 8 + (size_t)op->nnz * 8;
+    else if (op->kind == IPF_OP_PSF2D)
+        bytes += (size_t)op->ph * op->pw * 4;
+    return bytes;
+}
+
+ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const ipf_config* cfg_in, ipf_ctx** out) {
+    if (!out) return IPF_ERR_ARG;
+    *out = nullptr;
+    if (!cfg_in || !b) return IPF_ERR_ARG;
+    ipf_config cfg = *cfg_in;
+    std::string why;
+    const int B = cfg.nrhs;
+    if (!pow2_le32(B)) return IPF_ERR_ARG;
+    ipf_status st = check_op(op, B, &why);
+    if (st != IPF_OK) return st;
+    if (op->kind == IPF_OP_CSR && op->rows != op->cols) return IPF_ERR_UNSUPPORTED;   // square A (sCMRH)
+    if (cfg.k_max < 1 || cfg.zeta < 1 || cfg.zeta > 16 || cfg.m_s < cfg.zeta || cfg.m_s > 65536) return IPF_ERR_ARG;
+    if (cfg.storage < IPF_STORE_F64 || cfg.storage > IPF_STORE_F16) return IPF_ERR_ARG;
+    if (cfg.storage == IPF_STORE_F64 && B != 1) return IPF_ERR_UNSUPPORTED;
+    if (cfg.penalty != IPF_PEN_SKETCHED_X && cfg.penalty != IPF_PEN_Y) return IPF_ERR_ARG;
+    if (cfg.zform != IPF_Z_DIRECT && cfg.zform != IPF_Z_HESSENBERG) return IPF_ERR_ARG;
+    if (b_mem != IPF_MEM_HOST && b_mem != IPF_MEM_DEVICE) return IPF_ERR_ARG;
+    const size_t accb = cfg.storage == IPF_STORE_F64 ? 8 : 4;
+    const size_t pivsmem = (size_t)(cfg.k_max + 2) * 8 + (size_t)cfg.k_max * (cfg.k_max + 1) / 2 * accb;
+    if (pivsmem > 220 * 1024) return IPF_ERR_UNSUPPORTED;
+    const long long n = op_n(op);
+    if (n * B >= (1ll << 32)) return IPF_ERR_UNSUPPORTED;
+
+    ipf_ctx* c = new ipf_ctx();
+    c->cfg = cfg;
+    c->storage = cfg.storage;
+    c->B = B;
+    c->al.fa = cfg.alloc;
+    c->al.ff = cfg.free;
+    c->al.user = cfg.alloc_user;
+    c->user = (cudaStream_t)cfg.stream;
+    c->num_sms = device_sms();
+    c->want_sw = cfg.storage == IPF_STORE_BF16 || cfg.storage == IPF_STORE_F16;
+    cudaError_t e;
+#define CK(what, expr)                                              \
+    do {                                                            \
+        e = (expr);                                                 \
+        if (e != cudaSuccess) {                                     \
+            ipf_status code = cuda_fail(c, what, e);                \
+            ipf_destroy(c);                                         \
+            return code;                                            \
+        }                                                           \
+    } while (0)
+    CK("stream", cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking));
+    CK("event", cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming));
+    CK("order", enter(c));
+    CK("operator upload", upload_op(op, c->al, &c->op, c->s));
+
+    Geom& g = c->g;
+    g.n = n;
+    g.B = B;
+    g.N = n * B;
+    g.ldv = (long long)ldv_for(g.N);
+    g.k_max = cfg.k_max;
+    g.m_s = cfg.m_s;
+    g.F = fixed_exponent(n, 0);
+    c->sp = make_sketch_params(cfg.seed, cfg.m_s, cfg.zeta);
+    const size_t K1 = (size_t)cfg.k_max + 1;
+    const size_t sb = storage_bytes(cfg.storage);
+    Bufs& bf = c->bf;
+    CK("alloc V", c->al.get(&bf.V, K1 * g.ldv * sb));
+    CK("alloc w", c->al.get(&bf.w, g.ldv * accb));
+    CK("alloc state", c->al.get((void**)&bf.st, sizeof(DevState)));
+    CK("alloc piv", c->al.get((void**)&bf.piv, B * K1 * sizeof(int)));
+    CK("alloc H", c->al.get((void**)&bf.H, B * K1 * cfg.k_max * sizeof(double)));
+    CK("alloc Lp", c->al.get(&bf.LpT, B * K1 * K1 * accb));
+    CK("alloc coef", c->al.get(&bf.coef, K1 * B * accb));
+    CK("alloc ispiv", c->al.get((void**)&bf.ispiv, (g.ldv / 32 + 1) * sizeof(unsigned)));
+    CK("alloc SV", c->al.get((void**)&bf.accSV, B * K1 * cfg.m_s * sizeof(long long)));
+    CK("alloc SW", c->al.get((void**)&bf.accSW, B * K1 * cfg.m_s * sizeof(long long)));
+    c->solve_ws_bytes = solve_ws_for(g);
+    CK("alloc solve", c->al.get(&c->solve_ws, c->solve_ws_bytes));
+    CK("alloc lambdas", c->al.get((void**)&c->lam_dev, sizeof(double) * kLamChunk));
+    CK("alloc x stage", c->al.get((void**)&c->x_stage, sizeof(float) * (size_t)n * B));
+    CK("alloc b stage", c->al.get((void**)&c->b_stage, sizeof(float) * (size_t)n * B));
+
+    CK("memset V", cudaMemsetAsync(bf.V, 0, K1 * g.ldv * sb, c->s));
+    CK("memset w", cudaMemsetAsync(bf.w, 0, g.ldv * accb, c->s));
+    CK("memset Lp", cudaMemsetAsync(bf.LpT, 0, B * K1 * K1 * accb, c->s));
+    CK("memset piv", cudaMemsetAsync(bf.piv, 0, B * K1 * sizeof(int), c->s));
+    CK("memset coef", cudaMemsetAsync(bf.coef, 0, K1 * B * accb, c->s));
+    const float* bsrc = b;
+    if (b_mem == IPF_MEM_HOST) {
+        CK("b upload", cudaMemcpyAsync(c->b_stage, b, sizeof(float) * (size_t)n * B, cudaMemcpyHostToDevice, c->s));
+        bsrc = c->b_stage;
+    }
+    CK("init", init_solve(c, bsrc));
+    CK("order", leave(c));
+    if (b_mem == IPF_MEM_HOST) CK("sync", cudaStreamSynchronize(c->s));
+#undef CK
+    *out = c;
+    return IPF_OK;
+}
+
+ipf_status ipf_reset(ipf_ctx* c, const float* b, int b_mem) {
+    if (!c || !b) return IPF_ERR_ARG;
+    if (b_mem != IPF_MEM_HOST && b_mem != IPF_MEM_DEVICE) return IPF_ERR_ARG;
+    if (c->sticky == IPF_ERR_NONFINITE) { c->sticky = IPF_OK; c->err.clear(); }
+    if (c->sticky != IPF_OK) return c->sticky;
+    cudaError_t e = enter(c);
+    if (e != cudaSuccess) return cuda_fail(c, "order", e);
+    const float* bsrc = b;
+    if (b_mem == IPF_MEM_HOST) {
+        if ((e = cudaMemcpyAsync(c->b_stage, b, sizeof(float) * (size_t)c->g.n * c->B, cudaMemcpyHostToDevice,
+                                 c->s)) != cudaSuccess)
+            return cuda_fail(c, "b upload", e);
+        bsrc = c->b_stage;
+    }
+    if ((e = init_solve(c, bsrc)) != cudaSuccess) return cuda_fail(c, "init", e);
+    c->j_host = 0;
+    if ((e = leave(c)) != cudaSuccess) return cuda_fail(c, "order", e);
+    return IPF_OK;
+}
+
+ipf_status ipf_profile_read(ipf_ctx* c, double* ms, long long* launches, double* bytes) {
+    if (!c) return IPF_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(c->s);
+    if (e != cudaSuccess) return cuda_fail(c, "sync", e);
+    for (auto& m : c->marks) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, m.a, m.b) == cudaSuccess) {
+            c->prof_ms[m.kind] += t;
+            c->prof_n[m.kind] += 1;
+            c->prof_bytes[m.kind] += m.bytes;
+        }
+        c->spare.push_back(m.a);
+        c->spare.push_back(m.b);
+    }
+    c->marks.clear();
+    for (int k = 0; k < 8; ++k) {
+        if (ms) ms[k] = c->prof_ms[k];
+        if (launches) launches[k] = c->prof_n[k];
+        if (bytes) bytes[k] = c->prof_bytes[k];
+        c->prof_ms[k] = 0.0;
+        c->prof_n[k] = 0;
+        c->prof_bytes[k] = 0.0;
+    }
+    return IPF_OK;
+}
+
+ipf_status ipf_step(ipf_ctx* c, int nsteps, int* k_enqueued) {
+    if (!c) return IPF_ERR_ARG;
+    if (c->sticky != IPF_OK) return c->sticky;
+    if (nsteps < 0) return IPF_ERR_ARG;
+    int todo = nsteps;
+    if (todo > c->g.k_max - c->j_host) todo = c->g.k_max - c->j_host;
+    cudaError_t e = enter(c);
+    if (e != cudaSuccess) return cuda_fail(c, "order", e);
+    for (int t = 0; t < todo; ++t) {
+        if (c->cfg.use_graphs && !c->cfg.profile) {
+            if (!c->gexec) {
+                // first step eagerly (sets kernel attributes), then capture one step
+                if ((e = one_step(c, c->j_host)) != cudaSuccess) return cuda_fail(c, "step", e);
+                ++c->j_host;
+                if (t + 1 >= todo) break;
+                if ((e = cudaStreamBeginCapture(c->s, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+                    return cuda_fail(c, "capture", e);
+                cudaError_t e1 = one_step(c, 0);
+                cudaError_t e2 = cudaStreamEndCapture(c->s, &c->graph);
+                if (e1 != cudaSuccess) return cuda_fail(c, "capture step", e1);
+                if (e2 != cudaSuccess) return cuda_fail(c, "end capture", e2);
+                if ((e = cudaGraphInstantiate(&c->gexec, c->graph, 0)) != cudaSuccess)
+                    return cuda_fail(c, "instantiate", e);
+            }
+            if ((e = cudaGraphLaunch(c->gexec, c->s)) != cudaSuccess) return cuda_fail(c, "graph launch", e);
+        } else {
+            if ((e = one_step(c, c->j_host)) != cudaSuccess) return cuda_fail(c, "step", e);
+        }
+        ++c->j_host;
+    }
+    if ((e = leave(c)) != cudaSuccess) return cuda_fail(c, "order", e);
+    if (k_enqueued) *k_enqueued = c->j_host;
+    return IPF_OK;
+}
+
+static ipf_status read_state(ipf_ctx* c, DevState* h) {
+    cudaError_t e = cudaStreamSynchronize(c->s);
+    if (e != cudaSuccess) return cuda_fail(c, "sync", e);
+    e = cudaMemcpy(h, c->bf.st, sizeof(DevState), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, "state readback", e);
+    return IPF_OK;
+}
+
+static ipf_status worst(const DevState& h, int B) {
+    ipf_status w = IPF_OK;
+    for (int r = 0; r < B; ++r) {
+        const int s = h.status[r];
+        if (s < 0) return (ipf_status)s;
+        if (s == IPF_BREAKDOWN) w = IPF_BREAKDOWN;
+    }
+    return w;
+}
+
+ipf_status ipf_sync(ipf_ctx* c, int* k_done) {
+    if (!c) return IPF_ERR_ARG;
+    if (c->sticky != IPF_OK) return c->sticky;
+    DevState h;
+    ipf_status st = read_state(c, &h);
+    if (st != IPF_OK) return st;
+    int errflag = 0;
+    cudaError_t e = solve_error_flag(c->solve_ws, c->g, &errflag);
+    if (e != cudaSuccess) return cuda_fail(c, "solve flag", e);
+    if (errflag) return fail(c, IPF_ERR_TIMEOUT, "projected solve: a device-side barrier wait gave up");
+    if (k_done)
+        for (int r = 0; r < c->B; ++r) k_done[r] = h.kdone[r];
+    return worst(h, c->B);
+}
+
+ipf_status ipf_solve(ipf_ctx* c, int k, const double* lambdas, int nl, float* x_out, int x_mem, ipf_solve_info* info) {
+    if (!c) return IPF_ERR_ARG;
+    if (c->sticky != IPF_OK) return c->sticky;
+    if (k < 0 || nl < 1 || !lambdas || !x_out) return IPF_ERR_ARG;
+    if (x_mem != IPF_MEM_HOST && x_mem != IPF_MEM_DEVICE) return IPF_ERR_ARG;
+    if (k > c->j_host) return IPF_ERR_STATE;
+    for (int l = 0; l < nl; ++l)
+        if (!(lambdas[l] >= 0.0) || !std::isfinite(lambdas[l])) return IPF_ERR_ARG;
+    cudaError_t e = enter(c);
+    if (e != cudaSuccess) return cuda_fail(c, "order", e);
+    const Geom& g = c->g;
+    const int nlm = lam_chunk(c->B);
+    bool any_pos = false;
+    for (int l = 0; l < nl; ++l) any_pos |= lambdas[l] > 0.0;
+    const bool need_T = any_pos && c->cfg.penalty == IPF_PEN_SKETCHED_X;
+    e = timed(c, 5, 0.0, [&] {
+        return launch_solve_prepare(g, c->bf, c->cfg.zeta, k, need_T, c->cfg.zform, c->want_sw, c->solve_ws, nlm,
+                                    c->num_sms, c->s);
+    });
+    if (e != cudaSuccess) return cuda_fail(c, "solve prepare", e);
+    const size_t slice = (size_t)g.n * c->B;
+    const int step = x_mem == IPF_MEM_DEVICE ? nlm : 1;
+    for (int l0 = 0; l0 < nl; l0 += step) {
+        const int nlc = nl - l0 < step ? nl - l0 : step;
+        if ((e = cudaMemcpyAsync(c->lam_dev, lambdas + l0, sizeof(double) * nlc, cudaMemcpyHostToDevice, c->s)) != cudaSuccess)
+            return cuda_fail(c, "lambda upload", e);
+        float* dst = x_mem == IPF_MEM_DEVICE ? x_out + (size_t)l0 * slice : c->x_stage;
+        const double xb = (double)k * g.N * storage_bytes(c->storage) + (double)nlc * g.N * 4.0;
+        e = timed(c, 6, xb, [&] {
+            return launch_solve_lambdas(c->storage, g, c->bf, k, need_T, c->lam_dev, nlc, c->cfg.penalty, c->solve_ws,
+                                        nlm, dst, c->num_sms, c->s);
+        });
+        if (e != cudaSuccess) return cuda_fail(c, "solve", e);
+        if (x_mem == IPF_MEM_HOST) {
+            if ((e = cudaMemcpyAsync(x_out + (size_t)l0 * slice, c->x_stage, sizeof(float) * slice,
+                                     cudaMemcpyDeviceToHost, c->s)) != cudaSuccess)
+                return cuda_fail(c, "x download", e);
+        }
+    }
+    if ((e = leave(c)) != cudaSuccess) return cuda_fail(c, "order", e);
+    if (x_mem == IPF_MEM_DEVICE && !info) return IPF_OK;      // asynchronous form
+    DevState h;
+    ipf_status st = read_state(c, &h);
+    if (st != IPF_OK) return st;
+    int errflag = 0;
+    if ((e = solve_error_flag(c->solve_ws, g, &errflag)) != cudaSuccess) return cuda_fail(c, "solve flag", e);
+    if (errflag) return fail(c, IPF_ERR_TIMEOUT, "projected solve: a device-side barrier wait gave up");
+    if (info)
+        for (int r = 0; r < c->B; ++r) {
+            info[r].k_done = h.kdone[r];
+            info[r].k_used = h.kdone[r] < k ? h.kdone[r] : k;
+            info[r].status = h.status[r];
+            info[r].pad = 0;
+        }
+    return worst(h, c->B);
+}
+
+ipf_status ipf_export(ipf_ctx* c, int r, int* pivots, double* H, double* SV, double* SW, double* beta) {
+    if (!c) return IPF_ERR_ARG;
+    if (c->sticky != IPF_OK) return c->sticky;
+    if (r < 0 || r >= c->B) return IPF_ERR_ARG;
+    DevState h;
+    ipf_status st = read_state(c, &h);
+    if (st != IPF_OK) return st;
+    const size_t K1 = (size_t)c->g.k_max + 1;
+    const int m = c->g.m_s;
+    cudaError_t e = cudaSuccess;
+    if (pivots) {
+        std::vector<int> p(K1);
+        e = cudaMemcpy(p.data(), c->bf.piv + r * K1, K1 * sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, "export piv", e);
+        const int kd = h.kdone[r];
+        const int np = (h.status[r] == IPF_BREAKDOWN) ? kd : kd + 1;
+        for (int i = 0; i < (int)K1; ++i) pivots[i] = i < np ? p[i] : -1;
+    }
+    if (H) {
+        e = cudaMemcpy(H, c->bf.H + r * K1 * c->g.k_max, K1 * c->g.k_max * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, "export H", e);
+    }
+    const double scale = std::ldexp(1.0, -c->g.F) / std::sqrt((double)c->cfg.zeta);
+    for (int which = 0; which < 2; ++which) {
+        double* dst = which == 0 ? SV : SW;
+        if (!dst) continue;
+        const long long* src = (which == 0 ? c->bf.accSV : c->bf.accSW) + r * K1 * m;
+        std::vector<long long> a(K1 * m);
+        e = cudaMemcpy(a.data(), src, a.size() * sizeof(long long), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, "export sketch", e);
+        for (size_t t = 0; t < a.size(); ++t) dst[t] = (double)a[t] * scale;
+    }
+    if (beta) *beta = h.beta[r];
+    return IPF_OK;
+}
+
+ipf_status ipf_export_basis(ipf_ctx* c, int r, int j, float* v_out) {
+    if (!c || !v_out) return IPF_ERR_ARG;
+    if (c->sticky != IPF_OK) return c->sticky;
+    if (r < 0 || r >= c->B || j < 0 || j > c->g.k_max) return IPF_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(c->s);
+    if (e != cudaSuccess) return cuda_fail(c, "sync", e);
+    const size_t sb = storage_bytes(c->storage);
+    std::vector<unsigned char> raw((size_t)c->g.ldv * sb);
+    e = cudaMemcpy(raw.data(), (const char*)c->bf.V + (size_t)j * c->g.ldv * sb, raw.size(), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, "export basis", e);
+    const long long n = c->g.n;
+    const int B = c->B;
+    for (long long i = 0; i < n; ++i) {
+        const size_t el = (size_t)i * B + r;
+        float v;
+        switch (c->storage) {
+            case IPF_STORE_F64: v = (float)((const double*)raw.data())[el]; break;
+            case IPF_STORE_F32: v = ((const float*)raw.data())[el]; break;
+            case IPF_STORE_BF16: {
+                const unsigned short u = ((const unsigned short*)raw.data())[el];
+                const unsigned w = (unsigned)u << 16;
+                memcpy(&v, &w, 4);
+                break;
+            }
+            default: {
+                __half hv;
+                memcpy(&hv, (const unsigned short*)raw.data() + el, 2);
+                v = __half2float(hv);
+            }
+        }
+        v_out[i] = v;
+    }
+    return IPF_OK;
+}
+
+void ipf_destroy(ipf_ctx* c) {
+    if (!c) return;
+    if (c->s) cudaStreamSynchronize(c->s);
+    for (auto& m : c->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
+    for (auto ev : c->spare) cudaEventDestroy(ev);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->al.release();
+    if (c->ev) cudaEventDestroy(c->ev);
+    if (c->s) cudaStreamDestroy(c->s);
+    delete c;
+}
+
+const char* ipf_status_str(ipf_status s) {
+    switch (s) {
+        case IPF_OK: return "IPF_OK";
+        case IPF_BREAKDOWN: return "IPF_BREAKDOWN";
+        case IPF_PENDING: return "IPF_PENDING";
+        case IPF_ERR_ARG: return "IPF_ERR_ARG";
+        case IPF_ERR_OOM: return "IPF_ERR_OOM";
+        case IPF_ERR_CUDA: return "IPF_ERR_CUDA";
+        case IPF_ERR_NONFINITE: return "IPF_ERR_NONFINITE";
+        case IPF_ERR_TIMEOUT: return "IPF_ERR_TIMEOUT";
+        case IPF_ERR_STATE: return "IPF_ERR_STATE";
+        case IPF_ERR_UNSUPPORTED: return "IPF_ERR_UNSUPPORTED";
+        case IPF_ERR_REJECTED: return "IPF_ERR_REJECTED";
+        default: return "IPF_UNKNOWN";
+    }
+}
+
+const char* ipf_last_error(const ipf_ctx* c) {
+    if (!c) return "no context";
+    return c->err.c_str();
+}
+
+ipf_status ipf_op_create(const ipf_operator* op, ipf_op** out) {
+    if (!out) return IPF_ERR_ARG;
+    *out = nullptr;
+    std::string why;
+    ipf_status st = check_op(op, 1, &why);
+    if (st != IPF_OK) return st;
+    ipf_op* h = new ipf_op();
+    cudaError_t e = upload_op(op, h->al, &h->op, nullptr);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+    if (e != cudaSuccess) {
+        h->al.release();
+        delete h;
+        return e == cudaErrorMemoryAllocation ? IPF_ERR_OOM : IPF_ERR_CUDA;
+    }
+    *out = h;
+    return IPF_OK;
+}
+
+ipf_status ipf_op_apply(ipf_op* h, const float* v_dev, float* w_dev, int nrhs, void* stream) {
+    if (!h || !v_dev || !w_dev || nrhs < 1) return IPF_ERR_ARG;
+    if (h->op.kind != IPF_OP_CSR && nrhs > 1) {
+        // one product per vector
+    }
+    if (h->op.kind == IPF_OP_CSR && !pow2_le32(nrhs) && nrhs != 1) return IPF_ERR_ARG;
+    cudaError_t e = launch_op_apply_f32_plain(h->op, v_dev, w_dev, nrhs, (cudaStream_t)stream);
+    return e == cudaSuccess ? IPF_OK : IPF_ERR_CUDA;
+}
+
+void ipf_op_destroy(ipf_op* h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    h->al.release();
+    delete h;
+}
+
+ipf_status ipf_sketch_apply(const float* x_dev, long long n, int m_s, int zeta, unsigned long long seed, double* y_dev,
+                            void* stream) {
+    if (!x_dev || !y_dev || n < 1 || zeta < 1 || zeta > 16 || m_s < zeta) return IPF_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int sms = device_sms();
+    SketchParams sp = make_sketch_params(seed, m_s, zeta);
+    void* scratch = nullptr;
+    const size_t bytes = 256 + sizeof(long long) * (size_t)m_s;
+    cudaError_t e = cudaMallocAsync(&scratch, bytes, s);
+    if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? IPF_ERR_OOM : IPF_ERR_CUDA;
+    unsigned* amax = (unsigned*)scratch;
+    long long* acc = (long long*)((char*)scratch + 256);
+    e = cudaMemsetAsync(scratch, 0, bytes, s);
+    if (e == cudaSuccess) e = launch_sketch_vector(x_dev, n, sp, 0, acc, (float*)amax, s, sms, true);
+    if (e == cudaSuccess) e = launch_sketch_finish(acc, m_s, n, zeta, amax, y_dev, s);
+    cudaError_t e2 = cudaFreeAsync(scratch, s);
+    if (e != cudaSuccess || e2 != cudaSuccess) return IPF_ERR_CUDA;
+    return IPF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,261 @@
+// Internal definitions shared by the libipf translation units: storage
+// types, the sparse-sign counter hash, exact fixed-point sketch
+// accumulation, argmax keys and the launcher prototypes.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "../../include/ipf.h"
+
+namespace ipf {
+
+// ---------------------------------------------------------------------------
+// storage types: T is how basis vectors live in HBM, Acc the arithmetic type
+// ---------------------------------------------------------------------------
+template <class T> struct AccOf { using type = float; };
+template <> struct AccOf<double> { using type = double; };
+
+__device__ __forceinline__ float to_acc(float x) { return x; }
+__device__ __forceinline__ double to_acc(double x) { return x; }
+__device__ __forceinline__ float to_acc(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ float to_acc(__half x) { return __half2float(x); }
+
+template <class T> __device__ __forceinline__ T from_acc(float x);
+template <> __device__ __forceinline__ float from_acc<float>(float x) { return x; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_acc<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <> __device__ __forceinline__ __half from_acc<__half>(float x) { return __float2half_rn(x); }
+template <class T> __device__ __forceinline__ T from_acc(double x);
+template <> __device__ __forceinline__ double from_acc<double>(double x) { return x; }
+
+// ---------------------------------------------------------------------------
+// sparse-sign sketch: column i has one +-1/sqrt(zeta) entry in each of zeta
+// disjoint row blocks.  Row and sign come from SplitMix64 (Steele, Lea &
+// Flood 2014): output number c of the generator started at `seed` is
+// mix(seed + GAMMA*(c+1)); column i uses outputs W*i .. W*i+W-1,
+// W = ceil(24*zeta/64), read as one little-endian bit string whose bits
+// [24t, 24t+24) give block t: sign = bit 0 (1 = negative), r = the other
+// 23 bits, row = lo_t + (r * size_t) >> 23 with lo_t = floor(t*m/zeta).
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kGamma = 0x9E3779B97F4A7C15ull;
+
+__host__ __device__ __forceinline__ unsigned long long sm64_mix(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+struct SketchParams {
+    unsigned long long seed;
+    int m_s;
+    int zeta;
+    int W;                   // 64-bit words per column
+    int lo[17];              // block starts, lo[zeta] = m_s
+};
+
+inline SketchParams make_sketch_params(unsigned long long seed, int m_s, int zeta) {
+    SketchParams p;
+    p.seed = seed;
+    p.m_s = m_s;
+    p.zeta = zeta;
+    p.W = (24 * zeta + 63) / 64;
+    for (int t = 0; t <= zeta; ++t) p.lo[t] = (int)(((long long)t * m_s) / zeta);
+    for (int t = zeta + 1; t <= 16; ++t) p.lo[t] = m_s;
+    return p;
+}
+
+// rows[t], neg[t] for column i (t < zeta <= 16)
+__device__ __forceinline__ void sketch_column(const SketchParams& sp, long long i, int* rows,
+                                              unsigned* negmask) {
+    unsigned long long w[6];
+    const unsigned long long base = (unsigned long long)i * (unsigned long long)sp.W;
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+        if (q < sp.W) w[q] = sm64_mix(sp.seed + kGamma * (base + q + 1));
+    unsigned nm = 0;
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+        if (t < sp.zeta) {
+            const int bit = 24 * t, q = bit >> 6, off = bit & 63;
+            unsigned long long ch = w[q] >> off;
+            if (off > 40) ch |= w[q + 1] << (64 - off);
+            ch &= 0xFFFFFFull;
+            nm |= (unsigned)(ch & 1ull) << t;
+            const long long r = (long long)(ch >> 1);
+            const int size = sp.lo[t + 1] - sp.lo[t];
+            rows[t] = sp.lo[t] + (int)((r * size) >> 23);
+        }
+    }
+    *negmask = nm;
+}
+
+// Specialisation for the common zeta = 8 (3 words, fixed chunk offsets).
+__device__ __forceinline__ void sketch_column8(const SketchParams& sp, long long i, int* rows,
+                                               unsigned* negmask) {
+    const unsigned long long base = (unsigned long long)i * 3ull;
+    const unsigned long long w0 = sm64_mix(sp.seed + kGamma * (base + 1));
+    const unsigned long long w1 = sm64_mix(sp.seed + kGamma * (base + 2));
+    const unsigned long long w2 = sm64_mix(sp.seed + kGamma * (base + 3));
+    unsigned long long ch[8];
+    ch[0] = w0;
+    ch[1] = w0 >> 24;
+    ch[2] = (w0 >> 48) | (w1 << 16);
+    ch[3] = w1 >> 8;
+    ch[4] = w1 >> 32;
+    ch[5] = (w1 >> 56) | (w2 << 8);
+    ch[6] = w2 >> 16;
+    ch[7] = w2 >> 40;
+    unsigned nm = 0;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const unsigned c = (unsigned)(ch[t] & 0xFFFFFFull);
+        nm |= (c & 1u) << t;
+        const int size = sp.lo[t + 1] - sp.lo[t];
+        rows[t] = sp.lo[t] + (int)(((unsigned long long)(c >> 1) * (unsigned)size) >> 23);
+    }
+    *negmask = nm;
+}
+
+// ---------------------------------------------------------------------------
+// exact sketch sums: each contribution is rounded once to a 64-bit fixed
+// point value x * 2^F (F chosen per call so no sum can overflow), then all
+// additions are integer and therefore independent of their order.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long fixed_from(float v, int F) {
+    const unsigned u = __float_as_uint(v);
+    const int e = (int)((u >> 23) & 0xFFu);
+    if (e == 0) return 0;
+    const long long m = (long long)((u & 0x7FFFFFu) | 0x800000u);
+    const int sh = e - 150 + F;
+    long long q;
+    if (sh >= 0) q = m << (sh > 38 ? 38 : sh);
+    else if (sh > -26) q = (m + (1ll << (-sh - 1))) >> (-sh);
+    else q = 0;
+    return (u >> 31) ? -q : q;
+}
+
+__device__ __forceinline__ long long fixed_from(double v, int F) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((u >> 52) & 0x7FFull);
+    if (e == 0) return 0;
+    const long long m = (long long)((u & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
+    const int sh = e - 1075 + F;
+    long long q;
+    if (sh >= 0) q = m << (sh > 9 ? 9 : sh);
+    else if (sh > -55) q = (m + (1ll << (-sh - 1))) >> (-sh);
+    else q = 0;
+    return (u >> 63) ? -q : q;
+}
+
+// fixed-point exponent for sums of at most `count` terms of magnitude <= 2^e_max
+inline int fixed_exponent(long long count, int e_max) {
+    int lg = 0;
+    while ((1ll << lg) < count + 1) ++lg;
+    return 61 - lg - e_max;
+}
+
+// ---------------------------------------------------------------------------
+// argmax keys (float arithmetic): |w| bits in the high word, ~row in the low
+// word, so the max key is the largest |w| with the lowest row on ties.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long argmax_key(float w, unsigned row) {
+    return ((unsigned long long)__float_as_uint(fabsf(w)) << 32) | (unsigned long long)(0xFFFFFFFFu - row);
+}
+__device__ __forceinline__ unsigned key_row(unsigned long long k) { return 0xFFFFFFFFu - (unsigned)(k & 0xFFFFFFFFull); }
+__device__ __forceinline__ float key_absval(unsigned long long k) { return __uint_as_float((unsigned)(k >> 32)); }
+
+// ---------------------------------------------------------------------------
+// device-side state of one context (one batch of nrhs right-hand sides)
+// ---------------------------------------------------------------------------
+constexpr int kMaxRhs = 32;
+
+struct DevState {
+    int j;                         // current step: basis v_0..v_{j} exists (j = -1 before init)
+    unsigned ctr;                  // last-CTA ticket for the normalise kernel
+    int status[kMaxRhs];           // per RHS: IPF_OK, IPF_BREAKDOWN, IPF_ERR_NONFINITE
+    int kdone[kMaxRhs];            // completed Hessenberg steps per RHS
+    double beta[kMaxRhs];          // b(p_1)
+    unsigned long long key[2][kMaxRhs];      // argmax keys, double-buffered by step parity
+    unsigned long long maxbits[2];           // F64 mode: max |w| bits (nrhs == 1)
+    unsigned long long minidx[2];            // F64 mode: lowest row attaining it
+};
+
+// everything a kernel needs about the context, passed by value
+struct Geom {
+    long long n;        // unknowns per RHS
+    int B;              // RHS count (interleaved, element e = i*B + r)
+    long long N;        // n * B
+    long long ldv;      // stride between basis vectors (elements), multiple of 64
+    int k_max;
+    int m_s;
+    int F;              // fixed-point exponent of the sketch accumulators
+};
+
+struct Bufs {
+    void* V;                       // (k_max+1) x ldv storage-type basis
+    void* w;                       // ldv Acc work vector (u in Algorithm 1)
+    DevState* st;
+    int* piv;                      // [B][k_max+1]
+    double* H;                     // [B][(k_max+1)*k_max], column-major
+    void* LpT;                     // [B][(k_max+1)^2] Acc, L_p column-major (col c, row i)
+    void* coef;                    // [(k_max+1)*B] Acc, h for the update
+    unsigned* ispiv;               // bitmap over N elements
+    long long* accSV;              // [B][k_max+1][m_s] fixed-point S V
+    long long* accSW;              // [B][k_max+1][m_s] fixed-point S (u/H) before rounding
+};
+
+// operator on the device
+struct OpDev {
+    int kind;
+    int rows, cols;
+    int ph, pw;
+    const float* psf;
+    int slen;
+    const float* sep_row;
+    const float* sep_col;
+    int mlen;
+    const float* motion;
+    const long long* rowptr;
+    const int* colind;
+    const float* vals;
+    long long nnz;
+    float absmax;                  // ||A||_inf bound (max row sum of |a|)
+};
+
+// ---------------------------------------------------------------------------
+// launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+// k_ops.cu
+// vbase + (*jptr) * ldv is the input vector (jptr NULL: vbase itself)
+cudaError_t launch_op_apply(const OpDev& op, int storage, const void* vbase, long long ldv, const int* jptr, int B,
+                            void* w, cudaStream_t s);
+cudaError_t launch_op_apply_f32_plain(const OpDev& op, const float* v, float* w, int nrhs,
+                                      cudaStream_t s);
+// k_hess.cu
+cudaError_t launch_reset_state(DevState* st, cudaStream_t s);
+cudaError_t launch_load_rhs(int storage, const float* b, const Geom& g, const Bufs& bf, cudaStream_t s);
+cudaError_t launch_pivot_solve(int storage, const Geom& g, const Bufs& bf, cudaStream_t s);
+cudaError_t launch_update(int storage, const Geom& g, const Bufs& bf, int num_sms, cudaStream_t s);
+cudaError_t launch_normalize(int storage, const Geom& g, const Bufs& bf, const SketchParams& sp,
+                             bool want_sw, int num_sms, cudaStream_t s);
+cudaError_t launch_sketch_vector(const float* x, long long n, const SketchParams& sp, int F,
+                                 long long* acc, float* absmax_out, cudaStream_t s, int num_sms,
+                                 bool find_max);
+cudaError_t launch_fixed_to_double(const long long* acc, int m, double scale, double* y, cudaStream_t s);
+cudaError_t launch_sketch_finish(const long long* acc, int m, long long n, int zeta, const unsigned* absmax,
+                                 double* y, cudaStream_t s);
+// k_small.cu: workspace for k <= k_max and up to nl_max lambdas per chunk
+size_t solve_workspace_bytes(const Geom& g, int nl_max);
+// form M = [Z | c] (and T = S V_k) and their R factors
+cudaError_t launch_solve_prepare(const Geom& g, const Bufs& bf, int zeta, int k, bool need_T, int zform,
+                                 bool have_sw, void* work, int nl_max, int num_sms, cudaStream_t s);
+// per lambda: y, then x = V_k y into x_dev ([l][r][n] float32)
+cudaError_t launch_solve_lambdas(int storage, const Geom& g, const Bufs& bf, int k, bool need_T,
+                                 const double* lambdas_dev, int nl, int penalty, void* work, int nl_max,
+                                 float* x_dev, int num_sms, cudaStream_t s);
+// device-side barrier timeout flag of the last prepare (host read, synchronous)
+cudaError_t solve_error_flag(const void* work, const Geom& g, int* flag);
+
+}  // namespace ipf

@@ -1,0 +1,313 @@
+// Forward operators w = A v (A is reached only through products, Sec. 1 of
+// the paper), reading the basis vector in its storage type and accumulating
+// in FP32 (FP64 for F64 storage).
+//
+//   k_conv2d      zero-boundary 2-D convolution with an odd PSF, output tile
+//                 plus halo staged in shared memory, 4x8 outputs per thread
+//                 with the PSF row and the input row segment in registers.
+//   k_sep_motion  separable Gaussian (row pass, column pass), crop to the
+//                 image, then the motion stencil, all in one tile.
+//   k_csr         CSR product for B interleaved right-hand sides: one warp
+//                 per row, lanes grouped by RHS so A is read once for all B.
+#include "ipf_internal.cuh"
+
+namespace ipf {
+
+namespace {
+
+template <class T> __device__ __forceinline__ typename AccOf<T>::type ld_acc(const T* p) { return to_acc(*p); }
+
+// ------------------------------------------------------------------------
+// 2-D convolution.  KW = compile-time padded kernel width (odd), ph rows
+// (runtime, odd).  Tile: TY x TX outputs, 256 threads as 16 x 16, each
+// thread OY x OX = (TY/16) x (TX/16) outputs.
+// ------------------------------------------------------------------------
+template <class T, class Acc, int KW, int OY, int OX>
+__global__ void __launch_bounds__(256) k_conv2d(const T* __restrict__ vbase, long long ldv, const int* __restrict__ jptr,
+                                                 Acc* __restrict__ w, int H, int W,
+                                                 const float* __restrict__ psf, int ph, int pw) {
+    const T* v = jptr ? vbase + (size_t)(*jptr) * ldv : vbase;
+    constexpr int TY = 16 * OY, TX = 16 * OX;
+    constexpr int IW = TX + KW - 1;                  // input tile width
+    constexpr int IWP = (IW + 3) & ~3;
+    extern __shared__ unsigned char smem_raw[];
+    Acc* s_in = (Acc*)smem_raw;                      // (TY + ph - 1) x IWP
+    Acc* s_k = s_in + (size_t)(TY + ph - 1) * IWP;   // ph x KW, flipped, width-padded
+    const int cy = ph / 2, cx = KW / 2;
+    const int y0 = blockIdx.y * TY, x0 = blockIdx.x * TX;
+    const int IH = TY + ph - 1;
+    // flipped, zero-padded kernel: s_k[a][b] multiplies v(y - cy + a, x - cx + b)
+    const int padl = (KW - pw) / 2;
+    for (int t = threadIdx.x; t < ph * KW; t += blockDim.x) {
+        const int a = t / KW, bb = t - a * KW;
+        const int kb = bb - padl;
+        Acc val = 0;
+        if (kb >= 0 && kb < pw) val = (Acc)psf[(ph - 1 - a) * pw + (pw - 1 - kb)];
+        s_k[t] = val;
+    }
+    for (int t = threadIdx.x; t < IH * IWP; t += blockDim.x) {
+        const int a = t / IWP, bb = t - a * IWP;
+        const int yy = y0 - cy + a, xx = x0 - cx + bb;
+        Acc val = 0;
+        if (bb < IW && yy >= 0 && yy < H && xx >= 0 && xx < W) val = ld_acc(v + (size_t)yy * W + xx);
+        s_in[t] = val;
+    }
+    __syncthreads();
+    const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+    const int oy0 = ty * OY, ox0 = tx * OX;
+    Acc acc[OY][OX];
+#pragma unroll
+    for (int a = 0; a < OY; ++a)
+#pragma unroll
+        for (int bb = 0; bb < OX; ++bb) acc[a][bb] = 0;
+    for (int ky = 0; ky < ph; ++ky) {
+        Acc kr[KW];
+#pragma unroll
+        for (int q = 0; q < KW; ++q) kr[q] = s_k[ky * KW + q];
+#pragma unroll
+        for (int a = 0; a < OY; ++a) {
+            const Acc* row = s_in + (size_t)(oy0 + a + ky) * IWP + ox0;
+            Acc in[OX + KW - 1];
+#pragma unroll
+            for (int q = 0; q < OX + KW - 1; ++q) in[q] = row[q];
+#pragma unroll
+            for (int q = 0; q < KW; ++q)
+#pragma unroll
+                for (int bb = 0; bb < OX; ++bb) acc[a][bb] = fma(kr[q], in[bb + q], acc[a][bb]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < OY; ++a) {
+        const int yy = y0 + oy0 + a;
+        if (yy >= H) continue;
+#pragma unroll
+        for (int bb = 0; bb < OX; ++bb) {
+            const int xx = x0 + ox0 + bb;
+            if (xx < W) w[(size_t)yy * W + xx] = acc[a][bb];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
+// separable Gaussian then motion blur, each zero-boundary, fused per tile
+// ------------------------------------------------------------------------
+template <class T, class Acc, int TILE>
+__global__ void __launch_bounds__(256) k_sep_motion(const T* __restrict__ vbase, long long ldv, const int* __restrict__ jptr,
+                                                     Acc* __restrict__ w, int H, int W,
+                                                     const float* __restrict__ grow, const float* __restrict__ gcol,
+                                                     int slen, const float* __restrict__ mot, int mlen) {
+    const T* v = jptr ? vbase + (size_t)(*jptr) * ldv : vbase;
+    extern __shared__ unsigned char smem_raw[];
+    const int hs = slen / 2, hm = mlen / 2;
+    const int hal = hs + hm;
+    const int A0 = TILE + 2 * hal;      // input tile side
+    const int A1 = TILE + 2 * hm;       // after the separable pass
+    Acc* s_in = (Acc*)smem_raw;                      // A0 x A0
+    Acc* s_r = s_in + (size_t)A0 * A0;               // A0 rows x A1 cols (row pass)
+    Acc* s_c = s_r + (size_t)A0 * A1;                // A1 x A1 (column pass, cropped)
+    Acc* s_g = s_c + (size_t)A1 * A1;                // grow (slen), gcol (slen), motion (mlen^2)
+    const int y0 = blockIdx.y * TILE, x0 = blockIdx.x * TILE;
+    for (int t = threadIdx.x; t < slen; t += blockDim.x) {
+        s_g[t] = (Acc)grow[t];
+        s_g[slen + t] = (Acc)gcol[t];
+    }
+    for (int t = threadIdx.x; t < mlen * mlen; t += blockDim.x) s_g[2 * slen + t] = (Acc)mot[t];
+    for (int t = threadIdx.x; t < A0 * A0; t += blockDim.x) {
+        const int a = t / A0, bb = t - a * A0;
+        const int yy = y0 - hal + a, xx = x0 - hal + bb;
+        Acc val = 0;
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W) val = ld_acc(v + (size_t)yy * W + xx);
+        s_in[t] = val;
+    }
+    __syncthreads();
+    // row pass: s_r[a][c] = sum_q grow[q] * in[a][c + 2hs - q]   (c in 0..A1-1 -> x = x0-hm+c)
+    for (int t = threadIdx.x; t < A0 * A1; t += blockDim.x) {
+        const int a = t / A1, c = t - a * A1;
+        const Acc* row = s_in + (size_t)a * A0 + c;
+        Acc s = 0;
+        for (int q = 0; q < slen; ++q) s = fma(s_g[q], row[2 * hs - q], s);
+        s_r[t] = s;
+    }
+    __syncthreads();
+    // column pass, then crop to the image: s_c[a][c] at (y0-hm+a, x0-hm+c)
+    for (int t = threadIdx.x; t < A1 * A1; t += blockDim.x) {
+        const int a = t / A1, c = t - a * A1;
+        const int yy = y0 - hm + a, xx = x0 - hm + c;
+        Acc s = 0;
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+            for (int q = 0; q < slen; ++q) s = fma(s_g[slen + q], s_r[(size_t)(a + 2 * hs - q) * A1 + c], s);
+        }
+        s_c[t] = s;
+    }
+    __syncthreads();
+    const Acc* mk = s_g + 2 * slen;
+    for (int t = threadIdx.x; t < TILE * TILE; t += blockDim.x) {
+        const int a = t / TILE, c = t - a * TILE;
+        const int yy = y0 + a, xx = x0 + c;
+        if (yy >= H || xx >= W) continue;
+        Acc s = 0;
+        for (int p = 0; p < mlen; ++p)
+            for (int q = 0; q < mlen; ++q)
+                s = fma(mk[p * mlen + q], s_c[(size_t)(a + 2 * hm - p) * A1 + (c + 2 * hm - q)], s);
+        w[(size_t)yy * W + xx] = s;
+    }
+}
+
+// ------------------------------------------------------------------------
+// CSR, B interleaved right-hand sides, one warp per row.  The summation
+// order does not depend on B: the row's nonzeros are split into 32 classes
+// by (p - rowstart) mod 32, each class is summed in order, and the classes
+// are combined by the butterfly with offsets 16, 8, 4, 2, 1.  With G = 32/B
+// lane groups, lane (g, r) owns classes g + G*u (u < B) of RHS r: offsets
+// >= G pair classes inside a lane, smaller ones pair lanes g and g^o.  A
+// right-hand side therefore gets the same bits alone or in any batch.
+// ------------------------------------------------------------------------
+template <class T, class Acc, int B>
+__global__ void __launch_bounds__(256) k_csr(const long long* __restrict__ rowptr, const int* __restrict__ colind,
+                                              const float* __restrict__ vals, long long m,
+                                              const T* __restrict__ vbase, long long ldv,
+                                              const int* __restrict__ jptr, Acc* __restrict__ w) {
+    const T* v = jptr ? vbase + (size_t)(*jptr) * ldv : vbase;
+    constexpr int G = 32 / B;
+    const int lane = threadIdx.x & 31;
+    const int g = lane / B, rr = lane - g * B;
+    const long long warps = (long long)gridDim.x * (blockDim.x / 32);
+    for (long long row = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; row < m; row += warps) {
+        const long long s = rowptr[row], e = rowptr[row + 1];
+        Acc P[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) P[u] = 0;
+        for (long long base = s; base < e; base += 32) {
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+                const long long p = base + g + G * u;
+                if (p < e) P[u] = fma((Acc)vals[p], to_acc(v[(size_t)colind[p] * B + rr]), P[u]);
+            }
+        }
+        // in-lane levels: offsets o = 16 .. G pair classes c, c ^ o (u, u ^ o/G)
+#pragma unroll
+        for (int o = 16; o >= G && o >= 1; o >>= 1) {
+            const int ou = o / G;
+#pragma unroll
+            for (int u = 0; u < B; ++u)
+                if (!(u & ou)) P[u] = P[u] + P[u ^ ou];
+        }
+        Acc acc = P[0];
+        // cross-lane levels: offsets o < G pair groups g, g ^ o
+#pragma unroll
+        for (int o = (G >= 2 ? G / 2 : 0); o >= 1; o >>= 1) acc = acc + __shfl_xor_sync(0xffffffffu, acc, o * B);
+        if (g == 0) w[(size_t)row * B + rr] = acc;
+    }
+}
+
+template <class T, class Acc>
+cudaError_t conv_dispatch(const OpDev& op, const T* v, long long ldv, const int* jp, Acc* w, cudaStream_t s) {
+    const int H = op.rows, W = op.cols;
+    auto go = [&](auto kern, int KW, int TY, int TX) -> cudaError_t {
+        const int IWP = (TX + KW - 1 + 3) & ~3;
+        const size_t smem = ((size_t)(TY + op.ph - 1) * IWP + (size_t)op.ph * KW) * sizeof(Acc);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        dim3 grid((W + TX - 1) / TX, (H + TY - 1) / TY);
+        kern<<<grid, 256, smem, s>>>(v, ldv, jp, w, H, W, op.psf, op.ph, op.pw);
+        return cudaGetLastError();
+    };
+    const int mx = op.pw;
+    if (mx <= 7) return go(k_conv2d<T, Acc, 7, 2, 4>, 7, 32, 64);
+    if (mx <= 15) return go(k_conv2d<T, Acc, 15, 4, 8>, 15, 64, 128);
+    if (mx <= 31) return go(k_conv2d<T, Acc, 31, 4, 8>, 31, 64, 128);
+    return go(k_conv2d<T, Acc, 63, 2, 4>, 63, 32, 64);
+}
+
+template <class T, class Acc>
+cudaError_t sep_dispatch(const OpDev& op, const T* v, long long ldv, const int* jp, Acc* w, cudaStream_t s) {
+    constexpr int TILE = 32;
+    const int hal = op.slen / 2 + op.mlen / 2;
+    const int A0 = TILE + 2 * hal, A1 = TILE + 2 * (op.mlen / 2);
+    const size_t smem = ((size_t)A0 * A0 + (size_t)A0 * A1 + (size_t)A1 * A1 + 2 * op.slen +
+                         (size_t)op.mlen * op.mlen) * sizeof(Acc);
+    auto kern = k_sep_motion<T, Acc, TILE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((op.cols + TILE - 1) / TILE, (op.rows + TILE - 1) / TILE);
+    kern<<<grid, 256, smem, s>>>(v, ldv, jp, w, op.rows, op.cols, op.sep_row, op.sep_col, op.slen, op.motion, op.mlen);
+    return cudaGetLastError();
+}
+
+template <class T, class Acc>
+cudaError_t csr_dispatch(const OpDev& op, const T* v, long long ldv, const int* jp, Acc* w, int B, cudaStream_t s) {
+    const long long m = op.rows;
+    long long blocks = (m + 7) / 8;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    const int nb = (int)blocks;
+    switch (B) {
+        case 1: k_csr<T, Acc, 1><<<nb, 256, 0, s>>>(op.rowptr, op.colind, op.vals, m, v, ldv, jp, w); break;
+        case 2: k_csr<T, Acc, 2><<<nb, 256, 0, s>>>(op.rowptr, op.colind, op.vals, m, v, ldv, jp, w); break;
+        case 4: k_csr<T, Acc, 4><<<nb, 256, 0, s>>>(op.rowptr, op.colind, op.vals, m, v, ldv, jp, w); break;
+        case 8: k_csr<T, Acc, 8><<<nb, 256, 0, s>>>(op.rowptr, op.colind, op.vals, m, v, ldv, jp, w); break;
+        case 16: k_csr<T, Acc, 16><<<nb, 256, 0, s>>>(op.rowptr, op.colind, op.vals, m, v, ldv, jp, w); break;
+        case 32: k_csr<T, Acc, 32><<<nb, 256, 0, s>>>(op.rowptr, op.colind, op.vals, m, v, ldv, jp, w); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t apply_T(const OpDev& op, const void* v, long long ldv, const int* jp, void* w, int B, cudaStream_t s) {
+    using Acc = typename AccOf<T>::type;
+    switch (op.kind) {
+        case IPF_OP_PSF2D: return conv_dispatch<T, Acc>(op, (const T*)v, ldv, jp, (Acc*)w, s);
+        case IPF_OP_PSF2D_SEP_MOTION: return sep_dispatch<T, Acc>(op, (const T*)v, ldv, jp, (Acc*)w, s);
+        case IPF_OP_CSR: return csr_dispatch<T, Acc>(op, (const T*)v, ldv, jp, (Acc*)w, B, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+__global__ void k_interleave(const float* __restrict__ src, float* __restrict__ dst, long long n, int B, int dir) {
+    const long long N = n * B;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+        const long long i = e / B;
+        const int r = (int)(e - i * B);
+        if (dir == 0) dst[e] = src[(size_t)r * n + i];
+        else dst[(size_t)r * n + i] = src[e];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_op_apply(const OpDev& op, int storage, const void* vbase, long long ldv, const int* jptr, int B,
+                            void* w, cudaStream_t s) {
+    switch (storage) {
+        case IPF_STORE_F64: return apply_T<double>(op, vbase, ldv, jptr, w, B, s);
+        case IPF_STORE_F32: return apply_T<float>(op, vbase, ldv, jptr, w, B, s);
+        case IPF_STORE_BF16: return apply_T<__nv_bfloat16>(op, vbase, ldv, jptr, w, B, s);
+        case IPF_STORE_F16: return apply_T<__half>(op, vbase, ldv, jptr, w, B, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// plain float32 vectors, RHS-major (r*n + i), for the standalone apply call
+cudaError_t launch_op_apply_f32_plain(const OpDev& op, const float* v, float* w, int nrhs, cudaStream_t s) {
+    const long long n = (op.kind == IPF_OP_CSR) ? (long long)op.cols : (long long)op.rows * op.cols;
+    if (nrhs == 1 || op.kind != IPF_OP_CSR) {
+        for (int r = 0; r < nrhs; ++r) {
+            cudaError_t e = apply_T<float>(op, v + (size_t)r * n, 0, nullptr, w + (size_t)r * n, 1, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    // CSR with several RHS: interleave into scratch, one product, de-interleave
+    float* tmp = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&tmp, sizeof(float) * (size_t)n * nrhs * 2, s);
+    if (e != cudaSuccess) return e;
+    float* vi = tmp;
+    float* wi = tmp + (size_t)n * nrhs;
+    const int blocks = 1024;
+    k_interleave<<<blocks, 256, 0, s>>>(v, vi, n, nrhs, 0);
+    e = apply_T<float>(op, vi, 0, nullptr, wi, nrhs, s);
+    if (e == cudaSuccess) k_interleave<<<blocks, 256, 0, s>>>(wi, w, n, nrhs, 1);
+    cudaError_t e2 = cudaFreeAsync(tmp, s);
+    return e != cudaSuccess ? e : (e2 != cudaSuccess ? e2 : cudaGetLastError());
+}
+
+}  // namespace ipf

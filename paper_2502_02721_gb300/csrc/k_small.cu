@@ -1,0 +1,414 @@
+// The sketched projected problem (Sec. 3.2 Eq. sketched_LSLU, Sec. 3.3
+// Eq. sketched_LSLU_hybrid, Algorithm 2's last two lines) in FP64, then
+// x_k = V_k y:
+//
+//   k_form          M = [Z | c] with Z = S A V_k (m_s x k) and c = S b;
+//                   T = S V_k when a sketched-x penalty is asked for
+//   k_householder   Householder QR of every M (and T), R only; a
+//                   cooperative launch, a group of CTAs per matrix, one
+//                   column reflector per step, columns owned round-robin
+//   k_small_solve   per (RHS, lambda): lambda = 0 back substitution on R_M;
+//                   lambda > 0 QR of [R_M(:, 1:k); lambda R_T] (two stacked
+//                   upper triangles, structure kept) then back substitution
+//   k_reconstruct   x = V_k y for all lambdas in one pass over V_k
+//
+// ||c - Z y|| = ||R_M(:, k) - R_M(:, 1:k) y|| because M = Q R_M, and
+// ||S V_k y|| = ||R_T y||, so only (k+1)- and k-sized triangles enter the
+// per-lambda work.
+#include "ipf_internal.cuh"
+
+namespace ipf {
+
+namespace {
+
+struct SolveLayout {
+    size_t bar_off, err_off, M_off, T_off, dM_off, dT_off, Y_off, S_off, total;
+};
+
+// workspace for k <= g.k_max and nl_max lambdas; the barrier counters and
+// the error flag sit at fixed offsets at the start
+SolveLayout layout_for(const Geom& g, int nl_max) {
+    SolveLayout L;
+    const size_t k = (size_t)g.k_max;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
+    L.bar_off = take(sizeof(unsigned) * (size_t)g.B * 2);
+    L.err_off = take(sizeof(int) * 4);
+    L.M_off = take(sizeof(double) * (size_t)g.B * g.m_s * (k + 1));
+    L.T_off = take(sizeof(double) * (size_t)g.B * g.m_s * k);
+    L.dM_off = take(sizeof(double) * (size_t)g.B * (k + 1));
+    L.dT_off = take(sizeof(double) * (size_t)g.B * (k + 1));
+    L.Y_off = take(sizeof(double) * (size_t)g.B * nl_max * (k + 1));
+    L.S_off = take(sizeof(double) * (size_t)g.B * nl_max * (2 * k + 1) * (k + 1));
+    L.total = off;
+    return L;
+}
+
+__device__ __forceinline__ int kuse_of(const DevState* st, int r, int k) {
+    const int kd = st->kdone[r];
+    return kd < k ? kd : k;
+}
+
+// M[r][col], T[r][col] (column-major, ld = m)
+__global__ void k_form(Geom g, Bufs bf, int k, int zeta, int use_sw_direct, int need_T, double* Mw, double* Tw) {
+    const int r = blockIdx.y;
+    const int kb = kuse_of(bf.st, r, k);
+    const int K1 = g.k_max + 1;
+    const int m = g.m_s;
+    const double scale = ldexp(1.0, -g.F) / sqrt((double)zeta);
+    const long long* sv = bf.accSV + (size_t)r * K1 * m;
+    const long long* sw = bf.accSW + (size_t)r * K1 * m;
+    const double* H = bf.H + (size_t)r * K1 * g.k_max;
+    double* M = Mw + (size_t)r * m * (k + 1);
+    double* T = Tw ? Tw + (size_t)r * m * k : nullptr;
+    const double beta = bf.st->beta[r];
+    const long long total = (long long)m * (kb + 1);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int col = (int)(t / m), row = (int)(t - (long long)col * m);
+        double val;
+        if (col < kb) {
+            double s = 0.0;
+            const double* Hc = H + (size_t)K1 * col;
+            for (int i = 0; i <= col; ++i) s = fma((double)sv[(size_t)i * m + row] * scale, Hc[i], s);
+            const long long* last = use_sw_direct ? sw : sv;
+            s = fma((double)last[(size_t)(col + 1) * m + row] * scale, Hc[col + 1], s);
+            val = s;
+            if (need_T) T[(size_t)col * m + row] = (double)sv[(size_t)col * m + row] * scale;
+        } else {
+            val = beta * (double)sw[row] * scale;      // c = S b = beta * S (b / beta)
+        }
+        M[(size_t)col * m + row] = val;
+    }
+}
+
+// ------------------------------------------------------------------------
+// cooperative Householder QR (R only).  job = 2*r + which (which 0: M with
+// kb+1 columns, 1: T with kb columns).  cpj CTAs per job.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ double block_sum(double v, double* s_red) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) s_red[wid] = v;
+    __syncthreads();
+    double t = 0.0;
+    const int nw = blockDim.x >> 5;
+    for (int q = 0; q < nw; ++q) t += s_red[q];
+    return t;
+}
+
+__device__ bool job_barrier(unsigned* bar, unsigned target, int* err) {
+    __syncthreads();
+    __shared__ int s_fail;
+    if (threadIdx.x == 0) {
+        s_fail = 0;
+        __threadfence();
+        atomicAdd(bar, 1u);
+        long long spins = 0;
+        while (true) {
+            const unsigned seen = *(volatile unsigned*)bar;
+            if (seen >= target) break;
+            if (*(volatile int*)err) { s_fail = 1; break; }
+            if (++spins > (1ll << 22)) { atomicExch(err, 1); s_fail = 1; break; }
+            __nanosleep(64);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return s_fail == 0;
+}
+
+__global__ void __launch_bounds__(256) k_householder(Geom g, const DevState* st, int k, int need_T, int cpj,
+                                                      double* Mw, double* Tw, double* dM, double* dT,
+                                                      unsigned* bars, int* err) {
+    extern __shared__ unsigned char smem_raw[];
+    double* s_v = (double*)smem_raw;          // m doubles
+    __shared__ double s_red[32];
+    const int jobs_per_rhs = need_T ? 2 : 1;
+    const int job = blockIdx.x / cpj;
+    const int q = blockIdx.x - job * cpj;
+    const int njobs = g.B * jobs_per_rhs;
+    if (job >= njobs) return;
+    const int r = job / jobs_per_rhs, which = job - r * jobs_per_rhs;
+    const int kb = kuse_of(st, r, k);
+    const int m = g.m_s;
+    double* A;
+    double* diag;
+    int ncols;
+    if (which == 0) { A = Mw + (size_t)r * m * (k + 1); diag = dM + (size_t)r * (k + 1); ncols = kb + 1; }
+    else { A = Tw + (size_t)r * m * k; diag = dT + (size_t)r * (k + 1); ncols = kb; }
+    unsigned* bar = bars + job;
+    const int nsteps = ncols < m ? ncols : m;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i = 0; i < nsteps; ++i) {
+        const double* ci = A + (size_t)i * m;
+        double part = 0.0;
+        for (int row = i + threadIdx.x; row < m; row += blockDim.x) {
+            const double x = ci[row];
+            s_v[row] = x;
+            if (row > i) part = fma(x, x, part);
+        }
+        const double sigma = block_sum(part, s_red);
+        const double alpha = s_v[i];
+        double beta, tau, inv;
+        if (sigma == 0.0) { beta = alpha; tau = 0.0; inv = 0.0; }
+        else {
+            const double nrm = sqrt(fma(alpha, alpha, sigma));
+            beta = alpha <= 0.0 ? nrm : -nrm;
+            tau = (beta - alpha) / beta;
+            inv = 1.0 / (alpha - beta);
+        }
+        __syncthreads();
+        for (int row = i + 1 + threadIdx.x; row < m; row += blockDim.x) s_v[row] *= inv;
+        if (threadIdx.x == 0) s_v[i] = 1.0;
+        __syncthreads();
+        if ((i % cpj) == q && threadIdx.x == 0) diag[i] = beta;
+        if (tau != 0.0) {
+            // owned columns j > i: j = q, q + cpj, ...
+            int j0 = q;
+            if (j0 <= i) j0 += ((i - q) / cpj + 1) * cpj;
+            int idx = 0;
+            for (int jc = j0; jc < ncols; jc += cpj, ++idx) {
+                if ((idx % nw) != warp) continue;
+                double* cj = A + (size_t)jc * m;
+                double d = 0.0;
+                for (int row = i + lane; row < m; row += 32) d = fma(s_v[row], cj[row], d);
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+                const double f = tau * d;
+                for (int row = i + lane; row < m; row += 32) cj[row] = fma(-f, s_v[row], cj[row]);
+            }
+        }
+        if (!job_barrier(bar, (unsigned)(i + 1) * cpj, err)) return;
+    }
+    // columns beyond m (never for m_s >= k+1) have no diagonal
+}
+
+// ------------------------------------------------------------------------
+// per (RHS, lambda) small solve
+// ------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_small_solve(Geom g, const DevState* st, int k, int nl, const double* lams,
+                                                      int penalty, const double* Mw, const double* Tw,
+                                                      const double* dM, const double* dT, double* Sw, double* Yw) {
+    const int r = blockIdx.x / nl, l = blockIdx.x - (blockIdx.x / nl) * nl;
+    const int kb = kuse_of(st, r, k);
+    const int m = g.m_s;
+    const double lam = lams[l];
+    const double* M = Mw + (size_t)r * m * (k + 1);
+    const double* dm = dM + (size_t)r * (k + 1);
+    double* y = Yw + ((size_t)r * nl + l) * (k + 1);
+    __shared__ double s_red[32];
+    const int ld = 2 * kb + 1;
+    double* S = Sw + ((size_t)r * nl + l) * (size_t)(2 * k + 1) * (k + 1);
+    // top rows 0..kb: R_M restricted to columns 0..kb-1 plus rhs column kb
+    for (int t = threadIdx.x; t < (kb + 1) * ld; t += blockDim.x) {
+        const int col = t / ld, row = t - col * ld;
+        double v = 0.0;
+        if (row <= kb) {
+            if (row < col) v = M[(size_t)col * m + row];
+            else if (row == col) v = dm[col];
+        } else if (lam != 0.0 && col < kb) {
+            const int br = row - kb - 1;          // bottom row index
+            if (penalty == IPF_PEN_Y) v = (br == col) ? lam : 0.0;
+            else {
+                const double* T = Tw + (size_t)r * m * k;
+                const double* dt = dT + (size_t)r * (k + 1);
+                if (br < col) v = lam * T[(size_t)col * m + br];
+                else if (br == col) v = lam * dt[col];
+            }
+        }
+        S[(size_t)col * ld + row] = v;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (lam != 0.0) {
+        for (int i = 0; i < kb; ++i) {
+            // x = [top(i,i); bottom(0..i, i)]
+            double* ci = S + (size_t)i * ld;
+            double part = 0.0;
+            for (int br = threadIdx.x; br <= i; br += blockDim.x) { const double x = ci[kb + 1 + br]; part = fma(x, x, part); }
+            const double sigma = block_sum(part, s_red);
+            const double alpha = ci[i];
+            double beta, tau, inv;
+            if (sigma == 0.0) { beta = alpha; tau = 0.0; inv = 0.0; }
+            else {
+                const double nrm = sqrt(fma(alpha, alpha, sigma));
+                beta = alpha <= 0.0 ? nrm : -nrm;
+                tau = (beta - alpha) / beta;
+                inv = 1.0 / (alpha - beta);
+            }
+            __syncthreads();
+            if (tau != 0.0) {
+                for (int jc = i + 1 + warp; jc <= kb; jc += nw) {
+                    double* cj = S + (size_t)jc * ld;
+                    double d = (lane == 0) ? cj[i] : 0.0;
+                    for (int br = lane; br <= i; br += 32) d = fma(ci[kb + 1 + br] * inv, cj[kb + 1 + br], d);
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
+                    const double f = tau * d;
+                    if (lane == 0) cj[i] -= f;
+                    for (int br = lane; br <= i; br += 32) cj[kb + 1 + br] = fma(-f, ci[kb + 1 + br] * inv, cj[kb + 1 + br]);
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) ci[i] = beta;
+            for (int br = threadIdx.x; br <= i; br += blockDim.x) ci[kb + 1 + br] = 0.0;
+            __syncthreads();
+        }
+    }
+    // back substitution: top(0:kb, 0:kb) y = top(0:kb, kb)
+    if (threadIdx.x == 0) {
+        for (int i = kb - 1; i >= 0; --i) {
+            double s = S[(size_t)kb * ld + i];
+            for (int c = i + 1; c < kb; ++c) s = fma(-S[(size_t)c * ld + i], y[c], s);
+            const double d = S[(size_t)i * ld + i];
+            y[i] = d != 0.0 ? s / d : 0.0;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
+// x = V_k y for nl lambdas; output [l][r][i]
+// ------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(256) k_reconstruct(Geom g, Bufs bf, const DevState* st, int k, int nl,
+                                                      const double* Yw, int l0, int nlc, float* x) {
+    using Acc = typename AccOf<T>::type;
+    constexpr int VEC = 16 / sizeof(T);
+    extern __shared__ unsigned char smem_raw[];
+    Acc* s_y = (Acc*)smem_raw;                 // [nlc][B][k]
+    __shared__ int s_kb[kMaxRhs];
+    const int B = g.B;
+    if (threadIdx.x < B) s_kb[threadIdx.x] = kuse_of(st, threadIdx.x, k);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nlc * B * k; t += blockDim.x) {
+        const int l = t / (B * k), rem = t - l * B * k, r = rem / k, c = rem - r * k;
+        s_y[t] = (c < s_kb[r]) ? (Acc)Yw[((size_t)r * nl + l0 + l) * (k + 1) + c] : (Acc)0;
+    }
+    int kmax = 0;
+    for (int r = 0; r < B; ++r) kmax = s_kb[r] > kmax ? s_kb[r] : kmax;
+    __syncthreads();
+    const T* V = (const T*)bf.V;
+    const long long stride = (long long)gridDim.x * blockDim.x * VEC;
+    for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * VEC; base < g.N; base += stride) {
+        Acc acc[8][VEC];
+#pragma unroll
+        for (int l = 0; l < 8; ++l)
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) acc[l][q] = 0;
+        for (int c = 0; c < kmax; ++c) {
+            const uint4 raw = __ldcs((const uint4*)(V + (size_t)c * g.ldv + base));
+            const T* vv = (const T*)&raw;
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+                const int rr = (int)((base + q) & (B - 1));
+                const Acc vq = to_acc(vv[q]);
+#pragma unroll
+                for (int l = 0; l < 8; ++l)
+                    if (l < nlc) acc[l][q] = fma(s_y[((size_t)l * B + rr) * k + c], vq, acc[l][q]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+            const long long e = base + q;
+            if (e >= g.N) break;
+            const long long i = e / B;
+            const int rr = (int)(e - i * B);
+#pragma unroll
+            for (int l = 0; l < 8; ++l)
+                if (l < nlc) x[((size_t)(l0 + l) * B + rr) * g.n + i] = (float)acc[l][q];
+        }
+    }
+}
+
+}  // namespace
+
+size_t solve_workspace_bytes(const Geom& g, int nl_max) { return layout_for(g, nl_max).total; }
+
+cudaError_t solve_error_flag(const void* work, const Geom& g, int* flag) {
+    const SolveLayout L = layout_for(g, 1);          // err_off does not depend on nl_max
+    return cudaMemcpy(flag, (const char*)work + L.err_off, sizeof(int), cudaMemcpyDeviceToHost);
+}
+
+cudaError_t launch_solve_prepare(const Geom& g, const Bufs& bf, int zeta, int k, bool need_T, int zform,
+                                 bool have_sw, void* work, int nl_max, int num_sms, cudaStream_t s) {
+    SolveLayout L = layout_for(g, nl_max);
+    char* base = (char*)work;
+    double* Mw = (double*)(base + L.M_off);
+    double* Tw = need_T ? (double*)(base + L.T_off) : nullptr;
+    double* dM = (double*)(base + L.dM_off);
+    double* dT = (double*)(base + L.dT_off);
+    unsigned* bars = (unsigned*)(base + L.bar_off);
+    int* err = (int*)(base + L.err_off);
+    cudaError_t e = cudaMemsetAsync(base, 0, L.M_off, s);
+    if (e != cudaSuccess) return e;
+    {
+        dim3 grid((unsigned)((g.m_s * (k + 1) + 255) / 256), (unsigned)g.B);
+        const bool direct_sw = (zform == IPF_Z_DIRECT) && have_sw;
+        k_form<<<grid, 256, 0, s>>>(g, bf, k, zeta, direct_sw ? 1 : 0, need_T ? 1 : 0, Mw, Tw);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const int njobs = g.B * (need_T ? 2 : 1);
+    const size_t smem = sizeof(double) * (size_t)g.m_s;
+    e = cudaFuncSetAttribute(k_householder, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_householder, 256, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    const int maxblocks = occ * num_sms;
+    int cpj = maxblocks / njobs;
+    if (cpj > (k + 2) / 2) cpj = (k + 2) / 2;
+    if (cpj < 1) cpj = 1;
+    if (cpj * njobs > maxblocks) return cudaErrorInvalidConfiguration;   // cannot co-reside
+    const int nb = cpj * njobs;
+    Geom gg = g;
+    const DevState* stp = bf.st;
+    int kk = k, nt = need_T ? 1 : 0, cp = cpj;
+    void* args[] = {&gg, (void*)&stp, &kk, &nt, &cp, &Mw, &Tw, &dM, &dT, &bars, &err};
+    return cudaLaunchCooperativeKernel((void*)k_householder, dim3(nb), dim3(256), args, smem, s);
+}
+
+cudaError_t launch_solve_lambdas(int storage, const Geom& g, const Bufs& bf, int k, bool need_T,
+                                 const double* lambdas_dev, int nl, int penalty, void* work, int nl_max,
+                                 float* x_dev, int num_sms, cudaStream_t s) {
+    if (nl > nl_max) return cudaErrorInvalidValue;
+    SolveLayout L = layout_for(g, nl_max);
+    char* base = (char*)work;
+    const double* Mw = (const double*)(base + L.M_off);
+    const double* Tw = need_T ? (const double*)(base + L.T_off) : nullptr;
+    const double* dM = (const double*)(base + L.dM_off);
+    const double* dT = (const double*)(base + L.dT_off);
+    double* Yw = (double*)(base + L.Y_off);
+    double* Sw = (double*)(base + L.S_off);
+    if (penalty == IPF_PEN_SKETCHED_X && !need_T) penalty = IPF_PEN_Y;   // no lambda > 0 in this call
+    k_small_solve<<<g.B * nl, 256, 0, s>>>(g, bf.st, k, nl, lambdas_dev, penalty, Mw, Tw, dM, dT, Sw, Yw);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !x_dev) return e;
+    for (int l0 = 0; l0 < nl; l0 += 8) {
+        const int nlc = nl - l0 < 8 ? nl - l0 : 8;
+        auto launch = [&](auto kern, int vec, size_t accsz) -> cudaError_t {
+            const size_t smem = accsz * (size_t)nlc * g.B * (k > 0 ? k : 1);
+            cudaError_t ee = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (ee != cudaSuccess) return ee;
+            long long chunks = (g.N + 256LL * vec - 1) / (256LL * vec);
+            long long blocks = (long long)num_sms * 4;
+            if (blocks > chunks) blocks = chunks < 1 ? 1 : chunks;
+            kern<<<(int)blocks, 256, smem, s>>>(g, bf, bf.st, k, nl, Yw, l0, nlc, x_dev);
+            return cudaGetLastError();
+        };
+        switch (storage) {
+            case IPF_STORE_F64: e = launch(k_reconstruct<double>, 2, 8); break;
+            case IPF_STORE_F32: e = launch(k_reconstruct<float>, 4, 4); break;
+            case IPF_STORE_BF16: e = launch(k_reconstruct<__nv_bfloat16>, 8, 4); break;
+            case IPF_STORE_F16: e = launch(k_reconstruct<__half>, 8, 4); break;
+            default: return cudaErrorInvalidValue;
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace ipf

@@ -1,0 +1,218 @@
+"""End-to-end parity of the CUDA path (ipf_create / ipf_step / ipf_solve
+through the C ABI) with the FP64 oracle on the same seeded inputs: pivots
+identical up to near ties, the sketch of the first basis vector, and x_k per
+iterate for plain and Tikhonov problems, in every storage precision; plus
+breakdown, batching and ragged sizes."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+from _gpu_common import (U, compare_pivots, compare_solution, ensure_lib, gpu_context, oracle_run,  # noqa: E402
+                         rel, tolerance)
+from gen import problems as P  # noqa: E402
+from oracle import operators as ops, scmrh, sketch as sk  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    return ensure_lib()
+
+
+@pytest.fixture(scope="module")
+def deblur64():
+    p = P.make("deblur64")
+    return p, oracle_run(p)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_deblur64_parity(deblur64, storage):
+    p, st = deblur64
+    ctx = gpu_context(p, storage)
+    ctx.step(p.k)
+    status, kd = ctx.sync()
+    assert kd == [p.k]
+    ex = ctx.export(0)
+    agree = compare_pivots(ex["piv"][:p.k + 1], st, storage)
+    assert agree == p.k + 1, "pivots diverged (near tie)"
+    assert abs(ex["beta"] - st.beta) <= 1e-6 * abs(st.beta)
+    # sketch of v_1 = b / beta
+    assert rel(ex["SV"][:, 0], st.SV[:, 0]) < (1e-12 if storage == "f64" else 1e-6)
+    # Hessenberg columns: first steps tightly
+    for j in range(5):
+        assert rel(ex["H"][:j + 2, j], st.H[:j + 2, j]) < (1e-10 if storage == "f64" else 1e-5)
+    compare_solution(ctx, st, storage, [1, 2, 5, 10, 20, 30, 40, 50], p.lambdas)
+    ctx.close()
+
+
+@pytest.mark.parametrize("storage", ["bf16", "f16"])
+def test_deblur64_low_precision(deblur64, storage):
+    p, st = deblur64
+    ctx = gpu_context(p, storage)
+    ctx.step(p.k)
+    status, kd = ctx.sync()
+    ex = ctx.export(0)
+    agree = compare_pivots(ex["piv"][:kd[0] + 1], st, storage)
+    assert agree >= 2
+    # exact structure of the stored basis (unit lower trapezoid, |v| <= 1)
+    k = kd[0]
+    V = np.stack([ctx.basis(j) for j in range(k + 1)], axis=1).astype(np.float64)
+    piv = ex["piv"][:k + 1]
+    for i, pi in enumerate(piv):
+        assert V[pi, i] == 1.0 and np.all(V[pi, i + 1:] == 0.0)
+    assert np.abs(V).max() <= 1.0
+    # Hessenberg relation of the stored basis: column j is off by the rounding
+    # of v_{j+1} to storage (|H(j+1,j)| u_s) plus FP32 accumulation
+    A = ops.make_apply(p)
+    H = ex["H"][:k + 1, :k]
+    for j in range(k):
+        r = A(V[:, j]) - V[:, :j + 2] @ H[:j + 2, j]
+        bound = abs(H[j + 1, j]) * U[storage] + 1e-5 * (np.abs(A(V[:, j])).max() + np.abs(H[:j + 2, j]).sum())
+        assert np.abs(r).max() <= bound, (j, np.abs(r).max(), bound)
+    # iterates before the first pivot divergence, derived tolerance
+    ks = [kk for kk in (1, 2, 3, 5, 10) if kk < agree]
+    compare_solution(ctx, st, storage, ks, [0.0])
+    ctx.close()
+
+
+def test_zforms_agree_f32(deblur64):
+    from paper_2502_02721_gb300 import binding as bd
+    p, st = deblur64
+    xs = []
+    for zf in (bd.IPF_Z_DIRECT, bd.IPF_Z_HESSENBERG):
+        ctx = gpu_context(p, "f32", zform=zf)
+        ctx.step(20)
+        x, _ = ctx.solve(20, [0.0])
+        xs.append(x[0, 0].astype(np.float64))
+        ctx.close()
+    assert rel(xs[0], xs[1]) < 1e-6
+
+
+def test_penalty_on_y(deblur64):
+    from paper_2502_02721_gb300 import binding as bd
+    p, st = deblur64
+    ctx = gpu_context(p, "f64", penalty=bd.IPF_PEN_Y)
+    ctx.step(30)
+    lam = [0.05, 0.5]
+    x, _ = ctx.solve(30, lam)
+    for li, l in enumerate(lam):
+        assert rel(x[li, 0], scmrh.solve(st, 30, l, penalty="y")) < 1e-8
+    ctx.close()
+
+
+def test_deblur256_sep_motion_lambda_sweep():
+    p = P.make("deblur256")
+    st = oracle_run(p)
+    ctx = gpu_context(p, "f32")
+    ctx.step(p.k)
+    status, kd = ctx.sync()
+    assert kd == [p.k]
+    ex = ctx.export(0)
+    agree = compare_pivots(ex["piv"][:p.k + 1], st, "f32")
+    assert agree == p.k + 1
+    compare_solution(ctx, st, "f32", [5, 25, 50, 100], p.lambdas)
+    ctx.close()
+
+
+def test_graph_and_eager_paths_give_identical_bits(deblur64):
+    p, _ = deblur64
+    outs = []
+    for graphs in (0, 1):
+        ctx = gpu_context(p, "f32", k=20, graphs=graphs)
+        ctx.step(7)
+        ctx.step(13)
+        x, _ = ctx.solve(20, [0.0, 1e-3])
+        outs.append((x.copy(), ctx.export(0)))
+        ctx.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1]["SV"], outs[1][1]["SV"])
+    assert np.array_equal(outs[0][1]["piv"], outs[1][1]["piv"])
+
+
+def test_ragged_psf_image():
+    rng = np.random.default_rng(7)
+    H, W = 100, 130
+    psf = P.gaussian_psf(9, 1.5)
+    x = P.ellipse_phantom(H, W, 6, rng)
+    b = P.add_noise(P.blur_fft(x, psf), 0.01, rng).astype(np.float32)
+    p = P.Problem("ragged", "psf2d", H, W, b.reshape(1, -1), x.reshape(-1), k=25, m_s=100, zeta=8,
+                  sketch_seed=99, psf=psf)
+    st = oracle_run(p)
+    ctx = gpu_context(p, "f32")
+    ctx.step(p.k)
+    ex = ctx.export(0)
+    assert compare_pivots(ex["piv"][:p.k + 1], st, "f32") == p.k + 1
+    compare_solution(ctx, st, "f32", [3, 10, 25], [0.0, 1e-2])
+    ctx.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_ct_batched_rhs(storage):
+    p = P.ct_parallel(side=48, nrhs=4, k=30, m_s=120)
+    ctx = gpu_context(p, storage)
+    ctx.step(p.k)
+    status, kd = ctx.sync()
+    assert kd == [p.k] * 4
+    for r in range(4):
+        st = oracle_run(p, r=r)
+        ex = ctx.export(r)
+        agree = compare_pivots(ex["piv"][:p.k + 1], st, storage)
+        if storage == "f32":
+            assert agree == p.k + 1
+            compare_solution(ctx, st, storage, [1, 5, 15, 30], [0.0, 1.0], r=r)
+        else:
+            ks = [kk for kk in (1, 2) if kk < agree]
+            compare_solution(ctx, st, storage, ks, [0.0], r=r)
+    ctx.close()
+
+
+def test_batch_equals_single():
+    """A RHS solved inside a batch gives the same bits as solved alone."""
+    p = P.ct_parallel(side=32, nrhs=8, k=12, m_s=48)
+    ctx = gpu_context(p, "f32")
+    ctx.step(p.k)
+    xb, _ = ctx.solve(p.k, [0.0, 0.5])
+    ctx.close()
+    for r in (0, 5):
+        single = gpu_context(p, "f32", nrhs=1, b=p.b[r:r + 1])
+        single.step(p.k)
+        xs, _ = single.solve(p.k, [0.0, 0.5])
+        single.close()
+        assert np.array_equal(xb[:, r], xs[:, 0])
+
+
+def test_breakdown_on_invariant_subspace():
+    n = 64
+    d = np.linspace(1.0, 2.0, n).astype(np.float32)
+    rowptr = np.arange(n + 1, dtype=np.int64)
+    colind = np.arange(n, dtype=np.int32)
+    b = np.zeros((2, n), np.float32)
+    b[0, 5] = 3.0                 # eigenvector: breakdown after one step
+    b[1, :] = 0.0                 # zero RHS: nothing to do
+    p = P.Problem("diag", "csr", n, n, b, np.zeros((2, n)), k=4, m_s=16, zeta=8, sketch_seed=3,
+                  rowptr=rowptr, colind=colind, vals=d)
+    from paper_2502_02721_gb300 import binding as bd
+    ctx = gpu_context(p, "f32", nrhs=2)
+    ctx.step(4)
+    status, kd = ctx.sync()
+    assert status == bd.IPF_BREAKDOWN and kd == [1, 0]
+    x, info = ctx.solve(4, [0.0])
+    assert info[0][:2] == (1, 1) and info[1][:2] == (0, 0)
+    want = np.zeros(n)
+    want[5] = 3.0 / d[5]
+    assert rel(x[0, 0], want) < 1e-6
+    assert not np.any(x[0, 1])
+    ctx.close()
+
+
+def test_state_errors():
+    from paper_2502_02721_gb300 import binding as bd
+    p = P.make("deblur64")
+    ctx = gpu_context(p, "f32", k=5)
+    with pytest.raises(bd.IpfError) as ei:
+        ctx.solve(3, [0.0])
+    assert ei.value.code == bd.IPF_ERR_STATE
+    assert ctx.step(10) == 5                       # clipped to k_max
+    x, info = ctx.solve(5, [0.0])
+    assert info[0][0] == 5
+    ctx.close()
