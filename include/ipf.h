@@ -70,11 +70,13 @@ enum ipf_storage { IPF_STORE_F64 = 0, IPF_STORE_F32 = 1, IPF_STORE_BF16 = 2, IPF
  * S_1 = S) or lambda^2 ||y||^2 (the penalty of Eq. TSP).                   */
 enum ipf_penalty { IPF_PEN_SKETCHED_X = 0, IPF_PEN_Y = 1 };
 
-/* How S A V_k is assembled: DIRECT uses the sketch of each product A v_j
- * (Algorithm 1 line 11, z_k = S u, before the elimination), HESSENBERG uses
+/* How S A V_k is assembled: DIRECT sketches each product u = A v_j before
+ * the elimination (Algorithm 1 line 11, z_k = S u), HESSENBERG uses
  * S V_{k+1} H_k.  They agree in exact arithmetic; with BF16/FP16 storage
- * DIRECT is the sketch of the products of the stored basis.               */
-enum ipf_zform { IPF_Z_DIRECT = 0, IPF_Z_HESSENBERG = 1 };
+ * DIRECT is exactly the sketched objective over the stored basis.  DIRECT
+ * needs float storage and nrhs <= 4; AUTO picks DIRECT when it can and
+ * HESSENBERG otherwise.                                                    */
+enum ipf_zform { IPF_Z_DIRECT = 0, IPF_Z_HESSENBERG = 1, IPF_Z_AUTO = 2 };
 
 /* Forward operator.  For PSF kinds n = rows*cols and images are row-major.
  * For CSR, rows x cols is m x n and the method needs m == n (square A).
@@ -129,7 +131,7 @@ typedef struct ipf_ctx ipf_ctx;
 typedef struct ipf_op ipf_op;
 
 /* Fill *cfg with defaults: k_max 50, m_s 200, zeta 8, seed 1, F32 storage,
- * sketched-x penalty, direct Z, nrhs 1, graphs on, default stream, cudaMalloc. */
+ * sketched-x penalty, AUTO Z, nrhs 1, graphs on, default stream, cudaMalloc. */
 void ipf_config_default(ipf_config* cfg);
 
 /* Bytes of device memory ipf_create would allocate for this problem
@@ -194,13 +196,13 @@ ipf_status ipf_solve(ipf_ctx* ctx, int k, const double* lambdas, int nl,
 ipf_status ipf_profile_read(ipf_ctx* ctx, double* ms, long long* launches, double* bytes);
 
 /* Copy the method's state for RHS r to host memory (any pointer may be
- * NULL): pivots (k_done+1 ints, 0-based rows), H ((k_max+1) x k_max FP64,
- * column-major, column j holds H(0..j+1, j)), SV (m_s x (k_max+1) FP64,
- * column-major, the sketch of the stored basis), SW (same shape, sketch of
- * each normalised vector before rounding to storage), beta (1 double).
- * Synchronises.                                                           */
-ipf_status ipf_export(ipf_ctx* ctx, int r, int* pivots, double* H, double* SV, double* SW,
-                      double* beta);
+ * NULL): pivots (k_max+1 ints, 0-based rows, -1 past the last pivot),
+ * H ((k_max+1) x k_max FP64, column-major, column j holds H(0..j+1, j)),
+ * SV (m_s x (k_max+1) FP64, column-major: S v_j of the stored basis),
+ * SZ (m_s x k_max FP64: z_j = S A v_j, zero unless the DIRECT form is in
+ * use), c (m_s FP64: S b), beta (1 double).  Synchronises.                */
+ipf_status ipf_export(ipf_ctx* ctx, int r, int* pivots, double* H, double* SV, double* SZ,
+                      double* c, double* beta);
 
 /* Copy basis vector j (0-based, j <= k_done) of RHS r as float32 (host). */
 ipf_status ipf_export_basis(ipf_ctx* ctx, int r, int j, float* v_out);

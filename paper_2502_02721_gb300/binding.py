@@ -22,7 +22,7 @@ IPF_OP_PSF2D, IPF_OP_PSF2D_SEP_MOTION, IPF_OP_CSR = 1, 2, 3
 IPF_MEM_HOST, IPF_MEM_DEVICE = 0, 1
 IPF_STORE_F64, IPF_STORE_F32, IPF_STORE_BF16, IPF_STORE_F16 = 0, 1, 2, 3
 IPF_PEN_SKETCHED_X, IPF_PEN_Y = 0, 1
-IPF_Z_DIRECT, IPF_Z_HESSENBERG = 0, 1
+IPF_Z_DIRECT, IPF_Z_HESSENBERG, IPF_Z_AUTO = 0, 1, 2
 
 STORAGE = {"f64": IPF_STORE_F64, "f32": IPF_STORE_F32, "bf16": IPF_STORE_BF16, "f16": IPF_STORE_F16}
 
@@ -67,7 +67,7 @@ SIGNATURES = {
     "ipf_sync": (C.c_int, [C.c_void_p, _ip]),
     "ipf_solve": (C.c_int, [C.c_void_p, C.c_int, _dp, C.c_int, C.c_void_p, C.c_int,
                             C.POINTER(ipf_solve_info)]),
-    "ipf_export": (C.c_int, [C.c_void_p, C.c_int, _ip, _dp, _dp, _dp, _dp]),
+    "ipf_export": (C.c_int, [C.c_void_p, C.c_int, _ip, _dp, _dp, _dp, _dp, _dp]),
     "ipf_export_basis": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _fp]),
     "ipf_destroy": (None, [C.c_void_p]),
     "ipf_status_str": (C.c_char_p, [C.c_int]),
@@ -166,8 +166,12 @@ def make_operator(kind: str, rows: int, cols: int, *, psf=None, sep_row=None, se
 
 
 def operator_from_problem(p, keep: list | None = None) -> ipf_operator:
-    """ipf_operator for a gen.problems.Problem (host arrays)."""
-    return make_operator(p.kind, p.rows, p.cols, psf=p.psf, sep_row=p.sep_row, sep_col=p.sep_col,
+    """ipf_operator for a gen.problems.Problem (host arrays).  For CSR the
+    problem's rows x cols is the image; the operator is m x n = rays x pixels."""
+    rows, cols = p.rows, p.cols
+    if p.kind == "csr":
+        rows, cols = int(np.asarray(p.rowptr).size - 1), int(p.rows * p.cols)
+    return make_operator(p.kind, rows, cols, psf=p.psf, sep_row=p.sep_row, sep_col=p.sep_col,
                          motion=p.motion, rowptr=p.rowptr, colind=p.colind, vals=p.vals, keep=keep)
 
 
@@ -253,13 +257,15 @@ class Context:
         piv = np.zeros(K1, dtype=np.int32)
         H = np.zeros(K1 * self.cfg.k_max, dtype=np.float64)
         SV = np.zeros(K1 * self.cfg.m_s, dtype=np.float64)
-        SW = np.zeros(K1 * self.cfg.m_s, dtype=np.float64)
+        SZ = np.zeros(self.cfg.k_max * self.cfg.m_s, dtype=np.float64)
+        c = np.zeros(self.cfg.m_s, dtype=np.float64)
         beta = np.zeros(1, dtype=np.float64)
         st = self._lib.ipf_export(self.h, r, piv.ctypes.data_as(_ip), H.ctypes.data_as(_dp),
-                                  SV.ctypes.data_as(_dp), SW.ctypes.data_as(_dp), beta.ctypes.data_as(_dp))
+                                  SV.ctypes.data_as(_dp), SZ.ctypes.data_as(_dp), c.ctypes.data_as(_dp),
+                                  beta.ctypes.data_as(_dp))
         self._check(st, "ipf_export")
         return {"piv": piv, "H": H.reshape(self.cfg.k_max, K1).T, "SV": SV.reshape(K1, self.cfg.m_s).T,
-                "SW": SW.reshape(K1, self.cfg.m_s).T, "beta": float(beta[0])}
+                "SZ": SZ.reshape(self.cfg.k_max, self.cfg.m_s).T, "c": c, "beta": float(beta[0])}
 
     def basis(self, j: int, r: int = 0) -> np.ndarray:
         v = np.zeros(self.n, dtype=np.float32)

@@ -148,6 +148,46 @@ cudaError_t upload_op(const ipf_operator* op, Alloc& al, OpDev* d, cudaStream_t 
     return e;
 }
 
+// bound on ||A||_inf (max row sum of |a|) for the z-sketch's fixed-point scale
+cudaError_t operator_inf_norm(const ipf_operator* op, const OpDev& d, float* out, cudaStream_t s) {
+    auto host_copy = [&](const float* src, size_t count, std::vector<float>& dst) -> cudaError_t {
+        dst.resize(count);
+        if (op->mem == IPF_MEM_HOST) {
+            memcpy(dst.data(), src, count * sizeof(float));
+            return cudaSuccess;
+        }
+        return cudaMemcpy(dst.data(), src, count * sizeof(float), cudaMemcpyDeviceToHost);
+    };
+    auto l1 = [](const std::vector<float>& v) {
+        double t = 0;
+        for (float x : v) t += std::fabs((double)x);
+        return t;
+    };
+    std::vector<float> a, b2, m;
+    cudaError_t e = cudaSuccess;
+    if (op->kind == IPF_OP_PSF2D) {
+        if ((e = host_copy(op->psf, (size_t)op->ph * op->pw, a)) != cudaSuccess) return e;
+        *out = (float)l1(a);
+    } else if (op->kind == IPF_OP_PSF2D_SEP_MOTION) {
+        if ((e = host_copy(op->sep_row, op->slen, a)) != cudaSuccess) return e;
+        if ((e = host_copy(op->sep_col, op->slen, b2)) != cudaSuccess) return e;
+        if ((e = host_copy(op->motion, (size_t)op->mlen * op->mlen, m)) != cudaSuccess) return e;
+        *out = (float)(l1(a) * l1(b2) * l1(m));
+    } else if (op->mem == IPF_MEM_HOST) {
+        double mx = 0;
+        for (int r = 0; r < op->rows; ++r) {
+            double t = 0;
+            for (long long q = op->rowptr[r]; q < op->rowptr[r + 1]; ++q) t += std::fabs((double)op->vals[q]);
+            mx = t > mx ? t : mx;
+        }
+        *out = (float)mx;
+    } else {
+        e = launch_csr_row_abs_max(d, out, s);
+    }
+    if (!(*out > 0.f) || !std::isfinite(*out)) *out = 1.f;
+    return e;
+}
+
 }  // namespace
 
 struct ipf_ctx {
@@ -173,7 +213,6 @@ struct ipf_ctx {
     double* lam_dev = nullptr;
     float* x_stage = nullptr;          // B*n floats (host output path)
     float* b_stage = nullptr;          // B*n floats (host b)
-    bool want_sw = false;
     // profile mode: event pairs recorded around each kernel
     struct Mark { int kind; double bytes; cudaEvent_t a, b; };
     std::vector<Mark> marks;
@@ -267,10 +306,10 @@ cudaError_t one_step(ipf_ctx* c, int j) {
     if ((e = timed(c, 1, 0.0, [&] { return launch_pivot_solve(c->storage, c->g, c->bf, c->s); })) != cudaSuccess)
         return e;
     if ((e = timed(c, 2, (double)(j + 1) * N * sv + 2.0 * N * ab + N / 8.0,
-                   [&] { return launch_update(c->storage, c->g, c->bf, c->num_sms, c->s); })) != cudaSuccess)
+                   [&] { return launch_update(c->storage, c->g, c->bf, c->sp, c->num_sms, c->s); })) != cudaSuccess)
         return e;
     return timed(c, 3, N * ab + N * sv,
-                 [&] { return launch_normalize(c->storage, c->g, c->bf, c->sp, c->want_sw, c->num_sms, c->s); });
+                 [&] { return launch_normalize(c->storage, c->g, c->bf, c->sp, false, c->num_sms, c->s); });
 }
 
 // clear the state and enqueue Algorithm 1's initialisation for b
@@ -283,11 +322,13 @@ cudaError_t init_solve(ipf_ctx* c, const float* bdev) {
     if ((e = cudaMemsetAsync(c->bf.ispiv, 0, (g.ldv / 32 + 1) * sizeof(unsigned), c->s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->bf.accSV, 0, B * K1 * g.m_s * sizeof(long long), c->s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->bf.accSW, 0, B * K1 * g.m_s * sizeof(long long), c->s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->bf.accSZ, 0, B * (size_t)g.k_max * g.m_s * sizeof(long long), c->s)) != cudaSuccess)
+        return e;
     return timed(c, 4, 0.0, [&] {
         cudaError_t ee = launch_reset_state(c->bf.st, c->s);
         if (ee != cudaSuccess) return ee;
         if ((ee = launch_load_rhs(c->storage, bdev, g, c->bf, c->s)) != cudaSuccess) return ee;
-        if ((ee = launch_update(c->storage, g, c->bf, c->num_sms, c->s)) != cudaSuccess) return ee;
+        if ((ee = launch_update(c->storage, g, c->bf, c->sp, c->num_sms, c->s)) != cudaSuccess) return ee;
         return launch_normalize(c->storage, g, c->bf, c->sp, true, c->num_sms, c->s);
     });
 }
@@ -305,7 +346,7 @@ void ipf_config_default(ipf_config* cfg) {
     cfg->seed = 1;
     cfg->storage = IPF_STORE_F32;
     cfg->penalty = IPF_PEN_SKETCHED_X;
-    cfg->zform = IPF_Z_DIRECT;
+    cfg->zform = IPF_Z_AUTO;
     cfg->nrhs = 1;
     cfg->use_graphs = 1;
 }
@@ -325,7 +366,7 @@ size_t ipf_footprint(const ipf_operator* op, const ipf_config* cfg) {
     const size_t K1 = (size_t)cfg->k_max + 1;
     size_t bytes = K1 * ldv * sb + ldv * acc + ldv / 8 + 4096;
     bytes += B * K1 * (sizeof(int) + sizeof(double) * cfg->k_max + acc * K1) + K1 * B * acc;
-    bytes += 2 * (size_t)B * K1 * cfg->m_s * 8;
+    bytes += 3 * (size_t)B * K1 * cfg->m_s * 8;
     Geom g; g.n = n; g.B = B; g.N = n * B; g.ldv = (long long)ldv; g.k_max = cfg->k_max; g.m_s = cfg->m_s; g.F = 0;
     bytes += solve_ws_for(g) + 2 * (size_t)B * n * 4 + 256;
     if (op->kind == IPF_OP_CSR && op->mem == IPF_MEM_HOST)
@@ -350,13 +391,15 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     if (cfg.storage < IPF_STORE_F64 || cfg.storage > IPF_STORE_F16) return IPF_ERR_ARG;
     if (cfg.storage == IPF_STORE_F64 && B != 1) return IPF_ERR_UNSUPPORTED;
     if (cfg.penalty != IPF_PEN_SKETCHED_X && cfg.penalty != IPF_PEN_Y) return IPF_ERR_ARG;
-    if (cfg.zform != IPF_Z_DIRECT && cfg.zform != IPF_Z_HESSENBERG) return IPF_ERR_ARG;
+    if (cfg.zform != IPF_Z_DIRECT && cfg.zform != IPF_Z_HESSENBERG && cfg.zform != IPF_Z_AUTO) return IPF_ERR_ARG;
+    const bool z_ok = cfg.storage != IPF_STORE_F64 && B <= 4;
+    if (cfg.zform == IPF_Z_DIRECT && !z_ok) return IPF_ERR_UNSUPPORTED;
     if (b_mem != IPF_MEM_HOST && b_mem != IPF_MEM_DEVICE) return IPF_ERR_ARG;
     const size_t accb = cfg.storage == IPF_STORE_F64 ? 8 : 4;
     const size_t pivsmem = (size_t)(cfg.k_max + 2) * 8 + (size_t)cfg.k_max * (cfg.k_max + 1) / 2 * accb;
     if (pivsmem > 220 * 1024) return IPF_ERR_UNSUPPORTED;
     const long long n = op_n(op);
-    if (n * B >= (1ll << 32)) return IPF_ERR_UNSUPPORTED;
+    if (n * B >= (1ll << 32) || n >= (1ll << 29)) return IPF_ERR_UNSUPPORTED;
 
     ipf_ctx* c = new ipf_ctx();
     c->cfg = cfg;
@@ -367,7 +410,6 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     c->al.user = cfg.alloc_user;
     c->user = (cudaStream_t)cfg.stream;
     c->num_sms = device_sms();
-    c->want_sw = cfg.storage == IPF_STORE_BF16 || cfg.storage == IPF_STORE_F16;
     cudaError_t e;
 #define CK(what, expr)                                              \
     do {                                                            \
@@ -390,7 +432,17 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     g.ldv = (long long)ldv_for(g.N);
     g.k_max = cfg.k_max;
     g.m_s = cfg.m_s;
-    g.F = fixed_exponent(n, 0);
+    g.F = cfg.storage == IPF_STORE_F64 ? fixed_exponent(n, 0) : kSplitS;
+    g.want_z = (cfg.zform == IPF_Z_DIRECT || (cfg.zform == IPF_Z_AUTO && z_ok)) ? 1 : 0;
+    {
+        // |A v| <= ||A||_inf max|v| <= ||A||_inf (|v| <= 1 under max pivoting); the
+        // z-sketch scale puts that bound (with 0.1% headroom) just under 2^34
+        float bound = 1.f;
+        CK("operator norm", operator_inf_norm(op, c->op, &bound, c->s));
+        int ez = 0;
+        std::frexp((double)bound * 1.001 + 1e-30, &ez);
+        g.Fz = kSplitS - ez;
+    }
     c->sp = make_sketch_params(cfg.seed, cfg.m_s, cfg.zeta);
     const size_t K1 = (size_t)cfg.k_max + 1;
     const size_t sb = storage_bytes(cfg.storage);
@@ -405,6 +457,7 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     CK("alloc ispiv", c->al.get((void**)&bf.ispiv, (g.ldv / 32 + 1) * sizeof(unsigned)));
     CK("alloc SV", c->al.get((void**)&bf.accSV, B * K1 * cfg.m_s * sizeof(long long)));
     CK("alloc SW", c->al.get((void**)&bf.accSW, B * K1 * cfg.m_s * sizeof(long long)));
+    CK("alloc SZ", c->al.get((void**)&bf.accSZ, B * (size_t)cfg.k_max * cfg.m_s * sizeof(long long)));
     c->solve_ws_bytes = solve_ws_for(g);
     CK("alloc solve", c->al.get(&c->solve_ws, c->solve_ws_bytes));
     CK("alloc lambdas", c->al.get((void**)&c->lam_dev, sizeof(double) * kLamChunk));
@@ -416,6 +469,7 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     CK("memset Lp", cudaMemsetAsync(bf.LpT, 0, B * K1 * K1 * accb, c->s));
     CK("memset piv", cudaMemsetAsync(bf.piv, 0, B * K1 * sizeof(int), c->s));
     CK("memset coef", cudaMemsetAsync(bf.coef, 0, K1 * B * accb, c->s));
+    CK("memset solve", cudaMemsetAsync(c->solve_ws, 0, c->solve_ws_bytes, c->s));
     const float* bsrc = b;
     if (b_mem == IPF_MEM_HOST) {
         CK("b upload", cudaMemcpyAsync(c->b_stage, b, sizeof(float) * (size_t)n * B, cudaMemcpyHostToDevice, c->s));
@@ -483,22 +537,26 @@ ipf_status ipf_step(ipf_ctx* c, int nsteps, int* k_enqueued) {
     if (todo > c->g.k_max - c->j_host) todo = c->g.k_max - c->j_host;
     cudaError_t e = enter(c);
     if (e != cudaSuccess) return cuda_fail(c, "order", e);
-    for (int t = 0; t < todo; ++t) {
-        if (c->cfg.use_graphs && !c->cfg.profile) {
-            if (!c->gexec) {
-                // first step eagerly (sets kernel attributes), then capture one step
-                if ((e = one_step(c, c->j_host)) != cudaSuccess) return cuda_fail(c, "step", e);
-                ++c->j_host;
-                if (t + 1 >= todo) break;
-                if ((e = cudaStreamBeginCapture(c->s, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
-                    return cuda_fail(c, "capture", e);
-                cudaError_t e1 = one_step(c, 0);
-                cudaError_t e2 = cudaStreamEndCapture(c->s, &c->graph);
-                if (e1 != cudaSuccess) return cuda_fail(c, "capture step", e1);
-                if (e2 != cudaSuccess) return cuda_fail(c, "end capture", e2);
-                if ((e = cudaGraphInstantiate(&c->gexec, c->graph, 0)) != cudaSuccess)
-                    return cuda_fail(c, "instantiate", e);
-            }
+    int t = 0;
+    if (todo > 0 && c->cfg.use_graphs && !c->cfg.profile && !c->gexec) {
+        // the first step runs eagerly (it sets the kernels' attributes), then
+        // one step is captured and the rest replay the graph
+        if ((e = one_step(c, c->j_host)) != cudaSuccess) return cuda_fail(c, "step", e);
+        ++c->j_host;
+        ++t;
+        if (t < todo) {
+            if ((e = cudaStreamBeginCapture(c->s, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+                return cuda_fail(c, "capture", e);
+            cudaError_t e1 = one_step(c, 0);
+            cudaError_t e2 = cudaStreamEndCapture(c->s, &c->graph);
+            if (e1 != cudaSuccess) return cuda_fail(c, "capture step", e1);
+            if (e2 != cudaSuccess) return cuda_fail(c, "end capture", e2);
+            if ((e = cudaGraphInstantiate(&c->gexec, c->graph, 0)) != cudaSuccess)
+                return cuda_fail(c, "instantiate", e);
+        }
+    }
+    for (; t < todo; ++t) {
+        if (c->gexec && !c->cfg.profile) {
             if ((e = cudaGraphLaunch(c->gexec, c->s)) != cudaSuccess) return cuda_fail(c, "graph launch", e);
         } else {
             if ((e = one_step(c, c->j_host)) != cudaSuccess) return cuda_fail(c, "step", e);
@@ -559,8 +617,8 @@ ipf_status ipf_solve(ipf_ctx* c, int k, const double* lambdas, int nl, float* x_
     for (int l = 0; l < nl; ++l) any_pos |= lambdas[l] > 0.0;
     const bool need_T = any_pos && c->cfg.penalty == IPF_PEN_SKETCHED_X;
     e = timed(c, 5, 0.0, [&] {
-        return launch_solve_prepare(g, c->bf, c->cfg.zeta, k, need_T, c->cfg.zform, c->want_sw, c->solve_ws, nlm,
-                                    c->num_sms, c->s);
+        return launch_solve_prepare(g, c->bf, c->cfg.zeta, k, need_T, g.want_z != 0, c->solve_ws, nlm, c->num_sms,
+                                    c->s);
     });
     if (e != cudaSuccess) return cuda_fail(c, "solve prepare", e);
     const size_t slice = (size_t)g.n * c->B;
@@ -600,7 +658,7 @@ ipf_status ipf_solve(ipf_ctx* c, int k, const double* lambdas, int nl, float* x_
     return worst(h, c->B);
 }
 
-ipf_status ipf_export(ipf_ctx* c, int r, int* pivots, double* H, double* SV, double* SW, double* beta) {
+ipf_status ipf_export(ipf_ctx* c, int r, int* pivots, double* H, double* SV, double* SZ, double* cvec, double* beta) {
     if (!c) return IPF_ERR_ARG;
     if (c->sticky != IPF_OK) return c->sticky;
     if (r < 0 || r >= c->B) return IPF_ERR_ARG;
@@ -608,6 +666,7 @@ ipf_status ipf_export(ipf_ctx* c, int r, int* pivots, double* H, double* SV, dou
     ipf_status st = read_state(c, &h);
     if (st != IPF_OK) return st;
     const size_t K1 = (size_t)c->g.k_max + 1;
+    const size_t km = (size_t)c->g.k_max;
     const int m = c->g.m_s;
     cudaError_t e = cudaSuccess;
     if (pivots) {
@@ -619,18 +678,25 @@ ipf_status ipf_export(ipf_ctx* c, int r, int* pivots, double* H, double* SV, dou
         for (int i = 0; i < (int)K1; ++i) pivots[i] = i < np ? p[i] : -1;
     }
     if (H) {
-        e = cudaMemcpy(H, c->bf.H + r * K1 * c->g.k_max, K1 * c->g.k_max * sizeof(double), cudaMemcpyDeviceToHost);
+        e = cudaMemcpy(H, c->bf.H + r * K1 * km, K1 * km * sizeof(double), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(c, "export H", e);
     }
-    const double scale = std::ldexp(1.0, -c->g.F) / std::sqrt((double)c->cfg.zeta);
-    for (int which = 0; which < 2; ++which) {
-        double* dst = which == 0 ? SV : SW;
-        if (!dst) continue;
-        const long long* src = (which == 0 ? c->bf.accSV : c->bf.accSW) + r * K1 * m;
-        std::vector<long long> a(K1 * m);
-        e = cudaMemcpy(a.data(), src, a.size() * sizeof(long long), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return cuda_fail(c, "export sketch", e);
-        for (size_t t = 0; t < a.size(); ++t) dst[t] = (double)a[t] * scale;
+    const double sq = std::sqrt((double)c->cfg.zeta);
+    auto grab = [&](const long long* src, size_t count, double scale, double* dst) -> cudaError_t {
+        std::vector<long long> a(count);
+        cudaError_t ee = cudaMemcpy(a.data(), src, count * sizeof(long long), cudaMemcpyDeviceToHost);
+        if (ee != cudaSuccess) return ee;
+        for (size_t t = 0; t < count; ++t) dst[t] = (double)a[t] * scale;
+        return cudaSuccess;
+    };
+    if (SV && (e = grab(c->bf.accSV + r * K1 * m, K1 * m, std::ldexp(1.0, -c->g.F) / sq, SV)) != cudaSuccess)
+        return cuda_fail(c, "export SV", e);
+    if (SZ && (e = grab(c->bf.accSZ + r * km * m, km * m, std::ldexp(1.0, -c->g.Fz) / sq, SZ)) != cudaSuccess)
+        return cuda_fail(c, "export SZ", e);
+    if (cvec) {
+        if ((e = grab(c->bf.accSW + r * K1 * m, m, std::ldexp(1.0, -c->g.F) / sq, cvec)) != cudaSuccess)
+            return cuda_fail(c, "export c", e);
+        for (int t = 0; t < m; ++t) cvec[t] *= h.beta[r];
     }
     if (beta) *beta = h.beta[r];
     return IPF_OK;

@@ -149,6 +149,29 @@ __device__ __forceinline__ long long fixed_from(double v, int F) {
     return (u >> 63) ? -q : q;
 }
 
+// Float modes: contributions |x| <= 2^e are rounded once to q = x * 2^S with
+// S = kSplitS - e (|q| <= 2^34) and added into two int32 shared-memory
+// counters, hi = q >> 17 and lo = q & (2^17 - 1); both stay exact for up to
+// kFoldEvery contributions per counter, after which they are folded into an
+// int64 (hi * 2^17 + lo) and cleared.  Integer sums make the result
+// independent of thread order.
+constexpr int kSplitS = 34;
+constexpr int kFoldEvery = 8192;
+
+__device__ __forceinline__ void split_add(int* hi, int* lo, int row, long long q) {
+    atomicAdd(&hi[row], (int)(q >> 17));
+    atomicAdd(&lo[row], (int)(q & 0x1FFFFll));
+}
+
+// fold hi/lo counters [0, cnt) into wide and clear them (whole CTA, between barriers)
+__device__ __forceinline__ void split_fold(int* hi, int* lo, long long* wide, int cnt) {
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        wide[t] += ((long long)hi[t] << 17) + (long long)lo[t];
+        hi[t] = 0;
+        lo[t] = 0;
+    }
+}
+
 // fixed-point exponent for sums of at most `count` terms of magnitude <= 2^e_max
 inline int fixed_exponent(long long count, int e_max) {
     int lg = 0;
@@ -190,7 +213,9 @@ struct Geom {
     long long ldv;      // stride between basis vectors (elements), multiple of 64
     int k_max;
     int m_s;
-    int F;              // fixed-point exponent of the sketch accumulators
+    int F;              // fixed-point exponent of S V (and S b / beta)
+    int Fz;             // fixed-point exponent of S A v_j (|A v_j| <= 2^(kSplitS - Fz))
+    int want_z;         // accumulate z_j = S A v_j in the update kernel
 };
 
 struct Bufs {
@@ -203,7 +228,8 @@ struct Bufs {
     void* coef;                    // [(k_max+1)*B] Acc, h for the update
     unsigned* ispiv;               // bitmap over N elements
     long long* accSV;              // [B][k_max+1][m_s] fixed-point S V
-    long long* accSW;              // [B][k_max+1][m_s] fixed-point S (u/H) before rounding
+    long long* accSW;              // [B][k_max+1][m_s] fixed-point; column 0 = S (b / beta)
+    long long* accSZ;              // [B][k_max][m_s] fixed-point z_j = S A v_j
 };
 
 // operator on the device
@@ -231,13 +257,15 @@ struct OpDev {
 // vbase + (*jptr) * ldv is the input vector (jptr NULL: vbase itself)
 cudaError_t launch_op_apply(const OpDev& op, int storage, const void* vbase, long long ldv, const int* jptr, int B,
                             void* w, cudaStream_t s);
+cudaError_t launch_csr_row_abs_max(const OpDev& op, float* host_out, cudaStream_t s);
 cudaError_t launch_op_apply_f32_plain(const OpDev& op, const float* v, float* w, int nrhs,
                                       cudaStream_t s);
 // k_hess.cu
 cudaError_t launch_reset_state(DevState* st, cudaStream_t s);
 cudaError_t launch_load_rhs(int storage, const float* b, const Geom& g, const Bufs& bf, cudaStream_t s);
 cudaError_t launch_pivot_solve(int storage, const Geom& g, const Bufs& bf, cudaStream_t s);
-cudaError_t launch_update(int storage, const Geom& g, const Bufs& bf, int num_sms, cudaStream_t s);
+cudaError_t launch_update(int storage, const Geom& g, const Bufs& bf, const SketchParams& sp, int num_sms,
+                          cudaStream_t s);
 cudaError_t launch_normalize(int storage, const Geom& g, const Bufs& bf, const SketchParams& sp,
                              bool want_sw, int num_sms, cudaStream_t s);
 cudaError_t launch_sketch_vector(const float* x, long long n, const SketchParams& sp, int F,
@@ -249,8 +277,8 @@ cudaError_t launch_sketch_finish(const long long* acc, int m, long long n, int z
 // k_small.cu: workspace for k <= k_max and up to nl_max lambdas per chunk
 size_t solve_workspace_bytes(const Geom& g, int nl_max);
 // form M = [Z | c] (and T = S V_k) and their R factors
-cudaError_t launch_solve_prepare(const Geom& g, const Bufs& bf, int zeta, int k, bool need_T, int zform,
-                                 bool have_sw, void* work, int nl_max, int num_sms, cudaStream_t s);
+cudaError_t launch_solve_prepare(const Geom& g, const Bufs& bf, int zeta, int k, bool need_T, bool use_z,
+                                 void* work, int nl_max, int num_sms, cudaStream_t s);
 // per lambda: y, then x = V_k y into x_dev ([l][r][n] float32)
 cudaError_t launch_solve_lambdas(int storage, const Geom& g, const Bufs& bf, int k, bool need_T,
                                  const double* lambdas_dev, int nl, int penalty, void* work, int nl_max,

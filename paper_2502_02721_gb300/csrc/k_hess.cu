@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(256) k_pivot_solve(Geom g, Bufs bf) {
     DevState* st = bf.st;
     if (st->status[r] != IPF_OK) return;
     const int j = st->j;
-    if (j < 0) return;
+    if (j < 0 || j >= g.k_max) return;
     const int K1 = g.k_max + 1;
     const int B = g.B;
     const T* V = (const T*)bf.V;
@@ -92,20 +92,33 @@ __global__ void __launch_bounds__(256) k_pivot_solve(Geom g, Bufs bf) {
 
 // ------------------------------------------------------------------------
 // u -= V_j h ; u(pivots) = 0 ; argmax keys.  Acc = float.
+// With g.want_z (nrhs <= 4) the incoming u = A v_j is also sketched,
+// z_j = S u (Algorithm 1 line 11), exactly, while the V_j loads are in
+// flight: shared split counters [B][m_s], folded every kFoldEvery elements.
 // ------------------------------------------------------------------------
 template <class T>
-__global__ void __launch_bounds__(256) k_update_f(Geom g, Bufs bf) {
+__global__ void __launch_bounds__(256) k_update_f(Geom g, Bufs bf, SketchParams sp) {
     constexpr int VEC = Vec16<T>::n;
     extern __shared__ unsigned char smem_raw[];
-    float* s_coef = (float*)smem_raw;
+    const int B = g.B;
+    const int K1 = g.k_max + 1;
+    // smem: wide [B*m] int64, hi [B*m], lo [B*m] int32 (only with z), coefficients
+    const int zc = g.want_z ? B * g.m_s : 0;
+    long long* s_wide = (long long*)smem_raw;
+    int* s_hi = (int*)(s_wide + zc);
+    int* s_lo = s_hi + zc;
+    float* s_coef = (float*)(s_lo + zc);
     __shared__ unsigned long long s_key[kMaxRhs];
     __shared__ int s_ok[kMaxRhs];
     DevState* st = bf.st;
     const int j = st->j;
+    if (j >= g.k_max) return;            // never past the last basis column
     const int nc = j + 1;               // coefficients h_0..h_j (none during init)
-    const int B = g.B;
+    const bool do_z = g.want_z && j >= 0;
     const float* coef = (const float*)bf.coef;
     for (int t = threadIdx.x; t < nc * B; t += blockDim.x) s_coef[t] = coef[t];
+    if (do_z)
+        for (int t = threadIdx.x; t < zc; t += blockDim.x) { s_wide[t] = 0; s_hi[t] = 0; s_lo[t] = 0; }
     if (threadIdx.x < B) {
         s_key[threadIdx.x] = 0ull;
         s_ok[threadIdx.x] = st->status[threadIdx.x] == IPF_OK;
@@ -121,56 +134,111 @@ __global__ void __launch_bounds__(256) k_update_f(Geom g, Bufs bf) {
 
     const long long stride = (long long)gridDim.x * blockDim.x * VEC;
     const long long base0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * VEC;
-    for (long long base = base0; base < g.N; base += stride) {
+    const int fold_rounds = kFoldEvery / (256 * VEC);
+    int round = 0;
+    for (long long bstart = (long long)blockIdx.x * blockDim.x * VEC; bstart < g.N; bstart += stride) {
+        const long long base = bstart + (long long)threadIdx.x * VEC;
+        const bool live = base < g.N;
         float acc[VEC];
-        {
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) acc[q] = 0.f;
+        int c = 0;
+        uint4 raw[4];
+        if (live) {
             const float4* wp = (const float4*)(w + base);
 #pragma unroll
             for (int q = 0; q < VEC / 4; ++q) {
                 const float4 t4 = wp[q];
                 acc[4 * q] = t4.x; acc[4 * q + 1] = t4.y; acc[4 * q + 2] = t4.z; acc[4 * q + 3] = t4.w;
             }
-        }
-        int c = 0;
-        for (; c + 4 <= nc; c += 4) {
-            uint4 raw[4];
+            if (nc >= 4) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) raw[u] = __ldcs((const uint4*)(V + (size_t)(c + u) * g.ldv + base));
+                for (int u = 0; u < 4; ++u) raw[u] = __ldcs((const uint4*)(V + (size_t)u * g.ldv + base));
+            }
+            if (do_z) {
+                // z_j = S u for the incoming u = A v_j
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const T* vv = (const T*)&raw[u];
+                for (int q = 0; q < VEC; ++q) {
+                    const long long e = base + q;
+                    const long long i = (B == 1) ? e : e / B;
+                    const int rr = (B == 1) ? 0 : (int)(e & (B - 1));
+                    if (e < g.N && s_ok[rr]) {
+                        const long long f = fixed_from(acc[q], g.Fz);
+                        if (f) {
+                            int rows[16];
+                            unsigned neg;
+                            if (sp.zeta == 8) sketch_column8(sp, i, rows, &neg);
+                            else sketch_column(sp, i, rows, &neg);
+#pragma unroll
+                            for (int t = 0; t < 16; ++t)
+                                if (t < sp.zeta)
+                                    split_add(s_hi + rr * g.m_s, s_lo + rr * g.m_s, rows[t], ((neg >> t) & 1u) ? -f : f);
+                        }
+                    }
+                }
+            }
+            for (; c + 4 <= nc; c += 4) {
+                uint4 nxt[4];
+                const bool more = c + 8 <= nc;
+                if (more) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) nxt[u] = __ldcs((const uint4*)(V + (size_t)(c + 4 + u) * g.ldv + base));
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const T* vv = (const T*)&raw[u];
+#pragma unroll
+                    for (int q = 0; q < VEC; ++q) {
+                        const int rr = (B == 1) ? 0 : (int)((base + q) & (B - 1));
+                        acc[q] = fmaf(-s_coef[(c + u) * B + rr], to_acc(vv[q]), acc[q]);
+                    }
+                }
+                if (more) {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) raw[u] = nxt[u];
+                }
+            }
+            for (; c < nc; ++c) {
+                const uint4 r1 = __ldcs((const uint4*)(V + (size_t)c * g.ldv + base));
+                const T* vv = (const T*)&r1;
 #pragma unroll
                 for (int q = 0; q < VEC; ++q) {
                     const int rr = (B == 1) ? 0 : (int)((base + q) & (B - 1));
-                    acc[q] = fmaf(-s_coef[(c + u) * B + rr], to_acc(vv[q]), acc[q]);
+                    acc[q] = fmaf(-s_coef[c * B + rr], to_acc(vv[q]), acc[q]);
                 }
             }
-        }
-        for (; c < nc; ++c) {
-            const uint4 raw = __ldcs((const uint4*)(V + (size_t)c * g.ldv + base));
-            const T* vv = (const T*)&raw;
+            const unsigned bits = bf.ispiv[base >> 5] >> (unsigned)(base & 31);
 #pragma unroll
             for (int q = 0; q < VEC; ++q) {
-                const int rr = (B == 1) ? 0 : (int)((base + q) & (B - 1));
-                acc[q] = fmaf(-s_coef[c * B + rr], to_acc(vv[q]), acc[q]);
+                if ((bits >> q) & 1u) acc[q] = 0.f;
+                const long long e = base + q;
+                const int rr = (B == 1) ? 0 : (int)(e & (B - 1));
+                if (e < g.N && s_ok[rr]) {
+                    const unsigned long long k = argmax_key(acc[q], (unsigned)(e / B));
+                    best[q] = k > best[q] ? k : best[q];
+                }
             }
-        }
-        const unsigned bits = bf.ispiv[base >> 5] >> (unsigned)(base & 31);
-#pragma unroll
-        for (int q = 0; q < VEC; ++q) {
-            if ((bits >> q) & 1u) acc[q] = 0.f;
-            const long long e = base + q;
-            const int rr = (B == 1) ? 0 : (int)(e & (B - 1));
-            if (e < g.N && s_ok[rr]) {
-                const unsigned long long k = argmax_key(acc[q], (unsigned)(e / B));
-                best[q] = k > best[q] ? k : best[q];
-            }
-        }
-        {
-            float4* wp = (float4*)(w + base);
+            float4* wo = (float4*)(w + base);
 #pragma unroll
             for (int q = 0; q < VEC / 4; ++q)
-                wp[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+                wo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+        }
+        if (do_z && ++round == fold_rounds) {
+            __syncthreads();
+            split_fold(s_hi, s_lo, s_wide, zc);
+            __syncthreads();
+            round = 0;
+        }
+    }
+    if (do_z) {
+        __syncthreads();
+        split_fold(s_hi, s_lo, s_wide, zc);
+        __syncthreads();
+        for (int t = threadIdx.x; t < zc; t += blockDim.x) {
+            const int rr = t / g.m_s, row = t - rr * g.m_s;
+            if (s_wide[t] && s_ok[rr])
+                atomicAdd((unsigned long long*)&bf.accSZ[((size_t)rr * g.k_max + j) * g.m_s + row],
+                          (unsigned long long)s_wide[t]);
         }
     }
     // reduce keys: per RHS rr = (base0 + q) mod B (same for every grid-stride pass)
@@ -192,6 +260,7 @@ __global__ void __launch_bounds__(256) k_update_f(Geom g, Bufs bf) {
     __syncthreads();
     if (threadIdx.x < B && s_key[threadIdx.x])
         atomicMax(&st->key[(j + 1) & 1][threadIdx.x], s_key[threadIdx.x]);
+    (void)K1;
 }
 
 // ------------------------------------------------------------------------
@@ -205,6 +274,7 @@ __global__ void __launch_bounds__(256) k_update_d(Geom g, Bufs bf) {
     DevState* st = bf.st;
     if (st->status[0] != IPF_OK) return;
     const int j = st->j;
+    if (j >= g.k_max) return;
     const int nc = j + 1;
     const double* coef = (const double*)bf.coef;
     for (int t = threadIdx.x; t < nc; t += blockDim.x) s_coef[t] = coef[t];
@@ -260,13 +330,21 @@ __global__ void k_argmin_d(Geom g, Bufs bf) {
 }
 
 // ------------------------------------------------------------------------
-// normalise + store + sketch.  Bg RHS per CTA (grid.y = B / Bg).
+// normalise + store + sketch.  Bg RHS per CTA (grid.y = B / Bg).  want_sw
+// (initialisation only) also sketches the unrounded v_1 = b / beta, which
+// gives c = S b = beta * S v_1.  Float modes use split int32 counters
+// (2^-34 quantum); F64 storage uses int64 shared atomics with 2^-F,
+// F = 61 - ceil(log2(n+1)).
 // ------------------------------------------------------------------------
 template <class T, class Acc>
 __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams sp, int want_sw, int Bg) {
     extern __shared__ unsigned char smem_raw[];
-    long long* s_sv = (long long*)smem_raw;                 // [Bg][m_s]
-    long long* s_sw = s_sv + (size_t)Bg * sp.m_s;           // [Bg][m_s] if want_sw
+    constexpr bool f64 = sizeof(Acc) == 8;
+    const int nacc = want_sw ? 2 : 1;
+    const int cnt = nacc * Bg * sp.m_s;          // counters: [acc][rl][row]
+    long long* s_wide = (long long*)smem_raw;
+    int* s_hi = (int*)(s_wide + cnt);
+    int* s_lo = s_hi + cnt;
     __shared__ long long s_prow[kMaxRhs];
     __shared__ Acc s_hval[kMaxRhs];
     __shared__ int s_ok[kMaxRhs];
@@ -275,11 +353,11 @@ __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams
     DevState* st = bf.st;
     const int j = st->j;
     const int jn = j + 1;                 // index of the new basis vector
+    if (jn > g.k_max) return;             // a step past k_max writes nothing
     const int kb = jn & 1;
     const int B = g.B;
     const int r0 = blockIdx.y * Bg;
     const Acc* w = (const Acc*)bf.w;
-    const bool f64 = sizeof(Acc) == 8;
 
     if (threadIdx.x < Bg) {
         const int r = r0 + threadIdx.x;
@@ -312,58 +390,74 @@ __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams
         s_ok[threadIdx.x] = ok;
         s_code[threadIdx.x] = code;
     }
-    const int nacc = want_sw ? 2 : 1;
-    for (int t = threadIdx.x; t < nacc * Bg * sp.m_s; t += blockDim.x) s_sv[t] = 0;
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        s_wide[t] = 0;
+        if (!f64) { s_hi[t] = 0; s_lo[t] = 0; }
+    }
     __syncthreads();
 
     bool any_ok = false;
     for (int q = 0; q < Bg; ++q) any_ok |= s_ok[q] != 0;
+    const int F = g.F;
     if (any_ok) {
         T* vout = (T*)bf.V + (size_t)jn * g.ldv;
         const long long total = g.n * Bg;      // (i, rl) pairs this CTA's group covers
-        for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-             t += (long long)gridDim.x * blockDim.x) {
+        const long long stride = (long long)gridDim.x * blockDim.x;
+        const int fold_rounds = kFoldEvery / 256;
+        int round = 0;
+        for (long long t0 = blockIdx.x * (long long)blockDim.x; t0 < total; t0 += stride) {
+            const long long t = t0 + threadIdx.x;
             const long long i = t / Bg;
             const int rl = (int)(t - i * Bg);
-            if (!s_ok[rl]) continue;
-            const long long e = i * B + r0 + rl;
-            const Acc v = (i == s_prow[rl]) ? (Acc)1 : w[e] / s_hval[rl];
-            const T vs = from_acc<T>(v);
-            vout[e] = vs;
-            int rows[16];
-            unsigned neg;
-            if (sp.zeta == 8) sketch_column8(sp, i, rows, &neg);
-            else sketch_column(sp, i, rows, &neg);
-            const long long fv = fixed_from(to_acc(vs), g.F);
-            long long* acc = s_sv + (size_t)rl * sp.m_s;
-            if (fv) {
+            if (t < total && s_ok[rl]) {
+                const long long e = i * B + r0 + rl;
+                const Acc v = (i == s_prow[rl]) ? (Acc)1 : w[e] / s_hval[rl];
+                const T vs = from_acc<T>(v);
+                vout[e] = vs;
+                const long long fv = fixed_from(to_acc(vs), F);
+                const long long fw = want_sw ? fixed_from(v, F) : 0;
+                if (fv || fw) {
+                    int rows[16];
+                    unsigned neg;
+                    if (sp.zeta == 8) sketch_column8(sp, i, rows, &neg);
+                    else sketch_column(sp, i, rows, &neg);
+                    const int o1 = rl * sp.m_s, o2 = (Bg + rl) * sp.m_s;
 #pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    if (q < sp.zeta)
-                        atomicAdd((unsigned long long*)&acc[rows[q]],
-                                  (unsigned long long)(((neg >> q) & 1u) ? -fv : fv));
-            }
-            if (want_sw) {
-                const long long fw = fixed_from(v, g.F);
-                long long* acw = s_sw + (size_t)rl * sp.m_s;
-                if (fw) {
-#pragma unroll
-                    for (int q = 0; q < 16; ++q)
-                        if (q < sp.zeta)
-                            atomicAdd((unsigned long long*)&acw[rows[q]],
-                                      (unsigned long long)(((neg >> q) & 1u) ? -fw : fw));
+                    for (int q = 0; q < 16; ++q) {
+                        if (q < sp.zeta) {
+                            const bool ng = (neg >> q) & 1u;
+                            if (f64) {
+                                if (fv) atomicAdd((unsigned long long*)&s_wide[o1 + rows[q]], (unsigned long long)(ng ? -fv : fv));
+                                if (fw) atomicAdd((unsigned long long*)&s_wide[o2 + rows[q]], (unsigned long long)(ng ? -fw : fw));
+                            } else {
+                                if (fv) split_add(s_hi, s_lo, o1 + rows[q], ng ? -fv : fv);
+                                if (fw) split_add(s_hi, s_lo, o2 + rows[q], ng ? -fw : fw);
+                            }
+                        }
+                    }
                 }
+            }
+            if (!f64 && ++round == fold_rounds) {
+                __syncthreads();
+                split_fold(s_hi, s_lo, s_wide, cnt);
+                __syncthreads();
+                round = 0;
             }
         }
     }
     __syncthreads();
+    if (!f64) {
+        split_fold(s_hi, s_lo, s_wide, cnt);
+        __syncthreads();
+    }
     const int K1 = g.k_max + 1;
-    for (int t = threadIdx.x; t < Bg * sp.m_s; t += blockDim.x) {
-        const int rl = t / sp.m_s, row = t - rl * sp.m_s;
-        if (!s_ok[rl]) continue;
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const int a = t / (Bg * sp.m_s);
+        const int rem = t - a * Bg * sp.m_s;
+        const int rl = rem / sp.m_s, row = rem - rl * sp.m_s;
+        if (!s_ok[rl] || !s_wide[t]) continue;
         const size_t dst = ((size_t)(r0 + rl) * K1 + jn) * sp.m_s + row;
-        if (s_sv[t]) atomicAdd((unsigned long long*)&bf.accSV[dst], (unsigned long long)s_sv[t]);
-        if (want_sw && s_sw[t]) atomicAdd((unsigned long long*)&bf.accSW[dst], (unsigned long long)s_sw[t]);
+        atomicAdd((unsigned long long*)&((a == 0) ? bf.accSV : bf.accSW)[dst], (unsigned long long)s_wide[t]);
     }
     // bookkeeping for this CTA's RHS group (one CTA per group)
     if (blockIdx.x == 0 && threadIdx.x < Bg) {
@@ -519,7 +613,8 @@ cudaError_t launch_pivot_solve(int storage, const Geom& g, const Bufs& bf, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_update(int storage, const Geom& g, const Bufs& bf, int num_sms, cudaStream_t s) {
+cudaError_t launch_update(int storage, const Geom& g, const Bufs& bf, const SketchParams& sp, int num_sms,
+                          cudaStream_t s) {
     const int K1 = g.k_max + 1;
     int per_thread = 0;
     IPF_DISPATCH_STORAGE(storage, { per_thread = 16 / (int)sizeof(T); });
@@ -536,19 +631,25 @@ cudaError_t launch_update(int storage, const Geom& g, const Bufs& bf, int num_sm
         k_argmin_d<<<(int)b2, 256, 0, s>>>(g, bf);
         return cudaGetLastError();
     }
-    const size_t smem = (size_t)K1 * g.B * sizeof(float);
+    const size_t zc = g.want_z ? (size_t)g.B * g.m_s : 0;
+    const size_t smem = zc * 16 + (size_t)K1 * g.B * sizeof(float);
+    auto go = [&](auto fn) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        fn<<<(int)blocks, 256, smem, s>>>(g, bf, sp);
+        return cudaGetLastError();
+    };
     switch (storage) {
-        case IPF_STORE_F32: k_update_f<float><<<(int)blocks, 256, smem, s>>>(g, bf); break;
-        case IPF_STORE_BF16: k_update_f<__nv_bfloat16><<<(int)blocks, 256, smem, s>>>(g, bf); break;
-        case IPF_STORE_F16: k_update_f<__half><<<(int)blocks, 256, smem, s>>>(g, bf); break;
+        case IPF_STORE_F32: return go(k_update_f<float>);
+        case IPF_STORE_BF16: return go(k_update_f<__nv_bfloat16>);
+        case IPF_STORE_F16: return go(k_update_f<__half>);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 static int pick_group(int B, int m_s, int nacc) {
     int Bg = B;
-    while (Bg > 1 && (size_t)Bg * m_s * 8 * nacc > 96 * 1024) Bg >>= 1;
+    while (Bg > 1 && (size_t)Bg * m_s * 16 * nacc > 96 * 1024) Bg >>= 1;
     return Bg;
 }
 
@@ -556,7 +657,7 @@ cudaError_t launch_normalize(int storage, const Geom& g, const Bufs& bf, const S
                              int num_sms, cudaStream_t s) {
     const int nacc = want_sw ? 2 : 1;
     const int Bg = pick_group(g.B, g.m_s, nacc);
-    const size_t smem = (size_t)Bg * g.m_s * 8 * nacc;
+    const size_t smem = (size_t)Bg * g.m_s * 16 * nacc;
     const long long work = g.n * Bg;
     long long bx = (work + 255) / 256;
     const int groups = g.B / Bg;

@@ -9,6 +9,8 @@
 //                 image, then the motion stencil, all in one tile.
 //   k_csr         CSR product for B interleaved right-hand sides: one warp
 //                 per row, lanes grouped by RHS so A is read once for all B.
+#include <cstring>
+
 #include "ipf_internal.cuh"
 
 namespace ipf {
@@ -273,7 +275,37 @@ __global__ void k_interleave(const float* __restrict__ src, float* __restrict__ 
     }
 }
 
+__global__ void k_csr_row_abs_max(const long long* __restrict__ rowptr, const float* __restrict__ vals, long long m,
+                                  unsigned* out) {
+    unsigned best = 0;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < m; r += (long long)gridDim.x * blockDim.x) {
+        float t = 0.f;
+        for (long long q = rowptr[r]; q < rowptr[r + 1]; ++q) t += fabsf(vals[q]);
+        const unsigned u = __float_as_uint(t * 1.0001f);
+        best = u > best ? u : best;
+    }
+    atomicMax(out, best);
+}
+
 }  // namespace
+
+// max row sum of |a| for a device CSR matrix, synchronous, into *host_out
+cudaError_t launch_csr_row_abs_max(const OpDev& op, float* host_out, cudaStream_t s) {
+    unsigned* d = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&d, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(d, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) {
+        k_csr_row_abs_max<<<256, 256, 0, s>>>(op.rowptr, op.vals, op.rows, d);
+        e = cudaGetLastError();
+    }
+    unsigned h = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    cudaError_t e2 = cudaFreeAsync(d, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    memcpy(host_out, &h, sizeof(float));
+    return e != cudaSuccess ? e : e2;
+}
 
 cudaError_t launch_op_apply(const OpDev& op, int storage, const void* vbase, long long ldv, const int* jptr, int B,
                             void* w, cudaStream_t s) {

@@ -49,15 +49,20 @@ __device__ __forceinline__ int kuse_of(const DevState* st, int r, int k) {
     return kd < k ? kd : k;
 }
 
-// M[r][col], T[r][col] (column-major, ld = m)
-__global__ void k_form(Geom g, Bufs bf, int k, int zeta, int use_sw_direct, int need_T, double* Mw, double* Tw) {
+// M[r][col], T[r][col] (column-major, ld = m).  Column col < kb of M is
+// z_col = S A v_col (the DIRECT form) or (S V_{kb+1} H)(:, col); column kb is
+// c = S b = beta * S (b / beta).
+__global__ void k_form(Geom g, Bufs bf, int k, int zeta, int use_z, int need_T, double* Mw, double* Tw) {
     const int r = blockIdx.y;
     const int kb = kuse_of(bf.st, r, k);
     const int K1 = g.k_max + 1;
     const int m = g.m_s;
-    const double scale = ldexp(1.0, -g.F) / sqrt((double)zeta);
+    const double sq = sqrt((double)zeta);
+    const double scale = ldexp(1.0, -g.F) / sq;
+    const double scale_z = ldexp(1.0, -g.Fz) / sq;
     const long long* sv = bf.accSV + (size_t)r * K1 * m;
     const long long* sw = bf.accSW + (size_t)r * K1 * m;
+    const long long* sz = bf.accSZ + (size_t)r * g.k_max * m;
     const double* H = bf.H + (size_t)r * K1 * g.k_max;
     double* M = Mw + (size_t)r * m * (k + 1);
     double* T = Tw ? Tw + (size_t)r * m * k : nullptr;
@@ -68,15 +73,17 @@ __global__ void k_form(Geom g, Bufs bf, int k, int zeta, int use_sw_direct, int 
         const int col = (int)(t / m), row = (int)(t - (long long)col * m);
         double val;
         if (col < kb) {
-            double s = 0.0;
-            const double* Hc = H + (size_t)K1 * col;
-            for (int i = 0; i <= col; ++i) s = fma((double)sv[(size_t)i * m + row] * scale, Hc[i], s);
-            const long long* last = use_sw_direct ? sw : sv;
-            s = fma((double)last[(size_t)(col + 1) * m + row] * scale, Hc[col + 1], s);
-            val = s;
+            if (use_z) {
+                val = (double)sz[(size_t)col * m + row] * scale_z;
+            } else {
+                double s = 0.0;
+                const double* Hc = H + (size_t)K1 * col;
+                for (int i = 0; i <= col + 1; ++i) s = fma((double)sv[(size_t)i * m + row] * scale, Hc[i], s);
+                val = s;
+            }
             if (need_T) T[(size_t)col * m + row] = (double)sv[(size_t)col * m + row] * scale;
         } else {
-            val = beta * (double)sw[row] * scale;      // c = S b = beta * S (b / beta)
+            val = beta * (double)sw[row] * scale;
         }
         M[(size_t)col * m + row] = val;
     }
@@ -332,8 +339,8 @@ cudaError_t solve_error_flag(const void* work, const Geom& g, int* flag) {
     return cudaMemcpy(flag, (const char*)work + L.err_off, sizeof(int), cudaMemcpyDeviceToHost);
 }
 
-cudaError_t launch_solve_prepare(const Geom& g, const Bufs& bf, int zeta, int k, bool need_T, int zform,
-                                 bool have_sw, void* work, int nl_max, int num_sms, cudaStream_t s) {
+cudaError_t launch_solve_prepare(const Geom& g, const Bufs& bf, int zeta, int k, bool need_T, bool use_z,
+                                 void* work, int nl_max, int num_sms, cudaStream_t s) {
     SolveLayout L = layout_for(g, nl_max);
     char* base = (char*)work;
     double* Mw = (double*)(base + L.M_off);
@@ -346,8 +353,7 @@ cudaError_t launch_solve_prepare(const Geom& g, const Bufs& bf, int zeta, int k,
     if (e != cudaSuccess) return e;
     {
         dim3 grid((unsigned)((g.m_s * (k + 1) + 255) / 256), (unsigned)g.B);
-        const bool direct_sw = (zform == IPF_Z_DIRECT) && have_sw;
-        k_form<<<grid, 256, 0, s>>>(g, bf, k, zeta, direct_sw ? 1 : 0, need_T ? 1 : 0, Mw, Tw);
+        k_form<<<grid, 256, 0, s>>>(g, bf, k, zeta, use_z ? 1 : 0, need_T ? 1 : 0, Mw, Tw);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int njobs = g.B * (need_T ? 2 : 1);
