@@ -214,8 +214,10 @@ const char* ipf_last_error(const ipf_ctx* ctx);
 /* ---- operator and sketch kernels as standalone calls (device pointers) ---- */
 
 /* Upload an operator (see ipf_operator for ownership) and apply it:
- * w = A v for nrhs vectors, v and w device float32 nrhs x n, vector r at
- * offset r*n.  Runs on `stream` (cudaStream_t, may be NULL).              */
+ * w = A v for nrhs vectors (CSR: nrhs a power of two <= 32).  v is device
+ * float32 nrhs x n (vector r at offset r*n), w device float32 nrhs x m
+ * (m = rows for CSR, n otherwise); the caller guarantees those sizes.
+ * Runs on `stream` (cudaStream_t, may be NULL).                           */
 ipf_status ipf_op_create(const ipf_operator* op, ipf_op** out);
 ipf_status ipf_op_apply(ipf_op* h, const float* v_dev, float* w_dev, int nrhs, void* stream);
 void ipf_op_destroy(ipf_op* h);

@@ -105,6 +105,14 @@ class IpfError(RuntimeError):
         super().__init__(f"{status_str(code)}{': ' + msg if msg else ''}")
 
 
+def _check_size(a, want: int, name: str):
+    """Refuse buffers whose element count does not match the operator: the C
+    ABI takes raw pointers and cannot check them itself."""
+    got = int(a.size) if isinstance(a, np.ndarray) else int(a.numel())
+    if got != int(want):
+        raise ValueError(f"{name} has {got} elements, expected {want}")
+
+
 def status_str(code: int) -> str:
     return load().ipf_status_str(int(code)).decode()
 
@@ -193,11 +201,12 @@ class Context:
         self._keep = list(keep or [])
         if isinstance(b, np.ndarray):
             b = np.ascontiguousarray(b, dtype=np.float32)
-        self._keep.append(b)
-        ptr, mem = _ptr(b)
         self.cfg = cfg
         self.nrhs = cfg.nrhs
         self.n = op.cols if op.kind == IPF_OP_CSR else op.rows * op.cols
+        _check_size(b, self.nrhs * self.n, "b")
+        self._keep.append(b)
+        ptr, mem = _ptr(b)
         h = C.c_void_p()
         st = self._lib.ipf_create(C.byref(op), ptr, mem, C.byref(cfg), C.byref(h))
         if st != IPF_OK:
@@ -214,6 +223,7 @@ class Context:
         if isinstance(b, np.ndarray):
             b = np.ascontiguousarray(b, dtype=np.float32)
             self._keep.append(b)
+        _check_size(b, self.nrhs * self.n, "b")
         ptr, mem = _ptr(b)
         self._check(self._lib.ipf_reset(self.h, ptr, mem), "ipf_reset")
 
@@ -247,6 +257,7 @@ class Context:
             ptr, mem = x.ctypes.data, IPF_MEM_HOST
         else:
             x = out
+            _check_size(out, nl * self.nrhs * self.n, "out")
             ptr, mem = _ptr(out)
         st = self._lib.ipf_solve(self.h, int(k), lam.ctypes.data_as(_dp), nl, ptr, mem, info)
         self._check(st, "ipf_solve")
@@ -290,6 +301,8 @@ class Operator:
     def __init__(self, op: ipf_operator, keep=None):
         self._lib = load()
         self._keep = keep
+        self.m = op.rows if op.kind == IPF_OP_CSR else op.rows * op.cols
+        self.n = op.cols if op.kind == IPF_OP_CSR else op.rows * op.cols
         h = C.c_void_p()
         st = self._lib.ipf_op_create(C.byref(op), C.byref(h))
         if st != IPF_OK:
@@ -297,6 +310,8 @@ class Operator:
         self.h = h
 
     def apply(self, v, w, nrhs: int = 1, stream=None):
+        _check_size(v, nrhs * self.n, "v")
+        _check_size(w, nrhs * self.m, "w")
         st = self._lib.ipf_op_apply(self.h, v.data_ptr(), w.data_ptr(), int(nrhs), stream)
         if st != IPF_OK:
             raise IpfError(st, "ipf_op_apply")
@@ -315,6 +330,7 @@ class Operator:
 
 def sketch_apply(x, m_s: int, zeta: int, seed: int, y, stream=None):
     """y (device float64, m_s) = S x (device float32, n)."""
+    _check_size(y, m_s, "y")
     st = load().ipf_sketch_apply(x.data_ptr(), int(x.numel()), int(m_s), int(zeta), int(seed), y.data_ptr(), stream)
     if st != IPF_OK:
         raise IpfError(st, "ipf_sketch_apply")

@@ -148,46 +148,6 @@ cudaError_t upload_op(const ipf_operator* op, Alloc& al, OpDev* d, cudaStream_t 
     return e;
 }
 
-// bound on ||A||_inf (max row sum of |a|) for the z-sketch's fixed-point scale
-cudaError_t operator_inf_norm(const ipf_operator* op, const OpDev& d, float* out, cudaStream_t s) {
-    auto host_copy = [&](const float* src, size_t count, std::vector<float>& dst) -> cudaError_t {
-        dst.resize(count);
-        if (op->mem == IPF_MEM_HOST) {
-            memcpy(dst.data(), src, count * sizeof(float));
-            return cudaSuccess;
-        }
-        return cudaMemcpy(dst.data(), src, count * sizeof(float), cudaMemcpyDeviceToHost);
-    };
-    auto l1 = [](const std::vector<float>& v) {
-        double t = 0;
-        for (float x : v) t += std::fabs((double)x);
-        return t;
-    };
-    std::vector<float> a, b2, m;
-    cudaError_t e = cudaSuccess;
-    if (op->kind == IPF_OP_PSF2D) {
-        if ((e = host_copy(op->psf, (size_t)op->ph * op->pw, a)) != cudaSuccess) return e;
-        *out = (float)l1(a);
-    } else if (op->kind == IPF_OP_PSF2D_SEP_MOTION) {
-        if ((e = host_copy(op->sep_row, op->slen, a)) != cudaSuccess) return e;
-        if ((e = host_copy(op->sep_col, op->slen, b2)) != cudaSuccess) return e;
-        if ((e = host_copy(op->motion, (size_t)op->mlen * op->mlen, m)) != cudaSuccess) return e;
-        *out = (float)(l1(a) * l1(b2) * l1(m));
-    } else if (op->mem == IPF_MEM_HOST) {
-        double mx = 0;
-        for (int r = 0; r < op->rows; ++r) {
-            double t = 0;
-            for (long long q = op->rowptr[r]; q < op->rowptr[r + 1]; ++q) t += std::fabs((double)op->vals[q]);
-            mx = t > mx ? t : mx;
-        }
-        *out = (float)mx;
-    } else {
-        e = launch_csr_row_abs_max(d, out, s);
-    }
-    if (!(*out > 0.f) || !std::isfinite(*out)) *out = 1.f;
-    return e;
-}
-
 }  // namespace
 
 struct ipf_ctx {
@@ -293,6 +253,12 @@ double op_bytes(const ipf_ctx* c) {
     return b;
 }
 
+// the unrounded normalised vector differs from the stored one only for
+// BF16/FP16 storage; its sketch then gives the DIRECT z_j by linearity
+bool sw_on(const ipf_ctx* c) {
+    return c->g.want_z && (c->storage == IPF_STORE_BF16 || c->storage == IPF_STORE_F16);
+}
+
 // one Hessenberg step; every kernel takes j from device memory, so the same
 // sequence serves every step and can be captured once.  `j` (host count) is
 // only used to label profile bytes.
@@ -306,10 +272,10 @@ cudaError_t one_step(ipf_ctx* c, int j) {
     if ((e = timed(c, 1, 0.0, [&] { return launch_pivot_solve(c->storage, c->g, c->bf, c->s); })) != cudaSuccess)
         return e;
     if ((e = timed(c, 2, (double)(j + 1) * N * sv + 2.0 * N * ab + N / 8.0,
-                   [&] { return launch_update(c->storage, c->g, c->bf, c->sp, c->num_sms, c->s); })) != cudaSuccess)
+                   [&] { return launch_update(c->storage, c->g, c->bf, c->num_sms, c->s); })) != cudaSuccess)
         return e;
     return timed(c, 3, N * ab + N * sv,
-                 [&] { return launch_normalize(c->storage, c->g, c->bf, c->sp, false, c->num_sms, c->s); });
+                 [&] { return launch_normalize(c->storage, c->g, c->bf, c->sp, sw_on(c), c->num_sms, c->s); });
 }
 
 // clear the state and enqueue Algorithm 1's initialisation for b
@@ -322,13 +288,11 @@ cudaError_t init_solve(ipf_ctx* c, const float* bdev) {
     if ((e = cudaMemsetAsync(c->bf.ispiv, 0, (g.ldv / 32 + 1) * sizeof(unsigned), c->s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->bf.accSV, 0, B * K1 * g.m_s * sizeof(long long), c->s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->bf.accSW, 0, B * K1 * g.m_s * sizeof(long long), c->s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(c->bf.accSZ, 0, B * (size_t)g.k_max * g.m_s * sizeof(long long), c->s)) != cudaSuccess)
-        return e;
     return timed(c, 4, 0.0, [&] {
         cudaError_t ee = launch_reset_state(c->bf.st, c->s);
         if (ee != cudaSuccess) return ee;
         if ((ee = launch_load_rhs(c->storage, bdev, g, c->bf, c->s)) != cudaSuccess) return ee;
-        if ((ee = launch_update(c->storage, g, c->bf, c->sp, c->num_sms, c->s)) != cudaSuccess) return ee;
+        if ((ee = launch_update(c->storage, g, c->bf, c->num_sms, c->s)) != cudaSuccess) return ee;
         return launch_normalize(c->storage, g, c->bf, c->sp, true, c->num_sms, c->s);
     });
 }
@@ -366,7 +330,7 @@ size_t ipf_footprint(const ipf_operator* op, const ipf_config* cfg) {
     const size_t K1 = (size_t)cfg->k_max + 1;
     size_t bytes = K1 * ldv * sb + ldv * acc + ldv / 8 + 4096;
     bytes += B * K1 * (sizeof(int) + sizeof(double) * cfg->k_max + acc * K1) + K1 * B * acc;
-    bytes += 3 * (size_t)B * K1 * cfg->m_s * 8;
+    bytes += 2 * (size_t)B * K1 * cfg->m_s * 8;
     Geom g; g.n = n; g.B = B; g.N = n * B; g.ldv = (long long)ldv; g.k_max = cfg->k_max; g.m_s = cfg->m_s; g.F = 0;
     bytes += solve_ws_for(g) + 2 * (size_t)B * n * 4 + 256;
     if (op->kind == IPF_OP_CSR && op->mem == IPF_MEM_HOST)
@@ -392,8 +356,9 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     if (cfg.storage == IPF_STORE_F64 && B != 1) return IPF_ERR_UNSUPPORTED;
     if (cfg.penalty != IPF_PEN_SKETCHED_X && cfg.penalty != IPF_PEN_Y) return IPF_ERR_ARG;
     if (cfg.zform != IPF_Z_DIRECT && cfg.zform != IPF_Z_HESSENBERG && cfg.zform != IPF_Z_AUTO) return IPF_ERR_ARG;
-    const bool z_ok = cfg.storage != IPF_STORE_F64 && B <= 4;
+    const bool z_ok = cfg.storage != IPF_STORE_F64;
     if (cfg.zform == IPF_Z_DIRECT && !z_ok) return IPF_ERR_UNSUPPORTED;
+    if (cfg.k_max > 255) return IPF_ERR_UNSUPPORTED;
     if (b_mem != IPF_MEM_HOST && b_mem != IPF_MEM_DEVICE) return IPF_ERR_ARG;
     const size_t accb = cfg.storage == IPF_STORE_F64 ? 8 : 4;
     const size_t pivsmem = (size_t)(cfg.k_max + 2) * 8 + (size_t)cfg.k_max * (cfg.k_max + 1) / 2 * accb;
@@ -434,15 +399,6 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     g.m_s = cfg.m_s;
     g.F = cfg.storage == IPF_STORE_F64 ? fixed_exponent(n, 0) : kSplitS;
     g.want_z = (cfg.zform == IPF_Z_DIRECT || (cfg.zform == IPF_Z_AUTO && z_ok)) ? 1 : 0;
-    {
-        // |A v| <= ||A||_inf max|v| <= ||A||_inf (|v| <= 1 under max pivoting); the
-        // z-sketch scale puts that bound (with 0.1% headroom) just under 2^34
-        float bound = 1.f;
-        CK("operator norm", operator_inf_norm(op, c->op, &bound, c->s));
-        int ez = 0;
-        std::frexp((double)bound * 1.001 + 1e-30, &ez);
-        g.Fz = kSplitS - ez;
-    }
     c->sp = make_sketch_params(cfg.seed, cfg.m_s, cfg.zeta);
     const size_t K1 = (size_t)cfg.k_max + 1;
     const size_t sb = storage_bytes(cfg.storage);
@@ -457,7 +413,6 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     CK("alloc ispiv", c->al.get((void**)&bf.ispiv, (g.ldv / 32 + 1) * sizeof(unsigned)));
     CK("alloc SV", c->al.get((void**)&bf.accSV, B * K1 * cfg.m_s * sizeof(long long)));
     CK("alloc SW", c->al.get((void**)&bf.accSW, B * K1 * cfg.m_s * sizeof(long long)));
-    CK("alloc SZ", c->al.get((void**)&bf.accSZ, B * (size_t)cfg.k_max * cfg.m_s * sizeof(long long)));
     c->solve_ws_bytes = solve_ws_for(g);
     CK("alloc solve", c->al.get(&c->solve_ws, c->solve_ws_bytes));
     CK("alloc lambdas", c->al.get((void**)&c->lam_dev, sizeof(double) * kLamChunk));
@@ -617,8 +572,7 @@ ipf_status ipf_solve(ipf_ctx* c, int k, const double* lambdas, int nl, float* x_
     for (int l = 0; l < nl; ++l) any_pos |= lambdas[l] > 0.0;
     const bool need_T = any_pos && c->cfg.penalty == IPF_PEN_SKETCHED_X;
     e = timed(c, 5, 0.0, [&] {
-        return launch_solve_prepare(g, c->bf, c->cfg.zeta, k, need_T, g.want_z != 0, c->solve_ws, nlm, c->num_sms,
-                                    c->s);
+        return launch_solve_prepare(g, c->bf, c->cfg.zeta, k, need_T, sw_on(c), c->solve_ws, nlm, c->num_sms, c->s);
     });
     if (e != cudaSuccess) return cuda_fail(c, "solve prepare", e);
     const size_t slice = (size_t)g.n * c->B;
@@ -691,8 +645,27 @@ ipf_status ipf_export(ipf_ctx* c, int r, int* pivots, double* H, double* SV, dou
     };
     if (SV && (e = grab(c->bf.accSV + r * K1 * m, K1 * m, std::ldexp(1.0, -c->g.F) / sq, SV)) != cudaSuccess)
         return cuda_fail(c, "export SV", e);
-    if (SZ && (e = grab(c->bf.accSZ + r * km * m, km * m, std::ldexp(1.0, -c->g.Fz) / sq, SZ)) != cudaSuccess)
-        return cuda_fail(c, "export SZ", e);
+    if (SZ) {
+        // z_j = S A v_j = S V_{j+1} h_j + H(j+1,j) (S w)_{j+1}, w the unrounded
+        // normalised vector (the stored one unless the storage rounds)
+        const double sc = std::ldexp(1.0, -c->g.F) / sq;
+        std::vector<double> sv(K1 * m), sw(K1 * m), Hh(K1 * km);
+        if ((e = grab(c->bf.accSV + r * K1 * m, K1 * m, sc, sv.data())) != cudaSuccess) return cuda_fail(c, "export SZ", e);
+        if ((e = grab(c->bf.accSW + r * K1 * m, K1 * m, sc, sw.data())) != cudaSuccess) return cuda_fail(c, "export SZ", e);
+        if ((e = cudaMemcpy(Hh.data(), c->bf.H + r * K1 * km, K1 * km * sizeof(double), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(c, "export SZ", e);
+        const bool use_sw = sw_on(c);
+        for (size_t col = 0; col < km; ++col) {
+            const double* hcol = Hh.data() + K1 * col;
+            for (int row = 0; row < m; ++row) {
+                double t = 0.0;
+                for (size_t i = 0; i <= col; ++i) t += sv[i * m + row] * hcol[i];
+                const std::vector<double>& last = use_sw ? sw : sv;
+                t += last[(col + 1) * m + row] * hcol[col + 1];
+                SZ[col * m + row] = t;
+            }
+        }
+    }
     if (cvec) {
         if ((e = grab(c->bf.accSW + r * K1 * m, m, std::ldexp(1.0, -c->g.F) / sq, cvec)) != cudaSuccess)
             return cuda_fail(c, "export c", e);
@@ -792,10 +765,7 @@ ipf_status ipf_op_create(const ipf_operator* op, ipf_op** out) {
 
 ipf_status ipf_op_apply(ipf_op* h, const float* v_dev, float* w_dev, int nrhs, void* stream) {
     if (!h || !v_dev || !w_dev || nrhs < 1) return IPF_ERR_ARG;
-    if (h->op.kind != IPF_OP_CSR && nrhs > 1) {
-        // one product per vector
-    }
-    if (h->op.kind == IPF_OP_CSR && !pow2_le32(nrhs) && nrhs != 1) return IPF_ERR_ARG;
+    if (h->op.kind == IPF_OP_CSR && !pow2_le32(nrhs)) return IPF_ERR_ARG;
     cudaError_t e = launch_op_apply_f32_plain(h->op, v_dev, w_dev, nrhs, (cudaStream_t)stream);
     return e == cudaSuccess ? IPF_OK : IPF_ERR_CUDA;
 }

@@ -213,9 +213,8 @@ struct Geom {
     long long ldv;      // stride between basis vectors (elements), multiple of 64
     int k_max;
     int m_s;
-    int F;              // fixed-point exponent of S V (and S b / beta)
-    int Fz;             // fixed-point exponent of S A v_j (|A v_j| <= 2^(kSplitS - Fz))
-    int want_z;         // accumulate z_j = S A v_j in the update kernel
+    int F;              // fixed-point exponent of the sketch accumulators
+    int want_z;         // DIRECT form: z_j = S A v_j (needs S of the unrounded vectors)
 };
 
 struct Bufs {
@@ -228,8 +227,8 @@ struct Bufs {
     void* coef;                    // [(k_max+1)*B] Acc, h for the update
     unsigned* ispiv;               // bitmap over N elements
     long long* accSV;              // [B][k_max+1][m_s] fixed-point S V
-    long long* accSW;              // [B][k_max+1][m_s] fixed-point; column 0 = S (b / beta)
-    long long* accSZ;              // [B][k_max][m_s] fixed-point z_j = S A v_j
+    long long* accSW;              // [B][k_max+1][m_s] fixed-point S of the unrounded vectors
+                                   // (column 0 = S (b / beta), others for BF16/FP16 storage)
 };
 
 // operator on the device
@@ -257,15 +256,13 @@ struct OpDev {
 // vbase + (*jptr) * ldv is the input vector (jptr NULL: vbase itself)
 cudaError_t launch_op_apply(const OpDev& op, int storage, const void* vbase, long long ldv, const int* jptr, int B,
                             void* w, cudaStream_t s);
-cudaError_t launch_csr_row_abs_max(const OpDev& op, float* host_out, cudaStream_t s);
 cudaError_t launch_op_apply_f32_plain(const OpDev& op, const float* v, float* w, int nrhs,
                                       cudaStream_t s);
 // k_hess.cu
 cudaError_t launch_reset_state(DevState* st, cudaStream_t s);
 cudaError_t launch_load_rhs(int storage, const float* b, const Geom& g, const Bufs& bf, cudaStream_t s);
 cudaError_t launch_pivot_solve(int storage, const Geom& g, const Bufs& bf, cudaStream_t s);
-cudaError_t launch_update(int storage, const Geom& g, const Bufs& bf, const SketchParams& sp, int num_sms,
-                          cudaStream_t s);
+cudaError_t launch_update(int storage, const Geom& g, const Bufs& bf, int num_sms, cudaStream_t s);
 cudaError_t launch_normalize(int storage, const Geom& g, const Bufs& bf, const SketchParams& sp,
                              bool want_sw, int num_sms, cudaStream_t s);
 cudaError_t launch_sketch_vector(const float* x, long long n, const SketchParams& sp, int F,
@@ -277,7 +274,7 @@ cudaError_t launch_sketch_finish(const long long* acc, int m, long long n, int z
 // k_small.cu: workspace for k <= k_max and up to nl_max lambdas per chunk
 size_t solve_workspace_bytes(const Geom& g, int nl_max);
 // form M = [Z | c] (and T = S V_k) and their R factors
-cudaError_t launch_solve_prepare(const Geom& g, const Bufs& bf, int zeta, int k, bool need_T, bool use_z,
+cudaError_t launch_solve_prepare(const Geom& g, const Bufs& bf, int zeta, int k, bool need_T, bool use_sw,
                                  void* work, int nl_max, int num_sms, cudaStream_t s);
 // per lambda: y, then x = V_k y into x_dev ([l][r][n] float32)
 cudaError_t launch_solve_lambdas(int storage, const Geom& g, const Bufs& bf, int k, bool need_T,

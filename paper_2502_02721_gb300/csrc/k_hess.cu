@@ -36,8 +36,16 @@ __global__ void k_load_rhs(const float* __restrict__ b, Acc* __restrict__ w, lon
 }
 
 // ------------------------------------------------------------------------
-// pivot-block forward substitution, one CTA per RHS
+// pivot-block forward substitution, one CTA per RHS.  L_p is kept packed
+// row-major, strictly lower (row i, entries c < i, at offset i(i-1)/2; the
+// unit diagonal is implicit), so each step appends one contiguous row and
+// the whole block is one flat copy into shared memory.  Warp 0 then solves
+// L_p h = u(p) in FP64 with lane l holding rows l, l+32, ..., l+224 in
+// registers: x_c is broadcast by a shuffle and every lane updates its rows
+// below c, with no block-wide barrier per column.  j < 256.
 // ------------------------------------------------------------------------
+__host__ __device__ constexpr size_t lp_stride(int k_max) { return (size_t)(k_max + 1) * k_max / 2 + 1; }
+
 template <class T, class Acc>
 __global__ void __launch_bounds__(256) k_pivot_solve(Geom g, Bufs bf) {
     extern __shared__ unsigned char smem_raw[];
@@ -45,80 +53,85 @@ __global__ void __launch_bounds__(256) k_pivot_solve(Geom g, Bufs bf) {
     DevState* st = bf.st;
     if (st->status[r] != IPF_OK) return;
     const int j = st->j;
-    if (j < 0 || j >= g.k_max) return;
+    if (j < 0 || j >= g.k_max || j >= 256) return;
     const int K1 = g.k_max + 1;
     const int B = g.B;
     const T* V = (const T*)bf.V;
     const Acc* w = (const Acc*)bf.w;
-    Acc* LpT = (Acc*)bf.LpT + (size_t)r * K1 * K1;
+    Acc* Lp = (Acc*)bf.LpT + (size_t)r * lp_stride(g.k_max);
     const int* piv = bf.piv + (size_t)r * K1;
-
-    // smem: x[0..j] (double), then L strictly-lower packed by column (Acc)
-    double* s_x = (double*)smem_raw;
-    Acc* s_L = (Acc*)(s_x + ((K1 + 1) & ~1));
-
-    // row j of L_p: v_c(p_j), c < j (exact copies of the stored values)
-    const long long pj = (long long)piv[j] * B + r;
+    double* s_g = (double*)smem_raw;
+    Acc* s_L = (Acc*)(s_g + ((K1 + 1) & ~1));
+    const size_t rowj = (size_t)j * (j - 1) / 2;
+    // row j: L(j, c) = v_c(p_j), exact copies of the stored values
+    const size_t pj = (size_t)piv[j] * B + r;
     for (int c = threadIdx.x; c < j; c += blockDim.x) {
         const Acc val = to_acc(V[(size_t)c * g.ldv + pj]);
-        LpT[(size_t)c * K1 + j] = val;
+        Lp[rowj + c] = val;
+        s_L[rowj + c] = val;
     }
-    if (threadIdx.x == 0) LpT[(size_t)j * K1 + j] = (Acc)1;
+    for (size_t t = threadIdx.x; t < rowj; t += blockDim.x) s_L[t] = Lp[t];
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) s_g[i] = (double)w[(size_t)piv[i] * B + r];
     __syncthreads();
-    // packed column c holds rows c+1..j at offset c*j - c*(c-1)/2
-    for (int c = 0; c < j; ++c) {
-        const int off = c * j - (c * (c - 1)) / 2;
-        for (int i = c + 1 + threadIdx.x; i <= j; i += blockDim.x)
-            s_L[off + (i - c - 1)] = LpT[(size_t)c * K1 + i];
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    double x[8];
+    int off[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int i = q * 32 + lane;
+        x[q] = (i <= j) ? s_g[i] : 0.0;
+        off[q] = i * (i - 1) / 2;
     }
-    for (int i = threadIdx.x; i <= j; i += blockDim.x)
-        s_x[i] = (double)w[(long long)piv[i] * B + r];
-    // forward substitution, column oriented: x_i -= L(i,c) x_c for i > c
-    for (int c = 0; c < j; ++c) {
-        __syncthreads();
-        const double xc = s_x[c];
-        const int off = c * j - (c * (c - 1)) / 2;
-        for (int i = c + 1 + threadIdx.x; i <= j; i += blockDim.x)
-            s_x[i] = fma(-(double)s_L[off + (i - c - 1)], xc, s_x[i]);
+#pragma unroll
+    for (int cb = 0; cb < 8; ++cb) {
+        if (cb * 32 >= j) break;
+#pragma unroll
+        for (int cc = 0; cc < 32; ++cc) {
+            const int c = cb * 32 + cc;
+            if (c >= j) break;
+            const double xc = __shfl_sync(0xffffffffu, x[cb], cc);
+#pragma unroll
+            for (int q = cb; q < 8; ++q) {
+                const int i = q * 32 + lane;
+                if (i > c && i <= j) x[q] = fma(-(double)s_L[off[q] + c], xc, x[q]);
+            }
+        }
     }
-    __syncthreads();
     double* Hc = bf.H + (size_t)r * K1 * g.k_max + (size_t)K1 * j;
     Acc* coef = (Acc*)bf.coef;
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-        Hc[i] = s_x[i];
-        coef[(size_t)i * B + r] = (Acc)s_x[i];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int i = q * 32 + lane;
+        if (i <= j) {
+            Hc[i] = x[q];
+            coef[(size_t)i * B + r] = (Acc)x[q];
+        }
     }
 }
 
 // ------------------------------------------------------------------------
-// u -= V_j h ; u(pivots) = 0 ; argmax keys.  Acc = float.
-// With g.want_z (nrhs <= 4) the incoming u = A v_j is also sketched,
-// z_j = S u (Algorithm 1 line 11), exactly, while the V_j loads are in
-// flight: shared split counters [B][m_s], folded every kFoldEvery elements.
+// u -= V_j h ; u(pivots) = 0 ; argmax keys.  Acc = float, B RHS interleaved
+// (compile-time, so element -> (row, RHS) is a shift and a mask).  Each
+// thread owns 16 bytes of every basis column per grid-stride pass and keeps
+// two groups of four 128-bit loads in flight (evict-first: V_j is streamed
+// once, u stays in L2 for the normaliser).
 // ------------------------------------------------------------------------
-template <class T>
-__global__ void __launch_bounds__(256) k_update_f(Geom g, Bufs bf, SketchParams sp) {
+template <class T, int B>
+__global__ void __launch_bounds__(256, 4) k_update_f(Geom g, Bufs bf) {
     constexpr int VEC = Vec16<T>::n;
+    constexpr int LB = (B == 1) ? 0 : (B == 2) ? 1 : (B == 4) ? 2 : (B == 8) ? 3 : (B == 16) ? 4 : 5;
+    constexpr int NK = (B == 1) ? 1 : VEC;           // argmax keys kept per thread
     extern __shared__ unsigned char smem_raw[];
-    const int B = g.B;
-    const int K1 = g.k_max + 1;
-    // smem: wide [B*m] int64, hi [B*m], lo [B*m] int32 (only with z), coefficients
-    const int zc = g.want_z ? B * g.m_s : 0;
-    long long* s_wide = (long long*)smem_raw;
-    int* s_hi = (int*)(s_wide + zc);
-    int* s_lo = s_hi + zc;
-    float* s_coef = (float*)(s_lo + zc);
+    float* s_coef = (float*)smem_raw;
     __shared__ unsigned long long s_key[kMaxRhs];
     __shared__ int s_ok[kMaxRhs];
     DevState* st = bf.st;
     const int j = st->j;
-    if (j >= g.k_max) return;            // never past the last basis column
-    const int nc = j + 1;               // coefficients h_0..h_j (none during init)
-    const bool do_z = g.want_z && j >= 0;
+    if (j >= g.k_max) return;                       // never past the last basis column
+    const int nc = j + 1;                           // coefficients h_0..h_j (none during init)
     const float* coef = (const float*)bf.coef;
     for (int t = threadIdx.x; t < nc * B; t += blockDim.x) s_coef[t] = coef[t];
-    if (do_z)
-        for (int t = threadIdx.x; t < zc; t += blockDim.x) { s_wide[t] = 0; s_hi[t] = 0; s_lo[t] = 0; }
     if (threadIdx.x < B) {
         s_key[threadIdx.x] = 0ull;
         s_ok[threadIdx.x] = st->status[threadIdx.x] == IPF_OK;
@@ -128,124 +141,64 @@ __global__ void __launch_bounds__(256) k_update_f(Geom g, Bufs bf, SketchParams 
 
     const T* V = (const T*)bf.V;
     float* w = (float*)bf.w;
-    unsigned long long best[VEC];
+    const unsigned N = (unsigned)g.N;
+    unsigned long long best[NK];
 #pragma unroll
-    for (int q = 0; q < VEC; ++q) best[q] = 0ull;
-
-    const long long stride = (long long)gridDim.x * blockDim.x * VEC;
-    const long long base0 = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * VEC;
-    const int fold_rounds = kFoldEvery / (256 * VEC);
-    int round = 0;
-    for (long long bstart = (long long)blockIdx.x * blockDim.x * VEC; bstart < g.N; bstart += stride) {
-        const long long base = bstart + (long long)threadIdx.x * VEC;
-        const bool live = base < g.N;
+    for (int q = 0; q < NK; ++q) best[q] = 0ull;
+    const size_t ldv = (size_t)g.ldv;
+    const unsigned stride = gridDim.x * blockDim.x * VEC;
+    const unsigned base0 = (blockIdx.x * blockDim.x + threadIdx.x) * VEC;
+    for (unsigned base = base0; base < N; base += stride) {
         float acc[VEC];
-#pragma unroll
-        for (int q = 0; q < VEC; ++q) acc[q] = 0.f;
-        int c = 0;
-        uint4 raw[4];
-        if (live) {
+        {
             const float4* wp = (const float4*)(w + base);
 #pragma unroll
             for (int q = 0; q < VEC / 4; ++q) {
                 const float4 t4 = wp[q];
                 acc[4 * q] = t4.x; acc[4 * q + 1] = t4.y; acc[4 * q + 2] = t4.z; acc[4 * q + 3] = t4.w;
             }
-            if (nc >= 4) {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) raw[u] = __ldcs((const uint4*)(V + (size_t)u * g.ldv + base));
-            }
-            if (do_z) {
-                // z_j = S u for the incoming u = A v_j
-#pragma unroll
-                for (int q = 0; q < VEC; ++q) {
-                    const long long e = base + q;
-                    const long long i = (B == 1) ? e : e / B;
-                    const int rr = (B == 1) ? 0 : (int)(e & (B - 1));
-                    if (e < g.N && s_ok[rr]) {
-                        const long long f = fixed_from(acc[q], g.Fz);
-                        if (f) {
-                            int rows[16];
-                            unsigned neg;
-                            if (sp.zeta == 8) sketch_column8(sp, i, rows, &neg);
-                            else sketch_column(sp, i, rows, &neg);
-#pragma unroll
-                            for (int t = 0; t < 16; ++t)
-                                if (t < sp.zeta)
-                                    split_add(s_hi + rr * g.m_s, s_lo + rr * g.m_s, rows[t], ((neg >> t) & 1u) ? -f : f);
-                        }
-                    }
-                }
-            }
-            for (; c + 4 <= nc; c += 4) {
-                uint4 nxt[4];
-                const bool more = c + 8 <= nc;
-                if (more) {
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) nxt[u] = __ldcs((const uint4*)(V + (size_t)(c + 4 + u) * g.ldv + base));
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const T* vv = (const T*)&raw[u];
-#pragma unroll
-                    for (int q = 0; q < VEC; ++q) {
-                        const int rr = (B == 1) ? 0 : (int)((base + q) & (B - 1));
-                        acc[q] = fmaf(-s_coef[(c + u) * B + rr], to_acc(vv[q]), acc[q]);
-                    }
-                }
-                if (more) {
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) raw[u] = nxt[u];
-                }
-            }
-            for (; c < nc; ++c) {
-                const uint4 r1 = __ldcs((const uint4*)(V + (size_t)c * g.ldv + base));
-                const T* vv = (const T*)&r1;
-#pragma unroll
-                for (int q = 0; q < VEC; ++q) {
-                    const int rr = (B == 1) ? 0 : (int)((base + q) & (B - 1));
-                    acc[q] = fmaf(-s_coef[c * B + rr], to_acc(vv[q]), acc[q]);
-                }
-            }
-            const unsigned bits = bf.ispiv[base >> 5] >> (unsigned)(base & 31);
-#pragma unroll
-            for (int q = 0; q < VEC; ++q) {
-                if ((bits >> q) & 1u) acc[q] = 0.f;
-                const long long e = base + q;
-                const int rr = (B == 1) ? 0 : (int)(e & (B - 1));
-                if (e < g.N && s_ok[rr]) {
-                    const unsigned long long k = argmax_key(acc[q], (unsigned)(e / B));
-                    best[q] = k > best[q] ? k : best[q];
-                }
-            }
-            float4* wo = (float4*)(w + base);
-#pragma unroll
-            for (int q = 0; q < VEC / 4; ++q)
-                wo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
         }
-        if (do_z && ++round == fold_rounds) {
-            __syncthreads();
-            split_fold(s_hi, s_lo, s_wide, zc);
-            __syncthreads();
-            round = 0;
+        const T* vb = V + base;
+        int c = 0;
+        for (; c + 8 <= nc; c += 8) {
+            uint4 raw[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) raw[u] = __ldcs((const uint4*)(vb + (size_t)(c + u) * ldv));
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const T* vv = (const T*)&raw[u];
+#pragma unroll
+                for (int q = 0; q < VEC; ++q)
+                    acc[q] = fmaf(-s_coef[(c + u) * B + ((base + q) & (B - 1))], to_acc(vv[q]), acc[q]);
+            }
         }
+        for (; c < nc; ++c) {
+            const uint4 r1 = __ldcs((const uint4*)(vb + (size_t)c * ldv));
+            const T* vv = (const T*)&r1;
+#pragma unroll
+            for (int q = 0; q < VEC; ++q)
+                acc[q] = fmaf(-s_coef[c * B + ((base + q) & (B - 1))], to_acc(vv[q]), acc[q]);
+        }
+        const unsigned bits = bf.ispiv[base >> 5] >> (base & 31);
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+            if ((bits >> q) & 1u) acc[q] = 0.f;
+            const unsigned e = base + q;
+            const int rr = (int)(e & (B - 1));
+            if (e < N && s_ok[rr]) {
+                const unsigned long long k = argmax_key(acc[q], e >> LB);
+                const int slot = (B == 1) ? 0 : q;
+                best[slot] = k > best[slot] ? k : best[slot];
+            }
+        }
+        float4* wo = (float4*)(w + base);
+#pragma unroll
+        for (int q = 0; q < VEC / 4; ++q)
+            wo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
     }
-    if (do_z) {
-        __syncthreads();
-        split_fold(s_hi, s_lo, s_wide, zc);
-        __syncthreads();
-        for (int t = threadIdx.x; t < zc; t += blockDim.x) {
-            const int rr = t / g.m_s, row = t - rr * g.m_s;
-            if (s_wide[t] && s_ok[rr])
-                atomicAdd((unsigned long long*)&bf.accSZ[((size_t)rr * g.k_max + j) * g.m_s + row],
-                          (unsigned long long)s_wide[t]);
-        }
-    }
-    // reduce keys: per RHS rr = (base0 + q) mod B (same for every grid-stride pass)
+    // reduce keys: the RHS of slot q is (base0 + q) mod B on every pass
     if (B == 1) {
         unsigned long long k = best[0];
-#pragma unroll
-        for (int q = 1; q < VEC; ++q) k = best[q] > k ? best[q] : k;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             const unsigned long long o = __shfl_xor_sync(0xffffffffu, k, off);
@@ -254,13 +207,12 @@ __global__ void __launch_bounds__(256) k_update_f(Geom g, Bufs bf, SketchParams 
         if ((threadIdx.x & 31) == 0 && k) atomicMax(&s_key[0], k);
     } else {
 #pragma unroll
-        for (int q = 0; q < VEC; ++q)
+        for (int q = 0; q < NK; ++q)
             if (best[q]) atomicMax(&s_key[(int)((base0 + q) & (B - 1))], best[q]);
     }
     __syncthreads();
     if (threadIdx.x < B && s_key[threadIdx.x])
         atomicMax(&st->key[(j + 1) & 1][threadIdx.x], s_key[threadIdx.x]);
-    (void)K1;
 }
 
 // ------------------------------------------------------------------------
@@ -337,7 +289,8 @@ __global__ void k_argmin_d(Geom g, Bufs bf) {
 // F = 61 - ceil(log2(n+1)).
 // ------------------------------------------------------------------------
 template <class T, class Acc>
-__global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams sp, int want_sw, int Bg) {
+__global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams sp, int want_sw, int Bg, int lbg,
+                                                   int lb) {
     extern __shared__ unsigned char smem_raw[];
     constexpr bool f64 = sizeof(Acc) == 8;
     const int nacc = want_sw ? 2 : 1;
@@ -401,17 +354,17 @@ __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams
     const int F = g.F;
     if (any_ok) {
         T* vout = (T*)bf.V + (size_t)jn * g.ldv;
-        const long long total = g.n * Bg;      // (i, rl) pairs this CTA's group covers
-        const long long stride = (long long)gridDim.x * blockDim.x;
+        const unsigned total = (unsigned)g.n << lbg;     // (i, rl) pairs this CTA's group covers
+        const unsigned stride = gridDim.x * blockDim.x;
         const int fold_rounds = kFoldEvery / 256;
         int round = 0;
-        for (long long t0 = blockIdx.x * (long long)blockDim.x; t0 < total; t0 += stride) {
-            const long long t = t0 + threadIdx.x;
-            const long long i = t / Bg;
-            const int rl = (int)(t - i * Bg);
+        for (unsigned t0 = blockIdx.x * blockDim.x; t0 < total; t0 += stride) {
+            const unsigned t = t0 + threadIdx.x;
+            const unsigned i = t >> lbg;
+            const int rl = (int)(t & (unsigned)(Bg - 1));
             if (t < total && s_ok[rl]) {
-                const long long e = i * B + r0 + rl;
-                const Acc v = (i == s_prow[rl]) ? (Acc)1 : w[e] / s_hval[rl];
+                const unsigned e = (i << lb) + r0 + rl;
+                const Acc v = ((long long)i == s_prow[rl]) ? (Acc)1 : w[e] / s_hval[rl];
                 const T vs = from_acc<T>(v);
                 vout[e] = vs;
                 const long long fv = fixed_from(to_acc(vs), F);
@@ -603,8 +556,7 @@ cudaError_t launch_pivot_solve(int storage, const Geom& g, const Bufs& bf, cudaS
     const int K1 = g.k_max + 1;
     IPF_DISPATCH_STORAGE(storage, {
         using Acc = typename AccOf<T>::type;
-        const size_t smem = (size_t)((K1 + 1) & ~1) * sizeof(double) +
-                            (size_t)g.k_max * (g.k_max + 1) / 2 * sizeof(Acc);
+        const size_t smem = (size_t)((K1 + 1) & ~1) * sizeof(double) + lp_stride(g.k_max) * sizeof(Acc);
         auto fn = k_pivot_solve<T, Acc>;
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -613,8 +565,21 @@ cudaError_t launch_pivot_solve(int storage, const Geom& g, const Bufs& bf, cudaS
     return cudaGetLastError();
 }
 
-cudaError_t launch_update(int storage, const Geom& g, const Bufs& bf, const SketchParams& sp, int num_sms,
-                          cudaStream_t s) {
+template <class T>
+static cudaError_t update_B(const Geom& g, const Bufs& bf, int blocks, size_t smem, cudaStream_t s) {
+    switch (g.B) {
+        case 1: k_update_f<T, 1><<<blocks, 256, smem, s>>>(g, bf); break;
+        case 2: k_update_f<T, 2><<<blocks, 256, smem, s>>>(g, bf); break;
+        case 4: k_update_f<T, 4><<<blocks, 256, smem, s>>>(g, bf); break;
+        case 8: k_update_f<T, 8><<<blocks, 256, smem, s>>>(g, bf); break;
+        case 16: k_update_f<T, 16><<<blocks, 256, smem, s>>>(g, bf); break;
+        case 32: k_update_f<T, 32><<<blocks, 256, smem, s>>>(g, bf); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update(int storage, const Geom& g, const Bufs& bf, int num_sms, cudaStream_t s) {
     const int K1 = g.k_max + 1;
     int per_thread = 0;
     IPF_DISPATCH_STORAGE(storage, { per_thread = 16 / (int)sizeof(T); });
@@ -631,18 +596,11 @@ cudaError_t launch_update(int storage, const Geom& g, const Bufs& bf, const Sket
         k_argmin_d<<<(int)b2, 256, 0, s>>>(g, bf);
         return cudaGetLastError();
     }
-    const size_t zc = g.want_z ? (size_t)g.B * g.m_s : 0;
-    const size_t smem = zc * 16 + (size_t)K1 * g.B * sizeof(float);
-    auto go = [&](auto fn) -> cudaError_t {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        fn<<<(int)blocks, 256, smem, s>>>(g, bf, sp);
-        return cudaGetLastError();
-    };
+    const size_t smem = (size_t)K1 * g.B * sizeof(float);
     switch (storage) {
-        case IPF_STORE_F32: return go(k_update_f<float>);
-        case IPF_STORE_BF16: return go(k_update_f<__nv_bfloat16>);
-        case IPF_STORE_F16: return go(k_update_f<__half>);
+        case IPF_STORE_F32: return update_B<float>(g, bf, (int)blocks, smem, s);
+        case IPF_STORE_BF16: return update_B<__nv_bfloat16>(g, bf, (int)blocks, smem, s);
+        case IPF_STORE_F16: return update_B<__half>(g, bf, (int)blocks, smem, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -659,6 +617,9 @@ cudaError_t launch_normalize(int storage, const Geom& g, const Bufs& bf, const S
     const int Bg = pick_group(g.B, g.m_s, nacc);
     const size_t smem = (size_t)Bg * g.m_s * 16 * nacc;
     const long long work = g.n * Bg;
+    int lbg = 0, lb = 0;
+    while ((1 << lbg) < Bg) ++lbg;
+    while ((1 << lb) < g.B) ++lb;
     long long bx = (work + 255) / 256;
     const int groups = g.B / Bg;
     long long cap = (long long)num_sms * 2 / groups;
@@ -670,7 +631,7 @@ cudaError_t launch_normalize(int storage, const Geom& g, const Bufs& bf, const S
         auto fn = k_normalize<T, Acc>;
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        fn<<<grid, 256, smem, s>>>(g, bf, sp, want_sw ? 1 : 0, Bg);
+        fn<<<grid, 256, smem, s>>>(g, bf, sp, want_sw ? 1 : 0, Bg, lbg, lb);
     });
     return cudaGetLastError();
 }

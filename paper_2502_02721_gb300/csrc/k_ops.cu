@@ -25,7 +25,7 @@ template <class T> __device__ __forceinline__ typename AccOf<T>::type ld_acc(con
 // thread OY x OX = (TY/16) x (TX/16) outputs.
 // ------------------------------------------------------------------------
 template <class T, class Acc, int KW, int OY, int OX>
-__global__ void __launch_bounds__(256) k_conv2d(const T* __restrict__ vbase, long long ldv, const int* __restrict__ jptr,
+__global__ void __launch_bounds__(256, 4) k_conv2d(const T* __restrict__ vbase, long long ldv, const int* __restrict__ jptr,
                                                  Acc* __restrict__ w, int H, int W,
                                                  const float* __restrict__ psf, int ph, int pw) {
     const T* v = jptr ? vbase + (size_t)(*jptr) * ldv : vbase;
@@ -216,8 +216,8 @@ cudaError_t conv_dispatch(const OpDev& op, const T* v, long long ldv, const int*
     };
     const int mx = op.pw;
     if (mx <= 7) return go(k_conv2d<T, Acc, 7, 2, 4>, 7, 32, 64);
-    if (mx <= 15) return go(k_conv2d<T, Acc, 15, 4, 8>, 15, 64, 128);
-    if (mx <= 31) return go(k_conv2d<T, Acc, 31, 4, 8>, 31, 64, 128);
+    if (mx <= 15) return go(k_conv2d<T, Acc, 15, 2, 8>, 15, 32, 128);
+    if (mx <= 31) return go(k_conv2d<T, Acc, 31, 2, 8>, 31, 32, 128);
     return go(k_conv2d<T, Acc, 63, 2, 4>, 63, 32, 64);
 }
 
@@ -275,37 +275,7 @@ __global__ void k_interleave(const float* __restrict__ src, float* __restrict__ 
     }
 }
 
-__global__ void k_csr_row_abs_max(const long long* __restrict__ rowptr, const float* __restrict__ vals, long long m,
-                                  unsigned* out) {
-    unsigned best = 0;
-    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < m; r += (long long)gridDim.x * blockDim.x) {
-        float t = 0.f;
-        for (long long q = rowptr[r]; q < rowptr[r + 1]; ++q) t += fabsf(vals[q]);
-        const unsigned u = __float_as_uint(t * 1.0001f);
-        best = u > best ? u : best;
-    }
-    atomicMax(out, best);
-}
-
 }  // namespace
-
-// max row sum of |a| for a device CSR matrix, synchronous, into *host_out
-cudaError_t launch_csr_row_abs_max(const OpDev& op, float* host_out, cudaStream_t s) {
-    unsigned* d = nullptr;
-    cudaError_t e = cudaMallocAsync((void**)&d, sizeof(unsigned), s);
-    if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(d, 0, sizeof(unsigned), s);
-    if (e == cudaSuccess) {
-        k_csr_row_abs_max<<<256, 256, 0, s>>>(op.rowptr, op.vals, op.rows, d);
-        e = cudaGetLastError();
-    }
-    unsigned h = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
-    cudaError_t e2 = cudaFreeAsync(d, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    memcpy(host_out, &h, sizeof(float));
-    return e != cudaSuccess ? e : e2;
-}
 
 cudaError_t launch_op_apply(const OpDev& op, int storage, const void* vbase, long long ldv, const int* jptr, int B,
                             void* w, cudaStream_t s) {
@@ -318,26 +288,29 @@ cudaError_t launch_op_apply(const OpDev& op, int storage, const void* vbase, lon
     }
 }
 
-// plain float32 vectors, RHS-major (r*n + i), for the standalone apply call
+// plain float32 vectors, RHS-major (input r*n + i, output r*m + i), for the
+// standalone apply call
 cudaError_t launch_op_apply_f32_plain(const OpDev& op, const float* v, float* w, int nrhs, cudaStream_t s) {
-    const long long n = (op.kind == IPF_OP_CSR) ? (long long)op.cols : (long long)op.rows * op.cols;
-    if (nrhs == 1 || op.kind != IPF_OP_CSR) {
+    const bool csr = op.kind == IPF_OP_CSR;
+    const long long n = csr ? (long long)op.cols : (long long)op.rows * op.cols;
+    const long long m = csr ? (long long)op.rows : n;
+    if (nrhs == 1 || !csr) {
         for (int r = 0; r < nrhs; ++r) {
-            cudaError_t e = apply_T<float>(op, v + (size_t)r * n, 0, nullptr, w + (size_t)r * n, 1, s);
+            cudaError_t e = apply_T<float>(op, v + (size_t)r * n, 0, nullptr, w + (size_t)r * m, 1, s);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
     }
     // CSR with several RHS: interleave into scratch, one product, de-interleave
     float* tmp = nullptr;
-    cudaError_t e = cudaMallocAsync((void**)&tmp, sizeof(float) * (size_t)n * nrhs * 2, s);
+    cudaError_t e = cudaMallocAsync((void**)&tmp, sizeof(float) * (size_t)(n + m) * nrhs, s);
     if (e != cudaSuccess) return e;
     float* vi = tmp;
     float* wi = tmp + (size_t)n * nrhs;
     const int blocks = 1024;
     k_interleave<<<blocks, 256, 0, s>>>(v, vi, n, nrhs, 0);
     e = apply_T<float>(op, vi, 0, nullptr, wi, nrhs, s);
-    if (e == cudaSuccess) k_interleave<<<blocks, 256, 0, s>>>(wi, w, n, nrhs, 1);
+    if (e == cudaSuccess) k_interleave<<<blocks, 256, 0, s>>>(wi, w, m, nrhs, 1);
     cudaError_t e2 = cudaFreeAsync(tmp, s);
     return e != cudaSuccess ? e : (e2 != cudaSuccess ? e2 : cudaGetLastError());
 }

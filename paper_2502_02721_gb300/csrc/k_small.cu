@@ -50,19 +50,18 @@ __device__ __forceinline__ int kuse_of(const DevState* st, int r, int k) {
 }
 
 // M[r][col], T[r][col] (column-major, ld = m).  Column col < kb of M is
-// z_col = S A v_col (the DIRECT form) or (S V_{kb+1} H)(:, col); column kb is
-// c = S b = beta * S (b / beta).
-__global__ void k_form(Geom g, Bufs bf, int k, int zeta, int use_z, int need_T, double* Mw, double* Tw) {
+// z_col = S A v_col = (S V_{col+1}) h_col + H(col+1, col) (S w)_{col+1}, with
+// (S w) the sketch of the unrounded normalised vector when the storage
+// rounds it (use_sw, the DIRECT form) and S V otherwise (then the two forms
+// coincide: S V_{kb+1} H); column kb is c = S b = beta * S (b / beta).
+__global__ void k_form(Geom g, Bufs bf, int k, int zeta, int use_sw, int need_T, double* Mw, double* Tw) {
     const int r = blockIdx.y;
     const int kb = kuse_of(bf.st, r, k);
     const int K1 = g.k_max + 1;
     const int m = g.m_s;
-    const double sq = sqrt((double)zeta);
-    const double scale = ldexp(1.0, -g.F) / sq;
-    const double scale_z = ldexp(1.0, -g.Fz) / sq;
+    const double scale = ldexp(1.0, -g.F) / sqrt((double)zeta);
     const long long* sv = bf.accSV + (size_t)r * K1 * m;
     const long long* sw = bf.accSW + (size_t)r * K1 * m;
-    const long long* sz = bf.accSZ + (size_t)r * g.k_max * m;
     const double* H = bf.H + (size_t)r * K1 * g.k_max;
     double* M = Mw + (size_t)r * m * (k + 1);
     double* T = Tw ? Tw + (size_t)r * m * k : nullptr;
@@ -73,14 +72,11 @@ __global__ void k_form(Geom g, Bufs bf, int k, int zeta, int use_z, int need_T, 
         const int col = (int)(t / m), row = (int)(t - (long long)col * m);
         double val;
         if (col < kb) {
-            if (use_z) {
-                val = (double)sz[(size_t)col * m + row] * scale_z;
-            } else {
-                double s = 0.0;
-                const double* Hc = H + (size_t)K1 * col;
-                for (int i = 0; i <= col + 1; ++i) s = fma((double)sv[(size_t)i * m + row] * scale, Hc[i], s);
-                val = s;
-            }
+            double s = 0.0;
+            const double* Hc = H + (size_t)K1 * col;
+            for (int i = 0; i <= col; ++i) s = fma((double)sv[(size_t)i * m + row] * scale, Hc[i], s);
+            const long long* last = use_sw ? sw : sv;
+            val = fma((double)last[(size_t)(col + 1) * m + row] * scale, Hc[col + 1], s);
             if (need_T) T[(size_t)col * m + row] = (double)sv[(size_t)col * m + row] * scale;
         } else {
             val = beta * (double)sw[row] * scale;
@@ -339,7 +335,7 @@ cudaError_t solve_error_flag(const void* work, const Geom& g, int* flag) {
     return cudaMemcpy(flag, (const char*)work + L.err_off, sizeof(int), cudaMemcpyDeviceToHost);
 }
 
-cudaError_t launch_solve_prepare(const Geom& g, const Bufs& bf, int zeta, int k, bool need_T, bool use_z,
+cudaError_t launch_solve_prepare(const Geom& g, const Bufs& bf, int zeta, int k, bool need_T, bool use_sw,
                                  void* work, int nl_max, int num_sms, cudaStream_t s) {
     SolveLayout L = layout_for(g, nl_max);
     char* base = (char*)work;
@@ -353,7 +349,7 @@ cudaError_t launch_solve_prepare(const Geom& g, const Bufs& bf, int zeta, int k,
     if (e != cudaSuccess) return e;
     {
         dim3 grid((unsigned)((g.m_s * (k + 1) + 255) / 256), (unsigned)g.B);
-        k_form<<<grid, 256, 0, s>>>(g, bf, k, zeta, use_z ? 1 : 0, need_T ? 1 : 0, Mw, Tw);
+        k_form<<<grid, 256, 0, s>>>(g, bf, k, zeta, use_sw ? 1 : 0, need_T ? 1 : 0, Mw, Tw);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int njobs = g.B * (need_T ? 2 : 1);

@@ -105,7 +105,9 @@ def test_csr_matches_oracle(torch, nrhs):
     n = 48 * 48
     rng = np.random.default_rng(nrhs)
     v = rng.standard_normal((nrhs, n)).astype(np.float32)
-    got = _apply_gpu(torch, _Desc(kind="csr", rows=n, cols=n, rowptr=rowptr, colind=colind, vals=vals),
+    # rows x cols of a CSR problem description is the image (48 x 48); the
+    # operator is n x n with n = 48 * 48
+    got = _apply_gpu(torch, _Desc(kind="csr", rows=48, cols=48, rowptr=rowptr, colind=colind, vals=vals),
                      v.reshape(-1), nrhs).reshape(nrhs, n)
     for r in range(nrhs):
         want = ops.csr_apply(rowptr, colind, vals, v[r])

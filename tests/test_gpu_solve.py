@@ -194,7 +194,7 @@ def test_breakdown_on_invariant_subspace():
     b = np.zeros((2, n), np.float32)
     b[0, 5] = 3.0                 # eigenvector: breakdown after one step
     b[1, :] = 0.0                 # zero RHS: nothing to do
-    p = P.Problem("diag", "csr", n, n, b, np.zeros((2, n)), k=4, m_s=16, zeta=8, sketch_seed=3,
+    p = P.Problem("diag", "csr", 8, 8, b, np.zeros((2, n)), k=4, m_s=16, zeta=8, sketch_seed=3,
                   rowptr=rowptr, colind=colind, vals=d)
     from paper_2502_02721_gb300 import binding as bd
     ctx = gpu_context(p, "f32", nrhs=2)
