@@ -364,7 +364,7 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     const size_t pivsmem = (size_t)(cfg.k_max + 2) * 8 + (size_t)cfg.k_max * (cfg.k_max + 1) / 2 * accb;
     if (pivsmem > 220 * 1024) return IPF_ERR_UNSUPPORTED;
     const long long n = op_n(op);
-    if (n * B >= (1ll << 32) || n >= (1ll << 29)) return IPF_ERR_UNSUPPORTED;
+    if (n * B >= (1ll << 31) || n >= (1ll << 29)) return IPF_ERR_UNSUPPORTED;
 
     ipf_ctx* c = new ipf_ctx();
     c->cfg = cfg;
