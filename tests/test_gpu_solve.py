@@ -40,9 +40,13 @@ def test_deblur64_parity(deblur64, storage):
     assert rel(ex["SV"][:, 0], st.SV[:, 0]) < (1e-12 if storage == "f64" else 1e-6)
     assert rel(ex["c"], st.c) < (1e-12 if storage == "f64" else 1e-6)
     if storage == "f32":
-        # z_j = S A v_j (Algorithm 1 line 11), sketched inside the update kernel
-        for j in range(5):
-            assert rel(ex["SZ"][:, j], st.Zd[:, j]) < 1e-5
+        # z_j = S A v_j (Algorithm 1 line 11).  z_0 involves one FP32 product;
+        # later columns inherit the drift of individual basis vectors, which
+        # is larger than that of x_k (errors inside the Krylov subspace leave
+        # x_k unchanged), hence the looser bound
+        assert rel(ex["SZ"][:, 0], st.Zd[:, 0]) < 1e-6
+        for j in range(1, 5):
+            assert rel(ex["SZ"][:, j], st.Zd[:, j]) < 1e-4
     # Hessenberg columns: first steps tightly
     for j in range(5):
         assert rel(ex["H"][:j + 2, j], st.H[:j + 2, j]) < (1e-10 if storage == "f64" else 1e-5)
