@@ -73,9 +73,10 @@ enum ipf_penalty { IPF_PEN_SKETCHED_X = 0, IPF_PEN_Y = 1 };
 /* How S A V_k is assembled: DIRECT sketches each product u = A v_j before
  * the elimination (Algorithm 1 line 11, z_k = S u), HESSENBERG uses
  * S V_{k+1} H_k.  They agree in exact arithmetic; with BF16/FP16 storage
- * DIRECT is exactly the sketched objective over the stored basis.  DIRECT
- * needs float storage and nrhs <= 4; AUTO picks DIRECT when it can and
- * HESSENBERG otherwise.                                                    */
+ * DIRECT is the sketched objective over the stored basis (the sketch of
+ * each product is assembled by linearity from S of the stored basis and S
+ * of the unrounded new vector, which costs a second sketch per step for
+ * BF16/FP16).  DIRECT needs float storage.  AUTO uses HESSENBERG.          */
 enum ipf_zform { IPF_Z_DIRECT = 0, IPF_Z_HESSENBERG = 1, IPF_Z_AUTO = 2 };
 
 /* Forward operator.  For PSF kinds n = rows*cols and images are row-major.
@@ -102,7 +103,8 @@ typedef void* (*ipf_alloc_fn)(size_t bytes, void* user);
 typedef void (*ipf_free_fn)(void* ptr, void* user);
 
 typedef struct ipf_config {
-    int k_max;                   /* maximum Hessenberg steps (basis has k_max+1 vectors)   */
+    int k_max;                   /* maximum Hessenberg steps, 1..224 (basis has k_max+1
+                                    vectors; the FP64 pivot block lives in shared memory)  */
     int m_s;                     /* sketch rows (l in Sec. 2); m_s >= zeta                  */
     int zeta;                    /* nonzeros per sketch column, 1..16                       */
     unsigned long long seed;     /* sketch seed (SplitMix64 state)                          */

@@ -358,11 +358,10 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     if (cfg.zform != IPF_Z_DIRECT && cfg.zform != IPF_Z_HESSENBERG && cfg.zform != IPF_Z_AUTO) return IPF_ERR_ARG;
     const bool z_ok = cfg.storage != IPF_STORE_F64;
     if (cfg.zform == IPF_Z_DIRECT && !z_ok) return IPF_ERR_UNSUPPORTED;
-    if (cfg.k_max > 255) return IPF_ERR_UNSUPPORTED;
+    if (cfg.k_max > 224) return IPF_ERR_UNSUPPORTED;      // pivot block (FP64) fits shared memory
     if (b_mem != IPF_MEM_HOST && b_mem != IPF_MEM_DEVICE) return IPF_ERR_ARG;
     const size_t accb = cfg.storage == IPF_STORE_F64 ? 8 : 4;
-    const size_t pivsmem = (size_t)(cfg.k_max + 2) * 8 + (size_t)cfg.k_max * (cfg.k_max + 1) / 2 * accb;
-    if (pivsmem > 220 * 1024) return IPF_ERR_UNSUPPORTED;
+
     const long long n = op_n(op);
     if (n * B >= (1ll << 31) || n >= (1ll << 29)) return IPF_ERR_UNSUPPORTED;
 
@@ -398,7 +397,7 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     g.k_max = cfg.k_max;
     g.m_s = cfg.m_s;
     g.F = cfg.storage == IPF_STORE_F64 ? fixed_exponent(n, 0) : kSplitS;
-    g.want_z = (cfg.zform == IPF_Z_DIRECT || (cfg.zform == IPF_Z_AUTO && z_ok)) ? 1 : 0;
+    g.want_z = cfg.zform == IPF_Z_DIRECT ? 1 : 0;
     c->sp = make_sketch_params(cfg.seed, cfg.m_s, cfg.zeta);
     const size_t K1 = (size_t)cfg.k_max + 1;
     const size_t sb = storage_bytes(cfg.storage);

@@ -61,20 +61,21 @@ __global__ void __launch_bounds__(256) k_pivot_solve(Geom g, Bufs bf) {
     Acc* Lp = (Acc*)bf.LpT + (size_t)r * lp_stride(g.k_max);
     const int* piv = bf.piv + (size_t)r * K1;
     double* s_g = (double*)smem_raw;
-    Acc* s_L = (Acc*)(s_g + ((K1 + 1) & ~1));
+    double* s_L = s_g + ((K1 + 1) & ~1);          // FP64 copy: no conversions in the solve
     const size_t rowj = (size_t)j * (j - 1) / 2;
     // row j: L(j, c) = v_c(p_j), exact copies of the stored values
     const size_t pj = (size_t)piv[j] * B + r;
     for (int c = threadIdx.x; c < j; c += blockDim.x) {
         const Acc val = to_acc(V[(size_t)c * g.ldv + pj]);
         Lp[rowj + c] = val;
-        s_L[rowj + c] = val;
+        s_L[rowj + c] = (double)val;
     }
-    for (size_t t = threadIdx.x; t < rowj; t += blockDim.x) s_L[t] = Lp[t];
+    for (size_t t = threadIdx.x; t < rowj; t += blockDim.x) s_L[t] = (double)Lp[t];
     for (int i = threadIdx.x; i <= j; i += blockDim.x) s_g[i] = (double)w[(size_t)piv[i] * B + r];
     __syncthreads();
     if (threadIdx.x >= 32) return;
     const int lane = threadIdx.x;
+    const int qmax = j >> 5;                       // last row group holding a row <= j
     double x[8];
     int off[8];
 #pragma unroll
@@ -85,16 +86,18 @@ __global__ void __launch_bounds__(256) k_pivot_solve(Geom g, Bufs bf) {
     }
 #pragma unroll
     for (int cb = 0; cb < 8; ++cb) {
-        if (cb * 32 >= j) break;
+        if (cb > qmax) break;
 #pragma unroll
         for (int cc = 0; cc < 32; ++cc) {
             const int c = cb * 32 + cc;
             if (c >= j) break;
             const double xc = __shfl_sync(0xffffffffu, x[cb], cc);
+            // rows i > c with i <= j only: s_L holds rows 1..j and nothing beyond
+            if (lane > cc && cb * 32 + lane <= j) x[cb] = fma(-s_L[off[cb] + c], xc, x[cb]);
 #pragma unroll
-            for (int q = cb; q < 8; ++q) {
-                const int i = q * 32 + lane;
-                if (i > c && i <= j) x[q] = fma(-(double)s_L[off[q] + c], xc, x[q]);
+            for (int q = cb + 1; q < 8; ++q) {
+                if (q > qmax) break;
+                if (q * 32 + lane <= j) x[q] = fma(-s_L[off[q] + c], xc, x[q]);
             }
         }
     }
@@ -556,7 +559,7 @@ cudaError_t launch_pivot_solve(int storage, const Geom& g, const Bufs& bf, cudaS
     const int K1 = g.k_max + 1;
     IPF_DISPATCH_STORAGE(storage, {
         using Acc = typename AccOf<T>::type;
-        const size_t smem = (size_t)((K1 + 1) & ~1) * sizeof(double) + lp_stride(g.k_max) * sizeof(Acc);
+        const size_t smem = (size_t)((K1 + 1) & ~1) * sizeof(double) + lp_stride(g.k_max) * sizeof(double);
         auto fn = k_pivot_solve<T, Acc>;
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -622,7 +625,7 @@ cudaError_t launch_normalize(int storage, const Geom& g, const Bufs& bf, const S
     while ((1 << lb) < g.B) ++lb;
     long long bx = (work + 255) / 256;
     const int groups = g.B / Bg;
-    long long cap = (long long)num_sms * 2 / groups;
+    long long cap = (long long)num_sms * 4 / groups;
     if (cap < 1) cap = 1;
     if (bx > cap) bx = cap;
     dim3 grid((unsigned)bx, (unsigned)groups);

@@ -25,7 +25,7 @@ template <class T> __device__ __forceinline__ typename AccOf<T>::type ld_acc(con
 // thread OY x OX = (TY/16) x (TX/16) outputs.
 // ------------------------------------------------------------------------
 template <class T, class Acc, int KW, int OY, int OX>
-__global__ void __launch_bounds__(256, 4) k_conv2d(const T* __restrict__ vbase, long long ldv, const int* __restrict__ jptr,
+__global__ void __launch_bounds__(256, 3) k_conv2d(const T* __restrict__ vbase, long long ldv, const int* __restrict__ jptr,
                                                  Acc* __restrict__ w, int H, int W,
                                                  const float* __restrict__ psf, int ph, int pw) {
     const T* v = jptr ? vbase + (size_t)(*jptr) * ldv : vbase;
@@ -76,6 +76,87 @@ __global__ void __launch_bounds__(256, 4) k_conv2d(const T* __restrict__ vbase, 
             for (int q = 0; q < KW; ++q)
 #pragma unroll
                 for (int bb = 0; bb < OX; ++bb) acc[a][bb] = fma(kr[q], in[bb + q], acc[a][bb]);
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < OY; ++a) {
+        const int yy = y0 + oy0 + a;
+        if (yy >= H) continue;
+#pragma unroll
+        for (int bb = 0; bb < OX; ++bb) {
+            const int xx = x0 + ox0 + bb;
+            if (xx < W) w[(size_t)yy * W + xx] = acc[a][bb];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
+// 2-D convolution, FP32 accumulation, PSF width KW <= 31 (padded to KWP, a
+// multiple of 4).  Same tile scheme as k_conv2d, but the flipped PSF row
+// (KWP floats) and the thread's input row segment (NIN floats) are loaded
+// as float4 into registers, so the inner loop is OX FMAs per kernel column
+// with no shared-memory traffic.
+// ------------------------------------------------------------------------
+template <class T, int KW, int OY, int OX>
+__global__ void __launch_bounds__(256, 2) k_conv2d_v(const T* __restrict__ vbase, long long ldv,
+                                                    const int* __restrict__ jptr, float* __restrict__ w, int H,
+                                                    int W, const float* __restrict__ psf, int ph, int pw) {
+    const T* v = jptr ? vbase + (size_t)(*jptr) * ldv : vbase;
+    constexpr int KWP = (KW + 3) & ~3;
+    constexpr int TY = 16 * OY, TX = 16 * OX;
+    constexpr int NIN = (OX + KW - 1 + 3) & ~3;       // input floats per output row segment
+    constexpr int IWP = TX - OX + NIN;                // covers the last thread's segment
+    static_assert(OX % 4 == 0, "OX must be a multiple of 4");
+    extern __shared__ float4 smem_f4[];
+    float* s_in = (float*)smem_f4;                    // (TY + ph - 1) x IWP
+    float* s_k = s_in + (size_t)(TY + ph - 1) * IWP;  // ph x KWP
+    const int cy = ph / 2, cx = KW / 2;
+    const int y0 = blockIdx.y * TY, x0 = blockIdx.x * TX;
+    const int IH = TY + ph - 1;
+    const int padl = (KW - pw) / 2;
+    for (int t = threadIdx.x; t < ph * KWP; t += blockDim.x) {
+        const int a = t / KWP, bb = t - a * KWP;
+        const int kb = bb - padl;
+        float val = 0.f;
+        if (bb < KW && kb >= 0 && kb < pw) val = psf[(ph - 1 - a) * pw + (pw - 1 - kb)];
+        s_k[t] = val;
+    }
+    for (int t = threadIdx.x; t < IH * IWP; t += blockDim.x) {
+        const int a = t / IWP, bb = t - a * IWP;
+        const int yy = y0 - cy + a, xx = x0 - cx + bb;
+        float val = 0.f;
+        if (bb < TX + KW - 1 && yy >= 0 && yy < H && xx >= 0 && xx < W) val = to_acc(v[(size_t)yy * W + xx]);
+        s_in[t] = val;
+    }
+    __syncthreads();
+    const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+    const int oy0 = ty * OY, ox0 = tx * OX;
+    float acc[OY][OX];
+#pragma unroll
+    for (int a = 0; a < OY; ++a)
+#pragma unroll
+        for (int bb = 0; bb < OX; ++bb) acc[a][bb] = 0.f;
+    for (int ky = 0; ky < ph; ++ky) {
+        float kr[KWP];
+        const float4* kp = (const float4*)(s_k + ky * KWP);
+#pragma unroll
+        for (int q = 0; q < KWP / 4; ++q) {
+            const float4 t4 = kp[q];
+            kr[4 * q] = t4.x; kr[4 * q + 1] = t4.y; kr[4 * q + 2] = t4.z; kr[4 * q + 3] = t4.w;
+        }
+#pragma unroll
+        for (int a = 0; a < OY; ++a) {
+            const float4* rp = (const float4*)(s_in + (size_t)(oy0 + a + ky) * IWP + ox0);
+            float in[NIN];
+#pragma unroll
+            for (int q = 0; q < NIN / 4; ++q) {
+                const float4 t4 = rp[q];
+                in[4 * q] = t4.x; in[4 * q + 1] = t4.y; in[4 * q + 2] = t4.z; in[4 * q + 3] = t4.w;
+            }
+#pragma unroll
+            for (int q = 0; q < KW; ++q)
+#pragma unroll
+                for (int bb = 0; bb < OX; ++bb) acc[a][bb] = fmaf(kr[q], in[bb + q], acc[a][bb]);
         }
     }
 #pragma unroll
@@ -215,10 +296,30 @@ cudaError_t conv_dispatch(const OpDev& op, const T* v, long long ldv, const int*
         return cudaGetLastError();
     };
     const int mx = op.pw;
-    if (mx <= 7) return go(k_conv2d<T, Acc, 7, 2, 4>, 7, 32, 64);
-    if (mx <= 15) return go(k_conv2d<T, Acc, 15, 2, 8>, 15, 32, 128);
-    if (mx <= 31) return go(k_conv2d<T, Acc, 31, 2, 8>, 31, 32, 128);
-    return go(k_conv2d<T, Acc, 63, 2, 4>, 63, 32, 64);
+    if constexpr (sizeof(Acc) == 4) {
+        // register-blocked float path: 2 x 8 outputs per thread, 32 x 128 tiles
+        auto gov = [&](auto kern, int KW) -> cudaError_t {
+            constexpr int TY = 32, TX = 128, OX = 8;
+            const int KWP = (KW + 3) & ~3;
+            const int NIN = (OX + KW - 1 + 3) & ~3;
+            const int IWP = TX - OX + NIN;
+            const size_t smem = ((size_t)(TY + op.ph - 1) * IWP + (size_t)op.ph * KWP) * sizeof(float);
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            dim3 grid((W + TX - 1) / TX, (H + TY - 1) / TY);
+            kern<<<grid, 256, smem, s>>>(v, ldv, jp, (float*)w, H, W, op.psf, op.ph, op.pw);
+            return cudaGetLastError();
+        };
+        if (mx <= 7) return gov(k_conv2d_v<T, 7, 2, 8>, 7);
+        if (mx <= 15) return gov(k_conv2d_v<T, 15, 2, 8>, 15);
+        if (mx <= 31) return gov(k_conv2d_v<T, 31, 2, 8>, 31);
+        return go(k_conv2d<T, Acc, 63, 2, 4>, 63, 32, 64);
+    } else {
+        if (mx <= 7) return go(k_conv2d<T, Acc, 7, 2, 4>, 7, 32, 64);
+        if (mx <= 15) return go(k_conv2d<T, Acc, 15, 2, 8>, 15, 32, 128);
+        if (mx <= 31) return go(k_conv2d<T, Acc, 31, 2, 8>, 31, 32, 128);
+        return go(k_conv2d<T, Acc, 63, 2, 4>, 63, 32, 64);
+    }
 }
 
 template <class T, class Acc>

@@ -47,9 +47,10 @@ def test_deblur64_parity(deblur64, storage):
         assert rel(ex["SZ"][:, 0], st.Zd[:, 0]) < 1e-6
         for j in range(1, 5):
             assert rel(ex["SZ"][:, j], st.Zd[:, j]) < 1e-4
-    # Hessenberg columns: first steps tightly
-    for j in range(5):
-        assert rel(ex["H"][:j + 2, j], st.H[:j + 2, j]) < (1e-10 if storage == "f64" else 1e-5)
+    # Hessenberg columns: the first tightly, the next ones with the basis drift
+    assert rel(ex["H"][:2, 0], st.H[:2, 0]) < (1e-12 if storage == "f64" else 1e-6)
+    for j in range(1, 5):
+        assert rel(ex["H"][:j + 2, j], st.H[:j + 2, j]) < (1e-10 if storage == "f64" else 1e-4)
     compare_solution(ctx, st, storage, [1, 2, 5, 10, 20, 30, 40, 50], p.lambdas)
     ctx.close()
 
