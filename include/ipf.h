@@ -234,6 +234,26 @@ void ipf_op_destroy(ipf_op* h);
 ipf_status ipf_sketch_apply(const float* x_dev, long long n, int m_s, int zeta,
                             unsigned long long seed, double* y_dev, void* stream);
 
+/* ipf_sketch_apply without any device allocation.  The paper has no
+ * counterpart: this is a service for callers that cannot allocate device
+ * memory when they call, e.g. a runtime that owns and caps the GPU's memory
+ * in pre-reserved pools, or a latency-critical path where an allocation's
+ * cost or possible failure is not acceptable.  Same arguments, result and
+ * kernels as ipf_sketch_apply; x and y are still the caller's.
+ *  - Scratch is one fixed array of 33,024 bytes inside the library's device
+ *    image (every GPU that loads libipf holds it until the process exits),
+ *    so m_s must be <= 4096; larger m_s returns IPF_ERR_UNSUPPORTED.
+ *  - The first call on a device looks up that array's device address with
+ *    that device current; make that first call before any stream capture.
+ *  - Every call shares the array and it keeps the last call's contents; each
+ *    call clears the part it uses on `stream` first.  Calls whose work
+ *    overlaps on the GPU (other streams, unordered host threads) race on it:
+ *    order them on one stream or synchronise between them.
+ * Errors: IPF_ERR_ARG as ipf_sketch_apply, IPF_ERR_UNSUPPORTED (m_s > 4096),
+ * IPF_ERR_CUDA.                                                            */
+ipf_status ipf_sketch_apply_noalloc(const float* x_dev, long long n, int m_s, int zeta,
+                                    unsigned long long seed, double* y_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -77,6 +77,8 @@ SIGNATURES = {
     "ipf_op_destroy": (None, [C.c_void_p]),
     "ipf_sketch_apply": (C.c_int, [C.c_void_p, C.c_longlong, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p,
                                    C.c_void_p]),
+    "ipf_sketch_apply_noalloc": (C.c_int, [C.c_void_p, C.c_longlong, C.c_int, C.c_int, C.c_ulonglong,
+                                           C.c_void_p, C.c_void_p]),
 }
 
 _LIB = None
@@ -334,3 +336,13 @@ def sketch_apply(x, m_s: int, zeta: int, seed: int, y, stream=None):
     st = load().ipf_sketch_apply(x.data_ptr(), int(x.numel()), int(m_s), int(zeta), int(seed), y.data_ptr(), stream)
     if st != IPF_OK:
         raise IpfError(st, "ipf_sketch_apply")
+
+
+def sketch_apply_noalloc(x, m_s: int, zeta: int, seed: int, y, stream=None):
+    """ipf_sketch_apply_noalloc: y = S x with the library's fixed scratch
+    (no device allocation; m_s <= 4096; calls must not overlap on the GPU)."""
+    _check_size(y, m_s, "y")
+    st = load().ipf_sketch_apply_noalloc(x.data_ptr(), int(x.numel()), int(m_s), int(zeta), int(seed),
+                                         y.data_ptr(), stream)
+    if st != IPF_OK:
+        raise IpfError(st, "ipf_sketch_apply_noalloc")
