@@ -356,6 +356,27 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_small(storage: str):
+    """One solve of a small case (1024x1024 Moffat, k=64, m_s=256; the basis
+    plus work vector exceed L2) with eager launches: the ncu target."""
+    import torch
+    from gen import problems as P
+    from paper_2502_02721_gb300 import binding as bd, build as bl
+    if not os.path.exists(bl.lib_path()):
+        bl.build()
+    torch.cuda.set_device(0)
+    p = P.deblur_moffat(side=1024, k=64, m_s=256)
+    keep = []
+    op = bd.operator_from_problem(p, keep)
+    cfg = bd.default_config(k_max=64, m_s=256, zeta=8, seed=p.sketch_seed, storage=storage, use_graphs=0)
+    ctx = bd.Context(op, p.b, cfg, keep)
+    ctx.step(64)
+    x, info = ctx.solve(64, [0.0, 1e-3])
+    print(json.dumps({"small_case": "deblur1024 moffat31 k=64 m_s=256", "storage": storage, "info": info,
+                      "x_norm": float(np.linalg.norm(x[0, 0]))}))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -363,7 +384,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--small", default=None, choices=["f32", "bf16", "f16", "f64"],
+                    help="run one small solve (profiling target) and exit")
     args = ap.parse_args()
+    if args.small:
+        run_small(args.small)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":

@@ -329,8 +329,8 @@ size_t ipf_footprint(const ipf_operator* op, const ipf_config* cfg) {
     const size_t ldv = ldv_for(n * B);
     const size_t K1 = (size_t)cfg->k_max + 1;
     size_t bytes = K1 * ldv * sb + ldv * acc + ldv / 8 + 4096;
-    bytes += B * K1 * (sizeof(int) + sizeof(double) * cfg->k_max + acc * K1) + K1 * B * acc;
-    bytes += 2 * (size_t)B * K1 * cfg->m_s * 8;
+    bytes += B * K1 * (sizeof(int) + sizeof(double) * cfg->k_max + sizeof(double) * K1) + K1 * B * acc;
+    bytes += 2 * (size_t)B * K1 * cfg->m_s * 8 + (size_t)n * 8;
     Geom g; g.n = n; g.B = B; g.N = n * B; g.ldv = (long long)ldv; g.k_max = cfg->k_max; g.m_s = cfg->m_s; g.F = 0;
     bytes += solve_ws_for(g) + 2 * (size_t)B * n * 4 + 256;
     if (op->kind == IPF_OP_CSR && op->mem == IPF_MEM_HOST)
@@ -407,11 +407,19 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     CK("alloc state", c->al.get((void**)&bf.st, sizeof(DevState)));
     CK("alloc piv", c->al.get((void**)&bf.piv, B * K1 * sizeof(int)));
     CK("alloc H", c->al.get((void**)&bf.H, B * K1 * cfg.k_max * sizeof(double)));
-    CK("alloc Lp", c->al.get(&bf.LpT, B * K1 * K1 * accb));
+    CK("alloc Lp", c->al.get(&bf.LpT, B * K1 * K1 * sizeof(double)));
     CK("alloc coef", c->al.get(&bf.coef, K1 * B * accb));
     CK("alloc ispiv", c->al.get((void**)&bf.ispiv, (g.ldv / 32 + 1) * sizeof(unsigned)));
     CK("alloc SV", c->al.get((void**)&bf.accSV, B * K1 * cfg.m_s * sizeof(long long)));
     CK("alloc SW", c->al.get((void**)&bf.accSW, B * K1 * cfg.m_s * sizeof(long long)));
+    if (sketch_table_ok(c->sp)) {
+        unsigned long long* tab = nullptr;
+        CK("alloc sketch table", c->al.get((void**)&tab, sizeof(unsigned long long) * (size_t)n));
+        CK("sketch table", launch_sketch_table(c->sp, n, tab, c->s));
+        bf.sktab = tab;
+    } else {
+        bf.sktab = nullptr;
+    }
     c->solve_ws_bytes = solve_ws_for(g);
     CK("alloc solve", c->al.get(&c->solve_ws, c->solve_ws_bytes));
     CK("alloc lambdas", c->al.get((void**)&c->lam_dev, sizeof(double) * kLamChunk));
@@ -420,7 +428,7 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
 
     CK("memset V", cudaMemsetAsync(bf.V, 0, K1 * g.ldv * sb, c->s));
     CK("memset w", cudaMemsetAsync(bf.w, 0, g.ldv * accb, c->s));
-    CK("memset Lp", cudaMemsetAsync(bf.LpT, 0, B * K1 * K1 * accb, c->s));
+    CK("memset Lp", cudaMemsetAsync(bf.LpT, 0, B * K1 * K1 * sizeof(double), c->s));
     CK("memset piv", cudaMemsetAsync(bf.piv, 0, B * K1 * sizeof(int), c->s));
     CK("memset coef", cudaMemsetAsync(bf.coef, 0, K1 * B * accb, c->s));
     CK("memset solve", cudaMemsetAsync(c->solve_ws, 0, c->solve_ws_bytes, c->s));

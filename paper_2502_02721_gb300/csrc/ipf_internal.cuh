@@ -223,12 +223,14 @@ struct Bufs {
     DevState* st;
     int* piv;                      // [B][k_max+1]
     double* H;                     // [B][(k_max+1)*k_max], column-major
-    void* LpT;                     // [B][(k_max+1)^2] Acc, L_p column-major (col c, row i)
+    void* LpT;                     // [B][lp_stride] FP64, L_p packed by rows (strictly lower)
     void* coef;                    // [(k_max+1)*B] Acc, h for the update
     unsigned* ispiv;               // bitmap over N elements
     long long* accSV;              // [B][k_max+1][m_s] fixed-point S V
     long long* accSW;              // [B][k_max+1][m_s] fixed-point S of the unrounded vectors
                                    // (column 0 = S (b / beta), others for BF16/FP16 storage)
+    const unsigned long long* sktab;  // n entries (zeta = 8, blocks <= 128 rows) or NULL:
+                                      // byte t = row offset in block t | sign << 7
 };
 
 // operator on the device
@@ -265,6 +267,9 @@ cudaError_t launch_pivot_solve(int storage, const Geom& g, const Bufs& bf, cudaS
 cudaError_t launch_update(int storage, const Geom& g, const Bufs& bf, int num_sms, cudaStream_t s);
 cudaError_t launch_normalize(int storage, const Geom& g, const Bufs& bf, const SketchParams& sp,
                              bool want_sw, int num_sms, cudaStream_t s);
+// precomputed sketch columns for zeta = 8 with every block <= 128 rows
+bool sketch_table_ok(const SketchParams& sp);
+cudaError_t launch_sketch_table(const SketchParams& sp, long long n, unsigned long long* tab, cudaStream_t s);
 cudaError_t launch_sketch_vector(const float* x, long long n, const SketchParams& sp, int F,
                                  long long* acc, float* absmax_out, cudaStream_t s, int num_sms,
                                  bool find_max);

@@ -44,11 +44,16 @@ __global__ void k_load_rhs(const float* __restrict__ b, Acc* __restrict__ w, lon
 // registers: x_c is broadcast by a shuffle and every lane updates its rows
 // below c, with no block-wide barrier per column.  j < 256.
 // ------------------------------------------------------------------------
-__host__ __device__ constexpr size_t lp_stride(int k_max) { return (size_t)(k_max + 1) * k_max / 2 + 1; }
+// doubles per RHS for the packed L_p, rounded up to whole 16-byte chunks
+__host__ __device__ constexpr size_t lp_stride(int k_max) { return ((size_t)(k_max + 1) * k_max / 2 + 2) & ~(size_t)1; }
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 template <class T, class Acc>
 __global__ void __launch_bounds__(256) k_pivot_solve(Geom g, Bufs bf) {
-    extern __shared__ unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long s_bar;
+    __shared__ int s_timeout;
     const int r = blockIdx.x;
     DevState* st = bf.st;
     if (st->status[r] != IPF_OK) return;
@@ -58,24 +63,67 @@ __global__ void __launch_bounds__(256) k_pivot_solve(Geom g, Bufs bf) {
     const int B = g.B;
     const T* V = (const T*)bf.V;
     const Acc* w = (const Acc*)bf.w;
-    Acc* Lp = (Acc*)bf.LpT + (size_t)r * lp_stride(g.k_max);
+    double* Lp = (double*)bf.LpT + (size_t)r * lp_stride(g.k_max);
     const int* piv = bf.piv + (size_t)r * K1;
-    double* s_g = (double*)smem_raw;
-    double* s_L = s_g + ((K1 + 1) & ~1);          // FP64 copy: no conversions in the solve
-    const size_t rowj = (size_t)j * (j - 1) / 2;
-    // row j: L(j, c) = v_c(p_j), exact copies of the stored values
+    double* s_L = (double*)smem_raw;                      // rows 1..j, packed (16-byte aligned)
+    double* s_g = s_L + lp_stride(g.k_max);
+    const size_t rowj = (size_t)j * (j - 1) / 2;          // doubles in rows 1..j-1
+    const unsigned bytes = (unsigned)(((rowj + 1) & ~(size_t)1) * sizeof(double));   // whole 16-byte chunks
+    if (threadIdx.x == 0) {
+        s_timeout = 0;
+        if (bytes) {
+            // one bulk copy of the stored rows into shared memory, completion on an mbarrier
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar)));
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&s_bar)), "r"(bytes)
+                         : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_u32(s_L)),
+                "l"(Lp), "r"(bytes), "r"(smem_u32(&s_bar))
+                : "memory");
+        }
+    }
+    // meanwhile: row j (exact copies of the stored values) and u at the pivot rows
     const size_t pj = (size_t)piv[j] * B + r;
     for (int c = threadIdx.x; c < j; c += blockDim.x) {
-        const Acc val = to_acc(V[(size_t)c * g.ldv + pj]);
+        const double val = (double)to_acc(V[(size_t)c * g.ldv + pj]);
         Lp[rowj + c] = val;
-        s_L[rowj + c] = (double)val;
     }
-    for (size_t t = threadIdx.x; t < rowj; t += blockDim.x) s_L[t] = (double)Lp[t];
     for (int i = threadIdx.x; i <= j; i += blockDim.x) s_g[i] = (double)w[(size_t)piv[i] * B + r];
+    if (threadIdx.x == 0 && bytes) {
+        // bounded wait on the copy: gives up after ~2^22 polls and reports a timeout
+        unsigned done = 0;
+        for (long long it = 0; it < (1ll << 22) && !done; ++it) {
+            asm volatile(
+                "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+                : "=r"(done)
+                : "r"(smem_u32(&s_bar))
+                : "memory");
+        }
+        if (!done) {
+            s_timeout = 1;
+            // the copy is still ours: wait for it once more (bounded) before the CTA may exit
+            for (long long it = 0; it < (1ll << 22) && !done; ++it) {
+                asm volatile(
+                    "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
+                    : "=r"(done)
+                    : "r"(smem_u32(&s_bar))
+                    : "memory");
+            }
+        }
+    }
     __syncthreads();
+    // row j goes to shared memory after the bulk copy has landed (it is not part of it)
+    for (int c = threadIdx.x; c < j; c += blockDim.x) s_L[rowj + c] = Lp[rowj + c];
+    __syncthreads();
+    if (s_timeout) {
+        if (threadIdx.x == 0) st->status[r] = IPF_ERR_TIMEOUT;
+        return;
+    }
     if (threadIdx.x >= 32) return;
     const int lane = threadIdx.x;
-    const int qmax = j >> 5;                       // last row group holding a row <= j
+    const int qmax = j >> 5;                               // last row group holding a row <= j
     double x[8];
     int off[8];
 #pragma unroll
@@ -375,19 +423,45 @@ __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams
                 if (fv || fw) {
                     int rows[16];
                     unsigned neg;
-                    if (sp.zeta == 8) sketch_column8(sp, i, rows, &neg);
-                    else sketch_column(sp, i, rows, &neg);
-                    const int o1 = rl * sp.m_s, o2 = (Bg + rl) * sp.m_s;
+                    if (bf.sktab) {
+                        const unsigned long long ent = bf.sktab[i];
+                        neg = 0;
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        if (q < sp.zeta) {
+                        for (int q = 0; q < 8; ++q) {
+                            const unsigned byte = (unsigned)(ent >> (8 * q)) & 0xFFu;
+                            rows[q] = sp.lo[q] + (int)(byte & 0x7Fu);
+                            neg |= (byte >> 7) << q;
+                        }
+                    } else if (sp.zeta == 8) {
+                        sketch_column8(sp, i, rows, &neg);
+                    } else {
+                        sketch_column(sp, i, rows, &neg);
+                    }
+                    const int o1 = rl * sp.m_s, o2 = (Bg + rl) * sp.m_s;
+                    if (sp.zeta == 8) {
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
                             const bool ng = (neg >> q) & 1u;
                             if (f64) {
-                                if (fv) atomicAdd((unsigned long long*)&s_wide[o1 + rows[q]], (unsigned long long)(ng ? -fv : fv));
+                                atomicAdd((unsigned long long*)&s_wide[o1 + rows[q]], (unsigned long long)(ng ? -fv : fv));
                                 if (fw) atomicAdd((unsigned long long*)&s_wide[o2 + rows[q]], (unsigned long long)(ng ? -fw : fw));
                             } else {
-                                if (fv) split_add(s_hi, s_lo, o1 + rows[q], ng ? -fv : fv);
-                                if (fw) split_add(s_hi, s_lo, o2 + rows[q], ng ? -fw : fw);
+                                split_add(s_hi, s_lo, o1 + rows[q], ng ? -fv : fv);
+                                if (want_sw) split_add(s_hi, s_lo, o2 + rows[q], ng ? -fw : fw);
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            if (q < sp.zeta) {
+                                const bool ng = (neg >> q) & 1u;
+                                if (f64) {
+                                    atomicAdd((unsigned long long*)&s_wide[o1 + rows[q]], (unsigned long long)(ng ? -fv : fv));
+                                    if (fw) atomicAdd((unsigned long long*)&s_wide[o2 + rows[q]], (unsigned long long)(ng ? -fw : fw));
+                                } else {
+                                    split_add(s_hi, s_lo, o1 + rows[q], ng ? -fv : fv);
+                                    if (want_sw) split_add(s_hi, s_lo, o2 + rows[q], ng ? -fw : fw);
+                                }
                             }
                         }
                     }
@@ -510,6 +584,20 @@ __global__ void k_sketch_finish(const long long* acc, int m, long long n, int ze
         y[t] = (double)acc[t] * scale;
 }
 
+// sketch table: the 8 rows and signs of column i, one byte per block
+__global__ void k_sketch_table(SketchParams sp, long long n, unsigned long long* tab) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        int rows[16];
+        unsigned neg;
+        sketch_column8(sp, i, rows, &neg);
+        unsigned long long e = 0;
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+            e |= (unsigned long long)((unsigned)(rows[t] - sp.lo[t]) | (((neg >> t) & 1u) << 7)) << (8 * t);
+        tab[i] = e;
+    }
+}
+
 // fresh DevState for a new solve (j = -1, all RHS OK, keys cleared)
 __global__ void k_reset_state(DevState* st) {
     const int t = threadIdx.x;
@@ -529,6 +617,20 @@ __global__ void k_reset_state(DevState* st) {
 }
 
 }  // namespace
+
+bool sketch_table_ok(const SketchParams& sp) {
+    if (sp.zeta != 8) return false;
+    for (int t = 0; t < 8; ++t)
+        if (sp.lo[t + 1] - sp.lo[t] > 128) return false;
+    return true;
+}
+
+cudaError_t launch_sketch_table(const SketchParams& sp, long long n, unsigned long long* tab, cudaStream_t s) {
+    long long blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_sketch_table<<<(int)blocks, 256, 0, s>>>(sp, n, tab);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_reset_state(DevState* st, cudaStream_t s) {
     k_reset_state<<<1, 64, 0, s>>>(st);
@@ -559,7 +661,7 @@ cudaError_t launch_pivot_solve(int storage, const Geom& g, const Bufs& bf, cudaS
     const int K1 = g.k_max + 1;
     IPF_DISPATCH_STORAGE(storage, {
         using Acc = typename AccOf<T>::type;
-        const size_t smem = (size_t)((K1 + 1) & ~1) * sizeof(double) + lp_stride(g.k_max) * sizeof(double);
+        const size_t smem = lp_stride(g.k_max) * sizeof(double) + (size_t)((K1 + 1) & ~1) * sizeof(double);
         auto fn = k_pivot_solve<T, Acc>;
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

@@ -172,6 +172,72 @@ __global__ void __launch_bounds__(256, 2) k_conv2d_v(const T* __restrict__ vbase
 }
 
 // ------------------------------------------------------------------------
+// 2-D convolution, FP32 accumulation, square-padded PSF KW x KW (KW <= 31),
+// column formulation.  Thread t of a 256-thread block owns image column
+// x0 + t of a 256-column tile and OY consecutive output rows.  For each kernel column b it loads the PSF column F[0..KW)[b] into
+// registers, then walks the staged input column (OY + KW - 1 values, one
+// conflict-free 4-byte shared load each: consecutive lanes read consecutive
+// x) and adds F[r - a][b] * in[r] into the OY accumulators.
+// ------------------------------------------------------------------------
+template <class T, int KW, int OY>
+__global__ void __launch_bounds__(256, 4) k_conv2d_c(const T* __restrict__ vbase, long long ldv,
+                                                    const int* __restrict__ jptr, float* __restrict__ w, int H,
+                                                    int W, const float* __restrict__ psf, int ph, int pw) {
+    const T* v = jptr ? vbase + (size_t)(*jptr) * ldv : vbase;
+    constexpr int TX = 256, TY = OY;
+    constexpr int IH = TY + KW - 1, IW = TX + KW - 1;
+    constexpr int IWP = IW + 1;                       // odd pitch keeps column walks conflict-free
+    extern __shared__ float smem_c[];
+    float* s_in = smem_c;                             // IH x IWP
+    float* s_k = s_in + IH * IWP;                     // KW x KW flipped, zero-padded
+    const int c = KW / 2;
+    const int y0 = blockIdx.y * TY, x0 = blockIdx.x * TX;
+    const int pady = (KW - ph) / 2, padx = (KW - pw) / 2;
+    for (int t = threadIdx.x; t < KW * KW; t += blockDim.x) {
+        const int a = t / KW, bb = t - a * KW;
+        const int ka = a - pady, kb = bb - padx;
+        float val = 0.f;
+        if (ka >= 0 && ka < ph && kb >= 0 && kb < pw) val = psf[(ph - 1 - ka) * pw + (pw - 1 - kb)];
+        s_k[t] = val;
+    }
+    for (int t = threadIdx.x; t < IH * IW; t += blockDim.x) {
+        const int a = t / IW, bb = t - a * IW;
+        const int yy = y0 - c + a, xx = x0 - c + bb;
+        float val = 0.f;
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W) val = to_acc(v[(size_t)yy * W + xx]);
+        s_in[a * IWP + bb] = val;
+    }
+    __syncthreads();
+    const int ox = threadIdx.x;                        // 0..255
+    float acc[OY];
+#pragma unroll
+    for (int a = 0; a < OY; ++a) acc[a] = 0.f;
+    for (int b = 0; b < KW; ++b) {
+        float f[KW];
+#pragma unroll
+        for (int a = 0; a < KW; ++a) f[a] = s_k[a * KW + b];
+        const float* col = s_in + ox + b;
+#pragma unroll
+        for (int r = 0; r < IH; ++r) {
+            const float x = col[r * IWP];
+#pragma unroll
+            for (int a = 0; a < OY; ++a) {
+                const int ky = r - a;
+                if (ky >= 0 && ky < KW) acc[a] = fmaf(f[ky], x, acc[a]);
+            }
+        }
+    }
+    const int xx = x0 + ox;
+    if (xx < W) {
+#pragma unroll
+        for (int a = 0; a < OY; ++a) {
+            const int yy = y0 + a;
+            if (yy < H) w[(size_t)yy * W + xx] = acc[a];
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
 // separable Gaussian then motion blur, each zero-boundary, fused per tile
 // ------------------------------------------------------------------------
 template <class T, class Acc, int TILE>
@@ -310,9 +376,21 @@ cudaError_t conv_dispatch(const OpDev& op, const T* v, long long ldv, const int*
             kern<<<grid, 256, smem, s>>>(v, ldv, jp, (float*)w, H, W, op.psf, op.ph, op.pw);
             return cudaGetLastError();
         };
-        if (mx <= 7) return gov(k_conv2d_v<T, 7, 2, 8>, 7);
-        if (mx <= 15) return gov(k_conv2d_v<T, 15, 2, 8>, 15);
-        if (mx <= 31) return gov(k_conv2d_v<T, 31, 2, 8>, 31);
+        // column formulation for square-paddable PSFs (ph <= KW, pw <= KW)
+        auto goc = [&](auto kern, int KW, int OY) -> cudaError_t {
+            const int IH = OY + KW - 1, IWP = 256 + KW;
+            const size_t smem = ((size_t)IH * IWP + (size_t)KW * KW) * sizeof(float);
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            dim3 grid((W + 255) / 256, (H + OY - 1) / OY);
+            kern<<<grid, 256, smem, s>>>(v, ldv, jp, (float*)w, H, W, op.psf, op.ph, op.pw);
+            return cudaGetLastError();
+        };
+        const int mk = op.ph > op.pw ? op.ph : op.pw;
+        if (mk <= 7) return goc(k_conv2d_c<T, 7, 16>, 7, 16);
+        if (mk <= 15) return goc(k_conv2d_c<T, 15, 16>, 15, 16);
+        if (mk <= 31) return goc(k_conv2d_c<T, 31, 16>, 31, 16);
+        (void)gov;
         return go(k_conv2d<T, Acc, 63, 2, 4>, 63, 32, 64);
     } else {
         if (mx <= 7) return go(k_conv2d<T, Acc, 7, 2, 4>, 7, 32, 64);

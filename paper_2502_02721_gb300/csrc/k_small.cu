@@ -273,44 +273,64 @@ __global__ void __launch_bounds__(256) k_small_solve(Geom g, const DevState* st,
 }
 
 // ------------------------------------------------------------------------
-// x = V_k y for nl lambdas; output [l][r][i]
+// x = V_k y for up to NL lambdas in one pass over V_k; output [l][r][i].
+// Each thread owns 16 bytes of every basis column per pass and keeps eight
+// 128-bit column loads in flight.
 // ------------------------------------------------------------------------
-template <class T>
+template <class T, int NL>
 __global__ void __launch_bounds__(256) k_reconstruct(Geom g, Bufs bf, const DevState* st, int k, int nl,
                                                       const double* Yw, int l0, int nlc, float* x) {
     using Acc = typename AccOf<T>::type;
     constexpr int VEC = 16 / sizeof(T);
     extern __shared__ unsigned char smem_raw[];
-    Acc* s_y = (Acc*)smem_raw;                 // [nlc][B][k]
+    Acc* s_y = (Acc*)smem_raw;                 // [NL][B][k]
     __shared__ int s_kb[kMaxRhs];
     const int B = g.B;
     if (threadIdx.x < B) s_kb[threadIdx.x] = kuse_of(st, threadIdx.x, k);
     __syncthreads();
-    for (int t = threadIdx.x; t < nlc * B * k; t += blockDim.x) {
+    for (int t = threadIdx.x; t < NL * B * k; t += blockDim.x) {
         const int l = t / (B * k), rem = t - l * B * k, r = rem / k, c = rem - r * k;
-        s_y[t] = (c < s_kb[r]) ? (Acc)Yw[((size_t)r * nl + l0 + l) * (k + 1) + c] : (Acc)0;
+        s_y[t] = (l < nlc && c < s_kb[r]) ? (Acc)Yw[((size_t)r * nl + l0 + l) * (k + 1) + c] : (Acc)0;
     }
     int kmax = 0;
     for (int r = 0; r < B; ++r) kmax = s_kb[r] > kmax ? s_kb[r] : kmax;
     __syncthreads();
     const T* V = (const T*)bf.V;
+    const size_t ldv = (size_t)g.ldv;
     const long long stride = (long long)gridDim.x * blockDim.x * VEC;
     for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) * VEC; base < g.N; base += stride) {
-        Acc acc[8][VEC];
+        Acc acc[NL][VEC];
 #pragma unroll
-        for (int l = 0; l < 8; ++l)
+        for (int l = 0; l < NL; ++l)
 #pragma unroll
             for (int q = 0; q < VEC; ++q) acc[l][q] = 0;
-        for (int c = 0; c < kmax; ++c) {
-            const uint4 raw = __ldcs((const uint4*)(V + (size_t)c * g.ldv + base));
-            const T* vv = (const T*)&raw;
+        const T* vb = V + base;
+        int c = 0;
+        for (; c + 8 <= kmax; c += 8) {
+            uint4 raw[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) raw[u] = __ldcs((const uint4*)(vb + (size_t)(c + u) * ldv));
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const T* vv = (const T*)&raw[u];
+#pragma unroll
+                for (int q = 0; q < VEC; ++q) {
+                    const int rr = (int)((base + q) & (B - 1));
+                    const Acc vq = to_acc(vv[q]);
+#pragma unroll
+                    for (int l = 0; l < NL; ++l) acc[l][q] = fma(s_y[((size_t)l * B + rr) * k + c + u], vq, acc[l][q]);
+                }
+            }
+        }
+        for (; c < kmax; ++c) {
+            const uint4 r1 = __ldcs((const uint4*)(vb + (size_t)c * ldv));
+            const T* vv = (const T*)&r1;
 #pragma unroll
             for (int q = 0; q < VEC; ++q) {
                 const int rr = (int)((base + q) & (B - 1));
                 const Acc vq = to_acc(vv[q]);
 #pragma unroll
-                for (int l = 0; l < 8; ++l)
-                    if (l < nlc) acc[l][q] = fma(s_y[((size_t)l * B + rr) * k + c], vq, acc[l][q]);
+                for (int l = 0; l < NL; ++l) acc[l][q] = fma(s_y[((size_t)l * B + rr) * k + c], vq, acc[l][q]);
             }
         }
 #pragma unroll
@@ -320,7 +340,7 @@ __global__ void __launch_bounds__(256) k_reconstruct(Geom g, Bufs bf, const DevS
             const long long i = e / B;
             const int rr = (int)(e - i * B);
 #pragma unroll
-            for (int l = 0; l < 8; ++l)
+            for (int l = 0; l < NL; ++l)
                 if (l < nlc) x[((size_t)(l0 + l) * B + rr) * g.n + i] = (float)acc[l][q];
         }
     }
@@ -389,10 +409,15 @@ cudaError_t launch_solve_lambdas(int storage, const Geom& g, const Bufs& bf, int
     k_small_solve<<<g.B * nl, 256, 0, s>>>(g, bf.st, k, nl, lambdas_dev, penalty, Mw, Tw, dM, dT, Sw, Yw);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !x_dev) return e;
-    for (int l0 = 0; l0 < nl; l0 += 8) {
-        const int nlc = nl - l0 < 8 ? nl - l0 : 8;
-        auto launch = [&](auto kern, int vec, size_t accsz) -> cudaError_t {
-            const size_t smem = accsz * (size_t)nlc * g.B * (k > 0 ? k : 1);
+    // lambdas in chunks whose y fit in shared memory next to each other
+    const size_t accsz = storage == IPF_STORE_F64 ? 8 : 4;
+    int cap = 8;
+    while (cap > 1 && accsz * cap * g.B * (k > 0 ? k : 1) > 96 * 1024) cap >>= 1;
+    for (int l0 = 0; l0 < nl; l0 += cap) {
+        const int nlc = nl - l0 < cap ? nl - l0 : cap;
+        const int NLp = nlc <= 1 ? 1 : nlc <= 2 ? 2 : nlc <= 4 ? 4 : 8;
+        auto launch = [&](auto kern, int vec) -> cudaError_t {
+            const size_t smem = accsz * (size_t)NLp * g.B * (k > 0 ? k : 1);
             cudaError_t ee = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (ee != cudaSuccess) return ee;
             long long chunks = (g.N + 256LL * vec - 1) / (256LL * vec);
@@ -401,11 +426,20 @@ cudaError_t launch_solve_lambdas(int storage, const Geom& g, const Bufs& bf, int
             kern<<<(int)blocks, 256, smem, s>>>(g, bf, bf.st, k, nl, Yw, l0, nlc, x_dev);
             return cudaGetLastError();
         };
+        auto byNL = [&](auto tag, int vec) -> cudaError_t {
+            using T = decltype(tag);
+            switch (NLp) {
+                case 1: return launch(k_reconstruct<T, 1>, vec);
+                case 2: return launch(k_reconstruct<T, 2>, vec);
+                case 4: return launch(k_reconstruct<T, 4>, vec);
+                default: return launch(k_reconstruct<T, 8>, vec);
+            }
+        };
         switch (storage) {
-            case IPF_STORE_F64: e = launch(k_reconstruct<double>, 2, 8); break;
-            case IPF_STORE_F32: e = launch(k_reconstruct<float>, 4, 4); break;
-            case IPF_STORE_BF16: e = launch(k_reconstruct<__nv_bfloat16>, 8, 4); break;
-            case IPF_STORE_F16: e = launch(k_reconstruct<__half>, 8, 4); break;
+            case IPF_STORE_F64: e = byNL(double(), 2); break;
+            case IPF_STORE_F32: e = byNL(float(), 4); break;
+            case IPF_STORE_BF16: e = byNL(__nv_bfloat16(), 8); break;
+            case IPF_STORE_F16: e = byNL(__half(), 8); break;
             default: return cudaErrorInvalidValue;
         }
         if (e != cudaSuccess) return e;
