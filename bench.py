@@ -271,28 +271,30 @@ def run_ours(args, rank, world, torch, dist):
 
     # --- roofline of the dominant kernel ------------------------------------
     ms, cnt, byts = prof16
-    names = ["operator", "pivot_solve", "update_argmax", "normalize_sketch", "init", "solve_qr", "solve_x"]
+    names = ["operator", "pivot_solve", "update_or_Vh", "normalize_sketch", "init", "solve_qr", "solve_x",
+             "pivot_rows", "combine"]
+    busy = sum(ms[:9])
     kern = {names[i]: {"ms_total": ms[i], "launches": int(cnt[i]),
-                       "share": ms[i] / max(sum(ms[:7]), 1e-9),
+                       "share": ms[i] / max(busy, 1e-9),
                        "GBps": (byts[i] / (ms[i] * 1e-3) / 1e9) if ms[i] > 0 and byts[i] > 0 else None}
-            for i in range(7)}
+            for i in range(9)}
     peak, peak_kind = _peaks()
-    upd = kern["update_argmax"]
-    roof = {"kernel": "k_update_f (u -= V_j h, zero pivots, argmax)", "bound": "hbm",
+    upd = kern["update_or_Vh"]
+    roof = {"kernel": "k_gemv<bf16,1> (t = V_j h)", "bound": "hbm",
             "achieved": upd["GBps"], "peak": peak, "unit": "GB/s",
             "frac": (upd["GBps"] / peak) if upd["GBps"] else None, "traffic": None,
             "peak_source": f"{peak_kind} hbm_gbs", "bytes_per_launch": byts[2] / max(cnt[2], 1),
-            "algorithmic_bytes": "per launch at step j: (j+1)*n*2 (read V_j, BF16) + 8n (read+write u, FP32) + n/8 (pivot bitmap)"}
+            "algorithmic_bytes": "per launch at step j: (j+1)*n*2 (read V_j, BF16) + 4n (write t, FP32)"}
     # FP32 FMA peak for the convolution (152 SMs x 128 lanes x 2 flop x clock)
     sm_mhz = clk.get("sm_mhz") or 2070.0
     conv_flops = 2.0 * 961 * n * cnt[0]
     conv_tf = conv_flops / (ms[0] * 1e-3) / 1e12 if ms[0] > 0 else None
     alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    roof_conv = {"kernel": "k_conv2d<bf16,31> (w = P * v)", "bound": "alu", "achieved": conv_tf,
+    roof_conv = {"kernel": "k_conv2d_c<bf16,31,16> (w = P * v)", "bound": "alu", "achieved": conv_tf,
                  "peak": alu_peak, "unit": "TFLOP/s", "frac": (conv_tf / alu_peak) if conv_tf else None,
                  "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock under load"}
-    dominant = max(range(7), key=lambda i: ms[i])
-    launches = int(cnt[0] + cnt[1] + cnt[2] + cnt[3] + 4 * cnt[4] + 2 * cnt[5] + 2 * cnt[6])
+    dominant = max(range(9), key=lambda i: ms[i])
+    launches = int(cnt[0] + cnt[1] + cnt[2] + cnt[3] + 4 * cnt[4] + 2 * cnt[5] + 2 * cnt[6] + cnt[7] + cnt[8])
 
     iters = world * args.steps * k
     value = iters / (t_max * 1e-3)

@@ -190,11 +190,15 @@ ipf_status ipf_solve(ipf_ctx* ctx, int k, const double* lambdas, int nl,
  * failure of the solve is reported by the next ipf_sync.                  */
 
 /* Kernel timings of a context created with config.profile = 1: for each
- * kind (0 operator, 1 pivot-block solve, 2 update+argmax, 3 normalise+sketch,
- * 4 initialisation, 5 projected-solve QR, 6 per-lambda solve + x = V_k y)
- * the summed milliseconds, launch counts and the summed algorithmic bytes
- * of the launches (0 where not defined), since the previous read.
- * Arrays of 8 entries, host; synchronises.                                */
+ * kind (0 operator, 1 pivot-block solve, 2 update+argmax or V_j h,
+ * 3 normalise+sketch, 4 initialisation, 5 projected-solve QR, 6 per-lambda
+ * solve + x = V_k y, 7 operator at the pivot rows, 8 u = A v_j - V_j h with
+ * argmax) the summed milliseconds, launch counts and the summed algorithmic
+ * bytes of the launches (0 where not defined), since the previous read.
+ * For PSF2D and CSR operators with float storage a step runs the operator
+ * on a second stream beside the pivot-row products, the pivot-block solve
+ * and V_j h, so kinds 0 and 2 overlap in time.
+ * Arrays of 10 entries, host; synchronises.                               */
 ipf_status ipf_profile_read(ipf_ctx* ctx, double* ms, long long* launches, double* bytes);
 
 /* Copy the method's state for RHS r to host memory (any pointer may be

@@ -161,8 +161,11 @@ struct ipf_ctx {
     SketchParams sp;
     int num_sms = 1;
     cudaStream_t s = nullptr;
+    cudaStream_t s2 = nullptr;          // second stream of the split step (operator branch)
     cudaStream_t user = nullptr;
     cudaEvent_t ev = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool split = false;                 // operator overlapped with the V_j stream
     int j_host = 0;                    // Hessenberg steps enqueued
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -177,9 +180,9 @@ struct ipf_ctx {
     struct Mark { int kind; double bytes; cudaEvent_t a, b; };
     std::vector<Mark> marks;
     std::vector<cudaEvent_t> spare;
-    double prof_ms[8] = {0};
-    long long prof_n[8] = {0};
-    double prof_bytes[8] = {0};
+    double prof_ms[10] = {0};
+    long long prof_n[10] = {0};
+    double prof_bytes[10] = {0};
 };
 
 struct ipf_op {
@@ -232,16 +235,21 @@ cudaEvent_t take_event(ipf_ctx* c) {
 
 // run one launch, bracketed by events in profile mode
 template <class F>
-cudaError_t timed(ipf_ctx* c, int kind, double bytes, F&& launch) {
+cudaError_t timed_on(ipf_ctx* c, cudaStream_t st, int kind, double bytes, F&& launch) {
     if (!c->cfg.profile) return launch();
     ipf_ctx::Mark m{kind, bytes, take_event(c), take_event(c)};
-    cudaError_t e = cudaEventRecord(m.a, c->s);
+    cudaError_t e = cudaEventRecord(m.a, st);
     if (e != cudaSuccess) return e;
     e = launch();
     if (e != cudaSuccess) return e;
-    e = cudaEventRecord(m.b, c->s);
+    e = cudaEventRecord(m.b, st);
     c->marks.push_back(m);
     return e;
+}
+
+template <class F>
+cudaError_t timed(ipf_ctx* c, int kind, double bytes, F&& launch) {
+    return timed_on(c, c->s, kind, bytes, launch);
 }
 
 size_t acc_bytes(const ipf_ctx* c) { return c->storage == IPF_STORE_F64 ? 8 : 4; }
@@ -265,6 +273,32 @@ bool sw_on(const ipf_ctx* c) {
 cudaError_t one_step(ipf_ctx* c, int j) {
     cudaError_t e;
     const double N = (double)c->g.N, sv = (double)storage_bytes(c->storage), ab = (double)acc_bytes(c);
+    if (c->split) {
+        // operator branch on s2, elimination branch on s, joined before the combine
+        if ((e = cudaEventRecord(c->ev_fork, c->s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(c->s2, c->ev_fork, 0)) != cudaSuccess) return e;
+        if ((e = timed_on(c, c->s2, 0, op_bytes(c), [&] {
+                 return launch_op_apply(c->op, c->storage, c->bf.V, c->g.ldv, &c->bf.st->j, c->B, c->bf.w, c->s2);
+             })) != cudaSuccess)
+            return e;
+        if ((e = cudaEventRecord(c->ev_join, c->s2)) != cudaSuccess) return e;
+        if ((e = timed(c, 7, 0.0, [&] {
+                 return launch_pivot_rows(c->op, c->storage, c->bf.V, c->g.ldv, c->bf.st, c->bf.piv, c->B, c->g.k_max,
+                                          c->bf.gpiv, c->s);
+             })) != cudaSuccess)
+            return e;
+        if ((e = timed(c, 1, 0.0, [&] { return launch_pivot_solve(c->storage, c->g, c->bf, c->s); })) != cudaSuccess)
+            return e;
+        if ((e = timed(c, 2, (double)(j + 1) * N * sv + 4.0 * N,
+                       [&] { return launch_gemv(c->storage, c->g, c->bf, c->num_sms, c->s); })) != cudaSuccess)
+            return e;
+        if ((e = cudaStreamWaitEvent(c->s, c->ev_join, 0)) != cudaSuccess) return e;
+        if ((e = timed(c, 8, 12.0 * N + N / 8.0, [&] { return launch_combine(c->g, c->bf, c->num_sms, c->s); })) !=
+            cudaSuccess)
+            return e;
+        return timed(c, 3, N * ab + N * sv,
+                     [&] { return launch_normalize(c->storage, c->g, c->bf, c->sp, sw_on(c), c->num_sms, c->s); });
+    }
     if ((e = timed(c, 0, op_bytes(c), [&] {
              return launch_op_apply(c->op, c->storage, c->bf.V, c->g.ldv, &c->bf.st->j, c->B, c->bf.w, c->s);
          })) != cudaSuccess)
@@ -332,7 +366,7 @@ size_t ipf_footprint(const ipf_operator* op, const ipf_config* cfg) {
     bytes += B * K1 * (sizeof(int) + sizeof(double) * cfg->k_max + sizeof(double) * K1) + K1 * B * acc;
     bytes += 2 * (size_t)B * K1 * cfg->m_s * 8 + (size_t)n * 8;
     Geom g; g.n = n; g.B = B; g.N = n * B; g.ldv = (long long)ldv; g.k_max = cfg->k_max; g.m_s = cfg->m_s; g.F = 0;
-    bytes += solve_ws_for(g) + 2 * (size_t)B * n * 4 + 256;
+    bytes += solve_ws_for(g) + 2 * (size_t)B * n * 4 + 256 + ldv * 4 + B * K1 * 4;
     if (op->kind == IPF_OP_CSR && op->mem == IPF_MEM_HOST)
         bytes += (size_t)(op->rows + 1) * 8 + (size_t)op->nnz * 8;
     else if (op->kind == IPF_OP_PSF2D)
@@ -385,7 +419,11 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
         }                                                           \
     } while (0)
     CK("stream", cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking));
+    CK("stream", cudaStreamCreateWithFlags(&c->s2, cudaStreamNonBlocking));
     CK("event", cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming));
+    CK("event", cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    CK("event", cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+    c->split = (op->kind == IPF_OP_PSF2D || op->kind == IPF_OP_CSR) && cfg.storage != IPF_STORE_F64;
     CK("order", enter(c));
     CK("operator upload", upload_op(op, c->al, &c->op, c->s));
 
@@ -412,6 +450,13 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     CK("alloc ispiv", c->al.get((void**)&bf.ispiv, (g.ldv / 32 + 1) * sizeof(unsigned)));
     CK("alloc SV", c->al.get((void**)&bf.accSV, B * K1 * cfg.m_s * sizeof(long long)));
     CK("alloc SW", c->al.get((void**)&bf.accSW, B * K1 * cfg.m_s * sizeof(long long)));
+    bf.t = nullptr;
+    bf.gpiv = nullptr;
+    if (c->split) {
+        CK("alloc t", c->al.get((void**)&bf.t, g.ldv * sizeof(float)));
+        CK("alloc g", c->al.get((void**)&bf.gpiv, B * K1 * sizeof(float)));
+        CK("memset t", cudaMemsetAsync(bf.t, 0, g.ldv * sizeof(float), c->s));
+    }
     if (sketch_table_ok(c->sp)) {
         unsigned long long* tab = nullptr;
         CK("alloc sketch table", c->al.get((void**)&tab, sizeof(unsigned long long) * (size_t)n));
@@ -480,7 +525,7 @@ ipf_status ipf_profile_read(ipf_ctx* c, double* ms, long long* launches, double*
         c->spare.push_back(m.b);
     }
     c->marks.clear();
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < 10; ++k) {
         if (ms) ms[k] = c->prof_ms[k];
         if (launches) launches[k] = c->prof_n[k];
         if (bytes) bytes[k] = c->prof_bytes[k];
@@ -726,6 +771,10 @@ void ipf_destroy(ipf_ctx* c) {
     if (c->graph) cudaGraphDestroy(c->graph);
     c->al.release();
     if (c->ev) cudaEventDestroy(c->ev);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->s2) cudaStreamSynchronize(c->s2);
+    if (c->s2) cudaStreamDestroy(c->s2);
     if (c->s) cudaStreamDestroy(c->s);
     delete c;
 }

@@ -231,6 +231,8 @@ struct Bufs {
                                    // (column 0 = S (b / beta), others for BF16/FP16 storage)
     const unsigned long long* sktab;  // n entries (zeta = 8, blocks <= 128 rows) or NULL:
                                       // byte t = row offset in block t | sign << 7
+    float* t;                      // ldv FP32: V_j h (split step), else NULL
+    float* gpiv;                   // [B][k_max+1] FP32: (A v_j)(p_i) (split step), else NULL
 };
 
 // operator on the device
@@ -258,6 +260,9 @@ struct OpDev {
 // vbase + (*jptr) * ldv is the input vector (jptr NULL: vbase itself)
 cudaError_t launch_op_apply(const OpDev& op, int storage, const void* vbase, long long ldv, const int* jptr, int B,
                             void* w, cudaStream_t s);
+// (A v_j)(p_i) for i <= j directly at the pivot rows (PSF2D and CSR); float accumulation
+cudaError_t launch_pivot_rows(const OpDev& op, int storage, const void* vbase, long long ldv, const DevState* st,
+                              const int* piv, int B, int k_max, float* gout, cudaStream_t s);
 cudaError_t launch_op_apply_f32_plain(const OpDev& op, const float* v, float* w, int nrhs,
                                       cudaStream_t s);
 // k_hess.cu
@@ -265,6 +270,9 @@ cudaError_t launch_reset_state(DevState* st, cudaStream_t s);
 cudaError_t launch_load_rhs(int storage, const float* b, const Geom& g, const Bufs& bf, cudaStream_t s);
 cudaError_t launch_pivot_solve(int storage, const Geom& g, const Bufs& bf, cudaStream_t s);
 cudaError_t launch_update(int storage, const Geom& g, const Bufs& bf, int num_sms, cudaStream_t s);
+// split step: t = V_j h, then u = w - t with pivots zeroed and argmax keys
+cudaError_t launch_gemv(int storage, const Geom& g, const Bufs& bf, int num_sms, cudaStream_t s);
+cudaError_t launch_combine(const Geom& g, const Bufs& bf, int num_sms, cudaStream_t s);
 cudaError_t launch_normalize(int storage, const Geom& g, const Bufs& bf, const SketchParams& sp,
                              bool want_sw, int num_sms, cudaStream_t s);
 // precomputed sketch columns for zeta = 8 with every block <= 128 rows

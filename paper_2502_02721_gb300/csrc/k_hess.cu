@@ -90,7 +90,11 @@ __global__ void __launch_bounds__(256) k_pivot_solve(Geom g, Bufs bf) {
         const double val = (double)to_acc(V[(size_t)c * g.ldv + pj]);
         Lp[rowj + c] = val;
     }
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) s_g[i] = (double)w[(size_t)piv[i] * B + r];
+    if (bf.gpiv) {
+        for (int i = threadIdx.x; i <= j; i += blockDim.x) s_g[i] = (double)bf.gpiv[(size_t)r * K1 + i];
+    } else {
+        for (int i = threadIdx.x; i <= j; i += blockDim.x) s_g[i] = (double)w[(size_t)piv[i] * B + r];
+    }
     if (threadIdx.x == 0 && bytes) {
         // bounded wait on the copy: gives up after ~2^22 polls and reports a timeout
         unsigned done = 0;
@@ -259,6 +263,121 @@ __global__ void __launch_bounds__(256, 4) k_update_f(Geom g, Bufs bf) {
     } else {
 #pragma unroll
         for (int q = 0; q < NK; ++q)
+            if (best[q]) atomicMax(&s_key[(int)((base0 + q) & (B - 1))], best[q]);
+    }
+    __syncthreads();
+    if (threadIdx.x < B && s_key[threadIdx.x])
+        atomicMax(&st->key[(j + 1) & 1][threadIdx.x], s_key[threadIdx.x]);
+}
+
+// ------------------------------------------------------------------------
+// split step, part 1: t = V_j h (the HBM stream), independent of A v_j
+// except through h.  Same load scheme as k_update_f.
+// ------------------------------------------------------------------------
+template <class T, int B>
+__global__ void __launch_bounds__(256, 4) k_gemv(Geom g, Bufs bf) {
+    constexpr int VEC = Vec16<T>::n;
+    extern __shared__ unsigned char smem_raw[];
+    float* s_coef = (float*)smem_raw;
+    DevState* st = bf.st;
+    const int j = st->j;
+    if (j < 0 || j >= g.k_max) return;
+    if (B == 1 && st->status[0] != IPF_OK) return;
+    const int nc = j + 1;
+    const float* coef = (const float*)bf.coef;
+    for (int t = threadIdx.x; t < nc * B; t += blockDim.x) s_coef[t] = coef[t];
+    __syncthreads();
+    const T* V = (const T*)bf.V;
+    float* tout = bf.t;
+    const unsigned N = (unsigned)g.N;
+    const size_t ldv = (size_t)g.ldv;
+    const unsigned stride = gridDim.x * blockDim.x * VEC;
+    for (unsigned base = (blockIdx.x * blockDim.x + threadIdx.x) * VEC; base < N; base += stride) {
+        float acc[VEC];
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) acc[q] = 0.f;
+        const T* vb = V + base;
+        int c = 0;
+        for (; c + 8 <= nc; c += 8) {
+            uint4 raw[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) raw[u] = __ldcs((const uint4*)(vb + (size_t)(c + u) * ldv));
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const T* vv = (const T*)&raw[u];
+#pragma unroll
+                for (int q = 0; q < VEC; ++q)
+                    acc[q] = fmaf(s_coef[(c + u) * B + ((base + q) & (B - 1))], to_acc(vv[q]), acc[q]);
+            }
+        }
+        for (; c < nc; ++c) {
+            const uint4 r1 = __ldcs((const uint4*)(vb + (size_t)c * ldv));
+            const T* vv = (const T*)&r1;
+#pragma unroll
+            for (int q = 0; q < VEC; ++q)
+                acc[q] = fmaf(s_coef[c * B + ((base + q) & (B - 1))], to_acc(vv[q]), acc[q]);
+        }
+        float4* to = (float4*)(tout + base);
+#pragma unroll
+        for (int q = 0; q < VEC / 4; ++q)
+            to[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+    }
+}
+
+// ------------------------------------------------------------------------
+// split step, part 2: u = w - t, u(pivots) = 0, argmax keys
+// ------------------------------------------------------------------------
+template <int B>
+__global__ void __launch_bounds__(256) k_combine(Geom g, Bufs bf) {
+    constexpr int LB = (B == 1) ? 0 : (B == 2) ? 1 : (B == 4) ? 2 : (B == 8) ? 3 : (B == 16) ? 4 : 5;
+    __shared__ unsigned long long s_key[kMaxRhs];
+    __shared__ int s_ok[kMaxRhs];
+    DevState* st = bf.st;
+    const int j = st->j;
+    if (j < 0 || j >= g.k_max) return;
+    if (threadIdx.x < B) {
+        s_key[threadIdx.x] = 0ull;
+        s_ok[threadIdx.x] = st->status[threadIdx.x] == IPF_OK;
+    }
+    __syncthreads();
+    if (B == 1 && !s_ok[0]) return;
+    float* w = (float*)bf.w;
+    const float* t = bf.t;
+    const unsigned N = (unsigned)g.N;
+    unsigned long long best[(B == 1) ? 1 : 4];
+#pragma unroll
+    for (int q = 0; q < ((B == 1) ? 1 : 4); ++q) best[q] = 0ull;
+    const unsigned stride = gridDim.x * blockDim.x * 4;
+    const unsigned base0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    for (unsigned base = base0; base < N; base += stride) {
+        const float4 a = *(const float4*)(w + base);
+        const float4 b = *(const float4*)(t + base);
+        float u[4] = {a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w};
+        const unsigned bits = bf.ispiv[base >> 5] >> (base & 31);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if ((bits >> q) & 1u) u[q] = 0.f;
+            const unsigned e = base + q;
+            const int rr = (int)(e & (B - 1));
+            if (e < N && s_ok[rr]) {
+                const unsigned long long k = argmax_key(u[q], e >> LB);
+                const int slot = (B == 1) ? 0 : q;
+                best[slot] = k > best[slot] ? k : best[slot];
+            }
+        }
+        *(float4*)(w + base) = make_float4(u[0], u[1], u[2], u[3]);
+    }
+    if (B == 1) {
+        unsigned long long k = best[0];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, k, off);
+            k = o > k ? o : k;
+        }
+        if ((threadIdx.x & 31) == 0 && k) atomicMax(&s_key[0], k);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
             if (best[q]) atomicMax(&s_key[(int)((base0 + q) & (B - 1))], best[q]);
     }
     __syncthreads();
@@ -708,6 +827,50 @@ cudaError_t launch_update(int storage, const Geom& g, const Bufs& bf, int num_sm
         case IPF_STORE_F16: return update_B<__half>(g, bf, (int)blocks, smem, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+template <class T>
+static cudaError_t gemv_B(const Geom& g, const Bufs& bf, int blocks, size_t smem, cudaStream_t s) {
+    switch (g.B) {
+        case 1: k_gemv<T, 1><<<blocks, 256, smem, s>>>(g, bf); break;
+        case 2: k_gemv<T, 2><<<blocks, 256, smem, s>>>(g, bf); break;
+        case 4: k_gemv<T, 4><<<blocks, 256, smem, s>>>(g, bf); break;
+        case 8: k_gemv<T, 8><<<blocks, 256, smem, s>>>(g, bf); break;
+        case 16: k_gemv<T, 16><<<blocks, 256, smem, s>>>(g, bf); break;
+        case 32: k_gemv<T, 32><<<blocks, 256, smem, s>>>(g, bf); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemv(int storage, const Geom& g, const Bufs& bf, int num_sms, cudaStream_t s) {
+    int per_thread = 16 / (int)(storage == IPF_STORE_F32 ? 4 : 2);
+    const long long chunks = (g.N + (long long)256 * per_thread - 1) / ((long long)256 * per_thread);
+    long long blocks = (long long)num_sms * 4;
+    if (blocks > chunks) blocks = chunks < 1 ? 1 : chunks;
+    const size_t smem = (size_t)(g.k_max + 1) * g.B * sizeof(float);
+    switch (storage) {
+        case IPF_STORE_F32: return gemv_B<float>(g, bf, (int)blocks, smem, s);
+        case IPF_STORE_BF16: return gemv_B<__nv_bfloat16>(g, bf, (int)blocks, smem, s);
+        case IPF_STORE_F16: return gemv_B<__half>(g, bf, (int)blocks, smem, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_combine(const Geom& g, const Bufs& bf, int num_sms, cudaStream_t s) {
+    long long blocks = (g.N + 1023) / 1024;
+    if (blocks > (long long)num_sms * 8) blocks = (long long)num_sms * 8;
+    if (blocks < 1) blocks = 1;
+    switch (g.B) {
+        case 1: k_combine<1><<<(int)blocks, 256, 0, s>>>(g, bf); break;
+        case 2: k_combine<2><<<(int)blocks, 256, 0, s>>>(g, bf); break;
+        case 4: k_combine<4><<<(int)blocks, 256, 0, s>>>(g, bf); break;
+        case 8: k_combine<8><<<(int)blocks, 256, 0, s>>>(g, bf); break;
+        case 16: k_combine<16><<<(int)blocks, 256, 0, s>>>(g, bf); break;
+        case 32: k_combine<32><<<(int)blocks, 256, 0, s>>>(g, bf); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 static int pick_group(int B, int m_s, int nacc) {

@@ -444,6 +444,53 @@ cudaError_t apply_T(const OpDev& op, const void* v, long long ldv, const int* jp
     }
 }
 
+// (A v_j)(p_i), i <= j: one warp per (pivot, RHS), lanes over the stencil
+// taps or the row's nonzeros, a fixed-order shuffle reduction.
+template <class T>
+__global__ void __launch_bounds__(256) k_pivot_rows_psf(const T* __restrict__ vbase, long long ldv,
+                                                         const DevState* __restrict__ st, const int* __restrict__ piv,
+                                                         int H, int W, const float* __restrict__ psf, int ph, int pw,
+                                                         float* __restrict__ gout) {
+    const int j = st->j;
+    const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    if (j < 0 || i > j || st->status[0] != IPF_OK) return;
+    const T* v = vbase + (size_t)j * ldv;
+    const int lane = threadIdx.x & 31;
+    const int p = piv[i];
+    const int py = p / W, px = p - py * W;
+    const int cy = ph / 2, cx = pw / 2;
+    float acc = 0.f;
+    for (int t = lane; t < ph * pw; t += 32) {
+        const int ky = t / pw, kx = t - ky * pw;
+        const int yy = py - ky + cy, xx = px - kx + cx;
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W) acc = fmaf(psf[t], to_acc(v[(size_t)yy * W + xx]), acc);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) gout[i] = acc;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_pivot_rows_csr(const T* __restrict__ vbase, long long ldv,
+                                                         const DevState* __restrict__ st, const int* __restrict__ piv,
+                                                         int B, int K1, const long long* __restrict__ rowptr,
+                                                         const int* __restrict__ colind, const float* __restrict__ vals,
+                                                         float* __restrict__ gout) {
+    const int j = st->j;
+    const int wid = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int i = wid / B, r = wid - (wid / B) * B;
+    if (j < 0 || i > j || r >= B || st->status[r] != IPF_OK) return;
+    const T* v = vbase + (size_t)j * ldv;
+    const int lane = threadIdx.x & 31;
+    const long long row = piv[(size_t)r * K1 + i];
+    float acc = 0.f;
+    for (long long q = rowptr[row] + lane; q < rowptr[row + 1]; q += 32)
+        acc = fmaf(vals[q], to_acc(v[(size_t)colind[q] * B + r]), acc);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) gout[(size_t)r * K1 + i] = acc;
+}
+
 __global__ void k_interleave(const float* __restrict__ src, float* __restrict__ dst, long long n, int B, int dir) {
     const long long N = n * B;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
@@ -455,6 +502,31 @@ __global__ void k_interleave(const float* __restrict__ src, float* __restrict__ 
 }
 
 }  // namespace
+
+cudaError_t launch_pivot_rows(const OpDev& op, int storage, const void* vbase, long long ldv, const DevState* st,
+                              const int* piv, int B, int k_max, float* gout, cudaStream_t s) {
+    const int K1 = k_max + 1;
+    const int warps = K1 * (op.kind == IPF_OP_CSR ? B : 1);
+    const int blocks = (warps + 7) / 8;
+    auto go = [&](auto tag) -> cudaError_t {
+        using T = decltype(tag);
+        if (op.kind == IPF_OP_PSF2D)
+            k_pivot_rows_psf<T><<<blocks, 256, 0, s>>>((const T*)vbase, ldv, st, piv, op.rows, op.cols, op.psf, op.ph,
+                                                       op.pw, gout);
+        else if (op.kind == IPF_OP_CSR)
+            k_pivot_rows_csr<T><<<blocks, 256, 0, s>>>((const T*)vbase, ldv, st, piv, B, K1, op.rowptr, op.colind,
+                                                       op.vals, gout);
+        else
+            return cudaErrorInvalidValue;
+        return cudaGetLastError();
+    };
+    switch (storage) {
+        case IPF_STORE_F32: return go(float());
+        case IPF_STORE_BF16: return go(__nv_bfloat16());
+        case IPF_STORE_F16: return go(__half());
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_op_apply(const OpDev& op, int storage, const void* vbase, long long ldv, const int* jptr, int B,
                             void* w, cudaStream_t s) {
