@@ -274,14 +274,9 @@ cudaError_t one_step(ipf_ctx* c, int j) {
     cudaError_t e;
     const double N = (double)c->g.N, sv = (double)storage_bytes(c->storage), ab = (double)acc_bytes(c);
     if (c->split) {
-        // operator branch on s2, elimination branch on s, joined before the combine
-        if ((e = cudaEventRecord(c->ev_fork, c->s)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(c->s2, c->ev_fork, 0)) != cudaSuccess) return e;
-        if ((e = timed_on(c, c->s2, 0, op_bytes(c), [&] {
-                 return launch_op_apply(c->op, c->storage, c->bf.V, c->g.ldv, &c->bf.st->j, c->B, c->bf.w, c->s2);
-             })) != cudaSuccess)
-            return e;
-        if ((e = cudaEventRecord(c->ev_join, c->s2)) != cudaSuccess) return e;
+        // h first (products at the pivot rows + FP64 pivot-block solve, small),
+        // then the operator on s2 overlapped with V_j h on s, joined before the
+        // combine
         if ((e = timed(c, 7, 0.0, [&] {
                  return launch_pivot_rows(c->op, c->storage, c->bf.V, c->g.ldv, c->bf.st, c->bf.piv, c->B, c->g.k_max,
                                           c->bf.gpiv, c->s);
@@ -289,6 +284,13 @@ cudaError_t one_step(ipf_ctx* c, int j) {
             return e;
         if ((e = timed(c, 1, 0.0, [&] { return launch_pivot_solve(c->storage, c->g, c->bf, c->s); })) != cudaSuccess)
             return e;
+        if ((e = cudaEventRecord(c->ev_fork, c->s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(c->s2, c->ev_fork, 0)) != cudaSuccess) return e;
+        if ((e = timed_on(c, c->s2, 0, op_bytes(c), [&] {
+                 return launch_op_apply(c->op, c->storage, c->bf.V, c->g.ldv, &c->bf.st->j, c->B, c->bf.w, c->s2);
+             })) != cudaSuccess)
+            return e;
+        if ((e = cudaEventRecord(c->ev_join, c->s2)) != cudaSuccess) return e;
         if ((e = timed(c, 2, (double)(j + 1) * N * sv + 4.0 * N,
                        [&] { return launch_gemv(c->storage, c->g, c->bf, c->num_sms, c->s); })) != cudaSuccess)
             return e;
@@ -418,8 +420,14 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
             return code;                                            \
         }                                                           \
     } while (0)
-    CK("stream", cudaStreamCreateWithFlags(&c->s, cudaStreamNonBlocking));
-    CK("stream", cudaStreamCreateWithFlags(&c->s2, cudaStreamNonBlocking));
+    {
+        // the elimination branch (V_j h) gets the higher priority so its CTAs are
+        // placed first whenever the operator branch frees room
+        int lo = 0, hi = 0;
+        CK("priorities", cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        CK("stream", cudaStreamCreateWithPriority(&c->s, cudaStreamNonBlocking, hi));
+        CK("stream", cudaStreamCreateWithPriority(&c->s2, cudaStreamNonBlocking, lo));
+    }
     CK("event", cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming));
     CK("event", cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     CK("event", cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
