@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(256, 4) k_update_f(Geom g, Bufs bf) {
 // except through h.  Same load scheme as k_update_f.
 // ------------------------------------------------------------------------
 template <class T, int B>
-__global__ void __launch_bounds__(256, 4) k_gemv(Geom g, Bufs bf) {
+__global__ void __launch_bounds__(512, 1) k_gemv(Geom g, Bufs bf) {
     constexpr int VEC = Vec16<T>::n;
     extern __shared__ unsigned char smem_raw[];
     float* s_coef = (float*)smem_raw;
@@ -832,21 +832,23 @@ cudaError_t launch_update(int storage, const Geom& g, const Bufs& bf, int num_sm
 template <class T>
 static cudaError_t gemv_B(const Geom& g, const Bufs& bf, int blocks, size_t smem, cudaStream_t s) {
     switch (g.B) {
-        case 1: k_gemv<T, 1><<<blocks, 256, smem, s>>>(g, bf); break;
-        case 2: k_gemv<T, 2><<<blocks, 256, smem, s>>>(g, bf); break;
-        case 4: k_gemv<T, 4><<<blocks, 256, smem, s>>>(g, bf); break;
-        case 8: k_gemv<T, 8><<<blocks, 256, smem, s>>>(g, bf); break;
-        case 16: k_gemv<T, 16><<<blocks, 256, smem, s>>>(g, bf); break;
-        case 32: k_gemv<T, 32><<<blocks, 256, smem, s>>>(g, bf); break;
+        case 1: k_gemv<T, 1><<<blocks, 512, smem, s>>>(g, bf); break;
+        case 2: k_gemv<T, 2><<<blocks, 512, smem, s>>>(g, bf); break;
+        case 4: k_gemv<T, 4><<<blocks, 512, smem, s>>>(g, bf); break;
+        case 8: k_gemv<T, 8><<<blocks, 512, smem, s>>>(g, bf); break;
+        case 16: k_gemv<T, 16><<<blocks, 512, smem, s>>>(g, bf); break;
+        case 32: k_gemv<T, 32><<<blocks, 512, smem, s>>>(g, bf); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_gemv(int storage, const Geom& g, const Bufs& bf, int num_sms, cudaStream_t s) {
+    // one 512-thread CTA per SM: it co-resides with two operator CTAs, so the
+    // HBM stream and the FP32 operator run on every SM at the same time
     int per_thread = 16 / (int)(storage == IPF_STORE_F32 ? 4 : 2);
-    const long long chunks = (g.N + (long long)256 * per_thread - 1) / ((long long)256 * per_thread);
-    long long blocks = (long long)num_sms * 4;
+    const long long chunks = (g.N + (long long)512 * per_thread - 1) / ((long long)512 * per_thread);
+    long long blocks = (long long)num_sms;
     if (blocks > chunks) blocks = chunks < 1 ? 1 : chunks;
     const size_t smem = (size_t)(g.k_max + 1) * g.B * sizeof(float);
     switch (storage) {

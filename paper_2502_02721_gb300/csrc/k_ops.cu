@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(256, 2) k_conv2d_v(const T* __restrict__ vbase
 // x) and adds F[r - a][b] * in[r] into the OY accumulators.
 // ------------------------------------------------------------------------
 template <class T, int KW, int OY>
-__global__ void __launch_bounds__(256, 4) k_conv2d_c(const T* __restrict__ vbase, long long ldv,
+__global__ void __launch_bounds__(256, 2) k_conv2d_c(const T* __restrict__ vbase, long long ldv,
                                                     const int* __restrict__ jptr, float* __restrict__ w, int H,
                                                     int W, const float* __restrict__ psf, int ph, int pw) {
     const T* v = jptr ? vbase + (size_t)(*jptr) * ldv : vbase;
