@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(256, 4) k_update_f(Geom g, Bufs bf) {
 // except through h.  Same load scheme as k_update_f.
 // ------------------------------------------------------------------------
 template <class T, int B>
-__global__ void __launch_bounds__(512, 1) k_gemv(Geom g, Bufs bf) {
+__global__ void __launch_bounds__(512, 2) k_gemv(Geom g, Bufs bf) {
     constexpr int VEC = Vec16<T>::n;
     extern __shared__ unsigned char smem_raw[];
     float* s_coef = (float*)smem_raw;
