@@ -170,7 +170,8 @@ def run_ours(args, rank, world, torch, dist):
 
     def make_ctx(storage, profile):
         cfg = bd.default_config(k_max=k, m_s=p.m_s, zeta=p.zeta, seed=p.sketch_seed, storage=storage,
-                                profile=profile, use_graphs=0 if profile else 1, stream=stream.cuda_stream)
+                                profile=profile, use_graphs=0 if profile else 1, stream=stream.cuda_stream,
+                                overlap=1 if args.overlap else 0)
         return bd.Context(op, b_dev, cfg, keep)
 
     def timed_solves(ctx, x_out, steps, warmup, lam=(0.0,)):
@@ -305,7 +306,8 @@ def run_ours(args, rank, world, torch, dist):
         "config": {"workload": WORKLOAD, "n": n, "k": k, "m_s": p.m_s, "zeta": p.zeta, "storage": "bf16",
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2: the BF16 basis is 1.69 GB (L2 129 MB)",
-                   "launch": "eager launches with CUDA events around each kernel (profile mode)"},
+                   "launch": "eager launches with CUDA events around each kernel (profile mode)",
+                   "overlap": bool(args.overlap)},
         "solves_per_s": world * args.steps / (t_max * 1e-3),
         "latency_ms": {"p50": float(np.percentile(per16, 50)), "p99": float(np.percentile(per16, 99))},
         "fp32": {"iters_per_s": steps32 * k / (t32 * 1e-3), "solves_per_s": steps32 / (t32 * 1e-3),
@@ -386,6 +388,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--overlap", action="store_true", help="operator on a second stream beside V_j h")
     ap.add_argument("--small", default=None, choices=["f32", "bf16", "f16", "f64"],
                     help="run one small solve (profiling target) and exit")
     args = ap.parse_args()

@@ -116,6 +116,8 @@ typedef struct ipf_config {
     int use_graphs;              /* capture each Hessenberg step in a CUDA graph            */
     int profile;                 /* bracket every kernel with CUDA events on the context's
                                     stream (launches eagerly; read with ipf_profile_read)   */
+    int overlap;                 /* PSF2D/CSR with float storage: run the operator on a
+                                    second stream beside V_j h (default 0: one stream)      */
     void* stream;                /* cudaStream_t of the caller (NULL: legacy default)      */
     ipf_alloc_fn alloc;          /* optional device allocator (e.g. a framework's pool)    */
     ipf_free_fn free;
@@ -195,9 +197,8 @@ ipf_status ipf_solve(ipf_ctx* ctx, int k, const double* lambdas, int nl,
  * solve + x = V_k y, 7 operator at the pivot rows, 8 u = A v_j - V_j h with
  * argmax) the summed milliseconds, launch counts and the summed algorithmic
  * bytes of the launches (0 where not defined), since the previous read.
- * For PSF2D and CSR operators with float storage a step runs the operator
- * on a second stream beside the pivot-row products, the pivot-block solve
- * and V_j h, so kinds 0 and 2 overlap in time.
+ * With config.overlap a step runs the operator on a second stream beside
+ * V_j h, so kinds 0 and 2 overlap in time.
  * Arrays of 10 entries, host; synchronises.                               */
 ipf_status ipf_profile_read(ipf_ctx* ctx, double* ms, long long* launches, double* bytes);
 

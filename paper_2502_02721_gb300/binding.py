@@ -47,7 +47,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 class ipf_config(C.Structure):
     _fields_ = [("k_max", C.c_int), ("m_s", C.c_int), ("zeta", C.c_int), ("seed", C.c_ulonglong),
                 ("storage", C.c_int), ("penalty", C.c_int), ("zform", C.c_int), ("nrhs", C.c_int),
-                ("use_graphs", C.c_int), ("profile", C.c_int), ("stream", C.c_void_p),
+                ("use_graphs", C.c_int), ("profile", C.c_int), ("overlap", C.c_int),
+                ("stream", C.c_void_p),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
 
 

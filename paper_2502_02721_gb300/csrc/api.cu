@@ -431,7 +431,7 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     CK("event", cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming));
     CK("event", cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     CK("event", cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
-    c->split = (op->kind == IPF_OP_PSF2D || op->kind == IPF_OP_CSR) && cfg.storage != IPF_STORE_F64;
+    c->split = cfg.overlap && (op->kind == IPF_OP_PSF2D || op->kind == IPF_OP_CSR) && cfg.storage != IPF_STORE_F64;
     CK("order", enter(c));
     CK("operator upload", upload_op(op, c->al, &c->op, c->s));
 

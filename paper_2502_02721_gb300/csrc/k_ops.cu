@@ -238,6 +238,87 @@ __global__ void __launch_bounds__(256, 2) k_conv2d_c(const T* __restrict__ vbase
 }
 
 // ------------------------------------------------------------------------
+// Packed-FMA column convolution (Blackwell fma.rn.f32x2: two FP32 FMAs per
+// instruction).  Like k_conv2d_c, but output rows are paired: for input row
+// r and pair (2a, 2a+1), {acc[2a], acc[2a+1]} += {F[ky][b], F[ky-1][b]} * {x, x}
+// with ky = r - 2a, so one loaded value feeds both rows and the PSF column
+// lives in registers as KW+1 packed pairs (F[-1] = F[KW] = 0).
+// ------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+    return (unsigned long long)__float_as_uint(lo) | ((unsigned long long)__float_as_uint(hi) << 32);
+}
+
+template <class T, int KW, int OY>
+__global__ void __launch_bounds__(256, 2) k_conv2d_c2(const T* __restrict__ vbase, long long ldv,
+                                                     const int* __restrict__ jptr, float* __restrict__ w, int H,
+                                                     int W, const float* __restrict__ psf, int ph, int pw) {
+    static_assert(OY % 2 == 0, "OY must be even");
+    const T* v = jptr ? vbase + (size_t)(*jptr) * ldv : vbase;
+    constexpr int TX = 256, TY = OY;
+    constexpr int IH = TY + KW - 1, IW = TX + KW - 1;
+    constexpr int IWP = IW + 1;
+    constexpr int NP = KW + 1;                        // packed pairs per PSF column
+    extern __shared__ unsigned long long smem_p[];
+    unsigned long long* s_f2 = smem_p;                // KW columns x NP pairs
+    float* s_in = (float*)(s_f2 + KW * NP);           // IH x IWP
+    const int c = KW / 2;
+    const int y0 = blockIdx.y * TY, x0 = blockIdx.x * TX;
+    const int pady = (KW - ph) / 2, padx = (KW - pw) / 2;
+    auto F = [&](int a, int bb) -> float {            // flipped, zero-padded PSF
+        const int ka = a - pady, kb = bb - padx;
+        if (a < 0 || a >= KW || ka < 0 || ka >= ph || kb < 0 || kb >= pw) return 0.f;
+        return psf[(ph - 1 - ka) * pw + (pw - 1 - kb)];
+    };
+    for (int t = threadIdx.x; t < KW * NP; t += blockDim.x) {
+        const int bb = t / NP, ky = t - bb * NP;
+        s_f2[t] = pack2(F(ky, bb), F(ky - 1, bb));
+    }
+    for (int t = threadIdx.x; t < IH * IW; t += blockDim.x) {
+        const int a = t / IW, bb = t - a * IW;
+        const int yy = y0 - c + a, xx = x0 - c + bb;
+        float val = 0.f;
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W) val = to_acc(v[(size_t)yy * W + xx]);
+        s_in[a * IWP + bb] = val;
+    }
+    __syncthreads();
+    const int ox = threadIdx.x;
+    unsigned long long acc[OY / 2];
+#pragma unroll
+    for (int a = 0; a < OY / 2; ++a) acc[a] = 0ull;
+    for (int b = 0; b < KW; ++b) {
+        unsigned long long f2[NP];
+#pragma unroll
+        for (int q = 0; q < NP; ++q) f2[q] = s_f2[b * NP + q];
+        const float* col = s_in + ox + b;
+#pragma unroll
+        for (int r = 0; r < IH; ++r) {
+            const float x = col[r * IWP];
+            const unsigned long long xx = pack2(x, x);
+#pragma unroll
+            for (int a2 = 0; a2 < OY / 2; ++a2) {
+                const int ky = r - 2 * a2;
+                if (ky >= 0 && ky <= KW) acc[a2] = ffma2(f2[ky], xx, acc[a2]);
+            }
+        }
+    }
+    const int xo = x0 + ox;
+    if (xo < W) {
+#pragma unroll
+        for (int a2 = 0; a2 < OY / 2; ++a2) {
+            const int yy = y0 + 2 * a2;
+            if (yy < H) w[(size_t)yy * W + xo] = __uint_as_float((unsigned)(acc[a2] & 0xFFFFFFFFull));
+            if (yy + 1 < H) w[(size_t)(yy + 1) * W + xo] = __uint_as_float((unsigned)(acc[a2] >> 32));
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
 // separable Gaussian then motion blur, each zero-boundary, fused per tile
 // ------------------------------------------------------------------------
 template <class T, class Acc, int TILE>
@@ -386,10 +467,19 @@ cudaError_t conv_dispatch(const OpDev& op, const T* v, long long ldv, const int*
             kern<<<grid, 256, smem, s>>>(v, ldv, jp, (float*)w, H, W, op.psf, op.ph, op.pw);
             return cudaGetLastError();
         };
+        auto goc2 = [&](auto kern, int KW, int OY) -> cudaError_t {
+            const int IH = OY + KW - 1, IWP = 256 + KW;
+            const size_t smem = (size_t)KW * (KW + 1) * 8 + (size_t)IH * IWP * sizeof(float);
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            dim3 grid((W + 255) / 256, (H + OY - 1) / OY);
+            kern<<<grid, 256, smem, s>>>(v, ldv, jp, (float*)w, H, W, op.psf, op.ph, op.pw);
+            return cudaGetLastError();
+        };
         const int mk = op.ph > op.pw ? op.ph : op.pw;
         if (mk <= 7) return goc(k_conv2d_c<T, 7, 16>, 7, 16);
-        if (mk <= 15) return goc(k_conv2d_c<T, 15, 16>, 15, 16);
-        if (mk <= 31) return goc(k_conv2d_c<T, 31, 16>, 31, 16);
+        if (mk <= 15) return goc2(k_conv2d_c2<T, 15, 16>, 15, 16);
+        if (mk <= 31) return goc2(k_conv2d_c2<T, 31, 16>, 31, 16);
         (void)gov;
         return go(k_conv2d<T, Acc, 63, 2, 4>, 63, 32, 64);
     } else {
