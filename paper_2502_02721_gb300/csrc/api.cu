@@ -130,6 +130,37 @@ cudaError_t upload_op(const ipf_operator* op, Alloc& al, OpDev* d, cudaStream_t 
     if (op->kind == IPF_OP_PSF2D) {
         d->ph = op->ph; d->pw = op->pw;
         e = dup(op->psf, sizeof(float) * op->ph * op->pw, (const void**)&d->psf);
+        if (e != cudaSuccess) return e;
+        // packed pairs {F[ky][b], F[ky-1][b]} of the flipped PSF, zero-padded to a
+        // square kw x kw, for the packed-FMA column convolution
+        const int mk = op->ph > op->pw ? op->ph : op->pw;
+        const int kw = mk <= 7 ? 7 : mk <= 15 ? 15 : mk <= 31 ? 31 : 0;
+        if (kw) {
+            std::vector<float> P((size_t)op->ph * op->pw);
+            if (op->mem == IPF_MEM_HOST) memcpy(P.data(), op->psf, P.size() * sizeof(float));
+            else if ((e = cudaMemcpy(P.data(), op->psf, P.size() * sizeof(float), cudaMemcpyDeviceToHost)) != cudaSuccess)
+                return e;
+            const int pady = (kw - op->ph) / 2, padx = (kw - op->pw) / 2;
+            auto F = [&](int a, int bb) -> float {
+                const int ka = a - pady, kb = bb - padx;
+                if (a < 0 || a >= kw || ka < 0 || ka >= op->ph || kb < 0 || kb >= op->pw) return 0.f;
+                return P[(size_t)(op->ph - 1 - ka) * op->pw + (op->pw - 1 - kb)];
+            };
+            std::vector<unsigned long long> pairs((size_t)kw * (kw + 1));
+            for (int bb = 0; bb < kw; ++bb)
+                for (int ky = 0; ky <= kw; ++ky) {
+                    const float lo = F(ky, bb), hi = F(ky - 1, bb);
+                    unsigned ulo, uhi;
+                    memcpy(&ulo, &lo, 4);
+                    memcpy(&uhi, &hi, 4);
+                    pairs[(size_t)bb * (kw + 1) + ky] = (unsigned long long)ulo | ((unsigned long long)uhi << 32);
+                }
+            void* pp = nullptr;
+            if ((e = al.get(&pp, pairs.size() * 8)) != cudaSuccess) return e;
+            if ((e = cudaMemcpy(pp, pairs.data(), pairs.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+            d->kw = kw;
+            d->psf_pairs = (const unsigned long long*)pp;
+        }
     } else if (op->kind == IPF_OP_PSF2D_SEP_MOTION) {
         d->slen = op->slen; d->mlen = op->mlen;
         if ((e = dup(op->sep_row, sizeof(float) * op->slen, (const void**)&d->sep_row)) != cudaSuccess) return e;

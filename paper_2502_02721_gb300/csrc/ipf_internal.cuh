@@ -250,7 +250,8 @@ struct OpDev {
     const int* colind;
     const float* vals;
     long long nnz;
-    float absmax;                  // ||A||_inf bound (max row sum of |a|)
+    int kw;                        // PSF2D: padded square width (7, 15, 31) of psf_pairs, else 0
+    const unsigned long long* psf_pairs;   // [kw][kw+1] packed {F[ky][b], F[ky-1][b]}, F flipped + padded
 };
 
 // ---------------------------------------------------------------------------

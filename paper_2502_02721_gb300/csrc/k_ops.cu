@@ -255,30 +255,18 @@ __device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
 }
 
 template <class T, int KW, int OY>
-__global__ void __launch_bounds__(256, 2) k_conv2d_c2(const T* __restrict__ vbase, long long ldv,
+__global__ void __launch_bounds__(128, 7) k_conv2d_c2(const T* __restrict__ vbase, long long ldv,
                                                      const int* __restrict__ jptr, float* __restrict__ w, int H,
-                                                     int W, const float* __restrict__ psf, int ph, int pw) {
+                                                     int W, const unsigned long long* __restrict__ pairs) {
     static_assert(OY % 2 == 0, "OY must be even");
     const T* v = jptr ? vbase + (size_t)(*jptr) * ldv : vbase;
-    constexpr int TX = 256, TY = OY;
+    constexpr int TX = 128, TY = OY;
     constexpr int IH = TY + KW - 1, IW = TX + KW - 1;
     constexpr int IWP = IW + 1;
     constexpr int NP = KW + 1;                        // packed pairs per PSF column
-    extern __shared__ unsigned long long smem_p[];
-    unsigned long long* s_f2 = smem_p;                // KW columns x NP pairs
-    float* s_in = (float*)(s_f2 + KW * NP);           // IH x IWP
+    extern __shared__ float s_in[];                   // IH x IWP
     const int c = KW / 2;
     const int y0 = blockIdx.y * TY, x0 = blockIdx.x * TX;
-    const int pady = (KW - ph) / 2, padx = (KW - pw) / 2;
-    auto F = [&](int a, int bb) -> float {            // flipped, zero-padded PSF
-        const int ka = a - pady, kb = bb - padx;
-        if (a < 0 || a >= KW || ka < 0 || ka >= ph || kb < 0 || kb >= pw) return 0.f;
-        return psf[(ph - 1 - ka) * pw + (pw - 1 - kb)];
-    };
-    for (int t = threadIdx.x; t < KW * NP; t += blockDim.x) {
-        const int bb = t / NP, ky = t - bb * NP;
-        s_f2[t] = pack2(F(ky, bb), F(ky - 1, bb));
-    }
     for (int t = threadIdx.x; t < IH * IW; t += blockDim.x) {
         const int a = t / IW, bb = t - a * IW;
         const int yy = y0 - c + a, xx = x0 - c + bb;
@@ -294,7 +282,7 @@ __global__ void __launch_bounds__(256, 2) k_conv2d_c2(const T* __restrict__ vbas
     for (int b = 0; b < KW; ++b) {
         unsigned long long f2[NP];
 #pragma unroll
-        for (int q = 0; q < NP; ++q) f2[q] = s_f2[b * NP + q];
+        for (int q = 0; q < NP; ++q) f2[q] = __ldg(pairs + b * NP + q);   // same address for the whole CTA
         const float* col = s_in + ox + b;
 #pragma unroll
         for (int r = 0; r < IH; ++r) {
@@ -468,18 +456,21 @@ cudaError_t conv_dispatch(const OpDev& op, const T* v, long long ldv, const int*
             return cudaGetLastError();
         };
         auto goc2 = [&](auto kern, int KW, int OY) -> cudaError_t {
-            const int IH = OY + KW - 1, IWP = 256 + KW;
-            const size_t smem = (size_t)KW * (KW + 1) * 8 + (size_t)IH * IWP * sizeof(float);
+            const int IH = OY + KW - 1, IWP = 128 + KW;
+            const size_t smem = (size_t)IH * IWP * sizeof(float);
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            dim3 grid((W + 255) / 256, (H + OY - 1) / OY);
-            kern<<<grid, 256, smem, s>>>(v, ldv, jp, (float*)w, H, W, op.psf, op.ph, op.pw);
+            dim3 grid((W + 127) / 128, (H + OY - 1) / OY);
+            kern<<<grid, 128, smem, s>>>(v, ldv, jp, (float*)w, H, W, op.psf_pairs);
             return cudaGetLastError();
         };
+        if (op.psf_pairs) {
+            if (op.kw == 7) return goc2(k_conv2d_c2<T, 7, 16>, 7, 16);
+            if (op.kw == 15) return goc2(k_conv2d_c2<T, 15, 16>, 15, 16);
+            if (op.kw == 31) return goc2(k_conv2d_c2<T, 31, 16>, 31, 16);
+        }
         const int mk = op.ph > op.pw ? op.ph : op.pw;
-        if (mk <= 7) return goc(k_conv2d_c<T, 7, 16>, 7, 16);
-        if (mk <= 15) return goc2(k_conv2d_c2<T, 15, 16>, 15, 16);
-        if (mk <= 31) return goc2(k_conv2d_c2<T, 31, 16>, 31, 16);
+        if (mk <= 31) return goc(k_conv2d_c<T, 31, 16>, 31, 16);
         (void)gov;
         return go(k_conv2d<T, Acc, 63, 2, 4>, 63, 32, 64);
     } else {
