@@ -360,6 +360,88 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_serving(args):
+    """Serving workload: Poisson arrivals (200 req/s) of mixed solves, 70%
+    deblurring (side U{128,256,512,1024}, Gaussian sigma U(1,4)), 30% CT
+    (128^2 or 256^2 parallel beam), k U{30..150}, m_s = 4k, lambda
+    log-U(1e-4, 1e-1), BF16 basis, at most 64 in flight."""
+    import torch
+    from gen import problems as P
+    from paper_2502_02721_gb300 import binding as bd, build as bl
+    if not os.path.exists(bl.lib_path()):
+        bl.build()
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(2502021 + 4)
+    keep = []
+    # pools of distinct inputs, made before the timed window
+    deblur = []
+    for side in (128, 256, 512, 1024):
+        for _ in range(3):
+            sigma = float(rng.uniform(1.0, 4.0))
+            psf = P.gaussian_psf(2 * int(np.ceil(3 * sigma)) + 1, sigma)
+            x = P.ellipse_phantom(side, side, 20, rng)
+            b = P.add_noise(P.blur_fft(x, psf), 0.01, rng).astype(np.float32)
+            deblur.append((side, psf, b.reshape(1, -1)))
+    ct = []
+    for side in (128, 256):
+        pr = P.ct_parallel(side=side, nrhs=3)
+        dev = [torch.from_numpy(a).cuda() for a in (pr.rowptr, pr.colind, pr.vals)]
+        keep += dev
+        n = side * side
+        op = bd.make_operator("csr", n, n, rowptr=dev[0], colind=dev[1], vals=dev[2], keep=keep)
+        for r in range(pr.nrhs):
+            ct.append((op, pr.b[r:r + 1]))
+    srv = bd.Server(hbm_budget_bytes=64 << 30, max_inflight=64, steps_per_slice=8)
+    rate, duration = 200.0, float(args.serve_seconds)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * duration * 1.2)))
+    arrivals = arrivals[arrivals < duration]
+    plan = []
+    for a in arrivals:
+        k = int(rng.integers(30, 151))
+        lam = float(10 ** rng.uniform(-4, -1))
+        if rng.uniform() < 0.7:
+            side, psf, b = deblur[int(rng.integers(len(deblur)))]
+            op = bd.make_operator("psf2d", side, side, psf=psf, keep=keep)
+            kind = f"deblur{side}"
+        else:
+            op, b = ct[int(rng.integers(len(ct)))]
+            kind = "ct"
+        cfg = bd.default_config(k_max=k, m_s=4 * k, zeta=8, seed=int(rng.integers(1 << 30)), storage="bf16")
+        plan.append((a, op, b, cfg, k, lam, kind))
+    tickets = []
+    t0 = time.perf_counter()
+    for a, op, b, cfg, k, lam, kind in plan:
+        delay = t0 + a - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append((srv.submit(op, b, cfg, k, lam), kind))
+    results = {}
+    while len(results) < len(tickets) and time.perf_counter() - t0 < duration + 120:
+        for t, kind in tickets:
+            if t not in results:
+                out = srv.poll(t, want_x=False)
+                if out is not None:
+                    results[t] = (out, kind)
+        time.sleep(0.001)
+    t_end = time.perf_counter()
+    srv.close()
+    lat = np.array([r[0][2][2] - r[0][2][0] for r in results.values()])
+    ok = sum(1 for r in results.values() if r[0][0] in (0, 1))
+    done_times = np.array([r[0][2][2] for r in results.values()])
+    span = float(done_times.max() - min(r[0][2][0] for r in results.values())) if len(done_times) else 0.0
+    by = {}
+    for (out, kind) in results.values():
+        by.setdefault(kind, []).append(out[2][2] - out[2][0])
+    return {"metric": METRIC, "value": ok / span if span > 0 else 0.0, "unit": "solves/s",
+            "workload": "serving: Poisson 200 req/s, 70% deblur (side U{128,256,512,1024}, Gaussian sigma U(1,4)), "
+                        "30% CT 128^2/256^2; k U{30..150}, m_s=4k, lambda log-U(1e-4,1e-1); BF16; <=64 in flight",
+            "offered_req_per_s": rate, "submitted": len(tickets), "completed_ok": ok,
+            "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
+                           "mean": float(lat.mean() * 1e3)},
+            "latency_ms_by_kind_p50": {k2: float(np.percentile(v, 50) * 1e3) for k2, v in sorted(by.items())},
+            "span_s": span, "wall_s": t_end - t0}
+
+
 def run_small(storage: str):
     """One solve of a small case (1024x1024 Moffat, k=64, m_s=256; the basis
     plus work vector exceed L2) with eager launches: the ncu target."""
@@ -389,11 +471,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--overlap", action="store_true", help="operator on a second stream beside V_j h")
+    ap.add_argument("--workload", default="deblur2048", choices=["deblur2048", "serving"])
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--small", default=None, choices=["f32", "bf16", "f16", "f64"],
                     help="run one small solve (profiling target) and exit")
     args = ap.parse_args()
     if args.small:
         run_small(args.small)
+        return
+    if args.workload == "serving" and args.impl == "ours":
+        print(json.dumps(run_serving(args)), flush=True)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -239,6 +239,60 @@ void ipf_op_destroy(ipf_op* h);
 ipf_status ipf_sketch_apply(const float* x_dev, long long n, int m_s, int zeta,
                             unsigned long long seed, double* y_dev, void* stream);
 
+/* ---- serving: many solves in flight on one GPU ---- */
+
+typedef struct ipf_server ipf_server;
+
+typedef struct ipf_server_config {
+    size_t hbm_budget_bytes;     /* device memory for in-flight requests, reserved at
+                                    creation (0: 80% of the free memory)                  */
+    size_t pinned_bytes;         /* pinned host staging for results (0: 512 MiB)          */
+    int max_inflight;            /* requests on the GPU at once, 1..64                     */
+    int steps_per_slice;         /* Hessenberg steps enqueued per request per turn (0: 8)  */
+} ipf_server_config;
+
+typedef struct ipf_request {
+    ipf_operator op;             /* host arrays are copied at submit; device CSR arrays are
+                                    referenced (kept alive by the caller until polled)    */
+    const float* b;              /* host, nrhs x n, copied at submit                       */
+    ipf_config cfg;              /* k_max, m_s, zeta, seed, storage, penalty, nrhs, ...;
+                                    stream and allocator fields are ignored               */
+    int k;                       /* Hessenberg steps, 1..cfg.k_max                         */
+    double lambda;               /* Tikhonov parameter (0: plain sketched LS)              */
+} ipf_request;
+
+typedef struct ipf_result {
+    int status;                  /* IPF_PENDING, IPF_OK, IPF_BREAKDOWN or an error         */
+    int k_used;
+    double t_submit, t_admit, t_done;   /* host steady-clock seconds                        */
+} ipf_result;
+
+/* Start a serving loop on the current device: a scheduler thread admits
+ * requests when a slot is free and ipf_footprint(request) fits in what is
+ * left of the budget (first come, first served), runs each in its own
+ * context and streams (so in-flight requests overlap on the GPU), tops each
+ * up with steps_per_slice Hessenberg steps whenever its previous slice has
+ * finished, then solves at k with lambda and copies x to the host.  All
+ * device memory comes from one arena reserved here, so admission and
+ * retirement allocate nothing.  Errors: IPF_ERR_ARG, IPF_ERR_OOM (budget
+ * cannot be reserved), IPF_ERR_CUDA.                                     */
+ipf_status ipf_server_create(const ipf_server_config* cfg, ipf_server** out);
+
+/* Queue a request; *ticket identifies it.  IPF_ERR_REJECTED if it can never
+ * fit the budget; IPF_ERR_ARG for malformed requests.  Thread-safe.        */
+ipf_status ipf_submit(ipf_server* s, const ipf_request* rq, unsigned long long* ticket);
+
+/* IPF_PENDING until the request is done; then fills *res, copies x (nrhs x
+ * n float32) to x_out if not NULL, forgets the ticket and returns the
+ * request's status.  Thread-safe.                                         */
+ipf_status ipf_poll(ipf_server* s, unsigned long long ticket, ipf_result* res, float* x_out);
+
+/* In-flight requests, queued requests and the budget they reserve.        */
+ipf_status ipf_server_stats(ipf_server* s, int* inflight, int* queued, size_t* hbm_in_use);
+
+/* Stop the scheduler, finish nothing further, release all memory.        */
+void ipf_server_destroy(ipf_server* s);
+
 /* ipf_sketch_apply without any device allocation.  The paper has no
  * counterpart: this is a service for callers that cannot allocate device
  * memory when they call, e.g. a runtime that owns and caps the GPU's memory

@@ -52,6 +52,21 @@ class ipf_config(C.Structure):
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
 
 
+class ipf_server_config(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("pinned_bytes", C.c_size_t), ("max_inflight", C.c_int),
+                ("steps_per_slice", C.c_int)]
+
+
+class ipf_request(C.Structure):
+    _fields_ = [("op", ipf_operator), ("b", C.c_void_p), ("cfg", ipf_config), ("k", C.c_int),
+                ("lambda_", C.c_double)]
+
+
+class ipf_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("k_used", C.c_int), ("t_submit", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double)]
+
+
 class ipf_solve_info(C.Structure):
     _fields_ = [("k_used", C.c_int), ("k_done", C.c_int), ("status", C.c_int), ("pad", C.c_int)]
 
@@ -80,6 +95,11 @@ SIGNATURES = {
                                    C.c_void_p]),
     "ipf_sketch_apply_noalloc": (C.c_int, [C.c_void_p, C.c_longlong, C.c_int, C.c_int, C.c_ulonglong,
                                            C.c_void_p, C.c_void_p]),
+    "ipf_server_create": (C.c_int, [C.POINTER(ipf_server_config), C.POINTER(C.c_void_p)]),
+    "ipf_submit": (C.c_int, [C.c_void_p, C.POINTER(ipf_request), C.POINTER(C.c_ulonglong)]),
+    "ipf_poll": (C.c_int, [C.c_void_p, C.c_ulonglong, C.POINTER(ipf_result), C.c_void_p]),
+    "ipf_server_stats": (C.c_int, [C.c_void_p, _ip, _ip, C.POINTER(C.c_size_t)]),
+    "ipf_server_destroy": (None, [C.c_void_p]),
 }
 
 _LIB = None
@@ -322,6 +342,62 @@ class Operator:
     def close(self):
         if getattr(self, "h", None):
             self._lib.ipf_op_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """ipf_server: continuous serving of many solves on one GPU."""
+
+    def __init__(self, hbm_budget_bytes: int = 0, max_inflight: int = 64, steps_per_slice: int = 8,
+                 pinned_bytes: int = 0):
+        self._lib = load()
+        cfg = ipf_server_config(hbm_budget_bytes=int(hbm_budget_bytes), pinned_bytes=int(pinned_bytes),
+                                max_inflight=int(max_inflight), steps_per_slice=int(steps_per_slice))
+        h = C.c_void_p()
+        st = self._lib.ipf_server_create(C.byref(cfg), C.byref(h))
+        if st != IPF_OK:
+            raise IpfError(st, "ipf_server_create")
+        self.h = h
+        self._n = {}
+
+    def submit(self, op: ipf_operator, b: np.ndarray, cfg: ipf_config, k: int, lam: float = 0.0) -> int:
+        b = np.ascontiguousarray(b, dtype=np.float32)
+        n = op.cols if op.kind == IPF_OP_CSR else op.rows * op.cols
+        _check_size(b, n * cfg.nrhs, "b")
+        rq = ipf_request(op=op, b=b.ctypes.data, cfg=cfg, k=int(k), lambda_=float(lam))
+        t = C.c_ulonglong(0)
+        st = self._lib.ipf_submit(self.h, C.byref(rq), C.byref(t))
+        if st != IPF_OK:
+            raise IpfError(st, "ipf_submit")
+        self._n[t.value] = (n, cfg.nrhs)
+        return t.value
+
+    def poll(self, ticket: int, want_x: bool = True):
+        """None while pending, else (status, k_used, (t_submit, t_admit, t_done), x or None)."""
+        n, nrhs = self._n[ticket]
+        res = ipf_result()
+        x = np.zeros((nrhs, n), dtype=np.float32) if want_x else None
+        st = self._lib.ipf_poll(self.h, int(ticket), C.byref(res), x.ctypes.data if want_x else None)
+        if st == IPF_PENDING:
+            return None
+        del self._n[ticket]
+        return res.status, res.k_used, (res.t_submit, res.t_admit, res.t_done), x
+
+    def stats(self):
+        a, q = C.c_int(0), C.c_int(0)
+        m = C.c_size_t(0)
+        self._lib.ipf_server_stats(self.h, C.byref(a), C.byref(q), C.byref(m))
+        return a.value, q.value, m.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.ipf_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -1,0 +1,90 @@
+"""Serving (ipf_server_*): requests of different operators and sizes are
+admitted while others run, overlap on the GPU, and each result equals the
+same solve run alone through ipf_create/ipf_step/ipf_solve (the kernels of
+one context do not depend on what else runs, so the bits agree)."""
+import time
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+from _gpu_common import ensure_lib  # noqa: E402
+from gen import problems as P  # noqa: E402
+
+
+def _requests():
+    rng = np.random.default_rng(11)
+    reqs = []
+    for t in range(10):
+        side = int(rng.choice([48, 64, 96]))
+        sigma = float(rng.uniform(1.0, 2.5))
+        psf = P.gaussian_psf(2 * int(np.ceil(3 * sigma)) + 1, sigma)
+        x = P.ellipse_phantom(side, side, 6, rng)
+        b = P.add_noise(P.blur_fft(x, psf), 0.01, rng).astype(np.float32)
+        k = int(rng.integers(5, 25))
+        reqs.append(dict(kind="psf2d", rows=side, cols=side, psf=psf, b=b.reshape(1, -1), k=k, m_s=4 * k,
+                         lam=float(10 ** rng.uniform(-4, -1)), storage=["f32", "bf16"][t % 2], seed=1000 + t))
+    ct = P.ct_parallel(side=32, nrhs=1, k=20, m_s=80)
+    for t in range(4):
+        k = int(rng.integers(8, 20))
+        reqs.append(dict(kind="csr", rows=32, cols=32, rowptr=ct.rowptr, colind=ct.colind, vals=ct.vals,
+                         b=ct.b, k=k, m_s=4 * k, lam=0.0, storage="bf16", seed=2000 + t))
+    return reqs
+
+
+def _op(bd, r, keep):
+    if r["kind"] == "psf2d":
+        return bd.make_operator("psf2d", r["rows"], r["cols"], psf=r["psf"], keep=keep)
+    n = r["rows"] * r["cols"]
+    return bd.make_operator("csr", n, n, rowptr=r["rowptr"], colind=r["colind"], vals=r["vals"], keep=keep)
+
+
+def test_served_results_equal_solves_alone():
+    ensure_lib()
+    from paper_2502_02721_gb300 import binding as bd
+    reqs = _requests()
+    keep = []
+    srv = bd.Server(hbm_budget_bytes=2 << 30, max_inflight=6, steps_per_slice=4)
+    tickets = []
+    for r in reqs:
+        cfg = bd.default_config(k_max=r["k"], m_s=r["m_s"], zeta=8, seed=r["seed"], storage=r["storage"])
+        tickets.append(srv.submit(_op(bd, r, keep), r["b"], cfg, r["k"], r["lam"]))
+    results = {}
+    t0 = time.time()
+    while len(results) < len(tickets) and time.time() - t0 < 120:
+        for t in tickets:
+            if t not in results:
+                out = srv.poll(t)
+                if out is not None:
+                    results[t] = out
+        time.sleep(0.002)
+    srv.close()
+    assert len(results) == len(tickets)
+    # several requests were on the GPU at the same time
+    spans = [(results[t][2][1], results[t][2][2]) for t in tickets]
+    overlapping = sum(1 for i, a in enumerate(spans) for b in spans[i + 1:] if a[0] < b[1] and b[0] < a[1])
+    assert overlapping > 0
+    for r, t in zip(reqs, tickets):
+        status, k_used, _, x = results[t]
+        assert status == bd.IPF_OK and k_used == r["k"]
+        cfg = bd.default_config(k_max=r["k"], m_s=r["m_s"], zeta=8, seed=r["seed"], storage=r["storage"])
+        ctx = bd.Context(_op(bd, r, keep), r["b"], cfg, keep)
+        ctx.step(r["k"])
+        xa, _ = ctx.solve(r["k"], [r["lam"]])
+        ctx.close()
+        assert np.array_equal(x, xa[0]), (r["kind"], r["storage"])
+
+
+def test_server_rejects_what_can_never_fit():
+    ensure_lib()
+    from paper_2502_02721_gb300 import binding as bd
+    srv = bd.Server(hbm_budget_bytes=8 << 20, max_inflight=2)
+    psf = P.gaussian_psf(7, 1.0)
+    keep = []
+    op = bd.make_operator("psf2d", 512, 512, psf=psf, keep=keep)
+    cfg = bd.default_config(k_max=100, m_s=400, storage="f32")
+    with pytest.raises(bd.IpfError) as ei:
+        srv.submit(op, np.ones(512 * 512, np.float32), cfg, 100)
+    assert ei.value.code == bd.IPF_ERR_REJECTED
+    srv.close()
