@@ -35,6 +35,11 @@ WORKLOAD = ("deblur 2048x2048, Moffat 31x31 PSF (beta 2.5, alpha 4), ellipse pha
             "k=200, m_s=800, zeta=8; basis BF16 storage, FP32 accumulate; x = V_k y per solve")
 K_ITERS = 200
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# kernels named in the roofline, from one ncu capture of this workload; to be
+# cleared whenever the kernel changes
+TRAFFIC: dict = {"update": 858.31e6, "conv": 8.42e6}
+
 
 def _peaks():
     try:
@@ -281,19 +286,22 @@ def run_ours(args, rank, world, torch, dist):
             for i in range(9)}
     peak, peak_kind = _peaks()
     upd = kern["update_or_Vh"]
-    roof = {"kernel": "k_gemv<bf16,1> (t = V_j h)", "bound": "hbm",
+    roof = {"kernel": "k_update_f<bf16,1> (w -= V_j h, then the max-|w| pivot)", "bound": "hbm",
             "achieved": upd["GBps"], "peak": peak, "unit": "GB/s",
-            "frac": (upd["GBps"] / peak) if upd["GBps"] else None, "traffic": None,
+            "frac": (upd["GBps"] / peak) if upd["GBps"] else None, "traffic": TRAFFIC.get("update"),
             "peak_source": f"{peak_kind} hbm_gbs", "bytes_per_launch": byts[2] / max(cnt[2], 1),
-            "algorithmic_bytes": "per launch at step j: (j+1)*n*2 (read V_j, BF16) + 4n (write t, FP32)"}
+            "algorithmic_bytes": "per launch at step j: (j+1)*n*2 (read V_j, BF16) + 8n (read and write w, "
+                                 "FP32) + n/8 (pivot bitmap); averaged over j = 1..200"}
     # FP32 FMA peak for the convolution (152 SMs x 128 lanes x 2 flop x clock)
     sm_mhz = clk.get("sm_mhz") or 2070.0
     conv_flops = 2.0 * 961 * n * cnt[0]
     conv_tf = conv_flops / (ms[0] * 1e-3) / 1e12 if ms[0] > 0 else None
     alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    roof_conv = {"kernel": "k_conv2d_c<bf16,31,16> (w = P * v)", "bound": "alu", "achieved": conv_tf,
+    roof_conv = {"kernel": "k_conv2d_c2<bf16,31,16> (w = P * v_j)", "bound": "alu", "achieved": conv_tf,
                  "peak": alu_peak, "unit": "TFLOP/s", "frac": (conv_tf / alu_peak) if conv_tf else None,
-                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock under load"}
+                 "traffic": TRAFFIC.get("conv"),
+                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x median SM clock under load",
+                 "algorithmic_flops": "2 x 31 x 31 x n per launch (n = 2048^2)"}
     dominant = max(range(9), key=lambda i: ms[i])
     launches = int(cnt[0] + cnt[1] + cnt[2] + cnt[3] + 4 * cnt[4] + 2 * cnt[5] + 2 * cnt[6] + cnt[7] + cnt[8])
 
@@ -327,6 +335,10 @@ def run_ours(args, rank, world, torch, dist):
         out["cpu_baseline"] = cpu
     ctx16.close()
     ctx32.close()
+    if rank == 0 and not args.no_extra:
+        out["ct256_batch32"] = run_ct_batch(torch, stream)
+        sv = run_serving(args, duration=5.0)
+        out["serving"] = {k2: v for k2, v in sv.items() if k2 not in ("metric", "unit", "value")}
     return out
 
 
@@ -360,7 +372,47 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-def run_serving(args):
+def run_ct_batch(torch, stream, steps: int = 3) -> dict:
+    """CT 256x256 parallel beam (256 angles x 256 detectors, CSR Siddon
+    weights), 32 right-hand sides in one context, k = 150, m_s = 600: one
+    step = all 32 solves (150 Hessenberg iterations each + x = V_k y)."""
+    from gen import problems as P
+    from paper_2502_02721_gb300 import binding as bd
+    p = P.make("ct256")
+    dev = torch.cuda.current_device()
+    keep = []
+    op = bd.operator_from_problem(p, keep)
+    b_dev = torch.from_numpy(p.b.copy()).to(f"cuda:{dev}")
+    out = {"workload": "CT 256x256, 256 angles x 256 detectors, CSR FP32 (%d nonzeros), 32 RHS batched, "
+                       "k=150, m_s=600" % int(p.rowptr[-1])}
+    for storage in ("f32", "bf16"):
+        cfg = bd.default_config(k_max=p.k, m_s=p.m_s, zeta=p.zeta, seed=p.sketch_seed, storage=storage,
+                                nrhs=p.nrhs, use_graphs=1, stream=stream.cuda_stream)
+        ctx = bd.Context(op, b_dev, cfg, keep)
+        xo = torch.zeros((1, p.nrhs, p.n), dtype=torch.float32, device=f"cuda:{dev}")
+        ctx.reset(b_dev)
+        ctx.step(p.k)
+        ctx.solve(p.k, [0.0], out=xo, wait=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            ctx.reset(b_dev)
+            ctx.step(p.k)
+            ctx.solve(p.k, [0.0], out=xo, wait=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        x = xo[0].double().cpu().numpy()
+        err = float(np.median([np.linalg.norm(x[r] - p.x_true[r]) / np.linalg.norm(p.x_true[r])
+                               for r in range(p.nrhs)]))
+        out[storage] = {"ms_per_batch": ms, "solves_per_s": p.nrhs / (ms * 1e-3),
+                        "iters_per_s": p.nrhs * p.k / (ms * 1e-3), "median_err_vs_xtrue": err}
+        ctx.close()
+    return out
+
+
+def run_serving(args, duration=None):
     """Serving workload: Poisson arrivals (200 req/s) of mixed solves, 70%
     deblurring (side U{128,256,512,1024}, Gaussian sigma U(1,4)), 30% CT
     (128^2 or 256^2 parallel beam), k U{30..150}, m_s = 4k, lambda
@@ -370,7 +422,6 @@ def run_serving(args):
     from paper_2502_02721_gb300 import binding as bd, build as bl
     if not os.path.exists(bl.lib_path()):
         bl.build()
-    torch.cuda.set_device(0)
     rng = np.random.default_rng(2502021 + 4)
     keep = []
     # pools of distinct inputs, made before the timed window
@@ -391,55 +442,68 @@ def run_serving(args):
         op = bd.make_operator("csr", n, n, rowptr=dev[0], colind=dev[1], vals=dev[2], keep=keep)
         for r in range(pr.nrhs):
             ct.append((op, pr.b[r:r + 1]))
-    srv = bd.Server(hbm_budget_bytes=64 << 30, max_inflight=64, steps_per_slice=8)
-    rate, duration = 200.0, float(args.serve_seconds)
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * duration * 1.2)))
+
+    def draw(n_req):
+        plan = []
+        for _ in range(n_req):
+            k = int(rng.integers(30, 151))
+            lam = float(10 ** rng.uniform(-4, -1))
+            if rng.uniform() < 0.7:
+                side, psf, b = deblur[int(rng.integers(len(deblur)))]
+                op = bd.make_operator("psf2d", side, side, psf=psf, keep=keep)
+                kind = f"deblur{side}"
+            else:
+                op, b = ct[int(rng.integers(len(ct)))]
+                kind = "ct"
+            cfg = bd.default_config(k_max=k, m_s=4 * k, zeta=8, seed=int(rng.integers(1 << 30)), storage="bf16")
+            plan.append((op, b, cfg, k, lam, kind))
+        return plan
+
+    def serve(arrivals, plan):
+        srv = bd.Server(hbm_budget_bytes=64 << 30, max_inflight=64, steps_per_slice=8)
+        tickets = []
+        t0 = time.perf_counter()
+        for a, (op, b, cfg, k, lam, kind) in zip(arrivals, plan):
+            delay = t0 + a - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets.append((srv.submit(op, b, cfg, k, lam), kind))
+        results = {}
+        limit = float(arrivals[-1]) + 120.0
+        while len(results) < len(tickets) and time.perf_counter() - t0 < limit:
+            for t, kind in tickets:
+                if t not in results:
+                    out = srv.poll(t, want_x=False)
+                    if out is not None:
+                        results[t] = (out, kind)
+            time.sleep(0.001)
+        srv.close()
+        lat = np.array([r[0][2][2] - r[0][2][0] for r in results.values()])
+        ok = sum(1 for r in results.values() if r[0][0] in (0, 1))
+        t_first = min(r[0][2][0] for r in results.values())
+        span = float(max(r[0][2][2] for r in results.values()) - t_first)
+        by = {}
+        for (out, kind) in results.values():
+            by.setdefault(kind, []).append(out[2][2] - out[2][0])
+        return {"submitted": len(tickets), "completed_ok": ok, "solves_per_s": ok / span if span > 0 else 0.0,
+                "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3),
+                               "p99": float(np.percentile(lat, 99) * 1e3), "mean": float(lat.mean() * 1e3)},
+                "latency_ms_by_kind_p50": {k2: float(np.percentile(v, 50) * 1e3) for k2, v in sorted(by.items())},
+                "span_s": span}
+
+    rate = 200.0
+    duration = float(args.serve_seconds if duration is None else duration)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=int(rate * duration * 1.5) + 10))
     arrivals = arrivals[arrivals < duration]
-    plan = []
-    for a in arrivals:
-        k = int(rng.integers(30, 151))
-        lam = float(10 ** rng.uniform(-4, -1))
-        if rng.uniform() < 0.7:
-            side, psf, b = deblur[int(rng.integers(len(deblur)))]
-            op = bd.make_operator("psf2d", side, side, psf=psf, keep=keep)
-            kind = f"deblur{side}"
-        else:
-            op, b = ct[int(rng.integers(len(ct)))]
-            kind = "ct"
-        cfg = bd.default_config(k_max=k, m_s=4 * k, zeta=8, seed=int(rng.integers(1 << 30)), storage="bf16")
-        plan.append((a, op, b, cfg, k, lam, kind))
-    tickets = []
-    t0 = time.perf_counter()
-    for a, op, b, cfg, k, lam, kind in plan:
-        delay = t0 + a - time.perf_counter()
-        if delay > 0:
-            time.sleep(delay)
-        tickets.append((srv.submit(op, b, cfg, k, lam), kind))
-    results = {}
-    while len(results) < len(tickets) and time.perf_counter() - t0 < duration + 120:
-        for t, kind in tickets:
-            if t not in results:
-                out = srv.poll(t, want_x=False)
-                if out is not None:
-                    results[t] = (out, kind)
-        time.sleep(0.001)
-    t_end = time.perf_counter()
-    srv.close()
-    lat = np.array([r[0][2][2] - r[0][2][0] for r in results.values()])
-    ok = sum(1 for r in results.values() if r[0][0] in (0, 1))
-    done_times = np.array([r[0][2][2] for r in results.values()])
-    span = float(done_times.max() - min(r[0][2][0] for r in results.values())) if len(done_times) else 0.0
-    by = {}
-    for (out, kind) in results.values():
-        by.setdefault(kind, []).append(out[2][2] - out[2][0])
-    return {"metric": METRIC, "value": ok / span if span > 0 else 0.0, "unit": "solves/s",
+    poisson = serve(arrivals, draw(len(arrivals)))
+    # the same mix submitted all at once: what the loop sustains when saturated
+    n_burst = 400
+    burst = serve(np.zeros(n_burst), draw(n_burst))
+    return {"metric": METRIC, "value": poisson["solves_per_s"], "unit": "solves/s",
             "workload": "serving: Poisson 200 req/s, 70% deblur (side U{128,256,512,1024}, Gaussian sigma U(1,4)), "
                         "30% CT 128^2/256^2; k U{30..150}, m_s=4k, lambda log-U(1e-4,1e-1); BF16; <=64 in flight",
-            "offered_req_per_s": rate, "submitted": len(tickets), "completed_ok": ok,
-            "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3), "p99": float(np.percentile(lat, 99) * 1e3),
-                           "mean": float(lat.mean() * 1e3)},
-            "latency_ms_by_kind_p50": {k2: float(np.percentile(v, 50) * 1e3) for k2, v in sorted(by.items())},
-            "span_s": span, "wall_s": t_end - t0}
+            "offered_req_per_s": rate, "duration_s": duration, **{k2: v for k2, v in poisson.items()},
+            "saturated": {"burst_requests": n_burst, **burst}}
 
 
 def run_small(storage: str):
@@ -473,6 +537,8 @@ def main():
     ap.add_argument("--overlap", action="store_true", help="operator on a second stream beside V_j h")
     ap.add_argument("--workload", default="deblur2048", choices=["deblur2048", "serving"])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the CT 32-RHS batch and the 5 s serving run on the default line")
     ap.add_argument("--small", default=None, choices=["f32", "bf16", "f16", "f64"],
                     help="run one small solve (profiling target) and exit")
     args = ap.parse_args()
@@ -480,6 +546,8 @@ def main():
         run_small(args.small)
         return
     if args.workload == "serving" and args.impl == "ours":
+        import torch
+        torch.cuda.set_device(0)
         print(json.dumps(run_serving(args)), flush=True)
         return
     rank = int(os.environ.get("RANK", "0"))
