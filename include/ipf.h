@@ -118,6 +118,9 @@ typedef struct ipf_config {
                                     stream (launches eagerly; read with ipf_profile_read)   */
     int overlap;                 /* PSF2D/CSR with float storage: run the operator on a
                                     second stream beside V_j h (default 0: one stream)      */
+    int conv_fma;                /* PSF2D with BF16 storage: 0 (default) runs the product on
+                                    the tensor cores when the PSF pads to 15x15 or 31x31 and
+                                    cols % 8 == 0; 1 keeps the FP32 FMA convolution         */
     void* stream;                /* cudaStream_t of the caller (NULL: legacy default)      */
     ipf_alloc_fn alloc;          /* optional device allocator (e.g. a framework's pool)    */
     ipf_free_fn free;
@@ -227,6 +230,17 @@ const char* ipf_last_error(const ipf_ctx* ctx);
  * Runs on `stream` (cudaStream_t, may be NULL).                           */
 ipf_status ipf_op_create(const ipf_operator* op, ipf_op** out);
 ipf_status ipf_op_apply(ipf_op* h, const float* v_dev, float* w_dev, int nrhs, void* stream);
+
+/* w = A v for one vector stored in BF16 (v_dev: n BF16 values, device),
+ * accumulated in FP32 (w_dev: m float32, device): the product a Hessenberg
+ * step applies to a BF16 basis vector.  For PSF2D operators whose PSF pads
+ * to 15x15 or 31x31 with cols % 8 == 0 it runs on the tensor cores, with
+ * the PSF carried as the sum of two BF16 parts (about 2^-16 relative), unless
+ * use_fma != 0, which selects the FP32 FMA convolution.  v_dev must be
+ * 16-byte aligned for the tensor-core path.  Runs on `stream`; a stall of
+ * seconds inside the tensor-core kernel (which then gives up) leaves w
+ * unspecified and is not reported by this call.                           */
+ipf_status ipf_op_apply_bf16(ipf_op* h, const void* v_dev, float* w_dev, int use_fma, void* stream);
 void ipf_op_destroy(ipf_op* h);
 
 /* y = S x for the block sparse-sign sketch S (m_s x n, zeta nonzeros

@@ -47,7 +47,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 class ipf_config(C.Structure):
     _fields_ = [("k_max", C.c_int), ("m_s", C.c_int), ("zeta", C.c_int), ("seed", C.c_ulonglong),
                 ("storage", C.c_int), ("penalty", C.c_int), ("zform", C.c_int), ("nrhs", C.c_int),
-                ("use_graphs", C.c_int), ("profile", C.c_int), ("overlap", C.c_int),
+                ("use_graphs", C.c_int), ("profile", C.c_int), ("overlap", C.c_int), ("conv_fma", C.c_int),
                 ("stream", C.c_void_p),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
 
@@ -90,6 +90,7 @@ SIGNATURES = {
     "ipf_last_error": (C.c_char_p, [C.c_void_p]),
     "ipf_op_create": (C.c_int, [C.POINTER(ipf_operator), C.POINTER(C.c_void_p)]),
     "ipf_op_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "ipf_op_apply_bf16": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "ipf_op_destroy": (None, [C.c_void_p]),
     "ipf_sketch_apply": (C.c_int, [C.c_void_p, C.c_longlong, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p,
                                    C.c_void_p]),
@@ -338,6 +339,16 @@ class Operator:
         st = self._lib.ipf_op_apply(self.h, v.data_ptr(), w.data_ptr(), int(nrhs), stream)
         if st != IPF_OK:
             raise IpfError(st, "ipf_op_apply")
+
+    def apply_bf16(self, v, w, use_fma: bool = False, stream=None):
+        """w (float32, m) = A v for v a bfloat16 device tensor of n values."""
+        if str(v.dtype) != "torch.bfloat16" or str(w.dtype) != "torch.float32":
+            raise TypeError("apply_bf16 takes a bfloat16 v and a float32 w")
+        _check_size(v, self.n, "v")
+        _check_size(w, self.m, "w")
+        st = self._lib.ipf_op_apply_bf16(self.h, v.data_ptr(), w.data_ptr(), 1 if use_fma else 0, stream)
+        if st != IPF_OK:
+            raise IpfError(st, "ipf_op_apply_bf16")
 
     def close(self):
         if getattr(self, "h", None):

@@ -18,6 +18,20 @@ namespace {
 
 constexpr int kLamChunk = 16;
 
+// float -> BF16 bits, round to nearest even (finite inputs), and back
+unsigned short bf16_bits_rn(float f) {
+    unsigned u;
+    memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (unsigned short)(u >> 16);
+}
+float bf16_to_float(unsigned short h) {
+    const unsigned u = (unsigned)h << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
 size_t storage_bytes(int storage) {
     switch (storage) {
         case IPF_STORE_F64: return 8;
@@ -160,6 +174,26 @@ cudaError_t upload_op(const ipf_operator* op, Alloc& al, OpDev* d, cudaStream_t 
             if ((e = cudaMemcpy(pp, pairs.data(), pairs.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
             d->kw = kw;
             d->psf_pairs = (const unsigned long long*)pp;
+            if (kw == 15 || kw == 31) {
+                // [F_hi ; F_lo] for the tensor-core convolution: 2KP rows (a, then a
+                // again for the remainder) x KP columns (b), BF16, stored as K-major
+                // 8x8 core matrices: byte (b/8)*(2KP*16) + row*16 + (b%8)*2
+                const int KP = kw + 1, NR2 = 2 * KP;
+                std::vector<unsigned short> img((size_t)NR2 * KP, 0);
+                for (int row = 0; row < NR2; ++row)
+                    for (int bb = 0; bb < KP; ++bb) {
+                        const int a = row < KP ? row : row - KP;
+                        const float f = (a < kw && bb < kw) ? F(a, bb) : 0.f;
+                        const unsigned short hi = bf16_bits_rn(f);
+                        const unsigned short val = row < KP ? hi : bf16_bits_rn(f - bf16_to_float(hi));
+                        img[(size_t)(bb / 8) * NR2 * 8 + (size_t)row * 8 + (bb % 8)] = val;
+                    }
+                void* pt = nullptr;
+                if ((e = al.get(&pt, img.size() * 2)) != cudaSuccess) return e;
+                if ((e = cudaMemcpy(pt, img.data(), img.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+                d->tc_kp = KP;
+                d->psf_tc = pt;
+            }
         }
     } else if (op->kind == IPF_OP_PSF2D_SEP_MOTION) {
         d->slen = op->slen; d->mlen = op->mlen;
@@ -318,7 +352,8 @@ cudaError_t one_step(ipf_ctx* c, int j) {
         if ((e = cudaEventRecord(c->ev_fork, c->s)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(c->s2, c->ev_fork, 0)) != cudaSuccess) return e;
         if ((e = timed_on(c, c->s2, 0, op_bytes(c), [&] {
-                 return launch_op_apply(c->op, c->storage, c->bf.V, c->g.ldv, &c->bf.st->j, c->B, c->bf.w, c->s2);
+                 return launch_op_apply(c->op, c->storage, c->bf.V, c->g.ldv, c->g.k_max + 1, &c->bf.st->j, c->B,
+                                        c->bf.w, c->bf.st->status, c->s2);
              })) != cudaSuccess)
             return e;
         if ((e = cudaEventRecord(c->ev_join, c->s2)) != cudaSuccess) return e;
@@ -333,7 +368,8 @@ cudaError_t one_step(ipf_ctx* c, int j) {
                      [&] { return launch_normalize(c->storage, c->g, c->bf, c->sp, sw_on(c), c->num_sms, c->s); });
     }
     if ((e = timed(c, 0, op_bytes(c), [&] {
-             return launch_op_apply(c->op, c->storage, c->bf.V, c->g.ldv, &c->bf.st->j, c->B, c->bf.w, c->s);
+             return launch_op_apply(c->op, c->storage, c->bf.V, c->g.ldv, c->g.k_max + 1, &c->bf.st->j, c->B, c->bf.w,
+                                    c->bf.st->status, c->s);
          })) != cudaSuccess)
         return e;
     if ((e = timed(c, 1, 0.0, [&] { return launch_pivot_solve(c->storage, c->g, c->bf, c->s); })) != cudaSuccess)
@@ -403,7 +439,7 @@ size_t ipf_footprint(const ipf_operator* op, const ipf_config* cfg) {
     if (op->kind == IPF_OP_CSR && op->mem == IPF_MEM_HOST)
         bytes += (size_t)(op->rows + 1) * 8 + (size_t)op->nnz * 8;
     else if (op->kind == IPF_OP_PSF2D)
-        bytes += (size_t)op->ph * op->pw * 4;
+        bytes += (size_t)op->ph * op->pw * 4 + 32 * 33 * 8 + 64 * 32 * 2;   // PSF, packed pairs, tensor-core operand
     return bytes;
 }
 
@@ -465,6 +501,7 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     c->split = cfg.overlap && (op->kind == IPF_OP_PSF2D || op->kind == IPF_OP_CSR) && cfg.storage != IPF_STORE_F64;
     CK("order", enter(c));
     CK("operator upload", upload_op(op, c->al, &c->op, c->s));
+    c->op.conv_fma = cfg.conv_fma ? 1 : 0;
 
     Geom& g = c->g;
     g.n = n;
@@ -862,6 +899,15 @@ ipf_status ipf_op_apply(ipf_op* h, const float* v_dev, float* w_dev, int nrhs, v
     if (!h || !v_dev || !w_dev || nrhs < 1) return IPF_ERR_ARG;
     if (h->op.kind == IPF_OP_CSR && !pow2_le32(nrhs)) return IPF_ERR_ARG;
     cudaError_t e = launch_op_apply_f32_plain(h->op, v_dev, w_dev, nrhs, (cudaStream_t)stream);
+    return e == cudaSuccess ? IPF_OK : IPF_ERR_CUDA;
+}
+
+ipf_status ipf_op_apply_bf16(ipf_op* h, const void* v_dev, float* w_dev, int use_fma, void* stream) {
+    if (!h || !v_dev || !w_dev) return IPF_ERR_ARG;
+    OpDev op = h->op;
+    op.conv_fma = use_fma ? 1 : 0;
+    cudaError_t e =
+        launch_op_apply(op, IPF_STORE_BF16, v_dev, 0, 1, nullptr, 1, w_dev, nullptr, (cudaStream_t)stream);
     return e == cudaSuccess ? IPF_OK : IPF_ERR_CUDA;
 }
 

@@ -252,6 +252,9 @@ struct OpDev {
     long long nnz;
     int kw;                        // PSF2D: padded square width (7, 15, 31) of psf_pairs, else 0
     const unsigned long long* psf_pairs;   // [kw][kw+1] packed {F[ky][b], F[ky-1][b]}, F flipped + padded
+    int tc_kp;                     // PSF2D, kw 15 or 31: KP = kw + 1 of the tensor-core operand, else 0
+    const void* psf_tc;            // [F_hi ; F_lo] BF16, 2KP x KP, K-major core-matrix layout
+    int conv_fma;                  // 1: keep the FP32 FMA convolution for BF16 storage
 };
 
 // ---------------------------------------------------------------------------
@@ -259,8 +262,16 @@ struct OpDev {
 // ---------------------------------------------------------------------------
 // k_ops.cu
 // vbase + (*jptr) * ldv is the input vector (jptr NULL: vbase itself)
-cudaError_t launch_op_apply(const OpDev& op, int storage, const void* vbase, long long ldv, const int* jptr, int B,
-                            void* w, cudaStream_t s);
+// tensor-core convolution for BF16 storage (k_conv_tc.cu)
+bool conv_tc_eligible(const OpDev& op, const void* vbase, long long ldv);
+cudaError_t launch_conv_tc(const OpDev& op, const void* vbase, long long ldv, long long vcols, const int* jptr,
+                           float* w, int* err, cudaStream_t s);
+
+// w = A v_j: vbase/ldv/vcols describe the basis (vcols columns), j read from
+// jptr (column 0 when NULL); err receives IPF_ERR_TIMEOUT if a bounded wait
+// inside the tensor-core convolution gives up (may be NULL)
+cudaError_t launch_op_apply(const OpDev& op, int storage, const void* vbase, long long ldv, long long vcols,
+                            const int* jptr, int B, void* w, int* err, cudaStream_t s);
 // (A v_j)(p_i) for i <= j directly at the pivot rows (PSF2D and CSR); float accumulation
 cudaError_t launch_pivot_rows(const OpDev& op, int storage, const void* vbase, long long ldv, const DevState* st,
                               const int* piv, int B, int k_max, float* gout, cudaStream_t s);

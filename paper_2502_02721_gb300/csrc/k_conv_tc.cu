@@ -1,0 +1,415 @@
+// Zero-boundary 2-D convolution w = P * v on the 5th-generation tensor cores
+// (tcgen05) for basis vectors stored in BF16, FP32 accumulation.
+//
+// With F the flipped PSF padded to KW x KW (KW = 15 or 31, c = KW/2),
+//     w[y, x] = sum_{a,b} F[a][b] v[y - c + a, x - c + b].
+// For one image row iy and 128 output columns x0..x0+127 the products
+//     D_iy[x, a] = sum_b v[iy, x0 + x - c + b] F[a][b]
+// form a dense 128 x KP x KP contraction (KP = KW + 1, b and a zero-padded),
+// and output row y collects D_iy[:, a] from the KW image rows iy = y - c + a.
+// So each image row costs one MMA of M = 128, K = KP, N = 2 KP, and the
+// row sums (an overlap-add over a) run on the CUDA cores.
+//
+// Operands, both K-major without swizzle in shared memory:
+//   A  the Hankel matrix H[x, b] = v[iy, x0 - c + x + b].  A K-major core
+//      matrix (8 rows x 8 elements) of it depends only on (x/8 + b/8), so
+//      NQ = 16 + KP/8 - 1 blocks of 128 bytes hold it, block q row s =
+//      v[iy, x0 - c + 8q + s .. +7]; the descriptor uses 128 bytes for both
+//      the K and the M core-matrix strides.  Built from a staged row
+//      segment by two builder warps.
+//   B  [F_hi ; F_lo]: F rounded to BF16, and the BF16 rounding of the
+//      remainder, rows a (N = 2 KP), so hi + lo carries F to about 2^-16
+//      relative; the two halves land in separate TMEM columns and are added
+//      in FP32.  Built once on the host in this layout.
+// Image rows arrive by TMA (3-D map over the basis: x, y, basis column j, j
+// read from device memory), 8 rows of 160 elements per box starting at
+// x0 - 16 (a multiple of 8 elements), zero-filled outside the image.
+//
+// Warp roles (256 threads, one CTA per SM): warp 0 issues the TMA loads,
+// warp 1 owns TMEM and one lane issues the MMAs, warps 2-3 build A, warps
+// 4-7 read the accumulators (warp w reads TMEM lanes 32 (w % 4) ..) and
+// do the overlap-add with the KW running output rows in registers.  Every
+// wait is bounded in time; on a timeout the CTA stops issuing, drains its
+// copies and MMAs, frees TMEM and reports IPF_ERR_TIMEOUT.
+#include <cuda.h>
+
+#include <mutex>
+
+#include "ipf_internal.cuh"
+
+namespace ipf {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kSegW = 160;           // elements per staged row segment
+constexpr int kRB = 8;               // image rows per TMA box
+constexpr int kNSeg = 8;             // boxes in flight
+constexpr int kNH = 16;              // A operands (image rows) in flight
+constexpr int kND = 8;               // TMEM accumulator buffers
+constexpr int kHankBytes = 2560;     // up to 20 blocks of 128 bytes
+constexpr int kTmemCols = 512;
+constexpr int kSegBytes = kRB * kSegW * 2;
+constexpr int kOffB = 0;
+constexpr int kOffSeg = 4096;
+constexpr int kOffHank = kOffSeg + kNSeg * kSegBytes;          // 24576
+constexpr int kOffBar = kOffHank + kNH * kHankBytes;           // 65536
+constexpr int kNBar = 2 * kNSeg + 2 * kNH + 2 * kND + 1;
+constexpr int kOffMisc = kOffBar + 8 * kNBar;
+constexpr int kSmemUsed = kOffMisc + 16;
+// more than half of the SM's shared memory: one CTA per SM, so the 512
+// TMEM columns it allocates are never contended by a sibling CTA
+constexpr int kSmemRequest = 116 * 1024;
+static_assert(kSmemUsed + 1024 <= kSmemRequest, "shared memory layout");
+constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of `parity` to complete.  Gives up when another role
+// has aborted (if `honour_abort`) or after kWaitNs, which aborts the CTA and
+// records IPF_ERR_TIMEOUT.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, int* err, bool honour_abort = true) {
+    const unsigned long long t0 = globaltimer();
+    for (unsigned it = 1;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 255u) == 0) {
+            if (honour_abort && *abort) return false;
+            if (globaltimer() - t0 > kWaitNs) {
+                *abort = 1;
+                if (err) *(volatile int*)err = IPF_ERR_TIMEOUT;
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// shared-memory matrix descriptor: no swizzle, K-major; lbo = byte stride
+// between core matrices along K, sbo = along M/N
+__device__ __forceinline__ unsigned long long smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    unsigned long long d = 0;
+    d |= (unsigned long long)((addr & 0x3FFFFu) >> 4);
+    d |= (unsigned long long)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (unsigned long long)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= 1ull << 46;                                  // descriptor version for tcgen05
+    return d;                                         // base offset 0, layout type 0 (no swizzle)
+}
+
+// instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, unsigned long long a, unsigned long long b, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{ .reg .pred p; setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 32 consecutive TMEM columns of this warp's 32 lanes, one lane per thread
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+template <int KP>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_conv2d_tc(const __grid_constant__ CUtensorMap vmap, const int* __restrict__ jptr, float* __restrict__ w,
+                int H, int W, int R, int CT, const uint4* __restrict__ bimg, int* __restrict__ err) {
+    constexpr int KW = KP - 1;
+    constexpr int C = KW / 2;
+    constexpr int N = 2 * KP;                  // MMA N: hi rows then lo rows
+    constexpr int NQ = 16 + KP / 8 - 1;        // A blocks per image row
+    constexpr int OFF = 16 - C;                // segment index of v[iy, x0 - c]
+    constexpr int BBYTES = N * KP * 2;
+    constexpr uint32_t IDESC = idesc_bf16(128, N);
+    static_assert(KP == 16 || KP == 32, "KP");
+    static_assert(OFF + 8 * (NQ - 1) + 7 + 7 < kSegW, "segment width");
+    static_assert(NQ * 128 <= kHankBytes && BBYTES <= kOffSeg, "operand sizes");
+    static_assert(kND * N <= kTmemCols, "TMEM columns");
+
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm);
+    const uint32_t bar0 = sbase + kOffBar;
+    auto seg_full = [&](int i) { return bar0 + 8u * i; };
+    auto seg_empty = [&](int i) { return bar0 + 8u * (kNSeg + i); };
+    auto h_full = [&](int i) { return bar0 + 8u * (2 * kNSeg + i); };
+    auto h_empty = [&](int i) { return bar0 + 8u * (2 * kNSeg + kNH + i); };
+    auto d_full = [&](int i) { return bar0 + 8u * (2 * kNSeg + 2 * kNH + i); };
+    auto d_empty = [&](int i) { return bar0 + 8u * (2 * kNSeg + 2 * kNH + kND + i); };
+    const uint32_t done_bar = bar0 + 8u * (kNBar - 1);
+    uint32_t* s_tmem = (uint32_t*)(sm + kOffMisc);
+    volatile int* s_abort = (volatile int*)(sm + kOffMisc + 4);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ct = blockIdx.x % CT, sg = blockIdx.x / CT;
+    const int x0 = ct * 128, Y0 = sg * R;
+    if (Y0 >= H) return;                                  // uniform for the CTA
+    const int yEnd = min(Y0 + R, H);
+    const int NR = (yEnd - Y0) + 2 * C;                   // image rows Y0 - c .. yEnd - 1 + c
+    const int Ys = Y0 - C;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kNSeg; ++i) { mbar_init(seg_full(i), 1); mbar_init(seg_empty(i), 64); }
+        for (int i = 0; i < kNH; ++i) { mbar_init(h_full(i), 64); mbar_init(h_empty(i), 1); }
+        for (int i = 0; i < kND; ++i) { mbar_init(d_full(i), 1); mbar_init(d_empty(i), 128); }
+        mbar_init(done_bar, 1);
+        *s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int i = threadIdx.x; i < BBYTES / 16; i += kThreads) ((uint4*)(sm + kOffB))[i] = bimg[i];
+    fence_proxy_async_smem();
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(s_tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *s_tmem;
+
+    if (warp == 0) {
+        // ---- TMA producer ----
+        if (lane == 0) {
+            const int z = jptr ? *jptr : 0;
+            const int nch = (NR + kRB - 1) / kRB;
+            int issued = 0;
+            for (int t = 0; t < nch; ++t) {
+                const int sl = t % kNSeg;
+                if (!mbar_wait(seg_empty(sl), ((t / kNSeg) & 1) ^ 1, s_abort, err)) break;
+                mbar_expect_tx(seg_full(sl), kSegBytes);
+                tma_load_3d(sbase + kOffSeg + sl * kSegBytes, &vmap, x0 - 16, Ys + t * kRB, z, seg_full(sl));
+                issued = t + 1;
+            }
+            // every issued copy lands before the CTA may exit
+            for (int t = issued > kNSeg ? issued - kNSeg : 0; t < issued; ++t)
+                mbar_wait(seg_full(t % kNSeg), (t / kNSeg) & 1, s_abort, err, false);
+        }
+    } else if (warp == 1) {
+        // ---- MMA issuer ----
+        if (lane == 0) {
+            for (int i = 0; i < NR; ++i) {
+                if (*s_abort) break;
+                const int hs = i % kNH, ds = i % kND;
+                if (!mbar_wait(h_full(hs), (i / kNH) & 1, s_abort, err)) break;
+                if (!mbar_wait(d_empty(ds), ((i / kND) & 1) ^ 1, s_abort, err)) break;
+                tc_fence_after();
+                const uint32_t a0 = sbase + kOffHank + hs * kHankBytes;
+#pragma unroll
+                for (int kk = 0; kk < KP / 16; ++kk)
+                    mma_bf16(tmem + (uint32_t)(ds * N), smem_desc(a0 + kk * 256, 128, 128),
+                             smem_desc(sbase + kOffB + kk * 2 * N * 16, N * 16, 128), IDESC, kk > 0 ? 1u : 0u);
+                mma_commit(d_full(ds));
+                mma_commit(h_empty(hs));
+            }
+            // all MMAs issued by this thread complete before TMEM is freed
+            mma_commit(done_bar);
+            mbar_wait(done_bar, 0, s_abort, err, false);
+        }
+    } else if (warp < 4) {
+        // ---- A builders: Hankel blocks from the staged row ----
+        const int bt = threadIdx.x - 64;
+        for (int i = 0; i < NR; ++i) {
+            if (*s_abort) break;
+            const int t = i / kRB, r = i - t * kRB, sl = t % kNSeg;
+            if (r == 0 && !mbar_wait(seg_full(sl), (t / kNSeg) & 1, s_abort, err)) break;
+            const int hs = i % kNH;
+            if (!mbar_wait(h_empty(hs), ((i / kNH) & 1) ^ 1, s_abort, err)) break;
+            const uint32_t* src = (const uint32_t*)(sm + kOffSeg + sl * kSegBytes + r * kSegW * 2);
+            unsigned char* dst = sm + kOffHank + hs * kHankBytes;
+            for (int row = bt; row < NQ * 8; row += 64) {
+                const int q = row >> 3, s = row & 7;
+                const int e0 = OFF + 8 * q + s;               // first element of this 16-byte row
+                const int wb = e0 >> 1;
+                const uint32_t sel = (e0 & 1) ? 0x5432u : 0x3210u;
+                const uint32_t w0 = src[wb], w1 = src[wb + 1], w2 = src[wb + 2], w3 = src[wb + 3];
+                const uint32_t w4 = (e0 & 1) ? src[wb + 4] : 0u;
+                uint4 o;
+                o.x = __byte_perm(w0, w1, sel);
+                o.y = __byte_perm(w1, w2, sel);
+                o.z = __byte_perm(w2, w3, sel);
+                o.w = __byte_perm(w3, w4, sel);
+                *(uint4*)(dst + q * 128 + s * 16) = o;
+            }
+            fence_proxy_async_smem();
+            mbar_arrive(h_full(hs));
+            if (r == kRB - 1 || i == NR - 1) mbar_arrive(seg_empty(sl));
+        }
+    } else {
+        // ---- epilogue: overlap-add of the KW accumulator columns ----
+        const int q = warp & 3;
+        const int x = x0 + q * 32 + lane;
+        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+        float acc[KW];
+#pragma unroll
+        for (int t = 0; t < KW; ++t) acc[t] = 0.f;
+        bool live = true;
+        for (int i0 = 0; i0 < NR && live; i0 += KW) {
+#pragma unroll
+            for (int u = 0; u < KW; ++u) {
+                const int i = i0 + u;
+                if (live && i < NR) {
+                    const int ds = i % kND;
+                    const bool ok = mbar_wait(d_full(ds), (i / kND) & 1, s_abort, err);
+                    live = __all_sync(0xffffffffu, ok);
+                    if (live) {
+                        tc_fence_after();
+                        uint32_t hv[32], lv[32];
+                        if (KP == 32) {
+                            tmem_ld32(tl + (uint32_t)(ds * N), hv);
+                            tmem_ld32(tl + (uint32_t)(ds * N + KP), lv);
+                        } else {
+                            tmem_ld32(tl + (uint32_t)(ds * N), hv);     // hi 0..15, lo 16..31
+                        }
+                        tmem_wait_ld();
+                        tc_fence_before();
+                        mbar_arrive(d_empty(ds));
+#pragma unroll
+                        for (int t = 0; t < KW; ++t) {
+                            const int a = KW - 1 - t;
+                            const float hi = __uint_as_float(hv[a]);
+                            const float lo = __uint_as_float(KP == 32 ? lv[a] : hv[KP + a]);
+                            acc[(t + u) % KW] += hi + lo;
+                        }
+                        const int y = Y0 + i - 2 * C;
+                        if (i >= 2 * C && y < yEnd && x < W) w[(size_t)y * W + x] = acc[u];
+                        acc[u] = 0.f;
+                    }
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+template <int KP>
+cudaError_t launch_kp(const CUtensorMap& map, const int* jptr, float* w, int H, int W, const void* bimg, int* err,
+                      cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(k_conv2d_tc<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemRequest);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 1;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int CT = (W + 127) / 128;
+    int S = sms / CT;
+    const int smax = (H + 31) / 32;                       // at least 32 output rows per CTA
+    if (S > smax) S = smax;
+    if (S < 1) S = 1;
+    const int R = (H + S - 1) / S;
+    const int units = CT * ((H + R - 1) / R);
+    k_conv2d_tc<KP><<<units, kThreads, kSmemRequest, s>>>(map, jptr, w, H, W, R, CT, (const uint4*)bimg, err);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool conv_tc_eligible(const OpDev& op, const void* vbase, long long ldv) {
+    if (op.kind != IPF_OP_PSF2D || !op.psf_tc || op.conv_fma) return false;
+    if (op.cols % 8 != 0 || ((uintptr_t)vbase & 15u) != 0 || (ldv * 2) % 16 != 0) return false;
+    return encode_fn() != nullptr;
+}
+
+cudaError_t launch_conv_tc(const OpDev& op, const void* vbase, long long ldv, long long vcols, const int* jptr,
+                           float* w, int* err, cudaStream_t s) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    const int H = op.rows, W = op.cols;
+    const long long colstride = ldv > 0 ? ldv : (long long)H * W;
+    CUtensorMap map;
+    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)(vcols > 0 ? vcols : 1)};
+    const cuuint64_t strides[2] = {(cuuint64_t)W * 2, (cuuint64_t)colstride * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)kSegW, (cuuint32_t)kRB, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(vbase), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    if (op.tc_kp == 32) return launch_kp<32>(map, jptr, w, H, W, op.psf_tc, err, s);
+    if (op.tc_kp == 16) return launch_kp<16>(map, jptr, w, H, W, op.psf_tc, err, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace ipf

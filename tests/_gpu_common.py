@@ -22,7 +22,7 @@ def ensure_lib():
     return binding.load()
 
 
-def gpu_context(p, storage, k=None, m_s=None, zform=None, penalty=None, graphs=1, nrhs=None, b=None):
+def gpu_context(p, storage, k=None, m_s=None, zform=None, penalty=None, graphs=1, nrhs=None, b=None, **extra):
     from paper_2502_02721_gb300 import binding as bd
     keep = []
     op = bd.operator_from_problem(p, keep)
@@ -32,6 +32,7 @@ def gpu_context(p, storage, k=None, m_s=None, zform=None, penalty=None, graphs=1
         kw["zform"] = zform
     if penalty is not None:
         kw["penalty"] = penalty
+    kw.update(extra)
     cfg = bd.default_config(**kw)
     return bd.Context(op, p.b if b is None else b, cfg, keep)
 

@@ -88,6 +88,82 @@ def test_psf_conv_matches_oracle(torch, H, W, K):
     assert np.max(np.abs(got - want)) <= 2e-6 * scale
 
 
+# The BF16 product w = P * v for a BF16 vector v.  On the tensor cores each
+# PSF tap F is carried as hi + lo, two BF16 numbers: hi is F rounded to 8
+# significant bits and lo the remainder rounded to 8 more, so
+# |F - hi - lo| <= 2^-17 |F|.  Each output sums, in FP32, at most 2*32
+# products inside one MMA and then 2*KW partial sums in the epilogue: even with
+# truncating adds that is <= (64 + 62) 2^-23 of the sum of |terms|.  Hence
+# |w - w_exact| <= (2^-17 + 126 2^-23) (|F| * |v|) elementwise.  The FP32 FMA
+# path (kept for other sizes, and selectable) is bounded by KW^2 2^-24 (|F|*|v|).
+TC_REL = 2.0 ** -17 + 126 * 2.0 ** -23
+
+
+def _psf(name, rng):
+    return {"gauss15": P.gaussian_psf(15, 2.0), "moffat31": P.moffat_psf(31, 2.5, 4.0),
+            "gauss11": P.gaussian_psf(11, 1.5),
+            "rand31": rng.standard_normal((31, 31)).astype(np.float32),
+            "rand9x13": rng.standard_normal((9, 13)).astype(np.float32)}[name]
+
+
+def _oracle_windows(v, psf, wins, size):
+    """Exact FP64 products on size x size windows at (Y, X): the oracle runs on
+    the window plus a halo of the PSF radius cut from the zero-padded image."""
+    H, W = v.shape
+    cy, cx = psf.shape[0] // 2, psf.shape[1] // 2
+    vp = np.zeros((H + 2 * cy + size, W + 2 * cx + size))
+    vp[cy:cy + H, cx:cx + W] = v
+    out = []
+    for (Y, X) in wins:
+        crop = vp[Y:Y + size + 2 * cy, X:X + size + 2 * cx]
+        full = ops.conv2d_zero(crop, psf)
+        out.append(full[cy:cy + size, cx:cx + size][:H - Y, :W - X])
+    return out
+
+
+@pytest.mark.parametrize("H,W,K", [(64, 64, "gauss15"), (200, 136, "moffat31"), (257, 264, "rand31"),
+                                   (33, 1032, "gauss11"), (96, 104, "rand9x13"), (300, 130, "moffat31"),
+                                   (2048, 2048, "moffat31")])
+def test_psf_conv_bf16_matches_oracle(torch, H, W, K):
+    """Tensor-core product (PSF padding to 15x15 or 31x31, W % 8 == 0) and the
+    FP32 FMA product against the FP64 oracle on the same BF16 vector; W = 130
+    is not a multiple of 8 and takes the FMA kernel on both calls."""
+    from paper_2502_02721_gb300 import binding as bd
+    rng = np.random.default_rng(H * 7 + W)
+    psf = _psf(K, rng)
+    vb = torch.from_numpy(rng.standard_normal(H * W).astype(np.float32)).cuda().to(torch.bfloat16)
+    v = vb.float().cpu().numpy().astype(np.float64).reshape(H, W)
+    keep = []
+    op = bd.Operator(bd.make_operator("psf2d", H, W, psf=psf, keep=keep), keep)
+    got = {}
+    for fma in (False, True):
+        wd = torch.full((H * W,), float("nan"), dtype=torch.float32, device="cuda")
+        op.apply_bf16(vb, wd, use_fma=fma)
+        torch.cuda.synchronize()
+        got[fma] = wd.cpu().numpy().astype(np.float64).reshape(H, W)
+    op.close()
+    kw = max(psf.shape)
+    if H * W <= 300 * 300:
+        want = ops.conv2d_zero(v, psf)
+        mag = ops.conv2d_zero(np.abs(v), np.abs(psf))
+        cmp = [(got[False], want, mag), (got[True], want, mag)]
+    else:
+        # full size: the corners, the image edges and random interior windows
+        S = 64
+        wins = [(0, 0), (0, W - S), (H - S, 0), (H - S, W - S), (H // 2, 0), (0, W // 2)]
+        wins += [(int(rng.integers(0, H - S)), int(rng.integers(0, W - S))) for _ in range(10)]
+        want = _oracle_windows(v, psf, wins, S)
+        mag = _oracle_windows(np.abs(v), np.abs(psf), wins, S)
+        cmp = []
+        for fma in (False, True):
+            g = np.concatenate([got[fma][Y:Y + S, X:X + S].ravel() for (Y, X) in wins])
+            cmp.append((g, np.concatenate([a.ravel() for a in want]), np.concatenate([a.ravel() for a in mag])))
+    for (g, wnt, mg), rel_bound in zip(cmp, (TC_REL, kw * kw * 2.0 ** -24)):
+        assert np.all(np.isfinite(g))
+        err = np.abs(g - wnt)
+        assert np.all(err <= rel_bound * mg + 1e-30), (np.max(err / (mg + 1e-30)), rel_bound)
+
+
 @pytest.mark.parametrize("H,W", [(256, 256), (100, 130), (37, 300)])
 def test_sep_motion_matches_oracle(torch, H, W):
     rng = np.random.default_rng(H + W)

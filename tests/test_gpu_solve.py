@@ -55,10 +55,12 @@ def test_deblur64_parity(deblur64, storage):
     ctx.close()
 
 
-@pytest.mark.parametrize("storage", ["bf16", "f16"])
-def test_deblur64_low_precision(deblur64, storage):
+@pytest.mark.parametrize("storage,conv_fma", [("bf16", 0), ("bf16", 1), ("f16", 0)])
+def test_deblur64_low_precision(deblur64, storage, conv_fma):
+    """BF16 runs the 15x15 product on the tensor cores (conv_fma 0) and on
+    the FP32 FMA path (conv_fma 1); both must meet the same bounds."""
     p, st = deblur64
-    ctx = gpu_context(p, storage)
+    ctx = gpu_context(p, storage, conv_fma=conv_fma)
     ctx.step(p.k)
     status, kd = ctx.sync()
     ex = ctx.export(0)
