@@ -7,8 +7,9 @@
 //     D_iy[x, a] = sum_b v[iy, x0 + x - c + b] F[a][b]
 // form a dense 128 x KP x KP contraction (KP = KW + 1, b and a zero-padded),
 // and output row y collects D_iy[:, a] from the KW image rows iy = y - c + a.
-// So each image row costs one MMA of M = 128, K = KP, N = 2 KP, and the
-// row sums (an overlap-add over a) run on the CUDA cores.
+// So each image row costs a 128 x KP x KP product (two MMAs per 16-wide K
+// slice, one per PSF part, into the same accumulator), and the row sums (an
+// overlap-add over a) run on the CUDA cores.
 //
 // Operands, both K-major without swizzle in shared memory:
 //   A  the Hankel matrix H[x, b] = v[iy, x0 - c + x + b].  A K-major core
@@ -18,17 +19,21 @@
 //      the K and the M core-matrix strides.  Built from a staged row
 //      segment by two builder warps.
 //   B  [F_hi ; F_lo]: F rounded to BF16, and the BF16 rounding of the
-//      remainder, rows a (N = 2 KP), so hi + lo carries F to about 2^-16
-//      relative; the two halves land in separate TMEM columns and are added
-//      in FP32.  Built once on the host in this layout.
+//      remainder, rows a, so hi + lo carries F to about 2^-16 relative; the
+//      MMA adds both products into the same FP32 accumulator.  Built once on
+//      the host in this layout (2 KP rows, K-chunk stride 2 KP x 16 bytes).
 // Image rows arrive by TMA (3-D map over the basis: x, y, basis column j, j
 // read from device memory), 8 rows of 160 elements per box starting at
 // x0 - 16 (a multiple of 8 elements), zero-filled outside the image.
 //
-// Warp roles (256 threads, one CTA per SM): warp 0 issues the TMA loads,
-// warp 1 owns TMEM and one lane issues the MMAs, warps 2-3 build A, warps
-// 4-7 read the accumulators (warp w reads TMEM lanes 32 (w % 4) ..) and
-// do the overlap-add with the KW running output rows in registers.  Every
+// Warp roles (384 threads, one CTA per SM): warp 0 issues the TMA loads,
+// warp 1 owns TMEM; one lane each of warps 1-3 issues the MMAs of every
+// third image row (a single issuing thread is bound by the ~60-cycle issue
+// cost of each tcgen05 instruction and barrier test); warps 8-11 build A
+// (each a whole image row, rows dealt round robin); warps 4-7 read the
+// accumulators (warp w reads TMEM lanes 32 (w % 4) ..), one row ahead of
+// the overlap-add they do with the KW running output rows in registers
+// (a shift register).  Every
 // wait is bounded in time; on a timeout the CTA stops issuing, drains its
 // copies and MMAs, frees TMEM and reports IPF_ERR_TIMEOUT.
 #include <cuda.h>
@@ -41,12 +46,14 @@ namespace ipf {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 384;
+constexpr int kBuilders = 4;         // builder warps: 8 .. 11
+constexpr int kIssuers = 3;          // MMA-issuing warps: 1 .. 3
 constexpr int kSegW = 160;           // elements per staged row segment
 constexpr int kRB = 8;               // image rows per TMA box
 constexpr int kNSeg = 8;             // boxes in flight
 constexpr int kNH = 16;              // A operands (image rows) in flight
-constexpr int kND = 8;               // TMEM accumulator buffers
+constexpr int kND = 16;              // TMEM accumulator buffers (KP columns each)
 constexpr int kHankBytes = 2560;     // up to 20 blocks of 128 bytes
 constexpr int kTmemCols = 512;
 constexpr int kSegBytes = kRB * kSegW * 2;
@@ -91,7 +98,18 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 // Wait for the phase of `parity` to complete.  Gives up when another role
 // has aborted (if `honour_abort`) or after kWaitNs, which aborts the CTA and
 // records IPF_ERR_TIMEOUT.
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, int* err, bool honour_abort = true) {
+    if (mbar_test(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     for (unsigned it = 1;; ++it) {
         if (mbar_try(bar, parity)) return true;
@@ -155,6 +173,14 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
@@ -171,10 +197,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 int H, int W, int R, int CT, const uint4* __restrict__ bimg, int* __restrict__ err) {
     constexpr int KW = KP - 1;
     constexpr int C = KW / 2;
-    constexpr int N = 2 * KP;                  // MMA N: hi rows then lo rows
+    constexpr int N = KP;                      // MMA N: the rows a of one PSF part
     constexpr int NQ = 16 + KP / 8 - 1;        // A blocks per image row
     constexpr int OFF = 16 - C;                // segment index of v[iy, x0 - c]
-    constexpr int BBYTES = N * KP * 2;
+    constexpr int BBYTES = 2 * KP * KP * 2;    // hi and lo
+    constexpr int BLBO = 2 * KP * 16;          // K-chunk stride of the B image
     constexpr uint32_t IDESC = idesc_bf16(128, N);
     static_assert(KP == 16 || KP == 32, "KP");
     static_assert(OFF + 8 * (NQ - 1) + 7 + 7 < kSegW, "segment width");
@@ -204,10 +231,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int Ys = Y0 - C;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kNSeg; ++i) { mbar_init(seg_full(i), 1); mbar_init(seg_empty(i), 64); }
-        for (int i = 0; i < kNH; ++i) { mbar_init(h_full(i), 64); mbar_init(h_empty(i), 1); }
+        // seg_empty: one arrival per builder lane per row of the box
+        for (int i = 0; i < kNSeg; ++i) { mbar_init(seg_full(i), 1); mbar_init(seg_empty(i), kRB * 32); }
+        for (int i = 0; i < kNH; ++i) { mbar_init(h_full(i), 32); mbar_init(h_empty(i), 1); }
         for (int i = 0; i < kND; ++i) { mbar_init(d_full(i), 1); mbar_init(d_empty(i), 128); }
-        mbar_init(done_bar, 1);
+        mbar_init(done_bar, kIssuers);
         *s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -242,20 +270,22 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int t = issued > kNSeg ? issued - kNSeg : 0; t < issued; ++t)
                 mbar_wait(seg_full(t % kNSeg), (t / kNSeg) & 1, s_abort, err, false);
         }
-    } else if (warp == 1) {
-        // ---- MMA issuer ----
+    } else if (warp <= kIssuers) {
+        // ---- MMA issuers: rows i = warp - 1 (mod kIssuers) ----
         if (lane == 0) {
-            for (int i = 0; i < NR; ++i) {
-                if (*s_abort) break;
+            for (int i = warp - 1; i < NR; i += kIssuers) {
                 const int hs = i % kNH, ds = i % kND;
                 if (!mbar_wait(h_full(hs), (i / kNH) & 1, s_abort, err)) break;
                 if (!mbar_wait(d_empty(ds), ((i / kND) & 1) ^ 1, s_abort, err)) break;
                 tc_fence_after();
                 const uint32_t a0 = sbase + kOffHank + hs * kHankBytes;
 #pragma unroll
-                for (int kk = 0; kk < KP / 16; ++kk)
-                    mma_bf16(tmem + (uint32_t)(ds * N), smem_desc(a0 + kk * 256, 128, 128),
-                             smem_desc(sbase + kOffB + kk * 2 * N * 16, N * 16, 128), IDESC, kk > 0 ? 1u : 0u);
+                for (int kk = 0; kk < KP / 16; ++kk) {
+                    const unsigned long long ad = smem_desc(a0 + kk * 256, 128, 128);
+                    const uint32_t bk = sbase + kOffB + kk * 2 * BLBO;
+                    mma_bf16(tmem + (uint32_t)(ds * N), ad, smem_desc(bk, BLBO, 128), IDESC, kk > 0 ? 1u : 0u);
+                    mma_bf16(tmem + (uint32_t)(ds * N), ad, smem_desc(bk + KP * 16, BLBO, 128), IDESC, 1u);
+                }
                 mma_commit(d_full(ds));
                 mma_commit(h_empty(hs));
             }
@@ -263,76 +293,109 @@ __global__ void __launch_bounds__(kThreads, 1)
             mma_commit(done_bar);
             mbar_wait(done_bar, 0, s_abort, err, false);
         }
-    } else if (warp < 4) {
-        // ---- A builders: Hankel blocks from the staged row ----
-        const int bt = threadIdx.x - 64;
-        for (int i = 0; i < NR; ++i) {
+    } else if (warp >= 8) {
+        // ---- A builders: Hankel blocks from the staged row, one image row per warp ----
+        const int bw = warp - 8;                                 // 0 .. kBuilders-1
+        for (int i = bw; i < NR; i += kBuilders) {
             if (*s_abort) break;
             const int t = i / kRB, r = i - t * kRB, sl = t % kNSeg;
-            if (r == 0 && !mbar_wait(seg_full(sl), (t / kNSeg) & 1, s_abort, err)) break;
+            if (!mbar_wait(seg_full(sl), (t / kNSeg) & 1, s_abort, err)) break;
             const int hs = i % kNH;
             if (!mbar_wait(h_empty(hs), ((i / kNH) & 1) ^ 1, s_abort, err)) break;
             const uint32_t* src = (const uint32_t*)(sm + kOffSeg + sl * kSegBytes + r * kSegW * 2);
             unsigned char* dst = sm + kOffHank + hs * kHankBytes;
-            for (int row = bt; row < NQ * 8; row += 64) {
-                const int q = row >> 3, s = row & 7;
-                const int e0 = OFF + 8 * q + s;               // first element of this 16-byte row
-                const int wb = e0 >> 1;
-                const uint32_t sel = (e0 & 1) ? 0x5432u : 0x3210u;
-                const uint32_t w0 = src[wb], w1 = src[wb + 1], w2 = src[wb + 2], w3 = src[wb + 3];
-                const uint32_t w4 = (e0 & 1) ? src[wb + 4] : 0u;
-                uint4 o;
-                o.x = __byte_perm(w0, w1, sel);
-                o.y = __byte_perm(w1, w2, sel);
-                o.z = __byte_perm(w2, w3, sel);
-                o.w = __byte_perm(w3, w4, sel);
-                *(uint4*)(dst + q * 128 + s * 16) = o;
+#pragma unroll
+            for (int row0 = 0; row0 < NQ * 8; row0 += 32) {
+                const int row = row0 + lane;
+                if (row < NQ * 8) {
+                    const int q = row >> 3, s = row & 7;
+                    const int e0 = OFF + 8 * q + s;           // first element of this 16-byte row
+                    const int wb = e0 >> 1;
+                    const uint32_t sel = (e0 & 1) ? 0x5432u : 0x3210u;
+                    const uint32_t w0 = src[wb], w1 = src[wb + 1], w2 = src[wb + 2], w3 = src[wb + 3];
+                    const uint32_t w4 = (e0 & 1) ? src[wb + 4] : 0u;
+                    uint4 o;
+                    o.x = __byte_perm(w0, w1, sel);
+                    o.y = __byte_perm(w1, w2, sel);
+                    o.z = __byte_perm(w2, w3, sel);
+                    o.w = __byte_perm(w3, w4, sel);
+                    *(uint4*)(dst + q * 128 + s * 16) = o;
+                }
             }
             fence_proxy_async_smem();
             mbar_arrive(h_full(hs));
-            if (r == kRB - 1 || i == NR - 1) mbar_arrive(seg_empty(sl));
+            mbar_arrive(seg_empty(sl));
         }
     } else {
         // ---- epilogue: overlap-add of the KW accumulator columns ----
+        // Before image row iy, acc[t] holds output row (iy - c + t) summed over
+        // the image rows above iy.  Row iy completes output row iy - c (tap
+        // a = KW - 1) and shifts the others down one slot while adding tap
+        // KW - 2 - t, so each tap is one FADD into a fixed register and the
+        // loop body stays small (a fully unrolled ring overflows the
+        // instruction cache).
         const int q = warp & 3;
         const int x = x0 + q * 32 + lane;
         const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
         float acc[KW];
 #pragma unroll
         for (int t = 0; t < KW; ++t) acc[t] = 0.f;
-        bool live = true;
-        for (int i0 = 0; i0 < NR && live; i0 += KW) {
-#pragma unroll
-            for (int u = 0; u < KW; ++u) {
-                const int i = i0 + u;
-                if (live && i < NR) {
-                    const int ds = i % kND;
-                    const bool ok = mbar_wait(d_full(ds), (i / kND) & 1, s_abort, err);
-                    live = __all_sync(0xffffffffu, ok);
+        uint32_t ra[32], rb[32];
+        bool live = __all_sync(0xffffffffu, mbar_wait(d_full(0), 0, s_abort, err));
+        if (live) {
+            tc_fence_after();
+            if (KP == 32) tmem_ld32(tl, ra); else tmem_ld16(tl, ra);
+            tmem_wait_ld();
+            tc_fence_before();
+            mbar_arrive(d_empty(0));
+        }
+        // image rows in pairs so the two register sets swap roles without
+        // copies: start the load of row i + 1, add row i, store the output row
+        // that completes, finish the load
+        for (int i = 0; i < NR && live; i += 2) {
+            // row i (data in ra), then row i + 1 (data in rb)
+            {
+                const bool more = i + 1 < NR;
+                if (more) {
+                    const int dn = (i + 1) % kND;
+                    live = __all_sync(0xffffffffu, mbar_wait(d_full(dn), ((i + 1) / kND) & 1, s_abort, err));
                     if (live) {
                         tc_fence_after();
-                        uint32_t hv[32], lv[32];
-                        if (KP == 32) {
-                            tmem_ld32(tl + (uint32_t)(ds * N), hv);
-                            tmem_ld32(tl + (uint32_t)(ds * N + KP), lv);
-                        } else {
-                            tmem_ld32(tl + (uint32_t)(ds * N), hv);     // hi 0..15, lo 16..31
-                        }
-                        tmem_wait_ld();
-                        tc_fence_before();
-                        mbar_arrive(d_empty(ds));
-#pragma unroll
-                        for (int t = 0; t < KW; ++t) {
-                            const int a = KW - 1 - t;
-                            const float hi = __uint_as_float(hv[a]);
-                            const float lo = __uint_as_float(KP == 32 ? lv[a] : hv[KP + a]);
-                            acc[(t + u) % KW] += hi + lo;
-                        }
-                        const int y = Y0 + i - 2 * C;
-                        if (i >= 2 * C && y < yEnd && x < W) w[(size_t)y * W + x] = acc[u];
-                        acc[u] = 0.f;
+                        if (KP == 32) tmem_ld32(tl + (uint32_t)(dn * N), rb); else tmem_ld16(tl + (uint32_t)(dn * N), rb);
                     }
                 }
+                const float out = acc[0] + __uint_as_float(ra[KW - 1]);
+#pragma unroll
+                for (int t = 0; t < KW - 1; ++t) acc[t] = acc[t + 1] + __uint_as_float(ra[KW - 2 - t]);
+                acc[KW - 1] = 0.f;
+                const int y = Y0 + i - 2 * C;
+                if (i >= 2 * C && y < yEnd && x < W) w[(size_t)y * W + x] = out;
+                if (!(more && live)) break;
+                tmem_wait_ld();
+                tc_fence_before();
+                mbar_arrive(d_empty((i + 1) % kND));
+            }
+            {
+                const int i1 = i + 1;
+                const bool more = i1 + 1 < NR;
+                if (more) {
+                    const int dn = (i1 + 1) % kND;
+                    live = __all_sync(0xffffffffu, mbar_wait(d_full(dn), ((i1 + 1) / kND) & 1, s_abort, err));
+                    if (live) {
+                        tc_fence_after();
+                        if (KP == 32) tmem_ld32(tl + (uint32_t)(dn * N), ra); else tmem_ld16(tl + (uint32_t)(dn * N), ra);
+                    }
+                }
+                const float out = acc[0] + __uint_as_float(rb[KW - 1]);
+#pragma unroll
+                for (int t = 0; t < KW - 1; ++t) acc[t] = acc[t + 1] + __uint_as_float(rb[KW - 2 - t]);
+                acc[KW - 1] = 0.f;
+                const int y = Y0 + i1 - 2 * C;
+                if (i1 >= 2 * C && y < yEnd && x < W) w[(size_t)y * W + x] = out;
+                if (!(more && live)) break;
+                tmem_wait_ld();
+                tc_fence_before();
+                mbar_arrive(d_empty((i1 + 1) % kND));
             }
         }
     }
