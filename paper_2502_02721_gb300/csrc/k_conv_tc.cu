@@ -26,14 +26,15 @@
 // read from device memory), 8 rows of 160 elements per box starting at
 // x0 - 16 (a multiple of 8 elements), zero-filled outside the image.
 //
-// Warp roles (384 threads, one CTA per SM): warp 0 issues the TMA loads,
-// warp 1 owns TMEM; one lane each of warps 1-3 issues the MMAs of every
-// third image row (a single issuing thread is bound by the ~60-cycle issue
-// cost of each tcgen05 instruction and barrier test); warps 8-11 build A
-// (each a whole image row, rows dealt round robin); warps 4-7 read the
-// accumulators (warp w reads TMEM lanes 32 (w % 4) ..), one row ahead of
-// the overlap-add they do with the KW running output rows in registers
-// (a shift register).  Every
+// Image rows move through the pipeline in groups of kG = 4 (one barrier
+// wait, commit and arrive per group: each tcgen05 instruction and barrier
+// test costs tens of cycles of issue latency in its thread).  Warp roles
+// (320 threads, one CTA per SM): warp 0 issues the TMA loads; warp 1 owns
+// TMEM; one lane each of warps 1-3 issues the MMAs of every third group;
+// warps 8-9 build A (whole groups, dealt round robin); warps 4-7 read the
+// accumulators (warp w reads TMEM lanes 32 (w % 4) ..) and do the
+// overlap-add with the KW running output rows in registers (a shift
+// register).  Every
 // wait is bounded in time; on a timeout the CTA stops issuing, drains its
 // copies and MMAs, frees TMEM and reports IPF_ERR_TIMEOUT.
 #include <cuda.h>
@@ -46,9 +47,10 @@ namespace ipf {
 
 namespace {
 
-constexpr int kThreads = 384;
-constexpr int kBuilders = 4;         // builder warps: 8 .. 11
+constexpr int kThreads = 320;
+constexpr int kBuilders = 2;         // builder warps: 8, 9
 constexpr int kIssuers = 3;          // MMA-issuing warps: 1 .. 3
+constexpr int kG = 4;                // image rows per pipeline group
 constexpr int kSegW = 160;           // elements per staged row segment
 constexpr int kRB = 8;               // image rows per TMA box
 constexpr int kNSeg = 8;             // boxes in flight
@@ -61,7 +63,10 @@ constexpr int kOffB = 0;
 constexpr int kOffSeg = 4096;
 constexpr int kOffHank = kOffSeg + kNSeg * kSegBytes;          // 24576
 constexpr int kOffBar = kOffHank + kNH * kHankBytes;           // 65536
-constexpr int kNBar = 2 * kNSeg + 2 * kNH + 2 * kND + 1;
+constexpr int kNHG = kNH / kG;       // A-operand group slots
+constexpr int kNDG = kND / kG;       // accumulator group slots
+static_assert(kRB % kG == 0 && kNH % kG == 0 && kND % kG == 0, "groups");
+constexpr int kNBar = 2 * kNSeg + 2 * kNHG + 2 * kNDG + 1;
 constexpr int kOffMisc = kOffBar + 8 * kNBar;
 constexpr int kSmemUsed = kOffMisc + 16;
 // more than half of the SM's shared memory: one CTA per SM, so the 512
@@ -215,9 +220,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     auto seg_full = [&](int i) { return bar0 + 8u * i; };
     auto seg_empty = [&](int i) { return bar0 + 8u * (kNSeg + i); };
     auto h_full = [&](int i) { return bar0 + 8u * (2 * kNSeg + i); };
-    auto h_empty = [&](int i) { return bar0 + 8u * (2 * kNSeg + kNH + i); };
-    auto d_full = [&](int i) { return bar0 + 8u * (2 * kNSeg + 2 * kNH + i); };
-    auto d_empty = [&](int i) { return bar0 + 8u * (2 * kNSeg + 2 * kNH + kND + i); };
+    auto h_empty = [&](int i) { return bar0 + 8u * (2 * kNSeg + kNHG + i); };
+    auto d_full = [&](int i) { return bar0 + 8u * (2 * kNSeg + 2 * kNHG + i); };
+    auto d_empty = [&](int i) { return bar0 + 8u * (2 * kNSeg + 2 * kNHG + kNDG + i); };
     const uint32_t done_bar = bar0 + 8u * (kNBar - 1);
     uint32_t* s_tmem = (uint32_t*)(sm + kOffMisc);
     volatile int* s_abort = (volatile int*)(sm + kOffMisc + 4);
@@ -229,12 +234,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int yEnd = min(Y0 + R, H);
     const int NR = (yEnd - Y0) + 2 * C;                   // image rows Y0 - c .. yEnd - 1 + c
     const int Ys = Y0 - C;
+    const int NG = (NR + kG - 1) / kG;                    // row groups
 
     if (threadIdx.x == 0) {
         // seg_empty: one arrival per builder lane per row of the box
         for (int i = 0; i < kNSeg; ++i) { mbar_init(seg_full(i), 1); mbar_init(seg_empty(i), kRB * 32); }
-        for (int i = 0; i < kNH; ++i) { mbar_init(h_full(i), 32); mbar_init(h_empty(i), 1); }
-        for (int i = 0; i < kND; ++i) { mbar_init(d_full(i), 1); mbar_init(d_empty(i), 128); }
+        for (int i = 0; i < kNHG; ++i) { mbar_init(h_full(i), 32); mbar_init(h_empty(i), 1); }
+        for (int i = 0; i < kNDG; ++i) { mbar_init(d_full(i), 1); mbar_init(d_empty(i), 128); }
         mbar_init(done_bar, kIssuers);
         *s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -271,60 +277,68 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mbar_wait(seg_full(t % kNSeg), (t / kNSeg) & 1, s_abort, err, false);
         }
     } else if (warp <= kIssuers) {
-        // ---- MMA issuers: rows i = warp - 1 (mod kIssuers) ----
+        // ---- MMA issuers: groups g = warp - 1 (mod kIssuers) ----
         if (lane == 0) {
-            for (int i = warp - 1; i < NR; i += kIssuers) {
-                const int hs = i % kNH, ds = i % kND;
-                if (!mbar_wait(h_full(hs), (i / kNH) & 1, s_abort, err)) break;
-                if (!mbar_wait(d_empty(ds), ((i / kND) & 1) ^ 1, s_abort, err)) break;
+            for (int g = warp - 1; g < NG; g += kIssuers) {
+                const int hg = g % kNHG, dg = g % kNDG;
+                if (!mbar_wait(h_full(hg), (g / kNHG) & 1, s_abort, err)) break;
+                if (!mbar_wait(d_empty(dg), ((g / kNDG) & 1) ^ 1, s_abort, err)) break;
                 tc_fence_after();
-                const uint32_t a0 = sbase + kOffHank + hs * kHankBytes;
 #pragma unroll
-                for (int kk = 0; kk < KP / 16; ++kk) {
-                    const unsigned long long ad = smem_desc(a0 + kk * 256, 128, 128);
-                    const uint32_t bk = sbase + kOffB + kk * 2 * BLBO;
-                    mma_bf16(tmem + (uint32_t)(ds * N), ad, smem_desc(bk, BLBO, 128), IDESC, kk > 0 ? 1u : 0u);
-                    mma_bf16(tmem + (uint32_t)(ds * N), ad, smem_desc(bk + KP * 16, BLBO, 128), IDESC, 1u);
+                for (int r = 0; r < kG; ++r) {
+                    const int i = g * kG + r;
+                    if (i < NR) {
+                        const uint32_t a0 = sbase + kOffHank + (hg * kG + r) * kHankBytes;
+                        const uint32_t d = tmem + (uint32_t)((dg * kG + r) * N);
+#pragma unroll
+                        for (int kk = 0; kk < KP / 16; ++kk) {
+                            const unsigned long long ad = smem_desc(a0 + kk * 256, 128, 128);
+                            const uint32_t bk = sbase + kOffB + kk * 2 * BLBO;
+                            mma_bf16(d, ad, smem_desc(bk, BLBO, 128), IDESC, kk > 0 ? 1u : 0u);
+                            mma_bf16(d, ad, smem_desc(bk + KP * 16, BLBO, 128), IDESC, 1u);
+                        }
+                    }
                 }
-                mma_commit(d_full(ds));
-                mma_commit(h_empty(hs));
+                mma_commit(d_full(dg));
+                mma_commit(h_empty(hg));
             }
             // all MMAs issued by this thread complete before TMEM is freed
             mma_commit(done_bar);
             mbar_wait(done_bar, 0, s_abort, err, false);
         }
     } else if (warp >= 8) {
-        // ---- A builders: Hankel blocks from the staged row, one image row per warp ----
-        const int bw = warp - 8;                                 // 0 .. kBuilders-1
-        for (int i = bw; i < NR; i += kBuilders) {
-            if (*s_abort) break;
-            const int t = i / kRB, r = i - t * kRB, sl = t % kNSeg;
+        // ---- A builders: Hankel blocks from the staged rows, one group per warp ----
+        for (int g = warp - 8; g < NG; g += kBuilders) {
+            const int t = (g * kG) / kRB, sl = t % kNSeg, hg = g % kNHG;
             if (!mbar_wait(seg_full(sl), (t / kNSeg) & 1, s_abort, err)) break;
-            const int hs = i % kNH;
-            if (!mbar_wait(h_empty(hs), ((i / kNH) & 1) ^ 1, s_abort, err)) break;
-            const uint32_t* src = (const uint32_t*)(sm + kOffSeg + sl * kSegBytes + r * kSegW * 2);
-            unsigned char* dst = sm + kOffHank + hs * kHankBytes;
+            if (!mbar_wait(h_empty(hg), ((g / kNHG) & 1) ^ 1, s_abort, err)) break;
+            for (int r = 0; r < kG; ++r) {
+                const int i = g * kG + r;
+                if (i >= NR) break;
+                const uint32_t* src = (const uint32_t*)(sm + kOffSeg + sl * kSegBytes + (i - t * kRB) * kSegW * 2);
+                unsigned char* dst = sm + kOffHank + (hg * kG + r) * kHankBytes;
 #pragma unroll
-            for (int row0 = 0; row0 < NQ * 8; row0 += 32) {
-                const int row = row0 + lane;
-                if (row < NQ * 8) {
-                    const int q = row >> 3, s = row & 7;
-                    const int e0 = OFF + 8 * q + s;           // first element of this 16-byte row
-                    const int wb = e0 >> 1;
-                    const uint32_t sel = (e0 & 1) ? 0x5432u : 0x3210u;
-                    const uint32_t w0 = src[wb], w1 = src[wb + 1], w2 = src[wb + 2], w3 = src[wb + 3];
-                    const uint32_t w4 = (e0 & 1) ? src[wb + 4] : 0u;
-                    uint4 o;
-                    o.x = __byte_perm(w0, w1, sel);
-                    o.y = __byte_perm(w1, w2, sel);
-                    o.z = __byte_perm(w2, w3, sel);
-                    o.w = __byte_perm(w3, w4, sel);
-                    *(uint4*)(dst + q * 128 + s * 16) = o;
+                for (int row0 = 0; row0 < NQ * 8; row0 += 32) {
+                    const int row = row0 + lane;
+                    if (row < NQ * 8) {
+                        const int q = row >> 3, s = row & 7;
+                        const int e0 = OFF + 8 * q + s;       // first element of this 16-byte row
+                        const int wb = e0 >> 1;
+                        const uint32_t sel = (e0 & 1) ? 0x5432u : 0x3210u;
+                        const uint32_t w0 = src[wb], w1 = src[wb + 1], w2 = src[wb + 2], w3 = src[wb + 3];
+                        const uint32_t w4 = (e0 & 1) ? src[wb + 4] : 0u;
+                        uint4 o;
+                        o.x = __byte_perm(w0, w1, sel);
+                        o.y = __byte_perm(w1, w2, sel);
+                        o.z = __byte_perm(w2, w3, sel);
+                        o.w = __byte_perm(w3, w4, sel);
+                        *(uint4*)(dst + q * 128 + s * 16) = o;
+                    }
                 }
+                mbar_arrive(seg_empty(sl));
             }
             fence_proxy_async_smem();
-            mbar_arrive(h_full(hs));
-            mbar_arrive(seg_empty(sl));
+            mbar_arrive(h_full(hg));
         }
     } else {
         // ---- epilogue: overlap-add of the KW accumulator columns ----
@@ -340,62 +354,38 @@ __global__ void __launch_bounds__(kThreads, 1)
         float acc[KW];
 #pragma unroll
         for (int t = 0; t < KW; ++t) acc[t] = 0.f;
-        uint32_t ra[32], rb[32];
-        bool live = __all_sync(0xffffffffu, mbar_wait(d_full(0), 0, s_abort, err));
-        if (live) {
+        for (int g = 0; g < NG; ++g) {
+            const int dg = g % kNDG;
+            if (!__all_sync(0xffffffffu, mbar_wait(d_full(dg), (g / kNDG) & 1, s_abort, err))) break;
             tc_fence_after();
-            if (KP == 32) tmem_ld32(tl, ra); else tmem_ld16(tl, ra);
-            tmem_wait_ld();
-            tc_fence_before();
-            mbar_arrive(d_empty(0));
-        }
-        // image rows in pairs so the two register sets swap roles without
-        // copies: start the load of row i + 1, add row i, store the output row
-        // that completes, finish the load
-        for (int i = 0; i < NR && live; i += 2) {
-            // row i (data in ra), then row i + 1 (data in rb)
-            {
-                const bool more = i + 1 < NR;
-                if (more) {
-                    const int dn = (i + 1) % kND;
-                    live = __all_sync(0xffffffffu, mbar_wait(d_full(dn), ((i + 1) / kND) & 1, s_abort, err));
-                    if (live) {
-                        tc_fence_after();
-                        if (KP == 32) tmem_ld32(tl + (uint32_t)(dn * N), rb); else tmem_ld16(tl + (uint32_t)(dn * N), rb);
+            // two rows at a time keeps the loaded columns at 64 registers
+#pragma unroll
+            for (int h = 0; h < kG; h += 2) {
+                uint32_t rr[2][32];
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    if (g * kG + h + r < NR) {
+                        const uint32_t ta = tl + (uint32_t)((dg * kG + h + r) * N);
+                        if (KP == 32) tmem_ld32(ta, rr[r]); else tmem_ld16(ta, rr[r]);
                     }
                 }
-                const float out = acc[0] + __uint_as_float(ra[KW - 1]);
-#pragma unroll
-                for (int t = 0; t < KW - 1; ++t) acc[t] = acc[t + 1] + __uint_as_float(ra[KW - 2 - t]);
-                acc[KW - 1] = 0.f;
-                const int y = Y0 + i - 2 * C;
-                if (i >= 2 * C && y < yEnd && x < W) w[(size_t)y * W + x] = out;
-                if (!(more && live)) break;
                 tmem_wait_ld();
-                tc_fence_before();
-                mbar_arrive(d_empty((i + 1) % kND));
-            }
-            {
-                const int i1 = i + 1;
-                const bool more = i1 + 1 < NR;
-                if (more) {
-                    const int dn = (i1 + 1) % kND;
-                    live = __all_sync(0xffffffffu, mbar_wait(d_full(dn), ((i1 + 1) / kND) & 1, s_abort, err));
-                    if (live) {
-                        tc_fence_after();
-                        if (KP == 32) tmem_ld32(tl + (uint32_t)(dn * N), ra); else tmem_ld16(tl + (uint32_t)(dn * N), ra);
+                if (h + 2 >= kG) {
+                    tc_fence_before();
+                    mbar_arrive(d_empty(dg));
+                }
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const int i = g * kG + h + r;
+                    if (i < NR) {
+                        const float out = acc[0] + __uint_as_float(rr[r][KW - 1]);
+#pragma unroll
+                        for (int t = 0; t < KW - 1; ++t) acc[t] = acc[t + 1] + __uint_as_float(rr[r][KW - 2 - t]);
+                        acc[KW - 1] = 0.f;
+                        const int y = Y0 + i - 2 * C;
+                        if (i >= 2 * C && y < yEnd && x < W) w[(size_t)y * W + x] = out;
                     }
                 }
-                const float out = acc[0] + __uint_as_float(rb[KW - 1]);
-#pragma unroll
-                for (int t = 0; t < KW - 1; ++t) acc[t] = acc[t + 1] + __uint_as_float(rb[KW - 2 - t]);
-                acc[KW - 1] = 0.f;
-                const int y = Y0 + i1 - 2 * C;
-                if (i1 >= 2 * C && y < yEnd && x < W) w[(size_t)y * W + x] = out;
-                if (!(more && live)) break;
-                tmem_wait_ld();
-                tc_fence_before();
-                mbar_arrive(d_empty((i1 + 1) % kND));
             }
         }
     }
