@@ -29,9 +29,9 @@
 // Image rows move through the pipeline in groups of kG = 4 (one barrier
 // wait, commit and arrive per group: each tcgen05 instruction and barrier
 // test costs tens of cycles of issue latency in its thread).  Warp roles
-// (320 threads, one CTA per SM): warp 0 issues the TMA loads; warp 1 owns
+// (384 threads, one CTA per SM): warp 0 issues the TMA loads; warp 1 owns
 // TMEM; one lane each of warps 1-3 issues the MMAs of every third group;
-// warps 8-9 build A (whole groups, dealt round robin); warps 4-7 read the
+// warps 8-11 build A (whole groups, dealt round robin); warps 4-7 read the
 // accumulators (warp w reads TMEM lanes 32 (w % 4) ..) and do the
 // overlap-add with the KW running output rows in registers (a shift
 // register).  Every
@@ -47,8 +47,8 @@ namespace ipf {
 
 namespace {
 
-constexpr int kThreads = 320;
-constexpr int kBuilders = 2;         // builder warps: 8, 9
+constexpr int kThreads = 384;
+constexpr int kBuilders = 4;         // builder warps: 8 .. 11
 constexpr int kIssuers = 3;          // MMA-issuing warps: 1 .. 3
 constexpr int kG = 4;                // image rows per pipeline group
 constexpr int kSegW = 160;           // elements per staged row segment
@@ -237,8 +237,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int NG = (NR + kG - 1) / kG;                    // row groups
 
     if (threadIdx.x == 0) {
-        // seg_empty: one arrival per builder lane per row of the box
-        for (int i = 0; i < kNSeg; ++i) { mbar_init(seg_full(i), 1); mbar_init(seg_empty(i), kRB * 32); }
+        // seg_empty: one arrival per row of the box, once its builder warp has read it
+        for (int i = 0; i < kNSeg; ++i) { mbar_init(seg_full(i), 1); mbar_init(seg_empty(i), kRB); }
         for (int i = 0; i < kNHG; ++i) { mbar_init(h_full(i), 32); mbar_init(h_empty(i), 1); }
         for (int i = 0; i < kNDG; ++i) { mbar_init(d_full(i), 1); mbar_init(d_empty(i), 128); }
         mbar_init(done_bar, kIssuers);
@@ -317,25 +317,36 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (i >= NR) break;
                 const uint32_t* src = (const uint32_t*)(sm + kOffSeg + sl * kSegBytes + (i - t * kRB) * kSegW * 2);
                 unsigned char* dst = sm + kOffHank + (hg * kG + r) * kHankBytes;
+                // all source words first (independent loads in flight together),
+                // then the byte permutes and 16-byte stores
+                constexpr int NIT = (NQ * 8 + 31) / 32;
+                uint32_t wv[NIT][5];
 #pragma unroll
-                for (int row0 = 0; row0 < NQ * 8; row0 += 32) {
-                    const int row = row0 + lane;
+                for (int it = 0; it < NIT; ++it) {
+                    const int row = it * 32 + lane;
+                    const int e0 = OFF + 8 * (row >> 3) + (row & 7);
+                    const int wb = row < NQ * 8 ? (e0 >> 1) : 0;
+#pragma unroll
+                    for (int k = 0; k < 5; ++k) wv[it][k] = src[wb + k];
+                }
+#pragma unroll
+                for (int it = 0; it < NIT; ++it) {
+                    const int row = it * 32 + lane;
                     if (row < NQ * 8) {
                         const int q = row >> 3, s = row & 7;
-                        const int e0 = OFF + 8 * q + s;       // first element of this 16-byte row
-                        const int wb = e0 >> 1;
-                        const uint32_t sel = (e0 & 1) ? 0x5432u : 0x3210u;
-                        const uint32_t w0 = src[wb], w1 = src[wb + 1], w2 = src[wb + 2], w3 = src[wb + 3];
-                        const uint32_t w4 = (e0 & 1) ? src[wb + 4] : 0u;
+                        const uint32_t sel = ((OFF + s) & 1) ? 0x5432u : 0x3210u;
                         uint4 o;
-                        o.x = __byte_perm(w0, w1, sel);
-                        o.y = __byte_perm(w1, w2, sel);
-                        o.z = __byte_perm(w2, w3, sel);
-                        o.w = __byte_perm(w3, w4, sel);
+                        o.x = __byte_perm(wv[it][0], wv[it][1], sel);
+                        o.y = __byte_perm(wv[it][1], wv[it][2], sel);
+                        o.z = __byte_perm(wv[it][2], wv[it][3], sel);
+                        o.w = __byte_perm(wv[it][3], wv[it][4], sel);
                         *(uint4*)(dst + q * 128 + s * 16) = o;
                     }
                 }
-                mbar_arrive(seg_empty(sl));
+                // every word read from the staged row has been consumed by a
+                // store: the row may be overwritten by the next box
+                __syncwarp();
+                if (lane == 0) mbar_arrive(seg_empty(sl));
             }
             fence_proxy_async_smem();
             mbar_arrive(h_full(hg));
