@@ -18,20 +18,6 @@ namespace {
 
 constexpr int kLamChunk = 16;
 
-// float -> BF16 bits, round to nearest even (finite inputs), and back
-unsigned short bf16_bits_rn(float f) {
-    unsigned u;
-    memcpy(&u, &f, 4);
-    u += 0x7FFFu + ((u >> 16) & 1u);
-    return (unsigned short)(u >> 16);
-}
-float bf16_to_float(unsigned short h) {
-    const unsigned u = (unsigned)h << 16;
-    float f;
-    memcpy(&f, &u, 4);
-    return f;
-}
-
 size_t storage_bytes(int storage) {
     switch (storage) {
         case IPF_STORE_F64: return 8;
@@ -174,20 +160,9 @@ cudaError_t upload_op(const ipf_operator* op, Alloc& al, OpDev* d, cudaStream_t 
             if ((e = cudaMemcpy(pp, pairs.data(), pairs.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
             d->kw = kw;
             d->psf_pairs = (const unsigned long long*)pp;
-            if (kw == 15 || kw == 31) {
-                // [F_hi ; F_lo] for the tensor-core convolution: 2KP rows (a, then a
-                // again for the remainder) x KP columns (b), BF16, stored as K-major
-                // 8x8 core matrices: byte (b/8)*(2KP*16) + row*16 + (b%8)*2
-                const int KP = kw + 1, NR2 = 2 * KP;
-                std::vector<unsigned short> img((size_t)NR2 * KP, 0);
-                for (int row = 0; row < NR2; ++row)
-                    for (int bb = 0; bb < KP; ++bb) {
-                        const int a = row < KP ? row : row - KP;
-                        const float f = (a < kw && bb < kw) ? F(a, bb) : 0.f;
-                        const unsigned short hi = bf16_bits_rn(f);
-                        const unsigned short val = row < KP ? hi : bf16_bits_rn(f - bf16_to_float(hi));
-                        img[(size_t)(bb / 8) * NR2 * 8 + (size_t)row * 8 + (bb % 8)] = val;
-                    }
+            std::vector<unsigned short> img;
+            const int KP = conv_tc_operand(kw, F, &img);
+            if (KP) {
                 void* pt = nullptr;
                 if ((e = al.get(&pt, img.size() * 2)) != cudaSuccess) return e;
                 if ((e = cudaMemcpy(pt, img.data(), img.size() * 2, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
@@ -439,7 +414,7 @@ size_t ipf_footprint(const ipf_operator* op, const ipf_config* cfg) {
     if (op->kind == IPF_OP_CSR && op->mem == IPF_MEM_HOST)
         bytes += (size_t)(op->rows + 1) * 8 + (size_t)op->nnz * 8;
     else if (op->kind == IPF_OP_PSF2D)
-        bytes += (size_t)op->ph * op->pw * 4 + 32 * 33 * 8 + 64 * 32 * 2;   // PSF, packed pairs, tensor-core operand
+        bytes += (size_t)op->ph * op->pw * 4 + 32 * 33 * 8 + 40960;   // PSF, packed pairs, tensor-core operand
     return bytes;
 }
 

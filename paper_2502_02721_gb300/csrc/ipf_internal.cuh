@@ -4,6 +4,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <functional>
+#include <vector>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
@@ -263,6 +265,13 @@ struct OpDev {
 // k_ops.cu
 // vbase + (*jptr) * ldv is the input vector (jptr NULL: vbase itself)
 // tensor-core convolution for BF16 storage (k_conv_tc.cu)
+constexpr int kConvTcGroup = 8;    // image rows per MMA group
+// BF16 bits of f rounded to nearest even (finite f), and back
+unsigned short bf16_bits_rn(float f);
+float bf16_bits_to_float(unsigned short h);
+// the B operand of the tensor-core convolution for a kw x kw flipped PSF
+// F(a, b) (kw 15 or 31); returns KP (16 or 32), or 0 if kw is not supported
+int conv_tc_operand(int kw, const std::function<float(int, int)>& F, std::vector<unsigned short>* img);
 bool conv_tc_eligible(const OpDev& op, const void* vbase, long long ldv);
 cudaError_t launch_conv_tc(const OpDev& op, const void* vbase, long long ldv, long long vcols, const int* jptr,
                            float* w, int* err, cudaStream_t s);

@@ -2,44 +2,51 @@
 // (tcgen05) for basis vectors stored in BF16, FP32 accumulation.
 //
 // With F the flipped PSF padded to KW x KW (KW = 15 or 31, c = KW/2),
-//     w[y, x] = sum_{a,b} F[a][b] v[y - c + a, x - c + b].
-// For one image row iy and 128 output columns x0..x0+127 the products
-//     D_iy[x, a] = sum_b v[iy, x0 + x - c + b] F[a][b]
-// form a dense 128 x KP x KP contraction (KP = KW + 1, b and a zero-padded),
-// and output row y collects D_iy[:, a] from the KW image rows iy = y - c + a.
-// So each image row costs a 128 x KP x KP product (two MMAs per 16-wide K
-// slice, one per PSF part, into the same accumulator), and the row sums (an
-// overlap-add over a) run on the CUDA cores.
+//     w[y, x] = sum_{a,b} F[a][b] v[y - c + a, x - c + b],
+// so image row iy reaches output row y through tap a = iy - y + c.  A CTA
+// owns 128 output columns x0.. and a band of output rows, and takes the
+// image rows in groups of G = 8 (iy0 .. iy0 + 7).  For one group
+//     D[x, j] = sum_{r < G} sum_{b < KP} v[iy0 + r, x0 - c + x + b] B[j, (r, b)],
+//     B[j, (r, b)] = F[r + j + 1 - G][b]   (zero outside 0..KW-1),
+// is that group's whole contribution to output row y = iy0 + G - 1 + c - j,
+// j = 0 .. KW + G - 2: a dense 128 x N x (G KP) contraction (KP = KW + 1),
+// 2 G KP / 16 MMAs per group.  The CUDA cores only carry the KW - 1 output
+// rows that straddle two groups (a shift register of partial sums).
 //
 // Operands, both K-major without swizzle in shared memory:
-//   A  the Hankel matrix H[x, b] = v[iy, x0 - c + x + b].  A K-major core
-//      matrix (8 rows x 8 elements) of it depends only on (x/8 + b/8), so
-//      NQ = 16 + KP/8 - 1 blocks of 128 bytes hold it, block q row s =
-//      v[iy, x0 - c + 8q + s .. +7]; the descriptor uses 128 bytes for both
-//      the K and the M core-matrix strides.  Built from a staged row
-//      segment by two builder warps.
-//   B  [F_hi ; F_lo]: F rounded to BF16, and the BF16 rounding of the
-//      remainder, rows a, so hi + lo carries F to about 2^-16 relative; the
-//      MMA adds both products into the same FP32 accumulator.  Built once on
-//      the host in this layout (2 KP rows, K-chunk stride 2 KP x 16 bytes).
+//   A  per image row, the Hankel matrix H[x, b] = v[iy, x0 - c + x + b].  A
+//      K-major core matrix (8 rows x 8 elements) of it depends only on
+//      (x/8 + b/8), so NQ = 16 + KP/8 - 1 blocks of 128 bytes hold it, block
+//      q row s = v[iy, x0 - c + 8q + s .. +7]; the descriptor uses 128 bytes
+//      for both the K and the M core-matrix strides.  Built from a staged row
+//      segment by the builder warps.
+//   B  [B_hi ; B_lo] (N = 2 NP rows, NP = KW + G - 1 rounded up to 8): B with
+//      F rounded to BF16, and with the BF16 rounding of the remainder, so
+//      hi + lo carries F to about 2^-16 relative; the halves land in separate
+//      accumulator columns and are added in FP32.  Built once on the host
+//      (conv_tc_operand) in this layout.
 // Image rows arrive by TMA (3-D map over the basis: x, y, basis column j, j
 // read from device memory), 8 rows of 160 elements per box starting at
 // x0 - 16 (a multiple of 8 elements), zero-filled outside the image.
 //
-// Image rows move through the pipeline in groups of kG = 4 (one barrier
-// wait, commit and arrive per group: each tcgen05 instruction and barrier
-// test costs tens of cycles of issue latency in its thread).  Warp roles
-// (384 threads, one CTA per SM): warp 0 issues the TMA loads; warp 1 owns
-// TMEM; one lane each of warps 1-3 issues the MMAs of every third group;
-// warps 8-11 build A (whole groups, dealt round robin); warps 4-7 read the
-// accumulators (warp w reads TMEM lanes 32 (w % 4) ..) and do the
-// overlap-add with the KW running output rows in registers (a shift
-// register).  Every
-// wait is bounded in time; on a timeout the CTA stops issuing, drains its
-// copies and MMAs, frees TMEM and reports IPF_ERR_TIMEOUT.
+// One barrier wait, commit and arrive per group (each tcgen05 instruction
+// and barrier test costs tens of cycles of issue latency in its thread).
+// Warp roles (416 threads, one CTA per SM): warp 0 issues the TMA loads;
+// warp 1 owns TMEM; one lane each of warps 1-3 and 12 issues the MMAs of
+// every fourth group; warps 8-11 build A (every fourth group); warps 4-7
+// read the accumulators (warp w reads TMEM lanes 32 (w % 4) ..) and finish
+// the output rows.  Each ring slot is waited on by one role instance only
+// (groups g = slot mod 4 for both the A and the accumulator rings), so a
+// parity wait can never match a phase two generations old.  Every wait is
+// bounded in time; on a timeout the
+// CTA stops issuing, drains its copies and MMAs, frees TMEM and reports
+// IPF_ERR_TIMEOUT.
 #include <cuda.h>
 
+#include <cstring>
+#include <functional>
 #include <mutex>
+#include <vector>
 
 #include "ipf_internal.cuh"
 
@@ -47,32 +54,44 @@ namespace ipf {
 
 namespace {
 
-constexpr int kThreads = 384;
+constexpr int kThreads = 416;
 constexpr int kBuilders = 4;         // builder warps: 8 .. 11
-constexpr int kIssuers = 3;          // MMA-issuing warps: 1 .. 3
-constexpr int kG = 4;                // image rows per pipeline group
+constexpr int kIssuers = 4;          // MMA-issuing warps: 1, 2, 3, 12
+constexpr int kG = kConvTcGroup;     // image rows per MMA group
 constexpr int kSegW = 160;           // elements per staged row segment
 constexpr int kRB = 8;               // image rows per TMA box
 constexpr int kNSeg = 8;             // boxes in flight
-constexpr int kNH = 16;              // A operands (image rows) in flight
-constexpr int kND = 16;              // TMEM accumulator buffers (KP columns each)
+constexpr int kNHG = 4;              // A-operand groups in flight
+constexpr int kNDG = 4;              // accumulator groups in flight
 constexpr int kHankBytes = 2560;     // up to 20 blocks of 128 bytes
 constexpr int kTmemCols = 512;
 constexpr int kSegBytes = kRB * kSegW * 2;
+constexpr int kBMax = 40960;         // B image bytes for KP = 32
 constexpr int kOffB = 0;
-constexpr int kOffSeg = 4096;
-constexpr int kOffHank = kOffSeg + kNSeg * kSegBytes;          // 24576
-constexpr int kOffBar = kOffHank + kNH * kHankBytes;           // 65536
-constexpr int kNHG = kNH / kG;       // A-operand group slots
-constexpr int kNDG = kND / kG;       // accumulator group slots
-static_assert(kRB % kG == 0 && kNH % kG == 0 && kND % kG == 0, "groups");
+constexpr int kOffSeg = kBMax;
+constexpr int kOffHank = kOffSeg + kNSeg * kSegBytes;
+constexpr int kOffBar = kOffHank + kNHG * kG * kHankBytes;
 constexpr int kNBar = 2 * kNSeg + 2 * kNHG + 2 * kNDG + 1;
 constexpr int kOffMisc = kOffBar + 8 * kNBar;
 constexpr int kSmemUsed = kOffMisc + 16;
-// more than half of the SM's shared memory: one CTA per SM, so the 512
-// TMEM columns it allocates are never contended by a sibling CTA
-constexpr int kSmemRequest = 116 * 1024;
-static_assert(kSmemUsed + 1024 <= kSmemRequest, "shared memory layout");
+constexpr int kSmemRequest = kSmemUsed + 1024;
+static_assert(kRB == kG, "one staged box per group");
+static_assert(kNHG % kIssuers == 0 && kNDG % kIssuers == 0 && kNHG % kBuilders == 0,
+              "each ring slot belongs to one issuer and one builder");
+static_assert(kSmemRequest > 116 * 1024 && kSmemRequest <= 227 * 1024, "one CTA per SM, within the SM");
+
+// per KP: padded output rows per part, MMA N, K per group, B image bytes
+template <int KP> struct TcShape {
+    static constexpr int KW = KP - 1;
+    static constexpr int NU = KW + kG - 1;              // output rows a group touches
+    static constexpr int NP = (NU + 7) / 8 * 8;
+    static constexpr int N = 2 * NP;                    // hi columns, then lo columns
+    static constexpr int KG = kG * KP;
+    static constexpr int BLBO = N * 16;                 // K-chunk stride of the B image
+    static constexpr int BBYTES = KG * N * 2;
+};
+static_assert(TcShape<32>::BBYTES <= kBMax && TcShape<16>::BBYTES <= kBMax, "B image");
+
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s
 
 __device__ __forceinline__ unsigned long long globaltimer() {
@@ -168,7 +187,7 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 }
 
 // 32 consecutive TMEM columns of this warp's 32 lanes, one lane per thread
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
         "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
@@ -178,7 +197,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
           "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[32]) {
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
         "%15}, [%16];"
@@ -186,6 +205,26 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[32]) {
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
 }
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+
+// NP consecutive TMEM columns (NP = 40: 32 + 8; NP = 24: 16 + 8)
+template <int NP>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t (&r)[NP]) {
+    static_assert(NP == 40 || NP == 24, "column count");
+    if constexpr (NP == 40) {
+        tmem_ld32(taddr, r);
+        tmem_ld8(taddr + 32, &r[32]);
+    } else {
+        tmem_ld16(taddr, r);
+        tmem_ld8(taddr + 16, &r[16]);
+    }
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
@@ -200,18 +239,16 @@ template <int KP>
 __global__ void __launch_bounds__(kThreads, 1)
     k_conv2d_tc(const __grid_constant__ CUtensorMap vmap, const int* __restrict__ jptr, float* __restrict__ w,
                 int H, int W, int R, int CT, const uint4* __restrict__ bimg, int* __restrict__ err) {
-    constexpr int KW = KP - 1;
+    using S = TcShape<KP>;
+    constexpr int KW = S::KW, NU = S::NU, NP = S::NP, N = S::N;
     constexpr int C = KW / 2;
-    constexpr int N = KP;                      // MMA N: the rows a of one PSF part
     constexpr int NQ = 16 + KP / 8 - 1;        // A blocks per image row
     constexpr int OFF = 16 - C;                // segment index of v[iy, x0 - c]
-    constexpr int BBYTES = 2 * KP * KP * 2;    // hi and lo
-    constexpr int BLBO = 2 * KP * 16;          // K-chunk stride of the B image
     constexpr uint32_t IDESC = idesc_bf16(128, N);
     static_assert(KP == 16 || KP == 32, "KP");
     static_assert(OFF + 8 * (NQ - 1) + 7 + 7 < kSegW, "segment width");
-    static_assert(NQ * 128 <= kHankBytes && BBYTES <= kOffSeg, "operand sizes");
-    static_assert(kND * N <= kTmemCols, "TMEM columns");
+    static_assert(NQ * 128 <= kHankBytes, "A operand size");
+    static_assert(N % 16 == 0 && N <= 256 && kNDG * N <= kTmemCols, "MMA shape and TMEM columns");
 
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -234,10 +271,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int yEnd = min(Y0 + R, H);
     const int NR = (yEnd - Y0) + 2 * C;                   // image rows Y0 - c .. yEnd - 1 + c
     const int Ys = Y0 - C;
-    const int NG = (NR + kG - 1) / kG;                    // row groups
+    const int NG = (NR + kG - 1) / kG;                    // row groups (one TMA box each)
 
     if (threadIdx.x == 0) {
-        // seg_empty: one arrival per row of the box, once its builder warp has read it
+        // seg_empty: one arrival per row of the box, once its builder warp has used it
         for (int i = 0; i < kNSeg; ++i) { mbar_init(seg_full(i), 1); mbar_init(seg_empty(i), kRB); }
         for (int i = 0; i < kNHG; ++i) { mbar_init(h_full(i), 32); mbar_init(h_empty(i), 1); }
         for (int i = 0; i < kNDG; ++i) { mbar_init(d_full(i), 1); mbar_init(d_empty(i), 128); }
@@ -245,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         *s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int i = threadIdx.x; i < BBYTES / 16; i += kThreads) ((uint4*)(sm + kOffB))[i] = bimg[i];
+    for (int i = threadIdx.x; i < S::BBYTES / 16; i += kThreads) ((uint4*)(sm + kOffB))[i] = bimg[i];
     fence_proxy_async_smem();
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -260,12 +297,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = *s_tmem;
 
     if (warp == 0) {
-        // ---- TMA producer ----
+        // ---- TMA producer: one box of kRB = kG rows per group ----
         if (lane == 0) {
             const int z = jptr ? *jptr : 0;
-            const int nch = (NR + kRB - 1) / kRB;
             int issued = 0;
-            for (int t = 0; t < nch; ++t) {
+            for (int t = 0; t < NG; ++t) {
                 const int sl = t % kNSeg;
                 if (!mbar_wait(seg_empty(sl), ((t / kNSeg) & 1) ^ 1, s_abort, err)) break;
                 mbar_expect_tx(seg_full(sl), kSegBytes);
@@ -276,26 +312,27 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int t = issued > kNSeg ? issued - kNSeg : 0; t < issued; ++t)
                 mbar_wait(seg_full(t % kNSeg), (t / kNSeg) & 1, s_abort, err, false);
         }
-    } else if (warp <= kIssuers) {
-        // ---- MMA issuers: groups g = warp - 1 (mod kIssuers) ----
+    } else if (warp <= 3 || warp == 12) {
+        // ---- MMA issuers: groups g = issuer (mod kIssuers) ----
         if (lane == 0) {
-            for (int g = warp - 1; g < NG; g += kIssuers) {
+            const int issuer = warp == 12 ? 3 : warp - 1;
+            for (int g = issuer; g < NG; g += kIssuers) {
                 const int hg = g % kNHG, dg = g % kNDG;
                 if (!mbar_wait(h_full(hg), (g / kNHG) & 1, s_abort, err)) break;
                 if (!mbar_wait(d_empty(dg), ((g / kNDG) & 1) ^ 1, s_abort, err)) break;
                 tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(dg * N);
+                const int rows = min(kG, NR - g * kG);
 #pragma unroll
                 for (int r = 0; r < kG; ++r) {
-                    const int i = g * kG + r;
-                    if (i < NR) {
+                    if (r < rows) {
                         const uint32_t a0 = sbase + kOffHank + (hg * kG + r) * kHankBytes;
-                        const uint32_t d = tmem + (uint32_t)((dg * kG + r) * N);
 #pragma unroll
                         for (int kk = 0; kk < KP / 16; ++kk) {
-                            const unsigned long long ad = smem_desc(a0 + kk * 256, 128, 128);
-                            const uint32_t bk = sbase + kOffB + kk * 2 * BLBO;
-                            mma_bf16(d, ad, smem_desc(bk, BLBO, 128), IDESC, kk > 0 ? 1u : 0u);
-                            mma_bf16(d, ad, smem_desc(bk + KP * 16, BLBO, 128), IDESC, 1u);
+                            const int c16 = r * (KP / 16) + kk;           // 16-wide K slice of the group
+                            mma_bf16(d, smem_desc(a0 + kk * 256, 128, 128),
+                                     smem_desc(sbase + kOffB + c16 * 2 * S::BLBO, S::BLBO, 128), IDESC,
+                                     c16 > 0 ? 1u : 0u);
                         }
                     }
                 }
@@ -306,16 +343,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             mma_commit(done_bar);
             mbar_wait(done_bar, 0, s_abort, err, false);
         }
-    } else if (warp >= 8) {
-        // ---- A builders: Hankel blocks from the staged rows, one group per warp ----
+    } else if (warp >= 8 && warp < 12) {
+        // ---- A builders: Hankel blocks from the staged box, one group per warp ----
         for (int g = warp - 8; g < NG; g += kBuilders) {
-            const int t = (g * kG) / kRB, sl = t % kNSeg, hg = g % kNHG;
-            if (!mbar_wait(seg_full(sl), (t / kNSeg) & 1, s_abort, err)) break;
+            const int sl = g % kNSeg, hg = g % kNHG;
+            if (!mbar_wait(seg_full(sl), (g / kNSeg) & 1, s_abort, err)) break;
             if (!mbar_wait(h_empty(hg), ((g / kNHG) & 1) ^ 1, s_abort, err)) break;
-            for (int r = 0; r < kG; ++r) {
-                const int i = g * kG + r;
-                if (i >= NR) break;
-                const uint32_t* src = (const uint32_t*)(sm + kOffSeg + sl * kSegBytes + (i - t * kRB) * kSegW * 2);
+            const int rows = min(kG, NR - g * kG);
+            for (int r = 0; r < rows; ++r) {
+                const uint32_t* src = (const uint32_t*)(sm + kOffSeg + sl * kSegBytes + r * kSegW * 2);
                 unsigned char* dst = sm + kOffHank + (hg * kG + r) * kHankBytes;
                 // all source words first (independent loads in flight together),
                 // then the byte permutes and 16-byte stores
@@ -352,52 +388,42 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_arrive(h_full(hg));
         }
     } else {
-        // ---- epilogue: overlap-add of the KW accumulator columns ----
-        // Before image row iy, acc[t] holds output row (iy - c + t) summed over
-        // the image rows above iy.  Row iy completes output row iy - c (tap
-        // a = KW - 1) and shifts the others down one slot while adding tap
-        // KW - 2 - t, so each tap is one FADD into a fixed register and the
-        // loop body stays small (a fully unrolled ring overflows the
-        // instruction cache).
+        // ---- epilogue ----
+        // Before group g (image rows iy0 = Ys + g G ..), acc[t] holds output
+        // row iy0 - c + t summed over the image rows above iy0 (t < KW - 1).
+        // With the group's columns, total[t] = acc[t] + D[G + KW - 2 - t]
+        // (hi + lo), t < NU; rows t < G are complete, the rest shift down by G.
         const int q = warp & 3;
         const int x = x0 + q * 32 + lane;
         const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
-        float acc[KW];
+        float acc[KW - 1];
 #pragma unroll
-        for (int t = 0; t < KW; ++t) acc[t] = 0.f;
+        for (int t = 0; t < KW - 1; ++t) acc[t] = 0.f;
         for (int g = 0; g < NG; ++g) {
             const int dg = g % kNDG;
             if (!__all_sync(0xffffffffu, mbar_wait(d_full(dg), (g / kNDG) & 1, s_abort, err))) break;
             tc_fence_after();
-            // two rows at a time keeps the loaded columns at 64 registers
+            uint32_t hi[NP], lo[NP];
+            tmem_ld_cols<NP>(tl + (uint32_t)(dg * N), hi);
+            tmem_ld_cols<NP>(tl + (uint32_t)(dg * N + NP), lo);
+            tmem_wait_ld();
+            tc_fence_before();
+            mbar_arrive(d_empty(dg));
+            float total[NU];
 #pragma unroll
-            for (int h = 0; h < kG; h += 2) {
-                uint32_t rr[2][32];
-#pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    if (g * kG + h + r < NR) {
-                        const uint32_t ta = tl + (uint32_t)((dg * kG + h + r) * N);
-                        if (KP == 32) tmem_ld32(ta, rr[r]); else tmem_ld16(ta, rr[r]);
-                    }
-                }
-                tmem_wait_ld();
-                if (h + 2 >= kG) {
-                    tc_fence_before();
-                    mbar_arrive(d_empty(dg));
-                }
-#pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    const int i = g * kG + h + r;
-                    if (i < NR) {
-                        const float out = acc[0] + __uint_as_float(rr[r][KW - 1]);
-#pragma unroll
-                        for (int t = 0; t < KW - 1; ++t) acc[t] = acc[t + 1] + __uint_as_float(rr[r][KW - 2 - t]);
-                        acc[KW - 1] = 0.f;
-                        const int y = Y0 + i - 2 * C;
-                        if (i >= 2 * C && y < yEnd && x < W) w[(size_t)y * W + x] = out;
-                    }
-                }
+            for (int t = 0; t < NU; ++t) {
+                const int j = kG + KW - 2 - t;
+                const float d = __uint_as_float(hi[j]) + __uint_as_float(lo[j]);
+                total[t] = t < KW - 1 ? acc[t] + d : d;
             }
+#pragma unroll
+            for (int t = 0; t < kG; ++t) {
+                const int i = g * kG + t;                         // completing image row
+                const int y = Y0 + i - 2 * C;
+                if (i < NR && i >= 2 * C && y < yEnd && x < W) w[(size_t)y * W + x] = total[t];
+            }
+#pragma unroll
+            for (int t = 0; t < KW - 1; ++t) acc[t] = total[t + kG];
         }
     }
 
@@ -448,7 +474,46 @@ cudaError_t launch_kp(const CUtensorMap& map, const int* jptr, float* w, int H, 
     return cudaGetLastError();
 }
 
+template <int KP>
+void build_operand(const std::function<float(int, int)>& F, std::vector<unsigned short>* img) {
+    using S = TcShape<KP>;
+    img->assign(S::BBYTES / 2, 0);
+    for (int n = 0; n < S::N; ++n) {
+        const bool lo = n >= S::NP;
+        const int j = lo ? n - S::NP : n;
+        for (int k = 0; k < S::KG; ++k) {
+            const int r = k / KP, b = k % KP;
+            const int a = r + j + 1 - kG;
+            float f = 0.f;
+            if (j < S::NU && a >= 0 && a < S::KW && b < S::KW) f = F(a, b);
+            const unsigned short h = bf16_bits_rn(f);
+            const unsigned short v = lo ? bf16_bits_rn(f - bf16_bits_to_float(h)) : h;
+            (*img)[(size_t)(k / 8) * S::N * 8 + (size_t)n * 8 + (k % 8)] = v;
+        }
+    }
+}
+
 }  // namespace
+
+unsigned short bf16_bits_rn(float f) {
+    unsigned u;
+    memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (unsigned short)(u >> 16);
+}
+
+float bf16_bits_to_float(unsigned short h) {
+    const unsigned u = (unsigned)h << 16;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
+int conv_tc_operand(int kw, const std::function<float(int, int)>& F, std::vector<unsigned short>* img) {
+    if (kw == 31) { build_operand<32>(F, img); return 32; }
+    if (kw == 15) { build_operand<16>(F, img); return 16; }
+    return 0;
+}
 
 bool conv_tc_eligible(const OpDev& op, const void* vbase, long long ldv) {
     if (op.kind != IPF_OP_PSF2D || !op.psf_tc || op.conv_fma) return false;
