@@ -33,11 +33,12 @@
 // and barrier test costs tens of cycles of issue latency in its thread).
 // Warp roles (416 threads, one CTA per SM): warp 0 issues the TMA loads;
 // warp 1 owns TMEM; one lane each of warps 1-3 and 12 issues the MMAs of
-// every fourth group; warps 8-11 build A (every fourth group); warps 4-7
-// read the accumulators (warp w reads TMEM lanes 32 (w % 4) ..) and finish
-// the output rows.  Each ring slot is waited on by one role instance only
-// (groups g = slot mod 4 for both the A and the accumulator rings), so a
-// parity wait can never match a phase two generations old.  Every wait is
+// every fourth group; warps 8-11 build A (every fourth group, two image rows
+// at a time); warps 4-7 read the accumulators (warp w reads TMEM lanes
+// 32 (w % 4) ..) and finish the output rows.  Each ring slot is waited on by
+// one role instance only (the slot counts are multiples of 4 and group g goes
+// to instance g mod 4), so a parity wait can never match a phase two
+// generations old.  Every wait is
 // bounded in time; on a timeout the
 // CTA stops issuing, drains its copies and MMAs, frees TMEM and reports
 // IPF_ERR_TIMEOUT.
@@ -60,10 +61,10 @@ constexpr int kIssuers = 4;          // MMA-issuing warps: 1, 2, 3, 12
 constexpr int kG = kConvTcGroup;     // image rows per MMA group
 constexpr int kSegW = 160;           // elements per staged row segment
 constexpr int kRB = 8;               // image rows per TMA box
-constexpr int kNSeg = 8;             // boxes in flight
-constexpr int kNHG = 4;              // A-operand groups in flight
+constexpr int kNSeg = 4;             // boxes in flight
+constexpr int kNHG = 8;              // A-operand groups in flight
 constexpr int kNDG = 4;              // accumulator groups in flight
-constexpr int kHankBytes = 2560;     // up to 20 blocks of 128 bytes
+constexpr int kHankBytes = 2432;     // up to 19 blocks of 128 bytes
 constexpr int kTmemCols = 512;
 constexpr int kSegBytes = kRB * kSegW * 2;
 constexpr int kBMax = 40960;         // B image bytes for KP = 32
@@ -76,7 +77,7 @@ constexpr int kOffMisc = kOffBar + 8 * kNBar;
 constexpr int kSmemUsed = kOffMisc + 16;
 constexpr int kSmemRequest = kSmemUsed + 1024;
 static_assert(kRB == kG, "one staged box per group");
-static_assert(kNHG % kIssuers == 0 && kNDG % kIssuers == 0 && kNHG % kBuilders == 0,
+static_assert(kNHG % kIssuers == 0 && kNDG % kIssuers == 0 && kNHG % kBuilders == 0 && kNSeg % kBuilders == 0,
               "each ring slot belongs to one issuer and one builder");
 static_assert(kSmemRequest > 116 * 1024 && kSmemRequest <= 227 * 1024, "one CTA per SM, within the SM");
 
@@ -350,39 +351,51 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!mbar_wait(seg_full(sl), (g / kNSeg) & 1, s_abort, err)) break;
             if (!mbar_wait(h_empty(hg), ((g / kNHG) & 1) ^ 1, s_abort, err)) break;
             const int rows = min(kG, NR - g * kG);
-            for (int r = 0; r < rows; ++r) {
-                const uint32_t* src = (const uint32_t*)(sm + kOffSeg + sl * kSegBytes + r * kSegW * 2);
-                unsigned char* dst = sm + kOffHank + (hg * kG + r) * kHankBytes;
-                // all source words first (independent loads in flight together),
-                // then the byte permutes and 16-byte stores
-                constexpr int NIT = (NQ * 8 + 31) / 32;
-                uint32_t wv[NIT][5];
+            constexpr int NIT = (NQ * 8 + 31) / 32;
+            for (int r0 = 0; r0 < rows; r0 += 2) {
+                // two image rows: all their source words first (independent
+                // loads in flight together), then the byte permutes and stores
+                uint32_t wv[2][NIT][5];
 #pragma unroll
-                for (int it = 0; it < NIT; ++it) {
-                    const int row = it * 32 + lane;
-                    const int e0 = OFF + 8 * (row >> 3) + (row & 7);
-                    const int wb = row < NQ * 8 ? (e0 >> 1) : 0;
+                for (int p = 0; p < 2; ++p) {
+                    const int r = min(r0 + p, rows - 1);
+                    const uint32_t* src = (const uint32_t*)(sm + kOffSeg + sl * kSegBytes + r * kSegW * 2);
 #pragma unroll
-                    for (int k = 0; k < 5; ++k) wv[it][k] = src[wb + k];
-                }
+                    for (int it = 0; it < NIT; ++it) {
+                        const int row = it * 32 + lane;
+                        const int e0 = OFF + 8 * (row >> 3) + (row & 7);
+                        const int wb = row < NQ * 8 ? (e0 >> 1) : 0;
 #pragma unroll
-                for (int it = 0; it < NIT; ++it) {
-                    const int row = it * 32 + lane;
-                    if (row < NQ * 8) {
-                        const int q = row >> 3, s = row & 7;
-                        const uint32_t sel = ((OFF + s) & 1) ? 0x5432u : 0x3210u;
-                        uint4 o;
-                        o.x = __byte_perm(wv[it][0], wv[it][1], sel);
-                        o.y = __byte_perm(wv[it][1], wv[it][2], sel);
-                        o.z = __byte_perm(wv[it][2], wv[it][3], sel);
-                        o.w = __byte_perm(wv[it][3], wv[it][4], sel);
-                        *(uint4*)(dst + q * 128 + s * 16) = o;
+                        for (int k = 0; k < 5; ++k) wv[p][it][k] = src[wb + k];
                     }
                 }
-                // every word read from the staged row has been consumed by a
-                // store: the row may be overwritten by the next box
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    if (r0 + p < rows) {
+                        unsigned char* dst = sm + kOffHank + (hg * kG + r0 + p) * kHankBytes;
+#pragma unroll
+                        for (int it = 0; it < NIT; ++it) {
+                            const int row = it * 32 + lane;
+                            if (row < NQ * 8) {
+                                const int q = row >> 3, s = row & 7;
+                                const uint32_t sel = ((OFF + s) & 1) ? 0x5432u : 0x3210u;
+                                uint4 o;
+                                o.x = __byte_perm(wv[p][it][0], wv[p][it][1], sel);
+                                o.y = __byte_perm(wv[p][it][1], wv[p][it][2], sel);
+                                o.z = __byte_perm(wv[p][it][2], wv[p][it][3], sel);
+                                o.w = __byte_perm(wv[p][it][3], wv[p][it][4], sel);
+                                *(uint4*)(dst + q * 128 + s * 16) = o;
+                            }
+                        }
+                    }
+                }
+                // every word read from the two staged rows has been consumed
+                // by a store: they may be overwritten by the next box
                 __syncwarp();
-                if (lane == 0) mbar_arrive(seg_empty(sl));
+                if (lane == 0) {
+                    mbar_arrive(seg_empty(sl));
+                    if (r0 + 1 < rows) mbar_arrive(seg_empty(sl));
+                }
             }
             fence_proxy_async_smem();
             mbar_arrive(h_full(hg));
