@@ -176,7 +176,7 @@ def run_ours(args, rank, world, torch, dist):
     def make_ctx(storage, profile):
         cfg = bd.default_config(k_max=k, m_s=p.m_s, zeta=p.zeta, seed=p.sketch_seed, storage=storage,
                                 profile=profile, use_graphs=0 if profile else 1, stream=stream.cuda_stream,
-                                overlap=1 if args.overlap else 0)
+                                overlap=args.overlap)
         return bd.Context(op, b_dev, cfg, keep)
 
     def timed_solves(ctx, x_out, steps, warmup, lam=(0.0,)):
@@ -315,7 +315,7 @@ def run_ours(args, rank, world, torch, dist):
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2: the BF16 basis is 1.69 GB (L2 129 MB)",
                    "launch": "eager launches with CUDA events around each kernel (profile mode)",
-                   "overlap": bool(args.overlap)},
+                   "overlap": args.overlap},
         "solves_per_s": world * args.steps / (t_max * 1e-3),
         "latency_ms": {"p50": float(np.percentile(per16, 50)), "p99": float(np.percentile(per16, 99))},
         "fp32": {"iters_per_s": steps32 * k / (t32 * 1e-3), "solves_per_s": steps32 / (t32 * 1e-3),
@@ -443,6 +443,14 @@ def run_serving(args, duration=None):
         for r in range(pr.nrhs):
             ct.append((op, pr.b[r:r + 1]))
 
+    def serve_cfg(kind):
+        kw = {}
+        if args.serve_overlap is not None:
+            kw["overlap"] = args.serve_overlap
+        if args.serve_conv_fma is not None:
+            kw["conv_fma"] = args.serve_conv_fma
+        return kw
+
     def draw(n_req):
         plan = []
         for _ in range(n_req):
@@ -455,7 +463,8 @@ def run_serving(args, duration=None):
             else:
                 op, b = ct[int(rng.integers(len(ct)))]
                 kind = "ct"
-            cfg = bd.default_config(k_max=k, m_s=4 * k, zeta=8, seed=int(rng.integers(1 << 30)), storage="bf16")
+            cfg = bd.default_config(k_max=k, m_s=4 * k, zeta=8, seed=int(rng.integers(1 << 30)), storage="bf16",
+                                    **serve_cfg(kind))
             plan.append((op, b, cfg, k, lam, kind))
         return plan
 
@@ -534,9 +543,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--overlap", action="store_true", help="operator on a second stream beside V_j h")
+    ap.add_argument("--overlap", type=int, default=2, choices=[0, 1, 2],
+                    help="second stream per step: 0 none, 1 operator beside V_j h, "
+                         "2 (library default) operator beside the pivot-block solve")
     ap.add_argument("--workload", default="deblur2048", choices=["deblur2048", "serving"])
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-overlap", type=int, default=None, choices=[0, 1, 2])
+    ap.add_argument("--serve-conv-fma", type=int, default=None, choices=[0, 1])
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the CT 32-RHS batch and the 5 s serving run on the default line")
     ap.add_argument("--small", default=None, choices=["f32", "bf16", "f16", "f64"],

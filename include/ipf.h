@@ -116,8 +116,10 @@ typedef struct ipf_config {
     int use_graphs;              /* capture each Hessenberg step in a CUDA graph            */
     int profile;                 /* bracket every kernel with CUDA events on the context's
                                     stream (launches eagerly; read with ipf_profile_read)   */
-    int overlap;                 /* PSF2D/CSR with float storage: run the operator on a
-                                    second stream beside V_j h (default 0: one stream)      */
+    int overlap;                 /* PSF2D/CSR with float storage, second stream per step:
+                                    0 one stream; 1 the operator beside V_j h; 2 (default)
+                                    the operator beside the pivot-row products and the
+                                    FP64 pivot-block solve                                   */
     int conv_fma;                /* PSF2D with BF16 storage: 0 (default) runs the product on
                                     the tensor cores when the PSF pads to 15x15 or 31x31 and
                                     cols % 8 == 0; 1 keeps the FP32 FMA convolution         */
@@ -138,7 +140,8 @@ typedef struct ipf_ctx ipf_ctx;
 typedef struct ipf_op ipf_op;
 
 /* Fill *cfg with defaults: k_max 50, m_s 200, zeta 8, seed 1, F32 storage,
- * sketched-x penalty, AUTO Z, nrhs 1, graphs on, default stream, cudaMalloc. */
+ * sketched-x penalty, AUTO Z, nrhs 1, graphs on, overlap 2, tensor-core
+ * convolution where it applies, default stream, cudaMalloc.               */
 void ipf_config_default(ipf_config* cfg);
 
 /* Bytes of device memory ipf_create would allocate for this problem
@@ -200,8 +203,8 @@ ipf_status ipf_solve(ipf_ctx* ctx, int k, const double* lambdas, int nl,
  * solve + x = V_k y, 7 operator at the pivot rows, 8 u = A v_j - V_j h with
  * argmax) the summed milliseconds, launch counts and the summed algorithmic
  * bytes of the launches (0 where not defined), since the previous read.
- * With config.overlap a step runs the operator on a second stream beside
- * V_j h, so kinds 0 and 2 overlap in time.
+ * With config.overlap 1 a step runs the operator on a second stream beside
+ * V_j h, so kinds 0 and 2 overlap in time; with overlap 2, kinds 0, 7 and 1.
  * Arrays of 10 entries, host; synchronises.                               */
 ipf_status ipf_profile_read(ipf_ctx* ctx, double* ms, long long* launches, double* bytes);
 
@@ -286,7 +289,8 @@ typedef struct ipf_result {
  * left of the budget (first come, first served), runs each in its own
  * context and streams (so in-flight requests overlap on the GPU), tops each
  * up with steps_per_slice Hessenberg steps whenever its previous slice has
- * finished, then solves at k with lambda and copies x to the host.  All
+ * finished, then solves at k with lambda and copies x to the host.  Each
+ * request's steps run on one stream (its config.overlap is taken as 0).  All
  * device memory comes from one arena reserved here, so admission and
  * retirement allocate nothing.  Errors: IPF_ERR_ARG, IPF_ERR_OOM (budget
  * cannot be reserved), IPF_ERR_CUDA.                                     */

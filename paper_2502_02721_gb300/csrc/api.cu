@@ -206,6 +206,7 @@ struct ipf_ctx {
     cudaEvent_t ev = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool split = false;                 // operator overlapped with the V_j stream
+    bool fork_piv = false;              // operator overlapped with the pivot-block solve
     int j_host = 0;                    // Hessenberg steps enqueued
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -342,6 +343,32 @@ cudaError_t one_step(ipf_ctx* c, int j) {
         return timed(c, 3, N * ab + N * sv,
                      [&] { return launch_normalize(c->storage, c->g, c->bf, c->sp, sw_on(c), c->num_sms, c->s); });
     }
+    if (c->fork_piv) {
+        // the operator on s2 beside the pivot-row products and the FP64
+        // pivot-block solve on s (which need only v_j and the pivots), joined
+        // before the update that consumes both
+        if ((e = cudaEventRecord(c->ev_fork, c->s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(c->s2, c->ev_fork, 0)) != cudaSuccess) return e;
+        if ((e = timed_on(c, c->s2, 0, op_bytes(c), [&] {
+                 return launch_op_apply(c->op, c->storage, c->bf.V, c->g.ldv, c->g.k_max + 1, &c->bf.st->j, c->B,
+                                        c->bf.w, c->bf.st->status, c->s2);
+             })) != cudaSuccess)
+            return e;
+        if ((e = cudaEventRecord(c->ev_join, c->s2)) != cudaSuccess) return e;
+        if ((e = timed(c, 7, 0.0, [&] {
+                 return launch_pivot_rows(c->op, c->storage, c->bf.V, c->g.ldv, c->bf.st, c->bf.piv, c->B, c->g.k_max,
+                                          c->bf.gpiv, c->s);
+             })) != cudaSuccess)
+            return e;
+        if ((e = timed(c, 1, 0.0, [&] { return launch_pivot_solve(c->storage, c->g, c->bf, c->s); })) != cudaSuccess)
+            return e;
+        if ((e = cudaStreamWaitEvent(c->s, c->ev_join, 0)) != cudaSuccess) return e;
+        if ((e = timed(c, 2, (double)(j + 1) * N * sv + 2.0 * N * ab + N / 8.0,
+                       [&] { return launch_update(c->storage, c->g, c->bf, c->num_sms, c->s); })) != cudaSuccess)
+            return e;
+        return timed(c, 3, N * ab + N * sv,
+                     [&] { return launch_normalize(c->storage, c->g, c->bf, c->sp, sw_on(c), c->num_sms, c->s); });
+    }
     if ((e = timed(c, 0, op_bytes(c), [&] {
              return launch_op_apply(c->op, c->storage, c->bf.V, c->g.ldv, c->g.k_max + 1, &c->bf.st->j, c->B, c->bf.w,
                                     c->bf.st->status, c->s);
@@ -389,6 +416,7 @@ void ipf_config_default(ipf_config* cfg) {
     cfg->storage = IPF_STORE_F32;
     cfg->penalty = IPF_PEN_SKETCHED_X;
     cfg->zform = IPF_Z_AUTO;
+    cfg->overlap = 2;
     cfg->nrhs = 1;
     cfg->use_graphs = 1;
 }
@@ -473,7 +501,8 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     CK("event", cudaEventCreateWithFlags(&c->ev, cudaEventDisableTiming));
     CK("event", cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
     CK("event", cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
-    c->split = cfg.overlap && (op->kind == IPF_OP_PSF2D || op->kind == IPF_OP_CSR) && cfg.storage != IPF_STORE_F64;
+    c->split = cfg.overlap == 1 && (op->kind == IPF_OP_PSF2D || op->kind == IPF_OP_CSR) && cfg.storage != IPF_STORE_F64;
+    c->fork_piv = cfg.overlap == 2 && (op->kind == IPF_OP_PSF2D || op->kind == IPF_OP_CSR) && cfg.storage != IPF_STORE_F64;
     CK("order", enter(c));
     CK("operator upload", upload_op(op, c->al, &c->op, c->s));
     c->op.conv_fma = cfg.conv_fma ? 1 : 0;
@@ -505,9 +534,9 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     bf.gpiv = nullptr;
     if (c->split) {
         CK("alloc t", c->al.get((void**)&bf.t, g.ldv * sizeof(float)));
-        CK("alloc g", c->al.get((void**)&bf.gpiv, B * K1 * sizeof(float)));
         CK("memset t", cudaMemsetAsync(bf.t, 0, g.ldv * sizeof(float), c->s));
     }
+    if (c->split || c->fork_piv) CK("alloc g", c->al.get((void**)&bf.gpiv, B * K1 * sizeof(float)));
     if (sketch_table_ok(c->sp)) {
         unsigned long long* tab = nullptr;
         CK("alloc sketch table", c->al.get((void**)&tab, sizeof(unsigned long long) * (size_t)n));

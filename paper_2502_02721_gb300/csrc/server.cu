@@ -161,6 +161,10 @@ bool ipf_server::admit(Job* j) {
     c.alloc_user = &arena;
     c.stream = j->us;                                  // order against this request only
     c.profile = 0;
+    // requests in flight already overlap with one another; a second stream
+    // per step only adds launches and events (measured: lower capacity and
+    // higher latency under load), so every request steps on one stream
+    c.overlap = 0;
     ipf_ctx* ctx = nullptr;
     ipf_status st = ipf_create(&j->op, j->b.data(), IPF_MEM_HOST, &c, &ctx);
     if (st == IPF_ERR_OOM || (st == IPF_OK && !(j->x_dev = (float*)arena.get(xb)))) {

@@ -87,6 +87,30 @@ def test_deblur64_low_precision(deblur64, storage, conv_fma):
     ctx.close()
 
 
+@pytest.mark.parametrize("storage,overlap", [("f32", 0), ("f32", 1), ("f32", 2), ("bf16", 0), ("bf16", 2)])
+def test_step_modes_match_oracle(deblur64, storage, overlap):
+    """The one-stream step and the two-stream steps (operator beside V_j h, or
+    beside the pivot-row products and the FP64 pivot-block solve) against the
+    oracle, with graph replay and eager launches giving the same bits."""
+    p, st = deblur64
+    xs = []
+    for graphs in (1, 0):
+        ctx = gpu_context(p, storage, graphs=graphs, overlap=overlap)
+        ctx.step(p.k)
+        status, kd = ctx.sync()
+        assert kd == [p.k]
+        ex = ctx.export(0)
+        agree = compare_pivots(ex["piv"][:p.k + 1], st, storage)
+        if storage == "f32":
+            assert agree == p.k + 1
+            compare_solution(ctx, st, storage, [1, 5, 20, 50], p.lambdas)
+        else:
+            compare_solution(ctx, st, storage, [kk for kk in (1, 2, 3) if kk < agree], [0.0])
+        xs.append(ctx.solve(p.k, [0.0])[0])
+        ctx.close()
+    assert np.array_equal(xs[0], xs[1])
+
+
 def test_zforms_agree_f32(deblur64):
     from paper_2502_02721_gb300 import binding as bd
     p, st = deblur64
