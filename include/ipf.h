@@ -71,7 +71,7 @@ enum ipf_storage { IPF_STORE_F64 = 0, IPF_STORE_F32 = 1, IPF_STORE_BF16 = 2, IPF
 enum ipf_penalty { IPF_PEN_SKETCHED_X = 0, IPF_PEN_Y = 1 };
 
 /* How S A V_k is assembled: DIRECT sketches each product u = A v_j before
- * the elimination (Algorithm 1 line 11, z_k = S u), HESSENBERG uses
+ * the elimination (the sketched product of Algorithm 1, z_k = S u), HESSENBERG uses
  * S V_{k+1} H_k.  They agree in exact arithmetic; with BF16/FP16 storage
  * DIRECT is the sketched objective over the stored basis (the sketch of
  * each product is assembled by linearity from S of the stored basis and S
@@ -168,8 +168,8 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem,
  * nothing.  Clears a sticky error only if it was IPF_ERR_NONFINITE.        */
 ipf_status ipf_reset(ipf_ctx* ctx, const float* b, int b_mem);
 
-/* Enqueue nsteps Hessenberg steps (Algorithm 1 lines 10-19, square form):
- * u = A v_j; h = L_p^{-1} u(p) (the sequential elimination of lines 12-14
+/* Enqueue nsteps Hessenberg steps (the loop of Algorithm 1, square form):
+ * u = A v_j; h = L_p^{-1} u(p) (the sequential elimination of Algorithm 1
  * as a unit-lower forward substitution on the pivot rows, FP64);
  * u -= V_j h with the pivot rows set to 0; p_{j+1} = argmax |u| over
  * non-pivot rows (lowest index on ties); H(j+1, j) = u(p_{j+1});

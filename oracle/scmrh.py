@@ -5,8 +5,8 @@ Paper, Sec. 3.1, Eq. (Hessenberg_s): A L_k = L_{k+1} H_{k+1,k} with L unit
 lower triangular after the pivot permutation and range(L_k) = K_k(A, b).
 Sec. 3.2, Eq. (sketched_LSLU): y_k = argmin_y ||S (A L_k y - b)||, x_k = L_k y_k
 with x_0 = 0.  Algorithm 1 gives the loop (written there for the generalized
-process; the square process applies A where Algorithm 1 line 9 prints A^T,
-and names the new vector v_{j+1} where it prints d_k).  Sec. 3.3 /
+process; the square process applies A where Algorithm 1 applies A^T to the
+left vector, and calls the new vector v_{j+1} where it reuses the name d_k).  Sec. 3.3 /
 Algorithm 2 add the penalty lambda^2 ||S_1 L_k y||^2; for a square A one
 sketch S serves as both S_1 and S_2.
 

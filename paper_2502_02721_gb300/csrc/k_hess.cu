@@ -1,6 +1,6 @@
 // One step of the pivoted Hessenberg process with its sketch (Sec. 3.1 Eq.
-// Hessenberg_s; Algorithm 1 lines 10-19 in the square form, A in place of
-// the A^T the listing prints on line 9):
+// Hessenberg_s; the loop of Algorithm 1 in the square form, applying A where
+// the algorithm, written for the generalized process, applies A^T):
 //
 //   k_pivot_solve   append row p_j of L_p; h = L_p^{-1} u(p_1..p_j) in FP64
 //                   (the sequential elimination H(i,j) = u(p_i),

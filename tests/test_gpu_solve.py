@@ -40,7 +40,7 @@ def test_deblur64_parity(deblur64, storage):
     assert rel(ex["SV"][:, 0], st.SV[:, 0]) < (1e-12 if storage == "f64" else 1e-6)
     assert rel(ex["c"], st.c) < (1e-12 if storage == "f64" else 1e-6)
     if storage == "f32":
-        # z_j = S A v_j (Algorithm 1 line 11).  z_0 involves one FP32 product;
+        # z_j = S A v_j (the sketched product of Algorithm 1).  z_0 involves one FP32 product;
         # later columns inherit the drift of individual basis vectors, which
         # is larger than that of x_k (errors inside the Krylov subspace leave
         # x_k unchanged), hence the looser bound
