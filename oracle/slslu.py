@@ -61,10 +61,16 @@ class GenHessenbergState:
     k_done: int              # completed steps: d_1..d_{k+1}, l_1..l_k at least
     l_done: int              # columns of L formed
     breakdown: bool
+    gaps_t: list             # pivot-gap ratio (|u|_(1) - |u|_(2)) / |u|_(1) per pivot of D
+    gaps_g: list             # the same for the pivots of L
 
 
-def iterate(apply_A, apply_At, b, S1, S2, k_max: int):
-    """Yields (k, state) after the initialisation (k = 0) and after each step."""
+def iterate(apply_A, apply_At, b, S1, S2, k_max: int, forced_t=None, forced_g=None):
+    """Yields (k, state) after the initialisation (k = 0) and after each step.
+
+    forced_t / forced_g: optional pivot sequences to use instead of the
+    max-|.| choice (replays another run's order where two candidates are
+    within rounding of each other)."""
     b = np.asarray(b, dtype=np.float64).reshape(-1)
     m = b.size
     v0 = apply_At(b)
@@ -81,12 +87,21 @@ def iterate(apply_A, apply_At, b, S1, S2, k_max: int):
     gpiv = np.zeros(n, dtype=bool)
     c = S2.apply(b)
     pt, pg = [], []
+    gaps_t, gaps_g = [], []
 
     def state(k, beta, alpha, l_done, breakdown):
         return GenHessenbergState(D[:, :k + 1], L[:, :k + 1], H[:k + 1, :k], W[:k + 1, :k + 1], list(pt), list(pg),
-                                  SD[:, :k + 1], SL[:, :k + 1], Zd[:, :k], c, beta, alpha, k, l_done, breakdown)
+                                  SD[:, :k + 1], SL[:, :k + 1], Zd[:, :k], c, beta, alpha, k, l_done, breakdown,
+                                  list(gaps_t), list(gaps_g))
 
-    i, _, _ = _argmax_abs_excluding(b, tpiv)
+    def choose(vec, is_piv, forced, idx, gaps):
+        i_max, _, gap = _argmax_abs_excluding(vec, is_piv)
+        gaps.append(gap)
+        if forced is not None and idx < len(forced):
+            return int(forced[idx])
+        return i_max
+
+    i = choose(b, tpiv, forced_t, 0, gaps_t)
     beta = float(b[i])
     if beta == 0.0:
         yield 0, state(0, 0.0, 0.0, 0, True)
@@ -95,7 +110,7 @@ def iterate(apply_A, apply_At, b, S1, S2, k_max: int):
     pt.append(i)
     tpiv[i] = True
     SD[:, 0] = S2.apply(D[:, 0])
-    i2, _, _ = _argmax_abs_excluding(v0, gpiv)
+    i2 = choose(v0, gpiv, forced_g, 0, gaps_g)
     alpha = float(v0[i2])
     if alpha == 0.0:
         yield 0, state(0, beta, 0.0, 0, True)
@@ -118,7 +133,7 @@ def iterate(apply_A, apply_At, b, S1, S2, k_max: int):
             H[k + 1, k] = 0.0
             yield k + 1, state(k + 1, beta, alpha, k + 1, True)
             return
-        p, _, _ = _argmax_abs_excluding(u, tpiv)
+        p = choose(u, tpiv, forced_t, k + 1, gaps_t)
         H[k + 1, k] = u[p]
         D[:, k + 1] = u / H[k + 1, k]
         pt.append(p)
@@ -133,7 +148,7 @@ def iterate(apply_A, apply_At, b, S1, S2, k_max: int):
         if k + 1 >= n or not np.any(q):
             yield k + 1, state(k + 1, beta, alpha, k + 1, True)
             return
-        p2, _, _ = _argmax_abs_excluding(q, gpiv)
+        p2 = choose(q, gpiv, forced_g, k + 1, gaps_g)
         W[k + 1, k + 1] = q[p2]
         L[:, k + 1] = q / W[k + 1, k + 1]
         pg.append(p2)
@@ -142,9 +157,9 @@ def iterate(apply_A, apply_At, b, S1, S2, k_max: int):
         yield k + 1, state(k + 1, beta, alpha, k + 2, False)
 
 
-def run(apply_A, apply_At, b, S1, S2, k_max: int) -> GenHessenbergState:
+def run(apply_A, apply_At, b, S1, S2, k_max: int, forced_t=None, forced_g=None) -> GenHessenbergState:
     st = None
-    for _, st in iterate(apply_A, apply_At, b, S1, S2, k_max):
+    for _, st in iterate(apply_A, apply_At, b, S1, S2, k_max, forced_t, forced_g):
         pass
     return st
 
