@@ -79,6 +79,22 @@ enum ipf_penalty { IPF_PEN_SKETCHED_X = 0, IPF_PEN_Y = 1 };
  * BF16/FP16).  DIRECT needs float storage.  AUTO uses HESSENBERG.          */
 enum ipf_zform { IPF_Z_DIRECT = 0, IPF_Z_HESSENBERG = 1, IPF_Z_AUTO = 2 };
 
+/* Which process builds the basis.
+ * SCMRH  the pivoted Hessenberg process on a square A (Sec. 3.1 Eq.
+ *        Hessenberg_s): x_k in K_k(A, b).
+ * SLSLU  the generalized Hessenberg process (Sec. 3.1 Eq. Hessenberg_r;
+ *        Algorithm 1, Algorithm 2) for any m x n PSF2D or CSR operator:
+ *        A L_k = D_{k+1} H_{k+1,k} and A^T D_{k+1} = L_{k+1} W_{k+1} with two
+ *        pivoted unit lower trapezoidal bases, D in R^m and L in R^n, and
+ *        x_k = L_k y_k in K_k(A^T A, A^T b).  Each step applies A to l_k and
+ *        A^T to d_{k+1}; S_2 (l x m, config.seed) sketches D, S_1 (l x n,
+ *        seed config.seed XOR 0x5DEECE66DA3B1F27) sketches L; y minimises ||S_2 (A L_k y - b)||^2 +
+ *        lambda^2 ||S_1 L_k y||^2.  b has m entries per RHS, x has n.  A^T is
+ *        the convolution with the flipped PSF, or the CSR transpose (built on
+ *        the host at create).  Steps run on one stream (config.overlap is
+ *        ignored); the penalty is always the sketched-x form.               */
+enum ipf_method { IPF_METHOD_SCMRH = 0, IPF_METHOD_SLSLU = 1 };
+
 /* Forward operator.  For PSF kinds n = rows*cols and images are row-major.
  * For CSR, rows x cols is m x n and the method needs m == n (square A).
  * mem says where psf/sep_row/sep_col/motion/rowptr/colind/vals live:
@@ -120,6 +136,7 @@ typedef struct ipf_config {
                                     0 one stream; 1 the operator beside V_j h; 2 (default)
                                     the operator beside the pivot-row products and the
                                     FP64 pivot-block solve                                   */
+    int method;                  /* enum ipf_method (default IPF_METHOD_SCMRH)               */
     int conv_fma;                /* PSF2D with BF16 storage: 0 (default) runs the product on
                                     the tensor cores when the PSF pads to 15x15 or 31x31 and
                                     cols % 8 == 0; 1 keeps the FP32 FMA convolution         */
@@ -219,6 +236,17 @@ ipf_status ipf_export(ipf_ctx* ctx, int r, int* pivots, double* H, double* SV, d
 
 /* Copy basis vector j (0-based, j <= k_done) of RHS r as float32 (host). */
 ipf_status ipf_export_basis(ipf_ctx* ctx, int r, int j, float* v_out);
+
+/* SLSLU contexts: the second basis.  ipf_export and ipf_export_basis give
+ * the D side (pivots t, H, S_2 D, c = S_2 b, beta); these give the L side:
+ * pivots g (k_max + 1 entries, -1 past the last), a (k_max + 1) x k_max
+ * column-major table of W (Eq. Hessenberg_r) whose column c (0-based) holds
+ * W(1..c+1, c+2), the coefficients of q = A^T d_{c+2} on l_1..l_{c+1}, in
+ * rows 0..c and the pivot W(c+2, c+2) in row c+1, S_1 L ((k_max + 1) x m_s),
+ * and W(1, 1) = (A^T d_1)(g_1).  ipf_export_basis_l writes column j of L (n
+ * floats).  IPF_ERR_STATE for SCMRH contexts.                             */
+ipf_status ipf_export_dual(ipf_ctx* ctx, int r, int* pivots_l, double* W, double* SL, double* w11);
+ipf_status ipf_export_basis_l(ipf_ctx* ctx, int r, int j, float* l_out);
 
 void ipf_destroy(ipf_ctx* ctx);
 const char* ipf_status_str(ipf_status s);

@@ -44,10 +44,14 @@ ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
 
+METHOD = {"scmrh": 0, "slslu": 1}
+
+
 class ipf_config(C.Structure):
     _fields_ = [("k_max", C.c_int), ("m_s", C.c_int), ("zeta", C.c_int), ("seed", C.c_ulonglong),
                 ("storage", C.c_int), ("penalty", C.c_int), ("zform", C.c_int), ("nrhs", C.c_int),
-                ("use_graphs", C.c_int), ("profile", C.c_int), ("overlap", C.c_int), ("conv_fma", C.c_int),
+                ("use_graphs", C.c_int), ("profile", C.c_int), ("overlap", C.c_int), ("method", C.c_int),
+                ("conv_fma", C.c_int),
                 ("stream", C.c_void_p),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
 
@@ -90,6 +94,8 @@ SIGNATURES = {
     "ipf_last_error": (C.c_char_p, [C.c_void_p]),
     "ipf_op_create": (C.c_int, [C.POINTER(ipf_operator), C.POINTER(C.c_void_p)]),
     "ipf_op_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "ipf_export_dual": (C.c_int, [C.c_void_p, C.c_int, _ip, _dp, _dp, _dp]),
+    "ipf_export_basis_l": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _fp]),
     "ipf_op_apply_bf16": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "ipf_op_destroy": (None, [C.c_void_p]),
     "ipf_sketch_apply": (C.c_int, [C.c_void_p, C.c_longlong, C.c_int, C.c_int, C.c_ulonglong, C.c_void_p,
@@ -213,6 +219,8 @@ def default_config(**kw) -> ipf_config:
     for k, v in kw.items():
         if k == "storage" and isinstance(v, str):
             v = STORAGE[v]
+        if k == "method" and isinstance(v, str):
+            v = METHOD[v]
         setattr(cfg, k, v)
     return cfg
 
@@ -227,8 +235,11 @@ class Context:
             b = np.ascontiguousarray(b, dtype=np.float32)
         self.cfg = cfg
         self.nrhs = cfg.nrhs
+        # x has n entries per RHS; b has m (= n except for a rectangular CSR
+        # operator under the generalized process)
         self.n = op.cols if op.kind == IPF_OP_CSR else op.rows * op.cols
-        _check_size(b, self.nrhs * self.n, "b")
+        self.m = op.rows if (op.kind == IPF_OP_CSR and cfg.method == METHOD["slslu"]) else self.n
+        _check_size(b, self.nrhs * self.m, "b")
         self._keep.append(b)
         ptr, mem = _ptr(b)
         h = C.c_void_p()
@@ -247,7 +258,7 @@ class Context:
         if isinstance(b, np.ndarray):
             b = np.ascontiguousarray(b, dtype=np.float32)
             self._keep.append(b)
-        _check_size(b, self.nrhs * self.n, "b")
+        _check_size(b, self.nrhs * self.m, "b")
         ptr, mem = _ptr(b)
         self._check(self._lib.ipf_reset(self.h, ptr, mem), "ipf_reset")
 
@@ -303,8 +314,28 @@ class Context:
                 "SZ": SZ.reshape(self.cfg.k_max, self.cfg.m_s).T, "c": c, "beta": float(beta[0])}
 
     def basis(self, j: int, r: int = 0) -> np.ndarray:
-        v = np.zeros(self.n, dtype=np.float32)
+        """Column j of the basis (D for the generalized process)."""
+        v = np.zeros(self.m, dtype=np.float32)
         self._check(self._lib.ipf_export_basis(self.h, r, j, v.ctypes.data_as(_fp)), "ipf_export_basis")
+        return v
+
+    def export_dual(self, r: int = 0):
+        """Generalized process: pivots of L, the W table, S_1 L and W(1,1)."""
+        K1 = self.cfg.k_max + 1
+        piv = np.zeros(K1, dtype=np.int32)
+        W = np.zeros(K1 * self.cfg.k_max, dtype=np.float64)
+        SL = np.zeros(K1 * self.cfg.m_s, dtype=np.float64)
+        w11 = np.zeros(1, dtype=np.float64)
+        st = self._lib.ipf_export_dual(self.h, r, piv.ctypes.data_as(_ip), W.ctypes.data_as(_dp),
+                                       SL.ctypes.data_as(_dp), w11.ctypes.data_as(_dp))
+        self._check(st, "ipf_export_dual")
+        return {"piv": piv, "W": W.reshape(self.cfg.k_max, K1).T, "SL": SL.reshape(K1, self.cfg.m_s).T,
+                "w11": float(w11[0])}
+
+    def basis_l(self, j: int, r: int = 0) -> np.ndarray:
+        """Column j of the L basis of the generalized process (n floats)."""
+        v = np.zeros(self.n, dtype=np.float32)
+        self._check(self._lib.ipf_export_basis_l(self.h, r, j, v.ctypes.data_as(_fp)), "ipf_export_basis_l")
         return v
 
     def close(self):

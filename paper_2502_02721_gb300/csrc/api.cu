@@ -40,6 +40,12 @@ long long op_n(const ipf_operator* op) {
     return (long long)op->rows * op->cols;
 }
 
+// length of A's output (the m-space of the generalized process)
+long long op_m(const ipf_operator* op) {
+    if (op->kind == IPF_OP_CSR) return op->rows;
+    return (long long)op->rows * op->cols;
+}
+
 struct Alloc {
     ipf_alloc_fn fa = nullptr;
     ipf_free_fn ff = nullptr;
@@ -188,6 +194,65 @@ cudaError_t upload_op(const ipf_operator* op, Alloc& al, OpDev* d, cudaStream_t 
     return e;
 }
 
+// upload A^T: the convolution with the flipped PSF, or the CSR transpose
+// (built on the host; device CSR arrays are read back once)
+cudaError_t upload_transpose(const ipf_operator* op, Alloc& al, OpDev* d, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    ipf_operator t = *op;
+    t.mem = IPF_MEM_HOST;
+    if (op->kind == IPF_OP_PSF2D) {
+        const size_t np = (size_t)op->ph * op->pw;
+        std::vector<float> P(np), Pf(np);
+        if (op->mem == IPF_MEM_HOST) memcpy(P.data(), op->psf, np * sizeof(float));
+        else if ((e = cudaMemcpy(P.data(), op->psf, np * sizeof(float), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return e;
+        for (int a = 0; a < op->ph; ++a)
+            for (int b = 0; b < op->pw; ++b)
+                Pf[(size_t)a * op->pw + b] = P[(size_t)(op->ph - 1 - a) * op->pw + (op->pw - 1 - b)];
+        t.psf = Pf.data();
+        if ((e = upload_op(&t, al, d, s)) != cudaSuccess) return e;
+        return cudaStreamSynchronize(s);
+    }
+    if (op->kind != IPF_OP_CSR) return cudaErrorInvalidValue;
+    const int m = op->rows, n = op->cols;
+    const long long nnz = op->nnz;
+    std::vector<long long> rp(m + 1);
+    std::vector<int> ci(nnz > 0 ? nnz : 1);
+    std::vector<float> va(nnz > 0 ? nnz : 1);
+    if (op->mem == IPF_MEM_HOST) {
+        memcpy(rp.data(), op->rowptr, sizeof(long long) * (m + 1));
+        if (nnz) memcpy(ci.data(), op->colind, sizeof(int) * nnz);
+        if (nnz) memcpy(va.data(), op->vals, sizeof(float) * nnz);
+    } else {
+        if ((e = cudaMemcpy(rp.data(), op->rowptr, sizeof(long long) * (m + 1), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return e;
+        if (nnz && (e = cudaMemcpy(ci.data(), op->colind, sizeof(int) * nnz, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return e;
+        if (nnz && (e = cudaMemcpy(va.data(), op->vals, sizeof(float) * nnz, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return e;
+    }
+    // counting sort by column; entries of a column keep their row order
+    std::vector<long long> rpT(n + 1, 0);
+    for (long long t2 = 0; t2 < nnz; ++t2) ++rpT[ci[t2] + 1];
+    for (int c2 = 0; c2 < n; ++c2) rpT[c2 + 1] += rpT[c2];
+    std::vector<long long> fill(rpT.begin(), rpT.end() - 1);
+    std::vector<int> ciT(nnz > 0 ? nnz : 1);
+    std::vector<float> vaT(nnz > 0 ? nnz : 1);
+    for (int r = 0; r < m; ++r)
+        for (long long t2 = rp[r]; t2 < rp[r + 1]; ++t2) {
+            const long long dst = fill[ci[t2]]++;
+            ciT[dst] = r;
+            vaT[dst] = va[t2];
+        }
+    t.rows = n;
+    t.cols = m;
+    t.rowptr = rpT.data();
+    t.colind = ciT.data();
+    t.vals = vaT.data();
+    if ((e = upload_op(&t, al, d, s)) != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
+
 }  // namespace
 
 struct ipf_ctx {
@@ -207,6 +272,13 @@ struct ipf_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool split = false;                 // operator overlapped with the V_j stream
     bool fork_piv = false;              // operator overlapped with the pivot-block solve
+    // generalized process (SLSLU): g/bf/sp/op are the D side (m-space, A),
+    // these the L side (n-space, A^T)
+    bool gh = false;
+    OpDev opT;
+    Geom g2;
+    Bufs bf2;
+    SketchParams sp2;
     int j_host = 0;                    // Hessenberg steps enqueued
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
@@ -311,8 +383,35 @@ bool sw_on(const ipf_ctx* c) {
 // one Hessenberg step; every kernel takes j from device memory, so the same
 // sequence serves every step and can be captured once.  `j` (host count) is
 // only used to label profile bytes.
+// half of a generalized step: the operator applied to the other basis's
+// newest column, then this basis's elimination, update and normalisation
+cudaError_t half_step(ipf_ctx* c, const OpDev& op, const Bufs& in, const Geom& gin, const Geom& g, const Bufs& bf,
+                      const SketchParams& sp, int j) {
+    cudaError_t e;
+    const double N = (double)g.N, sv = (double)storage_bytes(c->storage), ab = (double)acc_bytes(c);
+    const double ob = (double)gin.N * sv + N * ab +
+                      (op.kind == IPF_OP_CSR ? (double)op.nnz * 8.0 + (double)(op.rows + 1) * 8.0 : 0.0);
+    if ((e = timed(c, 0, ob, [&] {
+             return launch_op_apply(op, c->storage, in.V, gin.ldv, gin.k_max + 1, &in.st->j, c->B, bf.w,
+                                    bf.st->status, c->s);
+         })) != cudaSuccess)
+        return e;
+    if ((e = timed(c, 1, 0.0, [&] { return launch_pivot_solve(c->storage, g, bf, c->s); })) != cudaSuccess) return e;
+    if ((e = timed(c, 2, (double)(j + 1) * N * sv + 2.0 * N * ab + N / 8.0,
+                   [&] { return launch_update(c->storage, g, bf, c->num_sms, c->s); })) != cudaSuccess)
+        return e;
+    return timed(c, 3, N * ab + N * sv,
+                 [&] { return launch_normalize(c->storage, g, bf, sp, false, c->num_sms, c->s); });
+}
+
 cudaError_t one_step(ipf_ctx* c, int j) {
     cudaError_t e;
+    if (c->gh) {
+        // u = A l_k eliminated against D (d_{k+1}), then q = A^T d_{k+1}
+        // eliminated against L (l_{k+1})
+        if ((e = half_step(c, c->op, c->bf2, c->g2, c->g, c->bf, c->sp, j)) != cudaSuccess) return e;
+        return half_step(c, c->opT, c->bf, c->g, c->g2, c->bf2, c->sp2, j);
+    }
     const double N = (double)c->g.N, sv = (double)storage_bytes(c->storage), ab = (double)acc_bytes(c);
     if (c->split) {
         // h first (products at the pivot rows + FP64 pivot-block solve, small),
@@ -393,12 +492,33 @@ cudaError_t init_solve(ipf_ctx* c, const float* bdev) {
     if ((e = cudaMemsetAsync(c->bf.ispiv, 0, (g.ldv / 32 + 1) * sizeof(unsigned), c->s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->bf.accSV, 0, B * K1 * g.m_s * sizeof(long long), c->s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->bf.accSW, 0, B * K1 * g.m_s * sizeof(long long), c->s)) != cudaSuccess) return e;
-    return timed(c, 4, 0.0, [&] {
+    if (c->gh) {
+        const Geom& g2 = c->g2;
+        if ((e = cudaMemsetAsync(c->bf2.H, 0, B * K1 * g2.k_max * sizeof(double), c->s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(c->bf2.ispiv, 0, (g2.ldv / 32 + 1) * sizeof(unsigned), c->s)) != cudaSuccess)
+            return e;
+        if ((e = cudaMemsetAsync(c->bf2.accSV, 0, B * K1 * g2.m_s * sizeof(long long), c->s)) != cudaSuccess)
+            return e;
+        if ((e = cudaMemsetAsync(c->bf2.accSW, 0, B * K1 * g2.m_s * sizeof(long long), c->s)) != cudaSuccess)
+            return e;
+        if ((e = launch_reset_state(c->bf2.st, c->s)) != cudaSuccess) return e;
+    }
+    e = timed(c, 4, 0.0, [&] {
         cudaError_t ee = launch_reset_state(c->bf.st, c->s);
         if (ee != cudaSuccess) return ee;
         if ((ee = launch_load_rhs(c->storage, bdev, g, c->bf, c->s)) != cudaSuccess) return ee;
         if ((ee = launch_update(c->storage, g, c->bf, c->num_sms, c->s)) != cudaSuccess) return ee;
         return launch_normalize(c->storage, g, c->bf, c->sp, true, c->num_sms, c->s);
+    });
+    if (e != cudaSuccess || !c->gh) return e;
+    // l_1 = A^T d_1 / (A^T d_1)(g_1): the same vector as A^T r_0 / alpha, and
+    // its pivot value is W(1,1)
+    return timed(c, 4, 0.0, [&] {
+        cudaError_t ee = launch_op_apply(c->opT, c->storage, c->bf.V, g.ldv, g.k_max + 1, &c->bf.st->j, B, c->bf2.w,
+                                         c->bf2.st->status, c->s);
+        if (ee != cudaSuccess) return ee;
+        if ((ee = launch_update(c->storage, c->g2, c->bf2, c->num_sms, c->s)) != cudaSuccess) return ee;
+        return launch_normalize(c->storage, c->g2, c->bf2, c->sp2, false, c->num_sms, c->s);
     });
 }
 
@@ -432,17 +552,25 @@ size_t ipf_footprint(const ipf_operator* op, const ipf_config* cfg) {
     const int B = cfg->nrhs > 0 ? cfg->nrhs : 1;
     const size_t sb = storage_bytes(cfg->storage);
     const size_t acc = cfg->storage == IPF_STORE_F64 ? 8 : 4;
-    const size_t ldv = ldv_for(n * B);
     const size_t K1 = (size_t)cfg->k_max + 1;
-    size_t bytes = K1 * ldv * sb + ldv * acc + ldv / 8 + 4096;
-    bytes += B * K1 * (sizeof(int) + sizeof(double) * cfg->k_max + sizeof(double) * K1) + K1 * B * acc;
-    bytes += 2 * (size_t)B * K1 * cfg->m_s * 8 + (size_t)n * 8;
+    // one basis of length np with its buffers
+    auto basis = [&](long long np) -> size_t {
+        const size_t l = ldv_for(np * B);
+        size_t b = K1 * l * sb + l * acc + l / 8 + 4096;
+        b += B * K1 * (sizeof(int) + sizeof(double) * cfg->k_max + sizeof(double) * K1) + K1 * B * acc;
+        return b + 2 * (size_t)B * K1 * cfg->m_s * 8 + (size_t)np * 8;
+    };
+    const bool gh = cfg->method == IPF_METHOD_SLSLU;
+    const size_t ldv = ldv_for(n * B);
+    size_t bytes = basis(gh ? op_m(op) : n) + (gh ? basis(n) : 0);
+    if (gh) bytes += 2 * (size_t)B * op_m(op) * 4;
     Geom g; g.n = n; g.B = B; g.N = n * B; g.ldv = (long long)ldv; g.k_max = cfg->k_max; g.m_s = cfg->m_s; g.F = 0;
     bytes += solve_ws_for(g) + 2 * (size_t)B * n * 4 + 256 + ldv * 4 + B * K1 * 4;
-    if (op->kind == IPF_OP_CSR && op->mem == IPF_MEM_HOST)
-        bytes += (size_t)(op->rows + 1) * 8 + (size_t)op->nnz * 8;
-    else if (op->kind == IPF_OP_PSF2D)
-        bytes += (size_t)op->ph * op->pw * 4 + 32 * 33 * 8 + 40960;   // PSF, packed pairs, tensor-core operand
+    const size_t opb = op->kind == IPF_OP_CSR ? (size_t)(op->rows + 1) * 8 + (size_t)op->nnz * 8
+                                              : (size_t)op->ph * op->pw * 4 + 32 * 33 * 8 + 40960;
+    if (op->kind == IPF_OP_CSR && op->mem == IPF_MEM_HOST) bytes += opb;
+    else if (op->kind == IPF_OP_PSF2D) bytes += opb;      // PSF, packed pairs, tensor-core operand
+    if (gh) bytes += op->kind == IPF_OP_CSR ? (size_t)(op->cols + 1) * 8 + (size_t)op->nnz * 8 : opb;   // A^T
     return bytes;
 }
 
@@ -456,7 +584,10 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     if (!pow2_le32(B)) return IPF_ERR_ARG;
     ipf_status st = check_op(op, B, &why);
     if (st != IPF_OK) return st;
-    if (op->kind == IPF_OP_CSR && op->rows != op->cols) return IPF_ERR_UNSUPPORTED;   // square A (sCMRH)
+    if (cfg.method != IPF_METHOD_SCMRH && cfg.method != IPF_METHOD_SLSLU) return IPF_ERR_ARG;
+    const bool gh = cfg.method == IPF_METHOD_SLSLU;
+    if (!gh && op->kind == IPF_OP_CSR && op->rows != op->cols) return IPF_ERR_UNSUPPORTED;   // square A (sCMRH)
+    if (gh && op->kind != IPF_OP_PSF2D && op->kind != IPF_OP_CSR) return IPF_ERR_UNSUPPORTED;
     if (cfg.k_max < 1 || cfg.zeta < 1 || cfg.zeta > 16 || cfg.m_s < cfg.zeta || cfg.m_s > 65536) return IPF_ERR_ARG;
     if (cfg.storage < IPF_STORE_F64 || cfg.storage > IPF_STORE_F16) return IPF_ERR_ARG;
     if (cfg.storage == IPF_STORE_F64 && B != 1) return IPF_ERR_UNSUPPORTED;
@@ -468,10 +599,18 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     if (b_mem != IPF_MEM_HOST && b_mem != IPF_MEM_DEVICE) return IPF_ERR_ARG;
     const size_t accb = cfg.storage == IPF_STORE_F64 ? 8 : 4;
 
-    const long long n = op_n(op);
-    if (n * B >= (1ll << 31) || n >= (1ll << 29)) return IPF_ERR_UNSUPPORTED;
+    const long long n = op_n(op);                 // length of x (the L space)
+    const long long nD = gh ? op_m(op) : n;       // length of b (the D space)
+    const long long nmax = n > nD ? n : nD;
+    if (nmax * B >= (1ll << 31) || nmax >= (1ll << 29)) return IPF_ERR_UNSUPPORTED;
+    if (gh) {
+        cfg.overlap = 0;                          // one stream per step
+        cfg.zform = IPF_Z_HESSENBERG;
+        cfg.penalty = IPF_PEN_SKETCHED_X;
+    }
 
     ipf_ctx* c = new ipf_ctx();
+    c->gh = gh;
     c->cfg = cfg;
     c->storage = cfg.storage;
     c->B = B;
@@ -506,60 +645,79 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     CK("order", enter(c));
     CK("operator upload", upload_op(op, c->al, &c->op, c->s));
     c->op.conv_fma = cfg.conv_fma ? 1 : 0;
+    if (gh) {
+        CK("transpose upload", upload_transpose(op, c->al, &c->opT, c->s));
+        c->opT.conv_fma = c->op.conv_fma;
+    }
 
+    // one basis with its work vector, state, pivots, Hessenberg columns,
+    // pivot block, sketches and sketch table
+    auto alloc_proc = [&](Geom& g, Bufs& bf, SketchParams& sp, long long np, unsigned long long seed) -> cudaError_t {
+        cudaError_t ee;
+        g.n = np;
+        g.B = B;
+        g.N = np * B;
+        g.ldv = (long long)ldv_for(g.N);
+        g.k_max = cfg.k_max;
+        g.m_s = cfg.m_s;
+        g.F = cfg.storage == IPF_STORE_F64 ? fixed_exponent(np, 0) : kSplitS;
+        g.want_z = cfg.zform == IPF_Z_DIRECT ? 1 : 0;
+        sp = make_sketch_params(seed, cfg.m_s, cfg.zeta);
+        const size_t K1 = (size_t)cfg.k_max + 1;
+        const size_t sb = storage_bytes(cfg.storage);
+#define AK(expr) do { if ((ee = (expr)) != cudaSuccess) return ee; } while (0)
+        AK(c->al.get(&bf.V, K1 * g.ldv * sb));
+        AK(c->al.get(&bf.w, g.ldv * accb));
+        AK(c->al.get((void**)&bf.st, sizeof(DevState)));
+        AK(c->al.get((void**)&bf.piv, B * K1 * sizeof(int)));
+        AK(c->al.get((void**)&bf.H, B * K1 * cfg.k_max * sizeof(double)));
+        AK(c->al.get(&bf.LpT, B * K1 * K1 * sizeof(double)));
+        AK(c->al.get(&bf.coef, K1 * B * accb));
+        AK(c->al.get((void**)&bf.ispiv, (g.ldv / 32 + 1) * sizeof(unsigned)));
+        AK(c->al.get((void**)&bf.accSV, B * K1 * cfg.m_s * sizeof(long long)));
+        AK(c->al.get((void**)&bf.accSW, B * K1 * cfg.m_s * sizeof(long long)));
+        bf.t = nullptr;
+        bf.gpiv = nullptr;
+        if (c->split) {
+            AK(c->al.get((void**)&bf.t, g.ldv * sizeof(float)));
+            AK(cudaMemsetAsync(bf.t, 0, g.ldv * sizeof(float), c->s));
+        }
+        if (c->split || c->fork_piv) AK(c->al.get((void**)&bf.gpiv, B * K1 * sizeof(float)));
+        if (sketch_table_ok(sp)) {
+            unsigned long long* tab = nullptr;
+            AK(c->al.get((void**)&tab, sizeof(unsigned long long) * (size_t)np));
+            AK(launch_sketch_table(sp, np, tab, c->s));
+            bf.sktab = tab;
+        } else {
+            bf.sktab = nullptr;
+        }
+        AK(cudaMemsetAsync(bf.V, 0, K1 * g.ldv * sb, c->s));
+        AK(cudaMemsetAsync(bf.w, 0, g.ldv * accb, c->s));
+        AK(cudaMemsetAsync(bf.LpT, 0, B * K1 * K1 * sizeof(double), c->s));
+        AK(cudaMemsetAsync(bf.piv, 0, B * K1 * sizeof(int), c->s));
+        AK(cudaMemsetAsync(bf.coef, 0, K1 * B * accb, c->s));
+#undef AK
+        return cudaSuccess;
+    };
+    CK("alloc basis", alloc_proc(c->g, c->bf, c->sp, nD, cfg.seed));
+    if (gh) {
+        // S_1 gets its own counter-hash stream: the seed with fixed bits flipped
+        CK("alloc second basis", alloc_proc(c->g2, c->bf2, c->sp2, n, cfg.seed ^ 0x5DEECE66DA3B1F27ull));
+        c->bf.st_peer = c->bf2.st;
+        c->bf2.st_peer = c->bf.st;
+    }
     Geom& g = c->g;
-    g.n = n;
-    g.B = B;
-    g.N = n * B;
-    g.ldv = (long long)ldv_for(g.N);
-    g.k_max = cfg.k_max;
-    g.m_s = cfg.m_s;
-    g.F = cfg.storage == IPF_STORE_F64 ? fixed_exponent(n, 0) : kSplitS;
-    g.want_z = cfg.zform == IPF_Z_DIRECT ? 1 : 0;
-    c->sp = make_sketch_params(cfg.seed, cfg.m_s, cfg.zeta);
-    const size_t K1 = (size_t)cfg.k_max + 1;
-    const size_t sb = storage_bytes(cfg.storage);
     Bufs& bf = c->bf;
-    CK("alloc V", c->al.get(&bf.V, K1 * g.ldv * sb));
-    CK("alloc w", c->al.get(&bf.w, g.ldv * accb));
-    CK("alloc state", c->al.get((void**)&bf.st, sizeof(DevState)));
-    CK("alloc piv", c->al.get((void**)&bf.piv, B * K1 * sizeof(int)));
-    CK("alloc H", c->al.get((void**)&bf.H, B * K1 * cfg.k_max * sizeof(double)));
-    CK("alloc Lp", c->al.get(&bf.LpT, B * K1 * K1 * sizeof(double)));
-    CK("alloc coef", c->al.get(&bf.coef, K1 * B * accb));
-    CK("alloc ispiv", c->al.get((void**)&bf.ispiv, (g.ldv / 32 + 1) * sizeof(unsigned)));
-    CK("alloc SV", c->al.get((void**)&bf.accSV, B * K1 * cfg.m_s * sizeof(long long)));
-    CK("alloc SW", c->al.get((void**)&bf.accSW, B * K1 * cfg.m_s * sizeof(long long)));
-    bf.t = nullptr;
-    bf.gpiv = nullptr;
-    if (c->split) {
-        CK("alloc t", c->al.get((void**)&bf.t, g.ldv * sizeof(float)));
-        CK("memset t", cudaMemsetAsync(bf.t, 0, g.ldv * sizeof(float), c->s));
-    }
-    if (c->split || c->fork_piv) CK("alloc g", c->al.get((void**)&bf.gpiv, B * K1 * sizeof(float)));
-    if (sketch_table_ok(c->sp)) {
-        unsigned long long* tab = nullptr;
-        CK("alloc sketch table", c->al.get((void**)&tab, sizeof(unsigned long long) * (size_t)n));
-        CK("sketch table", launch_sketch_table(c->sp, n, tab, c->s));
-        bf.sktab = tab;
-    } else {
-        bf.sktab = nullptr;
-    }
     c->solve_ws_bytes = solve_ws_for(g);
     CK("alloc solve", c->al.get(&c->solve_ws, c->solve_ws_bytes));
     CK("alloc lambdas", c->al.get((void**)&c->lam_dev, sizeof(double) * kLamChunk));
     CK("alloc x stage", c->al.get((void**)&c->x_stage, sizeof(float) * (size_t)n * B));
-    CK("alloc b stage", c->al.get((void**)&c->b_stage, sizeof(float) * (size_t)n * B));
-
-    CK("memset V", cudaMemsetAsync(bf.V, 0, K1 * g.ldv * sb, c->s));
-    CK("memset w", cudaMemsetAsync(bf.w, 0, g.ldv * accb, c->s));
-    CK("memset Lp", cudaMemsetAsync(bf.LpT, 0, B * K1 * K1 * sizeof(double), c->s));
-    CK("memset piv", cudaMemsetAsync(bf.piv, 0, B * K1 * sizeof(int), c->s));
-    CK("memset coef", cudaMemsetAsync(bf.coef, 0, K1 * B * accb, c->s));
+    CK("alloc b stage", c->al.get((void**)&c->b_stage, sizeof(float) * (size_t)nD * B));
+    (void)bf;
     CK("memset solve", cudaMemsetAsync(c->solve_ws, 0, c->solve_ws_bytes, c->s));
     const float* bsrc = b;
     if (b_mem == IPF_MEM_HOST) {
-        CK("b upload", cudaMemcpyAsync(c->b_stage, b, sizeof(float) * (size_t)n * B, cudaMemcpyHostToDevice, c->s));
+        CK("b upload", cudaMemcpyAsync(c->b_stage, b, sizeof(float) * (size_t)nD * B, cudaMemcpyHostToDevice, c->s));
         bsrc = c->b_stage;
     }
     CK("init", init_solve(c, bsrc));
@@ -703,20 +861,32 @@ ipf_status ipf_solve(ipf_ctx* c, int k, const double* lambdas, int nl, float* x_
     bool any_pos = false;
     for (int l = 0; l < nl; ++l) any_pos |= lambdas[l] > 0.0;
     const bool need_T = any_pos && c->cfg.penalty == IPF_PEN_SKETCHED_X;
+    // generalized process: Z and c from the D side, the penalty S_1 L_k from
+    // the L side, x = L_k y with the D side's completed-step count
+    Bufs bz = c->bf;
+    Geom gx = g;
+    Bufs bx = c->bf;
+    if (c->gh) {
+        bz.penSV = c->bf2.accSV;
+        bz.penF = c->g2.F;
+        gx = c->g2;
+        bx = c->bf2;
+        bx.st = c->bf.st;
+    }
     e = timed(c, 5, 0.0, [&] {
-        return launch_solve_prepare(g, c->bf, c->cfg.zeta, k, need_T, sw_on(c), c->solve_ws, nlm, c->num_sms, c->s);
+        return launch_solve_prepare(g, bz, c->cfg.zeta, k, need_T, sw_on(c), c->solve_ws, nlm, c->num_sms, c->s);
     });
     if (e != cudaSuccess) return cuda_fail(c, "solve prepare", e);
-    const size_t slice = (size_t)g.n * c->B;
+    const size_t slice = (size_t)gx.n * c->B;
     const int step = x_mem == IPF_MEM_DEVICE ? nlm : 1;
     for (int l0 = 0; l0 < nl; l0 += step) {
         const int nlc = nl - l0 < step ? nl - l0 : step;
         if ((e = cudaMemcpyAsync(c->lam_dev, lambdas + l0, sizeof(double) * nlc, cudaMemcpyHostToDevice, c->s)) != cudaSuccess)
             return cuda_fail(c, "lambda upload", e);
         float* dst = x_mem == IPF_MEM_DEVICE ? x_out + (size_t)l0 * slice : c->x_stage;
-        const double xb = (double)k * g.N * storage_bytes(c->storage) + (double)nlc * g.N * 4.0;
+        const double xb = (double)k * gx.N * storage_bytes(c->storage) + (double)nlc * gx.N * 4.0;
         e = timed(c, 6, xb, [&] {
-            return launch_solve_lambdas(c->storage, g, c->bf, k, need_T, c->lam_dev, nlc, c->cfg.penalty, c->solve_ws,
+            return launch_solve_lambdas(c->storage, gx, bx, k, need_T, c->lam_dev, nlc, c->cfg.penalty, c->solve_ws,
                                         nlm, dst, c->num_sms, c->s);
         });
         if (e != cudaSuccess) return cuda_fail(c, "solve", e);
@@ -807,17 +977,17 @@ ipf_status ipf_export(ipf_ctx* c, int r, int* pivots, double* H, double* SV, dou
     return IPF_OK;
 }
 
-ipf_status ipf_export_basis(ipf_ctx* c, int r, int j, float* v_out) {
+static ipf_status export_column(ipf_ctx* c, const Geom& g, const Bufs& bf, int r, int j, float* v_out) {
     if (!c || !v_out) return IPF_ERR_ARG;
     if (c->sticky != IPF_OK) return c->sticky;
-    if (r < 0 || r >= c->B || j < 0 || j > c->g.k_max) return IPF_ERR_ARG;
+    if (r < 0 || r >= c->B || j < 0 || j > g.k_max) return IPF_ERR_ARG;
     cudaError_t e = cudaStreamSynchronize(c->s);
     if (e != cudaSuccess) return cuda_fail(c, "sync", e);
     const size_t sb = storage_bytes(c->storage);
-    std::vector<unsigned char> raw((size_t)c->g.ldv * sb);
-    e = cudaMemcpy(raw.data(), (const char*)c->bf.V + (size_t)j * c->g.ldv * sb, raw.size(), cudaMemcpyDeviceToHost);
+    std::vector<unsigned char> raw((size_t)g.ldv * sb);
+    e = cudaMemcpy(raw.data(), (const char*)bf.V + (size_t)j * g.ldv * sb, raw.size(), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, "export basis", e);
-    const long long n = c->g.n;
+    const long long n = g.n;
     const int B = c->B;
     for (long long i = 0; i < n; ++i) {
         const size_t el = (size_t)i * B + r;
@@ -840,6 +1010,53 @@ ipf_status ipf_export_basis(ipf_ctx* c, int r, int j, float* v_out) {
         v_out[i] = v;
     }
     return IPF_OK;
+}
+
+ipf_status ipf_export_basis(ipf_ctx* c, int r, int j, float* v_out) {
+    if (!c) return IPF_ERR_ARG;
+    return export_column(c, c->g, c->bf, r, j, v_out);
+}
+
+ipf_status ipf_export_dual(ipf_ctx* c, int r, int* pivots_l, double* W, double* SL, double* w11) {
+    if (!c) return IPF_ERR_ARG;
+    if (c->sticky != IPF_OK) return c->sticky;
+    if (!c->gh) return IPF_ERR_STATE;
+    if (r < 0 || r >= c->B) return IPF_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(c->s);
+    if (e != cudaSuccess) return cuda_fail(c, "sync", e);
+    DevState h;
+    if ((e = cudaMemcpy(&h, c->bf2.st, sizeof(DevState), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(c, "state readback", e);
+    const size_t K1 = (size_t)c->g2.k_max + 1;
+    const size_t km = (size_t)c->g2.k_max;
+    const int m = c->g2.m_s;
+    if (pivots_l) {
+        std::vector<int> p(K1);
+        if ((e = cudaMemcpy(p.data(), c->bf2.piv + r * K1, K1 * sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(c, "export piv", e);
+        const int kd = h.kdone[r];
+        const int np = (h.status[r] == IPF_BREAKDOWN) ? kd : kd + 1;
+        for (int i = 0; i < (int)K1; ++i) pivots_l[i] = i < np ? p[i] : -1;
+    }
+    if (W && (e = cudaMemcpy(W, c->bf2.H + r * K1 * km, K1 * km * sizeof(double), cudaMemcpyDeviceToHost)) !=
+                 cudaSuccess)
+        return cuda_fail(c, "export W", e);
+    if (SL) {
+        std::vector<long long> a(K1 * m);
+        if ((e = cudaMemcpy(a.data(), c->bf2.accSV + r * K1 * m, a.size() * sizeof(long long),
+                            cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(c, "export SL", e);
+        const double sc = std::ldexp(1.0, -c->g2.F) / std::sqrt((double)c->cfg.zeta);
+        for (size_t t = 0; t < a.size(); ++t) SL[t] = (double)a[t] * sc;
+    }
+    if (w11) *w11 = h.beta[r];
+    return IPF_OK;
+}
+
+ipf_status ipf_export_basis_l(ipf_ctx* c, int r, int j, float* l_out) {
+    if (!c || !l_out) return IPF_ERR_ARG;
+    if (!c->gh) return IPF_ERR_STATE;
+    return export_column(c, c->g2, c->bf2, r, j, l_out);
 }
 
 void ipf_destroy(ipf_ctx* c) {

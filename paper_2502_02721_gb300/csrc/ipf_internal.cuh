@@ -235,6 +235,12 @@ struct Bufs {
                                       // byte t = row offset in block t | sign << 7
     float* t;                      // ldv FP32: V_j h (split step), else NULL
     float* gpiv;                   // [B][k_max+1] FP32: (A v_j)(p_i) (split step), else NULL
+    // generalized process (two bases): the other basis's state, told when this
+    // one stops, and for the projected solve the sketches of the penalty basis
+    // (S_1 L) with their fixed-point exponent; NULL / 0 for one basis
+    DevState* st_peer = nullptr;
+    const long long* penSV = nullptr;
+    int penF = 0;
 };
 
 // operator on the device

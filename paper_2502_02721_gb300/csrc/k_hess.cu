@@ -522,7 +522,53 @@ __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams
     bool any_ok = false;
     for (int q = 0; q < Bg; ++q) any_ok |= s_ok[q] != 0;
     const int F = g.F;
-    if (any_ok) {
+    // common case (float storage, one right-hand side, zeta = 8 with the
+    // sketch table, no second sketch): the same integer sums with the
+    // counter words of +q and -q formed once per element instead of once per
+    // sketch row, and the table bytes decoded in 32-bit halves
+    const bool fast = !f64 && Bg == 1 && g.B == 1 && bf.sktab && sp.zeta == 8 && !want_sw;
+    if (fast && any_ok) {
+        T* vout = (T*)bf.V + (size_t)jn * g.ldv;
+        const unsigned n = (unsigned)g.n;
+        const unsigned stride = gridDim.x * blockDim.x;
+        const long long prow = s_prow[0];
+        const Acc hval = s_hval[0];
+        int blo[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) blo[q] = sp.lo[q];
+        const uint2* tab = (const uint2*)bf.sktab;
+        const int fold_rounds = kFoldEvery / 256;
+        int round = 0;
+        for (unsigned t0 = blockIdx.x * blockDim.x; t0 < n; t0 += stride) {
+            const unsigned i = t0 + threadIdx.x;
+            if (i < n) {
+                const Acc v = ((long long)i == prow) ? (Acc)1 : w[i] / hval;
+                const T vs = from_acc<T>(v);
+                vout[i] = vs;
+                const long long qv = fixed_from(to_acc(vs), kSplitS);
+                if (qv) {
+                    const int hp = (int)(qv >> 17), lp = (int)(qv & 0x1FFFFll);
+                    const long long qn = -qv;
+                    const int hn = (int)(qn >> 17), ln = (int)(qn & 0x1FFFFll);
+                    const uint2 ent = tab[i];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const unsigned byte = ((q < 4 ? ent.x : ent.y) >> (8 * (q & 3))) & 0xFFu;
+                        const int row = blo[q] + (int)(byte & 0x7Fu);
+                        const bool ng = (byte & 0x80u) != 0;
+                        atomicAdd(&s_hi[row], ng ? hn : hp);
+                        atomicAdd(&s_lo[row], ng ? ln : lp);
+                    }
+                }
+            }
+            if (++round == fold_rounds) {
+                __syncthreads();
+                split_fold(s_hi, s_lo, s_wide, cnt);
+                __syncthreads();
+                round = 0;
+            }
+        }
+    } else if (any_ok) {
         T* vout = (T*)bf.V + (size_t)jn * g.ldv;
         const unsigned total = (unsigned)g.n << lbg;     // (i, rl) pairs this CTA's group covers
         const unsigned stride = gridDim.x * blockDim.x;
@@ -621,6 +667,10 @@ __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams
             st->kdone[r] = jn;
         } else if (st->status[r] == IPF_OK) {
             st->status[r] = s_code[rl];
+            // the generalized process stops as a whole; the other basis keeps
+            // its completed columns
+            if (bf.st_peer && bf.st_peer->status[r] == IPF_OK)
+                bf.st_peer->status[r] = s_code[rl] == IPF_ERR_NONFINITE ? IPF_ERR_NONFINITE : IPF_BREAKDOWN;
             st->kdone[r] = (s_code[rl] == IPF_BREAKDOWN) ? jn : (jn > 0 ? jn - 1 : 0);
             if (jn == 0) st->beta[r] = 0.0;
         }

@@ -62,6 +62,9 @@ __global__ void k_form(Geom g, Bufs bf, int k, int zeta, int use_sw, int need_T,
     const double scale = ldexp(1.0, -g.F) / sqrt((double)zeta);
     const long long* sv = bf.accSV + (size_t)r * K1 * m;
     const long long* sw = bf.accSW + (size_t)r * K1 * m;
+    // the penalty basis: S V itself, or S_1 L of the generalized process
+    const long long* pv = bf.penSV ? bf.penSV + (size_t)r * K1 * m : sv;
+    const double pscale = bf.penSV ? ldexp(1.0, -bf.penF) / sqrt((double)zeta) : scale;
     const double* H = bf.H + (size_t)r * K1 * g.k_max;
     double* M = Mw + (size_t)r * m * (k + 1);
     double* T = Tw ? Tw + (size_t)r * m * k : nullptr;
@@ -77,7 +80,7 @@ __global__ void k_form(Geom g, Bufs bf, int k, int zeta, int use_sw, int need_T,
             for (int i = 0; i <= col; ++i) s = fma((double)sv[(size_t)i * m + row] * scale, Hc[i], s);
             const long long* last = use_sw ? sw : sv;
             val = fma((double)last[(size_t)(col + 1) * m + row] * scale, Hc[col + 1], s);
-            if (need_T) T[(size_t)col * m + row] = (double)sv[(size_t)col * m + row] * scale;
+            if (need_T) T[(size_t)col * m + row] = (double)pv[(size_t)col * m + row] * pscale;
         } else {
             val = beta * (double)sw[row] * scale;
         }

@@ -68,7 +68,10 @@ def test_served_results_equal_solves_alone():
     for r, t in zip(reqs, tickets):
         status, k_used, _, x = results[t]
         assert status == bd.IPF_OK and k_used == r["k"]
-        cfg = bd.default_config(k_max=r["k"], m_s=r["m_s"], zeta=8, seed=r["seed"], storage=r["storage"])
+        # the server steps every request on one stream (overlap 0), so the
+        # solve alone uses the same step
+        cfg = bd.default_config(k_max=r["k"], m_s=r["m_s"], zeta=8, seed=r["seed"], storage=r["storage"],
+                                overlap=0)
         ctx = bd.Context(_op(bd, r, keep), r["b"], cfg, keep)
         ctx.step(r["k"])
         xa, _ = ctx.solve(r["k"], [r["lam"]])

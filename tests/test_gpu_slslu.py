@@ -1,0 +1,206 @@
+"""The generalized Hessenberg process (sLSLU, Algorithm 1 and Algorithm 2)
+through the C ABI against the FP64 oracle on the same seeded inputs: both
+pivot sequences identical up to near ties, beta and W(1,1), x_k per iterate
+for plain and Tikhonov problems; a rectangular CT operator (m != n); the
+exact structure of BF16 bases; exact breakdown."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+from _gpu_common import U, ensure_lib, rel, tolerance  # noqa: E402
+from gen import problems as P  # noqa: E402
+from oracle import operators as ops, slslu, sketch as sk  # noqa: E402
+
+S1_SEED_XOR = 0x5DEECE66DA3B1F27          # S_1 seed = config seed XOR this (include/ipf.h)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    return ensure_lib()
+
+
+def _sketches(seed, m, n, m_s, zeta):
+    return sk.SparseSignSketch(seed ^ S1_SEED_XOR, n, m_s, zeta), sk.SparseSignSketch(seed, m, m_s, zeta)
+
+
+def _context(op, b, k, m_s, zeta, seed, storage, keep, nrhs=1):
+    from paper_2502_02721_gb300 import binding as bd
+    cfg = bd.default_config(k_max=k, m_s=m_s, zeta=zeta, seed=seed, storage=storage, nrhs=nrhs, method="slslu")
+    return bd.Context(op, b, cfg, keep)
+
+
+def _first_divergence(a, b, k):
+    return next((j for j in range(k + 1) if int(a[j]) != int(b[j])), k + 1)
+
+
+def _perturbed(A, At, b, S1, S2, k, delta, seed=12345, forced=(None, None)):
+    """The oracle with every operator output perturbed elementwise by a
+    relative N(0, delta^2) error: the response of the process to rounding in
+    the products at that level."""
+    rng = np.random.default_rng(seed)
+    Ap = lambda v: (lambda w: w * (1.0 + delta * rng.standard_normal(w.size)))(A(v))
+    Atp = lambda v: (lambda w: w * (1.0 + delta * rng.standard_normal(w.size)))(At(v))
+    return slslu.run(Ap, Atp, b, S1, S2, k, forced_t=forced[0], forced_g=forced[1])
+
+
+def _verify(ctx, A, At, b, S1, S2, k, storage, taps, ks, lambdas):
+    """Pivots, then iterates.
+
+    Max-|.| pivoting in the generalized process is chaotic: a relative
+    perturbation of the products at rounding level (1e-15) changes the
+    oracle's own pivot choices after some 25 steps on the CT problem and
+    moves x_50 of the deblurring problem by ~3e-7 with identical pivots.  So
+    (i) the GPU's pivot sequences must agree with the oracle's until at least
+    the step where the oracle itself, perturbed by sqrt(K) u_s per product (K
+    terms summed in an order the oracle does not share), first departs from
+    its own sequence (earliest of three perturbations, less a margin of 3);
+    (ii) the iterates are compared with the oracle replaying the GPU's pivot
+    sequences, within max(floor, 10 u_s kappa(Z_k), 10 r_k), r_k the replay's
+    own response to that perturbation."""
+    st = slslu.run(A, At, b, S1, S2, k)
+    ex, du = ctx.export(0), ctx.export_dual(0)
+    gt = [int(v) for v in ex["piv"][:k + 1]]
+    gg = [int(v) for v in du["piv"][:k + 1]]
+    assert min(gt) >= 0 and min(gg) >= 0
+    delta = np.sqrt(taps) * U[storage]
+    j_gpu = min(_first_divergence(gt, st.pt, k), _first_divergence(gg, st.pg, k))
+    if j_gpu <= k:
+        j_or = k + 1
+        for seed in (1, 2, 3):
+            sp = _perturbed(A, At, b, S1, S2, k, delta, seed)
+            j_or = min(j_or, _first_divergence(sp.pt, st.pt, k), _first_divergence(sp.pg, st.pg, k))
+        assert j_gpu >= j_or - 3, (j_gpu, j_or)
+    st_f = slslu.run(A, At, b, S1, S2, k, forced_t=gt, forced_g=gg)
+    st_fp = _perturbed(A, At, b, S1, S2, k, delta, forced=(gt, gg))
+    for kk in ks:
+        x, info = ctx.solve(kk, lambdas)
+        kappa = np.linalg.cond(slslu.projected_matrix(st_f, kk))
+        for li, lam in enumerate(lambdas):
+            x_or = slslu.solve(st_f, kk, lam)
+            resp = rel(slslu.solve(st_fp, kk, lam), x_or)
+            tol = max(tolerance(storage, kappa), 10.0 * resp)
+            e = rel(x[li, 0].astype(np.float64), x_or)
+            assert e <= tol, (kk, lam, e, tol, kappa, resp)
+    return st, j_gpu
+
+
+@pytest.fixture(scope="module")
+def deblur64_slslu():
+    p = P.make("deblur64")
+    psf = p.psf.astype(np.float64)
+    A = lambda v: ops.conv2d_zero(v.reshape(p.rows, p.cols), psf).reshape(-1)
+    At = lambda v: ops.conv2d_zero(v.reshape(p.rows, p.cols), psf[::-1, ::-1]).reshape(-1)
+    S1, S2 = _sketches(p.sketch_seed, p.n, p.n, p.m_s, p.zeta)
+    b = p.b[0].astype(np.float64)
+    return p, A, At, b, S1, S2, np.count_nonzero(psf)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_deblur64_slslu_parity(deblur64_slslu, storage):
+    from paper_2502_02721_gb300 import binding as bd
+    p, A, At, b, S1, S2, taps = deblur64_slslu
+    keep = []
+    ctx = _context(bd.operator_from_problem(p, keep), p.b, p.k, p.m_s, p.zeta, p.sketch_seed, storage, keep)
+    ctx.step(p.k)
+    status, kd = ctx.sync()
+    assert kd == [p.k]
+    st, j_gpu = _verify(ctx, A, At, b, S1, S2, p.k, storage, taps, [1, 2, 5, 10, 20, 30, 50], p.lambdas)
+    ex, du = ctx.export(0), ctx.export_dual(0)
+    assert abs(ex["beta"] - st.beta) <= 1e-6 * abs(st.beta)
+    assert abs(du["w11"] - st.W[0, 0]) <= (1e-12 if storage == "f64" else 1e-5) * abs(st.W[0, 0])
+    # the first Hessenberg column and the first columns of W
+    assert rel(ex["H"][:2, 0], st.H[:2, 0]) < (1e-12 if storage == "f64" else 1e-5)
+    assert rel(du["W"][:2, 0], st.W[:2, 1]) < (1e-12 if storage == "f64" else 1e-5)
+    if storage == "f64":
+        assert j_gpu == p.k + 1
+    ctx.close()
+
+
+def _ct_rect(nimg=32, nangles=40, ndet=48, seed=2502021 + 13):
+    rowptr, colind, vals = P.siddon_parallel(nimg, nangles, ndet)
+    rng = np.random.default_rng(seed)
+    x = P.head_phantom(nimg, rng).reshape(-1)
+    clean = P.csr_matvec(rowptr, colind, vals, x)
+    b = P.add_noise(clean, 0.005, rng).astype(np.float32)
+    return rowptr, colind, vals, b, x
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_rectangular_ct_slslu_parity(storage):
+    """m = 40 angles x 48 detectors = 1920 rays, n = 32 x 32 = 1024 pixels."""
+    from scipy.sparse import csr_matrix
+    from paper_2502_02721_gb300 import binding as bd
+    rowptr, colind, vals, b, _ = _ct_rect()
+    m, n = rowptr.size - 1, 32 * 32
+    Asp = csr_matrix((vals.astype(np.float64), colind, rowptr), shape=(m, n))
+    k, m_s, zeta, seed = 40, 160, 8, 777
+    S1, S2 = _sketches(seed, m, n, m_s, zeta)
+    A, At = (lambda v: Asp @ v), (lambda v: Asp.T @ v)
+    taps = int(np.max(np.diff(rowptr)))
+    keep = []
+    op = bd.make_operator("csr", m, n, rowptr=rowptr, colind=colind, vals=vals, keep=keep)
+    ctx = _context(op, b.reshape(1, -1), k, m_s, zeta, seed, storage, keep)
+    ctx.step(k)
+    status, kd = ctx.sync()
+    assert kd == [k]
+    _verify(ctx, A, At, b.astype(np.float64), S1, S2, k, storage, taps, [1, 3, 10, 25, 40], [0.0, 0.1])
+    x, _ = ctx.solve(k, [0.0])
+    assert x.shape == (1, 1, n)
+    ctx.close()
+
+
+def test_bf16_bases_structure():
+    """BF16 storage: both stored bases are exactly unit lower trapezoidal under
+    their pivots with |.| <= 1, and the first relation of Eq. Hessenberg_r
+    holds for the stored bases to the rounding of d_{k+1} plus FP32 sums."""
+    from paper_2502_02721_gb300 import binding as bd
+    p = P.make("deblur64")
+    keep = []
+    k = 20
+    ctx = _context(bd.operator_from_problem(p, keep), p.b, k, p.m_s, p.zeta, p.sketch_seed, "bf16", keep)
+    ctx.step(k)
+    status, kd = ctx.sync()
+    assert kd == [k]
+    ex, du = ctx.export(0), ctx.export_dual(0)
+    D = np.stack([ctx.basis(j) for j in range(k + 1)], axis=1).astype(np.float64)
+    L = np.stack([ctx.basis_l(j) for j in range(k + 1)], axis=1).astype(np.float64)
+    for M, piv in ((D, ex["piv"]), (L, du["piv"])):
+        for i, pi in enumerate(piv[:k + 1]):
+            assert M[pi, i] == 1.0 and np.all(M[pi, i + 1:] == 0.0)
+        assert np.abs(M).max() <= 1.0
+    psf = p.psf.astype(np.float64)
+    A = lambda v: ops.conv2d_zero(v.reshape(p.rows, p.cols), psf).reshape(-1)
+    H = ex["H"][:k + 1, :k]
+    for j in range(k):
+        r = A(L[:, j]) - D[:, :j + 2] @ H[:j + 2, j]
+        bound = abs(H[j + 1, j]) * U["bf16"] + 1e-5 * (np.abs(A(L[:, j])).max() + np.abs(H[:j + 2, j]).sum())
+        assert np.abs(r).max() <= bound, (j, np.abs(r).max(), bound)
+    ctx.close()
+
+
+def test_slslu_breakdown_is_exact():
+    """Block-diagonal CSR A with b on its 3 x 3 block: the D side stops at
+    k = 3 with H(4,3) = 0 (the algorithm's stopping branch) and x_3 solves
+    the system."""
+    from paper_2502_02721_gb300 import binding as bd
+    rng = np.random.default_rng(4)
+    A = np.zeros((12, 12))
+    A[:3, :3] = rng.standard_normal((3, 3)) + 2 * np.eye(3)
+    A[3:, 3:] = rng.standard_normal((9, 9)) + 2 * np.eye(9)
+    b = np.zeros(12, dtype=np.float32)
+    b[:3] = rng.standard_normal(3)
+    nz = np.nonzero(A)
+    rowptr = np.concatenate([[0], np.cumsum(np.bincount(nz[0], minlength=12))]).astype(np.int64)
+    colind = nz[1].astype(np.int32)
+    vals = A[nz].astype(np.float32)
+    keep = []
+    op = bd.make_operator("csr", 12, 12, rowptr=rowptr, colind=colind, vals=vals, keep=keep)
+    ctx = _context(op, b.reshape(1, -1), 8, 16, 4, 99, "f64", keep)
+    ctx.step(8)
+    status, kd = ctx.sync()
+    assert status == bd.IPF_BREAKDOWN and kd == [3]
+    x, info = ctx.solve(3, [0.0])
+    Ad = A.astype(np.float32).astype(np.float64)
+    assert np.linalg.norm(Ad @ x[0, 0].astype(np.float64) - b) <= 1e-6 * np.linalg.norm(b)
+    ctx.close()
