@@ -31,6 +31,8 @@ from dataclasses import dataclass, field
 import numpy as np
 import scipy.linalg as sla
 
+from . import pivoting
+
 
 @dataclass
 class HessenbergState:
@@ -58,10 +60,13 @@ def _argmax_abs_excluding(u: np.ndarray, is_piv: np.ndarray):
     return i, float(top), gap
 
 
-def iterate(apply_A, b, sketch, k_max: int, forced_pivots=None):
+def iterate(apply_A, b, sketch, k_max: int, forced_pivots=None, pivot_sample: int = 0, pivot_seed: int = 0):
     """Generator form of run(): yields (j, state) after the initialisation
     (j = 0) and after each Hessenberg step j = 1..k_done.  Each state holds
-    views of the working arrays trimmed to the j completed steps."""
+    views of the working arrays trimmed to the j completed steps.
+
+    pivot_sample > 0 chooses each pivot by sampled pivoting (pivoting.py)
+    with sampling seed pivot_seed."""
     b = np.asarray(b, dtype=np.float64).reshape(-1)
     n = b.size
     m = sketch.m
@@ -83,6 +88,8 @@ def iterate(apply_A, b, sketch, k_max: int, forced_pivots=None):
     else:
         i, _, g = _argmax_abs_excluding(b, is_piv)
         gaps.append(g)
+        if pivot_sample > 0:
+            i = pivoting.sampled_pivot(b, is_piv, pivot_seed, 0, pivot_sample)
     beta = float(b[i])
     if beta == 0.0:
         yield 0, state(0, 0.0, [], True)
@@ -109,6 +116,8 @@ def iterate(apply_A, b, sketch, k_max: int, forced_pivots=None):
         else:
             p, _, g = _argmax_abs_excluding(u, is_piv)
             gaps.append(g)
+            if pivot_sample > 0:
+                p = pivoting.sampled_pivot(u, is_piv, pivot_seed, j + 1, pivot_sample)
         H[j + 1, j] = u[p]
         V[:, j + 1] = u / H[j + 1, j]
         piv.append(p)
@@ -117,7 +126,8 @@ def iterate(apply_A, b, sketch, k_max: int, forced_pivots=None):
         yield j + 1, state(j + 1, beta, piv, False)
 
 
-def run(apply_A, b, sketch, k_max: int, forced_pivots=None) -> HessenbergState:
+def run(apply_A, b, sketch, k_max: int, forced_pivots=None, pivot_sample: int = 0,
+        pivot_seed: int = 0) -> HessenbergState:
     """k_max steps of the pivoted Hessenberg process with sketch S.
 
     forced_pivots: optional sequence of rows to use as p_1, p_2, ... instead
@@ -125,7 +135,7 @@ def run(apply_A, b, sketch, k_max: int, forced_pivots=None) -> HessenbergState:
     candidates are within rounding of each other).
     """
     st = None
-    for _, st in iterate(apply_A, b, sketch, k_max, forced_pivots):
+    for _, st in iterate(apply_A, b, sketch, k_max, forced_pivots, pivot_sample, pivot_seed):
         pass
     return st
 

@@ -41,6 +41,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
+from . import pivoting
 from .scmrh import _argmax_abs_excluding, _lstsq_qr
 
 
@@ -65,12 +66,15 @@ class GenHessenbergState:
     gaps_g: list             # the same for the pivots of L
 
 
-def iterate(apply_A, apply_At, b, S1, S2, k_max: int, forced_t=None, forced_g=None):
+def iterate(apply_A, apply_At, b, S1, S2, k_max: int, forced_t=None, forced_g=None, pivot_sample: int = 0,
+            pivot_seeds=(0, 0)):
     """Yields (k, state) after the initialisation (k = 0) and after each step.
 
     forced_t / forced_g: optional pivot sequences to use instead of the
     max-|.| choice (replays another run's order where two candidates are
-    within rounding of each other)."""
+    within rounding of each other).  pivot_sample > 0 chooses the pivots by
+    sampled pivoting (pivoting.py), with sampling seeds pivot_seeds for D
+    and L."""
     b = np.asarray(b, dtype=np.float64).reshape(-1)
     m = b.size
     v0 = apply_At(b)
@@ -94,14 +98,16 @@ def iterate(apply_A, apply_At, b, S1, S2, k_max: int, forced_t=None, forced_g=No
                                   SD[:, :k + 1], SL[:, :k + 1], Zd[:, :k], c, beta, alpha, k, l_done, breakdown,
                                   list(gaps_t), list(gaps_g))
 
-    def choose(vec, is_piv, forced, idx, gaps):
+    def choose(vec, is_piv, forced, idx, gaps, side):
         i_max, _, gap = _argmax_abs_excluding(vec, is_piv)
         gaps.append(gap)
         if forced is not None and idx < len(forced):
             return int(forced[idx])
+        if pivot_sample > 0:
+            return pivoting.sampled_pivot(vec, is_piv, pivot_seeds[side], idx, pivot_sample)
         return i_max
 
-    i = choose(b, tpiv, forced_t, 0, gaps_t)
+    i = choose(b, tpiv, forced_t, 0, gaps_t, 0)
     beta = float(b[i])
     if beta == 0.0:
         yield 0, state(0, 0.0, 0.0, 0, True)
@@ -110,7 +116,7 @@ def iterate(apply_A, apply_At, b, S1, S2, k_max: int, forced_t=None, forced_g=No
     pt.append(i)
     tpiv[i] = True
     SD[:, 0] = S2.apply(D[:, 0])
-    i2 = choose(v0, gpiv, forced_g, 0, gaps_g)
+    i2 = choose(v0, gpiv, forced_g, 0, gaps_g, 1)
     alpha = float(v0[i2])
     if alpha == 0.0:
         yield 0, state(0, beta, 0.0, 0, True)
@@ -133,7 +139,7 @@ def iterate(apply_A, apply_At, b, S1, S2, k_max: int, forced_t=None, forced_g=No
             H[k + 1, k] = 0.0
             yield k + 1, state(k + 1, beta, alpha, k + 1, True)
             return
-        p = choose(u, tpiv, forced_t, k + 1, gaps_t)
+        p = choose(u, tpiv, forced_t, k + 1, gaps_t, 0)
         H[k + 1, k] = u[p]
         D[:, k + 1] = u / H[k + 1, k]
         pt.append(p)
@@ -148,7 +154,7 @@ def iterate(apply_A, apply_At, b, S1, S2, k_max: int, forced_t=None, forced_g=No
         if k + 1 >= n or not np.any(q):
             yield k + 1, state(k + 1, beta, alpha, k + 1, True)
             return
-        p2 = choose(q, gpiv, forced_g, k + 1, gaps_g)
+        p2 = choose(q, gpiv, forced_g, k + 1, gaps_g, 1)
         W[k + 1, k + 1] = q[p2]
         L[:, k + 1] = q / W[k + 1, k + 1]
         pg.append(p2)
@@ -157,9 +163,10 @@ def iterate(apply_A, apply_At, b, S1, S2, k_max: int, forced_t=None, forced_g=No
         yield k + 1, state(k + 1, beta, alpha, k + 2, False)
 
 
-def run(apply_A, apply_At, b, S1, S2, k_max: int, forced_t=None, forced_g=None) -> GenHessenbergState:
+def run(apply_A, apply_At, b, S1, S2, k_max: int, forced_t=None, forced_g=None, pivot_sample: int = 0,
+        pivot_seeds=(0, 0)) -> GenHessenbergState:
     st = None
-    for _, st in iterate(apply_A, apply_At, b, S1, S2, k_max, forced_t, forced_g):
+    for _, st in iterate(apply_A, apply_At, b, S1, S2, k_max, forced_t, forced_g, pivot_sample, pivot_seeds):
         pass
     return st
 
