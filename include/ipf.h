@@ -137,6 +137,17 @@ typedef struct ipf_config {
                                     the operator beside the pivot-row products and the
                                     FP64 pivot-block solve                                   */
     int method;                  /* enum ipf_method (default IPF_METHOD_SCMRH)               */
+    int pivot_sample;            /* 0 (default): each pivot is the largest |.| over all
+                                    candidate rows.  1..64: sampled pivoting (Sec. 3.2,
+                                    Sec. 4): the largest |.| over that many candidate rows
+                                    drawn for each pivot choice c (0 at the initialisation,
+                                    j+1 at step j): draw t is SplitMix64 output c*4096 + t
+                                    of the generator started at seed XOR 0xA5A5A5A5A5A5A5A5
+                                    (SLSLU's L basis: also XOR 0x5DEECE66DA3B1F27), row
+                                    floor(out * n / 2^64); draws hitting a pivot row or an
+                                    accepted row are skipped, at most 4096 draws; if no more
+                                    candidates remain than the sample size, or every sampled
+                                    entry is zero, the full maximum is used                   */
     int conv_fma;                /* PSF2D with BF16 storage: 0 (default) runs the product on
                                     the tensor cores when the PSF pads to 15x15 or 31x31 and
                                     cols % 8 == 0; 1 keeps the FP32 FMA convolution         */

@@ -380,6 +380,16 @@ bool sw_on(const ipf_ctx* c) {
     return c->g.want_z && (c->storage == IPF_STORE_BF16 || c->storage == IPF_STORE_F16);
 }
 
+// sampled pivoting (config.pivot_sample > 0): after the update has left the
+// full-max key, replace it by the largest |w| of the sample.  The second basis
+// of the generalized process draws from its own seed.
+cudaError_t sample_pivot(ipf_ctx* c, const Geom& g, const Bufs& bf) {
+    if (c->cfg.pivot_sample <= 0) return cudaSuccess;
+    const unsigned long long seed = c->cfg.seed ^ 0xA5A5A5A5A5A5A5A5ull ^
+                                    (bf.st == c->bf.st ? 0ull : 0x5DEECE66DA3B1F27ull);
+    return timed(c, 9, 0.0, [&] { return launch_sample_pivot(c->storage, g, bf, seed, c->cfg.pivot_sample, c->s); });
+}
+
 // one Hessenberg step; every kernel takes j from device memory, so the same
 // sequence serves every step and can be captured once.  `j` (host count) is
 // only used to label profile bytes.
@@ -400,6 +410,7 @@ cudaError_t half_step(ipf_ctx* c, const OpDev& op, const Bufs& in, const Geom& g
     if ((e = timed(c, 2, (double)(j + 1) * N * sv + 2.0 * N * ab + N / 8.0,
                    [&] { return launch_update(c->storage, g, bf, c->num_sms, c->s); })) != cudaSuccess)
         return e;
+    if ((e = sample_pivot(c, g, bf)) != cudaSuccess) return e;
     return timed(c, 3, N * ab + N * sv,
                  [&] { return launch_normalize(c->storage, g, bf, sp, false, c->num_sms, c->s); });
 }
@@ -439,6 +450,7 @@ cudaError_t one_step(ipf_ctx* c, int j) {
         if ((e = timed(c, 8, 12.0 * N + N / 8.0, [&] { return launch_combine(c->g, c->bf, c->num_sms, c->s); })) !=
             cudaSuccess)
             return e;
+        if ((e = sample_pivot(c, c->g, c->bf)) != cudaSuccess) return e;
         return timed(c, 3, N * ab + N * sv,
                      [&] { return launch_normalize(c->storage, c->g, c->bf, c->sp, sw_on(c), c->num_sms, c->s); });
     }
@@ -465,6 +477,7 @@ cudaError_t one_step(ipf_ctx* c, int j) {
         if ((e = timed(c, 2, (double)(j + 1) * N * sv + 2.0 * N * ab + N / 8.0,
                        [&] { return launch_update(c->storage, c->g, c->bf, c->num_sms, c->s); })) != cudaSuccess)
             return e;
+        if ((e = sample_pivot(c, c->g, c->bf)) != cudaSuccess) return e;
         return timed(c, 3, N * ab + N * sv,
                      [&] { return launch_normalize(c->storage, c->g, c->bf, c->sp, sw_on(c), c->num_sms, c->s); });
     }
@@ -478,6 +491,7 @@ cudaError_t one_step(ipf_ctx* c, int j) {
     if ((e = timed(c, 2, (double)(j + 1) * N * sv + 2.0 * N * ab + N / 8.0,
                    [&] { return launch_update(c->storage, c->g, c->bf, c->num_sms, c->s); })) != cudaSuccess)
         return e;
+    if ((e = sample_pivot(c, c->g, c->bf)) != cudaSuccess) return e;
     return timed(c, 3, N * ab + N * sv,
                  [&] { return launch_normalize(c->storage, c->g, c->bf, c->sp, sw_on(c), c->num_sms, c->s); });
 }
@@ -508,6 +522,7 @@ cudaError_t init_solve(ipf_ctx* c, const float* bdev) {
         if (ee != cudaSuccess) return ee;
         if ((ee = launch_load_rhs(c->storage, bdev, g, c->bf, c->s)) != cudaSuccess) return ee;
         if ((ee = launch_update(c->storage, g, c->bf, c->num_sms, c->s)) != cudaSuccess) return ee;
+        if ((ee = sample_pivot(c, g, c->bf)) != cudaSuccess) return ee;
         return launch_normalize(c->storage, g, c->bf, c->sp, true, c->num_sms, c->s);
     });
     if (e != cudaSuccess || !c->gh) return e;
@@ -518,6 +533,7 @@ cudaError_t init_solve(ipf_ctx* c, const float* bdev) {
                                          c->bf2.st->status, c->s);
         if (ee != cudaSuccess) return ee;
         if ((ee = launch_update(c->storage, c->g2, c->bf2, c->num_sms, c->s)) != cudaSuccess) return ee;
+        if ((ee = sample_pivot(c, c->g2, c->bf2)) != cudaSuccess) return ee;
         return launch_normalize(c->storage, c->g2, c->bf2, c->sp2, false, c->num_sms, c->s);
     });
 }
@@ -585,6 +601,7 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     ipf_status st = check_op(op, B, &why);
     if (st != IPF_OK) return st;
     if (cfg.method != IPF_METHOD_SCMRH && cfg.method != IPF_METHOD_SLSLU) return IPF_ERR_ARG;
+    if (cfg.pivot_sample < 0 || cfg.pivot_sample > 64) return IPF_ERR_ARG;
     const bool gh = cfg.method == IPF_METHOD_SLSLU;
     if (!gh && op->kind == IPF_OP_CSR && op->rows != op->cols) return IPF_ERR_UNSUPPORTED;   // square A (sCMRH)
     if (gh && op->kind != IPF_OP_PSF2D && op->kind != IPF_OP_CSR) return IPF_ERR_UNSUPPORTED;

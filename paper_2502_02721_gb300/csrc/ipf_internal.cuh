@@ -294,6 +294,9 @@ cudaError_t launch_op_apply_f32_plain(const OpDev& op, const float* v, float* w,
                                       cudaStream_t s);
 // k_hess.cu
 cudaError_t launch_reset_state(DevState* st, cudaStream_t s);
+// sampled pivoting: overwrite the step's pivot choice (after the update)
+cudaError_t launch_sample_pivot(int storage, const Geom& g, const Bufs& bf, unsigned long long seed, int size,
+                                cudaStream_t s);
 cudaError_t launch_load_rhs(int storage, const float* b, const Geom& g, const Bufs& bf, cudaStream_t s);
 cudaError_t launch_pivot_solve(int storage, const Geom& g, const Bufs& bf, cudaStream_t s);
 cudaError_t launch_update(int storage, const Geom& g, const Bufs& bf, int num_sms, cudaStream_t s);

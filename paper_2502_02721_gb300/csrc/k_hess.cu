@@ -693,6 +693,86 @@ __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams
 }
 
 // ------------------------------------------------------------------------
+// sampled pivoting (Sec. 3.2, Sec. 4): the pivot is the largest |w| over a
+// random sample of `size` candidate rows.  Draw t of pivot choice c (c = j+1,
+// 0 at the initialisation) is SplitMix64 output c*4096 + t of the generator
+// started at `seed`, index floor(out * n / 2^64); draws that hit a pivot row
+// or an already accepted row are discarded; at most 4096 draws.  If no more
+// than `size` candidates remain, or every sampled |w| is zero, the full-max
+// key left by the update stands.  One warp per right-hand side.
+// ------------------------------------------------------------------------
+template <class Acc>
+__global__ void k_sample_pivot(Geom g, Bufs bf, unsigned long long seed, int size) {
+    __shared__ long long s_draw[32];
+    __shared__ int s_hit[32];
+    __shared__ long long s_acc[64];
+    __shared__ int s_cnt;
+    const int r = blockIdx.x, lane = threadIdx.x;
+    DevState* st = bf.st;
+    if (st->status[r] != IPF_OK) return;
+    const int jn = st->j + 1;
+    if (jn > g.k_max) return;
+    const long long n = g.n;
+    const int B = g.B;
+    if (n - jn <= size) return;                       // every candidate: the full max stands
+    if (lane == 0) s_cnt = 0;
+    __syncwarp();
+    for (int t0 = 0; t0 < 4096; t0 += 32) {
+        const unsigned long long ctr = (unsigned long long)jn * 4096ull + (unsigned long long)(t0 + lane);
+        const unsigned long long out = sm64_mix(seed + kGamma * (ctr + 1ull));
+        const long long idx = (long long)__umul64hi(out, (unsigned long long)n);
+        const long long e = idx * B + r;
+        s_draw[lane] = idx;
+        s_hit[lane] = (bf.ispiv[e >> 5] >> (unsigned)(e & 31)) & 1u;
+        __syncwarp();
+        if (lane == 0) {
+            int cnt = s_cnt;
+            for (int q = 0; q < 32 && cnt < size; ++q) {
+                if (s_hit[q]) continue;
+                bool dup = false;
+                for (int a = 0; a < cnt; ++a) dup |= s_acc[a] == s_draw[q];
+                if (!dup) s_acc[cnt++] = s_draw[q];
+            }
+            s_cnt = cnt;
+        }
+        __syncwarp();
+        if (s_cnt >= size) break;
+    }
+    const int cnt = s_cnt;
+    const Acc* w = (const Acc*)bf.w;
+    if (sizeof(Acc) == 4) {
+        unsigned long long best = 0ull;
+        for (int a = lane; a < cnt; a += 32) {
+            const long long idx = s_acc[a];
+            const unsigned long long key = argmax_key((float)w[idx * B + r], (unsigned)idx);
+            best = key > best ? key : best;
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, off);
+            best = o > best ? o : best;
+        }
+        if (lane == 0 && best != 0ull && key_absval(best) > 0.f) st->key[jn & 1][r] = best;
+    } else {
+        // F64 storage (one right-hand side): max |w| bits, then the lowest row
+        unsigned long long bits = 0ull, row = ~0ull;
+        for (int a = lane; a < cnt; a += 32) {
+            const long long idx = s_acc[a];
+            const unsigned long long bb = (unsigned long long)__double_as_longlong(fabs((double)w[idx]));
+            if (bb > bits || (bb == bits && (unsigned long long)idx < row)) { bits = bb; row = (unsigned long long)idx; }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long ob = __shfl_xor_sync(0xffffffffu, bits, off);
+            const unsigned long long orow = __shfl_xor_sync(0xffffffffu, row, off);
+            if (ob > bits || (ob == bits && orow < row)) { bits = ob; row = orow; }
+        }
+        if (lane == 0 && bits != 0ull) {
+            st->maxbits[jn & 1] = bits;
+            st->minidx[jn & 1] = row;
+        }
+    }
+}
+
+// ------------------------------------------------------------------------
 // standalone sketch y = S x (one RHS, FP32 input): max |x| then exact sums
 // ------------------------------------------------------------------------
 __global__ void k_absmax(const float* __restrict__ x, long long n, unsigned* out) {
@@ -953,6 +1033,14 @@ cudaError_t launch_normalize(int storage, const Geom& g, const Bufs& bf, const S
         if (e != cudaSuccess) return e;
         fn<<<grid, 256, smem, s>>>(g, bf, sp, want_sw ? 1 : 0, Bg, lbg, lb);
     });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_pivot(int storage, const Geom& g, const Bufs& bf, unsigned long long seed, int size,
+                                cudaStream_t s) {
+    if (size < 1 || size > 64) return cudaErrorInvalidValue;
+    if (storage == IPF_STORE_F64) k_sample_pivot<double><<<g.B, 32, 0, s>>>(g, bf, seed, size);
+    else k_sample_pivot<float><<<g.B, 32, 0, s>>>(g, bf, seed, size);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,46 @@
+"""Sampled pivoting (Sec. 3.2, Sec. 4) through the C ABI against the oracle
+drawing the same samples: pivots identical (FP64) or identical up to a near
+tie among the sampled entries (FP32), and x_k per iterate."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+from _gpu_common import TIE, compare_solution, ensure_lib, gpu_context  # noqa: E402
+from gen import problems as P  # noqa: E402
+from oracle import operators as ops, scmrh, sketch as sk  # noqa: E402
+
+PIVOT_SEED_XOR = 0xA5A5A5A5A5A5A5A5       # include/ipf.h, config.pivot_sample
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    return ensure_lib()
+
+
+@pytest.mark.parametrize("storage,sample", [("f64", 5), ("f64", 25), ("f32", 25)])
+def test_sampled_pivoting_scmrh(storage, sample):
+    p = P.make("deblur64")
+    A = ops.make_apply(p)
+    S = sk.SparseSignSketch(p.sketch_seed, p.n, p.m_s, p.zeta)
+    b = p.b[0].astype(np.float64)
+    st = scmrh.run(A, b, S, p.k, pivot_sample=sample, pivot_seed=p.sketch_seed ^ PIVOT_SEED_XOR)
+    full = scmrh.run(A, b, S, p.k)
+    assert st.piv != full.piv                       # the samples change the pivot order
+    ctx = gpu_context(p, storage, pivot_sample=sample)
+    ctx.step(p.k)
+    status, kd = ctx.sync()
+    assert kd == [p.k]
+    piv = [int(v) for v in ctx.export(0)["piv"][:p.k + 1]]
+    j = next((i for i in range(p.k + 1) if piv[i] != st.piv[i]), p.k + 1)
+    if storage == "f64":
+        assert j == p.k + 1, j
+    elif j <= p.k:
+        # a near tie between the two sampled entries in the oracle's vector at
+        # that choice (v_j = u / u(p_j), so the ratio test is the one on u)
+        vec = b if j == 0 else scmrh.run(A, b, S, j, forced_pivots=st.piv[:j + 1]).V[:, j]
+        a, bb = abs(vec[piv[j]]), abs(vec[st.piv[j]])
+        assert abs(a - bb) <= TIE[storage] * max(a, bb), (j, a, bb)
+    ks = [k for k in (1, 2, 5, 10, 20, 30, 50) if k < j]
+    compare_solution(ctx, st, storage, ks, p.lambdas)
+    ctx.close()

@@ -13,6 +13,7 @@ from gen import problems as P  # noqa: E402
 from oracle import operators as ops, slslu, sketch as sk  # noqa: E402
 
 S1_SEED_XOR = 0x5DEECE66DA3B1F27          # S_1 seed = config seed XOR this (include/ipf.h)
+PIVOT_SEED_XOR = 0xA5A5A5A5A5A5A5A5       # sampled-pivoting seed = config seed XOR this (include/ipf.h)
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -24,9 +25,10 @@ def _sketches(seed, m, n, m_s, zeta):
     return sk.SparseSignSketch(seed ^ S1_SEED_XOR, n, m_s, zeta), sk.SparseSignSketch(seed, m, m_s, zeta)
 
 
-def _context(op, b, k, m_s, zeta, seed, storage, keep, nrhs=1):
+def _context(op, b, k, m_s, zeta, seed, storage, keep, nrhs=1, pivot_sample=0):
     from paper_2502_02721_gb300 import binding as bd
-    cfg = bd.default_config(k_max=k, m_s=m_s, zeta=zeta, seed=seed, storage=storage, nrhs=nrhs, method="slslu")
+    cfg = bd.default_config(k_max=k, m_s=m_s, zeta=zeta, seed=seed, storage=storage, nrhs=nrhs, method="slslu",
+                            pivot_sample=pivot_sample)
     return bd.Context(op, b, cfg, keep)
 
 
@@ -34,17 +36,17 @@ def _first_divergence(a, b, k):
     return next((j for j in range(k + 1) if int(a[j]) != int(b[j])), k + 1)
 
 
-def _perturbed(A, At, b, S1, S2, k, delta, seed=12345, forced=(None, None)):
+def _perturbed(A, At, b, S1, S2, k, delta, seed=12345, forced=(None, None), **sampling):
     """The oracle with every operator output perturbed elementwise by a
     relative N(0, delta^2) error: the response of the process to rounding in
     the products at that level."""
     rng = np.random.default_rng(seed)
     Ap = lambda v: (lambda w: w * (1.0 + delta * rng.standard_normal(w.size)))(A(v))
     Atp = lambda v: (lambda w: w * (1.0 + delta * rng.standard_normal(w.size)))(At(v))
-    return slslu.run(Ap, Atp, b, S1, S2, k, forced_t=forced[0], forced_g=forced[1])
+    return slslu.run(Ap, Atp, b, S1, S2, k, forced_t=forced[0], forced_g=forced[1], **sampling)
 
 
-def _verify(ctx, A, At, b, S1, S2, k, storage, taps, ks, lambdas):
+def _verify(ctx, A, At, b, S1, S2, k, storage, taps, ks, lambdas, **sampling):
     """Pivots, then iterates.
 
     Max-|.| pivoting in the generalized process is chaotic: a relative
@@ -58,7 +60,7 @@ def _verify(ctx, A, At, b, S1, S2, k, storage, taps, ks, lambdas):
     (ii) the iterates are compared with the oracle replaying the GPU's pivot
     sequences, within max(floor, 10 u_s kappa(Z_k), 10 r_k), r_k the replay's
     own response to that perturbation."""
-    st = slslu.run(A, At, b, S1, S2, k)
+    st = slslu.run(A, At, b, S1, S2, k, **sampling)
     ex, du = ctx.export(0), ctx.export_dual(0)
     gt = [int(v) for v in ex["piv"][:k + 1]]
     gg = [int(v) for v in du["piv"][:k + 1]]
@@ -68,7 +70,7 @@ def _verify(ctx, A, At, b, S1, S2, k, storage, taps, ks, lambdas):
     if j_gpu <= k:
         j_or = k + 1
         for seed in (1, 2, 3):
-            sp = _perturbed(A, At, b, S1, S2, k, delta, seed)
+            sp = _perturbed(A, At, b, S1, S2, k, delta, seed, **sampling)
             j_or = min(j_or, _first_divergence(sp.pt, st.pt, k), _first_divergence(sp.pg, st.pg, k))
         assert j_gpu >= j_or - 3, (j_gpu, j_or)
     st_f = slslu.run(A, At, b, S1, S2, k, forced_t=gt, forced_g=gg)
@@ -126,9 +128,11 @@ def _ct_rect(nimg=32, nangles=40, ndet=48, seed=2502021 + 13):
     return rowptr, colind, vals, b, x
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32"])
-def test_rectangular_ct_slslu_parity(storage):
-    """m = 40 angles x 48 detectors = 1920 rays, n = 32 x 32 = 1024 pixels."""
+@pytest.mark.parametrize("storage,sample", [("f64", 0), ("f32", 0), ("f64", 25), ("f32", 25)])
+def test_rectangular_ct_slslu_parity(storage, sample):
+    """m = 40 angles x 48 detectors = 1920 rays, n = 32 x 32 = 1024 pixels;
+    full max pivoting, and sampled pivoting with 25 entries (the paper's CT
+    setting, Sec. 4)."""
     from scipy.sparse import csr_matrix
     from paper_2502_02721_gb300 import binding as bd
     rowptr, colind, vals, b, _ = _ct_rect()
@@ -140,11 +144,16 @@ def test_rectangular_ct_slslu_parity(storage):
     taps = int(np.max(np.diff(rowptr)))
     keep = []
     op = bd.make_operator("csr", m, n, rowptr=rowptr, colind=colind, vals=vals, keep=keep)
-    ctx = _context(op, b.reshape(1, -1), k, m_s, zeta, seed, storage, keep)
+    ctx = _context(op, b.reshape(1, -1), k, m_s, zeta, seed, storage, keep, pivot_sample=sample)
     ctx.step(k)
     status, kd = ctx.sync()
     assert kd == [k]
-    _verify(ctx, A, At, b.astype(np.float64), S1, S2, k, storage, taps, [1, 3, 10, 25, 40], [0.0, 0.1])
+    sampling = {}
+    if sample:
+        sampling = dict(pivot_sample=sample,
+                        pivot_seeds=(seed ^ PIVOT_SEED_XOR, seed ^ PIVOT_SEED_XOR ^ S1_SEED_XOR))
+    _verify(ctx, A, At, b.astype(np.float64), S1, S2, k, storage, taps, [1, 3, 10, 25, 40], [0.0, 0.1],
+            **sampling)
     x, _ = ctx.solve(k, [0.0])
     assert x.shape == (1, 1, n)
     ctx.close()
