@@ -399,9 +399,12 @@ def run_ct_batch(torch, stream, steps: int = 3) -> dict:
     b_dev = torch.from_numpy(p.b.copy()).to(f"cuda:{dev}")
     out = {"workload": "CT 256x256, 256 angles x 256 detectors, CSR FP32 (%d nonzeros), 32 RHS batched, "
                        "k=150, m_s=600" % int(p.rowptr[-1])}
-    for method, storage in (("scmrh", "f32"), ("scmrh", "bf16"), ("slslu", "f32"), ("slslu", "bf16")):
+    variants = (("scmrh", "f32", 0), ("scmrh", "bf16", 0), ("slslu", "f32", 0), ("slslu", "bf16", 0),
+                ("slslu", "bf16", 25))
+    for method, storage, sample in variants:
         cfg = bd.default_config(k_max=p.k, m_s=p.m_s, zeta=p.zeta, seed=p.sketch_seed, storage=storage,
-                                nrhs=p.nrhs, use_graphs=1, stream=stream.cuda_stream, method=method)
+                                nrhs=p.nrhs, use_graphs=1, stream=stream.cuda_stream, method=method,
+                                pivot_sample=sample)
         ctx = bd.Context(op, b_dev, cfg, keep)
         xo = torch.zeros((1, p.nrhs, p.n), dtype=torch.float32, device=f"cuda:{dev}")
         ctx.reset(b_dev)
@@ -426,7 +429,7 @@ def run_ct_batch(torch, stream, steps: int = 3) -> dict:
         for kk in (10, 20, 40, 80):
             xk, _ = ctx.solve(kk, [0.0])
             errs[kk] = med_err(xk[0].astype(np.float64))
-        key = storage if method == "scmrh" else f"slslu_{storage}"
+        key = storage if method == "scmrh" else f"slslu_{storage}" + (f"_sampled{sample}" if sample else "")
         out[key] = {"ms_per_batch": ms, "solves_per_s": p.nrhs / (ms * 1e-3),
                     "iters_per_s": p.nrhs * p.k / (ms * 1e-3), "median_err_vs_xtrue": err,
                     "median_err_vs_xtrue_by_k": {str(kk): v for kk, v in errs.items()}}
