@@ -179,10 +179,19 @@ def solve(st: HessenbergState, k: int, lam: float = 0.0, zform: str = "hessenber
     return st.V[:, :k] @ y
 
 
-def cmrh_solve(st: HessenbergState, k: int) -> np.ndarray:
-    """CMRH quasi-minimal residual iterate (Eq. Hessenber_LS with M = L_{k+1}):
-    y = argmin ||beta e_1 - H_k y||, x = V_k y."""
+def qmr_y(H: np.ndarray, beta: float, k: int, lam: float = 0.0) -> np.ndarray:
+    """y = argmin ||beta e_1 - H_{k+1,k} y||^2 + lam^2 ||y||^2: the quasi-minimal
+    residual problem of Eq. (Hessenber_LS) (M^+ (A x - b) = H y - beta e_1),
+    with the Tikhonov term of Eq. (TSP) when lam > 0."""
     rhs = np.zeros(k + 1)
-    rhs[0] = st.beta
-    y = _lstsq_qr(st.H[:k + 1, :k], rhs)
-    return st.V[:, :k] @ y
+    rhs[0] = beta
+    Hk = H[:k + 1, :k]
+    if lam == 0.0:
+        return _lstsq_qr(Hk, rhs)
+    return _lstsq_qr(np.vstack([Hk, lam * np.eye(k)]), np.concatenate([rhs, np.zeros(k)]))
+
+
+def cmrh_solve(st: HessenbergState, k: int, lam: float = 0.0) -> np.ndarray:
+    """CMRH quasi-minimal residual iterate (Eq. Hessenber_LS with M = L_{k+1}),
+    HCMRH for lam > 0 (Eq. TSP): x = V_k y."""
+    return st.V[:, :k] @ qmr_y(st.H, st.beta, k, lam)

@@ -42,7 +42,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import pivoting
-from .scmrh import _argmax_abs_excluding, _lstsq_qr
+from .scmrh import _argmax_abs_excluding, _lstsq_qr, qmr_y
 
 
 @dataclass
@@ -200,9 +200,7 @@ def solve(st: GenHessenbergState, k: int, lam: float = 0.0, zform: str = "hessen
     return st.L[:, :k] @ solve_y(st, k, lam, zform)
 
 
-def lslu_solve(st: GenHessenbergState, k: int) -> np.ndarray:
-    """LSLU quasi-minimal residual iterate (Eq. Hessenber_LS with M = D_{k+1}):
-    y = argmin ||beta e_1 - H_{k+1,k} y||, x = L_k y."""
-    rhs = np.zeros(k + 1)
-    rhs[0] = st.beta
-    return st.L[:, :k] @ _lstsq_qr(st.H[:k + 1, :k], rhs)
+def lslu_solve(st: GenHessenbergState, k: int, lam: float = 0.0) -> np.ndarray:
+    """LSLU quasi-minimal residual iterate (Eq. Hessenber_LS with M = D_{k+1}),
+    with the Tikhonov term of Eq. (TSP) for lam > 0: x = L_k y."""
+    return st.L[:, :k] @ qmr_y(st.H, st.beta, k, lam)

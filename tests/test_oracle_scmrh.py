@@ -185,3 +185,26 @@ def test_pivot_ties_take_lowest_index():
     b = np.array([1.0, -3.0, 3.0, 2.0])
     st = scmrh.run(lambda v: A @ v, b, sk.IdentitySketch(4), 1)
     assert st.piv[0] == 1 and st.beta == -3.0
+
+
+@pytest.mark.parametrize("lam", [0.0, 0.2])
+def test_qmr_iterate_solves_its_normal_equations(lam):
+    """Eq. (Hessenber_LS) / Eq. (TSP): y minimises ||beta e_1 - H y||^2 +
+    lam^2 ||y||^2, i.e. (H^T H + lam^2 I) y = beta H^T e_1 (normal equations,
+    solved independently), and for lam = 0 the residual of the CMRH iterate
+    obeys the bounds of Eq. (eqthm) with M = L_{k+1}."""
+    A, b = _rand_system(30, 8)
+    st = scmrh.run(lambda v: A @ v, b, sk.IdentitySketch(30), 12)
+    k = 10
+    H = st.H[:k + 1, :k]
+    y = scmrh.qmr_y(st.H, st.beta, k, lam)
+    e1 = np.zeros(k + 1)
+    e1[0] = st.beta
+    y_ne = np.linalg.solve(H.T @ H + lam ** 2 * np.eye(k), H.T @ e1)
+    assert np.linalg.norm(y - y_ne) <= 1e-10 * np.linalg.norm(y_ne)
+    if lam == 0.0:
+        x = scmrh.cmrh_solve(st, k)
+        x_ls = scmrh.solve(st, k)                    # S = I: the minimal residual iterate
+        r, r_ls = np.linalg.norm(A @ x - b), np.linalg.norm(A @ x_ls - b)
+        kappa = np.linalg.cond(st.V[:, :k + 1])
+        assert r_ls <= r * (1 + 1e-12) and r <= kappa * r_ls * (1 + 1e-12)
