@@ -236,6 +236,16 @@ ipf_status ipf_solve(ipf_ctx* ctx, int k, const double* lambdas, int nl,
  * Arrays of 10 entries, host; synchronises.                               */
 ipf_status ipf_profile_read(ipf_ctx* ctx, double* ms, long long* launches, double* bytes);
 
+/* The quasi-minimal residual iterate of the same basis, without the sketch
+ * (Eq. Hessenber_LS: CMRH for SCMRH contexts, LSLU for SLSLU contexts), with
+ * the Tikhonov term of Eq. TSP for lambda > 0:
+ *     y = argmin ||beta e_1 - H_{k+1,k} y||^2 + lambda^2 ||y||^2,
+ * x = V_k y (L_k y for SLSLU).  The paper's non-sketched comparison method.
+ * Arguments, layout and errors as ipf_solve; IPF_ERR_UNSUPPORTED if
+ * k + 1 > m_s (the (k+1)-row problem is solved in the sketch's workspace). */
+ipf_status ipf_solve_qmr(ipf_ctx* ctx, int k, const double* lambdas, int nl, float* x_out, int x_mem,
+                         ipf_solve_info* info);
+
 /* Copy the method's state for RHS r to host memory (any pointer may be
  * NULL): pivots (k_max+1 ints, 0-based rows, -1 past the last pivot),
  * H ((k_max+1) x k_max FP64, column-major, column j holds H(0..j+1, j)),

@@ -94,6 +94,8 @@ SIGNATURES = {
     "ipf_last_error": (C.c_char_p, [C.c_void_p]),
     "ipf_op_create": (C.c_int, [C.POINTER(ipf_operator), C.POINTER(C.c_void_p)]),
     "ipf_op_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "ipf_solve_qmr": (C.c_int, [C.c_void_p, C.c_int, _dp, C.c_int, C.c_void_p, C.c_int,
+                                C.POINTER(ipf_solve_info)]),
     "ipf_export_dual": (C.c_int, [C.c_void_p, C.c_int, _ip, _dp, _dp, _dp]),
     "ipf_export_basis_l": (C.c_int, [C.c_void_p, C.c_int, C.c_int, _fp]),
     "ipf_op_apply_bf16": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
@@ -280,10 +282,11 @@ class Context:
         st = self._check(self._lib.ipf_sync(self.h, kd), "ipf_sync")
         return st, list(kd)
 
-    def solve(self, k: int, lambdas=(0.0,), out=None, wait: bool = True):
+    def solve(self, k: int, lambdas=(0.0,), out=None, wait: bool = True, qmr: bool = False):
         """x for every lambda: numpy (nl, nrhs, n) float32, or into ``out``
         (a CUDA tensor or pinned host tensor of that shape, written in place).
-        wait=False with a CUDA ``out`` returns without synchronising."""
+        wait=False with a CUDA ``out`` returns without synchronising.
+        qmr=True gives the quasi-minimal residual iterate (ipf_solve_qmr)."""
         lam = np.ascontiguousarray(np.asarray(lambdas, dtype=np.float64).reshape(-1))
         nl = lam.size
         info = (ipf_solve_info * self.nrhs)() if wait or out is None or not getattr(out, "is_cuda", False) else None
@@ -294,8 +297,9 @@ class Context:
             x = out
             _check_size(out, nl * self.nrhs * self.n, "out")
             ptr, mem = _ptr(out)
-        st = self._lib.ipf_solve(self.h, int(k), lam.ctypes.data_as(_dp), nl, ptr, mem, info)
-        self._check(st, "ipf_solve")
+        fn = self._lib.ipf_solve_qmr if qmr else self._lib.ipf_solve
+        st = fn(self.h, int(k), lam.ctypes.data_as(_dp), nl, ptr, mem, info)
+        self._check(st, "ipf_solve_qmr" if qmr else "ipf_solve")
         return x, ([(i.k_used, i.k_done, i.status) for i in info] if info is not None else None)
 
     def export(self, r: int = 0):

@@ -863,7 +863,8 @@ ipf_status ipf_sync(ipf_ctx* c, int* k_done) {
     return worst(h, c->B);
 }
 
-ipf_status ipf_solve(ipf_ctx* c, int k, const double* lambdas, int nl, float* x_out, int x_mem, ipf_solve_info* info) {
+static ipf_status solve_impl(ipf_ctx* c, int k, const double* lambdas, int nl, float* x_out, int x_mem,
+                             ipf_solve_info* info, bool qmr) {
     if (!c) return IPF_ERR_ARG;
     if (c->sticky != IPF_OK) return c->sticky;
     if (k < 0 || nl < 1 || !lambdas || !x_out) return IPF_ERR_ARG;
@@ -877,7 +878,9 @@ ipf_status ipf_solve(ipf_ctx* c, int k, const double* lambdas, int nl, float* x_
     const int nlm = lam_chunk(c->B);
     bool any_pos = false;
     for (int l = 0; l < nl; ++l) any_pos |= lambdas[l] > 0.0;
-    const bool need_T = any_pos && c->cfg.penalty == IPF_PEN_SKETCHED_X;
+    if (qmr && k + 1 > g.m_s) return IPF_ERR_UNSUPPORTED;   // [H | beta e_1] fills the m_s-row workspace
+    const bool need_T = !qmr && any_pos && c->cfg.penalty == IPF_PEN_SKETCHED_X;
+    const int penalty = qmr ? IPF_PEN_Y : c->cfg.penalty;
     // generalized process: Z and c from the D side, the penalty S_1 L_k from
     // the L side, x = L_k y with the D side's completed-step count
     Bufs bz = c->bf;
@@ -891,7 +894,8 @@ ipf_status ipf_solve(ipf_ctx* c, int k, const double* lambdas, int nl, float* x_
         bx.st = c->bf.st;
     }
     e = timed(c, 5, 0.0, [&] {
-        return launch_solve_prepare(g, bz, c->cfg.zeta, k, need_T, sw_on(c), c->solve_ws, nlm, c->num_sms, c->s);
+        return launch_solve_prepare(g, bz, c->cfg.zeta, k, need_T, sw_on(c), c->solve_ws, nlm, c->num_sms, c->s,
+                                    qmr);
     });
     if (e != cudaSuccess) return cuda_fail(c, "solve prepare", e);
     const size_t slice = (size_t)gx.n * c->B;
@@ -903,8 +907,8 @@ ipf_status ipf_solve(ipf_ctx* c, int k, const double* lambdas, int nl, float* x_
         float* dst = x_mem == IPF_MEM_DEVICE ? x_out + (size_t)l0 * slice : c->x_stage;
         const double xb = (double)k * gx.N * storage_bytes(c->storage) + (double)nlc * gx.N * 4.0;
         e = timed(c, 6, xb, [&] {
-            return launch_solve_lambdas(c->storage, gx, bx, k, need_T, c->lam_dev, nlc, c->cfg.penalty, c->solve_ws,
-                                        nlm, dst, c->num_sms, c->s);
+            return launch_solve_lambdas(c->storage, gx, bx, k, need_T, c->lam_dev, nlc, penalty, c->solve_ws, nlm,
+                                        dst, c->num_sms, c->s);
         });
         if (e != cudaSuccess) return cuda_fail(c, "solve", e);
         if (x_mem == IPF_MEM_HOST) {
@@ -929,6 +933,15 @@ ipf_status ipf_solve(ipf_ctx* c, int k, const double* lambdas, int nl, float* x_
             info[r].pad = 0;
         }
     return worst(h, c->B);
+}
+
+ipf_status ipf_solve(ipf_ctx* c, int k, const double* lambdas, int nl, float* x_out, int x_mem, ipf_solve_info* info) {
+    return solve_impl(c, k, lambdas, nl, x_out, x_mem, info, false);
+}
+
+ipf_status ipf_solve_qmr(ipf_ctx* c, int k, const double* lambdas, int nl, float* x_out, int x_mem,
+                         ipf_solve_info* info) {
+    return solve_impl(c, k, lambdas, nl, x_out, x_mem, info, true);
 }
 
 ipf_status ipf_export(ipf_ctx* c, int r, int* pivots, double* H, double* SV, double* SZ, double* cvec, double* beta) {

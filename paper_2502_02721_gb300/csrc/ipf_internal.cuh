@@ -318,7 +318,7 @@ cudaError_t launch_sketch_finish(const long long* acc, int m, long long n, int z
 size_t solve_workspace_bytes(const Geom& g, int nl_max);
 // form M = [Z | c] (and T = S V_k) and their R factors
 cudaError_t launch_solve_prepare(const Geom& g, const Bufs& bf, int zeta, int k, bool need_T, bool use_sw,
-                                 void* work, int nl_max, int num_sms, cudaStream_t s);
+                                 void* work, int nl_max, int num_sms, cudaStream_t s, bool qmr = false);
 // per lambda: y, then x = V_k y into x_dev ([l][r][n] float32)
 cudaError_t launch_solve_lambdas(int storage, const Geom& g, const Bufs& bf, int k, bool need_T,
                                  const double* lambdas_dev, int nl, int penalty, void* work, int nl_max,

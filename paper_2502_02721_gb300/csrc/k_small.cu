@@ -54,7 +54,12 @@ __device__ __forceinline__ int kuse_of(const DevState* st, int r, int k) {
 // (S w) the sketch of the unrounded normalised vector when the storage
 // rounds it (use_sw, the DIRECT form) and S V otherwise (then the two forms
 // coincide: S V_{kb+1} H); column kb is c = S b = beta * S (b / beta).
-__global__ void k_form(Geom g, Bufs bf, int k, int zeta, int use_sw, int need_T, double* Mw, double* Tw) {
+//
+// qmr != 0 forms the quasi-minimal residual problem instead (Eq.
+// Hessenber_LS): column col < kb is H(:, col) (rows 0..col+1, zero below)
+// and column kb is beta e_1, so the same QR and per-lambda solves give
+// y = argmin ||beta e_1 - H y||^2 + lambda^2 ||y||^2.
+__global__ void k_form(Geom g, Bufs bf, int k, int zeta, int use_sw, int need_T, double* Mw, double* Tw, int qmr) {
     const int r = blockIdx.y;
     const int kb = kuse_of(bf.st, r, k);
     const int K1 = g.k_max + 1;
@@ -74,7 +79,10 @@ __global__ void k_form(Geom g, Bufs bf, int k, int zeta, int use_sw, int need_T,
          t += (long long)gridDim.x * blockDim.x) {
         const int col = (int)(t / m), row = (int)(t - (long long)col * m);
         double val;
-        if (col < kb) {
+        if (qmr) {
+            if (col < kb) val = row <= col + 1 ? H[(size_t)K1 * col + row] : 0.0;
+            else val = row == 0 ? beta : 0.0;
+        } else if (col < kb) {
             double s = 0.0;
             const double* Hc = H + (size_t)K1 * col;
             for (int i = 0; i <= col; ++i) s = fma((double)sv[(size_t)i * m + row] * scale, Hc[i], s);
@@ -359,7 +367,7 @@ cudaError_t solve_error_flag(const void* work, const Geom& g, int* flag) {
 }
 
 cudaError_t launch_solve_prepare(const Geom& g, const Bufs& bf, int zeta, int k, bool need_T, bool use_sw,
-                                 void* work, int nl_max, int num_sms, cudaStream_t s) {
+                                 void* work, int nl_max, int num_sms, cudaStream_t s, bool qmr) {
     SolveLayout L = layout_for(g, nl_max);
     char* base = (char*)work;
     double* Mw = (double*)(base + L.M_off);
@@ -372,7 +380,7 @@ cudaError_t launch_solve_prepare(const Geom& g, const Bufs& bf, int zeta, int k,
     if (e != cudaSuccess) return e;
     {
         dim3 grid((unsigned)((g.m_s * (k + 1) + 255) / 256), (unsigned)g.B);
-        k_form<<<grid, 256, 0, s>>>(g, bf, k, zeta, use_sw ? 1 : 0, need_T ? 1 : 0, Mw, Tw);
+        k_form<<<grid, 256, 0, s>>>(g, bf, k, zeta, use_sw ? 1 : 0, need_T ? 1 : 0, Mw, Tw, qmr ? 1 : 0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int njobs = g.B * (need_T ? 2 : 1);

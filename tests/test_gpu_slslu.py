@@ -116,6 +116,11 @@ def test_deblur64_slslu_parity(deblur64_slslu, storage):
     assert rel(du["W"][:2, 0], st.W[:2, 1]) < (1e-12 if storage == "f64" else 1e-5)
     if storage == "f64":
         assert j_gpu == p.k + 1
+        # the LSLU quasi-minimal residual iterate on the same bases
+        for k in (1, 5, 20):
+            x, _ = ctx.solve(k, [0.0, 0.05], qmr=True)
+            for li, lam in enumerate((0.0, 0.05)):
+                assert rel(x[li, 0].astype(np.float64), slslu.lslu_solve(st, k, lam)) <= 2e-7
     ctx.close()
 
 
