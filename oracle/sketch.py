@@ -113,6 +113,48 @@ class SparseSignSketch:
         return S
 
 
+def round_to(a: np.ndarray, storage: str) -> np.ndarray:
+    """Entries rounded (to nearest even) to a storage type, returned as float64."""
+    a = np.asarray(a, dtype=np.float64)
+    if storage == "f64":
+        return a.copy()
+    if storage == "f32":
+        return a.astype(np.float32).astype(np.float64)
+    if storage == "f16":
+        return a.astype(np.float16).astype(np.float64)
+    if storage == "bf16":
+        u = a.astype(np.float32).view(np.uint32).astype(np.uint64)
+        u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+        return (u.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    raise ValueError(storage)
+
+
+class GaussianSketch:
+    """Gaussian embedding S (l x n) with N(0, 1/l) entries (Sec. 2; the
+    experiments of Sec. 4 use it), drawn from the SplitMix64 counter hash by
+    the Box-Muller transform (Box & Muller, Ann. Math. Stat. 1958): entry
+    (r, i) takes outputs 2c and 2c + 1, c = r*n + i, of the generator started
+    at ``seed``; u = ((out >> 11) + 1) * 2^-53 lies in (0, 1];
+    z = sqrt(-2 ln u_1) cos(2 pi u_2); S[r, i] = z / sqrt(l).  ``storage``
+    rounds the entries to the type the library keeps S in."""
+
+    def __init__(self, seed: int, n: int, m_s: int, storage: str = "f64"):
+        self.seed, self.n, self.m = int(seed), int(n), int(m_s)
+        c = np.arange(self.m * self.n, dtype=np.uint64)
+        o1 = splitmix64_at(self.seed, 2 * c)
+        o2 = splitmix64_at(self.seed, 2 * c + np.uint64(1))
+        u1 = ((o1 >> np.uint64(11)).astype(np.float64) + 1.0) * 2.0 ** -53
+        u2 = ((o2 >> np.uint64(11)).astype(np.float64) + 1.0) * 2.0 ** -53
+        z = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+        self.S = round_to((z / np.sqrt(self.m)).reshape(self.m, self.n), storage)
+
+    def apply(self, x):
+        return self.S @ np.asarray(x, dtype=np.float64)
+
+    def matrix(self):
+        return self.S
+
+
 class IdentitySketch:
     """S = I: the sketched problem is the unsketched one."""
 

@@ -100,3 +100,37 @@ def test_sparse_sign_preserves_norm_in_expectation():
               for s in range(400)]
     mean, sd = np.mean(ratios), np.std(ratios) / np.sqrt(len(ratios))
     assert abs(mean - 1.0) < 4 * sd + 1e-3
+
+
+def test_gaussian_sketch_entries_are_n01_over_l():
+    """Box-Muller on the counter hash: entries N(0, 1/l) — mean, variance,
+    kurtosis within CLT bands and a Kolmogorov-Smirnov test on l * n = 400k
+    entries; a different seed gives an uncorrelated matrix."""
+    from scipy import stats
+    l, n = 100, 4000
+    S = sk.GaussianSketch(2024, n, l).matrix()
+    z = S.ravel() * np.sqrt(l)
+    N = z.size
+    assert abs(z.mean()) < 5 / np.sqrt(N)
+    assert abs(z.var() - 1.0) < 5 * np.sqrt(2.0 / N)
+    assert abs(stats.kurtosis(z)) < 5 * np.sqrt(24.0 / N)
+    assert stats.kstest(z, "norm").pvalue > 1e-4
+    z2 = sk.GaussianSketch(2025, n, l).matrix().ravel() * np.sqrt(l)
+    assert abs(np.corrcoef(z, z2)[0, 1]) < 5 / np.sqrt(N)
+
+
+def test_gaussian_sketch_is_an_embedding_in_expectation():
+    """E||S x||^2 = ||x||^2 (Eq. 3 in expectation) over seeds."""
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(300)
+    vals = [np.linalg.norm(sk.GaussianSketch(s, 300, 40).apply(x)) ** 2 for s in range(300)]
+    # ||Sx||^2 / ||x||^2 ~ chi^2_l / l: mean 1, sd sqrt(2/l)
+    ratio = np.array(vals) / np.dot(x, x)
+    assert abs(ratio.mean() - 1.0) < 4 * np.sqrt(2.0 / 40) / np.sqrt(300)
+
+
+def test_round_to_bf16_is_rne():
+    v = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, -3.140625, 1e-30])
+    r = sk.round_to(v, "bf16")
+    assert r[0] == 1.0 and r[1] == 1.0 and r[2] == 1.0 + 2 ** -7 and r[3] == -3.140625
+    assert abs(r[4] - 1e-30) <= 2 ** -8 * 1e-30
