@@ -95,6 +95,23 @@ enum ipf_zform { IPF_Z_DIRECT = 0, IPF_Z_HESSENBERG = 1, IPF_Z_AUTO = 2 };
  *        ignored); the penalty is always the sketched-x form.               */
 enum ipf_method { IPF_METHOD_SCMRH = 0, IPF_METHOD_SLSLU = 1 };
 
+/* The sketching matrix S (m_s x n).
+ * SPARSE_SIGN  the block sparse-sign embedding (see ipf_sketch_apply),
+ *              applied to each basis vector as it is formed, exact sums.
+ * GAUSSIAN     the Gaussian embedding of the paper's experiments (Sec. 2,
+ *              Sec. 4): N(0, 1/m_s) entries from the SplitMix64 counter hash
+ *              by Box-Muller (entry (r, i) from outputs 2c, 2c+1, c = r*n + i,
+ *              of the generator started at config.seed; u = ((out >> 11) + 1)
+ *              2^-53; z = sqrt(-2 ln u1) cos(2 pi u2); S = z / sqrt(m_s)),
+ *              rounded to the storage type and kept in device memory
+ *              (m_s x n elements).  No per-step sketch: S V_{k+1} is one GEMM
+ *              (cuBLAS, FP32 accumulation, FP64 for F64 storage) at solve
+ *              time and c = S b an FP64 product at initialisation.  SCMRH with
+ *              nrhs == 1 only (else IPF_ERR_UNSUPPORTED, also when cuBLAS
+ *              cannot be loaded); the Z form is HESSENBERG; ipf_export's
+ *              SV, SZ and c are those of the sparse-sign path (zero here). */
+enum ipf_sketch { IPF_SKETCH_SPARSE_SIGN = 0, IPF_SKETCH_GAUSSIAN = 1 };
+
 /* Forward operator.  For PSF kinds n = rows*cols and images are row-major.
  * For CSR, rows x cols is m x n and the method needs m == n (square A).
  * mem says where psf/sep_row/sep_col/motion/rowptr/colind/vals live:
@@ -137,6 +154,7 @@ typedef struct ipf_config {
                                     the operator beside the pivot-row products and the
                                     FP64 pivot-block solve                                   */
     int method;                  /* enum ipf_method (default IPF_METHOD_SCMRH)               */
+    int sketch;                  /* enum ipf_sketch (default IPF_SKETCH_SPARSE_SIGN)        */
     int pivot_sample;            /* 0 (default): each pivot is the largest |.| over all
                                     candidate rows.  1..64: sampled pivoting (Sec. 3.2,
                                     Sec. 4): the largest |.| over that many candidate rows

@@ -45,12 +45,14 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
 
 METHOD = {"scmrh": 0, "slslu": 1}
+SKETCH = {"sparse_sign": 0, "gaussian": 1}
 
 
 class ipf_config(C.Structure):
     _fields_ = [("k_max", C.c_int), ("m_s", C.c_int), ("zeta", C.c_int), ("seed", C.c_ulonglong),
                 ("storage", C.c_int), ("penalty", C.c_int), ("zform", C.c_int), ("nrhs", C.c_int),
-                ("use_graphs", C.c_int), ("profile", C.c_int), ("overlap", C.c_int), ("method", C.c_int), ("pivot_sample", C.c_int),
+                ("use_graphs", C.c_int), ("profile", C.c_int), ("overlap", C.c_int), ("method", C.c_int), ("sketch", C.c_int),
+                ("pivot_sample", C.c_int),
                 ("conv_fma", C.c_int),
                 ("stream", C.c_void_p),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
@@ -223,6 +225,8 @@ def default_config(**kw) -> ipf_config:
             v = STORAGE[v]
         if k == "method" and isinstance(v, str):
             v = METHOD[v]
+        if k == "sketch" and isinstance(v, str):
+            v = SKETCH[v]
         setattr(cfg, k, v)
     return cfg
 

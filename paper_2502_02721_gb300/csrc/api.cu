@@ -275,6 +275,12 @@ struct ipf_ctx {
     // generalized process (SLSLU): g/bf/sp/op are the D side (m-space, A),
     // these the L side (n-space, A^T)
     bool gh = false;
+    // Gaussian sketch: S (m_s x n, storage type), S V_{k+1} and c = S b, cuBLAS handle
+    bool gauss = false;
+    void* gS = nullptr;
+    void* gSV = nullptr;
+    double* gC = nullptr;
+    void* blas = nullptr;
     OpDev opT;
     Geom g2;
     Bufs bf2;
@@ -525,6 +531,8 @@ cudaError_t init_solve(ipf_ctx* c, const float* bdev) {
         if ((ee = sample_pivot(c, g, c->bf)) != cudaSuccess) return ee;
         return launch_normalize(c->storage, g, c->bf, c->sp, true, c->num_sms, c->s);
     });
+    if (e == cudaSuccess && c->gauss)
+        e = launch_gauss_rhs(c->storage, c->gS, bdev, g.n, g.m_s, c->gC, c->s);
     if (e != cudaSuccess || !c->gh) return e;
     // l_1 = A^T d_1 / (A^T d_1)(g_1): the same vector as A^T r_0 / alpha, and
     // its pivot value is W(1,1)
@@ -580,6 +588,8 @@ size_t ipf_footprint(const ipf_operator* op, const ipf_config* cfg) {
     const size_t ldv = ldv_for(n * B);
     size_t bytes = basis(gh ? op_m(op) : n) + (gh ? basis(n) : 0);
     if (gh) bytes += 2 * (size_t)B * op_m(op) * 4;
+    if (cfg->sketch == IPF_SKETCH_GAUSSIAN)
+        bytes += (size_t)cfg->m_s * n * sb + (size_t)cfg->m_s * K1 * 8 + (size_t)cfg->m_s * 8;
     Geom g; g.n = n; g.B = B; g.N = n * B; g.ldv = (long long)ldv; g.k_max = cfg->k_max; g.m_s = cfg->m_s; g.F = 0;
     bytes += solve_ws_for(g) + 2 * (size_t)B * n * 4 + 256 + ldv * 4 + B * K1 * 4;
     const size_t opb = op->kind == IPF_OP_CSR ? (size_t)(op->rows + 1) * 8 + (size_t)op->nnz * 8
@@ -602,6 +612,9 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     if (st != IPF_OK) return st;
     if (cfg.method != IPF_METHOD_SCMRH && cfg.method != IPF_METHOD_SLSLU) return IPF_ERR_ARG;
     if (cfg.pivot_sample < 0 || cfg.pivot_sample > 64) return IPF_ERR_ARG;
+    if (cfg.sketch != IPF_SKETCH_SPARSE_SIGN && cfg.sketch != IPF_SKETCH_GAUSSIAN) return IPF_ERR_ARG;
+    const bool gauss = cfg.sketch == IPF_SKETCH_GAUSSIAN;
+    if (gauss && (B != 1 || cfg.method != IPF_METHOD_SCMRH)) return IPF_ERR_UNSUPPORTED;
     const bool gh = cfg.method == IPF_METHOD_SLSLU;
     if (!gh && op->kind == IPF_OP_CSR && op->rows != op->cols) return IPF_ERR_UNSUPPORTED;   // square A (sCMRH)
     if (gh && op->kind != IPF_OP_PSF2D && op->kind != IPF_OP_CSR) return IPF_ERR_UNSUPPORTED;
@@ -620,6 +633,10 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     const long long nD = gh ? op_m(op) : n;       // length of b (the D space)
     const long long nmax = n > nD ? n : nD;
     if (nmax * B >= (1ll << 31) || nmax >= (1ll << 29)) return IPF_ERR_UNSUPPORTED;
+    if (gauss) {
+        cfg.zform = IPF_Z_HESSENBERG;             // S A V_k = (S V_{k+1}) H from the solve-time GEMM
+        if (cfg.overlap == 1) cfg.overlap = 0;
+    }
     if (gh) {
         cfg.overlap = 0;                          // one stream per step
         cfg.zform = IPF_Z_HESSENBERG;
@@ -628,6 +645,7 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
 
     ipf_ctx* c = new ipf_ctx();
     c->gh = gh;
+    c->gauss = gauss;
     c->cfg = cfg;
     c->storage = cfg.storage;
     c->B = B;
@@ -679,6 +697,7 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
         g.m_s = cfg.m_s;
         g.F = cfg.storage == IPF_STORE_F64 ? fixed_exponent(np, 0) : kSplitS;
         g.want_z = cfg.zform == IPF_Z_DIRECT ? 1 : 0;
+        g.sketch_off = gauss ? 1 : 0;
         sp = make_sketch_params(seed, cfg.m_s, cfg.zeta);
         const size_t K1 = (size_t)cfg.k_max + 1;
         const size_t sb = storage_bytes(cfg.storage);
@@ -700,7 +719,7 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
             AK(cudaMemsetAsync(bf.t, 0, g.ldv * sizeof(float), c->s));
         }
         if (c->split || c->fork_piv) AK(c->al.get((void**)&bf.gpiv, B * K1 * sizeof(float)));
-        if (sketch_table_ok(sp)) {
+        if (!gauss && sketch_table_ok(sp)) {
             unsigned long long* tab = nullptr;
             AK(c->al.get((void**)&tab, sizeof(unsigned long long) * (size_t)np));
             AK(launch_sketch_table(sp, np, tab, c->s));
@@ -725,6 +744,18 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     }
     Geom& g = c->g;
     Bufs& bf = c->bf;
+    if (gauss) {
+        c->blas = gauss_blas_create();
+        if (!c->blas) {
+            ipf_destroy(c);
+            return IPF_ERR_UNSUPPORTED;                // cuBLAS not available
+        }
+        const size_t sb = storage_bytes(cfg.storage);
+        CK("alloc Gaussian S", c->al.get(&c->gS, (size_t)cfg.m_s * n * sb));
+        CK("alloc S V", c->al.get(&c->gSV, (size_t)cfg.m_s * (cfg.k_max + 1) * (cfg.storage == IPF_STORE_F64 ? 8 : 4)));
+        CK("alloc S b", c->al.get((void**)&c->gC, sizeof(double) * cfg.m_s));
+        CK("Gaussian S", launch_gauss_fill(cfg.storage, c->gS, n, cfg.m_s, cfg.seed, c->num_sms, c->s));
+    }
     c->solve_ws_bytes = solve_ws_for(g);
     CK("alloc solve", c->al.get(&c->solve_ws, c->solve_ws_bytes));
     CK("alloc lambdas", c->al.get((void**)&c->lam_dev, sizeof(double) * kLamChunk));
@@ -892,6 +923,16 @@ static ipf_status solve_impl(ipf_ctx* c, int k, const double* lambdas, int nl, f
         gx = c->g2;
         bx = c->bf2;
         bx.st = c->bf.st;
+    }
+    if (c->gauss && !qmr) {
+        // S V_{k+1} by one GEMM with the stored Gaussian S
+        e = timed(c, 5, 0.0, [&] {
+            return launch_gauss_sv(c->blas, c->storage, c->gS, g.m_s, g.n, c->bf.V, g.ldv, k + 1, c->gSV, c->s);
+        });
+        if (e != cudaSuccess) return cuda_fail(c, "Gaussian sketch GEMM", e);
+        bz.svd = c->gSV;
+        bz.svd_f64 = c->storage == IPF_STORE_F64 ? 1 : 0;
+        bz.cvec = c->gC;
     }
     e = timed(c, 5, 0.0, [&] {
         return launch_solve_prepare(g, bz, c->cfg.zeta, k, need_T, sw_on(c), c->solve_ws, nlm, c->num_sms, c->s,
@@ -1092,6 +1133,7 @@ ipf_status ipf_export_basis_l(ipf_ctx* c, int r, int j, float* l_out) {
 void ipf_destroy(ipf_ctx* c) {
     if (!c) return;
     if (c->s) cudaStreamSynchronize(c->s);
+    if (c->blas) gauss_blas_destroy(c->blas);
     for (auto& m : c->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
     for (auto ev : c->spare) cudaEventDestroy(ev);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);

@@ -217,6 +217,7 @@ struct Geom {
     int m_s;
     int F;              // fixed-point exponent of the sketch accumulators
     int want_z;         // DIRECT form: z_j = S A v_j (needs S of the unrounded vectors)
+    int sketch_off = 0; // Gaussian sketch: no per-step sparse sketch (S V is formed at solve time)
 };
 
 struct Bufs {
@@ -241,6 +242,11 @@ struct Bufs {
     DevState* st_peer = nullptr;
     const long long* penSV = nullptr;
     int penF = 0;
+    // Gaussian sketch: S V_{k+1} (m_s x (k+1), column-major, FP64 if svd_f64
+    // else FP32) and c = S b (m_s, FP64), formed at solve time; NULL otherwise
+    const void* svd = nullptr;
+    int svd_f64 = 0;
+    const double* cvec = nullptr;
 };
 
 // operator on the device
@@ -294,6 +300,15 @@ cudaError_t launch_op_apply_f32_plain(const OpDev& op, const float* v, float* w,
                                       cudaStream_t s);
 // k_hess.cu
 cudaError_t launch_reset_state(DevState* st, cudaStream_t s);
+// Gaussian sketch (gauss.cu)
+cudaError_t launch_gauss_fill(int storage, void* S, long long n, int m, unsigned long long seed, int num_sms,
+                              cudaStream_t s);
+cudaError_t launch_gauss_rhs(int storage, const void* S, const float* b, long long n, int m, double* c,
+                             cudaStream_t s);
+void* gauss_blas_create();
+void gauss_blas_destroy(void* h);
+cudaError_t launch_gauss_sv(void* handle, int storage, const void* S, int m, long long n, const void* V,
+                            long long ldv, int K, void* out, cudaStream_t s);
 // sampled pivoting: overwrite the step's pivot choice (after the update)
 cudaError_t launch_sample_pivot(int storage, const Geom& g, const Bufs& bf, unsigned long long seed, int size,
                                 cudaStream_t s);

@@ -526,7 +526,7 @@ __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams
     // sketch table, no second sketch): the same integer sums with the
     // counter words of +q and -q formed once per element instead of once per
     // sketch row, and the table bytes decoded in 32-bit halves
-    const bool fast = !f64 && Bg == 1 && g.B == 1 && bf.sktab && sp.zeta == 8 && !want_sw;
+    const bool fast = !f64 && Bg == 1 && g.B == 1 && (bf.sktab || g.sketch_off) && sp.zeta == 8 && !want_sw;
     if (fast && any_ok) {
         T* vout = (T*)bf.V + (size_t)jn * g.ldv;
         const unsigned n = (unsigned)g.n;
@@ -545,7 +545,7 @@ __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams
                 const Acc v = ((long long)i == prow) ? (Acc)1 : w[i] / hval;
                 const T vs = from_acc<T>(v);
                 vout[i] = vs;
-                const long long qv = fixed_from(to_acc(vs), kSplitS);
+                const long long qv = g.sketch_off ? 0ll : fixed_from(to_acc(vs), kSplitS);
                 if (qv) {
                     const int hp = (int)(qv >> 17), lp = (int)(qv & 0x1FFFFll);
                     const long long qn = -qv;
@@ -583,8 +583,8 @@ __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams
                 const Acc v = ((long long)i == s_prow[rl]) ? (Acc)1 : w[e] / s_hval[rl];
                 const T vs = from_acc<T>(v);
                 vout[e] = vs;
-                const long long fv = fixed_from(to_acc(vs), F);
-                const long long fw = want_sw ? fixed_from(v, F) : 0;
+                const long long fv = g.sketch_off ? 0ll : fixed_from(to_acc(vs), F);
+                const long long fw = (want_sw && !g.sketch_off) ? fixed_from(v, F) : 0;
                 if (fv || fw) {
                     int rows[16];
                     unsigned neg;

@@ -82,6 +82,21 @@ __global__ void k_form(Geom g, Bufs bf, int k, int zeta, int use_sw, int need_T,
         if (qmr) {
             if (col < kb) val = row <= col + 1 ? H[(size_t)K1 * col + row] : 0.0;
             else val = row == 0 ? beta : 0.0;
+        } else if (bf.svd) {
+            // Gaussian sketch: S V from the solve-time GEMM, c = S b
+            auto svx = [&](int i) -> double {
+                return bf.svd_f64 ? ((const double*)bf.svd)[(size_t)i * m + row]
+                                  : (double)((const float*)bf.svd)[(size_t)i * m + row];
+            };
+            if (col < kb) {
+                double s = 0.0;
+                const double* Hc = H + (size_t)K1 * col;
+                for (int i = 0; i <= col + 1; ++i) s = fma(svx(i), Hc[i], s);
+                val = s;
+                if (need_T) T[(size_t)col * m + row] = svx(col);
+            } else {
+                val = bf.cvec[row];
+            }
         } else if (col < kb) {
             double s = 0.0;
             const double* Hc = H + (size_t)K1 * col;
