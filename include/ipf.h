@@ -104,9 +104,11 @@ enum ipf_method { IPF_METHOD_SCMRH = 0, IPF_METHOD_SLSLU = 1 };
  *              of the generator started at config.seed; u = ((out >> 11) + 1)
  *              2^-53; z = sqrt(-2 ln u1) cos(2 pi u2); S = z / sqrt(m_s)),
  *              rounded to the storage type and kept in device memory
- *              (m_s x n elements).  No per-step sketch: S V_{k+1} is one GEMM
- *              (cuBLAS, FP32 accumulation, FP64 for F64 storage) at solve
- *              time and c = S b an FP64 product at initialisation.  SCMRH with
+ *              (m_s x n elements, see ipf_sketch_gaussian).  No per-step
+ *              sketch: S V_{k+1} is one GEMM (cuBLAS, FP32 accumulation, FP64
+ *              for F64 storage) at solve time; c = S b at initialisation sums
+ *              runs of 32 products in FP32 (FP64 for F64 storage) and adds the
+ *              runs in FP64, in a fixed order.  SCMRH with
  *              nrhs == 1 only (else IPF_ERR_UNSUPPORTED, also when cuBLAS
  *              cannot be loaded); the Z form is HESSENBERG; ipf_export's
  *              SV, SZ and c are those of the sparse-sign path (zero here). */
@@ -247,7 +249,7 @@ ipf_status ipf_solve(ipf_ctx* ctx, int k, const double* lambdas, int nl,
  * kind (0 operator, 1 pivot-block solve, 2 update+argmax or V_j h,
  * 3 normalise+sketch, 4 initialisation, 5 projected-solve QR, 6 per-lambda
  * solve + x = V_k y, 7 operator at the pivot rows, 8 u = A v_j - V_j h with
- * argmax) the summed milliseconds, launch counts and the summed algorithmic
+ * argmax, 9 the Gaussian sketch's S V_{k+1} GEMM) the summed milliseconds, launch counts and the summed algorithmic
  * bytes of the launches (0 where not defined), since the previous read.
  * With config.overlap 1 a step runs the operator on a second stream beside
  * V_j h, so kinds 0 and 2 overlap in time; with overlap 2, kinds 0, 7 and 1.
@@ -322,6 +324,19 @@ void ipf_op_destroy(ipf_op* h);
  * `stream` and frees it before returning.                                  */
 ipf_status ipf_sketch_apply(const float* x_dev, long long n, int m_s, int zeta,
                             unsigned long long seed, double* y_dev, void* stream);
+
+/* Writes the Gaussian sketch S (m_s x n) of config.sketch = GAUSSIAN
+ * (Sec. 2; Box-Muller on the SplitMix64 counter hash as described at
+ * enum ipf_sketch) to S_dev, column-major (entry (r, i) at r + i*m_s), each
+ * entry the FP64 value z / sqrt(m_s) rounded to nearest-even in `storage`
+ * (BF16 through FP32).  BF16 and F16 entries are evaluated in FP32 with an
+ * error bound and recomputed in FP64 where the bound does not fix the
+ * rounded value, so all storage types store the FP64 definition's rounding.
+ * S_dev: device, m_s * n elements of the storage type, caller-owned.
+ * Runs on `stream`, no allocation.  Errors: IPF_ERR_ARG (null S_dev,
+ * n < 1, m_s < 1, unknown storage), IPF_ERR_CUDA (launch failure).        */
+ipf_status ipf_sketch_gaussian(int storage, unsigned long long seed, long long n, int m_s, void* S_dev,
+                               void* stream);
 
 /* ---- serving: many solves in flight on one GPU ---- */
 

@@ -148,6 +148,20 @@ class GaussianSketch:
         z = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
         self.S = round_to((z / np.sqrt(self.m)).reshape(self.m, self.n), storage)
 
+    @staticmethod
+    def entries(seed: int, n: int, m_s: int, rows, cols, storage: str = "f64") -> np.ndarray:
+        """S[rows[t], cols[t]] by the same definition, for a few entries of a
+        sketch too large to form."""
+        r = np.asarray(rows, dtype=np.uint64)
+        i = np.asarray(cols, dtype=np.uint64)
+        c = r * np.uint64(n) + i
+        o1 = splitmix64_at(int(seed), 2 * c)
+        o2 = splitmix64_at(int(seed), 2 * c + np.uint64(1))
+        u1 = ((o1 >> np.uint64(11)).astype(np.float64) + 1.0) * 2.0 ** -53
+        u2 = ((o2 >> np.uint64(11)).astype(np.float64) + 1.0) * 2.0 ** -53
+        z = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+        return round_to(z / np.sqrt(int(m_s)), storage)
+
     def apply(self, x):
         return self.S @ np.asarray(x, dtype=np.float64)
 

@@ -106,6 +106,7 @@ SIGNATURES = {
                                    C.c_void_p]),
     "ipf_sketch_apply_noalloc": (C.c_int, [C.c_void_p, C.c_longlong, C.c_int, C.c_int, C.c_ulonglong,
                                            C.c_void_p, C.c_void_p]),
+    "ipf_sketch_gaussian": (C.c_int, [C.c_int, C.c_ulonglong, C.c_longlong, C.c_int, C.c_void_p, C.c_void_p]),
     "ipf_server_create": (C.c_int, [C.POINTER(ipf_server_config), C.POINTER(C.c_void_p)]),
     "ipf_submit": (C.c_int, [C.c_void_p, C.POINTER(ipf_request), C.POINTER(C.c_ulonglong)]),
     "ipf_poll": (C.c_int, [C.c_void_p, C.c_ulonglong, C.POINTER(ipf_result), C.c_void_p]),
@@ -145,6 +146,15 @@ def _check_size(a, want: int, name: str):
     got = int(a.size) if isinstance(a, np.ndarray) else int(a.numel())
     if got != int(want):
         raise ValueError(f"{name} has {got} elements, expected {want}")
+
+
+def _check_device(a, name: str, elem_bytes: int):
+    """Refuse a tensor that is not in device memory or has the wrong element
+    size for a call that writes it from a kernel."""
+    if not getattr(a, "is_cuda", False):
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if int(a.element_size()) != elem_bytes:
+        raise ValueError(f"{name} has {a.element_size()}-byte elements, expected {elem_bytes}")
 
 
 def status_str(code: int) -> str:
@@ -460,15 +470,29 @@ class Server:
 def sketch_apply(x, m_s: int, zeta: int, seed: int, y, stream=None):
     """y (device float64, m_s) = S x (device float32, n)."""
     _check_size(y, m_s, "y")
+    _check_device(x, "x", 4)
+    _check_device(y, "y", 8)
     st = load().ipf_sketch_apply(x.data_ptr(), int(x.numel()), int(m_s), int(zeta), int(seed), y.data_ptr(), stream)
     if st != IPF_OK:
         raise IpfError(st, "ipf_sketch_apply")
+
+
+def sketch_gaussian(storage: str, seed: int, n: int, m_s: int, S, stream=None):
+    """ipf_sketch_gaussian: the Gaussian sketch (m_s x n, column-major) into
+    the device tensor S of the storage type (m_s * n elements)."""
+    _check_size(S, int(m_s) * int(n), "S")
+    _check_device(S, "S", {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}[storage])
+    st = load().ipf_sketch_gaussian(STORAGE[storage], int(seed), int(n), int(m_s), S.data_ptr(), stream)
+    if st != IPF_OK:
+        raise IpfError(st, "ipf_sketch_gaussian")
 
 
 def sketch_apply_noalloc(x, m_s: int, zeta: int, seed: int, y, stream=None):
     """ipf_sketch_apply_noalloc: y = S x with the library's fixed scratch
     (no device allocation; m_s <= 4096; calls must not overlap on the GPU)."""
     _check_size(y, m_s, "y")
+    _check_device(x, "x", 4)
+    _check_device(y, "y", 8)
     st = load().ipf_sketch_apply_noalloc(x.data_ptr(), int(x.numel()), int(m_s), int(zeta), int(seed),
                                          y.data_ptr(), stream)
     if st != IPF_OK:

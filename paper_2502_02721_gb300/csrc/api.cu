@@ -532,7 +532,7 @@ cudaError_t init_solve(ipf_ctx* c, const float* bdev) {
         return launch_normalize(c->storage, g, c->bf, c->sp, true, c->num_sms, c->s);
     });
     if (e == cudaSuccess && c->gauss)
-        e = launch_gauss_rhs(c->storage, c->gS, bdev, g.n, g.m_s, c->gC, c->s);
+        e = launch_gauss_rhs(c->storage, c->gS, bdev, g.n, g.m_s, c->gC, c->gC + g.m_s, c->s);
     if (e != cudaSuccess || !c->gh) return e;
     // l_1 = A^T d_1 / (A^T d_1)(g_1): the same vector as A^T r_0 / alpha, and
     // its pivot value is W(1,1)
@@ -589,7 +589,7 @@ size_t ipf_footprint(const ipf_operator* op, const ipf_config* cfg) {
     size_t bytes = basis(gh ? op_m(op) : n) + (gh ? basis(n) : 0);
     if (gh) bytes += 2 * (size_t)B * op_m(op) * 4;
     if (cfg->sketch == IPF_SKETCH_GAUSSIAN)
-        bytes += (size_t)cfg->m_s * n * sb + (size_t)cfg->m_s * K1 * 8 + (size_t)cfg->m_s * 8;
+        bytes += (size_t)cfg->m_s * n * sb + (size_t)cfg->m_s * K1 * 8 + 8 * ((size_t)cfg->m_s + kGaussRhsPart(cfg->m_s));
     Geom g; g.n = n; g.B = B; g.N = n * B; g.ldv = (long long)ldv; g.k_max = cfg->k_max; g.m_s = cfg->m_s; g.F = 0;
     bytes += solve_ws_for(g) + 2 * (size_t)B * n * 4 + 256 + ldv * 4 + B * K1 * 4;
     const size_t opb = op->kind == IPF_OP_CSR ? (size_t)(op->rows + 1) * 8 + (size_t)op->nnz * 8
@@ -753,7 +753,7 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
         const size_t sb = storage_bytes(cfg.storage);
         CK("alloc Gaussian S", c->al.get(&c->gS, (size_t)cfg.m_s * n * sb));
         CK("alloc S V", c->al.get(&c->gSV, (size_t)cfg.m_s * (cfg.k_max + 1) * (cfg.storage == IPF_STORE_F64 ? 8 : 4)));
-        CK("alloc S b", c->al.get((void**)&c->gC, sizeof(double) * cfg.m_s));
+        CK("alloc S b", c->al.get((void**)&c->gC, sizeof(double) * (cfg.m_s + kGaussRhsPart(cfg.m_s))));
         CK("Gaussian S", launch_gauss_fill(cfg.storage, c->gS, n, cfg.m_s, cfg.seed, c->num_sms, c->s));
     }
     c->solve_ws_bytes = solve_ws_for(g);
@@ -926,7 +926,10 @@ static ipf_status solve_impl(ipf_ctx* c, int k, const double* lambdas, int nl, f
     }
     if (c->gauss && !qmr) {
         // S V_{k+1} by one GEMM with the stored Gaussian S
-        e = timed(c, 5, 0.0, [&] {
+        const double sb = storage_bytes(c->storage);
+        const double gb = (double)g.m_s * g.n * sb + (double)g.n * (k + 1) * sb +
+                          (double)g.m_s * (k + 1) * (c->storage == IPF_STORE_F64 ? 8.0 : 4.0);
+        e = timed(c, 9, gb, [&] {
             return launch_gauss_sv(c->blas, c->storage, c->gS, g.m_s, g.n, c->bf.V, g.ldv, k + 1, c->gSV, c->s);
         });
         if (e != cudaSuccess) return cuda_fail(c, "Gaussian sketch GEMM", e);
@@ -1229,6 +1232,14 @@ ipf_status ipf_sketch_apply(const float* x_dev, long long n, int m_s, int zeta, 
     cudaError_t e2 = cudaFreeAsync(scratch, s);
     if (e != cudaSuccess || e2 != cudaSuccess) return IPF_ERR_CUDA;
     return IPF_OK;
+}
+
+ipf_status ipf_sketch_gaussian(int storage, unsigned long long seed, long long n, int m_s, void* S_dev, void* stream) {
+    if (!S_dev || n < 1 || m_s < 1) return IPF_ERR_ARG;
+    if (storage != IPF_STORE_F64 && storage != IPF_STORE_F32 && storage != IPF_STORE_BF16 && storage != IPF_STORE_F16)
+        return IPF_ERR_ARG;
+    const cudaError_t e = launch_gauss_fill(storage, S_dev, n, m_s, seed, device_sms(), (cudaStream_t)stream);
+    return e == cudaSuccess ? IPF_OK : IPF_ERR_CUDA;
 }
 
 }  // extern "C"

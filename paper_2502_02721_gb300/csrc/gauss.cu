@@ -6,13 +6,15 @@
 // z = sqrt(-2 ln u1) cos(2 pi u2); S[r, i] = z / sqrt(m_s), rounded to the
 // storage type of the basis.  S is kept column-major (element (r, i) at
 // r + i*m_s), so S V_{k+1} is one dense GEMM with the basis (leading
-// dimension ldv), done at solve time by cuBLAS; c = S b is a fixed-order
-// FP64 reduction per row.  cuBLAS is loaded on first use (dlopen), so the
-// library does not depend on it unless the Gaussian sketch is asked for.
+// dimension ldv), done at solve time by cuBLAS; c = S b is a reduction in
+// a fixed order (FP32 runs of products added into FP64 sums).  cuBLAS is
+// loaded on first use (dlopen), so the library does not depend on it unless
+// the Gaussian sketch is asked for.
 #include <cublas_v2.h>
 #include <dlfcn.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "ipf_internal.cuh"
 
@@ -20,50 +22,178 @@ namespace ipf {
 
 namespace {
 
-template <class T> __device__ __forceinline__ T from_double(double v);
-template <> __device__ __forceinline__ double from_double<double>(double v) { return v; }
-template <> __device__ __forceinline__ float from_double<float>(double v) { return (float)v; }
-// through FP32, as the oracle rounds: FP64 -> FP32 -> BF16 (nearest even)
-template <> __device__ __forceinline__ __nv_bfloat16 from_double<__nv_bfloat16>(double v) {
-    return __float2bfloat16_rn((float)v);
+// One entry in FP64, the definition itself: v = z / sqrt(m).
+__device__ __forceinline__ double gauss_f64(unsigned long long o1, unsigned long long o2, double sqrt_m) {
+    const double u1 = ((double)(o1 >> 11) + 1.0) * 0x1.0p-53;
+    const double u2 = ((double)(o2 >> 11) + 1.0) * 0x1.0p-53;
+    const double z = sqrt(-2.0 * log(u1)) * cos(2.0 * 3.141592653589793 * u2);
+    return z / sqrt_m;
 }
-template <> __device__ __forceinline__ __half from_double<__half>(double v) { return __double2half(v); }
+
+// The same entry rounded to a 16-bit storage type, evaluated in FP32 with an
+// error bound; when the bound's interval does not round to one value of the
+// storage type the entry is recomputed in FP64, so the stored S equals the
+// FP64 definition rounded to storage.
+//  * ln u1: logf of u1 for u1 <= 1/2 (|ln u1| >= ln 2), else log1pf(-eps)
+//    with eps = 1 - u1 formed exactly from the integer (2^53 - 1 - k1);
+//    relative error <= 2.4e-7 (argument rounding 2^-24, 1 ulp of logf /
+//    log1pf).
+//  * cos(2 pi u2) = cos(pi t 2^-52), t = k2 + 1, reduced with integers:
+//    cos(pi x) = -cos(pi (x - 1)), cos(pi y) = -cos(pi (1 - y)) for y > 1/2,
+//    and cos(pi w) = sin(pi (1/2 - w)) for w > 1/4, so cospif or sinpif gets
+//    an argument in [0, 1/4]; relative error <= 1.8e-7.
+//  * R = sqrtf(-2 ln u1) (correctly rounded), v = R C / sqrt(m): relative
+//    error <= 5.4e-7 in all; the interval used is twice that, plus an
+//    absolute 2e-15 R / sqrt(m) for the FP64 definition's own rounding of
+//    2 pi u2 (which matters only where C is near zero).
+template <class T> __device__ __forceinline__ unsigned short store_bits(float v);
+template <> __device__ __forceinline__ unsigned short store_bits<__nv_bfloat16>(float v) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+template <> __device__ __forceinline__ unsigned short store_bits<__half>(float v) {
+    return __half_as_ushort(__float2half_rn(v));
+}
 
 template <class T>
-__global__ void k_gauss_fill(T* __restrict__ S, long long n, int m, unsigned long long seed) {
+__device__ __forceinline__ bool gauss_fast(unsigned long long o1, unsigned long long o2, float inv_sqrt_m,
+                                           unsigned short& bits) {
+    const unsigned long long k1 = o1 >> 11, k2 = o2 >> 11;
+    float L;
+    if (k1 + 1ull <= (1ull << 52)) {
+        L = logf(__ull2float_rn(k1 + 1ull) * 0x1.0p-53f);
+    } else {
+        const unsigned long long e = (1ull << 53) - 1ull - k1;
+        if (e == 0ull) return false;                                 // u1 = 1
+        L = log1pf(-(__ull2float_rn(e) * 0x1.0p-53f));
+    }
+    const float R = sqrtf(-2.f * L);
+    const long long sft = (long long)(k2 + 1ull) - (1ll << 52);
+    unsigned long long a = (unsigned long long)(sft < 0 ? -sft : sft);
+    float sign = -1.f;
+    if (a > (1ull << 51)) {
+        a = (1ull << 52) - a;
+        sign = -sign;
+    }
+    const float C = a <= (1ull << 50) ? cospif(__ull2float_rn(a) * 0x1.0p-52f)
+                                      : sinpif(__ull2float_rn((1ull << 51) - a) * 0x1.0p-52f);
+    const float v = __fmul_rn(__fmul_rn(R, sign * C), inv_sqrt_m);
+    const float E = __fmaf_ru(1.2e-6f, fabsf(v), __fmul_ru(__fmul_ru(2e-15f, R), inv_sqrt_m));
+    const unsigned short lo = store_bits<T>(__fsub_rd(v, E)), hi = store_bits<T>(__fadd_ru(v, E));
+    if (lo != hi) return false;
+    bits = lo;
+    return true;
+}
+
+// flat element t of S (column-major, t = r + i*m) walks with a carried
+// (r, i) instead of a 64-bit division per element; the counter is c = r*n + i
+template <class T>
+__global__ void __launch_bounds__(256) k_gauss_fill(T* __restrict__ S, long long n, int m, unsigned long long seed,
+                                                    double sqrt_m, float inv_sqrt_m) {
     const long long total = n * (long long)m;
-    const double scale = 1.0 / sqrt((double)m);
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        const long long i = t / m, r = t - i * m;                 // storage order: r + i*m
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long sr = stride % m, si = stride / m;
+    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long i = t / m, r = t - i * m;
+    for (; t < total; t += stride) {
         const unsigned long long c = (unsigned long long)(r * n + i);
         const unsigned long long o1 = sm64_mix(seed + kGamma * (2ull * c + 1ull));
         const unsigned long long o2 = sm64_mix(seed + kGamma * (2ull * c + 2ull));
-        const double u1 = ((double)(o1 >> 11) + 1.0) * 0x1.0p-53;
-        const double u2 = ((double)(o2 >> 11) + 1.0) * 0x1.0p-53;
-        const double z = sqrt(-2.0 * log(u1)) * cos(2.0 * 3.141592653589793 * u2);
-        S[t] = from_double<T>(z * scale);
+        if constexpr (sizeof(T) == 2) {
+            unsigned short bits;
+            if (!gauss_fast<T>(o1, o2, inv_sqrt_m, bits)) {
+                const double v = gauss_f64(o1, o2, sqrt_m);
+                if constexpr (std::is_same<T, __half>::value) bits = __half_as_ushort(__double2half(v));
+                else bits = store_bits<T>((float)v);                 // FP64 -> FP32 -> BF16
+            }
+            reinterpret_cast<unsigned short*>(S)[t] = bits;
+        } else {
+            S[t] = (T)gauss_f64(o1, o2, sqrt_m);
+        }
+        r += sr;
+        i += si;
+        if (r >= m) {
+            r -= m;
+            i += 1;
+        }
     }
 }
 
-// c[r] = sum_i S[r, i] b[i] in FP64, one CTA per row, fixed reduction order
-template <class T>
-__global__ void __launch_bounds__(256) k_gauss_rhs(const T* __restrict__ S, const float* __restrict__ b, long long n,
-                                                   int m, double* __restrict__ c) {
-    __shared__ double s_red[8];
-    const int r = blockIdx.x;
-    double acc = 0.0;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x)
-        acc = fma((double)to_acc(S[r + i * (long long)m]), (double)b[i], acc);
+// c = S b with a fixed summation order, in two passes.  Pass 1: CTA q takes
+// the columns [q*n/Q, (q+1)*n/Q); a column of S is cut into vectors of V
+// consecutive rows (16 bytes when the column is 16-byte aligned, else single
+// rows), thread t owns vector t % mv of every column i = i0 + t / mv (mod
+// cpi), so each load is one contiguous piece of a column.  Products are
+// summed in FP32 over runs of kRun of the thread's columns (FP64 for F64
+// storage: every product) and each run sum is added to an FP64 sum; the
+// thread's sums go to part[(q * cpi + phase) * m + row].  Pass 2 adds the
+// Q * cpi partial sums of each row in order.
+constexpr int kRun = 32;
+
+template <class T> struct RhsAcc { using type = float; };
+template <> struct RhsAcc<double> { using type = double; };
+
+template <class T, int V>
+__global__ void __launch_bounds__(256) k_gauss_rhs_part(const T* __restrict__ S, const float* __restrict__ b,
+                                                        long long n, int m, int mv, int cpi,
+                                                        double* __restrict__ part) {
+    using A = typename RhsAcc<T>::type;
+    const int q = blockIdx.x;
+    const long long i0 = n * q / kGaussRhsSlices, i1 = n * (q + 1) / kGaussRhsSlices;
+    const int phase = mv <= (int)blockDim.x ? threadIdx.x / mv : 0;
+    if (phase >= cpi) return;
+    const int vr0 = mv <= (int)blockDim.x ? threadIdx.x % mv : threadIdx.x;
+    const int vstep = mv <= (int)blockDim.x ? mv : blockDim.x;
+    double* out = part + ((size_t)q * cpi + phase) * m;
+    for (int vr = vr0; vr < mv; vr += vstep) {
+        double tot[V];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int q = 0; q < 8; ++q) t += s_red[q];
-        c[r] = t;
+        for (int e = 0; e < V; ++e) tot[e] = 0.0;
+        long long i = i0 + phase;
+        while (i < i1) {
+            A run[V];
+#pragma unroll
+            for (int e = 0; e < V; ++e) run[e] = A(0);
+#pragma unroll 4
+            for (int c = 0; c < kRun; ++c) {
+                if (i >= i1) break;
+                const T* col = S + i * (long long)m + (long long)vr * V;
+                const A bi = (A)__ldg(b + i);
+                if constexpr (V > 1) {
+                    union { uint4 u; T t[V]; } ld;
+                    ld.u = __ldg(reinterpret_cast<const uint4*>(col));
+#pragma unroll
+                    for (int e = 0; e < V; ++e) run[e] = fma((A)to_acc(ld.t[e]), bi, run[e]);
+                } else {
+                    run[0] = fma((A)to_acc(col[0]), bi, run[0]);
+                }
+                i += cpi;
+            }
+#pragma unroll
+            for (int e = 0; e < V; ++e) tot[e] += (double)run[e];
+        }
+#pragma unroll
+        for (int e = 0; e < V; ++e) out[vr * V + e] = tot[e];
     }
+}
+
+__global__ void k_gauss_rhs_sum(const double* __restrict__ part, int nparts, int m, double* __restrict__ c) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= m) return;
+    double t = 0.0;
+    for (int q = 0; q < nparts; ++q) t += part[(size_t)q * m + r];
+    c[r] = t;
+}
+
+template <class T>
+cudaError_t rhs_typed(const T* S, const float* b, long long n, int m, double* c, double* part, cudaStream_t s) {
+    constexpr int V = 16 / (int)sizeof(T);
+    const bool vec = ((size_t)m * sizeof(T)) % 16 == 0 && ((uintptr_t)S & 15) == 0;
+    const int mv = vec ? m / V : m;
+    const int cpi = mv <= 256 ? 256 / mv : 1;
+    if (vec) k_gauss_rhs_part<T, V><<<kGaussRhsSlices, 256, 0, s>>>(S, b, n, m, mv, cpi, part);
+    else k_gauss_rhs_part<T, 1><<<kGaussRhsSlices, 256, 0, s>>>(S, b, n, m, mv, cpi, part);
+    k_gauss_rhs_sum<<<(m + 255) / 256, 256, 0, s>>>(part, kGaussRhsSlices * cpi, m, c);
+    return cudaGetLastError();
 }
 
 // cuBLAS entry points, resolved once
@@ -99,27 +229,31 @@ Blas& blas() {
 
 cudaError_t launch_gauss_fill(int storage, void* S, long long n, int m, unsigned long long seed, int num_sms,
                               cudaStream_t s) {
+    if (n <= 0 || m <= 0) return cudaSuccess;
     const int blocks = num_sms * 8;
+    const double sm = sqrt((double)m);
+    const float inv = (float)(1.0 / sm);
     switch (storage) {
-        case IPF_STORE_F64: k_gauss_fill<double><<<blocks, 256, 0, s>>>((double*)S, n, m, seed); break;
-        case IPF_STORE_F32: k_gauss_fill<float><<<blocks, 256, 0, s>>>((float*)S, n, m, seed); break;
-        case IPF_STORE_BF16: k_gauss_fill<__nv_bfloat16><<<blocks, 256, 0, s>>>((__nv_bfloat16*)S, n, m, seed); break;
-        case IPF_STORE_F16: k_gauss_fill<__half><<<blocks, 256, 0, s>>>((__half*)S, n, m, seed); break;
+        case IPF_STORE_F64: k_gauss_fill<double><<<blocks, 256, 0, s>>>((double*)S, n, m, seed, sm, inv); break;
+        case IPF_STORE_F32: k_gauss_fill<float><<<blocks, 256, 0, s>>>((float*)S, n, m, seed, sm, inv); break;
+        case IPF_STORE_BF16:
+            k_gauss_fill<__nv_bfloat16><<<blocks, 256, 0, s>>>((__nv_bfloat16*)S, n, m, seed, sm, inv);
+            break;
+        case IPF_STORE_F16: k_gauss_fill<__half><<<blocks, 256, 0, s>>>((__half*)S, n, m, seed, sm, inv); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_gauss_rhs(int storage, const void* S, const float* b, long long n, int m, double* c,
-                             cudaStream_t s) {
+                             double* part, cudaStream_t s) {
     switch (storage) {
-        case IPF_STORE_F64: k_gauss_rhs<double><<<m, 256, 0, s>>>((const double*)S, b, n, m, c); break;
-        case IPF_STORE_F32: k_gauss_rhs<float><<<m, 256, 0, s>>>((const float*)S, b, n, m, c); break;
-        case IPF_STORE_BF16: k_gauss_rhs<__nv_bfloat16><<<m, 256, 0, s>>>((const __nv_bfloat16*)S, b, n, m, c); break;
-        case IPF_STORE_F16: k_gauss_rhs<__half><<<m, 256, 0, s>>>((const __half*)S, b, n, m, c); break;
+        case IPF_STORE_F64: return rhs_typed((const double*)S, b, n, m, c, part, s);
+        case IPF_STORE_F32: return rhs_typed((const float*)S, b, n, m, c, part, s);
+        case IPF_STORE_BF16: return rhs_typed((const __nv_bfloat16*)S, b, n, m, c, part, s);
+        case IPF_STORE_F16: return rhs_typed((const __half*)S, b, n, m, c, part, s);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 void* gauss_blas_create() {

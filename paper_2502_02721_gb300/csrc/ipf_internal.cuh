@@ -303,8 +303,12 @@ cudaError_t launch_reset_state(DevState* st, cudaStream_t s);
 // Gaussian sketch (gauss.cu)
 cudaError_t launch_gauss_fill(int storage, void* S, long long n, int m, unsigned long long seed, int num_sms,
                               cudaStream_t s);
+// column slices of c = S b; pass 1 writes at most kGaussRhsSlices x
+// max(m, 2048) FP64 partial sums (kGaussRhsPart(m) doubles)
+constexpr int kGaussRhsSlices = 608;
+inline size_t kGaussRhsPart(int m) { return (size_t)kGaussRhsSlices * (m > 2048 ? m : 2048); }
 cudaError_t launch_gauss_rhs(int storage, const void* S, const float* b, long long n, int m, double* c,
-                             cudaStream_t s);
+                             double* part, cudaStream_t s);
 void* gauss_blas_create();
 void gauss_blas_destroy(void* h);
 cudaError_t launch_gauss_sv(void* handle, int storage, const void* S, int m, long long n, const void* V,

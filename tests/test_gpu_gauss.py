@@ -52,3 +52,61 @@ def test_gaussian_sketch_needs_one_rhs():
     p = P.ct_parallel(side=16, nrhs=2, k=5, m_s=20)
     with pytest.raises(bd.IpfError):
         gpu_context(p, "f32", sketch="gaussian")
+
+
+_TORCH_DT = {"f64": "float64", "f32": "float32", "bf16": "bfloat16", "f16": "float16"}
+
+
+def _as_f64(t):
+    import torch
+    return t.to(torch.float64).cpu().numpy()
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16", "f16"])
+def test_gaussian_sketch_matrix_equals_oracle(storage):
+    """ipf_sketch_gaussian against the oracle's S (same definition, same
+    rounding) on 200 x 20011 entries: identical except where the FP64 log /
+    cos of CUDA and of numpy differ in the last bit and that decides a
+    rounding (expected about once in 1e8 entries for the narrow types); F64
+    entries within 16 ulp: each side's cos is within 2 ulp (CUDA) or 1 ulp
+    (numpy) of the true value, log within 1, and the product, square root and
+    division round once each, so the two sides can be up to about 8 ulp
+    apart."""
+    import torch
+    from paper_2502_02721_gb300 import binding as bd
+    m, n, seed = 200, 20011, 31337
+    S = torch.empty(m * n, dtype=getattr(torch, _TORCH_DT[storage]), device="cuda")
+    bd.sketch_gaussian(storage, seed, n, m, S)
+    torch.cuda.synchronize()
+    got = _as_f64(S).reshape(n, m).T                  # column-major: (r, i) at r + i*m
+    want = sk.GaussianSketch(seed, n, m, storage).matrix()
+    if storage == "f64":
+        assert np.max(np.abs(got - want) / np.maximum(np.abs(want), 1e-300)) <= 16 * 2.0 ** -53
+    else:
+        diff = got != want
+        assert int(diff.sum()) <= 1, int(diff.sum())
+
+
+def test_gaussian_sketch_full_size_samples():
+    """The 800 x 2048^2 BF16 sketch of the deblurring workload (6.7 GB):
+    200k sampled entries against the oracle's per-entry definition, and the
+    entry moments of the whole matrix."""
+    import torch
+    from paper_2502_02721_gb300 import binding as bd
+    m, n, seed = 800, 2048 * 2048, 4242
+    S = torch.empty(m * n, dtype=torch.bfloat16, device="cuda")
+    bd.sketch_gaussian("bf16", seed, n, m, S)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(5)
+    rows = rng.integers(0, m, 200000)
+    cols = rng.integers(0, n, 200000)
+    idx = torch.from_numpy(rows + cols * m).cuda()
+    got = _as_f64(S[idx])
+    want = sk.GaussianSketch.entries(seed, n, m, rows, cols, "bf16")
+    assert int((got != want).sum()) == 0
+    z = S[:m << 20].float() * np.sqrt(m)                    # the first 800M entries
+    N = z.numel()
+    assert abs(float(z.mean())) < 5 / np.sqrt(N)
+    assert abs(float(z.var()) - 1.0) < 5 * np.sqrt(2.0 / N) + 2e-3   # + BF16 rounding of the entries
+    del S, z
+    torch.cuda.empty_cache()

@@ -129,6 +129,18 @@ def test_gaussian_sketch_is_an_embedding_in_expectation():
     assert abs(ratio.mean() - 1.0) < 4 * np.sqrt(2.0 / 40) / np.sqrt(300)
 
 
+def test_gaussian_sketch_entries_match_matrix():
+    """The per-entry evaluation gives the matrix's entries (same definition,
+    used to check samples of sketches too large to form)."""
+    l, n = 30, 500
+    rng = np.random.default_rng(4)
+    rows, cols = rng.integers(0, l, 300), rng.integers(0, n, 300)
+    for storage in ("f64", "bf16", "f16"):
+        S = sk.GaussianSketch(77, n, l, storage).matrix()
+        e = sk.GaussianSketch.entries(77, n, l, rows, cols, storage)
+        assert np.array_equal(e, S[rows, cols])
+
+
 def test_round_to_bf16_is_rne():
     v = np.array([1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, -3.140625, 1e-30])
     r = sk.round_to(v, "bf16")
