@@ -154,7 +154,10 @@ typedef struct ipf_config {
     int overlap;                 /* PSF2D/CSR with float storage, second stream per step:
                                     0 one stream; 1 the operator beside V_j h; 2 (default)
                                     the operator beside the pivot-row products and the
-                                    FP64 pivot-block solve                                   */
+                                    FP64 pivot-block solve, and (one RHS, zeta 8, no DIRECT
+                                    Z with BF16/FP16) the sketch S v_j of the previous
+                                    column on a third stream beside them, the newest
+                                    column's sketch taken before a solve or export     */
     int method;                  /* enum ipf_method (default IPF_METHOD_SCMRH)               */
     int sketch;                  /* enum ipf_sketch (default IPF_SKETCH_SPARSE_SIGN)        */
     int pivot_sample;            /* 0 (default): each pivot is the largest |.| over all
@@ -247,13 +250,15 @@ ipf_status ipf_solve(ipf_ctx* ctx, int k, const double* lambdas, int nl,
 
 /* Kernel timings of a context created with config.profile = 1: for each
  * kind (0 operator, 1 pivot-block solve, 2 update+argmax or V_j h,
- * 3 normalise+sketch, 4 initialisation, 5 projected-solve QR, 6 per-lambda
- * solve + x = V_k y, 7 operator at the pivot rows, 8 u = A v_j - V_j h with
- * argmax, 9 the Gaussian sketch's S V_{k+1} GEMM) the summed milliseconds, launch counts and the summed algorithmic
- * bytes of the launches (0 where not defined), since the previous read.
- * With config.overlap 1 a step runs the operator on a second stream beside
- * V_j h, so kinds 0 and 2 overlap in time; with overlap 2, kinds 0, 7 and 1.
- * Arrays of 10 entries, host; synchronises.                               */
+ * 3 normalise (+ sketch unless deferred), 4 initialisation, 5 projected-solve
+ * QR, 6 per-lambda solve + x = V_k y, 7 operator at the pivot rows,
+ * 8 u = A v_j - V_j h with argmax, 9 the Gaussian sketch's S V_{k+1} GEMM,
+ * 10 sampled pivot choice, 11 deferred sketch S v_j) the summed
+ * milliseconds, launch counts and the summed algorithmic bytes of the
+ * launches (0 where not defined), since the previous read.  With
+ * config.overlap 1 a step runs the operator on a second stream beside V_j h,
+ * so kinds 0 and 2 overlap in time; with overlap 2, kinds 0, 7, 1 and 11.
+ * Arrays of 12 entries, host; synchronises.                               */
 ipf_status ipf_profile_read(ipf_ctx* ctx, double* ms, long long* launches, double* bytes);
 
 /* The quasi-minimal residual iterate of the same basis, without the sketch

@@ -279,10 +279,10 @@ class Context:
         self._check(self._lib.ipf_reset(self.h, ptr, mem), "ipf_reset")
 
     def profile_read(self):
-        """(ms[10], launches[10], bytes[10]) per kernel kind since the last read."""
-        ms = (C.c_double * 10)()
-        n = (C.c_longlong * 10)()
-        by = (C.c_double * 10)()
+        """(ms[12], launches[12], bytes[12]) per kernel kind since the last read."""
+        ms = (C.c_double * 12)()
+        n = (C.c_longlong * 12)()
+        by = (C.c_double * 12)()
         self._check(self._lib.ipf_profile_read(self.h, ms, n, by), "ipf_profile_read")
         return list(ms), list(n), list(by)
 

@@ -270,6 +270,7 @@ struct ipf_ctx {
     cudaStream_t user = nullptr;
     cudaEvent_t ev = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool defer_sketch = false;          // S v_{j+1} taken by the next step's update (or before a solve)
     bool split = false;                 // operator overlapped with the V_j stream
     bool fork_piv = false;              // operator overlapped with the pivot-block solve
     // generalized process (SLSLU): g/bf/sp/op are the D side (m-space, A),
@@ -299,9 +300,9 @@ struct ipf_ctx {
     struct Mark { int kind; double bytes; cudaEvent_t a, b; };
     std::vector<Mark> marks;
     std::vector<cudaEvent_t> spare;
-    double prof_ms[10] = {0};
-    long long prof_n[10] = {0};
-    double prof_bytes[10] = {0};
+    double prof_ms[kProfKinds] = {0};
+    long long prof_n[kProfKinds] = {0};
+    double prof_bytes[kProfKinds] = {0};
 };
 
 struct ipf_op {
@@ -393,7 +394,15 @@ cudaError_t sample_pivot(ipf_ctx* c, const Geom& g, const Bufs& bf) {
     if (c->cfg.pivot_sample <= 0) return cudaSuccess;
     const unsigned long long seed = c->cfg.seed ^ 0xA5A5A5A5A5A5A5A5ull ^
                                     (bf.st == c->bf.st ? 0ull : 0x5DEECE66DA3B1F27ull);
-    return timed(c, 9, 0.0, [&] { return launch_sample_pivot(c->storage, g, bf, seed, c->cfg.pivot_sample, c->s); });
+    return timed(c, 10, 0.0, [&] { return launch_sample_pivot(c->storage, g, bf, seed, c->cfg.pivot_sample, c->s); });
+}
+
+// the deferred sketch of the pending column on `st` (a no-op kernel when
+// nothing is pending)
+cudaError_t sketch_pending(ipf_ctx* c, cudaStream_t st) {
+    if (!c->defer_sketch) return cudaSuccess;
+    const double b = (double)c->g.N * storage_bytes(c->storage) + (double)c->g.n * 8.0;
+    return timed_on(c, st, 11, b, [&] { return launch_sketch_col(c->storage, c->g, c->bf, c->sp, c->num_sms, st); });
 }
 
 // one Hessenberg step; every kernel takes j from device memory, so the same
@@ -414,7 +423,7 @@ cudaError_t half_step(ipf_ctx* c, const OpDev& op, const Bufs& in, const Geom& g
         return e;
     if ((e = timed(c, 1, 0.0, [&] { return launch_pivot_solve(c->storage, g, bf, c->s); })) != cudaSuccess) return e;
     if ((e = timed(c, 2, (double)(j + 1) * N * sv + 2.0 * N * ab + N / 8.0,
-                   [&] { return launch_update(c->storage, g, bf, c->num_sms, c->s); })) != cudaSuccess)
+                   [&] { return launch_update(c->storage, g, bf, sp, c->num_sms, c->s); })) != cudaSuccess)
         return e;
     if ((e = sample_pivot(c, g, bf)) != cudaSuccess) return e;
     return timed(c, 3, N * ab + N * sv,
@@ -481,7 +490,7 @@ cudaError_t one_step(ipf_ctx* c, int j) {
             return e;
         if ((e = cudaStreamWaitEvent(c->s, c->ev_join, 0)) != cudaSuccess) return e;
         if ((e = timed(c, 2, (double)(j + 1) * N * sv + 2.0 * N * ab + N / 8.0,
-                       [&] { return launch_update(c->storage, c->g, c->bf, c->num_sms, c->s); })) != cudaSuccess)
+                       [&] { return launch_update(c->storage, c->g, c->bf, c->sp, c->num_sms, c->s); })) != cudaSuccess)
             return e;
         if ((e = sample_pivot(c, c->g, c->bf)) != cudaSuccess) return e;
         return timed(c, 3, N * ab + N * sv,
@@ -495,7 +504,7 @@ cudaError_t one_step(ipf_ctx* c, int j) {
     if ((e = timed(c, 1, 0.0, [&] { return launch_pivot_solve(c->storage, c->g, c->bf, c->s); })) != cudaSuccess)
         return e;
     if ((e = timed(c, 2, (double)(j + 1) * N * sv + 2.0 * N * ab + N / 8.0,
-                   [&] { return launch_update(c->storage, c->g, c->bf, c->num_sms, c->s); })) != cudaSuccess)
+                   [&] { return launch_update(c->storage, c->g, c->bf, c->sp, c->num_sms, c->s); })) != cudaSuccess)
         return e;
     if ((e = sample_pivot(c, c->g, c->bf)) != cudaSuccess) return e;
     return timed(c, 3, N * ab + N * sv,
@@ -512,6 +521,7 @@ cudaError_t init_solve(ipf_ctx* c, const float* bdev) {
     if ((e = cudaMemsetAsync(c->bf.ispiv, 0, (g.ldv / 32 + 1) * sizeof(unsigned), c->s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->bf.accSV, 0, B * K1 * g.m_s * sizeof(long long), c->s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(c->bf.accSW, 0, B * K1 * g.m_s * sizeof(long long), c->s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(c->bf.colE, 0, B * K1 * sizeof(int), c->s)) != cudaSuccess) return e;
     if (c->gh) {
         const Geom& g2 = c->g2;
         if ((e = cudaMemsetAsync(c->bf2.H, 0, B * K1 * g2.k_max * sizeof(double), c->s)) != cudaSuccess) return e;
@@ -521,15 +531,18 @@ cudaError_t init_solve(ipf_ctx* c, const float* bdev) {
             return e;
         if ((e = cudaMemsetAsync(c->bf2.accSW, 0, B * K1 * g2.m_s * sizeof(long long), c->s)) != cudaSuccess)
             return e;
+        if ((e = cudaMemsetAsync(c->bf2.colE, 0, B * K1 * sizeof(int), c->s)) != cudaSuccess) return e;
         if ((e = launch_reset_state(c->bf2.st, c->s)) != cudaSuccess) return e;
     }
     e = timed(c, 4, 0.0, [&] {
         cudaError_t ee = launch_reset_state(c->bf.st, c->s);
         if (ee != cudaSuccess) return ee;
         if ((ee = launch_load_rhs(c->storage, bdev, g, c->bf, c->s)) != cudaSuccess) return ee;
-        if ((ee = launch_update(c->storage, g, c->bf, c->num_sms, c->s)) != cudaSuccess) return ee;
+        if ((ee = launch_update(c->storage, g, c->bf, c->sp, c->num_sms, c->s)) != cudaSuccess) return ee;
         if ((ee = sample_pivot(c, g, c->bf)) != cudaSuccess) return ee;
-        return launch_normalize(c->storage, g, c->bf, c->sp, true, c->num_sms, c->s);
+        Geom gi = g;
+        gi.sketch_defer = 0;                       // v_1 (and S b) sketched here
+        return launch_normalize(c->storage, gi, c->bf, c->sp, true, c->num_sms, c->s);
     });
     if (e == cudaSuccess && c->gauss)
         e = launch_gauss_rhs(c->storage, c->gS, bdev, g.n, g.m_s, c->gC, c->gC + g.m_s, c->s);
@@ -540,7 +553,7 @@ cudaError_t init_solve(ipf_ctx* c, const float* bdev) {
         cudaError_t ee = launch_op_apply(c->opT, c->storage, c->bf.V, g.ldv, g.k_max + 1, &c->bf.st->j, B, c->bf2.w,
                                          c->bf2.st->status, c->s);
         if (ee != cudaSuccess) return ee;
-        if ((ee = launch_update(c->storage, c->g2, c->bf2, c->num_sms, c->s)) != cudaSuccess) return ee;
+        if ((ee = launch_update(c->storage, c->g2, c->bf2, c->sp2, c->num_sms, c->s)) != cudaSuccess) return ee;
         if ((ee = sample_pivot(c, c->g2, c->bf2)) != cudaSuccess) return ee;
         return launch_normalize(c->storage, c->g2, c->bf2, c->sp2, false, c->num_sms, c->s);
     });
@@ -581,8 +594,8 @@ size_t ipf_footprint(const ipf_operator* op, const ipf_config* cfg) {
     auto basis = [&](long long np) -> size_t {
         const size_t l = ldv_for(np * B);
         size_t b = K1 * l * sb + l * acc + l / 8 + 4096;
-        b += B * K1 * (sizeof(int) + sizeof(double) * cfg->k_max + sizeof(double) * K1) + K1 * B * acc;
-        return b + 2 * (size_t)B * K1 * cfg->m_s * 8 + (size_t)np * 8;
+        b += B * K1 * (2 * sizeof(int) + sizeof(double) * cfg->k_max + sizeof(double) * K1) + K1 * B * acc;
+        return b + 2 * (size_t)B * K1 * cfg->m_s * 8 + l * 8;
     };
     const bool gh = cfg->method == IPF_METHOD_SLSLU;
     const size_t ldv = ldv_for(n * B);
@@ -712,6 +725,8 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
         AK(c->al.get((void**)&bf.ispiv, (g.ldv / 32 + 1) * sizeof(unsigned)));
         AK(c->al.get((void**)&bf.accSV, B * K1 * cfg.m_s * sizeof(long long)));
         AK(c->al.get((void**)&bf.accSW, B * K1 * cfg.m_s * sizeof(long long)));
+        AK(c->al.get((void**)&bf.colE, B * K1 * sizeof(int)));
+        bf.sampled = cfg.pivot_sample > 0 ? 1 : 0;
         bf.t = nullptr;
         bf.gpiv = nullptr;
         if (c->split) {
@@ -721,7 +736,9 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
         if (c->split || c->fork_piv) AK(c->al.get((void**)&bf.gpiv, B * K1 * sizeof(float)));
         if (!gauss && sketch_table_ok(sp)) {
             unsigned long long* tab = nullptr;
-            AK(c->al.get((void**)&tab, sizeof(unsigned long long) * (size_t)np));
+            // ldv entries (the update reads the table 16 bytes at a time up to ldv)
+            AK(c->al.get((void**)&tab, sizeof(unsigned long long) * (size_t)g.ldv));
+            AK(cudaMemsetAsync(tab, 0, sizeof(unsigned long long) * (size_t)g.ldv, c->s));
             AK(launch_sketch_table(sp, np, tab, c->s));
             bf.sktab = tab;
         } else {
@@ -744,6 +761,13 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     }
     Geom& g = c->g;
     Bufs& bf = c->bf;
+    // the sketch of each new column moves from the normaliser into the next
+    // step's update, which streams that column anyway (one RHS, float
+    // storage with the zeta = 8 table, no sketch of unrounded vectors)
+    c->defer_sketch = B == 1 && !gh && !gauss && !c->split && c->storage != IPF_STORE_F64 && bf.sktab &&
+                      cfg.zeta == 8 && !sw_on(c) &&
+                      (((uintptr_t)bf.V | (uintptr_t)bf.sktab) & 15u) == 0 && (g.ldv & 7) == 0;
+    g.sketch_defer = c->defer_sketch ? 1 : 0;
     if (gauss) {
         c->blas = gauss_blas_create();
         if (!c->blas) {
@@ -811,7 +835,7 @@ ipf_status ipf_profile_read(ipf_ctx* c, double* ms, long long* launches, double*
         c->spare.push_back(m.b);
     }
     c->marks.clear();
-    for (int k = 0; k < 10; ++k) {
+    for (int k = 0; k < kProfKinds; ++k) {
         if (ms) ms[k] = c->prof_ms[k];
         if (launches) launches[k] = c->prof_n[k];
         if (bytes) bytes[k] = c->prof_bytes[k];
@@ -914,11 +938,13 @@ static ipf_status solve_impl(ipf_ctx* c, int k, const double* lambdas, int nl, f
     const int penalty = qmr ? IPF_PEN_Y : c->cfg.penalty;
     // generalized process: Z and c from the D side, the penalty S_1 L_k from
     // the L side, x = L_k y with the D side's completed-step count
+    if ((e = sketch_pending(c, c->s)) != cudaSuccess) return cuda_fail(c, "sketch", e);
     Bufs bz = c->bf;
     Geom gx = g;
     Bufs bx = c->bf;
     if (c->gh) {
         bz.penSV = c->bf2.accSV;
+        bz.penE = c->bf2.colE;
         bz.penF = c->g2.F;
         gx = c->g2;
         bx = c->bf2;
@@ -992,6 +1018,8 @@ ipf_status ipf_export(ipf_ctx* c, int r, int* pivots, double* H, double* SV, dou
     if (!c) return IPF_ERR_ARG;
     if (c->sticky != IPF_OK) return c->sticky;
     if (r < 0 || r >= c->B) return IPF_ERR_ARG;
+    cudaError_t e0 = sketch_pending(c, c->s);                 // the newest column's S v
+    if (e0 != cudaSuccess) return cuda_fail(c, "sketch", e0);
     DevState h;
     ipf_status st = read_state(c, &h);
     if (st != IPF_OK) return st;
@@ -1012,11 +1040,15 @@ ipf_status ipf_export(ipf_ctx* c, int r, int* pivots, double* H, double* SV, dou
         if (e != cudaSuccess) return cuda_fail(c, "export H", e);
     }
     const double sq = std::sqrt((double)c->cfg.zeta);
+    std::vector<int> ce(K1);
+    if ((e = cudaMemcpy(ce.data(), c->bf.colE + r * K1, K1 * sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(c, "export column exponents", e);
+    // column t / m of a fixed-point sketch block carries the exponent ce[t / m]
     auto grab = [&](const long long* src, size_t count, double scale, double* dst) -> cudaError_t {
         std::vector<long long> a(count);
         cudaError_t ee = cudaMemcpy(a.data(), src, count * sizeof(long long), cudaMemcpyDeviceToHost);
         if (ee != cudaSuccess) return ee;
-        for (size_t t = 0; t < count; ++t) dst[t] = (double)a[t] * scale;
+        for (size_t t = 0; t < count; ++t) dst[t] = (double)a[t] * std::ldexp(scale, ce[t / m]);
         return cudaSuccess;
     };
     if (SV && (e = grab(c->bf.accSV + r * K1 * m, K1 * m, std::ldexp(1.0, -c->g.F) / sq, SV)) != cudaSuccess)
@@ -1120,8 +1152,11 @@ ipf_status ipf_export_dual(ipf_ctx* c, int r, int* pivots_l, double* W, double* 
         if ((e = cudaMemcpy(a.data(), c->bf2.accSV + r * K1 * m, a.size() * sizeof(long long),
                             cudaMemcpyDeviceToHost)) != cudaSuccess)
             return cuda_fail(c, "export SL", e);
+        std::vector<int> ce(K1);
+        if ((e = cudaMemcpy(ce.data(), c->bf2.colE + r * K1, K1 * sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(c, "export SL", e);
         const double sc = std::ldexp(1.0, -c->g2.F) / std::sqrt((double)c->cfg.zeta);
-        for (size_t t = 0; t < a.size(); ++t) SL[t] = (double)a[t] * sc;
+        for (size_t t = 0; t < a.size(); ++t) SL[t] = (double)a[t] * std::ldexp(sc, ce[t / m]);
     }
     if (w11) *w11 = h.beta[r];
     return IPF_OK;

@@ -14,6 +14,9 @@
 
 namespace ipf {
 
+// kernel kinds of the profile mode (ipf_profile_read)
+constexpr int kProfKinds = 12;
+
 // ---------------------------------------------------------------------------
 // storage types: T is how basis vectors live in HBM, Acc the arithmetic type
 // ---------------------------------------------------------------------------
@@ -205,6 +208,9 @@ struct DevState {
     unsigned long long key[2][kMaxRhs];      // argmax keys, double-buffered by step parity
     unsigned long long maxbits[2];           // F64 mode: max |w| bits (nrhs == 1)
     unsigned long long minidx[2];            // F64 mode: lowest row attaining it
+    double wmax[kMaxRhs];          // sampled pivoting: max |w| over the candidates of this step
+    int sk_pending;                // deferred sketch: column of V still to be sketched, or -1
+    unsigned sk_ctr;               // last-CTA ticket for the deferred sketch kernel
 };
 
 // everything a kernel needs about the context, passed by value
@@ -218,6 +224,8 @@ struct Geom {
     int F;              // fixed-point exponent of the sketch accumulators
     int want_z;         // DIRECT form: z_j = S A v_j (needs S of the unrounded vectors)
     int sketch_off = 0; // Gaussian sketch: no per-step sparse sketch (S V is formed at solve time)
+    int sketch_defer = 0;  // the normaliser leaves S v_{j+1} to k_sketch_col (launched beside the
+                           // next step's operator, or before a solve) and marks the column pending
 };
 
 struct Bufs {
@@ -232,6 +240,10 @@ struct Bufs {
     long long* accSV;              // [B][k_max+1][m_s] fixed-point S V
     long long* accSW;              // [B][k_max+1][m_s] fixed-point S of the unrounded vectors
                                    // (column 0 = S (b / beta), others for BF16/FP16 storage)
+    int* colE;                     // [B][k_max+1] column exponents: column j of accSV / accSW
+                                   // holds S v_j * 2^(F - colE[j]), so |v_j| <= 2^colE[j] keeps
+                                   // the fixed-point sums in range (0 unless pivots are sampled)
+    int sampled;                   // pivots are sampled, so |v_j| may exceed 1
     const unsigned long long* sktab;  // n entries (zeta = 8, blocks <= 128 rows) or NULL:
                                       // byte t = row offset in block t | sign << 7
     float* t;                      // ldv FP32: V_j h (split step), else NULL
@@ -241,6 +253,7 @@ struct Bufs {
     // (S_1 L) with their fixed-point exponent; NULL / 0 for one basis
     DevState* st_peer = nullptr;
     const long long* penSV = nullptr;
+    const int* penE = nullptr;
     int penF = 0;
     // Gaussian sketch: S V_{k+1} (m_s x (k+1), column-major, FP64 if svd_f64
     // else FP32) and c = S b (m_s, FP64), formed at solve time; NULL otherwise
@@ -318,10 +331,15 @@ cudaError_t launch_sample_pivot(int storage, const Geom& g, const Bufs& bf, unsi
                                 cudaStream_t s);
 cudaError_t launch_load_rhs(int storage, const float* b, const Geom& g, const Bufs& bf, cudaStream_t s);
 cudaError_t launch_pivot_solve(int storage, const Geom& g, const Bufs& bf, cudaStream_t s);
-cudaError_t launch_update(int storage, const Geom& g, const Bufs& bf, int num_sms, cudaStream_t s);
+cudaError_t launch_update(int storage, const Geom& g, const Bufs& bf, const SketchParams& sp, int num_sms,
+                          cudaStream_t s);
 // split step: t = V_j h, then u = w - t with pivots zeroed and argmax keys
 cudaError_t launch_gemv(int storage, const Geom& g, const Bufs& bf, int num_sms, cudaStream_t s);
 cudaError_t launch_combine(const Geom& g, const Bufs& bf, int num_sms, cudaStream_t s);
+// S v_c for the pending column c (DevState::sk_pending) of a one-RHS float
+// basis with the zeta = 8 sketch table; no-op when nothing is pending
+cudaError_t launch_sketch_col(int storage, const Geom& g, const Bufs& bf, const SketchParams& sp, int num_sms,
+                              cudaStream_t s);
 cudaError_t launch_normalize(int storage, const Geom& g, const Bufs& bf, const SketchParams& sp,
                              bool want_sw, int num_sms, cudaStream_t s);
 // precomputed sketch columns for zeta = 8 with every block <= 128 rows

@@ -166,6 +166,28 @@ __global__ void __launch_bounds__(256) k_pivot_solve(Geom g, Bufs bf) {
 }
 
 // ------------------------------------------------------------------------
+// the zeta = 8 sketch of one element: q (its fixed-point value) added with
+// the element's signs to its 8 rows, decoded from the table entry (byte t =
+// row offset in block t | sign << 7) into the split int32 counters; a
+// counter word that is zero is not added (for BF16 values of magnitude at
+// least 2^(e-10) the low word is zero)
+// ------------------------------------------------------------------------
+__device__ __forceinline__ void scatter8(int* s_hi, int* s_lo, const SketchParams& sp, long long qv, uint2 ent) {
+    const int hp = (int)(qv >> 17), lp = (int)(qv & 0x1FFFFll);
+    const long long qn = -qv;
+    const int hn = (int)(qn >> 17), ln = (int)(qn & 0x1FFFFll);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const unsigned byte = ((q < 4 ? ent.x : ent.y) >> (8 * (q & 3))) & 0xFFu;
+        const int row = sp.lo[q] + (int)(byte & 0x7Fu);
+        const bool ng = (byte & 0x80u) != 0;
+        const int h = ng ? hn : hp, l = ng ? ln : lp;
+        if (h) atomicAdd(&s_hi[row], h);
+        if (l) atomicAdd(&s_lo[row], l);
+    }
+}
+
+// ------------------------------------------------------------------------
 // u -= V_j h ; u(pivots) = 0 ; argmax keys.  Acc = float, B RHS interleaved
 // (compile-time, so element -> (row, RHS) is a shift and a mask).  Each
 // thread owns 16 bytes of every basis column per grid-stride pass and keeps
@@ -173,7 +195,7 @@ __global__ void __launch_bounds__(256) k_pivot_solve(Geom g, Bufs bf) {
 // once, u stays in L2 for the normaliser).
 // ------------------------------------------------------------------------
 template <class T, int B>
-__global__ void __launch_bounds__(256, 4) k_update_f(Geom g, Bufs bf) {
+__global__ void __launch_bounds__(256, 4) k_update_f(Geom g, Bufs bf, SketchParams sp) {
     constexpr int VEC = Vec16<T>::n;
     constexpr int LB = (B == 1) ? 0 : (B == 2) ? 1 : (B == 4) ? 2 : (B == 8) ? 3 : (B == 16) ? 4 : 5;
     constexpr int NK = (B == 1) ? 1 : VEC;           // argmax keys kept per thread
@@ -191,8 +213,19 @@ __global__ void __launch_bounds__(256, 4) k_update_f(Geom g, Bufs bf) {
         s_key[threadIdx.x] = 0ull;
         s_ok[threadIdx.x] = st->status[threadIdx.x] == IPF_OK;
     }
+    // deferred sketch (one RHS): the newest column v_j, left pending by the
+    // previous normalisation, is sketched here from the same loads, into
+    // split counters after the coefficients (at most kFoldEvery elements per
+    // CTA, so no fold is needed before the flush)
+    const int csk = (B == 1 && g.sketch_defer && st->sk_pending == j) ? j : -1;
+    int* s_hi = (int*)(s_coef + ((nc * B + 3) & ~3));
+    int* s_lo = s_hi + sp.m_s;
+    if (csk >= 0)
+        for (int t = threadIdx.x; t < 2 * sp.m_s; t += blockDim.x) s_hi[t] = 0;
     __syncthreads();
     if (B == 1 && !s_ok[0]) return;
+    const int Ssk = csk >= 0 ? kSplitS - bf.colE[csk] : 0;
+    const uint2* tab = (const uint2*)bf.sktab;
 
     const T* V = (const T*)bf.V;
     float* w = (float*)bf.w;
@@ -214,6 +247,22 @@ __global__ void __launch_bounds__(256, 4) k_update_f(Geom g, Bufs bf) {
             }
         }
         const T* vb = V + base;
+        if (csk >= 0) {
+            const uint4 rv = *(const uint4*)(vb + (size_t)csk * ldv);
+            const T* vv = (const T*)&rv;
+#pragma unroll
+            for (int q = 0; q < VEC; q += 2) {
+                const uint4 te = *(const uint4*)(tab + base + q);
+                if (base + q < N) {
+                    const long long qv = fixed_from(to_acc(vv[q]), Ssk);
+                    if (qv) scatter8(s_hi, s_lo, sp, qv, make_uint2(te.x, te.y));
+                }
+                if (base + q + 1 < N) {
+                    const long long qv = fixed_from(to_acc(vv[q + 1]), Ssk);
+                    if (qv) scatter8(s_hi, s_lo, sp, qv, make_uint2(te.z, te.w));
+                }
+            }
+        }
         int c = 0;
         for (; c + 8 <= nc; c += 8) {
             uint4 raw[8];
@@ -268,6 +317,13 @@ __global__ void __launch_bounds__(256, 4) k_update_f(Geom g, Bufs bf) {
     __syncthreads();
     if (threadIdx.x < B && s_key[threadIdx.x])
         atomicMax(&st->key[(j + 1) & 1][threadIdx.x], s_key[threadIdx.x]);
+    if (csk >= 0) {
+        long long* dst = bf.accSV + (size_t)csk * sp.m_s;
+        for (int t = threadIdx.x; t < sp.m_s; t += blockDim.x) {
+            const long long v = ((long long)s_hi[t] << 17) + (long long)s_lo[t];
+            if (v) atomicAdd((unsigned long long*)&dst[t], (unsigned long long)v);
+        }
+    }
 }
 
 // ------------------------------------------------------------------------
@@ -472,6 +528,7 @@ __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams
     __shared__ Acc s_hval[kMaxRhs];
     __shared__ int s_ok[kMaxRhs];
     __shared__ int s_code[kMaxRhs];
+    __shared__ int s_e[kMaxRhs];
     __shared__ bool s_last;
     DevState* st = bf.st;
     const int j = st->j;
@@ -508,10 +565,18 @@ __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams
         } else {
             code = st->status[r];
         }
+        // column exponent: smallest e >= 0 with max |w| <= 2^e |H(j+1,j)|, so
+        // every |v_{j+1}| (also after rounding) is at most 2^e
+        int ex = 0;
+        if (ok && bf.sampled) {
+            const double a = fabs((double)hv), wm = st->wmax[r];
+            while (ex < 60 && wm > ldexp(a, ex)) ++ex;
+        }
         s_prow[threadIdx.x] = row;
         s_hval[threadIdx.x] = hv;
         s_ok[threadIdx.x] = ok;
         s_code[threadIdx.x] = code;
+        s_e[threadIdx.x] = ex;
     }
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
         s_wide[t] = 0;
@@ -526,38 +591,53 @@ __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams
     // sketch table, no second sketch): the same integer sums with the
     // counter words of +q and -q formed once per element instead of once per
     // sketch row, and the table bytes decoded in 32-bit halves
-    const bool fast = !f64 && Bg == 1 && g.B == 1 && (bf.sktab || g.sketch_off) && sp.zeta == 8 && !want_sw;
+    const bool skip_sketch = g.sketch_off || g.sketch_defer;
+    const bool fast = !f64 && Bg == 1 && g.B == 1 && (bf.sktab || skip_sketch) && sp.zeta == 8 && !want_sw &&
+                      (((uintptr_t)bf.w | (uintptr_t)bf.V | (uintptr_t)bf.sktab) & 15u) == 0 && (g.ldv & 7) == 0;
     if (fast && any_ok) {
+        // four consecutive elements per thread: one 16-byte load of w, one
+        // store of the four rounded values, two 16-byte table loads
         T* vout = (T*)bf.V + (size_t)jn * g.ldv;
         const unsigned n = (unsigned)g.n;
+        const unsigned n4 = n >> 2;
         const unsigned stride = gridDim.x * blockDim.x;
         const long long prow = s_prow[0];
         const Acc hval = s_hval[0];
-        int blo[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) blo[q] = sp.lo[q];
+        const int S = kSplitS - s_e[0];
         const uint2* tab = (const uint2*)bf.sktab;
-        const int fold_rounds = kFoldEvery / 256;
+        const bool sk = !skip_sketch;
+        const int fold_rounds = kFoldEvery / (256 * 4);
         int round = 0;
-        for (unsigned t0 = blockIdx.x * blockDim.x; t0 < n; t0 += stride) {
-            const unsigned i = t0 + threadIdx.x;
-            if (i < n) {
-                const Acc v = ((long long)i == prow) ? (Acc)1 : w[i] / hval;
-                const T vs = from_acc<T>(v);
-                vout[i] = vs;
-                const long long qv = g.sketch_off ? 0ll : fixed_from(to_acc(vs), kSplitS);
-                if (qv) {
-                    const int hp = (int)(qv >> 17), lp = (int)(qv & 0x1FFFFll);
-                    const long long qn = -qv;
-                    const int hn = (int)(qn >> 17), ln = (int)(qn & 0x1FFFFll);
-                    const uint2 ent = tab[i];
+        for (unsigned t0 = blockIdx.x * blockDim.x; t0 < n4; t0 += stride) {
+            const unsigned t = t0 + threadIdx.x;
+            if (t < n4) {
+                const unsigned i0 = t << 2;
+                const float4 w4 = *reinterpret_cast<const float4*>(w + i0);
+                const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
+                T vs[4];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const unsigned byte = ((q < 4 ? ent.x : ent.y) >> (8 * (q & 3))) & 0xFFu;
-                        const int row = blo[q] + (int)(byte & 0x7Fu);
-                        const bool ng = (byte & 0x80u) != 0;
-                        atomicAdd(&s_hi[row], ng ? hn : hp);
-                        atomicAdd(&s_lo[row], ng ? ln : lp);
+                for (int e = 0; e < 4; ++e) {
+                    const Acc v = ((long long)(i0 + e) == prow) ? (Acc)1 : wv[e] / hval;
+                    vs[e] = from_acc<T>(v);
+                }
+                if constexpr (sizeof(T) == 2) {
+                    union { uint2 u; T t[4]; } pk;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) pk.t[e] = vs[e];
+                    *reinterpret_cast<uint2*>(vout + i0) = pk.u;
+                } else {
+                    *reinterpret_cast<float4*>(vout + i0) = make_float4(to_acc(vs[0]), to_acc(vs[1]), to_acc(vs[2]),
+                                                                        to_acc(vs[3]));
+                }
+                if (sk) {
+                    const uint4 ta = *reinterpret_cast<const uint4*>(tab + i0);
+                    const uint4 tb = *reinterpret_cast<const uint4*>(tab + i0 + 2);
+                    const uint2 ents[4] = {make_uint2(ta.x, ta.y), make_uint2(ta.z, ta.w), make_uint2(tb.x, tb.y),
+                                           make_uint2(tb.z, tb.w)};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const long long qv = fixed_from(to_acc(vs[e]), S);
+                        if (qv) scatter8(s_hi, s_lo, sp, qv, ents[e]);
                     }
                 }
             }
@@ -566,6 +646,17 @@ __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams
                 split_fold(s_hi, s_lo, s_wide, cnt);
                 __syncthreads();
                 round = 0;
+            }
+        }
+        // the last n mod 4 elements
+        if (blockIdx.x == 0 && threadIdx.x < (n & 3u)) {
+            const unsigned i = (n4 << 2) + threadIdx.x;
+            const Acc v = ((long long)i == prow) ? (Acc)1 : w[i] / hval;
+            const T vsi = from_acc<T>(v);
+            vout[i] = vsi;
+            if (sk) {
+                const long long qv = fixed_from(to_acc(vsi), S);
+                if (qv) scatter8(s_hi, s_lo, sp, qv, tab[i]);
             }
         }
     } else if (any_ok) {
@@ -583,8 +674,8 @@ __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams
                 const Acc v = ((long long)i == s_prow[rl]) ? (Acc)1 : w[e] / s_hval[rl];
                 const T vs = from_acc<T>(v);
                 vout[e] = vs;
-                const long long fv = g.sketch_off ? 0ll : fixed_from(to_acc(vs), F);
-                const long long fw = (want_sw && !g.sketch_off) ? fixed_from(v, F) : 0;
+                const long long fv = skip_sketch ? 0ll : fixed_from(to_acc(vs), F - s_e[rl]);
+                const long long fw = (want_sw && !skip_sketch) ? fixed_from(v, F - s_e[rl]) : 0;
                 if (fv || fw) {
                     int rows[16];
                     unsigned neg;
@@ -660,6 +751,7 @@ __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams
         if (s_ok[rl]) {
             const long long row = s_prow[rl];
             bf.piv[(size_t)r * K1 + jn] = (int)row;
+            bf.colE[(size_t)r * K1 + jn] = s_e[rl];
             if (jn == 0) st->beta[r] = (double)s_hval[rl];
             else bf.H[(size_t)r * K1 * g.k_max + (size_t)K1 * j + jn] = (double)s_hval[rl];
             const long long e = row * B + r;
@@ -676,6 +768,7 @@ __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams
         }
         st->key[kb ^ 1][r] = 0ull;
         if (f64 && rl == 0) { st->maxbits[kb ^ 1] = 0ull; st->minidx[kb ^ 1] = ~0ull; }
+        if (g.sketch_defer && rl == 0) st->sk_pending = s_ok[0] ? jn : -1;   // one RHS
     }
     // last CTA advances the step counter
     __syncthreads();
@@ -688,6 +781,89 @@ __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams
     if (s_last && threadIdx.x == 0) {
         st->j = jn;
         st->ctr = 0u;
+        __threadfence();
+    }
+}
+
+// ------------------------------------------------------------------------
+// deferred sketch: S v_c for the pending column c, the same exact integer
+// sums as the normaliser's (so the result is bit-identical to sketching in
+// the normaliser), read back from the stored column.  Every CTA reads the
+// pending index first; the last CTA clears it, so a second launch before
+// the next normalisation does nothing.
+// ------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(256) k_sketch_col(Geom g, Bufs bf, SketchParams sp) {
+    extern __shared__ unsigned char smem_raw[];
+    const int cnt = sp.m_s;
+    long long* s_wide = (long long*)smem_raw;
+    int* s_hi = (int*)(s_wide + cnt);
+    int* s_lo = s_hi + cnt;
+    __shared__ bool s_last;
+    DevState* st = bf.st;
+    const int c = st->sk_pending;
+    if (c >= 0 && c <= g.k_max) {
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) { s_wide[t] = 0; s_hi[t] = 0; s_lo[t] = 0; }
+        __syncthreads();
+        const T* col = (const T*)bf.V + (size_t)c * g.ldv;
+        const int S = kSplitS - bf.colE[c];
+        const uint2* tab = (const uint2*)bf.sktab;
+        const unsigned n = (unsigned)g.n, n4 = n >> 2;
+        const unsigned stride = gridDim.x * blockDim.x;
+        const int fold_rounds = kFoldEvery / (256 * 4);
+        int round = 0;
+        for (unsigned t0 = blockIdx.x * blockDim.x; t0 < n4; t0 += stride) {
+            const unsigned t = t0 + threadIdx.x;
+            if (t < n4) {
+                const unsigned i0 = t << 2;
+                T vs[4];
+                if constexpr (sizeof(T) == 2) {
+                    union { uint2 u; T t[4]; } pk;
+                    pk.u = *reinterpret_cast<const uint2*>(col + i0);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) vs[e] = pk.t[e];
+                } else {
+                    const float4 f = *reinterpret_cast<const float4*>(col + i0);
+                    vs[0] = f.x; vs[1] = f.y; vs[2] = f.z; vs[3] = f.w;
+                }
+                const uint4 ta = *reinterpret_cast<const uint4*>(tab + i0);
+                const uint4 tb = *reinterpret_cast<const uint4*>(tab + i0 + 2);
+                const uint2 ents[4] = {make_uint2(ta.x, ta.y), make_uint2(ta.z, ta.w), make_uint2(tb.x, tb.y),
+                                       make_uint2(tb.z, tb.w)};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const long long qv = fixed_from(to_acc(vs[e]), S);
+                    if (qv) scatter8(s_hi, s_lo, sp, qv, ents[e]);
+                }
+            }
+            if (++round == fold_rounds) {
+                __syncthreads();
+                split_fold(s_hi, s_lo, s_wide, cnt);
+                __syncthreads();
+                round = 0;
+            }
+        }
+        if (blockIdx.x == 0 && threadIdx.x < (n & 3u)) {
+            const unsigned i = (n4 << 2) + threadIdx.x;
+            const long long qv = fixed_from(to_acc(col[i]), S);
+            if (qv) scatter8(s_hi, s_lo, sp, qv, tab[i]);
+        }
+        __syncthreads();
+        split_fold(s_hi, s_lo, s_wide, cnt);
+        __syncthreads();
+        long long* dst = bf.accSV + (size_t)c * sp.m_s;            // one RHS: [k_max+1][m_s]
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x)
+            if (s_wide[t]) atomicAdd((unsigned long long*)&dst[t], (unsigned long long)s_wide[t]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&st->sk_ctr, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        st->sk_pending = -1;
+        st->sk_ctr = 0u;
         __threadfence();
     }
 }
@@ -714,6 +890,10 @@ __global__ void k_sample_pivot(Geom g, Bufs bf, unsigned long long seed, int siz
     if (jn > g.k_max) return;
     const long long n = g.n;
     const int B = g.B;
+    // the full max |w| (left by the update) bounds |v_{j+1}| = |w| / |w(p)|
+    if (lane == 0)
+        st->wmax[r] = sizeof(Acc) == 4 ? (double)key_absval(st->key[jn & 1][r])
+                                       : __longlong_as_double((long long)st->maxbits[jn & 1]);
     if (n - jn <= size) return;                       // every candidate: the full max stands
     if (lane == 0) s_cnt = 0;
     __syncwarp();
@@ -860,6 +1040,8 @@ __global__ void k_reset_state(DevState* st) {
     if (t == 0) {
         st->j = -1;
         st->ctr = 0u;
+        st->sk_pending = -1;
+        st->sk_ctr = 0u;
         st->maxbits[0] = st->maxbits[1] = 0ull;
         st->minidx[0] = st->minidx[1] = ~0ull;
     }
@@ -920,20 +1102,29 @@ cudaError_t launch_pivot_solve(int storage, const Geom& g, const Bufs& bf, cudaS
 }
 
 template <class T>
-static cudaError_t update_B(const Geom& g, const Bufs& bf, int blocks, size_t smem, cudaStream_t s) {
+static cudaError_t update_B(const Geom& g, const Bufs& bf, const SketchParams& sp, int blocks, size_t smem,
+                           cudaStream_t s) {
+    auto go = [&](auto fn) -> cudaError_t {
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        fn<<<blocks, 256, smem, s>>>(g, bf, sp);
+        return cudaGetLastError();
+    };
     switch (g.B) {
-        case 1: k_update_f<T, 1><<<blocks, 256, smem, s>>>(g, bf); break;
-        case 2: k_update_f<T, 2><<<blocks, 256, smem, s>>>(g, bf); break;
-        case 4: k_update_f<T, 4><<<blocks, 256, smem, s>>>(g, bf); break;
-        case 8: k_update_f<T, 8><<<blocks, 256, smem, s>>>(g, bf); break;
-        case 16: k_update_f<T, 16><<<blocks, 256, smem, s>>>(g, bf); break;
-        case 32: k_update_f<T, 32><<<blocks, 256, smem, s>>>(g, bf); break;
+        case 1: return go(k_update_f<T, 1>);
+        case 2: return go(k_update_f<T, 2>);
+        case 4: return go(k_update_f<T, 4>);
+        case 8: return go(k_update_f<T, 8>);
+        case 16: return go(k_update_f<T, 16>);
+        case 32: return go(k_update_f<T, 32>);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
-cudaError_t launch_update(int storage, const Geom& g, const Bufs& bf, int num_sms, cudaStream_t s) {
+cudaError_t launch_update(int storage, const Geom& g, const Bufs& bf, const SketchParams& sp, int num_sms,
+                          cudaStream_t s) {
     const int K1 = g.k_max + 1;
     int per_thread = 0;
     IPF_DISPATCH_STORAGE(storage, { per_thread = 16 / (int)sizeof(T); });
@@ -950,11 +1141,18 @@ cudaError_t launch_update(int storage, const Geom& g, const Bufs& bf, int num_sm
         k_argmin_d<<<(int)b2, 256, 0, s>>>(g, bf);
         return cudaGetLastError();
     }
-    const size_t smem = (size_t)K1 * g.B * sizeof(float);
+    size_t smem = (size_t)K1 * g.B * sizeof(float);
+    if (g.sketch_defer) {
+        // split counters after the coefficients; enough CTAs that none takes
+        // more than kFoldEvery elements (one counter add per element)
+        smem = (size_t)((K1 * g.B + 3) & ~3) * sizeof(float) + (size_t)2 * sp.m_s * sizeof(int);
+        const long long need = (g.N + kFoldEvery - 1) / kFoldEvery;
+        if (blocks < need) blocks = need;
+    }
     switch (storage) {
-        case IPF_STORE_F32: return update_B<float>(g, bf, (int)blocks, smem, s);
-        case IPF_STORE_BF16: return update_B<__nv_bfloat16>(g, bf, (int)blocks, smem, s);
-        case IPF_STORE_F16: return update_B<__half>(g, bf, (int)blocks, smem, s);
+        case IPF_STORE_F32: return update_B<float>(g, bf, sp, (int)blocks, smem, s);
+        case IPF_STORE_BF16: return update_B<__nv_bfloat16>(g, bf, sp, (int)blocks, smem, s);
+        case IPF_STORE_F16: return update_B<__half>(g, bf, sp, (int)blocks, smem, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1033,6 +1231,38 @@ cudaError_t launch_normalize(int storage, const Geom& g, const Bufs& bf, const S
         if (e != cudaSuccess) return e;
         fn<<<grid, 256, smem, s>>>(g, bf, sp, want_sw ? 1 : 0, Bg, lbg, lb);
     });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sketch_col(int storage, const Geom& g, const Bufs& bf, const SketchParams& sp, int num_sms,
+                              cudaStream_t s) {
+    if (g.B != 1 || sp.zeta != 8 || !bf.sktab) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)sp.m_s * 16;
+    long long blocks = (g.N / 4 + 255) / 256;
+    if (blocks > (long long)num_sms * 4) blocks = (long long)num_sms * 4;
+    if (blocks < 1) blocks = 1;
+    switch (storage) {
+        case IPF_STORE_F32: {
+            cudaError_t e = cudaFuncSetAttribute(k_sketch_col<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            k_sketch_col<float><<<(int)blocks, 256, smem, s>>>(g, bf, sp);
+            break;
+        }
+        case IPF_STORE_BF16: {
+            cudaError_t e = cudaFuncSetAttribute(k_sketch_col<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)smem);
+            if (e != cudaSuccess) return e;
+            k_sketch_col<__nv_bfloat16><<<(int)blocks, 256, smem, s>>>(g, bf, sp);
+            break;
+        }
+        case IPF_STORE_F16: {
+            cudaError_t e = cudaFuncSetAttribute(k_sketch_col<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            k_sketch_col<__half><<<(int)blocks, 256, smem, s>>>(g, bf, sp);
+            break;
+        }
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -49,6 +49,9 @@ __device__ __forceinline__ int kuse_of(const DevState* st, int r, int k) {
     return kd < k ? kd : k;
 }
 
+// the scale of a fixed-point sketch column with exponent e (see Bufs::colE)
+__device__ __forceinline__ double col_scale(double scale, int e) { return e ? ldexp(scale, e) : scale; }
+
 // M[r][col], T[r][col] (column-major, ld = m).  Column col < kb of M is
 // z_col = S A v_col = (S V_{col+1}) h_col + H(col+1, col) (S w)_{col+1}, with
 // (S w) the sketch of the unrounded normalised vector when the storage
@@ -70,6 +73,8 @@ __global__ void k_form(Geom g, Bufs bf, int k, int zeta, int use_sw, int need_T,
     // the penalty basis: S V itself, or S_1 L of the generalized process
     const long long* pv = bf.penSV ? bf.penSV + (size_t)r * K1 * m : sv;
     const double pscale = bf.penSV ? ldexp(1.0, -bf.penF) / sqrt((double)zeta) : scale;
+    const int* ce = bf.colE + (size_t)r * K1;
+    const int* pe = bf.penE ? bf.penE + (size_t)r * K1 : ce;
     const double* H = bf.H + (size_t)r * K1 * g.k_max;
     double* M = Mw + (size_t)r * m * (k + 1);
     double* T = Tw ? Tw + (size_t)r * m * k : nullptr;
@@ -100,12 +105,12 @@ __global__ void k_form(Geom g, Bufs bf, int k, int zeta, int use_sw, int need_T,
         } else if (col < kb) {
             double s = 0.0;
             const double* Hc = H + (size_t)K1 * col;
-            for (int i = 0; i <= col; ++i) s = fma((double)sv[(size_t)i * m + row] * scale, Hc[i], s);
+            for (int i = 0; i <= col; ++i) s = fma((double)sv[(size_t)i * m + row] * col_scale(scale, ce[i]), Hc[i], s);
             const long long* last = use_sw ? sw : sv;
-            val = fma((double)last[(size_t)(col + 1) * m + row] * scale, Hc[col + 1], s);
-            if (need_T) T[(size_t)col * m + row] = (double)pv[(size_t)col * m + row] * pscale;
+            val = fma((double)last[(size_t)(col + 1) * m + row] * col_scale(scale, ce[col + 1]), Hc[col + 1], s);
+            if (need_T) T[(size_t)col * m + row] = (double)pv[(size_t)col * m + row] * col_scale(pscale, pe[col]);
         } else {
-            val = beta * (double)sw[row] * scale;
+            val = beta * (double)sw[row] * col_scale(scale, ce[0]);
         }
         M[(size_t)col * m + row] = val;
     }

@@ -44,3 +44,39 @@ def test_sampled_pivoting_scmrh(storage, sample):
     ks = [k for k in (1, 2, 5, 10, 20, 30, 50) if k < j]
     compare_solution(ctx, st, storage, ks, p.lambdas)
     ctx.close()
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
+def test_sampled_pivot_growth_keeps_sketch_exact(storage):
+    """Basis growth under sampled pivoting: a right-hand side with one entry
+    1e4 and the rest in [1e-3, 1e-2], with one-entry samples, gives pivots far
+    below the largest entry and |v_j| of about 1e6 (full pivoting keeps
+    |v| <= 1).  The sketch sums must stay exact for such columns: S v_j from
+    the library equals S applied to the stored v_j up to the fixed-point
+    quantum, n * 2^-34 relative to max |v_j| (overflowing integer counters
+    would be off by about max |v_j|); the pivots are the oracle's and, in
+    FP64, so are the sketches and the iterates."""
+    p = P.make("deblur64")
+    rng = np.random.default_rng(8)
+    b = rng.uniform(1e-3, 1e-2, p.n).astype(np.float32)
+    b[1234] = 1e4
+    k = 5
+    A = ops.make_apply(p)
+    S = sk.SparseSignSketch(p.sketch_seed, p.n, p.m_s, p.zeta)
+    st = scmrh.run(A, b.astype(np.float64), S, k, pivot_sample=1, pivot_seed=p.sketch_seed ^ PIVOT_SEED_XOR)
+    assert np.abs(st.V).max() > 1e5
+    ctx = gpu_context(p, storage, k=k, b=b.reshape(1, -1), pivot_sample=1)
+    ctx.step(k)
+    status, kd = ctx.sync()
+    assert kd == [k]
+    ex = ctx.export(0)
+    assert [int(v) for v in ex["piv"][:k + 1]] == list(st.piv)
+    Sd = S.matrix()
+    for j in range(k + 1):
+        vj = st.V[:, j] if storage == "f64" else ctx.basis(j).astype(np.float64)
+        ref = Sd @ vj
+        tol = p.n * 2.0 ** -34 * np.abs(vj).max()
+        assert np.abs(ex["SV"][:, j] - ref).max() <= tol, (j, np.abs(vj).max())
+    if storage == "f64":
+        compare_solution(ctx, st, storage, [1, 2, 3, 4, 5], [0.0])
+    ctx.close()
