@@ -489,7 +489,7 @@ cudaError_t one_step(ipf_ctx* c, int j) {
         if ((e = timed(c, 1, 0.0, [&] { return launch_pivot_solve(c->storage, c->g, c->bf, c->s); })) != cudaSuccess)
             return e;
         if ((e = cudaStreamWaitEvent(c->s, c->ev_join, 0)) != cudaSuccess) return e;
-        if ((e = timed(c, 2, (double)(j + 1) * N * sv + 2.0 * N * ab + N / 8.0,
+        if ((e = timed(c, 2, (double)(j + 1) * N * sv + 2.0 * N * ab + N / 8.0 + (c->defer_sketch ? 8.0 * N : 0.0),
                        [&] { return launch_update(c->storage, c->g, c->bf, c->sp, c->num_sms, c->s); })) != cudaSuccess)
             return e;
         if ((e = sample_pivot(c, c->g, c->bf)) != cudaSuccess) return e;
@@ -503,7 +503,7 @@ cudaError_t one_step(ipf_ctx* c, int j) {
         return e;
     if ((e = timed(c, 1, 0.0, [&] { return launch_pivot_solve(c->storage, c->g, c->bf, c->s); })) != cudaSuccess)
         return e;
-    if ((e = timed(c, 2, (double)(j + 1) * N * sv + 2.0 * N * ab + N / 8.0,
+    if ((e = timed(c, 2, (double)(j + 1) * N * sv + 2.0 * N * ab + N / 8.0 + (c->defer_sketch ? 8.0 * N : 0.0),
                    [&] { return launch_update(c->storage, c->g, c->bf, c->sp, c->num_sms, c->s); })) != cudaSuccess)
         return e;
     if ((e = sample_pivot(c, c->g, c->bf)) != cudaSuccess) return e;

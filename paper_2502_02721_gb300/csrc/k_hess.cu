@@ -125,42 +125,54 @@ __global__ void __launch_bounds__(256) k_pivot_solve(Geom g, Bufs bf) {
         if (threadIdx.x == 0) st->status[r] = IPF_ERR_TIMEOUT;
         return;
     }
-    if (threadIdx.x >= 32) return;
-    const int lane = threadIdx.x;
+    // four warps (one per SM partition, so four FP64 pipes): warp w holds the
+    // row groups w and w + 4 (rows 32q + lane) in registers.  Column c's
+    // value x_c is final in the warp holding its row group once columns < c
+    // are applied; that warp publishes it through shared memory, a 128-thread
+    // named barrier orders it, and every warp applies column c to its rows.
+    // Each row still takes its updates in column order.
+    if (threadIdx.x >= 128) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int qmax = j >> 5;                               // last row group holding a row <= j
-    double x[8];
-    int off[8];
+    double* s_x = s_g + ((j + 2) & ~1);                    // x_c per column, after g
+    double x[2];
+    int off[2];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int i = q * 32 + lane;
-        x[q] = (i <= j) ? s_g[i] : 0.0;
-        off[q] = i * (i - 1) / 2;
+    for (int h = 0; h < 2; ++h) {
+        const int i = (warp + 4 * h) * 32 + lane;
+        x[h] = (i <= j) ? s_g[i] : 0.0;
+        off[h] = i * (i - 1) / 2;
     }
-#pragma unroll
-    for (int cb = 0; cb < 8; ++cb) {
-        if (cb > qmax) break;
-#pragma unroll
-        for (int cc = 0; cc < 32; ++cc) {
+    for (int cb = 0; cb <= qmax; ++cb) {
+        const int cend = j - cb * 32 < 32 ? j - cb * 32 : 32;     // columns c = cb*32 + cc < j
+        const bool owner = warp == (cb & 3);
+        const int oh = cb >> 2;
+#pragma unroll 1
+        for (int cc = 0; cc < cend; ++cc) {
             const int c = cb * 32 + cc;
-            if (c >= j) break;
-            const double xc = __shfl_sync(0xffffffffu, x[cb], cc);
-            // rows i > c with i <= j only: s_L holds rows 1..j and nothing beyond
-            if (lane > cc && cb * 32 + lane <= j) x[cb] = fma(-s_L[off[cb] + c], xc, x[cb]);
+            if (owner) {
+                const double xc = __shfl_sync(0xffffffffu, oh ? x[1] : x[0], cc);
+                if (lane == 0) s_x[c] = xc;
+            }
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            const double xc = s_x[c];
 #pragma unroll
-            for (int q = cb + 1; q < 8; ++q) {
-                if (q > qmax) break;
-                if (q * 32 + lane <= j) x[q] = fma(-s_L[off[q] + c], xc, x[q]);
+            for (int h = 0; h < 2; ++h) {
+                const int q = warp + 4 * h;
+                // rows i > c with i <= j only: s_L holds rows 1..j and nothing beyond
+                if (q >= cb && q <= qmax && (q > cb || lane > cc) && q * 32 + lane <= j)
+                    x[h] = fma(-s_L[off[h] + c], xc, x[h]);
             }
         }
     }
     double* Hc = bf.H + (size_t)r * K1 * g.k_max + (size_t)K1 * j;
     Acc* coef = (Acc*)bf.coef;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int i = q * 32 + lane;
+    for (int h = 0; h < 2; ++h) {
+        const int i = (warp + 4 * h) * 32 + lane;
         if (i <= j) {
-            Hc[i] = x[q];
-            coef[(size_t)i * B + r] = (Acc)x[q];
+            Hc[i] = x[h];
+            coef[(size_t)i * B + r] = (Acc)x[h];
         }
     }
 }
@@ -1092,7 +1104,8 @@ cudaError_t launch_pivot_solve(int storage, const Geom& g, const Bufs& bf, cudaS
     const int K1 = g.k_max + 1;
     IPF_DISPATCH_STORAGE(storage, {
         using Acc = typename AccOf<T>::type;
-        const size_t smem = lp_stride(g.k_max) * sizeof(double) + (size_t)((K1 + 1) & ~1) * sizeof(double);
+        // packed L_p, then g (K1, rounded to even) and the column values x_c (K1)
+        const size_t smem = lp_stride(g.k_max) * sizeof(double) + (size_t)(((K1 + 1) & ~1) + K1 + 1) * sizeof(double);
         auto fn = k_pivot_solve<T, Acc>;
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
