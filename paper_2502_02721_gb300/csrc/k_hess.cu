@@ -550,6 +550,7 @@ __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams
     const int B = g.B;
     const int r0 = blockIdx.y * Bg;
     const Acc* w = (const Acc*)bf.w;
+    const bool skip_sketch = g.sketch_off || g.sketch_defer;   // no counters at all then
 
     if (threadIdx.x < Bg) {
         const int r = r0 + threadIdx.x;
@@ -590,10 +591,11 @@ __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams
         s_code[threadIdx.x] = code;
         s_e[threadIdx.x] = ex;
     }
-    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-        s_wide[t] = 0;
-        if (!f64) { s_hi[t] = 0; s_lo[t] = 0; }
-    }
+    if (!skip_sketch)
+        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+            s_wide[t] = 0;
+            if (!f64) { s_hi[t] = 0; s_lo[t] = 0; }
+        }
     __syncthreads();
 
     bool any_ok = false;
@@ -603,7 +605,6 @@ __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams
     // sketch table, no second sketch): the same integer sums with the
     // counter words of +q and -q formed once per element instead of once per
     // sketch row, and the table bytes decoded in 32-bit halves
-    const bool skip_sketch = g.sketch_off || g.sketch_defer;
     const bool fast = !f64 && Bg == 1 && g.B == 1 && (bf.sktab || skip_sketch) && sp.zeta == 8 && !want_sw &&
                       (((uintptr_t)bf.w | (uintptr_t)bf.V | (uintptr_t)bf.sktab) & 15u) == 0 && (g.ldv & 7) == 0;
     if (fast && any_ok) {
@@ -653,7 +654,7 @@ __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams
                     }
                 }
             }
-            if (++round == fold_rounds) {
+            if (sk && ++round == fold_rounds) {
                 __syncthreads();
                 split_fold(s_hi, s_lo, s_wide, cnt);
                 __syncthreads();
@@ -735,7 +736,7 @@ __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams
                     }
                 }
             }
-            if (!f64 && ++round == fold_rounds) {
+            if (!f64 && !skip_sketch && ++round == fold_rounds) {
                 __syncthreads();
                 split_fold(s_hi, s_lo, s_wide, cnt);
                 __syncthreads();
@@ -744,12 +745,12 @@ __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams
         }
     }
     __syncthreads();
-    if (!f64) {
+    if (!f64 && !skip_sketch) {
         split_fold(s_hi, s_lo, s_wide, cnt);
         __syncthreads();
     }
     const int K1 = g.k_max + 1;
-    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+    for (int t = threadIdx.x; t < (skip_sketch ? 0 : cnt); t += blockDim.x) {
         const int a = t / (Bg * sp.m_s);
         const int rem = t - a * Bg * sp.m_s;
         const int rl = rem / sp.m_s, row = rem - rl * sp.m_s;

@@ -5,8 +5,8 @@
 //   k_form          M = [Z | c] with Z = S A V_k (m_s x k) and c = S b;
 //                   T = S V_k when a sketched-x penalty is asked for
 //   k_householder   Householder QR of every M (and T), R only; a
-//                   cooperative launch, a group of CTAs per matrix, one
-//                   column reflector per step, columns owned round-robin
+//                   cooperative launch, a group of CTAs per matrix, columns
+//                   owned round-robin, reflectors passed on by column flags
 //   k_small_solve   per (RHS, lambda): lambda = 0 back substitution on R_M;
 //                   lambda > 0 QR of [R_M(:, 1:k); lambda R_T] (two stacked
 //                   upper triangles, structure kept) then back substitution
@@ -32,7 +32,7 @@ SolveLayout layout_for(const Geom& g, int nl_max) {
     const size_t k = (size_t)g.k_max;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
-    L.bar_off = take(sizeof(unsigned) * (size_t)g.B * 2);
+    L.bar_off = take(sizeof(unsigned) * (size_t)g.B * 2 * (g.k_max + 2));   // QR column flags per job
     L.err_off = take(sizeof(int) * 4);
     L.M_off = take(sizeof(double) * (size_t)g.B * g.m_s * (k + 1));
     L.T_off = take(sizeof(double) * (size_t)g.B * g.m_s * k);
@@ -133,20 +133,17 @@ __device__ __forceinline__ double block_sum(double v, double* s_red) {
     return t;
 }
 
-__device__ bool job_barrier(unsigned* bar, unsigned target, int* err) {
-    __syncthreads();
+// bounded wait by thread 0 for a column flag set by another CTA of the job;
+// every thread returns the same verdict (false: gave up or another CTA failed)
+__device__ __forceinline__ bool wait_flag(const unsigned* flag, int* err) {
     __shared__ int s_fail;
     if (threadIdx.x == 0) {
         s_fail = 0;
-        __threadfence();
-        atomicAdd(bar, 1u);
         long long spins = 0;
-        while (true) {
-            const unsigned seen = *(volatile unsigned*)bar;
-            if (seen >= target) break;
+        while (*(volatile const unsigned*)flag == 0u) {
             if (*(volatile int*)err) { s_fail = 1; break; }
             if (++spins > (1ll << 22)) { atomicExch(err, 1); s_fail = 1; break; }
-            __nanosleep(64);
+            __nanosleep(32);
         }
         __threadfence();
     }
@@ -154,38 +151,23 @@ __device__ bool job_barrier(unsigned* bar, unsigned target, int* err) {
     return s_fail == 0;
 }
 
-__global__ void __launch_bounds__(256) k_householder(Geom g, const DevState* st, int k, int need_T, int cpj,
-                                                      double* Mw, double* Tw, double* dM, double* dT,
-                                                      unsigned* bars, int* err) {
-    extern __shared__ unsigned char smem_raw[];
-    double* s_v = (double*)smem_raw;          // m doubles
-    __shared__ double s_red[32];
-    const int jobs_per_rhs = need_T ? 2 : 1;
-    const int job = blockIdx.x / cpj;
-    const int q = blockIdx.x - job * cpj;
-    const int njobs = g.B * jobs_per_rhs;
-    if (job >= njobs) return;
-    const int r = job / jobs_per_rhs, which = job - r * jobs_per_rhs;
-    const int kb = kuse_of(st, r, k);
-    const int m = g.m_s;
-    double* A;
-    double* diag;
-    int ncols;
-    if (which == 0) { A = Mw + (size_t)r * m * (k + 1); diag = dM + (size_t)r * (k + 1); ncols = kb + 1; }
-    else { A = Tw + (size_t)r * m * k; diag = dT + (size_t)r * (k + 1); ncols = kb; }
-    unsigned* bar = bars + job;
-    const int nsteps = ncols < m ? ncols : m;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int i = 0; i < nsteps; ++i) {
-        const double* ci = A + (size_t)i * m;
-        double part = 0.0;
-        for (int row = i + threadIdx.x; row < m; row += blockDim.x) {
-            const double x = ci[row];
-            s_v[row] = x;
-            if (row > i) part = fma(x, x, part);
-        }
-        const double sigma = block_sum(part, s_red);
-        const double alpha = s_v[i];
+// Reflector for column i (rows i..m-1 of col, every earlier reflector
+// already applied): v = (col(i+1..) / (alpha - beta)) with v(i) = 1,
+// tau = (beta - alpha) / beta, R(i,i) = beta.  v goes to buf (rows i..m-1)
+// and back into the column below the diagonal, tau into the column's
+// diagonal slot (R(i,i) lives in diag), then the column's flag is raised.
+__device__ __forceinline__ void make_reflector(double* col, int i, int m, double* buf, double* diag, unsigned* flag, double* s_red,
+                               double* s_tau) {
+    __shared__ double s_inv;
+    double part = 0.0;
+    for (int row = i + threadIdx.x; row < m; row += blockDim.x) {
+        const double x = col[row];
+        buf[row] = x;
+        if (row > i) part = fma(x, x, part);
+    }
+    const double sigma = block_sum(part, s_red);
+    if (threadIdx.x == 0) {
+        const double alpha = buf[i];
         double beta, tau, inv;
         if (sigma == 0.0) { beta = alpha; tau = 0.0; inv = 0.0; }
         else {
@@ -194,28 +176,110 @@ __global__ void __launch_bounds__(256) k_householder(Geom g, const DevState* st,
             tau = (beta - alpha) / beta;
             inv = 1.0 / (alpha - beta);
         }
-        __syncthreads();
-        for (int row = i + 1 + threadIdx.x; row < m; row += blockDim.x) s_v[row] *= inv;
-        if (threadIdx.x == 0) s_v[i] = 1.0;
-        __syncthreads();
-        if ((i % cpj) == q && threadIdx.x == 0) diag[i] = beta;
+        *diag = beta;
+        *s_tau = tau;
+        s_inv = inv;
+        buf[i] = 1.0;
+        col[i] = tau;
+    }
+    __syncthreads();
+    const double inv = s_inv;
+    for (int row = i + 1 + threadIdx.x; row < m; row += blockDim.x) {
+        const double v = buf[row] * inv;
+        buf[row] = v;
+        col[row] = v;
+    }
+    __threadfence();                          // every writer orders its stores before the flag
+    __syncthreads();
+    if (threadIdx.x == 0) atomicExch(flag, 1u);
+}
+
+// col -= tau v (v^T col) over rows i..m-1, the whole CTA (latency path)
+__device__ __forceinline__ void apply_block(const double* v, double tau, double* col, int i, int m, double* s_red) {
+    double d = 0.0;
+    for (int row = i + threadIdx.x; row < m; row += blockDim.x) d = fma(v[row], col[row], d);
+    const double f = tau * block_sum(d, s_red);
+    for (int row = i + threadIdx.x; row < m; row += blockDim.x) col[row] = fma(-f, v[row], col[row]);
+    __syncthreads();
+}
+
+// Householder QR (R only), pipelined by columns instead of a grid barrier
+// per column.  Column j belongs to CTA j mod cpj of its job.  Reflector i is
+// published by its owner (vector in the column below the diagonal, tau in
+// the diagonal slot, then a flag); a CTA waits only for the flag of the
+// reflector it applies next, and applies reflectors in order.  The owner of
+// column i+1 applies reflector i to that column first and publishes
+// reflector i+1 at once (lookahead), before its other columns; two shared
+// buffers hold v_i and v_{i+1}.  Cooperative launch: all CTAs co-resident.
+__global__ void __launch_bounds__(256) k_householder(Geom g, const DevState* st, int k, int need_T, int cpj,
+                                                      double* Mw, double* Tw, double* dM, double* dT,
+                                                      unsigned* flags, int* err) {
+    extern __shared__ unsigned char smem_raw[];
+    const int m = g.m_s;
+    double* s_buf = (double*)smem_raw;        // 2 x m doubles
+    __shared__ double s_red[32];
+    __shared__ double s_tau[2];
+    const int jobs_per_rhs = need_T ? 2 : 1;
+    const int job = blockIdx.x / cpj;
+    const int q = blockIdx.x - job * cpj;
+    const int njobs = g.B * jobs_per_rhs;
+    if (job >= njobs) return;
+    const int r = job / jobs_per_rhs, which = job - r * jobs_per_rhs;
+    const int kb = kuse_of(st, r, k);
+    double* A;
+    double* diag;
+    int ncols;
+    if (which == 0) { A = Mw + (size_t)r * m * (k + 1); diag = dM + (size_t)r * (k + 1); ncols = kb + 1; }
+    else { A = Tw + (size_t)r * m * k; diag = dT + (size_t)r * (k + 1); ncols = kb; }
+    unsigned* flag = flags + (size_t)job * (g.k_max + 2);
+    const int nsteps = ncols < m ? ncols : m;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    int have = -1;                            // reflector already made here by lookahead
+    for (int i = 0; i < nsteps; ++i) {
+        double* v = s_buf + (size_t)(i & 1) * m;
+        double* ci = A + (size_t)i * m;
+        double tau;
+        if (i % cpj == q) {
+            if (have != i) make_reflector(ci, i, m, v, diag + i, flag + i, s_red, &s_tau[i & 1]);
+            tau = s_tau[i & 1];
+        } else {
+            if (!wait_flag(flag + i, err)) return;
+            // written by another CTA: read through L2
+            for (int row = i + 1 + threadIdx.x; row < m; row += blockDim.x) v[row] = __ldcg(ci + row);
+            if (threadIdx.x == 0) { v[i] = 1.0; s_tau[i & 1] = __ldcg(ci + i); }
+            __syncthreads();
+            tau = s_tau[i & 1];
+        }
+        // owned columns j > i: j = q, q + cpj, ...
+        int j0 = q;
+        if (j0 <= i) j0 += ((i - q) / cpj + 1) * cpj;
+        if (j0 >= ncols) break;                // no column (and no reflector) left here
+        int jrest = j0;
+        if (j0 == i + 1) {
+            // lookahead: the next reflector's column first, then that reflector
+            if (tau != 0.0) apply_block(v, tau, A + (size_t)j0 * m, i, m, s_red);
+            if (i + 1 < nsteps) {
+                double* vn = s_buf + (size_t)((i + 1) & 1) * m;
+                make_reflector(A + (size_t)j0 * m, i + 1, m, vn, diag + i + 1, flag + i + 1, s_red,
+                               &s_tau[(i + 1) & 1]);
+                have = i + 1;
+            }
+            jrest = j0 + cpj;
+        }
         if (tau != 0.0) {
-            // owned columns j > i: j = q, q + cpj, ...
-            int j0 = q;
-            if (j0 <= i) j0 += ((i - q) / cpj + 1) * cpj;
             int idx = 0;
-            for (int jc = j0; jc < ncols; jc += cpj, ++idx) {
+            for (int jc = jrest; jc < ncols; jc += cpj, ++idx) {
                 if ((idx % nw) != warp) continue;
                 double* cj = A + (size_t)jc * m;
                 double d = 0.0;
-                for (int row = i + lane; row < m; row += 32) d = fma(s_v[row], cj[row], d);
+                for (int row = i + lane; row < m; row += 32) d = fma(v[row], cj[row], d);
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) d += __shfl_xor_sync(0xffffffffu, d, off);
                 const double f = tau * d;
-                for (int row = i + lane; row < m; row += 32) cj[row] = fma(-f, s_v[row], cj[row]);
+                for (int row = i + lane; row < m; row += 32) cj[row] = fma(-f, v[row], cj[row]);
             }
         }
-        if (!job_barrier(bar, (unsigned)(i + 1) * cpj, err)) return;
+        __syncthreads();
     }
     // columns beyond m (never for m_s >= k+1) have no diagonal
 }
@@ -292,14 +356,24 @@ __global__ void __launch_bounds__(256) k_small_solve(Geom g, const DevState* st,
             __syncthreads();
         }
     }
-    // back substitution: top(0:kb, 0:kb) y = top(0:kb, kb)
-    if (threadIdx.x == 0) {
-        for (int i = kb - 1; i >= 0; --i) {
-            double s = S[(size_t)kb * ld + i];
-            for (int c = i + 1; c < kb; ++c) s = fma(-S[(size_t)c * ld + i], y[c], s);
+    // back substitution top(0:kb, 0:kb) y = top(0:kb, kb) by columns: y_i
+    // from the right-hand side column (which already has columns > i
+    // applied), then column i applied to rows < i by all threads
+    // (one thread divides: FP64 division is scarce on this GPU)
+    __shared__ double s_yi;
+    double* rhs = S + (size_t)kb * ld;
+    for (int i = kb - 1; i >= 0; --i) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
             const double d = S[(size_t)i * ld + i];
-            y[i] = d != 0.0 ? s / d : 0.0;
+            const double yi = d != 0.0 ? rhs[i] / d : 0.0;
+            y[i] = yi;
+            s_yi = yi;
         }
+        __syncthreads();
+        const double yi = s_yi;
+        const double* ci = S + (size_t)i * ld;
+        for (int row = threadIdx.x; row < i; row += blockDim.x) rhs[row] = fma(-ci[row], yi, rhs[row]);
     }
 }
 
@@ -404,7 +478,7 @@ cudaError_t launch_solve_prepare(const Geom& g, const Bufs& bf, int zeta, int k,
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int njobs = g.B * (need_T ? 2 : 1);
-    const size_t smem = sizeof(double) * (size_t)g.m_s;
+    const size_t smem = 2 * sizeof(double) * (size_t)g.m_s;
     e = cudaFuncSetAttribute(k_householder, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
