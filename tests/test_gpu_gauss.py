@@ -47,6 +47,30 @@ def test_gaussian_sketch_matches_oracle(storage):
     ctx.close()
 
 
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_gaussian_sketch_odd_rows(storage):
+    """m_s = 203: a column of S is not a whole number of 16-byte vectors, so
+    c = S b takes the scalar path and the draw's row carry wraps mid-vector;
+    x_k against the oracle as above (k = 1, 2, 5)."""
+    p = P.make("deblur64")
+    m_s = 203
+    A = ops.make_apply(p)
+    S = sk.GaussianSketch(p.sketch_seed, p.n, m_s, storage)
+    st = scmrh.run(A, p.b[0].astype(np.float64), S, 5)
+    ctx = gpu_context(p, storage, k=5, m_s=m_s, sketch="gaussian")
+    ctx.step(5)
+    status, kd = ctx.sync()
+    assert kd == [5]
+    agree = compare_pivots(ctx.export(0)["piv"][:6], st, storage)
+    for k in [kk for kk in (1, 2, 5) if kk < agree]:
+        x, _ = ctx.solve(k, [0.0])
+        kappa = np.linalg.cond(scmrh.projected_matrix(st, k))
+        tol = max(FLOOR[storage], 10 * U[storage] * kappa, 10 * np.sqrt(p.n) * 2.0 ** -24 * kappa)
+        e = rel(x[0, 0].astype(np.float64), scmrh.solve(st, k, 0.0))
+        assert e <= tol, (k, e, tol)
+    ctx.close()
+
+
 def test_gaussian_sketch_needs_one_rhs():
     from paper_2502_02721_gb300 import binding as bd
     p = P.ct_parallel(side=16, nrhs=2, k=5, m_s=20)
