@@ -154,10 +154,12 @@ typedef struct ipf_config {
     int overlap;                 /* PSF2D/CSR with float storage, second stream per step:
                                     0 one stream; 1 the operator beside V_j h; 2 (default)
                                     the operator beside the pivot-row products and the
-                                    FP64 pivot-block solve, and (one RHS, zeta 8, no DIRECT
-                                    Z with BF16/FP16) the sketch S v_j of the previous
-                                    column on a third stream beside them, the newest
-                                    column's sketch taken before a solve or export     */
+                                    FP64 pivot-block solve.  In modes 0 and 2 with one
+                                    RHS, float storage, zeta 8 and no DIRECT Z with
+                                    BF16/FP16, the sketch S v_{j+1} of each new column is
+                                    taken by the next step's update (which streams that
+                                    column anyway) and the newest column's before a solve
+                                    or export; the sums are the same exact integers      */
     int method;                  /* enum ipf_method (default IPF_METHOD_SCMRH)               */
     int sketch;                  /* enum ipf_sketch (default IPF_SKETCH_SPARSE_SIGN)        */
     int pivot_sample;            /* 0 (default): each pivot is the largest |.| over all
