@@ -224,8 +224,8 @@ struct Geom {
     int F;              // fixed-point exponent of the sketch accumulators
     int want_z;         // DIRECT form: z_j = S A v_j (needs S of the unrounded vectors)
     int sketch_off = 0; // Gaussian sketch: no per-step sparse sketch (S V is formed at solve time)
-    int sketch_defer = 0;  // the normaliser leaves S v_{j+1} to k_sketch_col (launched beside the
-                           // next step's operator, or before a solve) and marks the column pending
+    int sketch_defer = 0;  // the normaliser leaves S v_{j+1} to the next step's update (or to
+                           // k_sketch_col before a solve) and marks the column pending
 };
 
 struct Bufs {
