@@ -3,7 +3,11 @@
 
 One step = one whole solve through the C ABI: initialisation (pivot of b,
 v_1, sketches), k Hessenberg steps (operator, pivot-block solve, update +
-argmax, normalise + sketch) and the sketched projected solve with x = V_k y.
+argmax + the sketch of the newest column, normalise) and the sketched
+projected solve with x = V_k y.  The timed region runs the library default
+(one CUDA graph per Hessenberg step); per-kernel times and the roofline come
+from a second, profiled pass of the same workload (CUDA events around every
+launch on the library's streams).
 
 Default workload: 2048 x 2048 deblurring with a 31 x 31 Moffat PSF
 (beta 2.5, alpha 4), ellipse phantom, 1% noise, k = 200, m_s = 800, zeta 8,
