@@ -173,6 +173,21 @@ def run_oracle_sample(steps: int) -> dict:
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def max_over_ranks(torch, dist, t_ms: float, device: str) -> float:
+    """The slowest rank's time (all ranks get it); t_ms itself on one process."""
+    if dist is None:
+        return float(t_ms)
+    tt = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def replica_throughput(world: int, steps: int, k: int, t_max_ms: float) -> float:
+    """Whole-job Hessenberg iterations/s: every rank solves `steps` times with
+    k iterations each (independent replicas), over the slowest rank's time."""
+    return world * steps * k / (t_max_ms * 1e-3)
+
+
 def run_ours(args, rank, world, torch, dist):
     from gen import problems as P
     from paper_2502_02721_gb300 import binding as bd, build as bl
@@ -227,11 +242,7 @@ def run_ours(args, rank, world, torch, dist):
     clocks.start()
     t16, per16, prof16, kd16 = timed_solves(ctx16, x16, args.steps, args.warmup)
     clk = clocks.stop()
-    t_max = t16
-    if dist is not None:
-        tt = torch.tensor([t16], dtype=torch.float64, device=f"cuda:{dev}")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(torch, dist, t16, f"cuda:{dev}")
 
     # --- per-kernel times: the same workload in profile mode (events around
     # every launch, eager), a separate pass after the timed region --------
@@ -279,13 +290,15 @@ def run_ours(args, rank, world, torch, dist):
     ctx16.step(k)
     ctx16.solve(k, [0.0], out=x_host)
     torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         ctx16.reset(b_host)
         ctx16.step(k)
         ctx16.solve(k, [0.0], out=x_host)
     torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
+    t_e2e_ms = max_over_ranks(torch, dist, 1e3 * (time.perf_counter() - t0), f"cuda:{dev}")
     ctx16.profile_read()
 
     # --- CPU baseline (rank 0 only, bounded oracle sample) -----------------
@@ -334,8 +347,7 @@ def run_ours(args, rank, world, torch, dist):
                      + cnt[9] + cnt[10] + cnt[11])
     launches = launches_p * args.steps // steps_p          # the profiled pass ran steps_p solves
 
-    iters = world * args.steps * k
-    value = iters / (t_max * 1e-3)
+    value = replica_throughput(world, args.steps, k, t_max)
     out = {
         "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -357,7 +369,8 @@ def run_ours(args, rank, world, torch, dist):
         "roofline_other": roof_conv if dominant in (2, 3, 6) else roof,
         "kernels": kern,
         "gpu_launches": launches * world,
-        "e2e": {"value": e2e_steps * k / t_e2e, "unit": "iters/s", "h2d_bytes_per_step": int(4 * n),
+        "e2e": {"value": replica_throughput(world, e2e_steps, k, t_e2e_ms), "unit": "iters/s",
+                "h2d_bytes_per_step": int(4 * n),
                 "d2h_bytes_per_step": int(4 * n)},
         "clocks": {k2: clk[k2] for k2 in ("sm_mhz", "sm_max_mhz", "reasons")},
         "k_done": kd16,
