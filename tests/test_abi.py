@@ -71,3 +71,47 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.ipf_create(C.byref(op), bb.ctypes.data, 0, C.byref(cfg), C.byref(h)) == b.IPF_ERR_ARG
     assert lib.ipf_step(None, 1, None) == b.IPF_ERR_ARG
     assert lib.ipf_footprint(C.byref(op), C.byref(b.default_config())) > 64 * 51 * 4
+
+
+def test_default_config_maps_string_options(lib):
+    """Library defaults (ipf_config_default, host only) and the binding's
+    names for the enums of include/ipf.h."""
+    from paper_2502_02721_gb300 import binding as bd
+    d = bd.default_config()
+    assert d.overlap == 2 and d.pivot_sample == 0 and d.sketch == 0 and d.method == 0
+    cfg = bd.default_config(storage="bf16", method="slslu", sketch="gaussian", pivot_sample=25)
+    assert cfg.storage == bd.STORAGE["bf16"]
+    assert cfg.method == bd.METHOD["slslu"] == 1
+    assert cfg.sketch == bd.SKETCH["gaussian"] == 1
+    assert cfg.pivot_sample == 25
+
+
+def test_footprint_counts_the_gaussian_sketch(lib):
+    """ipf_footprint (host arithmetic): a Gaussian sketch adds the stored S,
+    m_s x n elements of the basis storage type."""
+    import ctypes as C
+    from gen import problems as P
+    from paper_2502_02721_gb300 import binding as bd
+    p = P.make("deblur64")
+    keep = []
+    op = bd.operator_from_problem(p, keep)
+    base = bd.default_config(k_max=p.k, m_s=p.m_s, storage="bf16")
+    gauss = bd.default_config(k_max=p.k, m_s=p.m_s, storage="bf16", sketch="gaussian")
+    f0 = lib.ipf_footprint(C.byref(op), C.byref(base))
+    f1 = lib.ipf_footprint(C.byref(op), C.byref(gauss))
+    assert f1 - f0 >= p.m_s * p.n * 2
+
+
+def test_binding_refuses_host_buffers_for_device_calls(lib):
+    """Calls whose kernels write a buffer check, before reaching the
+    library, that it is a device tensor of the right size and element size."""
+    import torch
+    from paper_2502_02721_gb300 import binding as bd
+    S = torch.empty(8 * 100, dtype=torch.bfloat16)            # host memory
+    with pytest.raises(ValueError):
+        bd.sketch_gaussian("bf16", 1, 100, 8, S)
+    with pytest.raises(ValueError):
+        bd.sketch_gaussian("bf16", 1, 100, 8, torch.empty(10, dtype=torch.bfloat16))
+    x, y = torch.empty(100), torch.empty(8, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        bd.sketch_apply(x, 8, 8, 1, y)
