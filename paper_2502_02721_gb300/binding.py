@@ -383,8 +383,11 @@ class Operator:
         self.h = h
 
     def apply(self, v, w, nrhs: int = 1, stream=None):
+        """w (float32, nrhs x m) = A v (float32, nrhs x n), device tensors."""
         _check_size(v, nrhs * self.n, "v")
         _check_size(w, nrhs * self.m, "w")
+        _check_device(v, "v", 4)
+        _check_device(w, "w", 4)
         st = self._lib.ipf_op_apply(self.h, v.data_ptr(), w.data_ptr(), int(nrhs), stream)
         if st != IPF_OK:
             raise IpfError(st, "ipf_op_apply")
@@ -395,6 +398,8 @@ class Operator:
             raise TypeError("apply_bf16 takes a bfloat16 v and a float32 w")
         _check_size(v, self.n, "v")
         _check_size(w, self.m, "w")
+        _check_device(v, "v", 2)
+        _check_device(w, "w", 4)
         st = self._lib.ipf_op_apply_bf16(self.h, v.data_ptr(), w.data_ptr(), 1 if use_fma else 0, stream)
         if st != IPF_OK:
             raise IpfError(st, "ipf_op_apply_bf16")

@@ -115,3 +115,18 @@ def test_binding_refuses_host_buffers_for_device_calls(lib):
     x, y = torch.empty(100), torch.empty(8, dtype=torch.float64)
     with pytest.raises(ValueError):
         bd.sketch_apply(x, 8, 8, 1, y)
+
+
+def test_operator_apply_refuses_host_buffers(lib):
+    """Operator.apply / apply_bf16 check their tensors before the library call
+    (the handle is built without ipf_op_create, which needs a GPU)."""
+    import torch
+    from paper_2502_02721_gb300 import binding as bd
+    op = bd.Operator.__new__(bd.Operator)
+    op._lib, op.m, op.n, op.h = lib, 16, 16, None
+    with pytest.raises(ValueError):
+        op.apply(torch.empty(16), torch.empty(16))
+    with pytest.raises(ValueError):
+        op.apply_bf16(torch.empty(16, dtype=torch.bfloat16), torch.empty(16))
+    with pytest.raises(ValueError):
+        op.apply(torch.empty(15), torch.empty(16))
