@@ -177,20 +177,29 @@ def siddon_parallel(nimg: int, nangles: int, ndet: int, det_spacing: float = 1.0
                 tymax = np.where(inside, np.inf, -np.inf)
         tlo = np.maximum(txmin, tymin)
         thi = np.minimum(txmax, tymax)
-        T = np.clip(T, tlo[:, None], thi[:, None])
-        T = np.sort(T, axis=1)
-        t0, t1 = T[:, :-1], T[:, 1:]
+        # rays that miss the square have an empty (or infinite) interval: they
+        # get empty rows, and only the others reach the arithmetic below
+        hit = np.isfinite(tlo) & np.isfinite(thi) & (tlo < thi)
+        Th = np.sort(np.clip(T[hit], tlo[hit, None], thi[hit, None]), axis=1)
+        t0, t1 = Th[:, :-1], Th[:, 1:]
         L = t1 - t0
         tm = 0.5 * (t0 + t1)
-        xm = px[:, None] + tm * ux
-        ym = py[:, None] + tm * uy
+        xm = px[hit, None] + tm * ux
+        ym = py[hit, None] + tm * uy
         c = np.floor(xm + half).astype(np.int64)
         r = (nimg - 1) - np.floor(ym + half).astype(np.int64)
         ok = (L > 1e-9) & (c >= 0) & (c < nimg) & (r >= 0) & (r < nimg)
+        hit_row = np.cumsum(hit) - 1
         for d in range(ndet):
-            m = ok[d]
-            col = (r[d][m] * nimg + c[d][m])
-            val = L[d][m]
+            if not hit[d]:
+                rows_cols.append(np.zeros(0, np.int32))
+                rows_vals.append(np.zeros(0, np.float32))
+                counts.append(0)
+                continue
+            h = hit_row[d]
+            m = ok[h]
+            col = (r[h][m] * nimg + c[h][m])
+            val = L[h][m]
             # merge duplicate pixels (a crossing can split one pixel's chord)
             if col.size:
                 order = np.argsort(col, kind="stable")

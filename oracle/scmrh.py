@@ -23,6 +23,12 @@ The steps below follow Algorithm 1 in its order:
          x = V_k y
 The sequential elimination leaves u(p_i) = 0 exactly (v_i(p_i) = 1 and
 v_c(p_i) = 0 for c > i hold exactly in floating point), which run() asserts.
+
+Storage precision (storage = "f32", "bf16", "f16"; default "f64"): each new
+basis vector v_{j+1} = u / H(j+1, j) (and v_1 = b / beta) is rounded to the
+storage type right after its normalisation, and every later step reads the
+stored vector; all arithmetic stays float64.  Rounding keeps v(p_{j+1}) = 1
+and the zeros on earlier pivot rows exact, so the elimination is unchanged.
 """
 from __future__ import annotations
 
@@ -32,6 +38,7 @@ import numpy as np
 import scipy.linalg as sla
 
 from . import pivoting
+from .storage import round_to
 
 
 @dataclass
@@ -60,13 +67,15 @@ def _argmax_abs_excluding(u: np.ndarray, is_piv: np.ndarray):
     return i, float(top), gap
 
 
-def iterate(apply_A, b, sketch, k_max: int, forced_pivots=None, pivot_sample: int = 0, pivot_seed: int = 0):
+def iterate(apply_A, b, sketch, k_max: int, forced_pivots=None, pivot_sample: int = 0, pivot_seed: int = 0,
+            storage: str = "f64"):
     """Generator form of run(): yields (j, state) after the initialisation
     (j = 0) and after each Hessenberg step j = 1..k_done.  Each state holds
     views of the working arrays trimmed to the j completed steps.
 
     pivot_sample > 0 chooses each pivot by sampled pivoting (pivoting.py)
-    with sampling seed pivot_seed."""
+    with sampling seed pivot_seed.  storage rounds each new basis vector to
+    that type (module docstring)."""
     b = np.asarray(b, dtype=np.float64).reshape(-1)
     n = b.size
     m = sketch.m
@@ -94,7 +103,7 @@ def iterate(apply_A, b, sketch, k_max: int, forced_pivots=None, pivot_sample: in
     if beta == 0.0:
         yield 0, state(0, 0.0, [], True)
         return
-    V[:, 0] = b / beta
+    V[:, 0] = round_to(b / beta, storage)
     piv = [i]
     is_piv[i] = True
     SV[:, 0] = sketch.apply(V[:, 0])
@@ -119,7 +128,7 @@ def iterate(apply_A, b, sketch, k_max: int, forced_pivots=None, pivot_sample: in
             if pivot_sample > 0:
                 p = pivoting.sampled_pivot(u, is_piv, pivot_seed, j + 1, pivot_sample)
         H[j + 1, j] = u[p]
-        V[:, j + 1] = u / H[j + 1, j]
+        V[:, j + 1] = round_to(u / H[j + 1, j], storage)
         piv.append(p)
         is_piv[p] = True
         SV[:, j + 1] = sketch.apply(V[:, j + 1])
@@ -127,15 +136,16 @@ def iterate(apply_A, b, sketch, k_max: int, forced_pivots=None, pivot_sample: in
 
 
 def run(apply_A, b, sketch, k_max: int, forced_pivots=None, pivot_sample: int = 0,
-        pivot_seed: int = 0) -> HessenbergState:
+        pivot_seed: int = 0, storage: str = "f64") -> HessenbergState:
     """k_max steps of the pivoted Hessenberg process with sketch S.
 
     forced_pivots: optional sequence of rows to use as p_1, p_2, ... instead
     of the max-|.| choice (replays another run's pivot order when two
-    candidates are within rounding of each other).
+    candidates are within rounding of each other).  storage: the type the
+    basis is kept in (module docstring).
     """
     st = None
-    for _, st in iterate(apply_A, b, sketch, k_max, forced_pivots, pivot_sample, pivot_seed):
+    for _, st in iterate(apply_A, b, sketch, k_max, forced_pivots, pivot_sample, pivot_seed, storage):
         pass
     return st
 

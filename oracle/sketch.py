@@ -29,6 +29,8 @@ from __future__ import annotations
 
 import numpy as np
 
+from .storage import round_to  # noqa: F401  (S is kept in the basis storage type)
+
 GAMMA = 0x9E3779B97F4A7C15
 C1 = 0xBF58476D1CE4E5B9
 C2 = 0x94D049BB133111EB
@@ -111,22 +113,6 @@ class SparseSignSketch:
         for t in range(self.zeta):
             S[rows[:, t], np.arange(self.n)] = signs[:, t] / np.sqrt(self.zeta)
         return S
-
-
-def round_to(a: np.ndarray, storage: str) -> np.ndarray:
-    """Entries rounded (to nearest even) to a storage type, returned as float64."""
-    a = np.asarray(a, dtype=np.float64)
-    if storage == "f64":
-        return a.copy()
-    if storage == "f32":
-        return a.astype(np.float32).astype(np.float64)
-    if storage == "f16":
-        return a.astype(np.float16).astype(np.float64)
-    if storage == "bf16":
-        u = a.astype(np.float32).view(np.uint32).astype(np.uint64)
-        u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
-        return (u.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
-    raise ValueError(storage)
 
 
 class GaussianSketch:

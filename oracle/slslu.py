@@ -34,6 +34,11 @@ Steps, in the algorithm's order:
                               W(k+1,k+1) = q(g_{k+1}); l_{k+1} = q / W(k+1,k+1)
          else: stop
 Pivots are the largest magnitude with the lowest index on ties.
+
+Storage precision (storage = "f32", "bf16", "f16"; default "f64"): each new
+vector of D and of L is rounded to the storage type right after its
+normalisation, and every later step reads the stored vector (the reading of
+scmrh.py); all arithmetic stays float64.
 """
 from __future__ import annotations
 
@@ -42,6 +47,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import pivoting
+from .storage import round_to
 from .scmrh import _argmax_abs_excluding, _lstsq_qr, qmr_y
 
 
@@ -67,14 +73,14 @@ class GenHessenbergState:
 
 
 def iterate(apply_A, apply_At, b, S1, S2, k_max: int, forced_t=None, forced_g=None, pivot_sample: int = 0,
-            pivot_seeds=(0, 0)):
+            pivot_seeds=(0, 0), storage: str = "f64"):
     """Yields (k, state) after the initialisation (k = 0) and after each step.
 
     forced_t / forced_g: optional pivot sequences to use instead of the
     max-|.| choice (replays another run's order where two candidates are
     within rounding of each other).  pivot_sample > 0 chooses the pivots by
     sampled pivoting (pivoting.py), with sampling seeds pivot_seeds for D
-    and L."""
+    and L.  storage rounds each new basis vector to that type."""
     b = np.asarray(b, dtype=np.float64).reshape(-1)
     m = b.size
     v0 = apply_At(b)
@@ -112,7 +118,7 @@ def iterate(apply_A, apply_At, b, S1, S2, k_max: int, forced_t=None, forced_g=No
     if beta == 0.0:
         yield 0, state(0, 0.0, 0.0, 0, True)
         return
-    D[:, 0] = b / beta
+    D[:, 0] = round_to(b / beta, storage)
     pt.append(i)
     tpiv[i] = True
     SD[:, 0] = S2.apply(D[:, 0])
@@ -121,7 +127,7 @@ def iterate(apply_A, apply_At, b, S1, S2, k_max: int, forced_t=None, forced_g=No
     if alpha == 0.0:
         yield 0, state(0, beta, 0.0, 0, True)
         return
-    L[:, 0] = v0 / alpha
+    L[:, 0] = round_to(v0 / alpha, storage)
     pg.append(i2)
     gpiv[i2] = True
     SL[:, 0] = S1.apply(L[:, 0])
@@ -141,7 +147,7 @@ def iterate(apply_A, apply_At, b, S1, S2, k_max: int, forced_t=None, forced_g=No
             return
         p = choose(u, tpiv, forced_t, k + 1, gaps_t, 0)
         H[k + 1, k] = u[p]
-        D[:, k + 1] = u / H[k + 1, k]
+        D[:, k + 1] = round_to(u / H[k + 1, k], storage)
         pt.append(p)
         tpiv[p] = True
         SD[:, k + 1] = S2.apply(D[:, k + 1])
@@ -156,7 +162,7 @@ def iterate(apply_A, apply_At, b, S1, S2, k_max: int, forced_t=None, forced_g=No
             return
         p2 = choose(q, gpiv, forced_g, k + 1, gaps_g, 1)
         W[k + 1, k + 1] = q[p2]
-        L[:, k + 1] = q / W[k + 1, k + 1]
+        L[:, k + 1] = round_to(q / W[k + 1, k + 1], storage)
         pg.append(p2)
         gpiv[p2] = True
         SL[:, k + 1] = S1.apply(L[:, k + 1])
@@ -164,9 +170,10 @@ def iterate(apply_A, apply_At, b, S1, S2, k_max: int, forced_t=None, forced_g=No
 
 
 def run(apply_A, apply_At, b, S1, S2, k_max: int, forced_t=None, forced_g=None, pivot_sample: int = 0,
-        pivot_seeds=(0, 0)) -> GenHessenbergState:
+        pivot_seeds=(0, 0), storage: str = "f64") -> GenHessenbergState:
     st = None
-    for _, st in iterate(apply_A, apply_At, b, S1, S2, k_max, forced_t, forced_g, pivot_sample, pivot_seeds):
+    for _, st in iterate(apply_A, apply_At, b, S1, S2, k_max, forced_t, forced_g, pivot_sample, pivot_seeds,
+                         storage):
         pass
     return st
 

@@ -8,7 +8,7 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
-from _gpu_common import U, ensure_lib, rel, tolerance  # noqa: E402
+from _gpu_common import PAR_FLOOR, RECORD, STATED, U, U_ACC, ensure_lib, rel  # noqa: E402
 from gen import problems as P  # noqa: E402
 from oracle import operators as ops, slslu, sketch as sk  # noqa: E402
 
@@ -36,54 +36,66 @@ def _first_divergence(a, b, k):
     return next((j for j in range(k + 1) if int(a[j]) != int(b[j])), k + 1)
 
 
-def _perturbed(A, At, b, S1, S2, k, delta, seed=12345, forced=(None, None), **sampling):
+def _perturbed(A, At, b, S1, S2, k, delta, seed=12345, forced=(None, None), storage="f64", **sampling):
     """The oracle with every operator output perturbed elementwise by a
     relative N(0, delta^2) error: the response of the process to rounding in
     the products at that level."""
     rng = np.random.default_rng(seed)
     Ap = lambda v: (lambda w: w * (1.0 + delta * rng.standard_normal(w.size)))(A(v))
     Atp = lambda v: (lambda w: w * (1.0 + delta * rng.standard_normal(w.size)))(At(v))
-    return slslu.run(Ap, Atp, b, S1, S2, k, forced_t=forced[0], forced_g=forced[1], **sampling)
+    return slslu.run(Ap, Atp, b, S1, S2, k, forced_t=forced[0], forced_g=forced[1], storage=storage, **sampling)
 
 
-def _verify(ctx, A, At, b, S1, S2, k, storage, taps, ks, lambdas, **sampling):
+def _verify(ctx, A, At, b, S1, S2, k, storage, taps, ks, lambdas, name="", **sampling):
     """Pivots, then iterates.
 
     Max-|.| pivoting in the generalized process is chaotic: a relative
     perturbation of the products at rounding level (1e-15) changes the
     oracle's own pivot choices after some 25 steps on the CT problem and
     moves x_50 of the deblurring problem by ~3e-7 with identical pivots.  So
-    (i) the GPU's pivot sequences must agree with the oracle's until at least
-    the step where the oracle itself, perturbed by sqrt(K) u_s per product (K
-    terms summed in an order the oracle does not share), first departs from
-    its own sequence (earliest of three perturbations, less a margin of 3);
-    (ii) the iterates are compared with the oracle replaying the GPU's pivot
-    sequences, within max(floor, 10 u_s kappa(Z_k), 10 r_k), r_k the replay's
-    own response to that perturbation."""
-    st = slslu.run(A, At, b, S1, S2, k, **sampling)
+    (i) the GPU's pivot sequences must agree with the oracle's (the oracle
+    keeping its bases in the same storage type) until at least the step
+    where that oracle, perturbed by sqrt(K) u_acc per product (K terms summed
+    in an order the oracle does not share), first departs from its own
+    sequence (earliest of three perturbations, less a margin of 3); (ii) the
+    iterates are compared with the storage-matched oracle replaying the GPU's
+    pivot sequences, within max(floor, 10 r_k), r_k the replay's own response
+    to that perturbation; (iii) against the FP64 oracle the stated tolerance
+    is asserted wherever the storage type can reach it (_gpu_common)."""
+    st64 = slslu.run(A, At, b, S1, S2, k, **sampling)
+    st = st64 if storage == "f64" else slslu.run(A, At, b, S1, S2, k, storage=storage, **sampling)
     ex, du = ctx.export(0), ctx.export_dual(0)
     gt = [int(v) for v in ex["piv"][:k + 1]]
     gg = [int(v) for v in du["piv"][:k + 1]]
     assert min(gt) >= 0 and min(gg) >= 0
-    delta = np.sqrt(taps) * U[storage]
+    delta = np.sqrt(taps) * U_ACC[storage]
     j_gpu = min(_first_divergence(gt, st.pt, k), _first_divergence(gg, st.pg, k))
     if j_gpu <= k:
         j_or = k + 1
         for seed in (1, 2, 3):
-            sp = _perturbed(A, At, b, S1, S2, k, delta, seed, **sampling)
+            sp = _perturbed(A, At, b, S1, S2, k, delta, seed, storage=storage, **sampling)
             j_or = min(j_or, _first_divergence(sp.pt, st.pt, k), _first_divergence(sp.pg, st.pg, k))
         assert j_gpu >= j_or - 3, (j_gpu, j_or)
-    st_f = slslu.run(A, At, b, S1, S2, k, forced_t=gt, forced_g=gg)
-    st_fp = _perturbed(A, At, b, S1, S2, k, delta, forced=(gt, gg))
+    st_f = slslu.run(A, At, b, S1, S2, k, forced_t=gt, forced_g=gg, storage=storage)
+    st_fp = _perturbed(A, At, b, S1, S2, k, delta, forced=(gt, gg), storage=storage)
     for kk in ks:
         x, info = ctx.solve(kk, lambdas)
-        kappa = np.linalg.cond(slslu.projected_matrix(st_f, kk))
         for li, lam in enumerate(lambdas):
             x_or = slslu.solve(st_f, kk, lam)
             resp = rel(slslu.solve(st_fp, kk, lam), x_or)
-            tol = max(tolerance(storage, kappa), 10.0 * resp)
-            e = rel(x[li, 0].astype(np.float64), x_or)
-            assert e <= tol, (kk, lam, e, tol, kappa, resp)
+            tol = max(PAR_FLOOR, 10.0 * resp)
+            xg = x[li, 0].astype(np.float64)
+            e = rel(xg, x_or)
+            x64 = slslu.solve(st64, kk, lam)
+            e64, d_s = rel(xg, x64), rel(x_or, x64)
+            reach = d_s + tol <= STATED[storage]
+            rec = {"test": name, "storage": storage, "k": kk, "lam": lam, "e_par": e, "tol_par": tol, "e64": e64,
+                   "stated": STATED[storage], "storage_only": d_s, "stated_reachable": bool(reach),
+                   "pivots_agree": j_gpu}
+            RECORD.append(rec)
+            assert e <= tol, rec
+            if reach:
+                assert e64 <= STATED[storage], rec
     return st, j_gpu
 
 
@@ -98,7 +110,7 @@ def deblur64_slslu():
     return p, A, At, b, S1, S2, np.count_nonzero(psf)
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
 def test_deblur64_slslu_parity(deblur64_slslu, storage):
     from paper_2502_02721_gb300 import binding as bd
     p, A, At, b, S1, S2, taps = deblur64_slslu
@@ -107,13 +119,16 @@ def test_deblur64_slslu_parity(deblur64_slslu, storage):
     ctx.step(p.k)
     status, kd = ctx.sync()
     assert kd == [p.k]
-    st, j_gpu = _verify(ctx, A, At, b, S1, S2, p.k, storage, taps, [1, 2, 5, 10, 20, 30, 50], p.lambdas)
+    st, j_gpu = _verify(ctx, A, At, b, S1, S2, p.k, storage, taps, [1, 2, 5, 10, 20, 30, 50], p.lambdas,
+                        name=f"slslu_deblur64_{storage}")
     ex, du = ctx.export(0), ctx.export_dual(0)
     assert abs(ex["beta"] - st.beta) <= 1e-6 * abs(st.beta)
-    assert abs(du["w11"] - st.W[0, 0]) <= (1e-12 if storage == "f64" else 1e-5) * abs(st.W[0, 0])
-    # the first Hessenberg column and the first columns of W
-    assert rel(ex["H"][:2, 0], st.H[:2, 0]) < (1e-12 if storage == "f64" else 1e-5)
-    assert rel(du["W"][:2, 0], st.W[:2, 1]) < (1e-12 if storage == "f64" else 1e-5)
+    # W(1,1) and the first columns of H and W come from the stored d_1, l_1,
+    # so they match the storage-matched oracle to the accumulation precision
+    tol1 = 1e-12 if storage == "f64" else 1e-5
+    assert abs(du["w11"] - st.W[0, 0]) <= tol1 * abs(st.W[0, 0])
+    assert rel(ex["H"][:2, 0], st.H[:2, 0]) < tol1
+    assert rel(du["W"][:2, 0], st.W[:2, 1]) < tol1
     if storage == "f64":
         assert j_gpu == p.k + 1
         # the LSLU quasi-minimal residual iterate on the same bases
@@ -158,7 +173,7 @@ def test_rectangular_ct_slslu_parity(storage, sample):
         sampling = dict(pivot_sample=sample,
                         pivot_seeds=(seed ^ PIVOT_SEED_XOR, seed ^ PIVOT_SEED_XOR ^ S1_SEED_XOR))
     _verify(ctx, A, At, b.astype(np.float64), S1, S2, k, storage, taps, [1, 3, 10, 25, 40], [0.0, 0.1],
-            **sampling)
+            name=f"slslu_ct_rect_{storage}_s{sample}", **sampling)
     x, _ = ctx.solve(k, [0.0])
     assert x.shape == (1, 1, n)
     ctx.close()

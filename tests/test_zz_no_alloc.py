@@ -1,8 +1,14 @@
-"""The allocation-free sketch entry point (ipf_sketch_apply_noalloc) gives
-the same result as ipf_sketch_apply, through the C ABI, on two calls in a
-row of different sizes (the shared scratch keeps the previous call's
-contents, so the second call checks that it is cleared).  This file is
-collected last so a run that stops at its failure has run everything else.
+"""The allocation-free sketch entry point (ipf_sketch_apply_noalloc) against
+the allocating one (ipf_sketch_apply) and the oracle, through the C ABI.
+
+Both entry points run the same kernels with exact 64-bit integer sums, so
+their results must be bit-identical; a partial clear of the shared scratch
+(which keeps the previous call's contents) would leave stale residues that
+this equality catches.  The two cases run back to back with different sizes,
+largest first, so the second call starts from a scratch array the first one
+filled.  The result is also compared with the oracle's sparse-sign S x
+within the rounding bound of the fixed-point sums.  This file is collected
+last so a run that stops at its failure has run everything else.
 """
 import numpy as np
 import pytest
@@ -11,7 +17,9 @@ pytestmark = pytest.mark.gpu
 
 
 def _tol(x, n, m_s, zeta, seed):
-    # the rounding bound of the exact fixed-point sums (as in the sketch parity test)
+    # rounding bound of the exact fixed-point sums: each of the at most cmax
+    # contributions to a row is rounded once to the quantum 2^-F (half a
+    # quantum each, taken as a random walk with a factor 10 of margin)
     from oracle import sketch as sk
     e_max = int(np.frexp(np.float64(np.abs(x).max()))[1])
     F = 61 - int(np.ceil(np.log2(n + 1))) - e_max
@@ -23,6 +31,7 @@ def _tol(x, n, m_s, zeta, seed):
 def test_noalloc_matches_allocating_entry_point_twice():
     import torch
     from _gpu_common import ensure_lib
+    from oracle import sketch as sk
     from paper_2502_02721_gb300 import binding as bd
     ensure_lib()
     cases = [(300001, 800, 8, 0xABCDEF), (4097, 120, 3, 77)]
@@ -37,7 +46,9 @@ def test_noalloc_matches_allocating_entry_point_twice():
         torch.cuda.synchronize()
         a, b = y_ref.cpu().numpy(), y_new.cpu().numpy()
         assert np.all(np.isfinite(b))
-        assert np.max(np.abs(a - b)) <= _tol(x, n, m_s, zeta, seed)
+        assert np.array_equal(a, b), (n, m_s, int(np.count_nonzero(a != b)))
+        want = sk.SparseSignSketch(seed, n, m_s, zeta).apply(x.astype(np.float64))
+        assert np.max(np.abs(b - want)) <= _tol(x, n, m_s, zeta, seed)
 
 
 def test_noalloc_rejects_too_many_rows():
