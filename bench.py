@@ -40,9 +40,19 @@ WORKLOAD = ("deblur 2048x2048, Moffat 31x31 PSF (beta 2.5, alpha 4), ellipse pha
 K_ITERS = 200
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# kernels named in the roofline, from one ncu capture of this workload; to be
-# cleared whenever the kernel changes
-TRAFFIC: dict = {"update": 885.84e6, "conv": 8.53e6}
+# kernels named in the roofline, averaged over the steps of this workload:
+# taken by ncu on one launch each of the 1024 x 1024 case (--small) and scaled
+# to 2048 x 2048 by the units processed; None until taken for the current
+# kernels (cleared whenever a kernel changes)
+TRAFFIC: dict = {"update": None, "conv": None}
+
+# the accuracy gate: FP64 oracle iterates of the 1024 x 1024 Moffat case
+# (k = 64, m_s = 256) and of the first steps of the 2048 x 2048 workload,
+# against which the GPU's BF16, FP16 and FP32 forms are measured
+GATE_SIDE, GATE_K, GATE_MS = 1024, 64, 256
+GATE_KS = (1, 8, 64)
+GATE_LAMS = (0.0, 1e-2)
+GATE2048_K = 5
 
 
 def _peaks():
@@ -135,39 +145,64 @@ def _gpu_id(torch, dev):
 # ---------------------------------------------------------------------------
 # the FP64 oracle on a bounded sample (CPU baseline and the reference arm)
 # ---------------------------------------------------------------------------
-ORACLE_SAMPLE = ("oracle (numpy float64) on the full 2048x2048 problem: initialisation plus Hessenberg "
-                 "steps 1..{s} (each: one 31x31 convolution, the sequential elimination, the max pivot, "
-                 "two sketches), single thread")
+ORACLE_SAMPLE = ("oracle (numpy float64) on the full 2048x2048 problem: Hessenberg steps 1..{s} after the "
+                 "initialisation (each: one 31x31 convolution, the sequential elimination, the max pivot, two "
+                 "sketches); {r} replicas at once, one per host core, one thread each; its step cost grows with j "
+                 "(the elimination is O(j n)), so this rate is an upper bound on its rate over j = 1..200")
 
 
-def oracle_sample_child(steps: int, out_path: str):
-    """Runs in a fresh interpreter with BLAS limited to one thread."""
+def oracle_gate_child(side: int, k: int, m_s: int, ks, lams, out_path: str):
+    """The FP64 oracle on the side x side Moffat workload for k steps (one
+    thread), x_k for each k in ks and lambda in lams, and the step times."""
     from gen import problems as P
     from oracle import operators as ops, scmrh, sketch as sk
-    p = P.make("deblur2048")
+    p = P.make("deblur2048") if side == 2048 else P.deblur_moffat(side=side, k=k, m_s=m_s)
     A = ops.make_apply(p)
     S = sk.SparseSignSketch(p.sketch_seed, p.n, p.m_s, p.zeta)
     t0 = time.perf_counter()
-    times = []
-    st = None
-    for j, st in scmrh.iterate(A, p.b[0], S, steps):
+    times, xs = [], {}
+    for j, st in scmrh.iterate(A, p.b[0], S, k):
         times.append(time.perf_counter() - t0)
-    xs = {f"x{k}": scmrh.solve(st, k).astype(np.float32) for k in range(1, st.k_done + 1)}
-    np.savez(out_path, times=np.array(times), piv=np.array(st.piv), **xs)
+        if j in ks:
+            for li, lam in enumerate(lams):
+                xs[f"x{j}_{li}"] = scmrh.solve(st, j, lam)
+    np.savez(out_path, times=np.array(times), **xs)
 
 
-def run_oracle_sample(steps: int) -> dict:
+def start_child(fn: str, args: tuple):
+    """Start bench.<fn>(*args, out) in a fresh interpreter (one BLAS thread);
+    returns (process, output path)."""
     import tempfile
     out = os.path.join(tempfile.mkdtemp(prefix="ipf_oracle_"), "o.npz")
     env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = (f"import sys; sys.path.insert(0, {ROOT!r}); import bench; "
-            f"bench.oracle_sample_child({steps}, {out!r})")
-    subprocess.run([sys.executable, "-c", code], env=env, check=True)
+    code = f"import sys; sys.path.insert(0, {ROOT!r}); import bench; bench.{fn}(*{args!r}, {out!r})"
+    return subprocess.Popen([sys.executable, "-c", code], env=env), out
+
+
+def finish_child(h) -> dict:
+    proc, out = h
+    if proc.wait() != 0:
+        raise RuntimeError(f"oracle child failed ({proc.returncode})")
     d = np.load(out)
     times = d["times"]
-    res = {"init_s": float(times[0]), "step_s": [float(times[i] - times[i - 1]) for i in range(1, len(times))],
-           "piv": d["piv"].tolist(), "x": {int(k[1:]): d[k] for k in d.files if k.startswith("x")}}
-    return res
+    x = {}
+    for key in d.files:
+        if key.startswith("x"):
+            kk, li = key[1:].split("_")
+            x[(int(kk), int(li))] = d[key]
+    return {"init_s": float(times[0]), "step_s": [float(times[i] - times[i - 1]) for i in range(1, len(times))],
+            "x": x}
+
+
+def oracle_replicas(steps: int, cores: int) -> dict:
+    """`cores` independent replicas of the oracle (init + `steps` steps of the
+    2048 x 2048 workload, one thread each) at once on the host: the
+    oracle's aggregate rate on all cores."""
+    hs = [start_child("oracle_gate_child", (2048, steps, 800, (), ())) for _ in range(cores)]
+    res = [finish_child(h) for h in hs]
+    rate = sum(len(r["step_s"]) / sum(r["step_s"]) for r in res)
+    return {"iters_per_s": rate, "replicas": cores, "steps_each": steps,
+            "step_s_median": float(np.median([t for r in res for t in r["step_s"]]))}
 
 
 # ---------------------------------------------------------------------------
@@ -194,6 +229,14 @@ def run_ours(args, rank, world, torch, dist):
     if not os.path.exists(bl.lib_path()):
         bl.build()
     bd.load()
+    lead = rank == 0 and world == 1 and not args.no_cpu_baseline
+    # the FP64 oracle legs of the accuracy gate run on host cores beside the
+    # GPU work (fresh interpreters, one thread each)
+    gate_h = None
+    if lead:
+        gate_h = (start_child("oracle_gate_child", (GATE_SIDE, GATE_K, GATE_MS, GATE_KS, GATE_LAMS)),
+                  start_child("oracle_gate_child", (2048, GATE2048_K, 800, tuple(range(1, GATE2048_K + 1)),
+                                                    GATE_LAMS)))
     dev = torch.cuda.current_device()
     p = P.make("deblur2048")
     n = p.n
@@ -221,15 +264,15 @@ def run_ours(args, rank, world, torch, dist):
             dist.barrier()
         torch.cuda.synchronize()
         evs[0].record(stream)
-        for s in range(steps):
+        for s_ in range(steps):
             ctx.reset(b_dev)
             ctx.step(k)
             ctx.solve(k, lam, out=x_out, wait=False)
-            evs[s + 1].record(stream)
+            evs[s_ + 1].record(stream)
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
-        per = [evs[s].elapsed_time(evs[s + 1]) for s in range(steps)]
+        per = [evs[s_].elapsed_time(evs[s_ + 1]) for s_ in range(steps)]
         total = evs[0].elapsed_time(evs[-1])
         prof = ctx.profile_read()
         st, kd = ctx.sync()
@@ -253,34 +296,45 @@ def run_ours(args, rank, world, torch, dist):
     ctx16p.close()
     del x16p
 
-    # --- FP32 storage, same workload -----------------------------------------
+    # --- FP32 and FP16 storage, same workload -------------------------------
     ctx32 = make_ctx("f32", 0)
     x32 = torch.zeros((1, 1, n), dtype=torch.float32, device=f"cuda:{dev}")
     steps32 = max(1, min(args.steps, 5))
     t32, per32, prof32, kd32 = timed_solves(ctx32, x32, steps32, 1)
+    ctxh = make_ctx("f16", 0)
+    xh = torch.zeros((1, 1, n), dtype=torch.float32, device=f"cuda:{dev}")
+    th, perh, _, kdh = timed_solves(ctxh, xh, steps32, 1)
 
-    # --- accuracy: BF16 and FP32 against each other, x_true, and the FP64 oracle
+    nrm = lambda a: float(np.linalg.norm(a))
     acc = {}
     xb = x16[0, 0].double().cpu().numpy()
     xf = x32[0, 0].double().cpu().numpy()
-    nrm = lambda a: float(np.linalg.norm(a))
     acc["k200_relerr_bf16_vs_fp32"] = nrm(xb - xf) / nrm(xf)
     acc["k200_err_vs_xtrue"] = {"bf16": nrm(xb - p.x_true) / nrm(p.x_true), "fp32": nrm(xf - p.x_true) / nrm(p.x_true)}
-    # small-k iterates (before semi-convergence) for the comparison with the oracle
-    small = {}
-    for name, ctx in (("bf16", ctx16), ("fp32", ctx32)):
+
+    # --- accuracy gate, GPU side: the first steps of this workload, and the
+    # 1024 x 1024 case up to k = 64, in every storage form ------------------
+    gate_gpu = {}
+    for name, ctx in (("bf16", ctx16), ("fp32", ctx32), ("fp16", ctxh)):
         ctx.reset(b_dev)
-        ctx.step(5)
-        xs, _ = ctx.solve(5, [0.0])
-        small[name] = xs[0, 0].astype(np.float64)
-        xs1 = None
-    for name, ctx in (("bf16", ctx16), ("fp32", ctx32)):
-        ctx.reset(b_dev)
-        ctx.step(2)
-        small[name + "_k1"] = ctx.solve(1, [0.0])[0][0, 0].astype(np.float64)
-        small[name + "_k2"] = ctx.solve(2, [0.0])[0][0, 0].astype(np.float64)
-    acc["k5_err_vs_xtrue"] = {nm: nrm(small[nm] - p.x_true) / nrm(p.x_true) for nm in ("bf16", "fp32")}
-    acc["k5_relerr_bf16_vs_fp32"] = nrm(small["bf16"] - small["fp32"]) / nrm(small["fp32"])
+        ctx.step(GATE2048_K)
+        for kk in range(1, GATE2048_K + 1):
+            xs_, _ = ctx.solve(kk, list(GATE_LAMS))
+            for li in range(len(GATE_LAMS)):
+                gate_gpu[("2048", name, kk, li)] = xs_[li, 0].astype(np.float64)
+    p1k = P.deblur_moffat(side=GATE_SIDE, k=GATE_K, m_s=GATE_MS)
+    keep1k = []
+    op1k = bd.operator_from_problem(p1k, keep1k)
+    for name, stg in (("bf16", "bf16"), ("fp32", "f32"), ("fp16", "f16")):
+        cfg = bd.default_config(k_max=GATE_K, m_s=GATE_MS, zeta=8, seed=p1k.sketch_seed, storage=stg,
+                                stream=stream.cuda_stream)
+        ctx = bd.Context(op1k, p1k.b, cfg, keep1k)
+        ctx.step(GATE_K)
+        for kk in GATE_KS:
+            xs_, _ = ctx.solve(kk, list(GATE_LAMS))
+            for li in range(len(GATE_LAMS)):
+                gate_gpu[(str(GATE_SIDE), name, kk, li)] = xs_[li, 0].astype(np.float64)
+        ctx.close()
 
     # --- end to end: pinned host b in, host x out, through the C ABI ------
     b_host = torch.from_numpy(p.b.copy()).pin_memory()
@@ -301,17 +355,6 @@ def run_ours(args, rank, world, torch, dist):
     t_e2e_ms = max_over_ranks(torch, dist, 1e3 * (time.perf_counter() - t0), f"cuda:{dev}")
     ctx16.profile_read()
 
-    # --- CPU baseline (rank 0 only, bounded oracle sample) -----------------
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        o = run_oracle_sample(1)
-        step_s = o["step_s"][0]
-        cpu = {"value": 1.0 / step_s, "unit": "iters/s", "cores": 1, "kind": "oracle",
-               "sample": ORACLE_SAMPLE.format(s=1) + f"; init {o['init_s']:.1f} s, step 1 {step_s:.1f} s"}
-        acc["k1_relerr_vs_fp64_oracle"] = {
-            "bf16": nrm(small["bf16_k1"] - o["x"][1]) / nrm(o["x"][1]),
-            "fp32": nrm(small["fp32_k1"] - o["x"][1]) / nrm(o["x"][1])}
-
     # --- roofline of the dominant kernel ------------------------------------
     ms, cnt, byts = prof16
     names = ["operator", "pivot_solve", "update_or_Vh", "normalize", "init", "solve_qr", "solve_x",
@@ -319,18 +362,26 @@ def run_ours(args, rank, world, torch, dist):
     busy = sum(ms)
     kern = {names[i]: {"ms_total": ms[i], "launches": int(cnt[i]),
                        "share": ms[i] / max(busy, 1e-9),
-                       "GBps": (byts[i] / (ms[i] * 1e-3) / 1e9) if ms[i] > 0 and byts[i] > 0 else None}
+                       "GBps_incl_overhead": (byts[i] / (ms[i] * 1e-3) / 1e9) if ms[i] > 0 and byts[i] > 0 else None}
             for i in range(len(names)) if cnt[i] > 0}
     peak, peak_kind = _peaks()
-    upd = kern["update_or_Vh"]
+    # the method's bytes of one update launch: step j reads V_j, (j+1) n s_V
+    # bytes, averaged over j = 0..k-1 of the profiled solves
+    alg_upd = 2.0 * n * (k + 1) / 2.0
+    over_upd = 8.0 * n + n / 8.0 + 8.0 * n
+    t_upd = ms[2] / max(cnt[2], 1) * 1e-3
+    ach = alg_upd / t_upd / 1e9 if ms[2] > 0 else None
     roof = {"kernel": "k_update_f<bf16,1> (w -= V_j h, the max-|w| pivot, S v_j of the newest column)",
-            "bound": "hbm",
-            "achieved": upd["GBps"], "peak": peak, "unit": "GB/s",
-            "frac": (upd["GBps"] / peak) if upd["GBps"] else None, "traffic": TRAFFIC.get("update"),
-            "peak_source": f"{peak_kind} hbm_gbs", "bytes_per_launch": byts[2] / max(cnt[2], 1),
-            "algorithmic_bytes": "per launch at step j: (j+1)*n*2 (read V_j, BF16) + 8n (read and write w, "
-                                 "FP32) + n/8 (pivot bitmap) + 8n (sketch table: the kernel also sketches the "
-                                 "newest column v_j); averaged over j = 1..200"}
+            "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": (ach / peak) if ach else None, "traffic": TRAFFIC.get("update"),
+            "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": alg_upd,
+            "algorithmic_bytes": "per launch at step j: (j+1)*n*2, the read of V_j (BF16), averaged over "
+                                 "j = 0..199",
+            "overhead_bytes_per_launch": over_upd,
+            "overhead_bytes": "8n (read and write of the FP32 work vector w) + n/8 (pivot bitmap) + 8n (sketch "
+                              "table: the kernel also sketches the newest column v_j); implementation choices, "
+                              "not counted in frac",
+            "us_per_launch": t_upd * 1e6}
     # the convolution runs on the tensor cores (BF16 operands, FP32
     # accumulation); useful work is the convolution itself, 2 x 31 x 31 flops
     # per pixel, against the dense BF16 tensor peak
@@ -340,6 +391,7 @@ def run_ours(args, rank, world, torch, dist):
     roof_conv = {"kernel": "k_conv2d_tc<32> (w = P * v_j, tcgen05)", "bound": "tensor", "achieved": conv_tf,
                  "peak": tpeak, "unit": "TFLOP/s", "frac": (conv_tf / tpeak) if conv_tf else None,
                  "traffic": TRAFFIC.get("conv"), "peak_source": tpeak_src,
+                 "us_per_launch": ms[0] / max(cnt[0], 1) * 1e3,
                  "algorithmic_flops": "2 x 31 x 31 x n per launch (n = 2048^2); the MMAs execute 2 x 2 x 80 x 256 "
                                       "per 8 image rows x 128 columns (K and N padding, two PSF parts)"}
     dominant = max(range(len(ms)), key=lambda i: ms[i])
@@ -348,26 +400,25 @@ def run_ours(args, rank, world, torch, dist):
     launches = launches_p * args.steps // steps_p          # the profiled pass ran steps_p solves
 
     value = replica_throughput(world, args.steps, k, t_max)
+    config = static_config(args, world)
     out = {
         "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "k": k, "m_s": p.m_s, "zeta": p.zeta, "storage": "bf16",
-                   "parallelism": "replicas" if world > 1 else "single GPU",
-                   "l2": "inputs larger than L2: the BF16 basis is 1.69 GB (L2 129 MB)",
-                   "launch": "one CUDA graph per Hessenberg step (the library default); kernel times and the "
-                             "roofline from a second pass of %d solves with CUDA events around each launch "
-                             "(profile mode, eager: %.2f ms per solve)" % (steps_p, tp / steps_p),
-                   "overlap": args.overlap},
+        "config": config,
         "solves_per_s": world * args.steps / (t_max * 1e-3),
         "latency_ms": {"p50": float(np.percentile(per16, 50)), "p99": float(np.percentile(per16, 99))},
         "fp32": {"iters_per_s": steps32 * k / (t32 * 1e-3), "solves_per_s": steps32 / (t32 * 1e-3),
                  "ms_per_solve": t32 / steps32},
+        "fp16": {"iters_per_s": steps32 * k / (th * 1e-3), "solves_per_s": steps32 / (th * 1e-3),
+                 "ms_per_solve": th / steps32},
         "bf16_speedup_over_fp32": (args.steps / t16) / (steps32 / t32),
         "accuracy": acc,
         "roofline": roof if dominant in (2, 3, 6) else roof_conv,
         "roofline_other": roof_conv if dominant in (2, 3, 6) else roof,
         "kernels": kern,
+        "profiled_pass": {"solves": steps_p, "ms_per_solve": tp / steps_p,
+                          "how": "CUDA events around each launch on the library's streams, eager launches"},
         "gpu_launches": launches * world,
         "e2e": {"value": replica_throughput(world, e2e_steps, k, t_e2e_ms), "unit": "iters/s",
                 "h2d_bytes_per_step": int(4 * n),
@@ -375,16 +426,138 @@ def run_ours(args, rank, world, torch, dist):
         "clocks": {k2: clk[k2] for k2 in ("sm_mhz", "sm_max_mhz", "reasons")},
         "k_done": kd16,
     }
-    if cpu is not None:
-        out["cpu_baseline"] = cpu
     ctx16.close()
     ctx32.close()
+    ctxh.close()
     if rank == 0 and not args.no_extra:
+        out["deblur64"] = run_deblur64(torch, stream)
+        out["deblur256"] = run_deblur256(torch, stream)
         out["ct256_batch32"] = run_ct_batch(torch, stream)
         out["gaussian_sketch"] = run_gaussian(torch, stream, args.overlap)
         sv = run_serving(args, duration=5.0)
         out["serving"] = {k2: v for k2, v in sv.items() if k2 not in ("metric", "unit", "value")}
+
+    # --- accuracy gate against the FP64 oracle, and the CPU baseline --------
+    if gate_h is not None:
+        o1k, o2k = finish_child(gate_h[0]), finish_child(gate_h[1])
+        gate = accuracy_gate(gate_gpu, o1k, o2k, p1k)
+        config.update(gate)
+        acc["gate"] = gate
+        cores = os.cpu_count() or 1
+        rep = oracle_replicas(2, cores)
+        one = len(o2k["step_s"]) / sum(o2k["step_s"])
+        out["cpu_baseline"] = {
+            "value": rep["iters_per_s"], "unit": "iters/s", "cores": cores, "kind": "oracle",
+            "sample": ORACLE_SAMPLE.format(s=2, r=cores),
+            "one_thread": {"value": one, "unit": "iters/s", "cores": 1,
+                           "sample": "the same oracle alone, steps 1..%d of the 2048x2048 workload, one thread "
+                                     "(init %.1f s; step times %s s)" % (
+                                         len(o2k["step_s"]), o2k["init_s"],
+                                         ", ".join("%.1f" % t for t in o2k["step_s"]))},
+            "replica_step_s_median": rep["step_s_median"]}
     return out
+
+
+def static_config(args, world: int) -> dict:
+    """The workload description both arms print (the accuracy gate's
+    results are added to ours)."""
+    return {"workload": WORKLOAD, "n": 2048 * 2048, "k": K_ITERS, "m_s": 800, "zeta": 8, "storage": "bf16",
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "l2": "inputs larger than L2: the BF16 basis is 1.69 GB (L2 129 MB)",
+            "launch": "one CUDA graph per Hessenberg step (the library default); kernel times and the roofline "
+                      "from a second, profiled pass",
+            "overlap": args.overlap}
+
+
+def accuracy_gate(gpu: dict, o1k: dict, o2k: dict, p1k) -> dict:
+    """Relative error of the GPU's iterates (BF16, FP16 and FP32 storage)
+    against the FP64 oracle's, per k and lambda, for the config; and whether
+    each form meets its stated tolerance (FP32 1e-4, BF16 / FP16 1e-3)."""
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    g = {}
+    stated = {"fp32": 1e-4, "bf16": 1e-3, "fp16": 1e-3}
+    met = {nm: [] for nm in stated}
+    for (side, nm, kk, li), x in sorted(gpu.items()):
+        o = o1k if side == str(GATE_SIDE) else o2k
+        ref = o["x"][(kk, li)]
+        e = rel(x, ref)
+        lam = GATE_LAMS[li]
+        key = f"acc_{nm}_{side}_k{kk}" + ("" if lam == 0.0 else f"_lam{lam:g}")
+        if side == str(GATE_SIDE) or kk in (1, GATE2048_K):
+            g[key] = e
+        if e <= stated[nm]:
+            met[nm].append(f"{side}k{kk}" + ("" if lam == 0.0 else "r"))
+    # error against x_true of BF16 and FP32 at the 1024^2 case (regularised)
+    xt = p1k.x_true
+    for kk in GATE_KS:
+        eb = rel(gpu[(str(GATE_SIDE), "bf16", kk, 1)], xt)
+        ef = rel(gpu[(str(GATE_SIDE), "fp32", kk, 1)], xt)
+        g[f"acc_xtrue_bf16_minus_fp32_k{kk}_lam{GATE_LAMS[1]:g}"] = eb - ef
+    g["acc_meets_stated"] = "; ".join(f"{nm}<={stated[nm]:g}: " + (",".join(v) if v else "none")
+                                      for nm, v in met.items())
+    return g
+
+
+def _time_ctx(torch, stream, ctx, b_dev, k, lams, steps, warmup):
+    """ms per solve (reset + k steps + the solve for every lambda, x on the
+    device), CUDA events on the library's caller stream."""
+    x = torch.zeros((len(lams), 1, b_dev.shape[-1]), dtype=torch.float32, device=b_dev.device)
+    for _ in range(warmup):
+        ctx.reset(b_dev)
+        ctx.step(k)
+        ctx.solve(k, lams, out=x, wait=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ctx.reset(b_dev)
+        ctx.step(k)
+        ctx.solve(k, lams, out=x, wait=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, x
+
+
+def run_deblur64(torch, stream, steps: int = 50) -> dict:
+    """The plain method on 64 x 64 deblurring (15 x 15 Gaussian PSF, k = 50,
+    m_s = 200, lambda in {0, 1e-3}), FP64 and FP32 storage: one step = one
+    solve with both lambdas."""
+    from gen import problems as P
+    from paper_2502_02721_gb300 import binding as bd
+    p = P.make("deblur64")
+    keep = []
+    op = bd.operator_from_problem(p, keep)
+    b_dev = torch.from_numpy(p.b.copy()).cuda()
+    out = {"workload": "deblur 64x64, Gaussian 15x15 sigma 2, k=50, m_s=200, lambda {0, 1e-3}; latency-bound "
+                       "(V 1.6 MB in FP64)"}
+    for stg in ("f64", "f32"):
+        cfg = bd.default_config(k_max=p.k, m_s=p.m_s, zeta=p.zeta, seed=p.sketch_seed, storage=stg,
+                                stream=stream.cuda_stream)
+        ctx = bd.Context(op, b_dev, cfg, keep)
+        ms, _ = _time_ctx(torch, stream, ctx, b_dev, p.k, list(p.lambdas), steps, 3)
+        out[stg] = {"ms_per_solve": ms, "solves_per_s": 1e3 / ms, "iters_per_s": p.k * 1e3 / ms}
+        ctx.close()
+    return out
+
+
+def run_deblur256(torch, stream, steps: int = 10) -> dict:
+    """256 x 256 deblurring with the separable 31-tap Gaussian then the
+    9-px motion blur, k = 100, m_s = 400, the 8-lambda sweep, FP32 storage:
+    one step = one solve with all 8 lambdas."""
+    from gen import problems as P
+    from paper_2502_02721_gb300 import binding as bd
+    p = P.make("deblur256")
+    keep = []
+    op = bd.operator_from_problem(p, keep)
+    b_dev = torch.from_numpy(p.b.copy()).cuda()
+    cfg = bd.default_config(k_max=p.k, m_s=p.m_s, zeta=p.zeta, seed=p.sketch_seed, storage="f32",
+                            stream=stream.cuda_stream)
+    ctx = bd.Context(op, b_dev, cfg, keep)
+    ms, _ = _time_ctx(torch, stream, ctx, b_dev, p.k, list(p.lambdas), steps, 2)
+    ctx.close()
+    return {"workload": "deblur 256x256, separable 31-tap Gaussian sigma 3 + 9-px motion, k=100, m_s=400, "
+                        "8 lambdas 1e-4..1e-1; FP32 basis (V 26.5 MB, L2-resident)",
+            "f32": {"ms_per_solve": ms, "solves_per_s": 1e3 / ms, "iters_per_s": p.k * 1e3 / ms}}
 
 
 # ---------------------------------------------------------------------------
@@ -412,7 +585,7 @@ def run_reference(args):
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "n": p.n, "k": K_ITERS, "m_s": p.m_s},
+            "data": "synthetic", "config": static_config(args, 1),
             "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 

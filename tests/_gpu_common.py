@@ -15,10 +15,12 @@ and the GPU must stay within max(floor, 10 x that response).
 
 The stated tolerance.  1e-4 (FP32) and 1e-3 (BF16, FP16) relative to the
 FP64 oracle are asserted wherever they are reachable in that storage type:
-where the oracle's own storage-rounded run, plus the parity bound, stays
-within them.  Where the storage rounding alone exceeds them (BF16 from k = 1
-on, FP16 beyond the first steps, because the iterates' sensitivity grows
-with kappa(Z_k)), the record says so; the parity check still holds there.
+where the oracle's storage-rounded run stays within them even with the
+least rounding any implementation of the products must make (one rounding
+to the accumulation type per entry: the response to delta = u_acc).  Where
+that is exceeded (BF16 from k = 1 on, FP16 beyond the first steps, FP32
+where kappa(Z_k) amplifies its rounding past 1e-4), the record says so; the
+parity check still holds there.
 
 Every comparison is appended to RECORD (test, storage, k, lambda, the
 errors and bounds); conftest.py prints the worst cases at the end of the
@@ -167,6 +169,9 @@ def verify_scmrh(ctx, p, storage, ks, lambdas, r=0, k=None, conv_fma=0, zform="h
         assert j_gpu >= j_or - 3, (j_gpu, j_or)
     rep = oracle_run(p, r=r, k=kk, forced=gpiv, storage=storage, apply=A)
     rep_p = oracle_run(p, r=r, k=kk, forced=gpiv, storage=storage, apply=perturbed(A, delta, 12345))
+    # the least rounding of the products: one rounding per entry
+    delta_min = U_ACC[storage] + (PSF_SPLIT if uses_tensor_cores(p, storage, conv_fma) else 0.0)
+    rep_m = oracle_run(p, r=r, k=kk, forced=gpiv, storage=storage, apply=perturbed(A, delta_min, 54321))
     out = []
     for k1 in ks:
         if k1 > kd:
@@ -181,11 +186,12 @@ def verify_scmrh(ctx, p, storage, ks, lambdas, r=0, k=None, conv_fma=0, zform="h
             x64 = scmrh.solve(ref64, k1, lam, "hessenberg", penalty)
             e64 = rel(xg, x64)
             d_s = rel(xr, x64)
+            r_min = rel(scmrh.solve(rep_m, k1, lam, zform, penalty), xr)
             stated = STATED[storage]
-            reach = d_s + tol_par <= stated
+            reach = d_s + r_min <= stated
             rec = {"test": name, "storage": storage, "k": k1, "lam": lam, "e_par": e_par, "tol_par": tol_par,
-                   "e64": e64, "stated": stated, "storage_only": d_s, "stated_reachable": bool(reach),
-                   "pivots_agree": j_gpu}
+                   "e64": e64, "stated": stated, "storage_only": d_s, "least_rounding": r_min,
+                   "stated_reachable": bool(reach), "pivots_agree": j_gpu}
             RECORD.append(rec)
             out.append(rec)
             assert e_par <= tol_par, rec
