@@ -40,11 +40,14 @@ WORKLOAD = ("deblur 2048x2048, Moffat 31x31 PSF (beta 2.5, alpha 4), ellipse pha
 K_ITERS = 200
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# kernels named in the roofline, averaged over the steps of this workload:
-# taken by ncu on one launch each of the 1024 x 1024 case (--small) and scaled
-# to 2048 x 2048 by the units processed; None until taken for the current
-# kernels (cleared whenever a kernel changes)
-TRAFFIC: dict = {"update": None, "conv": None}
+# kernels named in the roofline, averaged over the steps of this workload,
+# from ncu on single launches of the 1024 x 1024 case (--small bf16) scaled
+# to 2048 x 2048 by the units processed: the update at steps j = 19 and 49
+# (54.71 and 120.32 MB) fits T(j) = 1.043 (j+1) 2n + 10.47 n bytes, which at
+# n = 2048^2 averages 923.1 MB over j = 0..199; the convolution read 2.23 MB
+# for 2n = 2.10 MB of v_j, 8.93 MB at 2048^2.  Cleared whenever a kernel
+# changes.
+TRAFFIC: dict = {"update": 923.1e6, "conv": 8.93e6}
 
 # the accuracy gate: FP64 oracle iterates of the 1024 x 1024 Moffat case
 # (k = 64, m_s = 256) and of the first steps of the 2048 x 2048 workload,
@@ -647,7 +650,8 @@ def run_gaussian(torch, stream, overlap: int, steps: int = 3) -> dict:
     """The headline deblurring workload (2048^2, k = 200, m_s = 800, BF16
     basis) with the Gaussian embedding in place of the sparse sign sketch:
     S (800 x 2048^2, BF16, 6.7 GB) is drawn once when the context is created,
-    the steps do no sketching, and each solve forms S V_{k+1} by one GEMM."""
+    the steps do no sketching, and each solve forms [S V_{k+1} | S b] by one
+    tensor-core contraction (k_gauss_mma)."""
     from gen import problems as P
     from paper_2502_02721_gb300 import binding as bd
     p = P.make("deblur2048")
@@ -690,10 +694,12 @@ def run_gaussian(torch, stream, overlap: int, steps: int = 3) -> dict:
         if sketch == "gaussian" and pc[9] > 0:
             gbs = pb[9] / (pm[9] * 1e-3) / 1e9
             peak, kind = _peaks()
-            r["gemm"] = {"kernel": "cuBLAS GemmEx S V_{k+1} (BF16 in, FP32 accumulate)", "bound": "hbm",
+            fl = 2.0 * p.m_s * p.n * (p.k + 1) * pc[9] / (pm[9] * 1e-3) / 1e12
+            r["gemm"] = {"kernel": "k_gauss_mma<bf16> + k_gauss_reduce ([S V_{k+1} | S b], tcgen05, FP32 sums per "
+                                   "slice, FP64 across slices)", "bound": "hbm",
                          "ms": pm[9] / pc[9], "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                         "peak_source": f"{kind} hbm_gbs",
-                         "algorithmic_bytes": "m_s*n*2 (S) + n*(k+1)*2 (V_{k+1}) + m_s*(k+1)*4 (out) per solve"}
+                         "peak_source": f"{kind} hbm_gbs", "tensor_tflops_useful": fl,
+                         "algorithmic_bytes": "m_s*n*2 (S) + n*(k+1)*2 (V_{k+1}) per solve"}
         out[sketch] = r
         ctx.close()
     a, g = xs["sparse_sign"], xs["gaussian"]

@@ -104,13 +104,14 @@ enum ipf_method { IPF_METHOD_SCMRH = 0, IPF_METHOD_SLSLU = 1 };
  *              of the generator started at config.seed; u = ((out >> 11) + 1)
  *              2^-53; z = sqrt(-2 ln u1) cos(2 pi u2); S = z / sqrt(m_s)),
  *              rounded to the storage type and kept in device memory
- *              (m_s x n elements, see ipf_sketch_gaussian).  No per-step
- *              sketch: S V_{k+1} is one GEMM (cuBLAS, FP32 accumulation, FP64
- *              for F64 storage) at solve time; c = S b at initialisation sums
- *              runs of 32 products in FP32 (FP64 for F64 storage) and adds the
- *              runs in FP64, in a fixed order.  SCMRH with
- *              nrhs == 1 only (else IPF_ERR_UNSUPPORTED, also when cuBLAS
- *              cannot be loaded); the Z form is HESSENBERG; ipf_export's
+ *              (m_s x n elements, row-major, see ipf_sketch_gaussian).  No
+ *              per-step sketch: at solve time one contraction forms
+ *              [S V_{k+1} | S b] (the library's own kernels: tensor cores for
+ *              BF16 / FP16 storage, with b entering as three exact parts of
+ *              the storage type, and FP32 accumulation in slices of n added
+ *              in FP64 in a fixed order; CUDA cores for FP32 / FP64
+ *              storage).  SCMRH with nrhs == 1 only (else
+ *              IPF_ERR_UNSUPPORTED); the Z form is HESSENBERG; ipf_export's
  *              SV, SZ and c are those of the sparse-sign path (zero here). */
 enum ipf_sketch { IPF_SKETCH_SPARSE_SIGN = 0, IPF_SKETCH_GAUSSIAN = 1 };
 
@@ -254,7 +255,7 @@ ipf_status ipf_solve(ipf_ctx* ctx, int k, const double* lambdas, int nl,
  * kind (0 operator, 1 pivot-block solve, 2 update+argmax or V_j h,
  * 3 normalise (+ sketch unless deferred), 4 initialisation, 5 projected-solve
  * QR, 6 per-lambda solve + x = V_k y, 7 operator at the pivot rows,
- * 8 u = A v_j - V_j h with argmax, 9 the Gaussian sketch's S V_{k+1} GEMM,
+ * 8 u = A v_j - V_j h with argmax, 9 the Gaussian sketch's [S V_{k+1} | S b],
  * 10 sampled pivot choice, 11 deferred sketch S v_j) the summed
  * milliseconds, launch counts and the summed algorithmic bytes of the
  * launches (0 where not defined), since the previous read.  With
@@ -334,14 +335,14 @@ ipf_status ipf_sketch_apply(const float* x_dev, long long n, int m_s, int zeta,
 
 /* Writes the Gaussian sketch S (m_s x n) of config.sketch = GAUSSIAN
  * (Sec. 2; Box-Muller on the SplitMix64 counter hash as described at
- * enum ipf_sketch) to S_dev, column-major (entry (r, i) at r + i*m_s), each
- * entry the FP64 value z / sqrt(m_s) rounded to nearest-even in `storage`
- * (BF16 through FP32).  BF16 and F16 entries are evaluated in FP32 with an
- * error bound and recomputed in FP64 where the bound does not fix the
- * rounded value, so all storage types store the FP64 definition's rounding.
- * S_dev: device, m_s * n elements of the storage type, caller-owned.
- * Runs on `stream`, no allocation.  Errors: IPF_ERR_ARG (null S_dev,
- * n < 1, m_s < 1, unknown storage), IPF_ERR_CUDA (launch failure).        */
+ * enum ipf_sketch) to S_dev, row-major (entry (r, i) at r*n + i, the entry's
+ * counter), each entry the FP64 value z / sqrt(m_s) rounded to nearest-even
+ * in `storage` (BF16 through FP32).  BF16 and F16 entries are evaluated in
+ * FP32 with an error bound and recomputed in FP64 where the bound does not
+ * fix the rounded value, so all storage types store the FP64 definition's
+ * rounding.  S_dev: device, m_s * n elements of the storage type,
+ * caller-owned.  Runs on `stream`, no allocation.  Errors: IPF_ERR_ARG (null
+ * S_dev, n < 1, m_s < 1, unknown storage), IPF_ERR_CUDA (launch failure).  */
 ipf_status ipf_sketch_gaussian(int storage, unsigned long long seed, long long n, int m_s, void* S_dev,
                                void* stream);
 

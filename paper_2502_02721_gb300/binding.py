@@ -483,7 +483,7 @@ def sketch_apply(x, m_s: int, zeta: int, seed: int, y, stream=None):
 
 
 def sketch_gaussian(storage: str, seed: int, n: int, m_s: int, S, stream=None):
-    """ipf_sketch_gaussian: the Gaussian sketch (m_s x n, column-major) into
+    """ipf_sketch_gaussian: the Gaussian sketch (m_s x n, row-major) into
     the device tensor S of the storage type (m_s * n elements)."""
     _check_size(S, int(m_s) * int(n), "S")
     _check_device(S, "S", {"f64": 8, "f32": 4, "bf16": 2, "f16": 2}[storage])

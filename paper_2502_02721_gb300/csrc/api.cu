@@ -276,12 +276,13 @@ struct ipf_ctx {
     // generalized process (SLSLU): g/bf/sp/op are the D side (m-space, A),
     // these the L side (n-space, A^T)
     bool gh = false;
-    // Gaussian sketch: S (m_s x n, storage type), S V_{k+1} and c = S b, cuBLAS handle
+    // Gaussian sketch: S (m_s x lds, storage type, row-major), S V_{k+1},
+    // c = S b and the contraction's workspace (b rows, partial tiles)
     bool gauss = false;
     void* gS = nullptr;
     void* gSV = nullptr;
     double* gC = nullptr;
-    void* blas = nullptr;
+    void* gWs = nullptr;
     OpDev opT;
     Geom g2;
     Bufs bf2;
@@ -544,8 +545,7 @@ cudaError_t init_solve(ipf_ctx* c, const float* bdev) {
         gi.sketch_defer = 0;                       // v_1 (and S b) sketched here
         return launch_normalize(c->storage, gi, c->bf, c->sp, true, c->num_sms, c->s);
     });
-    if (e == cudaSuccess && c->gauss)
-        e = launch_gauss_rhs(c->storage, c->gS, bdev, g.n, g.m_s, c->gC, c->gC + g.m_s, c->s);
+    if (e == cudaSuccess && c->gauss) e = launch_gauss_bparts(c->storage, bdev, g.n, c->gWs, c->s);
     if (e != cudaSuccess || !c->gh) return e;
     // l_1 = A^T d_1 / (A^T d_1)(g_1): the same vector as A^T r_0 / alpha, and
     // its pivot value is W(1,1)
@@ -602,7 +602,8 @@ size_t ipf_footprint(const ipf_operator* op, const ipf_config* cfg) {
     size_t bytes = basis(gh ? op_m(op) : n) + (gh ? basis(n) : 0);
     if (gh) bytes += 2 * (size_t)B * op_m(op) * 4;
     if (cfg->sketch == IPF_SKETCH_GAUSSIAN)
-        bytes += (size_t)cfg->m_s * n * sb + (size_t)cfg->m_s * K1 * 8 + 8 * ((size_t)cfg->m_s + kGaussRhsPart(cfg->m_s));
+        bytes += (size_t)cfg->m_s * gauss_lds(n) * sb + (size_t)cfg->m_s * K1 * 8 + 8 * (size_t)cfg->m_s +
+                 gauss_workspace_bytes(cfg->storage, cfg->m_s, n, cfg->k_max, device_sms()) + 3 * 256;
     Geom g; g.n = n; g.B = B; g.N = n * B; g.ldv = (long long)ldv; g.k_max = cfg->k_max; g.m_s = cfg->m_s; g.F = 0;
     bytes += solve_ws_for(g) + 2 * (size_t)B * n * 4 + 256 + ldv * 4 + B * K1 * 4;
     const size_t opb = op->kind == IPF_OP_CSR ? (size_t)(op->rows + 1) * 8 + (size_t)op->nnz * 8
@@ -769,16 +770,14 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
                       (((uintptr_t)bf.V | (uintptr_t)bf.sktab) & 15u) == 0 && (g.ldv & 7) == 0;
     g.sketch_defer = c->defer_sketch ? 1 : 0;
     if (gauss) {
-        c->blas = gauss_blas_create();
-        if (!c->blas) {
-            ipf_destroy(c);
-            return IPF_ERR_UNSUPPORTED;                // cuBLAS not available
-        }
         const size_t sb = storage_bytes(cfg.storage);
-        CK("alloc Gaussian S", c->al.get(&c->gS, (size_t)cfg.m_s * n * sb));
+        const size_t wsb = gauss_workspace_bytes(cfg.storage, cfg.m_s, n, cfg.k_max, c->num_sms);
+        CK("alloc Gaussian S", c->al.get(&c->gS, (size_t)cfg.m_s * gauss_lds(n) * sb));
         CK("alloc S V", c->al.get(&c->gSV, (size_t)cfg.m_s * (cfg.k_max + 1) * (cfg.storage == IPF_STORE_F64 ? 8 : 4)));
-        CK("alloc S b", c->al.get((void**)&c->gC, sizeof(double) * (cfg.m_s + kGaussRhsPart(cfg.m_s))));
-        CK("Gaussian S", launch_gauss_fill(cfg.storage, c->gS, n, cfg.m_s, cfg.seed, c->num_sms, c->s));
+        CK("alloc S b", c->al.get((void**)&c->gC, sizeof(double) * cfg.m_s));
+        CK("alloc Gaussian workspace", c->al.get(&c->gWs, wsb));
+        CK("memset Gaussian workspace", cudaMemsetAsync(c->gWs, 0, wsb, c->s));
+        CK("Gaussian S", launch_gauss_fill(cfg.storage, c->gS, n, cfg.m_s, gauss_lds(n), cfg.seed, c->num_sms, c->s));
     }
     c->solve_ws_bytes = solve_ws_for(g);
     CK("alloc solve", c->al.get(&c->solve_ws, c->solve_ws_bytes));
@@ -951,14 +950,14 @@ static ipf_status solve_impl(ipf_ctx* c, int k, const double* lambdas, int nl, f
         bx.st = c->bf.st;
     }
     if (c->gauss && !qmr) {
-        // S V_{k+1} by one GEMM with the stored Gaussian S
+        // [S V_{k+1} | S b] by one contraction with the stored Gaussian S
         const double sb = storage_bytes(c->storage);
-        const double gb = (double)g.m_s * g.n * sb + (double)g.n * (k + 1) * sb +
-                          (double)g.m_s * (k + 1) * (c->storage == IPF_STORE_F64 ? 8.0 : 4.0);
+        const double gb = (double)g.m_s * g.n * sb + (double)g.n * (k + 1) * sb;
         e = timed(c, 9, gb, [&] {
-            return launch_gauss_sv(c->blas, c->storage, c->gS, g.m_s, g.n, c->bf.V, g.ldv, k + 1, c->gSV, c->s);
+            return launch_gauss_sv(c->storage, c->gS, g.m_s, g.n, c->bf.V, g.ldv, g.k_max + 1, k + 1, c->gWs, c->gSV,
+                                   c->gC, &c->bf.st->status[0], c->num_sms, c->s);
         });
-        if (e != cudaSuccess) return cuda_fail(c, "Gaussian sketch GEMM", e);
+        if (e != cudaSuccess) return cuda_fail(c, "Gaussian sketch contraction", e);
         bz.svd = c->gSV;
         bz.svd_f64 = c->storage == IPF_STORE_F64 ? 1 : 0;
         bz.cvec = c->gC;
@@ -1171,7 +1170,6 @@ ipf_status ipf_export_basis_l(ipf_ctx* c, int r, int j, float* l_out) {
 void ipf_destroy(ipf_ctx* c) {
     if (!c) return;
     if (c->s) cudaStreamSynchronize(c->s);
-    if (c->blas) gauss_blas_destroy(c->blas);
     for (auto& m : c->marks) { cudaEventDestroy(m.a); cudaEventDestroy(m.b); }
     for (auto ev : c->spare) cudaEventDestroy(ev);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -1273,7 +1271,7 @@ ipf_status ipf_sketch_gaussian(int storage, unsigned long long seed, long long n
     if (!S_dev || n < 1 || m_s < 1) return IPF_ERR_ARG;
     if (storage != IPF_STORE_F64 && storage != IPF_STORE_F32 && storage != IPF_STORE_BF16 && storage != IPF_STORE_F16)
         return IPF_ERR_ARG;
-    const cudaError_t e = launch_gauss_fill(storage, S_dev, n, m_s, seed, device_sms(), (cudaStream_t)stream);
+    const cudaError_t e = launch_gauss_fill(storage, S_dev, n, m_s, n, seed, device_sms(), (cudaStream_t)stream);
     return e == cudaSuccess ? IPF_OK : IPF_ERR_CUDA;
 }
 

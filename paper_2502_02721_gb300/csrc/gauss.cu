@@ -4,19 +4,24 @@
 // entry (r, i) takes outputs 2c and 2c+1, c = r*n + i, of the generator
 // started at the seed; u = ((out >> 11) + 1) * 2^-53 in (0, 1];
 // z = sqrt(-2 ln u1) cos(2 pi u2); S[r, i] = z / sqrt(m_s), rounded to the
-// storage type of the basis.  S is kept column-major (element (r, i) at
-// r + i*m_s), so S V_{k+1} is one dense GEMM with the basis (leading
-// dimension ldv), done at solve time by cuBLAS; c = S b is a reduction in
-// a fixed order (FP32 runs of products added into FP64 sums).  cuBLAS is
-// loaded on first use (dlopen), so the library does not depend on it unless
-// the Gaussian sketch is asked for.
-#include <cublas_v2.h>
-#include <dlfcn.h>
-
-#include <mutex>
+// storage type of the basis.  S is kept row-major (entry (r, i) at
+// r*lds + i), so both S and the basis V (column j at j*ldv) are K-major
+// operands of the one contraction the method needs at solve time:
+//
+//     [S V_{k+1} | S b] = S [V_{k+1} | b]      (m_s x (k+2), K = n).
+//
+// For BF16 / FP16 storage it runs on the tensor cores (k_gauss_mma, tcgen05
+// with TMEM accumulators, operands staged by TMA): b enters as three extra
+// B rows b0 + b1 + b2 = b (each the storage-type rounding of what is left,
+// so the split is exact for FP32 b), so c = S b costs no pass of its own.
+// The n-long contraction is split into slices; each CTA sums one slice in
+// FP32 in TMEM and writes its partial tile, and k_gauss_reduce adds the
+// slices in FP64 in a fixed order (so the result does not depend on
+// scheduling).  FP32 / FP64 storage use a CUDA-core kernel of the same
+// structure (k_gauss_simt; FP32 / FP64 accumulation).
 #include <type_traits>
 
-#include "ipf_internal.cuh"
+#include "tc_common.cuh"
 
 namespace ipf {
 
@@ -84,20 +89,20 @@ __device__ __forceinline__ bool gauss_fast(unsigned long long o1, unsigned long 
     return true;
 }
 
-// flat element t of S (column-major, t = r + i*m) walks with a carried
-// (r, i) instead of a 64-bit division per element; the counter is c = r*n + i
+// entry c = r*n + i (the counter) goes to S[r*lds + i]; the walk carries
+// (r, i) instead of a 64-bit division per entry
 template <class T>
-__global__ void __launch_bounds__(256) k_gauss_fill(T* __restrict__ S, long long n, int m, unsigned long long seed,
-                                                    double sqrt_m, float inv_sqrt_m) {
+__global__ void __launch_bounds__(256) k_gauss_fill(T* __restrict__ S, long long n, int m, long long lds,
+                                                    unsigned long long seed, double sqrt_m, float inv_sqrt_m) {
     const long long total = n * (long long)m;
     const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long sr = stride % m, si = stride / m;
-    long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    long long i = t / m, r = t - i * m;
-    for (; t < total; t += stride) {
-        const unsigned long long c = (unsigned long long)(r * n + i);
-        const unsigned long long o1 = sm64_mix(seed + kGamma * (2ull * c + 1ull));
-        const unsigned long long o2 = sm64_mix(seed + kGamma * (2ull * c + 2ull));
+    const long long si = stride % n, sr = stride / n;
+    long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long r = c / n, i = c - r * n;
+    for (; c < total; c += stride) {
+        const unsigned long long o1 = sm64_mix(seed + kGamma * (2ull * (unsigned long long)c + 1ull));
+        const unsigned long long o2 = sm64_mix(seed + kGamma * (2ull * (unsigned long long)c + 2ull));
+        const long long t = r * lds + i;
         if constexpr (sizeof(T) == 2) {
             unsigned short bits;
             if (!gauss_fast<T>(o1, o2, inv_sqrt_m, bits)) {
@@ -109,188 +114,377 @@ __global__ void __launch_bounds__(256) k_gauss_fill(T* __restrict__ S, long long
         } else {
             S[t] = (T)gauss_f64(o1, o2, sqrt_m);
         }
-        r += sr;
         i += si;
-        if (r >= m) {
-            r -= m;
-            i += 1;
+        r += sr;
+        if (i >= n) {
+            i -= n;
+            r += 1;
         }
     }
 }
 
-// c = S b with a fixed summation order, in two passes.  Pass 1: CTA q takes
-// the columns [q*n/Q, (q+1)*n/Q); a column of S is cut into vectors of V
-// consecutive rows (16 bytes when the column is 16-byte aligned, else single
-// rows), thread t owns vector t % mv of every column i = i0 + t / mv (mod
-// cpi), so each load is one contiguous piece of a column.  Products are
-// summed in FP32 over runs of kRun of the thread's columns (FP64 for F64
-// storage: every product) and each run sum is added to an FP64 sum; the
-// thread's sums go to part[(q * cpi + phase) * m + row].  Pass 2 adds the
-// Q * cpi partial sums of each row in order.
-constexpr int kRun = 32;
-
-template <class T> struct RhsAcc { using type = float; };
-template <> struct RhsAcc<double> { using type = double; };
-
-template <class T, int V>
-__global__ void __launch_bounds__(256) k_gauss_rhs_part(const T* __restrict__ S, const float* __restrict__ b,
-                                                        long long n, int m, int mv, int cpi,
-                                                        double* __restrict__ part) {
-    using A = typename RhsAcc<T>::type;
-    const int q = blockIdx.x;
-    const long long i0 = n * q / kGaussRhsSlices, i1 = n * (q + 1) / kGaussRhsSlices;
-    const int phase = mv <= (int)blockDim.x ? threadIdx.x / mv : 0;
-    if (phase >= cpi) return;
-    const int vr0 = mv <= (int)blockDim.x ? threadIdx.x % mv : threadIdx.x;
-    const int vstep = mv <= (int)blockDim.x ? mv : blockDim.x;
-    double* out = part + ((size_t)q * cpi + phase) * m;
-    for (int vr = vr0; vr < mv; vr += vstep) {
-        double tot[V];
-#pragma unroll
-        for (int e = 0; e < V; ++e) tot[e] = 0.0;
-        long long i = i0 + phase;
-        while (i < i1) {
-            A run[V];
-#pragma unroll
-            for (int e = 0; e < V; ++e) run[e] = A(0);
-#pragma unroll 4
-            for (int c = 0; c < kRun; ++c) {
-                if (i >= i1) break;
-                const T* col = S + i * (long long)m + (long long)vr * V;
-                const A bi = (A)__ldg(b + i);
-                if constexpr (V > 1) {
-                    union { uint4 u; T t[V]; } ld;
-                    ld.u = __ldg(reinterpret_cast<const uint4*>(col));
-#pragma unroll
-                    for (int e = 0; e < V; ++e) run[e] = fma((A)to_acc(ld.t[e]), bi, run[e]);
-                } else {
-                    run[0] = fma((A)to_acc(col[0]), bi, run[0]);
-                }
-                i += cpi;
-            }
-#pragma unroll
-            for (int e = 0; e < V; ++e) tot[e] += (double)run[e];
-        }
-#pragma unroll
-        for (int e = 0; e < V; ++e) out[vr * V + e] = tot[e];
-    }
-}
-
-__global__ void k_gauss_rhs_sum(const double* __restrict__ part, int nparts, int m, double* __restrict__ c) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= m) return;
-    double t = 0.0;
-    for (int q = 0; q < nparts; ++q) t += part[(size_t)q * m + r];
-    c[r] = t;
-}
-
+// b (FP32) as the extra B rows: for 16-bit storage three parts, part p the
+// storage-type rounding of b - (parts before it), whose sum is b exactly for
+// normal values (8 + 8 + 8 significant bits for BF16, 11 x 3 for FP16); for
+// FP32 / FP64 storage b itself.  parts: [8][ldb], rows 3..7 stay zero.
 template <class T>
-cudaError_t rhs_typed(const T* S, const float* b, long long n, int m, double* c, double* part, cudaStream_t s) {
-    constexpr int V = 16 / (int)sizeof(T);
-    const bool vec = ((size_t)m * sizeof(T)) % 16 == 0 && ((uintptr_t)S & 15) == 0;
-    const int mv = vec ? m / V : m;
-    const int cpi = mv <= 256 ? 256 / mv : 1;
-    if (vec) k_gauss_rhs_part<T, V><<<kGaussRhsSlices, 256, 0, s>>>(S, b, n, m, mv, cpi, part);
-    else k_gauss_rhs_part<T, 1><<<kGaussRhsSlices, 256, 0, s>>>(S, b, n, m, mv, cpi, part);
-    k_gauss_rhs_sum<<<(m + 255) / 256, 256, 0, s>>>(part, kGaussRhsSlices * cpi, m, c);
-    return cudaGetLastError();
+__global__ void k_gauss_bparts(const float* __restrict__ b, long long n, long long ldb, T* __restrict__ parts) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float v = b[i];
+        if constexpr (sizeof(T) == 2) {
+            const T p0 = from_acc<T>(v);
+            const float r1 = v - to_acc(p0);
+            const T p1 = from_acc<T>(r1);
+            const float r2 = r1 - to_acc(p1);
+            parts[i] = p0;
+            parts[ldb + i] = p1;
+            parts[2 * ldb + i] = from_acc<T>(r2);
+        } else {
+            parts[i] = (T)v;
+        }
+    }
 }
 
-// cuBLAS entry points, resolved once
-struct Blas {
-    bool ok = false;
-    cublasStatus_t (*create)(cublasHandle_t*) = nullptr;
-    cublasStatus_t (*destroy)(cublasHandle_t) = nullptr;
-    cublasStatus_t (*set_stream)(cublasHandle_t, cudaStream_t) = nullptr;
-    cublasStatus_t (*gemm_ex)(cublasHandle_t, cublasOperation_t, cublasOperation_t, int, int, int, const void*,
-                              const void*, cudaDataType, int, const void*, cudaDataType, int, const void*, void*,
-                              cudaDataType, int, cublasComputeType_t, cublasGemmAlgo_t) = nullptr;
-};
+// ---------------------------------------------------------------------------
+// tensor-core contraction.  CTA (slice s, row group q) sums K = i in
+// [s*chunk, min(n, (s+1)*chunk)) for the rows 256q .. 256q + 255 of S (one or
+// two M = 128 tiles) against all N = Ntot rows of B = [V_0 .. V_{Nv-1};
+// b0, b1, b2, 0 x 5] (Nv >= k + 1, Ntot = Nv + 8, a multiple of 16).  Per
+// stage of 64 K elements (one 128-byte swizzle row): TMA brings the A tiles
+// (128 rows x 128 bytes each) and B (Ntot rows) into shared memory with the
+// 128-byte swizzle, zero-filled outside S, V and b; the MMA thread issues
+// 4 x ntile tcgen05.mma (M 128, N Ntot, K 16) into TMEM (ntile x Ntot FP32
+// columns) and commits to the stage's empty barrier.  Roles (192 threads,
+// one CTA per SM): warp 0 TMA, warp 1 TMEM owner and MMA issuer, warps 2-5
+// epilogue (warp w reads TMEM lanes 32 (w % 4) ..).  Every wait is bounded
+// (2 s); on a timeout the CTA stops issuing, drains its copies and MMAs,
+// frees TMEM, writes nothing and records IPF_ERR_TIMEOUT.
+// ---------------------------------------------------------------------------
+constexpr int kGmThreads = 192;
+constexpr int kGmBK = 64;
+constexpr int kGmStages = 3;
+constexpr int kGmATile = 128 * 128;
+constexpr int kGmBRowsMax = 256;
+constexpr int kGmStageBytes = 2 * kGmATile + kGmBRowsMax * 128;
+constexpr int kGmOffBar = kGmStages * kGmStageBytes;
+constexpr int kGmNBar = 2 * kGmStages + 1;
+constexpr int kGmOffMisc = kGmOffBar + 8 * kGmNBar;
+constexpr int kGmSmemRequest = kGmOffMisc + 16 + 1024;
+constexpr int kGmBRows = 8;          // rows of the b block: 3 parts + 5 zero rows
+static_assert(kGmSmemRequest <= 227 * 1024, "shared memory per CTA");
+static_assert(kGmStageBytes % 1024 == 0 && kGmATile % 1024 == 0, "swizzle atoms stay 1024-byte aligned");
 
-Blas& blas() {
-    static Blas b;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        const char* names[] = {"libcublas.so.13", "/usr/local/cuda/lib64/libcublas.so.13", "libcublas.so"};
-        void* h = nullptr;
-        for (const char* nm : names)
-            if ((h = dlopen(nm, RTLD_NOW | RTLD_LOCAL)) != nullptr) break;
-        if (!h) return;
-        b.create = (decltype(b.create))dlsym(h, "cublasCreate_v2");
-        b.destroy = (decltype(b.destroy))dlsym(h, "cublasDestroy_v2");
-        b.set_stream = (decltype(b.set_stream))dlsym(h, "cublasSetStream_v2");
-        b.gemm_ex = (decltype(b.gemm_ex))dlsym(h, "cublasGemmEx");
-        b.ok = b.create && b.destroy && b.set_stream && b.gemm_ex;
-    });
-    return b;
+template <bool BF16>
+__global__ void __launch_bounds__(kGmThreads, 1)
+    k_gauss_mma(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensorMap vmap,
+                const __grid_constant__ CUtensorMap bmap, long long n, int m, long long chunk, int mg, int Nv,
+                int Ntot, float* __restrict__ part, int m_pad, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm);
+    const uint32_t bar0 = sbase + kGmOffBar;
+    auto full = [&](int i) { return bar0 + 8u * i; };
+    auto empty = [&](int i) { return bar0 + 8u * (kGmStages + i); };
+    const uint32_t done = bar0 + 8u * (2 * kGmStages);
+    uint32_t* s_tmem = (uint32_t*)(sm + kGmOffMisc);
+    volatile int* s_abort = (volatile int*)(sm + kGmOffMisc + 4);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int slice = blockIdx.x / mg, q = blockIdx.x % mg;
+    const int row0 = q * 256;
+    const int ntile = min(2, (m - row0 + 127) / 128);          // >= 1: q < mg = ceil(m / 256)
+    const long long i0 = (long long)slice * chunk;
+    const long long i1 = min(n, i0 + chunk);
+    const int nkb = (int)((i1 - i0 + kGmBK - 1) / kGmBK);      // >= 1: slices = ceil(n / chunk)
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kGmStages; ++i) { mbar_init(full(i), 1); mbar_init(empty(i), 1); }
+        mbar_init(done, 1);
+        *s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         (uint32_t)__cvta_generic_to_shared(s_tmem)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *s_tmem;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            const uint32_t bytes = (uint32_t)(ntile * kGmATile + Ntot * 128);
+            int issued = 0;
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb % kGmStages;
+                if (!mbar_wait(empty(s), ((kb / kGmStages) & 1) ^ 1, s_abort, err)) break;
+                mbar_expect_tx(full(s), bytes);
+                const int x = (int)(i0 + (long long)kb * kGmBK);
+                const uint32_t st = sbase + (uint32_t)(s * kGmStageBytes);
+                for (int t = 0; t < ntile; ++t) tma_load_2d(st + t * kGmATile, &smap, x, row0 + 128 * t, full(s));
+                tma_load_2d(st + 2 * kGmATile, &vmap, x, 0, full(s));
+                tma_load_2d(st + 2 * kGmATile + Nv * 128, &bmap, x, 0, full(s));
+                issued = kb + 1;
+            }
+            // every issued copy lands before the CTA may exit
+            for (int kb = issued > kGmStages ? issued - kGmStages : 0; kb < issued; ++kb)
+                mbar_wait(full(kb % kGmStages), (kb / kGmStages) & 1, s_abort, err, false);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_f16kind(128, Ntot, BF16);
+            for (int kb = 0; kb < nkb; ++kb) {
+                const int s = kb % kGmStages;
+                if (!mbar_wait(full(s), (kb / kGmStages) & 1, s_abort, err)) break;
+                tc_fence_after();
+                const uint32_t st = sbase + (uint32_t)(s * kGmStageBytes);
+                for (int t = 0; t < ntile; ++t) {
+#pragma unroll
+                    for (int kk = 0; kk < kGmBK / 16; ++kk)
+                        mma_bf16(tmem + (uint32_t)(t * Ntot), smem_desc_sw128(st + t * kGmATile + kk * 32),
+                                 smem_desc_sw128(st + 2 * kGmATile + kk * 32), idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                }
+                mma_commit(empty(s));
+            }
+            // arrives once every MMA issued above has completed
+            mma_commit(done);
+        }
+    } else {
+        // ---- epilogue: this slice's partial tile, FP32, to part[slice][row][col] ----
+        const bool ok = mbar_wait(done, 0, s_abort, err, false);
+        tc_fence_after();
+        const int qw = warp & 3;
+        const bool write = ok && !*s_abort;
+        for (int t = 0; t < ntile; ++t) {
+            const int r = row0 + 128 * t + 32 * qw + lane;
+            float* dst = part + ((size_t)slice * m_pad + r) * Ntot;
+            for (int c0 = 0; c0 < Ntot; c0 += 16) {
+                uint32_t v[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)(t * Ntot + c0), v);
+                tmem_wait_ld();
+                if (write && r < m) {
+#pragma unroll
+                    for (int e = 0; e < 16; e += 4)
+                        *reinterpret_cast<float4*>(dst + c0 + e) =
+                            make_float4(__uint_as_float(v[e]), __uint_as_float(v[e + 1]), __uint_as_float(v[e + 2]),
+                                        __uint_as_float(v[e + 3]));
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+}
+
+// CUDA-core contraction for FP32 / FP64 storage: CTA (slice, 16 rows, 16
+// columns), the slice's K in chunks of 64 through shared memory; column
+// Nv of B is b.  A = float for FP32 storage, double for FP64.
+template <class T, class A>
+__global__ void __launch_bounds__(256) k_gauss_simt(const T* __restrict__ S, long long lds, int m, long long n,
+                                                    const T* __restrict__ V, long long ldv, int K1,
+                                                    const T* __restrict__ bcol, long long chunk,
+                                                    double* __restrict__ part, int m_pad, int Ntot) {
+    __shared__ A sS[16][65];
+    __shared__ A sV[16][65];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int slice = blockIdx.x;
+    const int r0 = blockIdx.y * 16, c0 = blockIdx.z * 16;
+    const long long i0 = (long long)slice * chunk, i1 = min(n, i0 + chunk);
+    A acc = A(0);
+    for (long long kb = i0; kb < i1; kb += 64) {
+        for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+            const int rr = e >> 6, kk = e & 63;
+            const long long i = kb + kk;
+            const int r = r0 + rr, c = c0 + rr;
+            sS[rr][kk] = (r < m && i < i1) ? (A)S[(size_t)r * lds + i] : A(0);
+            const T* col = c < K1 ? V + (size_t)c * ldv : (c == K1 ? bcol : nullptr);
+            sV[rr][kk] = (col && i < i1) ? (A)col[i] : A(0);
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < 64; ++kk) acc = fma(sS[ty][kk], sV[tx][kk], acc);
+        __syncthreads();
+    }
+    const int r = r0 + ty, c = c0 + tx;
+    if (r < m && c < Ntot) part[((size_t)slice * m_pad + r) * Ntot + c] = (double)acc;
+}
+
+// [S V | S b] = the sum of the slices' partial tiles, in FP64 and in slice
+// order.  Thread (r, j): j < K1 gives (S V)(r, j) into svd (column-major
+// m x K1, FP32 or FP64), j = K1 gives c(r) = sum over the nb b rows.
+template <class P>
+__global__ void k_gauss_reduce(const P* __restrict__ part, int nsplit, int m, int m_pad, int Ntot, int K1, int Nv,
+                               int nb, float* __restrict__ svd32, double* __restrict__ svd64,
+                               double* __restrict__ c) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int cols = K1 + 1;
+    if (t >= (long long)m * cols) return;
+    const int r = (int)(t / cols), j = (int)(t - (long long)r * cols);
+    double sum = 0.0;
+    if (j < K1) {
+        for (int s = 0; s < nsplit; ++s) sum += (double)part[((size_t)s * m_pad + r) * Ntot + j];
+        if (svd64) svd64[(size_t)j * m + r] = sum;
+        else svd32[(size_t)j * m + r] = (float)sum;
+    } else {
+        for (int s = 0; s < nsplit; ++s)
+            for (int p = 0; p < nb; ++p) sum += (double)part[((size_t)s * m_pad + r) * Ntot + Nv + p];
+        c[r] = sum;
+    }
+}
+
+// slices of the n-long contraction: `groups` CTAs per slice, at most one CTA
+// per SM in all; chunk a multiple of 64 so slices never share a stage
+void split_plan(long long n, int groups, int num_sms, long long* chunk, int* nsplit) {
+    int target = num_sms / groups;
+    if (target < 1) target = 1;
+    long long ch = (n + target - 1) / target;
+    ch = (ch + kGmBK - 1) / kGmBK * kGmBK;
+    *chunk = ch;
+    *nsplit = (int)((n + ch - 1) / ch);
+}
+
+int v_rows(int K1) { return (K1 + kGmBRows + 15) / 16 * 16 - kGmBRows; }     // Nv: Nv + 8 a multiple of 16
+
+bool is16(int storage) { return storage == IPF_STORE_BF16 || storage == IPF_STORE_F16; }
+
+size_t part_bytes(int storage, int m, long long n, int K1max, int num_sms) {
+    const int m_pad = (m + 255) / 256 * 256;
+    long long chunk;
+    int nsplit;
+    if (is16(storage)) {
+        split_plan(n, m_pad / 256, num_sms, &chunk, &nsplit);
+        return (size_t)nsplit * m_pad * (v_rows(K1max) + kGmBRows) * sizeof(float);
+    }
+    split_plan(n, 1, num_sms, &chunk, &nsplit);
+    return (size_t)nsplit * m_pad * (K1max + 1) * sizeof(double);
 }
 
 }  // namespace
 
-cudaError_t launch_gauss_fill(int storage, void* S, long long n, int m, unsigned long long seed, int num_sms,
-                              cudaStream_t s) {
+long long gauss_lds(long long n) { return (n + 63) / 64 * 64; }
+
+size_t gauss_workspace_bytes(int storage, int m, long long n, int k_max, int num_sms) {
+    const size_t sb = storage == IPF_STORE_F64 ? 8 : storage == IPF_STORE_F32 ? 4 : 2;
+    return (size_t)kGmBRows * gauss_lds(n) * sb + 256 + part_bytes(storage, m, n, k_max + 1, num_sms);
+}
+
+cudaError_t launch_gauss_fill(int storage, void* S, long long n, int m, long long lds, unsigned long long seed,
+                              int num_sms, cudaStream_t s) {
     if (n <= 0 || m <= 0) return cudaSuccess;
     const int blocks = num_sms * 8;
-    const double sm = sqrt((double)m);
-    const float inv = (float)(1.0 / sm);
+    const double sq = sqrt((double)m);
+    const float inv = (float)(1.0 / sq);
     switch (storage) {
-        case IPF_STORE_F64: k_gauss_fill<double><<<blocks, 256, 0, s>>>((double*)S, n, m, seed, sm, inv); break;
-        case IPF_STORE_F32: k_gauss_fill<float><<<blocks, 256, 0, s>>>((float*)S, n, m, seed, sm, inv); break;
+        case IPF_STORE_F64: k_gauss_fill<double><<<blocks, 256, 0, s>>>((double*)S, n, m, lds, seed, sq, inv); break;
+        case IPF_STORE_F32: k_gauss_fill<float><<<blocks, 256, 0, s>>>((float*)S, n, m, lds, seed, sq, inv); break;
         case IPF_STORE_BF16:
-            k_gauss_fill<__nv_bfloat16><<<blocks, 256, 0, s>>>((__nv_bfloat16*)S, n, m, seed, sm, inv);
+            k_gauss_fill<__nv_bfloat16><<<blocks, 256, 0, s>>>((__nv_bfloat16*)S, n, m, lds, seed, sq, inv);
             break;
-        case IPF_STORE_F16: k_gauss_fill<__half><<<blocks, 256, 0, s>>>((__half*)S, n, m, seed, sm, inv); break;
+        case IPF_STORE_F16: k_gauss_fill<__half><<<blocks, 256, 0, s>>>((__half*)S, n, m, lds, seed, sq, inv); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_gauss_rhs(int storage, const void* S, const float* b, long long n, int m, double* c,
-                             double* part, cudaStream_t s) {
+cudaError_t launch_gauss_bparts(int storage, const float* b, long long n, void* ws, cudaStream_t s) {
+    const long long ldb = gauss_lds(n);
+    const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
     switch (storage) {
-        case IPF_STORE_F64: return rhs_typed((const double*)S, b, n, m, c, part, s);
-        case IPF_STORE_F32: return rhs_typed((const float*)S, b, n, m, c, part, s);
-        case IPF_STORE_BF16: return rhs_typed((const __nv_bfloat16*)S, b, n, m, c, part, s);
-        case IPF_STORE_F16: return rhs_typed((const __half*)S, b, n, m, c, part, s);
+        case IPF_STORE_F64: k_gauss_bparts<double><<<blocks, 256, 0, s>>>(b, n, ldb, (double*)ws); break;
+        case IPF_STORE_F32: k_gauss_bparts<float><<<blocks, 256, 0, s>>>(b, n, ldb, (float*)ws); break;
+        case IPF_STORE_BF16:
+            k_gauss_bparts<__nv_bfloat16><<<blocks, 256, 0, s>>>(b, n, ldb, (__nv_bfloat16*)ws);
+            break;
+        case IPF_STORE_F16: k_gauss_bparts<__half><<<blocks, 256, 0, s>>>(b, n, ldb, (__half*)ws); break;
         default: return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
 }
 
-void* gauss_blas_create() {
-    Blas& b = blas();
-    if (!b.ok) return nullptr;
-    cublasHandle_t h = nullptr;
-    if (b.create(&h) != CUBLAS_STATUS_SUCCESS) return nullptr;
-    return (void*)h;
-}
-
-void gauss_blas_destroy(void* h) {
-    if (h && blas().ok) blas().destroy((cublasHandle_t)h);
-}
-
-// out (m x K, column-major; FP64 for F64 storage, else FP32) = S (m x n) V (n x K, leading dimension ldv)
-cudaError_t launch_gauss_sv(void* handle, int storage, const void* S, int m, long long n, const void* V,
-                            long long ldv, int K, void* out, cudaStream_t s) {
-    Blas& b = blas();
-    if (!b.ok || !handle) return cudaErrorNotSupported;
-    cublasHandle_t h = (cublasHandle_t)handle;
-    if (b.set_stream(h, s) != CUBLAS_STATUS_SUCCESS) return cudaErrorUnknown;
-    cudaDataType t;
-    switch (storage) {
-        case IPF_STORE_F64: t = CUDA_R_64F; break;
-        case IPF_STORE_F32: t = CUDA_R_32F; break;
-        case IPF_STORE_BF16: t = CUDA_R_16BF; break;
-        case IPF_STORE_F16: t = CUDA_R_16F; break;
-        default: return cudaErrorInvalidValue;
+// [S V_{K1} | S b] for the basis columns 0 .. K1-1 (V: kcols columns of
+// ldv elements) into svd (column-major m x K1, FP64 for F64 storage, else
+// FP32) and c (m, FP64).  ws: the workspace of gauss_workspace_bytes (the b
+// rows written by launch_gauss_bparts first, then the partial tiles).
+cudaError_t launch_gauss_sv(int storage, const void* S, int m, long long n, const void* V, long long ldv, int kcols,
+                            int K1, void* ws, void* svd, double* c, int* err, int num_sms, cudaStream_t s) {
+    if (K1 < 1 || K1 > kcols || m < 1 || n < 1) return cudaErrorInvalidValue;
+    const long long lds = gauss_lds(n);
+    const size_t sb = storage == IPF_STORE_F64 ? 8 : storage == IPF_STORE_F32 ? 4 : 2;
+    const void* bpart = ws;
+    void* part = (char*)ws + ((size_t)kGmBRows * lds * sb + 255) / 256 * 256;
+    const int m_pad = (m + 255) / 256 * 256;
+    const int rb = 256;
+    if (is16(storage)) {
+        EncodeTiledFn enc = encode_fn();
+        if (!enc) return cudaErrorNotSupported;
+        const int Nv = v_rows(K1), Ntot = Nv + kGmBRows;
+        if (Ntot > kGmBRowsMax) return cudaErrorInvalidValue;
+        const int mg = m_pad / 256;
+        long long chunk;
+        int nsplit;
+        split_plan(n, mg, num_sms, &chunk, &nsplit);
+        const CUtensorMapDataType dt =
+            storage == IPF_STORE_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+        const cuuint32_t estr[2] = {1, 1};
+        CUtensorMap smap, vmap, bmap;
+        auto make = [&](CUtensorMap* map, const void* base, cuuint64_t rows, cuuint64_t ld, cuuint32_t box_rows) {
+            const cuuint64_t dims[2] = {(cuuint64_t)n, rows};
+            const cuuint64_t strides[1] = {ld * 2};
+            const cuuint32_t box[2] = {(cuuint32_t)kGmBK, box_rows};
+            return enc(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        };
+        if (make(&smap, S, (cuuint64_t)m, (cuuint64_t)lds, 128) != CUDA_SUCCESS ||
+            make(&vmap, V, (cuuint64_t)kcols, (cuuint64_t)ldv, (cuuint32_t)Nv) != CUDA_SUCCESS ||
+            make(&bmap, bpart, (cuuint64_t)kGmBRows, (cuuint64_t)lds, kGmBRows) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+        const int bi = storage == IPF_STORE_BF16 ? 1 : 0;
+        const cudaError_t attr =
+            bi ? cudaFuncSetAttribute(k_gauss_mma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGmSmemRequest)
+               : cudaFuncSetAttribute(k_gauss_mma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGmSmemRequest);
+        if (attr != cudaSuccess) return attr;
+        if (bi)
+            k_gauss_mma<true><<<nsplit * mg, kGmThreads, kGmSmemRequest, s>>>(smap, vmap, bmap, n, m, chunk, mg, Nv,
+                                                                            Ntot, (float*)part, m_pad, err);
+        else
+            k_gauss_mma<false><<<nsplit * mg, kGmThreads, kGmSmemRequest, s>>>(smap, vmap, bmap, n, m, chunk, mg, Nv,
+                                                                             Ntot, (float*)part, m_pad, err);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        const long long th = (long long)m * (K1 + 1);
+        k_gauss_reduce<float><<<(unsigned)((th + rb - 1) / rb), rb, 0, s>>>(
+            (const float*)part, nsplit, m, m_pad, Ntot, K1, Nv, 3, (float*)svd, nullptr, c);
+        return cudaGetLastError();
     }
-    const bool f64 = storage == IPF_STORE_F64;
-    const double a64 = 1.0, b64 = 0.0;
-    const float a32 = 1.f, b32 = 0.f;
-    const cublasStatus_t st = b.gemm_ex(h, CUBLAS_OP_N, CUBLAS_OP_N, m, K, (int)n, f64 ? (const void*)&a64 : &a32, S,
-                                        t, m, V, t, (int)ldv, f64 ? (const void*)&b64 : &b32, out,
-                                        f64 ? CUDA_R_64F : CUDA_R_32F, m,
-                                        f64 ? CUBLAS_COMPUTE_64F : CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
-    return st == CUBLAS_STATUS_SUCCESS ? cudaSuccess : cudaErrorUnknown;
+    long long chunk;
+    int nsplit;
+    split_plan(n, 1, num_sms, &chunk, &nsplit);
+    const int Ntot = K1 + 1;
+    const dim3 grid(nsplit, (m + 15) / 16, (Ntot + 15) / 16);
+    if (storage == IPF_STORE_F64)
+        k_gauss_simt<double, double><<<grid, 256, 0, s>>>((const double*)S, lds, m, n, (const double*)V, ldv, K1,
+                                                          (const double*)bpart, chunk, (double*)part, m_pad, Ntot);
+    else
+        k_gauss_simt<float, float><<<grid, 256, 0, s>>>((const float*)S, lds, m, n, (const float*)V, ldv, K1,
+                                                        (const float*)bpart, chunk, (double*)part, m_pad, Ntot);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long th = (long long)m * (K1 + 1);
+    k_gauss_reduce<double><<<(unsigned)((th + rb - 1) / rb), rb, 0, s>>>(
+        (const double*)part, nsplit, m, m_pad, Ntot, K1, K1, 1,
+        storage == IPF_STORE_F64 ? nullptr : (float*)svd, storage == IPF_STORE_F64 ? (double*)svd : nullptr, c);
+    return cudaGetLastError();
 }
 
 }  // namespace ipf

@@ -285,6 +285,36 @@ struct OpDev {
 };
 
 // ---------------------------------------------------------------------------
+// batched step: many one-RHS solves in flight advanced by one launch per
+// phase.  The work list is a table of slots (each a context's geometry,
+// buffers, sketch and operator, and the number of steps it takes) and, per
+// phase, a flat table of (slot, tile) pairs; a CTA takes the table entries
+// blockIdx.x, blockIdx.x + gridDim.x, ...  A slot is active in a step while
+// its status is IPF_OK and its step counter is below k_target.
+// ---------------------------------------------------------------------------
+constexpr int kMaxSlots = 64;
+constexpr int kBatchUpdTile = kFoldEvery;      // update tile: the split counters' exact range
+constexpr int kBatchNormTile = 4096;           // normalise tile (elements)
+constexpr int kBatchCsrRows = 16;              // CSR rows per operator tile
+
+struct SlotDesc {
+    Geom g;
+    Bufs bf;
+    SketchParams sp;
+    OpDev op;
+    int k_target;
+    int norm_tiles;                // tiles of this slot in the normalise table (its last-tile ticket)
+    int conv_cols;                 // operator tiles: PSF FMA path, tiles per image row of tiles; CSR 0
+    int tc_ct, tc_rows;            // tensor-core convolution: column tiles and output rows per unit
+    const void* tc_map;            // its 64-byte aligned CUtensorMap in device memory, or NULL
+};
+
+struct TileRef {
+    int slot;
+    int tile;
+};
+
+// ---------------------------------------------------------------------------
 // launchers (defined in the .cu files)
 // ---------------------------------------------------------------------------
 // k_ops.cu
@@ -313,19 +343,20 @@ cudaError_t launch_op_apply_f32_plain(const OpDev& op, const float* v, float* w,
                                       cudaStream_t s);
 // k_hess.cu
 cudaError_t launch_reset_state(DevState* st, cudaStream_t s);
-// Gaussian sketch (gauss.cu)
-cudaError_t launch_gauss_fill(int storage, void* S, long long n, int m, unsigned long long seed, int num_sms,
-                              cudaStream_t s);
-// column slices of c = S b; pass 1 writes at most kGaussRhsSlices x
-// max(m, 2048) FP64 partial sums (kGaussRhsPart(m) doubles)
-constexpr int kGaussRhsSlices = 608;
-inline size_t kGaussRhsPart(int m) { return (size_t)kGaussRhsSlices * (m > 2048 ? m : 2048); }
-cudaError_t launch_gauss_rhs(int storage, const void* S, const float* b, long long n, int m, double* c,
-                             double* part, cudaStream_t s);
-void* gauss_blas_create();
-void gauss_blas_destroy(void* h);
-cudaError_t launch_gauss_sv(void* handle, int storage, const void* S, int m, long long n, const void* V,
-                            long long ldv, int K, void* out, cudaStream_t s);
+// Gaussian sketch (gauss.cu).  S is row-major, m rows of lds = gauss_lds(n)
+// elements (entry (r, i) at r*lds + i); the workspace holds the rows of b
+// the contraction takes as extra B columns (zeroed at creation, written per
+// right-hand side by launch_gauss_bparts) and the slices' partial tiles.
+long long gauss_lds(long long n);
+size_t gauss_workspace_bytes(int storage, int m, long long n, int k_max, int num_sms);
+cudaError_t launch_gauss_fill(int storage, void* S, long long n, int m, long long lds, unsigned long long seed,
+                              int num_sms, cudaStream_t s);
+cudaError_t launch_gauss_bparts(int storage, const float* b, long long n, void* ws, cudaStream_t s);
+// [S V_{K1} | S b]: svd (column-major m x K1, FP64 for F64 storage, else
+// FP32) and c = S b (FP64); err receives IPF_ERR_TIMEOUT if a bounded wait
+// inside the tensor-core kernel gives up
+cudaError_t launch_gauss_sv(int storage, const void* S, int m, long long n, const void* V, long long ldv, int kcols,
+                            int K1, void* ws, void* svd, double* c, int* err, int num_sms, cudaStream_t s);
 // sampled pivoting: overwrite the step's pivot choice (after the update)
 cudaError_t launch_sample_pivot(int storage, const Geom& g, const Bufs& bf, unsigned long long seed, int size,
                                 cudaStream_t s);
@@ -351,6 +382,21 @@ cudaError_t launch_sketch_vector(const float* x, long long n, const SketchParams
 cudaError_t launch_fixed_to_double(const long long* acc, int m, double scale, double* y, cudaStream_t s);
 cudaError_t launch_sketch_finish(const long long* acc, int m, long long n, int zeta, const unsigned* absmax,
                                  double* y, cudaStream_t s);
+// batched step (k_hess.cu, k_ops.cu, k_conv_tc.cu): one launch per phase for
+// every slot of the table; storage is the slots' common float storage type
+cudaError_t launch_batch_pivot_solve(int storage, const SlotDesc* slots, int nslots, int k_max, cudaStream_t s);
+cudaError_t launch_batch_update(int storage, const SlotDesc* slots, const TileRef* tiles, int ntiles, int k_max,
+                                int m_s_max, int num_sms, cudaStream_t s);
+cudaError_t launch_batch_normalize(int storage, const SlotDesc* slots, const TileRef* tiles, int ntiles, int num_sms,
+                                   cudaStream_t s);
+// PSF (FMA column convolution, kw 7 / 15 / 31) and CSR products
+cudaError_t launch_batch_operator(int storage, const SlotDesc* slots, const TileRef* tiles, int ntiles, int num_sms,
+                                  cudaStream_t s);
+// tensor-core convolution (BF16) of the slots with tc_map, units of one KP
+cudaError_t launch_batch_conv_tc(int kp, const SlotDesc* slots, const TileRef* units, int nunits, cudaStream_t s);
+// the tensor map of a slot's basis for the tensor-core convolution (host)
+bool conv_tc_map(const OpDev& op, const void* vbase, long long ldv, long long vcols, void* map_out);
+
 // k_small.cu: workspace for k <= k_max and up to nl_max lambdas per chunk
 size_t solve_workspace_bytes(const Geom& g, int nl_max);
 // form M = [Z | c] (and T = S V_k) and their R factors

@@ -50,11 +50,10 @@ __host__ __device__ constexpr size_t lp_stride(int k_max) { return ((size_t)(k_m
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 template <class T, class Acc>
-__global__ void __launch_bounds__(256) k_pivot_solve(Geom g, Bufs bf) {
+__device__ __forceinline__ void pivot_solve_body(const Geom& g, const Bufs& bf, int r) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long s_bar;
     __shared__ int s_timeout;
-    const int r = blockIdx.x;
     DevState* st = bf.st;
     if (st->status[r] != IPF_OK) return;
     const int j = st->j;
@@ -175,6 +174,11 @@ __global__ void __launch_bounds__(256) k_pivot_solve(Geom g, Bufs bf) {
             coef[(size_t)i * B + r] = (Acc)x[h];
         }
     }
+}
+
+template <class T, class Acc>
+__global__ void __launch_bounds__(256) k_pivot_solve(Geom g, Bufs bf) {
+    pivot_solve_body<T, Acc>(g, bf, blockIdx.x);
 }
 
 // ------------------------------------------------------------------------
@@ -1082,6 +1086,256 @@ cudaError_t launch_reset_state(DevState* st, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------------
+// batched step: the update, normalisation and pivot-block solve of every
+// active slot of the work list in one launch each (persistent CTAs over the
+// (slot, tile) tables).  Per element the arithmetic is that of k_update_f,
+// k_normalize and k_pivot_solve for one right-hand side with float storage
+// and the deferred sketch, so a solve gets the same bits whatever else is
+// in the batch and however its elements are tiled.
+// ------------------------------------------------------------------------
+// the slot's state at the start of a phase, read by thread 0 and shared
+__device__ __forceinline__ int slot_step(const SlotDesc* sd, int* s_j) {
+    __syncthreads();                                   // the previous tile is done with shared memory
+    if (threadIdx.x == 0) {
+        const DevState* st = sd->bf.st;
+        const int j = st->j;
+        *s_j = (st->status[0] == IPF_OK && j < sd->k_target && j < sd->g.k_max) ? j : -1;
+    }
+    __syncthreads();
+    return *s_j;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256, 4) kb_update(const SlotDesc* __restrict__ slots,
+                                                    const TileRef* __restrict__ tiles, int ntiles) {
+    constexpr int VEC = Vec16<T>::n;
+    extern __shared__ unsigned char smem_raw[];
+    float* s_coef = (float*)smem_raw;
+    __shared__ unsigned long long s_key;
+    __shared__ int s_j;
+    for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+        const TileRef tr = tiles[tt];
+        const SlotDesc* sd = slots + tr.slot;
+        const int j = slot_step(sd, &s_j);
+        if (j < 0) continue;
+        const Geom g = sd->g;
+        const Bufs bf = sd->bf;
+        const SketchParams sp = sd->sp;
+        DevState* st = bf.st;
+        const int nc = j + 1;
+        const float* coef = (const float*)bf.coef;
+        for (int t = threadIdx.x; t < nc; t += blockDim.x) s_coef[t] = coef[t];
+        const int csk = (g.sketch_defer && st->sk_pending == j) ? j : -1;
+        int* s_hi = (int*)(s_coef + ((nc + 3) & ~3));
+        int* s_lo = s_hi + sp.m_s;
+        if (csk >= 0)
+            for (int t = threadIdx.x; t < 2 * sp.m_s; t += blockDim.x) s_hi[t] = 0;
+        if (threadIdx.x == 0) s_key = 0ull;
+        __syncthreads();
+        const int Ssk = csk >= 0 ? kSplitS - bf.colE[csk] : 0;
+        const uint2* tab = (const uint2*)bf.sktab;
+        const T* V = (const T*)bf.V;
+        float* w = (float*)bf.w;
+        const unsigned N = (unsigned)g.N;
+        const unsigned e0 = (unsigned)tr.tile * (unsigned)kBatchUpdTile;
+        const unsigned e1 = min(N, e0 + (unsigned)kBatchUpdTile);
+        const size_t ldv = (size_t)g.ldv;
+        unsigned long long best = 0ull;
+        for (unsigned base = e0 + threadIdx.x * VEC; base < e1; base += blockDim.x * VEC) {
+            float acc[VEC];
+            {
+                const float4* wp = (const float4*)(w + base);
+#pragma unroll
+                for (int q = 0; q < VEC / 4; ++q) {
+                    const float4 t4 = wp[q];
+                    acc[4 * q] = t4.x; acc[4 * q + 1] = t4.y; acc[4 * q + 2] = t4.z; acc[4 * q + 3] = t4.w;
+                }
+            }
+            const T* vb = V + base;
+            if (csk >= 0) {
+                const uint4 rv = *(const uint4*)(vb + (size_t)csk * ldv);
+                const T* vv = (const T*)&rv;
+#pragma unroll
+                for (int q = 0; q < VEC; q += 2) {
+                    const uint4 te = *(const uint4*)(tab + base + q);
+                    if (base + q < N) {
+                        const long long qv = fixed_from(to_acc(vv[q]), Ssk);
+                        if (qv) scatter8(s_hi, s_lo, sp, qv, make_uint2(te.x, te.y));
+                    }
+                    if (base + q + 1 < N) {
+                        const long long qv = fixed_from(to_acc(vv[q + 1]), Ssk);
+                        if (qv) scatter8(s_hi, s_lo, sp, qv, make_uint2(te.z, te.w));
+                    }
+                }
+            }
+            int c = 0;
+            for (; c + 8 <= nc; c += 8) {
+                uint4 raw[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) raw[u] = __ldcs((const uint4*)(vb + (size_t)(c + u) * ldv));
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const T* vv = (const T*)&raw[u];
+#pragma unroll
+                    for (int q = 0; q < VEC; ++q) acc[q] = fmaf(-s_coef[c + u], to_acc(vv[q]), acc[q]);
+                }
+            }
+            for (; c < nc; ++c) {
+                const uint4 r1 = __ldcs((const uint4*)(vb + (size_t)c * ldv));
+                const T* vv = (const T*)&r1;
+#pragma unroll
+                for (int q = 0; q < VEC; ++q) acc[q] = fmaf(-s_coef[c], to_acc(vv[q]), acc[q]);
+            }
+            const unsigned bits = bf.ispiv[base >> 5] >> (base & 31);
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) {
+                if ((bits >> q) & 1u) acc[q] = 0.f;
+                const unsigned e = base + q;
+                if (e < N) {
+                    const unsigned long long k = argmax_key(acc[q], e);
+                    best = k > best ? k : best;
+                }
+            }
+            float4* wo = (float4*)(w + base);
+#pragma unroll
+            for (int q = 0; q < VEC / 4; ++q)
+                wo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, best, off);
+            best = o > best ? o : best;
+        }
+        if ((threadIdx.x & 31) == 0 && best) atomicMax(&s_key, best);
+        __syncthreads();
+        if (threadIdx.x == 0 && s_key) atomicMax(&st->key[(j + 1) & 1][0], s_key);
+        if (csk >= 0) {
+            long long* dst = bf.accSV + (size_t)csk * sp.m_s;
+            for (int t = threadIdx.x; t < sp.m_s; t += blockDim.x) {
+                const long long v = ((long long)s_hi[t] << 17) + (long long)s_lo[t];
+                if (v) atomicAdd((unsigned long long*)&dst[t], (unsigned long long)v);
+            }
+        }
+    }
+}
+
+// the fast path of k_normalize (one RHS, float storage, the sketch deferred
+// to the next update), over the tile's elements; tile 0 of a slot keeps its
+// books and the slot's last tile advances its step counter
+template <class T>
+__global__ void __launch_bounds__(256) kb_normalize(const SlotDesc* __restrict__ slots,
+                                                    const TileRef* __restrict__ tiles, int ntiles) {
+    __shared__ long long s_prow;
+    __shared__ float s_hval;
+    __shared__ int s_ok, s_code, s_j;
+    __shared__ bool s_last;
+    for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+        const TileRef tr = tiles[tt];
+        const SlotDesc* sd = slots + tr.slot;
+        const int j = slot_step(sd, &s_j);
+        if (j < 0) continue;
+        const Geom g = sd->g;
+        const Bufs bf = sd->bf;
+        DevState* st = bf.st;
+        const int jn = j + 1;
+        const int kb = jn & 1;
+        const float* w = (const float*)bf.w;
+        if (threadIdx.x == 0) {
+            int ok = 1, code = IPF_OK;
+            long long row = 0;
+            float hv = 0.f;
+            const unsigned long long key = st->key[kb][0];
+            if (key == 0ull || key_absval(key) == 0.f) {
+                ok = 0; code = IPF_BREAKDOWN;
+            } else {
+                row = (long long)key_row(key);
+                hv = w[row];
+                if (!isfinite(hv)) { ok = 0; code = IPF_ERR_NONFINITE; }
+                else if (hv == 0.f) { ok = 0; code = IPF_BREAKDOWN; }
+            }
+            s_prow = row;
+            s_hval = hv;
+            s_ok = ok;
+            s_code = code;
+        }
+        __syncthreads();
+        const unsigned n = (unsigned)g.n;
+        if (s_ok) {
+            T* vout = (T*)bf.V + (size_t)jn * g.ldv;
+            const unsigned n4 = n >> 2;
+            const unsigned q0 = (unsigned)tr.tile * (kBatchNormTile / 4);
+            const unsigned q1 = min(n4, q0 + kBatchNormTile / 4);
+            const long long prow = s_prow;
+            const float hval = s_hval;
+            for (unsigned t = q0 + threadIdx.x; t < q1; t += blockDim.x) {
+                const unsigned i0 = t << 2;
+                const float4 w4 = *reinterpret_cast<const float4*>(w + i0);
+                const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
+                T vs[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float v = ((long long)(i0 + e) == prow) ? 1.f : wv[e] / hval;
+                    vs[e] = from_acc<T>(v);
+                }
+                if constexpr (sizeof(T) == 2) {
+                    union { uint2 u; T t[4]; } pk;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) pk.t[e] = vs[e];
+                    *reinterpret_cast<uint2*>(vout + i0) = pk.u;
+                } else {
+                    *reinterpret_cast<float4*>(vout + i0) =
+                        make_float4(to_acc(vs[0]), to_acc(vs[1]), to_acc(vs[2]), to_acc(vs[3]));
+                }
+            }
+            // the last n mod 4 elements belong to the tile holding element 4 n4
+            if (4u * n4 >= (unsigned)tr.tile * kBatchNormTile && 4u * n4 < (unsigned)(tr.tile + 1) * kBatchNormTile &&
+                threadIdx.x < (n & 3u)) {
+                const unsigned i = (n4 << 2) + threadIdx.x;
+                const float v = ((long long)i == prow) ? 1.f : w[i] / hval;
+                vout[i] = from_acc<T>(v);
+            }
+        }
+        if (tr.tile == 0 && threadIdx.x == 0) {
+            const int K1 = g.k_max + 1;
+            if (s_ok) {
+                const long long row = s_prow;
+                bf.piv[jn] = (int)row;
+                bf.colE[jn] = 0;
+                bf.H[(size_t)K1 * j + jn] = (double)s_hval;
+                atomicOr(&bf.ispiv[row >> 5], 1u << (unsigned)(row & 31));
+                st->kdone[0] = jn;
+            } else if (st->status[0] == IPF_OK) {
+                st->status[0] = s_code;
+                st->kdone[0] = (s_code == IPF_BREAKDOWN) ? jn : (jn > 0 ? jn - 1 : 0);
+            }
+            st->key[kb ^ 1][0] = 0ull;
+            if (g.sketch_defer) st->sk_pending = s_ok ? jn : -1;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            s_last = atomicAdd(&st->ctr, 1u) == (unsigned)sd->norm_tiles - 1u;
+        }
+        __syncthreads();
+        if (s_last && threadIdx.x == 0) {
+            st->j = jn;
+            st->ctr = 0u;
+            __threadfence();
+        }
+    }
+}
+
+template <class T, class Acc>
+__global__ void __launch_bounds__(256) kb_pivot_solve(const SlotDesc* __restrict__ slots) {
+    const SlotDesc* sd = slots + blockIdx.x;
+    const DevState* st = sd->bf.st;
+    if (st->j >= sd->k_target) return;
+    const Geom g = sd->g;
+    const Bufs bf = sd->bf;
+    pivot_solve_body<T, Acc>(g, bf, 0);
+}
+
+// ------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------
 #define IPF_DISPATCH_STORAGE(storage, ...)                                         \
@@ -1307,6 +1561,61 @@ cudaError_t launch_sketch_vector(const float* x, long long n, const SketchParams
 cudaError_t launch_sketch_finish(const long long* acc, int m, long long n, int zeta, const unsigned* absmax,
                                  double* y, cudaStream_t s) {
     k_sketch_finish<<<(m + 255) / 256, 256, 0, s>>>(acc, m, n, zeta, absmax, y);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------
+// batched step launchers
+// ------------------------------------------------------------------------
+cudaError_t launch_batch_pivot_solve(int storage, const SlotDesc* slots, int nslots, int k_max, cudaStream_t s) {
+    if (nslots <= 0) return cudaSuccess;
+    const int K1 = k_max + 1;
+    const size_t smem = lp_stride(k_max) * sizeof(double) + (size_t)(((K1 + 1) & ~1) + K1 + 1) * sizeof(double);
+    auto go = [&](auto fn) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        fn<<<nslots, 256, smem, s>>>(slots);
+        return cudaGetLastError();
+    };
+    switch (storage) {
+        case IPF_STORE_F32: return go(kb_pivot_solve<float, float>);
+        case IPF_STORE_BF16: return go(kb_pivot_solve<__nv_bfloat16, float>);
+        case IPF_STORE_F16: return go(kb_pivot_solve<__half, float>);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_batch_update(int storage, const SlotDesc* slots, const TileRef* tiles, int ntiles, int k_max,
+                                int m_s_max, int num_sms, cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    const size_t smem = (size_t)((k_max + 1 + 3) & ~3) * sizeof(float) + (size_t)2 * m_s_max * sizeof(int);
+    const int blocks = ntiles < num_sms * 4 ? ntiles : num_sms * 4;
+    auto go = [&](auto fn) -> cudaError_t {
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        fn<<<blocks, 256, smem, s>>>(slots, tiles, ntiles);
+        return cudaGetLastError();
+    };
+    switch (storage) {
+        case IPF_STORE_F32: return go(kb_update<float>);
+        case IPF_STORE_BF16: return go(kb_update<__nv_bfloat16>);
+        case IPF_STORE_F16: return go(kb_update<__half>);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_batch_normalize(int storage, const SlotDesc* slots, const TileRef* tiles, int ntiles, int num_sms,
+                                   cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    const int blocks = ntiles < num_sms * 8 ? ntiles : num_sms * 8;
+    switch (storage) {
+        case IPF_STORE_F32: kb_normalize<float><<<blocks, 256, 0, s>>>(slots, tiles, ntiles); break;
+        case IPF_STORE_BF16: kb_normalize<__nv_bfloat16><<<blocks, 256, 0, s>>>(slots, tiles, ntiles); break;
+        case IPF_STORE_F16: kb_normalize<__half><<<blocks, 256, 0, s>>>(slots, tiles, ntiles); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

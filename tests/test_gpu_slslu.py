@@ -61,8 +61,8 @@ def _verify(ctx, A, At, b, S1, S2, k, storage, taps, ks, lambdas, name="", **sam
     iterates are compared with the storage-matched oracle replaying the GPU's
     pivot sequences, within max(floor, 10 r_k), r_k the replay's own response
     to that perturbation; (iii) against the FP64 oracle the stated tolerance
-    is asserted wherever the storage type can reach it with one rounding per
-    product entry (_gpu_common)."""
+    is asserted wherever the storage type can reach it (the two criteria of
+    _gpu_common)."""
     st64 = slslu.run(A, At, b, S1, S2, k, **sampling)
     st = st64 if storage == "f64" else slslu.run(A, At, b, S1, S2, k, storage=storage, **sampling)
     ex, du = ctx.export(0), ctx.export_dual(0)
@@ -79,7 +79,8 @@ def _verify(ctx, A, At, b, S1, S2, k, storage, taps, ks, lambdas, name="", **sam
         assert j_gpu >= j_or - 3, (j_gpu, j_or)
     st_f = slslu.run(A, At, b, S1, S2, k, forced_t=gt, forced_g=gg, storage=storage)
     st_fp = _perturbed(A, At, b, S1, S2, k, delta, forced=(gt, gg), storage=storage)
-    st_fm = _perturbed(A, At, b, S1, S2, k, U_ACC[storage], 54321, forced=(gt, gg), storage=storage)
+    st_fm = _perturbed(A, At, b, S1, S2, k, np.sqrt(taps / 12.0) * U_ACC[storage], 54321, forced=(gt, gg),
+                       storage=storage)
     for kk in ks:
         x, info = ctx.solve(kk, lambdas)
         for li, lam in enumerate(lambdas):
@@ -90,10 +91,11 @@ def _verify(ctx, A, At, b, S1, S2, k, storage, taps, ks, lambdas, name="", **sam
             e = rel(xg, x_or)
             x64 = slslu.solve(st64, kk, lam)
             e64, d_s = rel(xg, x64), rel(x_or, x64)
-            r_min = rel(slslu.solve(st_fm, kk, lam), x_or)
-            reach = d_s + r_min <= STATED[storage]
+            r_typ = rel(slslu.solve(st_fm, kk, lam), x_or)
+            kappa = np.linalg.cond(slslu.projected_matrix(st_f, kk))
+            reach = kappa * U[storage] <= STATED[storage] and d_s + 3.0 * r_typ <= STATED[storage]
             rec = {"test": name, "storage": storage, "k": kk, "lam": lam, "e_par": e, "tol_par": tol, "e64": e64,
-                   "stated": STATED[storage], "storage_only": d_s, "least_rounding": r_min,
+                   "stated": STATED[storage], "storage_only": d_s, "rms_rounding": r_typ, "kappa": kappa,
                    "stated_reachable": bool(reach), "pivots_agree": j_gpu}
             RECORD.append(rec)
             assert e <= tol, rec
@@ -126,9 +128,13 @@ def test_deblur64_slslu_parity(deblur64_slslu, storage):
                         name=f"slslu_deblur64_{storage}")
     ex, du = ctx.export(0), ctx.export_dual(0)
     assert abs(ex["beta"] - st.beta) <= 1e-6 * abs(st.beta)
-    # W(1,1) and the first columns of H and W come from the stored d_1, l_1,
-    # so they match the storage-matched oracle to the accumulation precision
-    tol1 = 1e-12 if storage == "f64" else 1e-5
+    # W(1,1) and the first columns of H and W come from the stored d_1, l_1:
+    # they match the storage-matched oracle to the accumulation precision,
+    # and for 16-bit storage to one storage unit (an entry of l_1 formed in
+    # FP32 on the GPU and in FP64 in the oracle can round to neighbouring
+    # values of the storage type, which moves a product of the nonnegative
+    # PSF with it by at most u_s of its size)
+    tol1 = {"f64": 1e-12, "f32": 1e-5, "bf16": U["bf16"], "f16": U["f16"]}[storage]
     assert abs(du["w11"] - st.W[0, 0]) <= tol1 * abs(st.W[0, 0])
     assert rel(ex["H"][:2, 0], st.H[:2, 0]) < tol1
     assert rel(du["W"][:2, 0], st.W[:2, 1]) < tol1
