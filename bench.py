@@ -764,7 +764,8 @@ def run_serving(args, duration=None):
         return plan
 
     def serve(arrivals, plan):
-        srv = bd.Server(hbm_budget_bytes=64 << 30, max_inflight=64, steps_per_slice=8)
+        srv = bd.Server(hbm_budget_bytes=64 << 30, max_inflight=64, steps_per_slice=args.serve_slice,
+                        per_request=args.serve_per_request)
         tickets = []
         t0 = time.perf_counter()
         for a, (op, b, cfg, k, lam, kind) in zip(arrivals, plan):
@@ -781,6 +782,7 @@ def run_serving(args, duration=None):
                     if out is not None:
                         results[t] = (out, kind)
             time.sleep(0.001)
+        bstats = srv.batch_stats()
         srv.close()
         lat = np.array([r[0][2][2] - r[0][2][0] for r in results.values()])
         ok = sum(1 for r in results.values() if r[0][0] in (0, 1))
@@ -793,7 +795,9 @@ def run_serving(args, duration=None):
                 "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3),
                                "p99": float(np.percentile(lat, 99) * 1e3), "mean": float(lat.mean() * 1e3)},
                 "latency_ms_by_kind_p50": {k2: float(np.percentile(v, 50) * 1e3) for k2, v in sorted(by.items())},
-                "span_s": span}
+                "span_s": span,
+                "batched_step": {"requests_batched": bstats[0], "graph_turns": bstats[1], "eager_turns": bstats[2],
+                                 "graph_captures": bstats[3]}}
 
     rate = 200.0
     duration = float(args.serve_seconds if duration is None else duration)
@@ -812,7 +816,10 @@ def run_serving(args, duration=None):
 
 def run_small(storage: str):
     """One solve of a small case (1024x1024 Moffat, k=64, m_s=256; the basis
-    plus work vector exceed L2) with eager launches: the ncu target."""
+    plus work vector exceed L2) with eager launches: the ncu target.
+    storage "gauss": the same with a BF16 basis and the Gaussian sketch (S is
+    256 x 1024^2 BF16, 0.5 GB), whose solve runs the tensor-core
+    contraction [S V_{k+1} | S b]."""
     import torch
     from gen import problems as P
     from paper_2502_02721_gb300 import binding as bd, build as bl
@@ -822,7 +829,9 @@ def run_small(storage: str):
     p = P.deblur_moffat(side=1024, k=64, m_s=256)
     keep = []
     op = bd.operator_from_problem(p, keep)
-    cfg = bd.default_config(k_max=64, m_s=256, zeta=8, seed=p.sketch_seed, storage=storage, use_graphs=0)
+    extra = {"sketch": "gaussian"} if storage == "gauss" else {}
+    cfg = bd.default_config(k_max=64, m_s=256, zeta=8, seed=p.sketch_seed,
+                            storage="bf16" if storage == "gauss" else storage, use_graphs=0, **extra)
     ctx = bd.Context(op, p.b, cfg, keep)
     ctx.step(64)
     x, info = ctx.solve(64, [0.0, 1e-3])
@@ -845,9 +854,12 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-overlap", type=int, default=None, choices=[0, 1, 2])
     ap.add_argument("--serve-conv-fma", type=int, default=None, choices=[0, 1])
+    ap.add_argument("--serve-slice", type=int, default=8, help="Hessenberg steps per serving turn")
+    ap.add_argument("--serve-per-request", action="store_true",
+                    help="serve without the batched step (each request on its own streams)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the CT 32-RHS batch and the 5 s serving run on the default line")
-    ap.add_argument("--small", default=None, choices=["f32", "bf16", "f16", "f64"],
+    ap.add_argument("--small", default=None, choices=["f32", "bf16", "f16", "f64", "gauss"],
                     help="run one small solve (profiling target) and exit")
     args = ap.parse_args()
     if args.small:

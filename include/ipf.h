@@ -353,9 +353,12 @@ typedef struct ipf_server ipf_server;
 typedef struct ipf_server_config {
     size_t hbm_budget_bytes;     /* device memory for in-flight requests, reserved at
                                     creation (0: 80% of the free memory)                  */
-    size_t pinned_bytes;         /* pinned host staging for results (0: 512 MiB)          */
+    size_t pinned_bytes;         /* pinned host staging for b and x (0: 1 GiB)             */
     int max_inflight;            /* requests on the GPU at once, 1..64                     */
     int steps_per_slice;         /* Hessenberg steps enqueued per request per turn (0: 8)  */
+    int per_request;             /* 0 (default): requests the batched step can drive share
+                                    it (see ipf_server_create); 1: every request steps on
+                                    its own context and streams                           */
 } ipf_server_config;
 
 typedef struct ipf_request {
@@ -376,12 +379,24 @@ typedef struct ipf_result {
 
 /* Start a serving loop on the current device: a scheduler thread admits
  * requests when a slot is free and ipf_footprint(request) fits in what is
- * left of the budget (first come, first served), runs each in its own
- * context and streams (so in-flight requests overlap on the GPU), tops each
- * up with steps_per_slice Hessenberg steps whenever its previous slice has
- * finished, then solves at k with lambda and copies x to the host.  Each
- * request's steps run on one stream (its config.overlap is taken as 0).  All
- * device memory comes from one arena reserved here, so admission and
+ * left of the budget (first come, first served), each into its own context
+ * (its basis, pivots and sketches stay on the device until it retires).
+ * Requests with one RHS, float storage, the sparse-sign sketch with zeta 8
+ * and m_s <= 1024, full pivoting, no DIRECT Z form for BF16/FP16, and a PSF2D
+ * operator whose PSF pads to 7x7, 15x15 or 31x31 or a CSR operator, share the
+ * batched step: one turn advances every such in-flight request by
+ * steps_per_slice Hessenberg steps with one launch per phase per step over
+ * a device work list of all of them (requests of different n, k and step
+ * counts in the same launches; a turn is replayed from a CUDA graph while
+ * the set of requests stays the same).  For a BF16 PSF the product is the
+ * FP32 FMA convolution or the tensor-core convolution with a band height
+ * chosen by timing them on the request the first time its (PSF width, image
+ * size) is seen, kept per process and, if the environment variable
+ * IPF_TUNE_CACHE names a file, in that JSON file.  A request's result does not
+ * depend on which other requests share its launches.  Other requests (and
+ * all of them with per_request) step on their own streams.  After k steps
+ * the request solves at k with lambda and copies x to the host.  All device
+ * memory of requests comes from one arena reserved here, so admission and
  * retirement allocate nothing.  Errors: IPF_ERR_ARG, IPF_ERR_OOM (budget
  * cannot be reserved), IPF_ERR_CUDA.                                     */
 ipf_status ipf_server_create(const ipf_server_config* cfg, ipf_server** out);
@@ -394,6 +409,12 @@ ipf_status ipf_submit(ipf_server* s, const ipf_request* rq, unsigned long long* 
  * n float32) to x_out if not NULL, forgets the ticket and returns the
  * request's status.  Thread-safe.                                         */
 ipf_status ipf_poll(ipf_server* s, unsigned long long ticket, ipf_result* res, float* x_out);
+
+/* Requests that took a slot of the batched step so far, and the engine's
+ * turns launched from a CUDA graph, launched eagerly, and graph captures
+ * (any pointer may be NULL).                                              */
+ipf_status ipf_server_batch_stats(ipf_server* s, int* batched, long long* graph_turns, long long* eager_turns,
+                                  long long* captures);
 
 /* In-flight requests, queued requests and the budget they reserve.        */
 ipf_status ipf_server_stats(ipf_server* s, int* inflight, int* queued, size_t* hbm_in_use);

@@ -60,7 +60,7 @@ class ipf_config(C.Structure):
 
 class ipf_server_config(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("pinned_bytes", C.c_size_t), ("max_inflight", C.c_int),
-                ("steps_per_slice", C.c_int)]
+                ("steps_per_slice", C.c_int), ("per_request", C.c_int)]
 
 
 class ipf_request(C.Structure):
@@ -111,6 +111,8 @@ SIGNATURES = {
     "ipf_submit": (C.c_int, [C.c_void_p, C.POINTER(ipf_request), C.POINTER(C.c_ulonglong)]),
     "ipf_poll": (C.c_int, [C.c_void_p, C.c_ulonglong, C.POINTER(ipf_result), C.c_void_p]),
     "ipf_server_stats": (C.c_int, [C.c_void_p, _ip, _ip, C.POINTER(C.c_size_t)]),
+    "ipf_server_batch_stats": (C.c_int, [C.c_void_p, _ip, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                                         C.POINTER(C.c_longlong)]),
     "ipf_server_destroy": (None, [C.c_void_p]),
 }
 
@@ -420,10 +422,11 @@ class Server:
     """ipf_server: continuous serving of many solves on one GPU."""
 
     def __init__(self, hbm_budget_bytes: int = 0, max_inflight: int = 64, steps_per_slice: int = 8,
-                 pinned_bytes: int = 0):
+                 pinned_bytes: int = 0, per_request: bool = False):
         self._lib = load()
         cfg = ipf_server_config(hbm_budget_bytes=int(hbm_budget_bytes), pinned_bytes=int(pinned_bytes),
-                                max_inflight=int(max_inflight), steps_per_slice=int(steps_per_slice))
+                                max_inflight=int(max_inflight), steps_per_slice=int(steps_per_slice),
+                                per_request=1 if per_request else 0)
         h = C.c_void_p()
         st = self._lib.ipf_server_create(C.byref(cfg), C.byref(h))
         if st != IPF_OK:
@@ -459,6 +462,13 @@ class Server:
         m = C.c_size_t(0)
         self._lib.ipf_server_stats(self.h, C.byref(a), C.byref(q), C.byref(m))
         return a.value, q.value, m.value
+
+    def batch_stats(self):
+        """(requests that took a batch slot, graph turns, eager turns, graph captures)."""
+        b = C.c_int(0)
+        g, e, c = C.c_longlong(0), C.c_longlong(0), C.c_longlong(0)
+        self._lib.ipf_server_batch_stats(self.h, C.byref(b), C.byref(g), C.byref(e), C.byref(c))
+        return b.value, g.value, e.value, c.value
 
     def close(self):
         if getattr(self, "h", None):

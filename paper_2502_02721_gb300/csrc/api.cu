@@ -1276,3 +1276,35 @@ ipf_status ipf_sketch_gaussian(int storage, unsigned long long seed, long long n
 }
 
 }  // extern "C"
+
+namespace ipf {
+
+// The batched step of the serving loop drives contexts whose every step is
+// one of the batched kernels: one RHS, float storage, the sparse-sign sketch
+// with its table and the deferred sketch, full pivoting, steps on one stream,
+// and a PSF on the FMA column path (kw 7, 15, 31; BF16 may use the tensor
+// cores) or a CSR matrix.  Fills d (k_target and the tile counts are left
+// to the caller) and returns true for such a context.
+bool ctx_slot_desc(ipf_ctx* c, SlotDesc* d, int* storage) {
+    if (!c || c->sticky != IPF_OK || c->gh || c->gauss || c->B != 1 || c->storage == IPF_STORE_F64) return false;
+    if (!c->defer_sketch || c->split || c->fork_piv || c->cfg.pivot_sample != 0 || sw_on(c)) return false;
+    if (c->op.kind == IPF_OP_PSF2D) {
+        if (!c->op.psf_pairs || (c->op.kw != 7 && c->op.kw != 15 && c->op.kw != 31)) return false;
+    } else if (c->op.kind != IPF_OP_CSR) {
+        return false;
+    }
+    memset(d, 0, sizeof(*d));
+    d->g = c->g;
+    d->bf = c->bf;
+    d->sp = c->sp;
+    d->op = c->op;
+    *storage = c->storage;
+    return true;
+}
+
+// the context's steps were taken by the batched step: k steps are enqueued
+void ctx_steps_taken(ipf_ctx* c, int k) {
+    if (c) c->j_host = k < c->g.k_max ? k : c->g.k_max;
+}
+
+}  // namespace ipf

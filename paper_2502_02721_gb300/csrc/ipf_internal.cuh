@@ -305,14 +305,32 @@ struct SlotDesc {
     int k_target;
     int norm_tiles;                // tiles of this slot in the normalise table (its last-tile ticket)
     int conv_cols;                 // operator tiles: PSF FMA path, tiles per image row of tiles; CSR 0
-    int tc_ct, tc_rows;            // tensor-core convolution: column tiles and output rows per unit
-    const void* tc_map;            // its 64-byte aligned CUtensorMap in device memory, or NULL
+    int tc_kp;                     // tensor-core convolution: KP (16 or 32), 0 for the other operators
+    int tc_ct, tc_rows;            // its column tiles and output rows per unit
 };
 
 struct TileRef {
     int slot;
     int tile;
 };
+
+// the slot's step index at the start of a phase (-1 if the slot takes no
+// step now), read by thread 0 and shared with the CTA; also a barrier
+// between the tiles a CTA takes
+__device__ __forceinline__ int slot_step(const SlotDesc* sd, int* s_j) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int j = -1;
+        if (sd->k_target > 0) {
+            const DevState* st = sd->bf.st;
+            j = st->j;
+            if (st->status[0] != IPF_OK || j >= sd->k_target || j >= sd->g.k_max) j = -1;
+        }
+        *s_j = j;
+    }
+    __syncthreads();
+    return *s_j;
+}
 
 // ---------------------------------------------------------------------------
 // launchers (defined in the .cu files)
@@ -383,8 +401,10 @@ cudaError_t launch_fixed_to_double(const long long* acc, int m, double scale, do
 cudaError_t launch_sketch_finish(const long long* acc, int m, long long n, int zeta, const unsigned* absmax,
                                  double* y, cudaStream_t s);
 // batched step (k_hess.cu, k_ops.cu, k_conv_tc.cu): one launch per phase for
-// every slot of the table; storage is the slots' common float storage type
-cudaError_t launch_batch_pivot_solve(int storage, const SlotDesc* slots, int nslots, int k_max, cudaStream_t s);
+// the slots of one float storage type
+// one CTA per entry of list (its slot field)
+cudaError_t launch_batch_pivot_solve(int storage, const SlotDesc* slots, const TileRef* list, int nslots, int k_max,
+                                     cudaStream_t s);
 cudaError_t launch_batch_update(int storage, const SlotDesc* slots, const TileRef* tiles, int ntiles, int k_max,
                                 int m_s_max, int num_sms, cudaStream_t s);
 cudaError_t launch_batch_normalize(int storage, const SlotDesc* slots, const TileRef* tiles, int ntiles, int num_sms,
@@ -392,10 +412,32 @@ cudaError_t launch_batch_normalize(int storage, const SlotDesc* slots, const Til
 // PSF (FMA column convolution, kw 7 / 15 / 31) and CSR products
 cudaError_t launch_batch_operator(int storage, const SlotDesc* slots, const TileRef* tiles, int ntiles, int num_sms,
                                   cudaStream_t s);
-// tensor-core convolution (BF16) of the slots with tc_map, units of one KP
-cudaError_t launch_batch_conv_tc(int kp, const SlotDesc* slots, const TileRef* units, int nunits, cudaStream_t s);
-// the tensor map of a slot's basis for the tensor-core convolution (host)
+// tensor-core convolution (BF16) of the slots with tc_kp == kp; maps: the
+// slots' tensor maps, kMaxSlots x conv_tc_map_bytes() bytes of host memory
+// (entry s for slot s, built by conv_tc_map)
+cudaError_t launch_batch_conv_tc(int kp, const void* maps, const SlotDesc* slots, const TileRef* units, int nunits,
+                                 cudaStream_t s);
 bool conv_tc_map(const OpDev& op, const void* vbase, long long ldv, long long vcols, void* map_out);
+size_t conv_tc_map_bytes();
+
+// api.cu: contexts the batched step can drive (see there)
+bool ctx_slot_desc(ipf_ctx* c, SlotDesc* d, int* storage);
+void ctx_steps_taken(ipf_ctx* c, int k);
+
+// batch.cu: the batched step of the serving loop (one engine per server,
+// used from its scheduler thread only)
+struct BatchEngine;
+BatchEngine* batch_create();
+void batch_destroy(BatchEngine* b);
+// put a context in a free slot to take k steps (its initialisation enqueued
+// before `ready`); returns the slot, or -1 if the context cannot be batched
+// or no slot is free
+int batch_add(BatchEngine* b, ipf_ctx* c, int k, cudaStream_t ready);
+void batch_remove(BatchEngine* b, int slot);
+int batch_steps(const BatchEngine* b, int slot);
+int batch_used(const BatchEngine* b);
+cudaError_t batch_run(BatchEngine* b, int steps, cudaEvent_t done);
+void batch_counters(const BatchEngine* b, long long* graph_turns, long long* eager_turns, long long* captures);
 
 // k_small.cu: workspace for k <= k_max and up to nl_max lambdas per chunk
 size_t solve_workspace_bytes(const Geom& g, int nl_max);

@@ -106,10 +106,12 @@ __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t (&r)[NP]) 
     }
 }
 
+// one unit (128 output columns x R output rows: column tile unit % CT, row
+// band unit / CT) of the convolution; vmap in parameter space
 template <int KP>
-__global__ void __launch_bounds__(kThreads, 1)
-    k_conv2d_tc(const __grid_constant__ CUtensorMap vmap, const int* __restrict__ jptr, float* __restrict__ w,
-                int H, int W, int R, int CT, const uint4* __restrict__ bimg, int* __restrict__ err) {
+__device__ __forceinline__ void conv_tc_body(const CUtensorMap* vmap, const int* __restrict__ jptr,
+                                             float* __restrict__ w, int H, int W, int R, int CT,
+                                             const uint4* __restrict__ bimg, int* __restrict__ err, int unit) {
     using S = TcShape<KP>;
     constexpr int KW = S::KW, NU = S::NU, NP = S::NP, N = S::N;
     constexpr int C = KW / 2;
@@ -136,7 +138,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     volatile int* s_abort = (volatile int*)(sm + kOffMisc + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ct = blockIdx.x % CT, sg = blockIdx.x / CT;
+    const int ct = unit % CT, sg = unit / CT;
     const int x0 = ct * 128, Y0 = sg * R;
     if (Y0 >= H) return;                                  // uniform for the CTA
     const int yEnd = min(Y0 + R, H);
@@ -176,7 +178,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int sl = t % kNSeg;
                 if (!mbar_wait(seg_empty(sl), ((t / kNSeg) & 1) ^ 1, s_abort, err)) break;
                 mbar_expect_tx(seg_full(sl), kSegBytes);
-                tma_load_3d(sbase + kOffSeg + sl * kSegBytes, &vmap, x0 - 16, Ys + t * kRB, z, seg_full(sl));
+                tma_load_3d(sbase + kOffSeg + sl * kSegBytes, vmap, x0 - 16, Ys + t * kRB, z, seg_full(sl));
                 issued = t + 1;
             }
             // every issued copy lands before the CTA may exit
@@ -319,6 +321,33 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+template <int KP>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_conv2d_tc(const __grid_constant__ CUtensorMap vmap, const int* __restrict__ jptr, float* __restrict__ w,
+                int H, int W, int R, int CT, const uint4* __restrict__ bimg, int* __restrict__ err) {
+    conv_tc_body<KP>(&vmap, jptr, w, H, W, R, CT, bimg, err, blockIdx.x);
+}
+
+// the batched step: one unit of one slot per CTA; every slot's tensor map
+// travels in the parameter struct
+struct TcMaps {
+    CUtensorMap m[kMaxSlots];
+};
+
+template <int KP>
+__global__ void __launch_bounds__(kThreads, 1)
+    kb_conv_tc(const __grid_constant__ TcMaps maps, const SlotDesc* __restrict__ slots,
+               const TileRef* __restrict__ units, int nunits) {
+    __shared__ int s_j;
+    if ((int)blockIdx.x >= nunits) return;
+    const TileRef tr = units[blockIdx.x];
+    const SlotDesc* sd = slots + tr.slot;
+    if (slot_step(sd, &s_j) < 0) return;                 // uniform for the CTA
+    DevState* st = sd->bf.st;
+    conv_tc_body<KP>(&maps.m[tr.slot], &st->j, (float*)sd->bf.w, sd->op.rows, sd->op.cols, sd->tc_rows, sd->tc_ct,
+                     (const uint4*)sd->op.psf_tc, &st->status[0], tr.tile);
+}
+
 
 template <int KP>
 cudaError_t launch_kp(const CUtensorMap& map, const int* jptr, float* w, int H, int W, const void* bimg, int* err,
@@ -405,6 +434,39 @@ cudaError_t launch_conv_tc(const OpDev& op, const void* vbase, long long ldv, lo
     if (op.tc_kp == 32) return launch_kp<32>(map, jptr, w, H, W, op.psf_tc, err, s);
     if (op.tc_kp == 16) return launch_kp<16>(map, jptr, w, H, W, op.psf_tc, err, s);
     return cudaErrorInvalidValue;
+}
+
+bool conv_tc_map(const OpDev& op, const void* vbase, long long ldv, long long vcols, void* map_out) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc || !conv_tc_eligible(op, vbase, ldv)) return false;
+    const int H = op.rows, W = op.cols;
+    const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)(vcols > 0 ? vcols : 1)};
+    const cuuint64_t strides[2] = {(cuuint64_t)W * 2, (cuuint64_t)ldv * 2};
+    const cuuint32_t box[3] = {(cuuint32_t)kSegW, (cuuint32_t)kRB, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc((CUtensorMap*)map_out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(vbase), dims, strides,
+               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+size_t conv_tc_map_bytes() { return sizeof(CUtensorMap); }
+
+cudaError_t launch_batch_conv_tc(int kp, const void* maps, const SlotDesc* slots, const TileRef* units, int nunits,
+                                 cudaStream_t s) {
+    if (nunits <= 0) return cudaSuccess;
+    const TcMaps& m = *(const TcMaps*)maps;
+    if (kp == 32) {
+        cudaError_t e = cudaFuncSetAttribute(kb_conv_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemRequest);
+        if (e != cudaSuccess) return e;
+        kb_conv_tc<32><<<nunits, kThreads, kSmemRequest, s>>>(m, slots, units, nunits);
+    } else if (kp == 16) {
+        cudaError_t e = cudaFuncSetAttribute(kb_conv_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemRequest);
+        if (e != cudaSuccess) return e;
+        kb_conv_tc<16><<<nunits, kThreads, kSmemRequest, s>>>(m, slots, units, nunits);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace ipf

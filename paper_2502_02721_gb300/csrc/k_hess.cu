@@ -1093,18 +1093,6 @@ cudaError_t launch_reset_state(DevState* st, cudaStream_t s) {
 // and the deferred sketch, so a solve gets the same bits whatever else is
 // in the batch and however its elements are tiled.
 // ------------------------------------------------------------------------
-// the slot's state at the start of a phase, read by thread 0 and shared
-__device__ __forceinline__ int slot_step(const SlotDesc* sd, int* s_j) {
-    __syncthreads();                                   // the previous tile is done with shared memory
-    if (threadIdx.x == 0) {
-        const DevState* st = sd->bf.st;
-        const int j = st->j;
-        *s_j = (st->status[0] == IPF_OK && j < sd->k_target && j < sd->g.k_max) ? j : -1;
-    }
-    __syncthreads();
-    return *s_j;
-}
-
 template <class T>
 __global__ void __launch_bounds__(256, 4) kb_update(const SlotDesc* __restrict__ slots,
                                                     const TileRef* __restrict__ tiles, int ntiles) {
@@ -1326,8 +1314,10 @@ __global__ void __launch_bounds__(256) kb_normalize(const SlotDesc* __restrict__
 }
 
 template <class T, class Acc>
-__global__ void __launch_bounds__(256) kb_pivot_solve(const SlotDesc* __restrict__ slots) {
-    const SlotDesc* sd = slots + blockIdx.x;
+__global__ void __launch_bounds__(256) kb_pivot_solve(const SlotDesc* __restrict__ slots,
+                                                      const TileRef* __restrict__ list) {
+    const SlotDesc* sd = slots + list[blockIdx.x].slot;
+    if (sd->k_target <= 0) return;
     const DevState* st = sd->bf.st;
     if (st->j >= sd->k_target) return;
     const Geom g = sd->g;
@@ -1567,14 +1557,15 @@ cudaError_t launch_sketch_finish(const long long* acc, int m, long long n, int z
 // ------------------------------------------------------------------------
 // batched step launchers
 // ------------------------------------------------------------------------
-cudaError_t launch_batch_pivot_solve(int storage, const SlotDesc* slots, int nslots, int k_max, cudaStream_t s) {
+cudaError_t launch_batch_pivot_solve(int storage, const SlotDesc* slots, const TileRef* list, int nslots, int k_max,
+                                     cudaStream_t s) {
     if (nslots <= 0) return cudaSuccess;
     const int K1 = k_max + 1;
     const size_t smem = lp_stride(k_max) * sizeof(double) + (size_t)(((K1 + 1) & ~1) + K1 + 1) * sizeof(double);
     auto go = [&](auto fn) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        fn<<<nslots, 256, smem, s>>>(slots);
+        fn<<<nslots, 256, smem, s>>>(slots, list);
         return cudaGetLastError();
     };
     switch (storage) {

@@ -255,19 +255,18 @@ __device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
     return (unsigned long long)__float_as_uint(lo) | ((unsigned long long)__float_as_uint(hi) << 32);
 }
 
+// one 128 x OY output tile (tile column bx, tile row by), 128 threads
 template <class T, int KW, int OY>
-__global__ void __launch_bounds__(128, 7) k_conv2d_c2(const T* __restrict__ vbase, long long ldv,
-                                                     const int* __restrict__ jptr, float* __restrict__ w, int H,
-                                                     int W, const unsigned long long* __restrict__ pairs) {
+__device__ __forceinline__ void conv_c2_tile(const T* __restrict__ v, float* __restrict__ w, int H, int W,
+                                             const unsigned long long* __restrict__ pairs, int bx, int by) {
     static_assert(OY % 2 == 0, "OY must be even");
-    const T* v = jptr ? vbase + (size_t)(*jptr) * ldv : vbase;
     constexpr int TX = 128, TY = OY;
     constexpr int IH = TY + KW - 1, IW = TX + KW - 1;
     constexpr int IWP = IW + 1;
     constexpr int NP = KW + 1;                        // packed pairs per PSF column
     extern __shared__ float s_in[];                   // IH x IWP
     const int c = KW / 2;
-    const int y0 = blockIdx.y * TY, x0 = blockIdx.x * TX;
+    const int y0 = by * TY, x0 = bx * TX;
     for (int t = threadIdx.x; t < IH * IW; t += blockDim.x) {
         const int a = t / IW, bb = t - a * IW;
         const int yy = y0 - c + a, xx = x0 - c + bb;
@@ -305,6 +304,14 @@ __global__ void __launch_bounds__(128, 7) k_conv2d_c2(const T* __restrict__ vbas
             if (yy + 1 < H) w[(size_t)(yy + 1) * W + xo] = __uint_as_float((unsigned)(acc[a2] >> 32));
         }
     }
+}
+
+template <class T, int KW, int OY>
+__global__ void __launch_bounds__(128, 7) k_conv2d_c2(const T* __restrict__ vbase, long long ldv,
+                                                     const int* __restrict__ jptr, float* __restrict__ w, int H,
+                                                     int W, const unsigned long long* __restrict__ pairs) {
+    const T* v = jptr ? vbase + (size_t)(*jptr) * ldv : vbase;
+    conv_c2_tile<T, KW, OY>(v, w, H, W, pairs, blockIdx.x, blockIdx.y);
 }
 
 // ------------------------------------------------------------------------
@@ -381,17 +388,15 @@ __global__ void __launch_bounds__(256) k_sep_motion(const T* __restrict__ vbase,
 // >= G pair classes inside a lane, smaller ones pair lanes g and g^o.  A
 // right-hand side therefore gets the same bits alone or in any batch.
 // ------------------------------------------------------------------------
+// rows row0, row0 + step, ... below row1, one warp per row
 template <class T, class Acc, int B>
-__global__ void __launch_bounds__(256) k_csr(const long long* __restrict__ rowptr, const int* __restrict__ colind,
-                                              const float* __restrict__ vals, long long m,
-                                              const T* __restrict__ vbase, long long ldv,
-                                              const int* __restrict__ jptr, Acc* __restrict__ w) {
-    const T* v = jptr ? vbase + (size_t)(*jptr) * ldv : vbase;
+__device__ __forceinline__ void csr_rows(const long long* __restrict__ rowptr, const int* __restrict__ colind,
+                                         const float* __restrict__ vals, const T* __restrict__ v,
+                                         Acc* __restrict__ w, long long row0, long long row1, long long step) {
     constexpr int G = 32 / B;
     const int lane = threadIdx.x & 31;
     const int g = lane / B, rr = lane - g * B;
-    const long long warps = (long long)gridDim.x * (blockDim.x / 32);
-    for (long long row = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32; row < m; row += warps) {
+    for (long long row = row0; row < row1; row += step) {
         const long long s = rowptr[row], e = rowptr[row + 1];
         Acc P[B];
 #pragma unroll
@@ -417,6 +422,17 @@ __global__ void __launch_bounds__(256) k_csr(const long long* __restrict__ rowpt
         for (int o = (G >= 2 ? G / 2 : 0); o >= 1; o >>= 1) acc = acc + __shfl_xor_sync(0xffffffffu, acc, o * B);
         if (g == 0) w[(size_t)row * B + rr] = acc;
     }
+}
+
+template <class T, class Acc, int B>
+__global__ void __launch_bounds__(256) k_csr(const long long* __restrict__ rowptr, const int* __restrict__ colind,
+                                              const float* __restrict__ vals, long long m,
+                                              const T* __restrict__ vbase, long long ldv,
+                                              const int* __restrict__ jptr, Acc* __restrict__ w) {
+    const T* v = jptr ? vbase + (size_t)(*jptr) * ldv : vbase;
+    const long long warps = (long long)gridDim.x * (blockDim.x / 32);
+    csr_rows<T, Acc, B>(rowptr, colind, vals, v, w, (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, m,
+                        warps);
 }
 
 template <class T, class Acc>
@@ -653,6 +669,59 @@ cudaError_t launch_op_apply_f32_plain(const OpDev& op, const float* v, float* w,
     if (e == cudaSuccess) k_interleave<<<blocks, 256, 0, s>>>(wi, w, m, nrhs, 1);
     cudaError_t e2 = cudaFreeAsync(tmp, s);
     return e != cudaSuccess ? e : (e2 != cudaSuccess ? e2 : cudaGetLastError());
+}
+
+// ------------------------------------------------------------------------
+// batched step: the products of every active slot of the work list whose
+// operator is a PSF on the FMA column path (kw 7, 15, 31) or a CSR matrix,
+// in one launch of 128-thread CTAs over the (slot, tile) table: a PSF tile
+// is one 128 x 16 output tile of k_conv2d_c2, a CSR tile kBatchCsrRows rows
+// of k_csr.  Same per-output arithmetic as those kernels.
+// ------------------------------------------------------------------------
+namespace {
+
+template <class T>
+__global__ void __launch_bounds__(128, 7) kb_operator(const SlotDesc* __restrict__ slots,
+                                                      const TileRef* __restrict__ tiles, int ntiles) {
+    __shared__ int s_j;
+    for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+        const TileRef tr = tiles[tt];
+        const SlotDesc* sd = slots + tr.slot;
+        const int j = slot_step(sd, &s_j);
+        if (j < 0) continue;
+        const T* v = (const T*)sd->bf.V + (size_t)j * sd->g.ldv;
+        float* w = (float*)sd->bf.w;
+        const OpDev& op = sd->op;
+        if (op.kind == IPF_OP_CSR) {
+            const long long r0 = (long long)tr.tile * kBatchCsrRows;
+            const long long r1 = min((long long)op.rows, r0 + kBatchCsrRows);
+            csr_rows<T, float, 1>(op.rowptr, op.colind, op.vals, v, w, r0 + threadIdx.x / 32, r1, blockDim.x / 32);
+        } else {
+            const int bx = tr.tile % sd->conv_cols, by = tr.tile / sd->conv_cols;
+            switch (op.kw) {
+                case 7: conv_c2_tile<T, 7, 16>(v, w, op.rows, op.cols, op.psf_pairs, bx, by); break;
+                case 15: conv_c2_tile<T, 15, 16>(v, w, op.rows, op.cols, op.psf_pairs, bx, by); break;
+                default: conv_c2_tile<T, 31, 16>(v, w, op.rows, op.cols, op.psf_pairs, bx, by); break;
+            }
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_batch_operator(int storage, const SlotDesc* slots, const TileRef* tiles, int ntiles, int num_sms,
+                                  cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    // the largest tile of conv_c2_tile: (16 + 30) x (128 + 31) floats for kw 31
+    const size_t smem = (size_t)(16 + 31 - 1) * (128 + 31) * sizeof(float);
+    const int blocks = ntiles < num_sms * 7 ? ntiles : num_sms * 7;
+    switch (storage) {
+        case IPF_STORE_F32: kb_operator<float><<<blocks, 128, smem, s>>>(slots, tiles, ntiles); break;
+        case IPF_STORE_BF16: kb_operator<__nv_bfloat16><<<blocks, 128, smem, s>>>(slots, tiles, ntiles); break;
+        case IPF_STORE_F16: kb_operator<__half><<<blocks, 128, smem, s>>>(slots, tiles, ntiles); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace ipf

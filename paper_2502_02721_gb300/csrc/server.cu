@@ -11,6 +11,15 @@
 // of Hessenberg steps whenever its previous slice has finished, enqueues the
 // projected solve and the copy of x to pinned host memory after the last
 // slice, and retires the request when that copy has landed.
+//
+// Requests the batched step can drive (one RHS, float storage, sparse-sign
+// sketch, full pivoting, a PSF on the FMA or tensor-core path or a CSR
+// matrix: see batch.cu) do not step on their own streams: each takes a slot
+// of the server's batch engine, and one turn of the engine advances every
+// slot by steps_per_slice steps with one launch per phase per step.  When a
+// slot has taken its k steps it leaves the batch and its solve runs on the
+// request's stream after that turn.  b is staged in pinned host memory that
+// the device reads directly, so admitting a request never waits for the GPU.
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -102,6 +111,8 @@ struct Job {
     std::vector<long long> rowptr;
     std::vector<int> colind;
     std::vector<float> b;
+    float* b_pin = nullptr;                 // pinned copy of b, read by the device
+    int slot = -1;                          // batch engine slot, or -1
     ipf_config cfg{};
     int k = 0;
     double lambda = 0.0;
@@ -138,8 +149,12 @@ struct ipf_server {
     std::thread worker;
     size_t reserved = 0;                     // footprints of active jobs
     int device = 0;
+    ipf::BatchEngine* eng = nullptr;         // the batched step (NULL with cfg.per_request)
+    std::deque<cudaEvent_t> turns;           // engine turns in flight
+    std::vector<cudaEvent_t> spare_ev;
     // statistics
     unsigned long long n_done = 0, n_rejected = 0;
+    int n_batched = 0;                       // requests that took a batch slot
 
     void loop();
     bool admit(Job* j);
@@ -150,6 +165,13 @@ bool ipf_server::admit(Job* j) {
     const size_t xb = sizeof(float) * (size_t)j->n * j->cfg.nrhs;
     j->x_pin = (float*)pinned.get(xb);
     if (!j->x_pin) return false;                       // wait for pinned space
+    j->b_pin = (float*)pinned.get(sizeof(float) * j->b.size());
+    if (!j->b_pin) {
+        pinned.put(j->x_pin);
+        j->x_pin = nullptr;
+        return false;
+    }
+    memcpy(j->b_pin, j->b.data(), sizeof(float) * j->b.size());
     if (cudaStreamCreateWithFlags(&j->us, cudaStreamNonBlocking) != cudaSuccess) {
         pinned.put(j->x_pin);
         j->x_pin = nullptr;
@@ -165,14 +187,18 @@ bool ipf_server::admit(Job* j) {
     // per step only adds launches and events (measured: lower capacity and
     // higher latency under load), so every request steps on one stream
     c.overlap = 0;
+    if (eng) c.use_graphs = 0;                         // steps come from the batch engine where it can
     ipf_ctx* ctx = nullptr;
-    ipf_status st = ipf_create(&j->op, j->b.data(), IPF_MEM_HOST, &c, &ctx);
+    // the device reads b from pinned host memory: no wait for the GPU here
+    ipf_status st = ipf_create(&j->op, j->b_pin, IPF_MEM_DEVICE, &c, &ctx);
     if (st == IPF_ERR_OOM || (st == IPF_OK && !(j->x_dev = (float*)arena.get(xb)))) {
         if (ctx) ipf_destroy(ctx);
         cudaStreamDestroy(j->us);
         j->us = nullptr;
         pinned.put(j->x_pin);
         j->x_pin = nullptr;
+        pinned.put(j->b_pin);
+        j->b_pin = nullptr;
         return false;                                  // try again when memory frees up
     }
     j->t_admit = now_s();
@@ -191,10 +217,20 @@ bool ipf_server::admit(Job* j) {
         retire(j);
         return true;
     }
+    // a request the batched step cannot drive steps on its own stream (eagerly)
+    if (eng) j->slot = ipf::batch_add(eng, ctx, j->k, j->us);
+    if (j->slot >= 0) ++n_batched;
     return true;
 }
 
 void ipf_server::retire(Job* j) {
+    if (j->slot >= 0) {
+        // still in the batch (an error or shutdown): drop it, and let the
+        // turns that read it finish first
+        ipf::batch_remove(eng, j->slot);
+        j->slot = -1;
+        for (cudaEvent_t ev : turns) cudaEventSynchronize(ev);
+    }
     if (j->ctx) {
         int kd = 0;
         ipf_status st = ipf_sync(j->ctx, &kd);
@@ -215,6 +251,8 @@ void ipf_server::retire(Job* j) {
     j->x_dev = nullptr;
     if (j->x_pin) pinned.put(j->x_pin);
     j->x_pin = nullptr;
+    if (j->b_pin) pinned.put(j->b_pin);
+    j->b_pin = nullptr;
     if (j->ev) cudaEventDestroy(j->ev);
     j->ev = nullptr;
     j->t_done = now_s();
@@ -259,9 +297,58 @@ void ipf_server::loop() {
                 }
             }
         }
+        // one turn of the batch engine (at most two in flight); slots that
+        // have taken their k steps leave the batch, and their solves (below)
+        // follow this turn on their own streams
+        if (eng) {
+            while (!turns.empty() && cudaEventQuery(turns.front()) == cudaSuccess) {
+                spare_ev.push_back(turns.front());
+                turns.pop_front();
+            }
+            if (ipf::batch_used(eng) > 0 && turns.size() < 2) {
+                cudaEvent_t ev = nullptr;
+                if (!spare_ev.empty()) {
+                    ev = spare_ev.back();
+                    spare_ev.pop_back();
+                } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+                    ev = nullptr;
+                }
+                const cudaError_t e = ev ? ipf::batch_run(eng, slice, ev) : cudaErrorMemoryAllocation;
+                worked = true;
+                if (ev) turns.push_back(ev);
+                for (auto& up : active) {
+                    Job* j = up.get();
+                    if (j->slot < 0) continue;
+                    if (e != cudaSuccess) {
+                        ipf::batch_remove(eng, j->slot);
+                        j->slot = -1;
+                        j->status = IPF_ERR_CUDA;
+                        j->enqueued = j->k;
+                        continue;
+                    }
+                    if (ipf::batch_steps(eng, j->slot) < j->k) continue;
+                    ipf::batch_remove(eng, j->slot);
+                    j->slot = -1;
+                    cudaStreamWaitEvent(j->us, ev, 0);
+                    ipf::ctx_steps_taken(j->ctx, j->k);
+                    j->enqueued = j->k;
+                }
+            }
+        }
         // top up every in-flight request whose previous work has finished
         for (size_t a = 0; a < active.size();) {
             Job* j = active[a].get();
+            if (j->slot >= 0) { ++a; continue; }         // advanced by the batch engine
+            if (j->status < 0 && !j->solving) {
+                retire(j);
+                std::lock_guard<std::mutex> lk(mu);
+                reserved -= j->footprint;
+                ++n_done;
+                done[j->ticket] = std::move(active[a]);
+                active.erase(active.begin() + a);
+                cv.notify_all();
+                continue;
+            }
             const bool idle = j->enqueued == 0 || cudaEventQuery(j->ev) == cudaSuccess;
             if (!idle) { ++a; continue; }
             worked = true;
@@ -328,10 +415,15 @@ ipf_status ipf_server_create(const ipf_server_config* cfg, ipf_server** out) {
         s->cfg.hbm_budget_bytes = fr / 10 * 8;
     }
     if (!s->arena.init(s->cfg.hbm_budget_bytes)) return IPF_ERR_OOM;
-    if (s->cfg.pinned_bytes == 0) s->cfg.pinned_bytes = (size_t)512 << 20;
+    if (s->cfg.pinned_bytes == 0) s->cfg.pinned_bytes = (size_t)1 << 30;
     if (!s->pinned.init(s->cfg.pinned_bytes, true)) {
         s->arena.release();
         return IPF_ERR_OOM;
+    }
+    if (!s->cfg.per_request && !(s->eng = ipf::batch_create())) {
+        s->arena.release();
+        s->pinned.release();
+        return IPF_ERR_CUDA;
     }
     ipf_server* raw = s.release();
     raw->worker = std::thread([raw] { raw->loop(); });
@@ -439,6 +531,20 @@ ipf_status ipf_poll(ipf_server* s, unsigned long long ticket, ipf_result* res, f
     return st;
 }
 
+ipf_status ipf_server_batch_stats(ipf_server* s, int* batched, long long* graph_turns, long long* eager_turns,
+                                  long long* captures) {
+    if (!s) return IPF_ERR_ARG;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (batched) *batched = s->n_batched;
+    ipf::batch_counters(s->eng, graph_turns, eager_turns, captures);
+    if (!s->eng) {
+        if (graph_turns) *graph_turns = 0;
+        if (eager_turns) *eager_turns = 0;
+        if (captures) *captures = 0;
+    }
+    return IPF_OK;
+}
+
 ipf_status ipf_server_stats(ipf_server* s, int* inflight, int* queued, size_t* hbm_in_use) {
     if (!s) return IPF_ERR_ARG;
     std::lock_guard<std::mutex> lk(s->mu);
@@ -458,6 +564,9 @@ void ipf_server_destroy(ipf_server* s) {
     s->done.clear();
     s->pending.clear();
     cudaDeviceSynchronize();
+    for (cudaEvent_t ev : s->turns) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : s->spare_ev) cudaEventDestroy(ev);
+    ipf::batch_destroy(s->eng);
     s->arena.release();
     s->pinned.release();
     delete s;

@@ -1,7 +1,14 @@
 """Serving (ipf_server_*): requests of different operators and sizes are
 admitted while others run, overlap on the GPU, and each result equals the
 same solve run alone through ipf_create/ipf_step/ipf_solve (the kernels of
-one context do not depend on what else runs, so the bits agree)."""
+one context do not depend on what else runs, so the bits agree).
+
+With the batched step (the default), the requests it can drive share one
+launch per phase per step: each result must be bit-identical served alone
+and served in a mix of requests of other sizes, operators and k; on the FMA
+column convolution and the CSR product it must also equal the solve alone
+through a context; on the tensor-core convolution too, when the tuner's
+choice is pinned to the band height the context uses."""
 import time
 
 import numpy as np
@@ -40,15 +47,15 @@ def _op(bd, r, keep):
     return bd.make_operator("csr", n, n, rowptr=r["rowptr"], colind=r["colind"], vals=r["vals"], keep=keep)
 
 
-def test_served_results_equal_solves_alone():
-    ensure_lib()
-    from paper_2502_02721_gb300 import binding as bd
-    reqs = _requests()
-    keep = []
-    srv = bd.Server(hbm_budget_bytes=2 << 30, max_inflight=6, steps_per_slice=4)
+def _serve(bd, reqs, keep, per_request=False, max_inflight=6, steps_per_slice=4, extra=None):
+    """Submit all requests at once; returns the results by request index and
+    the server's batch statistics."""
+    srv = bd.Server(hbm_budget_bytes=2 << 30, max_inflight=max_inflight, steps_per_slice=steps_per_slice,
+                    per_request=per_request)
     tickets = []
     for r in reqs:
-        cfg = bd.default_config(k_max=r["k"], m_s=r["m_s"], zeta=8, seed=r["seed"], storage=r["storage"])
+        cfg = bd.default_config(k_max=r["k"], m_s=r["m_s"], zeta=8, seed=r["seed"], storage=r["storage"],
+                                **(extra or {}))
         tickets.append(srv.submit(_op(bd, r, keep), r["b"], cfg, r["k"], r["lam"]))
     results = {}
     t0 = time.time()
@@ -59,8 +66,31 @@ def test_served_results_equal_solves_alone():
                 if out is not None:
                     results[t] = out
         time.sleep(0.002)
+    stats = srv.batch_stats()
     srv.close()
     assert len(results) == len(tickets)
+    return [results[t] for t in tickets], stats
+
+
+def _alone(bd, r, keep, **extra):
+    cfg = bd.default_config(k_max=r["k"], m_s=r["m_s"], zeta=8, seed=r["seed"], storage=r["storage"], overlap=0,
+                            **extra)
+    ctx = bd.Context(_op(bd, r, keep), r["b"], cfg, keep)
+    ctx.step(r["k"])
+    xa, _ = ctx.solve(r["k"], [r["lam"]])
+    ctx.close()
+    return xa[0]
+
+
+def test_served_results_equal_solves_alone():
+    ensure_lib()
+    from paper_2502_02721_gb300 import binding as bd
+    reqs = _requests()
+    keep = []
+    res, stats = _serve(bd, reqs, keep, per_request=True)
+    assert stats[0] == 0                               # no request took the batched step
+    results = {i: r for i, r in enumerate(res)}
+    tickets = list(range(len(reqs)))
     # several requests were on the GPU at the same time
     spans = [(results[t][2][1], results[t][2][2]) for t in tickets]
     overlapping = sum(1 for i, a in enumerate(spans) for b in spans[i + 1:] if a[0] < b[1] and b[0] < a[1])
@@ -70,13 +100,69 @@ def test_served_results_equal_solves_alone():
         assert status == bd.IPF_OK and k_used == r["k"]
         # the server steps every request on one stream (overlap 0), so the
         # solve alone uses the same step
-        cfg = bd.default_config(k_max=r["k"], m_s=r["m_s"], zeta=8, seed=r["seed"], storage=r["storage"],
-                                overlap=0)
-        ctx = bd.Context(_op(bd, r, keep), r["b"], cfg, keep)
-        ctx.step(r["k"])
-        xa, _ = ctx.solve(r["k"], [r["lam"]])
-        ctx.close()
-        assert np.array_equal(x, xa[0]), (r["kind"], r["storage"])
+        assert np.array_equal(x, _alone(bd, r, keep)), (r["kind"], r["storage"])
+
+
+def test_batched_results_alone_and_in_the_mix():
+    """The batched step: every request served alone (one at a time) and in
+    the mix (all at once, six in flight, so requests of different sizes,
+    operators, k and step counts share launches) gives the same bits; the
+    mix ran in batch slots, partly from captured graphs."""
+    ensure_lib()
+    from paper_2502_02721_gb300 import binding as bd
+    reqs = _requests()
+    keep = []
+    mix, stats = _serve(bd, reqs, keep)
+    assert stats[0] == len(reqs)                       # every request took a batch slot
+    assert stats[1] + stats[2] > 0
+    for i, r in enumerate(reqs):
+        (one,), _ = _serve(bd, [r], keep, max_inflight=1)
+        assert mix[i][0] == bd.IPF_OK and one[0] == bd.IPF_OK and mix[i][1] == r["k"]
+        assert np.array_equal(mix[i][3], one[3]), (i, r["kind"], r["storage"])
+
+
+def test_batched_fma_and_csr_equal_the_context():
+    """FMA column convolution (BF16 with conv_fma, and FP32) and CSR: the
+    batched step computes each element as the one-context kernels do, so the
+    served x equals the context's x bit for bit."""
+    ensure_lib()
+    from paper_2502_02721_gb300 import binding as bd
+    reqs = _requests()
+    keep = []
+    res, stats = _serve(bd, reqs, keep, extra={"conv_fma": 1})
+    assert stats[0] == len(reqs)
+    for r, out in zip(reqs, res):
+        assert out[0] == bd.IPF_OK
+        assert np.array_equal(out[3], _alone(bd, r, keep, conv_fma=1)), (r["kind"], r["storage"])
+
+
+def test_batched_tensor_cores_equal_the_context(tmp_path, monkeypatch):
+    """BF16 PSF requests on the tensor-core convolution, with the tuner's
+    choice pinned (IPF_TUNE_CACHE) to the band height a context uses on a
+    64 x 64 image (32 output rows per CTA): the served x equals the
+    context's x bit for bit."""
+    ensure_lib()
+    from paper_2502_02721_gb300 import binding as bd
+    cache = tmp_path / "tune.json"
+    cache.write_text('{"version": 1, "entries": [\n'
+                     '  {"key": "bf16/psf/kw15/64x64", "conv": "tc", "rows": 32, "us": 1.0},\n'
+                     '  {"key": "bf16/psf/kw31/64x64", "conv": "tc", "rows": 32, "us": 1.0}\n]}\n')
+    monkeypatch.setenv("IPF_TUNE_CACHE", str(cache))
+    rng = np.random.default_rng(23)
+    reqs = []
+    for t, sigma in enumerate((1.5, 2.0, 3.0, 3.5)):
+        psf = P.gaussian_psf(2 * int(np.ceil(3 * sigma)) + 1, sigma)
+        x = P.ellipse_phantom(64, 64, 6, rng)
+        b = P.add_noise(P.blur_fft(x, psf), 0.01, rng).astype(np.float32)
+        k = 12 + 3 * t
+        reqs.append(dict(kind="psf2d", rows=64, cols=64, psf=psf, b=b.reshape(1, -1), k=k, m_s=4 * k, lam=1e-3,
+                         storage="bf16", seed=3000 + t))
+    keep = []
+    res, stats = _serve(bd, reqs, keep)
+    assert stats[0] == len(reqs)
+    for r, out in zip(reqs, res):
+        assert out[0] == bd.IPF_OK
+        assert np.array_equal(out[3], _alone(bd, r, keep)), r["psf"].shape
 
 
 def test_server_rejects_what_can_never_fit():
