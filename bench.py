@@ -819,23 +819,27 @@ def run_small(storage: str):
     plus work vector exceed L2) with eager launches: the ncu target.
     storage "gauss": the same with a BF16 basis and the Gaussian sketch (S is
     256 x 1024^2 BF16, 0.5 GB), whose solve runs the tensor-core
-    contraction [S V_{k+1} | S b]."""
+    contraction [S V_{k+1} | S b]; "gauss800": the Gaussian sketch with the
+    shape of the 2048^2 workload's contraction (m_s = 800, k = 200: four row
+    groups of S, 201 basis columns) on the 1024^2 image (S 1.7 GB)."""
     import torch
     from gen import problems as P
     from paper_2502_02721_gb300 import binding as bd, build as bl
     if not os.path.exists(bl.lib_path()):
         bl.build()
     torch.cuda.set_device(0)
-    p = P.deblur_moffat(side=1024, k=64, m_s=256)
+    kk, ms = (200, 800) if storage == "gauss800" else (64, 256)
+    p = P.deblur_moffat(side=1024, k=kk, m_s=ms)
     keep = []
     op = bd.operator_from_problem(p, keep)
-    extra = {"sketch": "gaussian"} if storage == "gauss" else {}
-    cfg = bd.default_config(k_max=64, m_s=256, zeta=8, seed=p.sketch_seed,
-                            storage="bf16" if storage == "gauss" else storage, use_graphs=0, **extra)
+    gauss = storage.startswith("gauss")
+    extra = {"sketch": "gaussian"} if gauss else {}
+    cfg = bd.default_config(k_max=kk, m_s=ms, zeta=8, seed=p.sketch_seed,
+                            storage="bf16" if gauss else storage, use_graphs=0, **extra)
     ctx = bd.Context(op, p.b, cfg, keep)
-    ctx.step(64)
-    x, info = ctx.solve(64, [0.0, 1e-3])
-    print(json.dumps({"small_case": "deblur1024 moffat31 k=64 m_s=256", "storage": storage, "info": info,
+    ctx.step(kk)
+    x, info = ctx.solve(kk, [0.0, 1e-3])
+    print(json.dumps({"small_case": f"deblur1024 moffat31 k={kk} m_s={ms}", "storage": storage, "info": info,
                       "x_norm": float(np.linalg.norm(x[0, 0]))}))
     ctx.close()
 
@@ -859,7 +863,7 @@ def main():
                     help="serve without the batched step (each request on its own streams)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the CT 32-RHS batch and the 5 s serving run on the default line")
-    ap.add_argument("--small", default=None, choices=["f32", "bf16", "f16", "f64", "gauss"],
+    ap.add_argument("--small", default=None, choices=["f32", "bf16", "f16", "f64", "gauss", "gauss800"],
                     help="run one small solve (profiling target) and exit")
     args = ap.parse_args()
     if args.small:

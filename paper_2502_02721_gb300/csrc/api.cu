@@ -283,6 +283,7 @@ struct ipf_ctx {
     void* gSV = nullptr;
     double* gC = nullptr;
     void* gWs = nullptr;
+    int gvariant = 0;                   // the contraction's pipeline (gauss_variant)
     OpDev opT;
     Geom g2;
     Bufs bf2;
@@ -778,6 +779,8 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
         CK("alloc Gaussian workspace", c->al.get(&c->gWs, wsb));
         CK("memset Gaussian workspace", cudaMemsetAsync(c->gWs, 0, wsb, c->s));
         CK("Gaussian S", launch_gauss_fill(cfg.storage, c->gS, n, cfg.m_s, gauss_lds(n), cfg.seed, c->num_sms, c->s));
+        c->gvariant = gauss_variant(cfg.storage, c->gS, cfg.m_s, n, c->bf.V, c->g.ldv, cfg.k_max + 1, c->gWs, c->gSV,
+                                    c->gC, &c->bf.st->status[0], c->num_sms, c->s);
     }
     c->solve_ws_bytes = solve_ws_for(g);
     CK("alloc solve", c->al.get(&c->solve_ws, c->solve_ws_bytes));
@@ -955,7 +958,7 @@ static ipf_status solve_impl(ipf_ctx* c, int k, const double* lambdas, int nl, f
         const double gb = (double)g.m_s * g.n * sb + (double)g.n * (k + 1) * sb;
         e = timed(c, 9, gb, [&] {
             return launch_gauss_sv(c->storage, c->gS, g.m_s, g.n, c->bf.V, g.ldv, g.k_max + 1, k + 1, c->gWs, c->gSV,
-                                   c->gC, &c->bf.st->status[0], c->num_sms, c->s);
+                                   c->gC, &c->bf.st->status[0], c->num_sms, c->gvariant, c->s);
         });
         if (e != cudaSuccess) return cuda_fail(c, "Gaussian sketch contraction", e);
         bz.svd = c->gSV;

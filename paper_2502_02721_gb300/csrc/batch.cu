@@ -33,9 +33,9 @@ namespace {
 // autotuner
 // ---------------------------------------------------------------------------
 struct TuneChoice {
-    int tc = 0;          // 1: tensor-core convolution, 0: FMA column convolution
-    int rows = 0;        // output rows per tensor-core unit
-    double us = 0.0;     // time of the chosen variant per product
+    int variant = 0;     // which kernel (e.g. 1: tensor-core convolution, 0: FMA)
+    int param = 0;       // its tile parameter (e.g. output rows per unit)
+    double us = 0.0;     // time of the chosen variant
 };
 
 struct Tuner {
@@ -60,7 +60,7 @@ struct Tuner {
         size_t got;
         while ((got = fread(buf, 1, sizeof buf, f)) > 0) text.append(buf, got);
         fclose(f);
-        // entries: {"key": "...", "conv": "tc"|"fma", "rows": R, "us": T}
+        // entries: {"key": "...", "variant": V, "param": P, "us": T}
         size_t at = 0;
         while ((at = text.find("\"key\": \"", at)) != std::string::npos) {
             at += 8;
@@ -68,12 +68,12 @@ struct Tuner {
             if (end == std::string::npos) break;
             const std::string key = text.substr(at, end - at);
             TuneChoice c;
-            const size_t cv = text.find("\"conv\": \"", end);
-            const size_t rw = text.find("\"rows\": ", end);
+            const size_t va = text.find("\"variant\": ", end);
+            const size_t pa = text.find("\"param\": ", end);
             const size_t us = text.find("\"us\": ", end);
-            if (cv == std::string::npos || rw == std::string::npos || us == std::string::npos) break;
-            c.tc = text.compare(cv + 9, 2, "tc") == 0 ? 1 : 0;
-            c.rows = atoi(text.c_str() + rw + 8);
+            if (va == std::string::npos || pa == std::string::npos || us == std::string::npos) break;
+            c.variant = atoi(text.c_str() + va + 11);
+            c.param = atoi(text.c_str() + pa + 9);
             c.us = atof(text.c_str() + us + 6);
             table[key] = c;
             at = end;
@@ -88,8 +88,9 @@ struct Tuner {
         fprintf(f, "{\"version\": 1, \"entries\": [\n");
         size_t i = 0;
         for (const auto& kv : table) {
-            fprintf(f, "  {\"key\": \"%s\", \"conv\": \"%s\", \"rows\": %d, \"us\": %.3f}%s\n", kv.first.c_str(),
-                    kv.second.tc ? "tc" : "fma", kv.second.rows, kv.second.us, ++i < table.size() ? "," : "");
+            fprintf(f, "  {\"key\": \"%s\", \"variant\": %d, \"param\": %d, \"us\": %.3f}%s\n",
+                    kv.first.c_str(), kv.second.variant, kv.second.param, kv.second.us,
+                    ++i < table.size() ? "," : "");
         }
         fprintf(f, "]}\n");
         fclose(f);
@@ -104,7 +105,7 @@ Tuner& tuner() {
 
 std::string tune_key(int storage, const OpDev& op) {
     char b[96];
-    snprintf(b, sizeof b, "%s/psf/kw%d/%dx%d", storage == IPF_STORE_BF16 ? "bf16" : "other", op.kw, op.rows,
+    snprintf(b, sizeof b, "conv/%s/kw%d/%dx%d", storage == IPF_STORE_BF16 ? "bf16" : "other", op.kw, op.rows,
              op.cols);
     return b;
 }
@@ -112,6 +113,29 @@ std::string tune_key(int storage, const OpDev& op) {
 int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 }  // namespace
+
+bool tune_lookup(const char* key, int* variant, int* param) {
+    Tuner& tn = tuner();
+    std::lock_guard<std::mutex> lk(tn.mu);
+    tn.load();
+    auto it = tn.table.find(key);
+    if (it == tn.table.end()) return false;
+    *variant = it->second.variant;
+    *param = it->second.param;
+    return true;
+}
+
+void tune_store(const char* key, int variant, int param, double us) {
+    Tuner& tn = tuner();
+    std::lock_guard<std::mutex> lk(tn.mu);
+    tn.load();
+    TuneChoice c;
+    c.variant = variant;
+    c.param = param;
+    c.us = us;
+    tn.table[key] = c;
+    tn.save();
+}
 
 // ---------------------------------------------------------------------------
 // the engine
@@ -310,9 +334,9 @@ struct BatchEngine {
             tn.load();
             auto it = tn.table.find(key);
             if (it != tn.table.end()) {
-                if (it->second.tc) {
+                if (it->second.variant == 1 && it->second.param > 0) {
                     d->tc_kp = d->op.tc_kp;
-                    d->tc_rows = it->second.rows;
+                    d->tc_rows = it->second.param;
                 }
                 return cudaSuccess;
             }
@@ -331,8 +355,8 @@ struct BatchEngine {
             if ((e = time_variant(i, c, &ms)) != cudaSuccess) return e;
             if (ms * 1e3 < best.us) {
                 best.us = ms * 1e3;
-                best.tc = 1;
-                best.rows = rows;
+                best.variant = 1;
+                best.param = rows;
             }
         }
         {
@@ -340,9 +364,9 @@ struct BatchEngine {
             tn.table[key] = best;
             tn.save();
         }
-        if (best.tc) {
+        if (best.variant == 1) {
             d->tc_kp = d->op.tc_kp;
-            d->tc_rows = best.rows;
+            d->tc_rows = best.param;
         }
         return cudaSuccess;
     }

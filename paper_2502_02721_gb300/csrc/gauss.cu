@@ -19,6 +19,7 @@
 // slices in FP64 in a fixed order (so the result does not depend on
 // scheduling).  FP32 / FP64 storage use a CUDA-core kernel of the same
 // structure (k_gauss_simt; FP32 / FP64 accumulation).
+#include <cstdio>
 #include <type_traits>
 
 #include "tc_common.cuh"
@@ -161,24 +162,44 @@ __global__ void k_gauss_bparts(const float* __restrict__ b, long long n, long lo
 // frees TMEM, writes nothing and records IPF_ERR_TIMEOUT.
 // ---------------------------------------------------------------------------
 constexpr int kGmThreads = 192;
-constexpr int kGmBK = 64;
-constexpr int kGmStages = 3;
-constexpr int kGmATile = 128 * 128;
 constexpr int kGmBRowsMax = 256;
-constexpr int kGmStageBytes = 2 * kGmATile + kGmBRowsMax * 128;
-constexpr int kGmOffBar = kGmStages * kGmStageBytes;
-constexpr int kGmNBar = 2 * kGmStages + 1;
-constexpr int kGmOffMisc = kGmOffBar + 8 * kGmNBar;
-constexpr int kGmSmemRequest = kGmOffMisc + 16 + 1024;
 constexpr int kGmBRows = 8;          // rows of the b block: 3 parts + 5 zero rows
-static_assert(kGmSmemRequest <= 227 * 1024, "shared memory per CTA");
-static_assert(kGmStageBytes % 1024 == 0 && kGmATile % 1024 == 0, "swizzle atoms stay 1024-byte aligned");
+constexpr int kGmChunkAlign = 64;    // slices start at multiples of 64 elements
 
-template <bool BF16>
+// the two pipelines: BK K elements per stage (one swizzle row of 2 BK
+// bytes), the stage slots fixed for the largest B
+template <int BK> struct GmShape {
+    static_assert(BK == 64 || BK == 32, "stage width");
+    static constexpr int kRowBytes = 2 * BK;                    // 128 or 64: the swizzle span
+    static constexpr int kStages = BK == 64 ? 3 : 7;
+    static constexpr int kATile = 128 * kRowBytes;
+    static constexpr int kStageBytes = 2 * kATile + kGmBRowsMax * kRowBytes;
+    static constexpr int kOffBar = kStages * kStageBytes;
+    static constexpr int kNBar = 2 * kStages + 1;
+    static constexpr int kOffMisc = kOffBar + 8 * kNBar;
+    static constexpr int kSmemRequest = kOffMisc + 16 + 1024;
+    static_assert(kSmemRequest <= 227 * 1024, "shared memory per CTA");
+    static_assert(kStageBytes % 1024 == 0 && kATile % 1024 == 0, "swizzle atoms stay aligned");
+};
+
+// shared-memory descriptor of a K-major tile in the stage's swizzle
+template <int BK> __device__ __forceinline__ unsigned long long gm_desc(uint32_t addr);
+template <> __device__ __forceinline__ unsigned long long gm_desc<64>(uint32_t addr) { return smem_desc_sw128(addr); }
+template <> __device__ __forceinline__ unsigned long long gm_desc<32>(uint32_t addr) { return smem_desc_sw64(addr); }
+
+template <bool BF16, int BK>
 __global__ void __launch_bounds__(kGmThreads, 1)
     k_gauss_mma(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensorMap vmap,
                 const __grid_constant__ CUtensorMap bmap, long long n, int m, long long chunk, int mg, int Nv,
                 int Ntot, float* __restrict__ part, int m_pad, int* __restrict__ err) {
+    using G = GmShape<BK>;
+    constexpr int kGmBK = BK;
+    constexpr int kGmStages = G::kStages;
+    constexpr int kGmATile = G::kATile;
+    constexpr int kGmStageBytes = G::kStageBytes;
+    constexpr int kGmOffBar = G::kOffBar;
+    constexpr int kGmOffMisc = G::kOffMisc;
+    constexpr int kRow = G::kRowBytes;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(sm);
@@ -217,7 +238,7 @@ __global__ void __launch_bounds__(kGmThreads, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            const uint32_t bytes = (uint32_t)(ntile * kGmATile + Ntot * 128);
+            const uint32_t bytes = (uint32_t)(ntile * kGmATile + Ntot * kRow);
             int issued = 0;
             for (int kb = 0; kb < nkb; ++kb) {
                 const int s = kb % kGmStages;
@@ -227,7 +248,7 @@ __global__ void __launch_bounds__(kGmThreads, 1)
                 const uint32_t st = sbase + (uint32_t)(s * kGmStageBytes);
                 for (int t = 0; t < ntile; ++t) tma_load_2d(st + t * kGmATile, &smap, x, row0 + 128 * t, full(s));
                 tma_load_2d(st + 2 * kGmATile, &vmap, x, 0, full(s));
-                tma_load_2d(st + 2 * kGmATile + Nv * 128, &bmap, x, 0, full(s));
+                tma_load_2d(st + 2 * kGmATile + Nv * kRow, &bmap, x, 0, full(s));
                 issued = kb + 1;
             }
             // every issued copy lands before the CTA may exit
@@ -245,8 +266,8 @@ __global__ void __launch_bounds__(kGmThreads, 1)
                 for (int t = 0; t < ntile; ++t) {
 #pragma unroll
                     for (int kk = 0; kk < kGmBK / 16; ++kk)
-                        mma_bf16(tmem + (uint32_t)(t * Ntot), smem_desc_sw128(st + t * kGmATile + kk * 32),
-                                 smem_desc_sw128(st + 2 * kGmATile + kk * 32), idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                        mma_bf16(tmem + (uint32_t)(t * Ntot), gm_desc<BK>(st + t * kGmATile + kk * 32),
+                                 gm_desc<BK>(st + 2 * kGmATile + kk * 32), idesc, (kb > 0 || kk > 0) ? 1u : 0u);
                 }
                 mma_commit(empty(s));
             }
@@ -348,7 +369,7 @@ void split_plan(long long n, int groups, int num_sms, long long* chunk, int* nsp
     int target = num_sms / groups;
     if (target < 1) target = 1;
     long long ch = (n + target - 1) / target;
-    ch = (ch + kGmBK - 1) / kGmBK * kGmBK;
+    ch = (ch + kGmChunkAlign - 1) / kGmChunkAlign * kGmChunkAlign;
     *chunk = ch;
     *nsplit = (int)((n + ch - 1) / ch);
 }
@@ -416,7 +437,8 @@ cudaError_t launch_gauss_bparts(int storage, const float* b, long long n, void* 
 // FP32) and c (m, FP64).  ws: the workspace of gauss_workspace_bytes (the b
 // rows written by launch_gauss_bparts first, then the partial tiles).
 cudaError_t launch_gauss_sv(int storage, const void* S, int m, long long n, const void* V, long long ldv, int kcols,
-                            int K1, void* ws, void* svd, double* c, int* err, int num_sms, cudaStream_t s) {
+                            int K1, void* ws, void* svd, double* c, int* err, int num_sms, int variant,
+                            cudaStream_t s) {
     if (K1 < 1 || K1 > kcols || m < 1 || n < 1) return cudaErrorInvalidValue;
     const long long lds = gauss_lds(n);
     const size_t sb = storage == IPF_STORE_F64 ? 8 : storage == IPF_STORE_F32 ? 4 : 2;
@@ -429,6 +451,7 @@ cudaError_t launch_gauss_sv(int storage, const void* S, int m, long long n, cons
         if (!enc) return cudaErrorNotSupported;
         const int Nv = v_rows(K1), Ntot = Nv + kGmBRows;
         if (Ntot > kGmBRowsMax) return cudaErrorInvalidValue;
+        const int BK = variant == 32 ? 32 : 64;
         const int mg = m_pad / 256;
         long long chunk;
         int nsplit;
@@ -440,27 +463,28 @@ cudaError_t launch_gauss_sv(int storage, const void* S, int m, long long n, cons
         auto make = [&](CUtensorMap* map, const void* base, cuuint64_t rows, cuuint64_t ld, cuuint32_t box_rows) {
             const cuuint64_t dims[2] = {(cuuint64_t)n, rows};
             const cuuint64_t strides[1] = {ld * 2};
-            const cuuint32_t box[2] = {(cuuint32_t)kGmBK, box_rows};
+            const cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
             return enc(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                       CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                       BK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         };
         if (make(&smap, S, (cuuint64_t)m, (cuuint64_t)lds, 128) != CUDA_SUCCESS ||
             make(&vmap, V, (cuuint64_t)kcols, (cuuint64_t)ldv, (cuuint32_t)Nv) != CUDA_SUCCESS ||
             make(&bmap, bpart, (cuuint64_t)kGmBRows, (cuuint64_t)lds, kGmBRows) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
-        const int bi = storage == IPF_STORE_BF16 ? 1 : 0;
-        const cudaError_t attr =
-            bi ? cudaFuncSetAttribute(k_gauss_mma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGmSmemRequest)
-               : cudaFuncSetAttribute(k_gauss_mma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kGmSmemRequest);
-        if (attr != cudaSuccess) return attr;
-        if (bi)
-            k_gauss_mma<true><<<nsplit * mg, kGmThreads, kGmSmemRequest, s>>>(smap, vmap, bmap, n, m, chunk, mg, Nv,
-                                                                            Ntot, (float*)part, m_pad, err);
-        else
-            k_gauss_mma<false><<<nsplit * mg, kGmThreads, kGmSmemRequest, s>>>(smap, vmap, bmap, n, m, chunk, mg, Nv,
-                                                                             Ntot, (float*)part, m_pad, err);
-        cudaError_t e = cudaGetLastError();
+        auto go = [&](auto kern, int smem) -> cudaError_t {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            kern<<<nsplit * mg, kGmThreads, smem, s>>>(smap, vmap, bmap, n, m, chunk, mg, Nv, Ntot, (float*)part,
+                                                      m_pad, err);
+            return cudaGetLastError();
+        };
+        const bool bf = storage == IPF_STORE_BF16;
+        cudaError_t e;
+        if (BK == 64) e = bf ? go(k_gauss_mma<true, 64>, GmShape<64>::kSmemRequest)
+                             : go(k_gauss_mma<false, 64>, GmShape<64>::kSmemRequest);
+        else e = bf ? go(k_gauss_mma<true, 32>, GmShape<32>::kSmemRequest)
+                    : go(k_gauss_mma<false, 32>, GmShape<32>::kSmemRequest);
         if (e != cudaSuccess) return e;
         const long long th = (long long)m * (K1 + 1);
         k_gauss_reduce<float><<<(unsigned)((th + rb - 1) / rb), rb, 0, s>>>(
@@ -485,6 +509,45 @@ cudaError_t launch_gauss_sv(int storage, const void* S, int m, long long n, cons
         (const double*)part, nsplit, m, m_pad, Ntot, K1, K1, 1,
         storage == IPF_STORE_F64 ? nullptr : (float*)svd, storage == IPF_STORE_F64 ? (double*)svd : nullptr, c);
     return cudaGetLastError();
+}
+
+// The contraction's pipeline for one shape: 64-element stages (3 in flight)
+// or 32-element stages (7 in flight), whichever is faster on this GPU for
+// (storage, m, n, kcols), timed once per shape (two launches each after a
+// warm-up, on `s`, synchronising) and kept by the autotuner.  FP32 / FP64
+// storage has one kernel (returns 0).
+int gauss_variant(int storage, const void* S, int m, long long n, const void* V, long long ldv, int kcols, void* ws,
+                  void* svd, double* c, int* err, int num_sms, cudaStream_t s) {
+    if (!is16(storage)) return 0;
+    char key[128];
+    snprintf(key, sizeof key, "gauss/%s/m%d/n%lld/k%d", storage == IPF_STORE_BF16 ? "bf16" : "f16", m, n, kcols);
+    int v = 0, p = 0;
+    if (tune_lookup(key, &v, &p)) return v;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return 64;
+    }
+    int best = 64;
+    float best_ms = 1e30f;
+    for (int bk : {64, 32}) {
+        bool ok = launch_gauss_sv(storage, S, m, n, V, ldv, kcols, kcols, ws, svd, c, err, num_sms, bk, s) ==
+                  cudaSuccess;
+        ok = ok && cudaEventRecord(e0, s) == cudaSuccess;
+        for (int r = 0; r < 2 && ok; ++r)
+            ok = launch_gauss_sv(storage, S, m, n, V, ldv, kcols, kcols, ws, svd, c, err, num_sms, bk, s) ==
+                 cudaSuccess;
+        ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+        float ms = 0.f;
+        if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms / 2 < best_ms) {
+            best_ms = ms / 2;
+            best = bk;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    tune_store(key, best, 0, best_ms * 1e3);
+    return best;
 }
 
 }  // namespace ipf

@@ -373,8 +373,13 @@ cudaError_t launch_gauss_bparts(int storage, const float* b, long long n, void* 
 // [S V_{K1} | S b]: svd (column-major m x K1, FP64 for F64 storage, else
 // FP32) and c = S b (FP64); err receives IPF_ERR_TIMEOUT if a bounded wait
 // inside the tensor-core kernel gives up
+// variant: the pipeline of the 16-bit tensor-core kernel (64 or 32 K elements
+// per stage), from gauss_variant (timed once per shape by the autotuner)
 cudaError_t launch_gauss_sv(int storage, const void* S, int m, long long n, const void* V, long long ldv, int kcols,
-                            int K1, void* ws, void* svd, double* c, int* err, int num_sms, cudaStream_t s);
+                            int K1, void* ws, void* svd, double* c, int* err, int num_sms, int variant,
+                            cudaStream_t s);
+int gauss_variant(int storage, const void* S, int m, long long n, const void* V, long long ldv, int kcols, void* ws,
+                  void* svd, double* c, int* err, int num_sms, cudaStream_t s);
 // sampled pivoting: overwrite the step's pivot choice (after the update)
 cudaError_t launch_sample_pivot(int storage, const Geom& g, const Bufs& bf, unsigned long long seed, int size,
                                 cudaStream_t s);
@@ -423,6 +428,11 @@ size_t conv_tc_map_bytes();
 // api.cu: contexts the batched step can drive (see there)
 bool ctx_slot_desc(ipf_ctx* c, SlotDesc* d, int* storage);
 void ctx_steps_taken(ipf_ctx* c, int k);
+
+// batch.cu: the project's autotuner cache (per process, and in the JSON file
+// named by IPF_TUNE_CACHE): per key the chosen variant, its parameter and time
+bool tune_lookup(const char* key, int* variant, int* param);
+void tune_store(const char* key, int variant, int param, double us);
 
 // batch.cu: the batched step of the serving loop (one engine per server,
 // used from its scheduler thread only)

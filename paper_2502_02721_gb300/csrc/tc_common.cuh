@@ -161,6 +161,20 @@ __device__ __forceinline__ unsigned long long smem_desc_sw128(uint32_t addr) {
     return d;
 }
 
+// the same with the 64-byte swizzle (rows of 64 bytes, 16-byte chunks XOR-ed
+// with (row / 2) mod 4 inside each 512-byte group of 8 rows, as a TMA copy
+// with CU_TENSOR_MAP_SWIZZLE_64B writes them): stride between 8-row groups
+// 512 bytes
+__device__ __forceinline__ unsigned long long smem_desc_sw64(uint32_t addr) {
+    unsigned long long d = 0;
+    d |= (unsigned long long)((addr & 0x3FFFFu) >> 4);
+    d |= 1ull << 16;                                  // leading byte offset (unused): 16 bytes
+    d |= (unsigned long long)(512u >> 4) << 32;       // stride byte offset: 512 bytes
+    d |= 1ull << 46;                                  // descriptor version for tcgen05
+    d |= 4ull << 61;                                  // layout: 64-byte swizzle
+    return d;
+}
+
 // instruction descriptor, kind::f16: D FP32, A and B both FP16 (f16) or
 // both BF16, both K-major
 __host__ __device__ constexpr uint32_t idesc_f16kind(int M, int N, bool bf16) {

@@ -140,3 +140,25 @@ def test_gaussian_sketch_full_size_samples():
     assert abs(float(z.var()) - 1.0) < 5 * np.sqrt(2.0 / N) + 2e-3   # + BF16 rounding of the entries
     del S, z
     torch.cuda.empty_cache()
+
+
+def test_gaussian_contraction_pipelines_agree(tmp_path, monkeypatch):
+    """The two pipelines of the tensor-core contraction (64-element stages,
+    3 in flight; 32-element stages, 7 in flight) issue the same MMAs in the
+    same K order, only grouped differently per stage: with each pinned in
+    turn through the autotuner cache, the solves give the same bits."""
+    p = P.make("deblur64")
+    xs = []
+    for bk in (64, 32):
+        cache = tmp_path / f"tune{bk}.json"
+        cache.write_text('{"version": 1, "entries": [\n'
+                         f'  {{"key": "gauss/bf16/m{p.m_s}/n{p.n}/k{p.k + 1}", "variant": {bk}, "param": 0, '
+                         '"us": 1.0}\n]}\n')
+        monkeypatch.setenv("IPF_TUNE_CACHE", str(cache))
+        ctx = gpu_context(p, "bf16", sketch="gaussian")
+        ctx.step(p.k)
+        x, _ = ctx.solve(p.k, p.lambdas)
+        x20, _ = ctx.solve(20, p.lambdas)
+        xs.append((x, x20))
+        ctx.close()
+    assert np.array_equal(xs[0][0], xs[1][0]) and np.array_equal(xs[0][1], xs[1][1])

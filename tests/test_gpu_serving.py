@@ -145,8 +145,8 @@ def test_batched_tensor_cores_equal_the_context(tmp_path, monkeypatch):
     from paper_2502_02721_gb300 import binding as bd
     cache = tmp_path / "tune.json"
     cache.write_text('{"version": 1, "entries": [\n'
-                     '  {"key": "bf16/psf/kw15/64x64", "conv": "tc", "rows": 32, "us": 1.0},\n'
-                     '  {"key": "bf16/psf/kw31/64x64", "conv": "tc", "rows": 32, "us": 1.0}\n]}\n')
+                     '  {"key": "conv/bf16/kw15/64x64", "variant": 1, "param": 32, "us": 1.0},\n'
+                     '  {"key": "conv/bf16/kw31/64x64", "variant": 1, "param": 32, "us": 1.0}\n]}\n')
     monkeypatch.setenv("IPF_TUNE_CACHE", str(cache))
     rng = np.random.default_rng(23)
     reqs = []
