@@ -579,7 +579,11 @@ void ipf_config_default(ipf_config* cfg) {
     cfg->use_graphs = 1;
 }
 
-static size_t ldv_for(long long N) { return (size_t)((N + 63) / 64 * 64); }
+// stride between basis vectors: N rounded up to 64 elements (16-byte
+// aligned columns for 128-bit loads and TMA) plus 128 elements, so that
+// columns of a power-of-two length do not all start at the same offset of
+// the same DRAM partitions (every step streams all columns side by side)
+static size_t ldv_for(long long N) { return (size_t)((N + 63) / 64 * 64 + 128); }
 
 static int lam_chunk(int B) { return B >= kLamChunk ? 1 : kLamChunk / B; }
 static size_t solve_ws_for(const Geom& g) { return solve_workspace_bytes(g, lam_chunk(g.B)); }
@@ -1284,13 +1288,16 @@ namespace ipf {
 
 // The batched step of the serving loop drives contexts whose every step is
 // one of the batched kernels: one RHS, float storage, the sparse-sign sketch
-// with its table and the deferred sketch, full pivoting, steps on one stream,
-// and a PSF on the FMA column path (kw 7, 15, 31; BF16 may use the tensor
-// cores) or a CSR matrix.  Fills d (k_target and the tile counts are left
+// with its table and the deferred sketch, full pivoting, step mode 2 (the
+// products at the pivot rows beside the operator), and a PSF on the FMA
+// column path (kw 7, 15, 31; BF16 may use the tensor cores) or a CSR matrix.  Fills d (k_target and the tile counts are left
 // to the caller) and returns true for such a context.
 bool ctx_slot_desc(ipf_ctx* c, SlotDesc* d, int* storage) {
     if (!c || c->sticky != IPF_OK || c->gh || c->gauss || c->B != 1 || c->storage == IPF_STORE_F64) return false;
-    if (!c->defer_sketch || c->split || c->fork_piv || c->cfg.pivot_sample != 0 || sw_on(c)) return false;
+    // the batched step runs the pivot-row products beside the operator: the
+    // context must have their buffer (step mode 2)
+    if (!c->defer_sketch || c->split || !c->fork_piv || !c->bf.gpiv || c->cfg.pivot_sample != 0 || sw_on(c))
+        return false;
     if (c->op.kind == IPF_OP_PSF2D) {
         if (!c->op.psf_pairs || (c->op.kw != 7 && c->op.kw != 15 && c->op.kw != 31)) return false;
     } else if (c->op.kind != IPF_OP_CSR) {

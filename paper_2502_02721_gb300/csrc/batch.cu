@@ -154,8 +154,8 @@ struct BatchEngine {
         cudaEvent_t ev = nullptr;
     };
     int num_sms = 1;
-    cudaStream_t s = nullptr;
-    cudaEvent_t ev_ready = nullptr, ev_t0 = nullptr, ev_t1 = nullptr;
+    cudaStream_t s = nullptr, s2 = nullptr;   // the step's stream, and the pivot branch beside the operator
+    cudaEvent_t ev_ready = nullptr, ev_t0 = nullptr, ev_t1 = nullptr, ev_fork = nullptr, ev_join = nullptr;
     Slot slots[kMaxSlots];
     std::vector<unsigned char> maps;     // kMaxSlots tensor maps, host (passed by value at launch)
     SlotDesc* d_slots = nullptr;         // kMaxSlots entries
@@ -201,7 +201,7 @@ struct BatchEngine {
     // tensor-core units (BF16: KP 16 and 32), the slot list of the pivot
     // solve, the update and the normalisation tiles
     static constexpr int kGroups = 3;
-    static constexpr int kTables = 6;        // op, tc16, tc32, piv, upd, norm
+    static constexpr int kTables = 7;        // op, tc16, tc32, piv, upd, norm, pivot-row products
     struct Group {
         int storage = 0;
         int count[kTables] = {0};
@@ -237,6 +237,7 @@ struct BatchEngine {
             t[3].push_back({i, 0});
             for (int q = 0, nq = cdiv(d.g.N, kBatchUpdTile); q < nq; ++q) t[4].push_back({i, q});
             for (int q = 0; q < d.norm_tiles; ++q) t[5].push_back({i, q});
+            for (int q = 0, nq = cdiv(d.g.k_max + 1, 8); q < nq; ++q) t[6].push_back({i, q});
         }
         std::vector<TileRef> all;
         for (int g = 0; g < kGroups; ++g)
@@ -263,9 +264,24 @@ struct BatchEngine {
         return cudaSuccess;
     }
 
-    // one batched step of every slot of the uploaded composition
+    // one batched step of every slot of the uploaded composition: the
+    // products at the pivot rows and the FP64 pivot-block solve on the
+    // second stream beside the operator (they need only v_j and the
+    // pivots), joined before the update that consumes both
     cudaError_t step_launches() {
         cudaError_t e;
+        if ((e = cudaEventRecord(ev_fork, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(s2, ev_fork, 0)) != cudaSuccess) return e;
+        for (const Group& G : grp) {
+            if (!G.count[3]) continue;
+            TileRef* t = d_tiles;
+            if ((e = launch_batch_pivot_rows(G.storage, d_slots, t + G.off[6], G.count[6], num_sms, s2)) != cudaSuccess)
+                return e;
+            if ((e = launch_batch_pivot_solve(G.storage, d_slots, t + G.off[3], G.count[3], G.k_max, s2)) !=
+                cudaSuccess)
+                return e;
+        }
+        if ((e = cudaEventRecord(ev_join, s2)) != cudaSuccess) return e;
         for (const Group& G : grp) {
             if (!G.count[3]) continue;
             const int st = G.storage;
@@ -275,8 +291,12 @@ struct BatchEngine {
                 return e;
             if ((e = launch_batch_conv_tc(32, maps.data(), d_slots, t + G.off[2], G.count[2], s)) != cudaSuccess)
                 return e;
-            if ((e = launch_batch_pivot_solve(st, d_slots, t + G.off[3], G.count[3], G.k_max, s)) != cudaSuccess)
-                return e;
+        }
+        if ((e = cudaStreamWaitEvent(s, ev_join, 0)) != cudaSuccess) return e;
+        for (const Group& G : grp) {
+            if (!G.count[3]) continue;
+            const int st = G.storage;
+            TileRef* t = d_tiles;
             if ((e = launch_batch_update(st, d_slots, t + G.off[4], G.count[4], G.k_max, G.m_s_max, num_sms, s)) !=
                 cudaSuccess)
                 return e;
@@ -379,8 +399,11 @@ BatchEngine* batch_create() {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev);
     int lo = 0, hi = 0;
     if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
-    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b->s, cudaStreamNonBlocking, hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b->s, cudaStreamNonBlocking, lo);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b->s2, cudaStreamNonBlocking, hi);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev_t0);
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev_t1);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_slots, sizeof(SlotDesc) * kMaxSlots);
@@ -410,6 +433,10 @@ void batch_destroy(BatchEngine* b) {
     if (b->ev_ready) cudaEventDestroy(b->ev_ready);
     if (b->ev_t0) cudaEventDestroy(b->ev_t0);
     if (b->ev_t1) cudaEventDestroy(b->ev_t1);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
+    if (b->s2) cudaStreamSynchronize(b->s2);
+    if (b->s2) cudaStreamDestroy(b->s2);
     if (b->s) cudaStreamDestroy(b->s);
     delete b;
 }

@@ -392,7 +392,10 @@ size_t part_bytes(int storage, int m, long long n, int K1max, int num_sms) {
 
 }  // namespace
 
-long long gauss_lds(long long n) { return (n + 63) / 64 * 64; }
+// row stride of S: n rounded up to 64 elements plus 128, so that the m_s rows
+// a contraction stage reads at the same column do not fall on the same DRAM
+// partitions when n is a power of two
+long long gauss_lds(long long n) { return (n + 63) / 64 * 64 + 128; }
 
 size_t gauss_workspace_bytes(int storage, int m, long long n, int k_max, int num_sms) {
     const size_t sb = storage == IPF_STORE_F64 ? 8 : storage == IPF_STORE_F32 ? 4 : 2;

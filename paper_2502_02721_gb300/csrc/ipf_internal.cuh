@@ -414,6 +414,9 @@ cudaError_t launch_batch_update(int storage, const SlotDesc* slots, const TileRe
                                 int m_s_max, int num_sms, cudaStream_t s);
 cudaError_t launch_batch_normalize(int storage, const SlotDesc* slots, const TileRef* tiles, int ntiles, int num_sms,
                                    cudaStream_t s);
+// (A v_j)(p_i) at the pivot rows into bf.gpiv: tile t of a slot = pivots 8t .. 8t+7
+cudaError_t launch_batch_pivot_rows(int storage, const SlotDesc* slots, const TileRef* tiles, int ntiles, int num_sms,
+                                    cudaStream_t s);
 // PSF (FMA column convolution, kw 7 / 15 / 31) and CSR products
 cudaError_t launch_batch_operator(int storage, const SlotDesc* slots, const TileRef* tiles, int ntiles, int num_sms,
                                   cudaStream_t s);

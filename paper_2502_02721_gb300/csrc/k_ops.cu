@@ -551,17 +551,13 @@ cudaError_t apply_T(const OpDev& op, const void* v, long long ldv, long long vco
 
 // (A v_j)(p_i), i <= j: one warp per (pivot, RHS), lanes over the stencil
 // taps or the row's nonzeros, a fixed-order shuffle reduction.
+// (A v)(p) for one pivot row p, one warp: the stencil taps (PSF) or the row's
+// nonzeros (CSR, RHS r of B interleaved) over the lanes, a fixed-order
+// shuffle reduction; every lane returns the sum
 template <class T>
-__global__ void __launch_bounds__(256) k_pivot_rows_psf(const T* __restrict__ vbase, long long ldv,
-                                                         const DevState* __restrict__ st, const int* __restrict__ piv,
-                                                         int H, int W, const float* __restrict__ psf, int ph, int pw,
-                                                         float* __restrict__ gout) {
-    const int j = st->j;
-    const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-    if (j < 0 || i > j || st->status[0] != IPF_OK) return;
-    const T* v = vbase + (size_t)j * ldv;
+__device__ __forceinline__ float pivot_row_psf(const T* __restrict__ v, int p, int H, int W,
+                                               const float* __restrict__ psf, int ph, int pw) {
     const int lane = threadIdx.x & 31;
-    const int p = piv[i];
     const int py = p / W, px = p - py * W;
     const int cy = ph / 2, cx = pw / 2;
     float acc = 0.f;
@@ -572,7 +568,33 @@ __global__ void __launch_bounds__(256) k_pivot_rows_psf(const T* __restrict__ vb
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) gout[i] = acc;
+    return acc;
+}
+
+template <class T>
+__device__ __forceinline__ float pivot_row_csr(const T* __restrict__ v, long long row, int B, int r,
+                                               const long long* __restrict__ rowptr, const int* __restrict__ colind,
+                                               const float* __restrict__ vals) {
+    const int lane = threadIdx.x & 31;
+    float acc = 0.f;
+    for (long long q = rowptr[row] + lane; q < rowptr[row + 1]; q += 32)
+        acc = fmaf(vals[q], to_acc(v[(size_t)colind[q] * B + r]), acc);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    return acc;
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_pivot_rows_psf(const T* __restrict__ vbase, long long ldv,
+                                                         const DevState* __restrict__ st, const int* __restrict__ piv,
+                                                         int H, int W, const float* __restrict__ psf, int ph, int pw,
+                                                         float* __restrict__ gout) {
+    const int j = st->j;
+    const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    if (j < 0 || i > j || st->status[0] != IPF_OK) return;
+    const T* v = vbase + (size_t)j * ldv;
+    const float acc = pivot_row_psf<T>(v, piv[i], H, W, psf, ph, pw);
+    if ((threadIdx.x & 31) == 0) gout[i] = acc;
 }
 
 template <class T>
@@ -586,14 +608,8 @@ __global__ void __launch_bounds__(256) k_pivot_rows_csr(const T* __restrict__ vb
     const int i = wid / B, r = wid - (wid / B) * B;
     if (j < 0 || i > j || r >= B || st->status[r] != IPF_OK) return;
     const T* v = vbase + (size_t)j * ldv;
-    const int lane = threadIdx.x & 31;
-    const long long row = piv[(size_t)r * K1 + i];
-    float acc = 0.f;
-    for (long long q = rowptr[row] + lane; q < rowptr[row + 1]; q += 32)
-        acc = fmaf(vals[q], to_acc(v[(size_t)colind[q] * B + r]), acc);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) gout[(size_t)r * K1 + i] = acc;
+    const float acc = pivot_row_csr<T>(v, piv[(size_t)r * K1 + i], B, r, rowptr, colind, vals);
+    if ((threadIdx.x & 31) == 0) gout[(size_t)r * K1 + i] = acc;
 }
 
 __global__ void k_interleave(const float* __restrict__ src, float* __restrict__ dst, long long n, int B, int dir) {
@@ -707,7 +723,43 @@ __global__ void __launch_bounds__(128, 7) kb_operator(const SlotDesc* __restrict
     }
 }
 
+// (A v_j)(p_i), i <= j, of every active slot: tile t of a slot holds the
+// pivots 8t .. 8t + 7, one warp each (the arithmetic of k_pivot_rows_*)
+template <class T>
+__global__ void __launch_bounds__(256) kb_pivot_rows(const SlotDesc* __restrict__ slots,
+                                                     const TileRef* __restrict__ tiles, int ntiles) {
+    __shared__ int s_j;
+    for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+        const TileRef tr = tiles[tt];
+        const SlotDesc* sd = slots + tr.slot;
+        const int j = slot_step(sd, &s_j);
+        if (j < 0) continue;
+        const int i = tr.tile * 8 + (int)(threadIdx.x >> 5);
+        if (i > j) continue;                               // uniform per warp
+        const T* v = (const T*)sd->bf.V + (size_t)j * sd->g.ldv;
+        const OpDev& op = sd->op;
+        const int p = sd->bf.piv[i];
+        const float acc = op.kind == IPF_OP_CSR
+                              ? pivot_row_csr<T>(v, p, 1, 0, op.rowptr, op.colind, op.vals)
+                              : pivot_row_psf<T>(v, p, op.rows, op.cols, op.psf, op.ph, op.pw);
+        if ((threadIdx.x & 31) == 0) sd->bf.gpiv[i] = acc;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_batch_pivot_rows(int storage, const SlotDesc* slots, const TileRef* tiles, int ntiles, int num_sms,
+                                    cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    const int blocks = ntiles < num_sms * 8 ? ntiles : num_sms * 8;
+    switch (storage) {
+        case IPF_STORE_F32: kb_pivot_rows<float><<<blocks, 256, 0, s>>>(slots, tiles, ntiles); break;
+        case IPF_STORE_BF16: kb_pivot_rows<__nv_bfloat16><<<blocks, 256, 0, s>>>(slots, tiles, ntiles); break;
+        case IPF_STORE_F16: kb_pivot_rows<__half><<<blocks, 256, 0, s>>>(slots, tiles, ntiles); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_batch_operator(int storage, const SlotDesc* slots, const TileRef* tiles, int ntiles, int num_sms,
                                   cudaStream_t s) {

@@ -113,6 +113,7 @@ struct Job {
     std::vector<float> b;
     float* b_pin = nullptr;                 // pinned copy of b, read by the device
     int slot = -1;                          // batch engine slot, or -1
+    int cls = 0;                            // its engine (size class)
     ipf_config cfg{};
     int k = 0;
     double lambda = 0.0;
@@ -149,8 +150,13 @@ struct ipf_server {
     std::thread worker;
     size_t reserved = 0;                     // footprints of active jobs
     int device = 0;
-    ipf::BatchEngine* eng = nullptr;         // the batched step (NULL with cfg.per_request)
-    std::deque<cudaEvent_t> turns;           // engine turns in flight
+    // the batched step: one engine (stream, work list) per size class, so a
+    // small request steps in lockstep only with requests of similar work per
+    // step, and the classes' launches overlap on the GPU (NULL with
+    // cfg.per_request)
+    static constexpr int kClasses = 3;
+    ipf::BatchEngine* eng[kClasses] = {};
+    std::deque<cudaEvent_t> turns[kClasses]; // engine turns in flight
     std::vector<cudaEvent_t> spare_ev;
     // statistics
     unsigned long long n_done = 0, n_rejected = 0;
@@ -185,9 +191,15 @@ bool ipf_server::admit(Job* j) {
     c.profile = 0;
     // requests in flight already overlap with one another; a second stream
     // per step only adds launches and events (measured: lower capacity and
-    // higher latency under load), so every request steps on one stream
+    // higher latency under load), so a request on its own streams steps on
+    // one stream
     c.overlap = 0;
-    if (eng) c.use_graphs = 0;                         // steps come from the batch engine where it can
+    if (eng[0]) {
+        // steps come from the batch engine where it can, which runs the
+        // products at the pivot rows beside the operator (step mode 2)
+        c.use_graphs = 0;
+        c.overlap = 2;
+    }
     ipf_ctx* ctx = nullptr;
     // the device reads b from pinned host memory: no wait for the GPU here
     ipf_status st = ipf_create(&j->op, j->b_pin, IPF_MEM_DEVICE, &c, &ctx);
@@ -217,8 +229,16 @@ bool ipf_server::admit(Job* j) {
         retire(j);
         return true;
     }
-    // a request the batched step cannot drive steps on its own stream (eagerly)
-    if (eng) j->slot = ipf::batch_add(eng, ctx, j->k, j->us);
+    // a request the batched step cannot drive steps on its own stream
+    // (eagerly); the others go to the engine of their size class: bytes a
+    // step moves, about n s_V (k + 1) / 2 of the basis plus the operator's
+    if (eng[0]) {
+        const double sv = j->cfg.storage == IPF_STORE_F32 ? 4.0 : 2.0;
+        double per_step = (double)j->n * sv * (j->k + 1) / 2.0 +
+                          (j->op.kind == IPF_OP_CSR ? (double)j->op.nnz * 8.0 : (double)j->n * 8.0);
+        j->cls = per_step < 16e6 ? 0 : per_step < 96e6 ? 1 : 2;
+        j->slot = ipf::batch_add(eng[j->cls], ctx, j->k, j->us);
+    }
     if (j->slot >= 0) ++n_batched;
     return true;
 }
@@ -227,9 +247,9 @@ void ipf_server::retire(Job* j) {
     if (j->slot >= 0) {
         // still in the batch (an error or shutdown): drop it, and let the
         // turns that read it finish first
-        ipf::batch_remove(eng, j->slot);
+        ipf::batch_remove(eng[j->cls], j->slot);
         j->slot = -1;
-        for (cudaEvent_t ev : turns) cudaEventSynchronize(ev);
+        for (cudaEvent_t ev : turns[j->cls]) cudaEventSynchronize(ev);
     }
     if (j->ctx) {
         int kd = 0;
@@ -297,42 +317,42 @@ void ipf_server::loop() {
                 }
             }
         }
-        // one turn of the batch engine (at most two in flight); slots that
-        // have taken their k steps leave the batch, and their solves (below)
-        // follow this turn on their own streams
-        if (eng) {
-            while (!turns.empty() && cudaEventQuery(turns.front()) == cudaSuccess) {
-                spare_ev.push_back(turns.front());
-                turns.pop_front();
+        // one turn of each size class's engine (at most two in flight per
+        // class); slots that have taken their k steps leave the batch, and
+        // their solves (below) follow that turn on their own streams
+        for (int cl = 0; cl < kClasses && eng[cl]; ++cl) {
+            std::deque<cudaEvent_t>& tq = turns[cl];
+            while (!tq.empty() && cudaEventQuery(tq.front()) == cudaSuccess) {
+                spare_ev.push_back(tq.front());
+                tq.pop_front();
             }
-            if (ipf::batch_used(eng) > 0 && turns.size() < 2) {
-                cudaEvent_t ev = nullptr;
-                if (!spare_ev.empty()) {
-                    ev = spare_ev.back();
-                    spare_ev.pop_back();
-                } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
-                    ev = nullptr;
-                }
-                const cudaError_t e = ev ? ipf::batch_run(eng, slice, ev) : cudaErrorMemoryAllocation;
-                worked = true;
-                if (ev) turns.push_back(ev);
-                for (auto& up : active) {
-                    Job* j = up.get();
-                    if (j->slot < 0) continue;
-                    if (e != cudaSuccess) {
-                        ipf::batch_remove(eng, j->slot);
-                        j->slot = -1;
-                        j->status = IPF_ERR_CUDA;
-                        j->enqueued = j->k;
-                        continue;
-                    }
-                    if (ipf::batch_steps(eng, j->slot) < j->k) continue;
-                    ipf::batch_remove(eng, j->slot);
+            if (ipf::batch_used(eng[cl]) == 0 || tq.size() >= 2) continue;
+            cudaEvent_t ev = nullptr;
+            if (!spare_ev.empty()) {
+                ev = spare_ev.back();
+                spare_ev.pop_back();
+            } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+                ev = nullptr;
+            }
+            const cudaError_t e = ev ? ipf::batch_run(eng[cl], slice, ev) : cudaErrorMemoryAllocation;
+            worked = true;
+            if (ev) tq.push_back(ev);
+            for (auto& up : active) {
+                Job* j = up.get();
+                if (j->slot < 0 || j->cls != cl) continue;
+                if (e != cudaSuccess) {
+                    ipf::batch_remove(eng[cl], j->slot);
                     j->slot = -1;
-                    cudaStreamWaitEvent(j->us, ev, 0);
-                    ipf::ctx_steps_taken(j->ctx, j->k);
+                    j->status = IPF_ERR_CUDA;
                     j->enqueued = j->k;
+                    continue;
                 }
+                if (ipf::batch_steps(eng[cl], j->slot) < j->k) continue;
+                ipf::batch_remove(eng[cl], j->slot);
+                j->slot = -1;
+                cudaStreamWaitEvent(j->us, ev, 0);
+                ipf::ctx_steps_taken(j->ctx, j->k);
+                j->enqueued = j->k;
             }
         }
         // top up every in-flight request whose previous work has finished
@@ -420,10 +440,13 @@ ipf_status ipf_server_create(const ipf_server_config* cfg, ipf_server** out) {
         s->arena.release();
         return IPF_ERR_OOM;
     }
-    if (!s->cfg.per_request && !(s->eng = ipf::batch_create())) {
-        s->arena.release();
-        s->pinned.release();
-        return IPF_ERR_CUDA;
+    for (int cl = 0; cl < ipf_server::kClasses && !s->cfg.per_request; ++cl) {
+        if (!(s->eng[cl] = ipf::batch_create())) {
+            for (int c2 = 0; c2 < cl; ++c2) ipf::batch_destroy(s->eng[c2]);
+            s->arena.release();
+            s->pinned.release();
+            return IPF_ERR_CUDA;
+        }
     }
     ipf_server* raw = s.release();
     raw->worker = std::thread([raw] { raw->loop(); });
@@ -536,12 +559,17 @@ ipf_status ipf_server_batch_stats(ipf_server* s, int* batched, long long* graph_
     if (!s) return IPF_ERR_ARG;
     std::lock_guard<std::mutex> lk(s->mu);
     if (batched) *batched = s->n_batched;
-    ipf::batch_counters(s->eng, graph_turns, eager_turns, captures);
-    if (!s->eng) {
-        if (graph_turns) *graph_turns = 0;
-        if (eager_turns) *eager_turns = 0;
-        if (captures) *captures = 0;
+    long long g = 0, e = 0, c = 0;
+    for (auto* en : s->eng) {
+        long long g1 = 0, e1 = 0, c1 = 0;
+        if (en) ipf::batch_counters(en, &g1, &e1, &c1);
+        g += g1;
+        e += e1;
+        c += c1;
     }
+    if (graph_turns) *graph_turns = g;
+    if (eager_turns) *eager_turns = e;
+    if (captures) *captures = c;
     return IPF_OK;
 }
 
@@ -564,9 +592,10 @@ void ipf_server_destroy(ipf_server* s) {
     s->done.clear();
     s->pending.clear();
     cudaDeviceSynchronize();
-    for (cudaEvent_t ev : s->turns) cudaEventDestroy(ev);
+    for (auto& tq : s->turns)
+        for (cudaEvent_t ev : tq) cudaEventDestroy(ev);
     for (cudaEvent_t ev : s->spare_ev) cudaEventDestroy(ev);
-    ipf::batch_destroy(s->eng);
+    for (auto* e : s->eng) ipf::batch_destroy(e);
     s->arena.release();
     s->pinned.release();
     delete s;

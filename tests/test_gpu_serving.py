@@ -72,9 +72,9 @@ def _serve(bd, reqs, keep, per_request=False, max_inflight=6, steps_per_slice=4,
     return [results[t] for t in tickets], stats
 
 
-def _alone(bd, r, keep, **extra):
-    cfg = bd.default_config(k_max=r["k"], m_s=r["m_s"], zeta=8, seed=r["seed"], storage=r["storage"], overlap=0,
-                            **extra)
+def _alone(bd, r, keep, overlap=0, **extra):
+    cfg = bd.default_config(k_max=r["k"], m_s=r["m_s"], zeta=8, seed=r["seed"], storage=r["storage"],
+                            overlap=overlap, **extra)
     ctx = bd.Context(_op(bd, r, keep), r["b"], cfg, keep)
     ctx.step(r["k"])
     xa, _ = ctx.solve(r["k"], [r["lam"]])
@@ -123,8 +123,9 @@ def test_batched_results_alone_and_in_the_mix():
 
 def test_batched_fma_and_csr_equal_the_context():
     """FMA column convolution (BF16 with conv_fma, and FP32) and CSR: the
-    batched step computes each element as the one-context kernels do, so the
-    served x equals the context's x bit for bit."""
+    batched step computes each element as the one-context kernels of step
+    mode 2 do (products at the pivot rows beside the operator), so the served
+    x equals such a context's x bit for bit."""
     ensure_lib()
     from paper_2502_02721_gb300 import binding as bd
     reqs = _requests()
@@ -133,14 +134,14 @@ def test_batched_fma_and_csr_equal_the_context():
     assert stats[0] == len(reqs)
     for r, out in zip(reqs, res):
         assert out[0] == bd.IPF_OK
-        assert np.array_equal(out[3], _alone(bd, r, keep, conv_fma=1)), (r["kind"], r["storage"])
+        assert np.array_equal(out[3], _alone(bd, r, keep, overlap=2, conv_fma=1)), (r["kind"], r["storage"])
 
 
 def test_batched_tensor_cores_equal_the_context(tmp_path, monkeypatch):
     """BF16 PSF requests on the tensor-core convolution, with the tuner's
     choice pinned (IPF_TUNE_CACHE) to the band height a context uses on a
-    64 x 64 image (32 output rows per CTA): the served x equals the
-    context's x bit for bit."""
+    64 x 64 image (32 output rows per CTA): the served x equals the x of a
+    context in step mode 2 bit for bit."""
     ensure_lib()
     from paper_2502_02721_gb300 import binding as bd
     cache = tmp_path / "tune.json"
@@ -162,7 +163,7 @@ def test_batched_tensor_cores_equal_the_context(tmp_path, monkeypatch):
     assert stats[0] == len(reqs)
     for r, out in zip(reqs, res):
         assert out[0] == bd.IPF_OK
-        assert np.array_equal(out[3], _alone(bd, r, keep)), r["psf"].shape
+        assert np.array_equal(out[3], _alone(bd, r, keep, overlap=2)), r["psf"].shape
 
 
 def test_server_rejects_what_can_never_fit():
