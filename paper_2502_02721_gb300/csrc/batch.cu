@@ -160,6 +160,7 @@ struct BatchEngine {
     std::vector<unsigned char> maps;     // kMaxSlots tensor maps, host (passed by value at launch)
     SlotDesc* d_slots = nullptr;         // kMaxSlots entries
     SlotDesc* d_tune = nullptr;          // kMaxSlots entries, for the tuner's one-slot tables
+    int* d_groups = nullptr;             // kMaxSlots x (kCsrGroup + 1): CSR slots sharing one matrix
     TileRef* d_tiles = nullptr;
     size_t tile_cap = 0;
     unsigned epoch = 1, uploaded_epoch = 0, ran_epoch = 0;
@@ -199,9 +200,11 @@ struct BatchEngine {
     // the (slot, tile) tables of the current composition, to the device:
     // per storage group (FP32, BF16, FP16) the operator tiles, the
     // tensor-core units (BF16: KP 16 and 32), the slot list of the pivot
-    // solve, the update and the normalisation tiles
+    // solve, the update, the normalisation tiles, the products at the pivot
+    // rows and the CSR tiles of slot groups sharing one matrix (each row's
+    // nonzeros read once for up to kCsrGroup slots)
     static constexpr int kGroups = 3;
-    static constexpr int kTables = 7;        // op, tc16, tc32, piv, upd, norm, pivot-row products
+    static constexpr int kTables = 8;        // op, tc16, tc32, piv, upd, norm, pivot-row products, CSR groups
     struct Group {
         int storage = 0;
         int count[kTables] = {0};
@@ -214,6 +217,9 @@ struct BatchEngine {
         std::vector<SlotDesc> hs(kMaxSlots);
         memset(hs.data(), 0, hs.size() * sizeof(SlotDesc));
         std::vector<TileRef> tab[kGroups][kTables];
+        std::vector<int> hg((size_t)kMaxSlots * (kCsrGroup + 1), 0);
+        int ngroups = 0;
+        std::vector<int> csr[kGroups];
         for (int g = 0; g < kGroups; ++g) grp[g] = Group();
         for (int i = 0; i < kMaxSlots; ++i) {
             const Slot& sl = slots[i];
@@ -230,7 +236,7 @@ struct BatchEngine {
                 std::vector<TileRef>& u = t[d.tc_kp == 32 ? 2 : 1];
                 for (int q = 0, nq = d.tc_ct * cdiv(d.op.rows, d.tc_rows); q < nq; ++q) u.push_back({i, q});
             } else if (d.op.kind == IPF_OP_CSR) {
-                for (int q = 0, nq = cdiv(d.op.rows, kBatchCsrRows); q < nq; ++q) t[0].push_back({i, q});
+                csr[g].push_back(i);
             } else {
                 for (int q = 0, nq = d.conv_cols * cdiv(d.op.rows, 16); q < nq; ++q) t[0].push_back({i, q});
             }
@@ -238,6 +244,28 @@ struct BatchEngine {
             for (int q = 0, nq = cdiv(d.g.N, kBatchUpdTile); q < nq; ++q) t[4].push_back({i, q});
             for (int q = 0; q < d.norm_tiles; ++q) t[5].push_back({i, q});
             for (int q = 0, nq = cdiv(d.g.k_max + 1, 8); q < nq; ++q) t[6].push_back({i, q});
+        }
+        // CSR slots of one storage type on the same matrix, in groups of up
+        // to kCsrGroup (slot order), one tile list per group
+        for (int g = 0; g < kGroups; ++g) {
+            std::vector<int>& c = csr[g];
+            std::vector<char> done(c.size(), 0);
+            for (size_t a = 0; a < c.size(); ++a) {
+                if (done[a]) continue;
+                const OpDev& oa = slots[c[a]].d.op;
+                int* gr = hg.data() + (size_t)ngroups * (kCsrGroup + 1);
+                gr[0] = 0;
+                for (size_t b = a; b < c.size() && gr[0] < kCsrGroup; ++b) {
+                    const OpDev& ob = slots[c[b]].d.op;
+                    if (done[b] || ob.rowptr != oa.rowptr || ob.colind != oa.colind || ob.vals != oa.vals ||
+                        ob.rows != oa.rows)
+                        continue;
+                    done[b] = 1;
+                    gr[1 + gr[0]++] = c[b];
+                }
+                for (int q = 0, nq = cdiv(oa.rows, kBatchCsrRows); q < nq; ++q) tab[g][7].push_back({ngroups, q});
+                ++ngroups;
+            }
         }
         std::vector<TileRef> all;
         for (int g = 0; g < kGroups; ++g)
@@ -259,6 +287,9 @@ struct BatchEngine {
             tile_cap = cap;
         }
         if ((e = stage_copy(d_slots, hs.data(), hs.size() * sizeof(SlotDesc))) != cudaSuccess) return e;
+        if (ngroups && (e = stage_copy(d_groups, hg.data(), (size_t)ngroups * (kCsrGroup + 1) * sizeof(int))) !=
+                           cudaSuccess)
+            return e;
         if (total && (e = stage_copy(d_tiles, all.data(), total * sizeof(TileRef))) != cudaSuccess) return e;
         uploaded_epoch = epoch;
         return cudaSuccess;
@@ -287,6 +318,9 @@ struct BatchEngine {
             const int st = G.storage;
             TileRef* t = d_tiles;
             if ((e = launch_batch_operator(st, d_slots, t + G.off[0], G.count[0], num_sms, s)) != cudaSuccess) return e;
+            if ((e = launch_batch_csr_group(st, d_slots, d_groups, t + G.off[7], G.count[7], num_sms, s)) !=
+                cudaSuccess)
+                return e;
             if ((e = launch_batch_conv_tc(16, maps.data(), d_slots, t + G.off[1], G.count[1], s)) != cudaSuccess)
                 return e;
             if ((e = launch_batch_conv_tc(32, maps.data(), d_slots, t + G.off[2], G.count[2], s)) != cudaSuccess)
@@ -408,6 +442,7 @@ BatchEngine* batch_create() {
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev_t1);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_slots, sizeof(SlotDesc) * kMaxSlots);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_tune, sizeof(SlotDesc) * kMaxSlots);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_groups, sizeof(int) * kMaxSlots * (kCsrGroup + 1));
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_slots, 0, sizeof(SlotDesc) * kMaxSlots, b->s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_tune, 0, sizeof(SlotDesc) * kMaxSlots, b->s);
     if (e != cudaSuccess) {
@@ -430,6 +465,7 @@ void batch_destroy(BatchEngine* b) {
     if (b->d_tune_tiles) cudaFree(b->d_tune_tiles);
     if (b->d_slots) cudaFree(b->d_slots);
     if (b->d_tune) cudaFree(b->d_tune);
+    if (b->d_groups) cudaFree(b->d_groups);
     if (b->ev_ready) cudaEventDestroy(b->ev_ready);
     if (b->ev_t0) cudaEventDestroy(b->ev_t0);
     if (b->ev_t1) cudaEventDestroy(b->ev_t1);

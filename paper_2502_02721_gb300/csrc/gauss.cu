@@ -148,8 +148,11 @@ __global__ void k_gauss_bparts(const float* __restrict__ b, long long n, long lo
 
 // ---------------------------------------------------------------------------
 // tensor-core contraction.  CTA (slice s, row group q) sums K = i in
-// [s*chunk, min(n, (s+1)*chunk)) for the rows 256q .. 256q + 255 of S (one or
-// two M = 128 tiles) against all N = Ntot rows of B = [V_0 .. V_{Nv-1};
+// [s*chunk, min(n, (s+1)*chunk)) for the rows rg q .. rg q + rg - 1 of S (rg
+// = the rows per group, a multiple of 16 up to 256, the same for every
+// group but the last, so that the CTAs carry equal shares of S: one or two
+// M = 128 tiles, a tile of R < 128 rows loaded as boxes of 64, 32 and 16
+// rows, its other TMEM lanes unused) against all N = Ntot rows of B = [V_0 .. V_{Nv-1};
 // b0, b1, b2, 0 x 5] (Nv >= k + 1, Ntot = Nv + 8, a multiple of 16).  Per
 // stage of 64 K elements (one 128-byte swizzle row): TMA brings the A tiles
 // (128 rows x 128 bytes each) and B (Ntot rows) into shared memory with the
@@ -187,11 +190,16 @@ template <int BK> __device__ __forceinline__ unsigned long long gm_desc(uint32_t
 template <> __device__ __forceinline__ unsigned long long gm_desc<64>(uint32_t addr) { return smem_desc_sw128(addr); }
 template <> __device__ __forceinline__ unsigned long long gm_desc<32>(uint32_t addr) { return smem_desc_sw64(addr); }
 
+// S through four maps of box heights 128, 64, 32 and 16 rows
+struct GmSMaps {
+    CUtensorMap box[4];
+};
+
 template <bool BF16, int BK>
 __global__ void __launch_bounds__(kGmThreads, 1)
-    k_gauss_mma(const __grid_constant__ CUtensorMap smap, const __grid_constant__ CUtensorMap vmap,
-                const __grid_constant__ CUtensorMap bmap, long long n, int m, long long chunk, int mg, int Nv,
-                int Ntot, float* __restrict__ part, int m_pad, int* __restrict__ err) {
+    k_gauss_mma(const __grid_constant__ GmSMaps smaps, const __grid_constant__ CUtensorMap vmap,
+                const __grid_constant__ CUtensorMap bmap, long long n, int m, long long chunk, int mg, int rg,
+                int Nv, int Ntot, float* __restrict__ part, int m_pad, int* __restrict__ err) {
     using G = GmShape<BK>;
     constexpr int kGmBK = BK;
     constexpr int kGmStages = G::kStages;
@@ -212,8 +220,12 @@ __global__ void __launch_bounds__(kGmThreads, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int slice = blockIdx.x / mg, q = blockIdx.x % mg;
-    const int row0 = q * 256;
-    const int ntile = min(2, (m - row0 + 127) / 128);          // >= 1: q < mg = ceil(m / 256)
+    const int row0 = q * rg;
+    const int rows_q = min(rg, m - row0);                      // >= 1: q < mg, (mg - 1) rg < m
+    const int ntile = (rows_q + 127) / 128;                    // 1 or 2
+    // rows of each tile, rounded up to 16 (beyond m: TMA zero fill)
+    const int R0 = min(128, (rows_q + 15) / 16 * 16);
+    const int R1 = ntile > 1 ? (rows_q - 128 + 15) / 16 * 16 : 0;
     const long long i0 = (long long)slice * chunk;
     const long long i1 = min(n, i0 + chunk);
     const int nkb = (int)((i1 - i0 + kGmBK - 1) / kGmBK);      // >= 1: slices = ceil(n / chunk)
@@ -238,7 +250,7 @@ __global__ void __launch_bounds__(kGmThreads, 1)
 
     if (warp == 0) {
         if (lane == 0) {
-            const uint32_t bytes = (uint32_t)(ntile * kGmATile + Ntot * kRow);
+            const uint32_t bytes = (uint32_t)((R0 + R1 + Ntot) * kRow);
             int issued = 0;
             for (int kb = 0; kb < nkb; ++kb) {
                 const int s = kb % kGmStages;
@@ -246,7 +258,25 @@ __global__ void __launch_bounds__(kGmThreads, 1)
                 mbar_expect_tx(full(s), bytes);
                 const int x = (int)(i0 + (long long)kb * kGmBK);
                 const uint32_t st = sbase + (uint32_t)(s * kGmStageBytes);
-                for (int t = 0; t < ntile; ++t) tma_load_2d(st + t * kGmATile, &smap, x, row0 + 128 * t, full(s));
+                for (int t = 0; t < ntile; ++t) {
+                    // Rt = 128, or the sum of the boxes 64, 32, 16 its bits select;
+                    // each box lands at a multiple of 16 rows (1024-byte aligned)
+                    const int y0 = row0 + 128 * t;
+                    const int Rt = t ? R1 : R0;
+                    if (Rt == 128) {
+                        tma_load_2d(st + t * kGmATile, &smaps.box[0], x, y0, full(s));
+                    } else {
+                        int done = 0;
+#pragma unroll
+                        for (int b = 1; b < 4; ++b) {
+                            const int h = 128 >> b;
+                            if (Rt & h) {
+                                tma_load_2d(st + t * kGmATile + done * kRow, &smaps.box[b], x, y0 + done, full(s));
+                                done += h;
+                            }
+                        }
+                    }
+                }
                 tma_load_2d(st + 2 * kGmATile, &vmap, x, 0, full(s));
                 tma_load_2d(st + 2 * kGmATile + Nv * kRow, &bmap, x, 0, full(s));
                 issued = kb + 1;
@@ -281,13 +311,14 @@ __global__ void __launch_bounds__(kGmThreads, 1)
         const int qw = warp & 3;
         const bool write = ok && !*s_abort;
         for (int t = 0; t < ntile; ++t) {
-            const int r = row0 + 128 * t + 32 * qw + lane;
+            const int rl = 32 * qw + lane;
+            const int r = row0 + 128 * t + rl;
             float* dst = part + ((size_t)slice * m_pad + r) * Ntot;
             for (int c0 = 0; c0 < Ntot; c0 += 16) {
                 uint32_t v[16];
                 tmem_ld16(tmem + ((uint32_t)(32 * qw) << 16) + (uint32_t)(t * Ntot + c0), v);
                 tmem_wait_ld();
-                if (write && r < m) {
+                if (write && 128 * t + rl < rows_q) {          // this group's rows only (all < m)
 #pragma unroll
                     for (int e = 0; e < 16; e += 4)
                         *reinterpret_cast<float4*>(dst + c0 + e) =
@@ -374,6 +405,14 @@ void split_plan(long long n, int groups, int num_sms, long long* chunk, int* nsp
     *nsplit = (int)((n + ch - 1) / ch);
 }
 
+// rows per row group: ceil(m / 256) groups of equal height, a multiple of 16
+// (the smallest S box), the last group taking what is left
+int gauss_group_rows(int m) {
+    const int mg = (m + 255) / 256;
+    const int rg = ((m + mg - 1) / mg + 15) / 16 * 16;
+    return (mg - 1) * rg < m ? rg : 256;              // every group keeps at least one row
+}
+
 int v_rows(int K1) { return (K1 + kGmBRows + 15) / 16 * 16 - kGmBRows; }     // Nv: Nv + 8 a multiple of 16
 
 bool is16(int storage) { return storage == IPF_STORE_BF16 || storage == IPF_STORE_F16; }
@@ -456,13 +495,15 @@ cudaError_t launch_gauss_sv(int storage, const void* S, int m, long long n, cons
         if (Ntot > kGmBRowsMax) return cudaErrorInvalidValue;
         const int BK = variant == 32 ? 32 : 64;
         const int mg = m_pad / 256;
+        const int rg = gauss_group_rows(m);
         long long chunk;
         int nsplit;
         split_plan(n, mg, num_sms, &chunk, &nsplit);
         const CUtensorMapDataType dt =
             storage == IPF_STORE_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
         const cuuint32_t estr[2] = {1, 1};
-        CUtensorMap smap, vmap, bmap;
+        GmSMaps smaps;
+        CUtensorMap vmap, bmap;
         auto make = [&](CUtensorMap* map, const void* base, cuuint64_t rows, cuuint64_t ld, cuuint32_t box_rows) {
             const cuuint64_t dims[2] = {(cuuint64_t)n, rows};
             const cuuint64_t strides[1] = {ld * 2};
@@ -471,15 +512,17 @@ cudaError_t launch_gauss_sv(int storage, const void* S, int m, long long n, cons
                        BK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         };
-        if (make(&smap, S, (cuuint64_t)m, (cuuint64_t)lds, 128) != CUDA_SUCCESS ||
-            make(&vmap, V, (cuuint64_t)kcols, (cuuint64_t)ldv, (cuuint32_t)Nv) != CUDA_SUCCESS ||
+        for (int b = 0; b < 4; ++b)
+            if (make(&smaps.box[b], S, (cuuint64_t)m, (cuuint64_t)lds, (cuuint32_t)(128 >> b)) != CUDA_SUCCESS)
+                return cudaErrorInvalidValue;
+        if (make(&vmap, V, (cuuint64_t)kcols, (cuuint64_t)ldv, (cuuint32_t)Nv) != CUDA_SUCCESS ||
             make(&bmap, bpart, (cuuint64_t)kGmBRows, (cuuint64_t)lds, kGmBRows) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
         auto go = [&](auto kern, int smem) -> cudaError_t {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
             if (e != cudaSuccess) return e;
-            kern<<<nsplit * mg, kGmThreads, smem, s>>>(smap, vmap, bmap, n, m, chunk, mg, Nv, Ntot, (float*)part,
-                                                      m_pad, err);
+            kern<<<nsplit * mg, kGmThreads, smem, s>>>(smaps, vmap, bmap, n, m, chunk, mg, rg, Nv, Ntot,
+                                                      (float*)part, m_pad, err);
             return cudaGetLastError();
         };
         const bool bf = storage == IPF_STORE_BF16;

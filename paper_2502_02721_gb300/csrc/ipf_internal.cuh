@@ -296,6 +296,7 @@ constexpr int kMaxSlots = 64;
 constexpr int kBatchUpdTile = kFoldEvery;      // update tile: the split counters' exact range
 constexpr int kBatchNormTile = 4096;           // normalise tile (elements)
 constexpr int kBatchCsrRows = 16;              // CSR rows per operator tile
+constexpr int kCsrGroup = 8;                   // slots sharing one CSR matrix per pass over it
 
 struct SlotDesc {
     Geom g;
@@ -417,6 +418,10 @@ cudaError_t launch_batch_normalize(int storage, const SlotDesc* slots, const Til
 // (A v_j)(p_i) at the pivot rows into bf.gpiv: tile t of a slot = pivots 8t .. 8t+7
 cudaError_t launch_batch_pivot_rows(int storage, const SlotDesc* slots, const TileRef* tiles, int ntiles, int num_sms,
                                     cudaStream_t s);
+// CSR products of groups of slots sharing one matrix (groups: per group
+// kCsrGroup + 1 ints, the count then the slots; tile.slot = the group)
+cudaError_t launch_batch_csr_group(int storage, const SlotDesc* slots, const int* groups, const TileRef* tiles,
+                                   int ntiles, int num_sms, cudaStream_t s);
 // PSF (FMA column convolution, kw 7 / 15 / 31) and CSR products
 cudaError_t launch_batch_operator(int storage, const SlotDesc* slots, const TileRef* tiles, int ntiles, int num_sms,
                                   cudaStream_t s);

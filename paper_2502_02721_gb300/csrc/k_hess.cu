@@ -625,28 +625,52 @@ __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams
         const bool sk = !skip_sketch;
         const int fold_rounds = kFoldEvery / (256 * 4);
         int round = 0;
-        for (unsigned t0 = blockIdx.x * blockDim.x; t0 < n4; t0 += stride) {
+        // v = u / H(j+1, j) (1 at the pivot) rounded to the storage type, four
+        // elements from i0 on
+        auto emit = [&](unsigned i0, const float4 w4, T* vs) {
+            const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const Acc v = ((long long)(i0 + e) == prow) ? (Acc)1 : wv[e] / hval;
+                vs[e] = from_acc<T>(v);
+            }
+            if constexpr (sizeof(T) == 2) {
+                union { uint2 u; T t[4]; } pk;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) pk.t[e] = vs[e];
+                *reinterpret_cast<uint2*>(vout + i0) = pk.u;
+            } else {
+                *reinterpret_cast<float4*>(vout + i0) =
+                    make_float4(to_acc(vs[0]), to_acc(vs[1]), to_acc(vs[2]), to_acc(vs[3]));
+            }
+        };
+        if (!sk) {
+            // no counters: four loads of w in flight per thread before the
+            // stores (w is dead after this kernel: streamed past L2)
+            constexpr unsigned U = 4;
+            for (unsigned t0 = blockIdx.x * blockDim.x + threadIdx.x; t0 < n4; t0 += stride * U) {
+                float4 w4[U];
+#pragma unroll
+                for (unsigned u = 0; u < U; ++u) {
+                    const unsigned t = t0 + u * stride;
+                    if (t < n4) w4[u] = __ldcs(reinterpret_cast<const float4*>(w) + t);
+                }
+#pragma unroll
+                for (unsigned u = 0; u < U; ++u) {
+                    const unsigned t = t0 + u * stride;
+                    T vs[4];
+                    if (t < n4) emit(t << 2, w4[u], vs);
+                }
+            }
+        }
+        for (unsigned t0 = blockIdx.x * blockDim.x; sk && t0 < n4; t0 += stride) {
             const unsigned t = t0 + threadIdx.x;
             if (t < n4) {
                 const unsigned i0 = t << 2;
                 const float4 w4 = *reinterpret_cast<const float4*>(w + i0);
-                const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
                 T vs[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const Acc v = ((long long)(i0 + e) == prow) ? (Acc)1 : wv[e] / hval;
-                    vs[e] = from_acc<T>(v);
-                }
-                if constexpr (sizeof(T) == 2) {
-                    union { uint2 u; T t[4]; } pk;
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) pk.t[e] = vs[e];
-                    *reinterpret_cast<uint2*>(vout + i0) = pk.u;
-                } else {
-                    *reinterpret_cast<float4*>(vout + i0) = make_float4(to_acc(vs[0]), to_acc(vs[1]), to_acc(vs[2]),
-                                                                        to_acc(vs[3]));
-                }
-                if (sk) {
+                emit(i0, w4, vs);
+                {
                     const uint4 ta = *reinterpret_cast<const uint4*>(tab + i0);
                     const uint4 tb = *reinterpret_cast<const uint4*>(tab + i0 + 2);
                     const uint2 ents[4] = {make_uint2(ta.x, ta.y), make_uint2(ta.z, ta.w), make_uint2(tb.x, tb.y),

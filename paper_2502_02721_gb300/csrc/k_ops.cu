@@ -746,7 +746,86 @@ __global__ void __launch_bounds__(256) kb_pivot_rows(const SlotDesc* __restrict_
     }
 }
 
+// CSR products of up to kCsrGroup slots that share one matrix: tile t of a
+// group = its rows 16t .. 16t + 15, one warp per row; a row's nonzeros are
+// loaded once for all slots of the group, and each slot's sum runs over them
+// in the order of csr_rows (lane-strided, then the same shuffle tree), so a
+// slot gets the same bits as alone.  groups[g]: count, then the slots.
+template <class T>
+__global__ void __launch_bounds__(128) kb_csr_group(const SlotDesc* __restrict__ slots,
+                                                    const int* __restrict__ groups,
+                                                    const TileRef* __restrict__ tiles, int ntiles) {
+    __shared__ int s_j[kCsrGroup];
+    __shared__ int s_n;
+    for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+        const TileRef tr = tiles[tt];
+        const int* grp = groups + (size_t)tr.slot * (kCsrGroup + 1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_n = grp[0];
+            for (int q = 0; q < s_n; ++q) {
+                const SlotDesc* sd = slots + grp[1 + q];
+                int j = -1;
+                if (sd->k_target > 0) {
+                    const DevState* st = sd->bf.st;
+                    j = st->j;
+                    if (st->status[0] != IPF_OK || j >= sd->k_target || j >= sd->g.k_max) j = -1;
+                }
+                s_j[q] = j;
+            }
+        }
+        __syncthreads();
+        const int ng = s_n;
+        const OpDev& op = slots[grp[1]].op;
+        const long long r0 = (long long)tr.tile * kBatchCsrRows;
+        const long long r1 = min((long long)op.rows, r0 + kBatchCsrRows);
+        const int lane = threadIdx.x & 31;
+        for (long long row = r0 + threadIdx.x / 32; row < r1; row += blockDim.x / 32) {
+            const long long b0 = op.rowptr[row], b1 = op.rowptr[row + 1];
+            float P[kCsrGroup];
+            const T* v[kCsrGroup];
+#pragma unroll
+            for (int q = 0; q < kCsrGroup; ++q) {
+                P[q] = 0.f;
+                const SlotDesc* sd = slots + grp[1 + (q < ng ? q : 0)];
+                v[q] = (q < ng && s_j[q] >= 0) ? (const T*)sd->bf.V + (size_t)s_j[q] * sd->g.ldv : nullptr;
+            }
+            for (long long base = b0; base < b1; base += 32) {
+                const long long pq = base + lane;
+                if (pq < b1) {
+                    const float a = op.vals[pq];
+                    const int c = op.colind[pq];
+#pragma unroll
+                    for (int q = 0; q < kCsrGroup; ++q)
+                        if (v[q]) P[q] = fmaf(a, to_acc(v[q][c]), P[q]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kCsrGroup; ++q) {
+                if (q >= ng || s_j[q] < 0) continue;             // uniform for the warp
+                float acc = P[q];
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) acc = acc + __shfl_xor_sync(0xffffffffu, acc, o);
+                if (lane == 0) ((float*)slots[grp[1 + q]].bf.w)[row] = acc;
+            }
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_batch_csr_group(int storage, const SlotDesc* slots, const int* groups, const TileRef* tiles,
+                                   int ntiles, int num_sms, cudaStream_t s) {
+    if (ntiles <= 0) return cudaSuccess;
+    const int blocks = ntiles < num_sms * 8 ? ntiles : num_sms * 8;
+    switch (storage) {
+        case IPF_STORE_F32: kb_csr_group<float><<<blocks, 128, 0, s>>>(slots, groups, tiles, ntiles); break;
+        case IPF_STORE_BF16: kb_csr_group<__nv_bfloat16><<<blocks, 128, 0, s>>>(slots, groups, tiles, ntiles); break;
+        case IPF_STORE_F16: kb_csr_group<__half><<<blocks, 128, 0, s>>>(slots, groups, tiles, ntiles); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_batch_pivot_rows(int storage, const SlotDesc* slots, const TileRef* tiles, int ntiles, int num_sms,
                                     cudaStream_t s) {

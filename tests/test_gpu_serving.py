@@ -137,6 +137,52 @@ def test_batched_fma_and_csr_equal_the_context():
         assert np.array_equal(out[3], _alone(bd, r, keep, overlap=2, conv_fma=1)), (r["kind"], r["storage"])
 
 
+def test_batched_csr_requests_sharing_a_matrix():
+    """CSR requests on one operator (one set of device arrays) share each
+    pass over its nonzeros in the batched step (groups of up to eight);
+    each request's sums keep the one-request order, so every x equals the
+    context's x bit for bit, whatever the group it ran in."""
+    import torch
+    ensure_lib()
+    from paper_2502_02721_gb300 import binding as bd
+    ct = P.ct_parallel(side=32, nrhs=1, k=20, m_s=80)
+    keep = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (ct.rowptr, ct.colind, ct.vals)]
+    n = 32 * 32
+    # device arrays: referenced by every request, not copied
+    op = bd.make_operator("csr", n, n, rowptr=keep[0], colind=keep[1], vals=keep[2], keep=keep)
+    rng = np.random.default_rng(5)
+    reqs = []
+    for t in range(11):                       # one full group of eight and one of three
+        k = int(rng.integers(6, 20))
+        b = (ct.b * (1.0 + 0.1 * rng.standard_normal(ct.b.shape))).astype(np.float32)
+        reqs.append(dict(b=b, k=k, m_s=4 * k, lam=float(10 ** rng.uniform(-4, -2)),
+                         storage=["bf16", "f32"][t % 3 == 2], seed=4000 + t))
+    srv = bd.Server(hbm_budget_bytes=2 << 30, max_inflight=16, steps_per_slice=4)
+    tickets = [srv.submit(op, r["b"], bd.default_config(k_max=r["k"], m_s=r["m_s"], zeta=8, seed=r["seed"],
+                                                        storage=r["storage"]), r["k"], r["lam"]) for r in reqs]
+    results = {}
+    t0 = time.time()
+    while len(results) < len(tickets) and time.time() - t0 < 120:
+        for t in tickets:
+            if t not in results:
+                out = srv.poll(t)
+                if out is not None:
+                    results[t] = out
+        time.sleep(0.002)
+    stats = srv.batch_stats()
+    srv.close()
+    assert len(results) == len(tickets) and stats[0] == len(reqs)
+    for r, t in zip(reqs, tickets):
+        out = results[t]
+        assert out[0] == bd.IPF_OK and out[1] == r["k"]
+        cfg = bd.default_config(k_max=r["k"], m_s=r["m_s"], zeta=8, seed=r["seed"], storage=r["storage"], overlap=2)
+        ctx = bd.Context(op, r["b"], cfg, keep)
+        ctx.step(r["k"])
+        xa, _ = ctx.solve(r["k"], [r["lam"]])
+        ctx.close()
+        assert np.array_equal(out[3], xa[0]), (r["storage"], r["k"])
+
+
 def test_batched_tensor_cores_equal_the_context(tmp_path, monkeypatch):
     """BF16 PSF requests on the tensor-core convolution, with the tuner's
     choice pinned (IPF_TUNE_CACHE) to the band height a context uses on a
