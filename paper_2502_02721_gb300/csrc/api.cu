@@ -607,7 +607,7 @@ size_t ipf_footprint(const ipf_operator* op, const ipf_config* cfg) {
     size_t bytes = basis(gh ? op_m(op) : n) + (gh ? basis(n) : 0);
     if (gh) bytes += 2 * (size_t)B * op_m(op) * 4;
     if (cfg->sketch == IPF_SKETCH_GAUSSIAN)
-        bytes += (size_t)cfg->m_s * gauss_lds(n) * sb + (size_t)cfg->m_s * K1 * 8 + 8 * (size_t)cfg->m_s +
+        bytes += gauss_s_bytes(cfg->storage, cfg->m_s, n) + (size_t)cfg->m_s * K1 * 8 + 8 * (size_t)cfg->m_s +
                  gauss_workspace_bytes(cfg->storage, cfg->m_s, n, cfg->k_max, device_sms()) + 3 * 256;
     Geom g; g.n = n; g.B = B; g.N = n * B; g.ldv = (long long)ldv; g.k_max = cfg->k_max; g.m_s = cfg->m_s; g.F = 0;
     bytes += solve_ws_for(g) + 2 * (size_t)B * n * 4 + 256 + ldv * 4 + B * K1 * 4;
@@ -775,14 +775,13 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
                       (((uintptr_t)bf.V | (uintptr_t)bf.sktab) & 15u) == 0 && (g.ldv & 7) == 0;
     g.sketch_defer = c->defer_sketch ? 1 : 0;
     if (gauss) {
-        const size_t sb = storage_bytes(cfg.storage);
         const size_t wsb = gauss_workspace_bytes(cfg.storage, cfg.m_s, n, cfg.k_max, c->num_sms);
-        CK("alloc Gaussian S", c->al.get(&c->gS, (size_t)cfg.m_s * gauss_lds(n) * sb));
+        CK("alloc Gaussian S", c->al.get(&c->gS, gauss_s_bytes(cfg.storage, cfg.m_s, n)));
         CK("alloc S V", c->al.get(&c->gSV, (size_t)cfg.m_s * (cfg.k_max + 1) * (cfg.storage == IPF_STORE_F64 ? 8 : 4)));
         CK("alloc S b", c->al.get((void**)&c->gC, sizeof(double) * cfg.m_s));
         CK("alloc Gaussian workspace", c->al.get(&c->gWs, wsb));
         CK("memset Gaussian workspace", cudaMemsetAsync(c->gWs, 0, wsb, c->s));
-        CK("Gaussian S", launch_gauss_fill(cfg.storage, c->gS, n, cfg.m_s, gauss_lds(n), cfg.seed, c->num_sms, c->s));
+        CK("Gaussian S", launch_gauss_fill_ctx(cfg.storage, c->gS, n, cfg.m_s, cfg.seed, c->num_sms, c->s));
         c->gvariant = gauss_variant(cfg.storage, c->gS, cfg.m_s, n, c->bf.V, c->g.ldv, cfg.k_max + 1, c->gWs, c->gSV,
                                     c->gC, &c->bf.st->status[0], c->num_sms, c->s);
     }
@@ -1285,6 +1284,22 @@ ipf_status ipf_sketch_gaussian(int storage, unsigned long long seed, long long n
 }  // extern "C"
 
 namespace ipf {
+
+cudaError_t raise_smem_ptr(const void* fn, size_t bytes) {
+    static std::mutex mu;
+    static std::vector<std::pair<const void*, size_t>> set;   // kernel, limit in force
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto& e : set)
+        if (e.first == fn) {
+            if (e.second >= bytes) return cudaSuccess;
+            const cudaError_t r = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+            if (r == cudaSuccess) e.second = bytes;
+            return r;
+        }
+    const cudaError_t r = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (r == cudaSuccess) set.emplace_back(fn, bytes);
+    return r;
+}
 
 // The batched step of the serving loop drives contexts whose every step is
 // one of the batched kernels: one RHS, float storage, the sparse-sign sketch

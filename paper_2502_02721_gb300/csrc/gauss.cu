@@ -90,6 +90,43 @@ __device__ __forceinline__ bool gauss_fast(unsigned long long o1, unsigned long 
     return true;
 }
 
+// entry with counter c = r*n + i in the storage type (16-bit types as bits)
+template <class T>
+__device__ __forceinline__ unsigned short gauss_bits16(unsigned long long c, unsigned long long seed, double sqrt_m,
+                                                       float inv_sqrt_m) {
+    const unsigned long long o1 = sm64_mix(seed + kGamma * (2ull * c + 1ull));
+    const unsigned long long o2 = sm64_mix(seed + kGamma * (2ull * c + 2ull));
+    unsigned short bits;
+    if (!gauss_fast<T>(o1, o2, inv_sqrt_m, bits)) {
+        const double v = gauss_f64(o1, o2, sqrt_m);
+        if constexpr (std::is_same<T, __half>::value) bits = __half_as_ushort(__double2half(v));
+        else bits = store_bits<T>((float)v);                 // FP64 -> FP32 -> BF16
+    }
+    return bits;
+}
+
+// The tiled layout of S for the tensor-core contraction (16-bit storage):
+// units of 16 rows x 64 elements (2 KB, row-major inside), unit (rt, kb) =
+// rows 16 rt .., elements 64 kb .. at offset (rt * nkb + kb) * 1024 elements,
+// nkb = ceil(n / 64).  A stage of the contraction then reads whole 2 KB
+// pieces of DRAM instead of 128 bytes of each of 128 rows 2n bytes apart.
+// Entries outside m x n are zero (the basis is zero-filled there, and
+// 0 x 0 must stay 0).
+template <class T>
+__global__ void __launch_bounds__(256) k_gauss_fill_tiled(T* __restrict__ S, long long n, int m, unsigned nkb,
+                                                          unsigned long long total, unsigned long long seed,
+                                                          double sqrt_m, float inv_sqrt_m) {
+    unsigned short* S16 = reinterpret_cast<unsigned short*>(S);
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long t = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; t < total; t += stride) {
+        const unsigned u = (unsigned)(t >> 10), w = (unsigned)(t & 1023u);
+        const unsigned rt = u / nkb, kb = u - rt * nkb;
+        const long long r = 16ll * rt + (w >> 6), i = 64ll * kb + (w & 63u);
+        S16[t] = (r < m && i < n) ? gauss_bits16<T>((unsigned long long)(r * n + i), seed, sqrt_m, inv_sqrt_m)
+                                  : (unsigned short)0;
+    }
+}
+
 // entry c = r*n + i (the counter) goes to S[r*lds + i]; the walk carries
 // (r, i) instead of a 64-bit division per entry
 template <class T>
@@ -101,18 +138,12 @@ __global__ void __launch_bounds__(256) k_gauss_fill(T* __restrict__ S, long long
     long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     long long r = c / n, i = c - r * n;
     for (; c < total; c += stride) {
-        const unsigned long long o1 = sm64_mix(seed + kGamma * (2ull * (unsigned long long)c + 1ull));
-        const unsigned long long o2 = sm64_mix(seed + kGamma * (2ull * (unsigned long long)c + 2ull));
         const long long t = r * lds + i;
         if constexpr (sizeof(T) == 2) {
-            unsigned short bits;
-            if (!gauss_fast<T>(o1, o2, inv_sqrt_m, bits)) {
-                const double v = gauss_f64(o1, o2, sqrt_m);
-                if constexpr (std::is_same<T, __half>::value) bits = __half_as_ushort(__double2half(v));
-                else bits = store_bits<T>((float)v);                 // FP64 -> FP32 -> BF16
-            }
-            reinterpret_cast<unsigned short*>(S)[t] = bits;
+            reinterpret_cast<unsigned short*>(S)[t] = gauss_bits16<T>((unsigned long long)c, seed, sqrt_m, inv_sqrt_m);
         } else {
+            const unsigned long long o1 = sm64_mix(seed + kGamma * (2ull * (unsigned long long)c + 1ull));
+            const unsigned long long o2 = sm64_mix(seed + kGamma * (2ull * (unsigned long long)c + 2ull));
             S[t] = (T)gauss_f64(o1, o2, sqrt_m);
         }
         i += si;
@@ -261,17 +292,21 @@ __global__ void __launch_bounds__(kGmThreads, 1)
                 for (int t = 0; t < ntile; ++t) {
                     // Rt = 128, or the sum of the boxes 64, 32, 16 its bits select;
                     // each box lands at a multiple of 16 rows (1024-byte aligned)
+                    // S is tiled (units of 16 rows x 64 elements): element x is
+                    // (x mod 64) of unit column x / 64, row y of unit row y / 16
                     const int y0 = row0 + 128 * t;
                     const int Rt = t ? R1 : R0;
+                    const int xu = x & 63, zu = x >> 6;
                     if (Rt == 128) {
-                        tma_load_2d(st + t * kGmATile, &smaps.box[0], x, y0, full(s));
+                        tma_load_4d(st + t * kGmATile, &smaps.box[0], xu, 0, zu, y0 >> 4, full(s));
                     } else {
                         int done = 0;
 #pragma unroll
                         for (int b = 1; b < 4; ++b) {
                             const int h = 128 >> b;
                             if (Rt & h) {
-                                tma_load_2d(st + t * kGmATile + done * kRow, &smaps.box[b], x, y0 + done, full(s));
+                                tma_load_4d(st + t * kGmATile + done * kRow, &smaps.box[b], xu, 0, zu,
+                                            (y0 + done) >> 4, full(s));
                                 done += h;
                             }
                         }
@@ -459,6 +494,29 @@ cudaError_t launch_gauss_fill(int storage, void* S, long long n, int m, long lon
     return cudaGetLastError();
 }
 
+size_t gauss_s_bytes(int storage, int m, long long n) {
+    if (is16(storage)) return (size_t)((m + 15) / 16) * (size_t)((n + 63) / 64) * 1024 * 2;
+    const size_t sb = storage == IPF_STORE_F64 ? 8 : 4;
+    return (size_t)m * gauss_lds(n) * sb;
+}
+
+cudaError_t launch_gauss_fill_ctx(int storage, void* S, long long n, int m, unsigned long long seed, int num_sms,
+                                  cudaStream_t s) {
+    if (n <= 0 || m <= 0) return cudaSuccess;
+    if (!is16(storage)) return launch_gauss_fill(storage, S, n, m, gauss_lds(n), seed, num_sms, s);
+    const unsigned nkb = (unsigned)((n + 63) / 64);
+    const unsigned long long total = (unsigned long long)((m + 15) / 16) * nkb * 1024ull;
+    if (total / 1024ull >= (1ull << 32)) return cudaErrorInvalidValue;
+    const int blocks = num_sms * 8;
+    const double sq = sqrt((double)m);
+    const float inv = (float)(1.0 / sq);
+    if (storage == IPF_STORE_BF16)
+        k_gauss_fill_tiled<__nv_bfloat16><<<blocks, 256, 0, s>>>((__nv_bfloat16*)S, n, m, nkb, total, seed, sq, inv);
+    else
+        k_gauss_fill_tiled<__half><<<blocks, 256, 0, s>>>((__half*)S, n, m, nkb, total, seed, sq, inv);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gauss_bparts(int storage, const float* b, long long n, void* ws, cudaStream_t s) {
     const long long ldb = gauss_lds(n);
     const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
@@ -512,14 +570,23 @@ cudaError_t launch_gauss_sv(int storage, const void* S, int m, long long n, cons
                        BK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         };
-        for (int b = 0; b < 4; ++b)
-            if (make(&smaps.box[b], S, (cuuint64_t)m, (cuuint64_t)lds, (cuuint32_t)(128 >> b)) != CUDA_SUCCESS)
+        // S tiled: dims (64 elements, 16 rows, nkb unit columns, nrt unit rows)
+        const cuuint64_t nkb = (cuuint64_t)((n + 63) / 64), nrt = (cuuint64_t)((m + 15) / 16);
+        for (int b = 0; b < 4; ++b) {
+            const cuuint64_t dims[4] = {64, 16, nkb, nrt};
+            const cuuint64_t strides[3] = {128, 2048, nkb * 2048};
+            const cuuint32_t box[4] = {(cuuint32_t)BK, 16, 1, (cuuint32_t)(8 >> b)};
+            const cuuint32_t e4[4] = {1, 1, 1, 1};
+            if (enc(&smaps.box[b], dt, 4, const_cast<void*>(S), dims, strides, box, e4, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    BK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
                 return cudaErrorInvalidValue;
+        }
         if (make(&vmap, V, (cuuint64_t)kcols, (cuuint64_t)ldv, (cuuint32_t)Nv) != CUDA_SUCCESS ||
             make(&bmap, bpart, (cuuint64_t)kGmBRows, (cuuint64_t)lds, kGmBRows) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
         auto go = [&](auto kern, int smem) -> cudaError_t {
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            cudaError_t e = raise_smem(kern, smem);
             if (e != cudaSuccess) return e;
             kern<<<nsplit * mg, kGmThreads, smem, s>>>(smaps, vmap, bmap, n, m, chunk, mg, rg, Nv, Ntot,
                                                       (float*)part, m_pad, err);

@@ -333,6 +333,16 @@ __device__ __forceinline__ int slot_step(const SlotDesc* sd, int* s_j) {
     return *s_j;
 }
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes`, never
+// lowering it: the limit is one process-wide attribute of the function, and
+// a launch captured in a CUDA graph with a larger size (another context's or
+// engine's k_max) must stay valid after a smaller launch elsewhere (api.cu;
+// thread safe).
+cudaError_t raise_smem_ptr(const void* fn, size_t bytes);
+template <class F> inline cudaError_t raise_smem(F fn, size_t bytes) {
+    return raise_smem_ptr(reinterpret_cast<const void*>(fn), bytes);
+}
+
 // ---------------------------------------------------------------------------
 // launchers (defined in the .cu files)
 // ---------------------------------------------------------------------------
@@ -362,10 +372,18 @@ cudaError_t launch_op_apply_f32_plain(const OpDev& op, const float* v, float* w,
                                       cudaStream_t s);
 // k_hess.cu
 cudaError_t launch_reset_state(DevState* st, cudaStream_t s);
-// Gaussian sketch (gauss.cu).  S is row-major, m rows of lds = gauss_lds(n)
-// elements (entry (r, i) at r*lds + i); the workspace holds the rows of b
-// the contraction takes as extra B columns (zeroed at creation, written per
-// right-hand side by launch_gauss_bparts) and the slices' partial tiles.
+// Gaussian sketch (gauss.cu).  A context's S (launch_gauss_fill_ctx,
+// gauss_s_bytes): for BF16 / FP16 storage tiled in units of 16 rows x 64
+// elements (unit (r / 16, i / 64) at ((r / 16) ceil(n / 64) + i / 64) 1024
+// elements, row-major inside, zero outside m x n), for FP32 / FP64 row-major
+// with m rows of lds = gauss_lds(n) elements (entry (r, i) at r*lds + i);
+// launch_gauss_fill writes the row-major form with any lds (the public
+// ipf_sketch_gaussian).  The workspace holds the rows of b the contraction
+// takes as extra B columns (zeroed at creation, written per right-hand side
+// by launch_gauss_bparts) and the slices' partial tiles.
+size_t gauss_s_bytes(int storage, int m, long long n);
+cudaError_t launch_gauss_fill_ctx(int storage, void* S, long long n, int m, unsigned long long seed, int num_sms,
+                                  cudaStream_t s);
 long long gauss_lds(long long n);
 size_t gauss_workspace_bytes(int storage, int m, long long n, int k_max, int num_sms);
 cudaError_t launch_gauss_fill(int storage, void* S, long long n, int m, long long lds, unsigned long long seed,

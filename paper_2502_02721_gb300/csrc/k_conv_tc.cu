@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 template <int KP>
 cudaError_t launch_kp(const CUtensorMap& map, const int* jptr, float* w, int H, int W, const void* bimg, int* err,
                       cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv2d_tc<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemRequest);
+    cudaError_t e = raise_smem(k_conv2d_tc<KP>, kSmemRequest);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 1;
     e = cudaGetDevice(&dev);
@@ -456,11 +456,11 @@ cudaError_t launch_batch_conv_tc(int kp, const void* maps, const SlotDesc* slots
     if (nunits <= 0) return cudaSuccess;
     const TcMaps& m = *(const TcMaps*)maps;
     if (kp == 32) {
-        cudaError_t e = cudaFuncSetAttribute(kb_conv_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemRequest);
+        cudaError_t e = raise_smem(kb_conv_tc<32>, kSmemRequest);
         if (e != cudaSuccess) return e;
         kb_conv_tc<32><<<nunits, kThreads, kSmemRequest, s>>>(m, slots, units, nunits);
     } else if (kp == 16) {
-        cudaError_t e = cudaFuncSetAttribute(kb_conv_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemRequest);
+        cudaError_t e = raise_smem(kb_conv_tc<16>, kSmemRequest);
         if (e != cudaSuccess) return e;
         kb_conv_tc<16><<<nunits, kThreads, kSmemRequest, s>>>(m, slots, units, nunits);
     } else {

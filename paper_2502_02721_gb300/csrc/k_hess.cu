@@ -125,11 +125,13 @@ __device__ __forceinline__ void pivot_solve_body(const Geom& g, const Bufs& bf, 
         return;
     }
     // four warps (one per SM partition, so four FP64 pipes): warp w holds the
-    // row groups w and w + 4 (rows 32q + lane) in registers.  Column c's
-    // value x_c is final in the warp holding its row group once columns < c
-    // are applied; that warp publishes it through shared memory, a 128-thread
-    // named barrier orders it, and every warp applies column c to its rows.
-    // Each row still takes its updates in column order.
+    // row groups w and w + 4 (rows 32q + lane) in registers.  Column block cb
+    // (columns 32cb .. 32cb + 31): the warp holding row group cb solves its
+    // diagonal block alone (x_c by a shuffle, no barrier), publishes the 32
+    // final values through shared memory, one 128-thread named barrier
+    // orders them, and every warp applies the block's columns to its rows
+    // below.  Each row still takes its updates in column order (blocks in
+    // order, columns in order within a block), one barrier per 32 columns.
     if (threadIdx.x >= 128) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int qmax = j >> 5;                               // last row group holding a row <= j
@@ -143,24 +145,31 @@ __device__ __forceinline__ void pivot_solve_body(const Geom& g, const Bufs& bf, 
         off[h] = i * (i - 1) / 2;
     }
     for (int cb = 0; cb <= qmax; ++cb) {
-        const int cend = j - cb * 32 < 32 ? j - cb * 32 : 32;     // columns c = cb*32 + cc < j
-        const bool owner = warp == (cb & 3);
-        const int oh = cb >> 2;
+        const int c0 = cb * 32;
+        const int cend = j - c0 < 32 ? j - c0 : 32;            // columns c = c0 + cc < j
+        if (warp == (cb & 3)) {
+            const int oh = cb >> 2;
+            double xv = oh ? x[1] : x[0];
+            const int offr = oh ? off[1] : off[0];
+            const bool row_ok = c0 + lane <= j;
 #pragma unroll 1
-        for (int cc = 0; cc < cend; ++cc) {
-            const int c = cb * 32 + cc;
-            if (owner) {
-                const double xc = __shfl_sync(0xffffffffu, oh ? x[1] : x[0], cc);
-                if (lane == 0) s_x[c] = xc;
+            for (int cc = 0; cc < cend; ++cc) {
+                const double xc = __shfl_sync(0xffffffffu, xv, cc);
+                if (row_ok && lane > cc) xv = fma(-s_L[offr + c0 + cc], xc, xv);
             }
-            asm volatile("bar.sync 1, 128;" ::: "memory");
-            const double xc = s_x[c];
+            if (oh) x[1] = xv; else x[0] = xv;
+            if (c0 + lane < j) s_x[c0 + lane] = xv;
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int q = warp + 4 * h;
-                // rows i > c with i <= j only: s_L holds rows 1..j and nothing beyond
-                if (q >= cb && q <= qmax && (q > cb || lane > cc) && q * 32 + lane <= j)
-                    x[h] = fma(-s_L[off[h] + c], xc, x[h]);
+        for (int h = 0; h < 2; ++h) {
+            const int q = warp + 4 * h;
+            // rows i > c with i <= j only: s_L holds rows 1..j and nothing beyond
+            if (q > cb && q <= qmax && q * 32 + lane <= j) {
+                double xv = x[h];
+#pragma unroll 4
+                for (int cc = 0; cc < cend; ++cc) xv = fma(-s_L[off[h] + c0 + cc], s_x[c0 + cc], xv);
+                x[h] = xv;
             }
         }
     }
@@ -1376,7 +1385,7 @@ cudaError_t launch_pivot_solve(int storage, const Geom& g, const Bufs& bf, cudaS
         // packed L_p, then g (K1, rounded to even) and the column values x_c (K1)
         const size_t smem = lp_stride(g.k_max) * sizeof(double) + (size_t)(((K1 + 1) & ~1) + K1 + 1) * sizeof(double);
         auto fn = k_pivot_solve<T, Acc>;
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = raise_smem(fn, (int)smem);
         if (e != cudaSuccess) return e;
         fn<<<g.B, 256, smem, s>>>(g, bf);
     });
@@ -1388,7 +1397,7 @@ static cudaError_t update_B(const Geom& g, const Bufs& bf, const SketchParams& s
                            cudaStream_t s) {
     auto go = [&](auto fn) -> cudaError_t {
         if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaError_t e = raise_smem(fn, (int)smem);
             if (e != cudaSuccess) return e;
         }
         fn<<<blocks, 256, smem, s>>>(g, bf, sp);
@@ -1509,7 +1518,7 @@ cudaError_t launch_normalize(int storage, const Geom& g, const Bufs& bf, const S
     IPF_DISPATCH_STORAGE(storage, {
         using Acc = typename AccOf<T>::type;
         auto fn = k_normalize<T, Acc>;
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = raise_smem(fn, (int)smem);
         if (e != cudaSuccess) return e;
         fn<<<grid, 256, smem, s>>>(g, bf, sp, want_sw ? 1 : 0, Bg, lbg, lb);
     });
@@ -1525,20 +1534,19 @@ cudaError_t launch_sketch_col(int storage, const Geom& g, const Bufs& bf, const 
     if (blocks < 1) blocks = 1;
     switch (storage) {
         case IPF_STORE_F32: {
-            cudaError_t e = cudaFuncSetAttribute(k_sketch_col<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaError_t e = raise_smem(k_sketch_col<float>, (int)smem);
             if (e != cudaSuccess) return e;
             k_sketch_col<float><<<(int)blocks, 256, smem, s>>>(g, bf, sp);
             break;
         }
         case IPF_STORE_BF16: {
-            cudaError_t e = cudaFuncSetAttribute(k_sketch_col<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)smem);
+            cudaError_t e = raise_smem(k_sketch_col<__nv_bfloat16>, (int)smem);
             if (e != cudaSuccess) return e;
             k_sketch_col<__nv_bfloat16><<<(int)blocks, 256, smem, s>>>(g, bf, sp);
             break;
         }
         case IPF_STORE_F16: {
-            cudaError_t e = cudaFuncSetAttribute(k_sketch_col<__half>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaError_t e = raise_smem(k_sketch_col<__half>, (int)smem);
             if (e != cudaSuccess) return e;
             k_sketch_col<__half><<<(int)blocks, 256, smem, s>>>(g, bf, sp);
             break;
@@ -1566,7 +1574,7 @@ cudaError_t launch_sketch_vector(const float* x, long long n, const SketchParams
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = (size_t)sp.m_s * 8;
-    e = cudaFuncSetAttribute(k_sketch_vec, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = raise_smem(k_sketch_vec, (int)smem);
     if (e != cudaSuccess) return e;
     k_sketch_vec<<<(int)blocks, 256, smem, s>>>(x, n, sp, amax, acc);
     return cudaGetLastError();
@@ -1587,7 +1595,7 @@ cudaError_t launch_batch_pivot_solve(int storage, const SlotDesc* slots, const T
     const int K1 = k_max + 1;
     const size_t smem = lp_stride(k_max) * sizeof(double) + (size_t)(((K1 + 1) & ~1) + K1 + 1) * sizeof(double);
     auto go = [&](auto fn) -> cudaError_t {
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = raise_smem(fn, (int)smem);
         if (e != cudaSuccess) return e;
         fn<<<nslots, 256, smem, s>>>(slots, list);
         return cudaGetLastError();
@@ -1607,7 +1615,7 @@ cudaError_t launch_batch_update(int storage, const SlotDesc* slots, const TileRe
     const int blocks = ntiles < num_sms * 4 ? ntiles : num_sms * 4;
     auto go = [&](auto fn) -> cudaError_t {
         if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaError_t e = raise_smem(fn, (int)smem);
             if (e != cudaSuccess) return e;
         }
         fn<<<blocks, 256, smem, s>>>(slots, tiles, ntiles);

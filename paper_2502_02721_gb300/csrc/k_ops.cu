@@ -441,7 +441,7 @@ cudaError_t conv_dispatch(const OpDev& op, const T* v, long long ldv, const int*
     auto go = [&](auto kern, int KW, int TY, int TX) -> cudaError_t {
         const int IWP = (TX + KW - 1 + 3) & ~3;
         const size_t smem = ((size_t)(TY + op.ph - 1) * IWP + (size_t)op.ph * KW) * sizeof(Acc);
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = raise_smem(kern, (int)smem);
         if (e != cudaSuccess) return e;
         dim3 grid((W + TX - 1) / TX, (H + TY - 1) / TY);
         kern<<<grid, 256, smem, s>>>(v, ldv, jp, w, H, W, op.psf, op.ph, op.pw);
@@ -456,7 +456,7 @@ cudaError_t conv_dispatch(const OpDev& op, const T* v, long long ldv, const int*
             const int NIN = (OX + KW - 1 + 3) & ~3;
             const int IWP = TX - OX + NIN;
             const size_t smem = ((size_t)(TY + op.ph - 1) * IWP + (size_t)op.ph * KWP) * sizeof(float);
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaError_t e = raise_smem(kern, (int)smem);
             if (e != cudaSuccess) return e;
             dim3 grid((W + TX - 1) / TX, (H + TY - 1) / TY);
             kern<<<grid, 256, smem, s>>>(v, ldv, jp, (float*)w, H, W, op.psf, op.ph, op.pw);
@@ -466,7 +466,7 @@ cudaError_t conv_dispatch(const OpDev& op, const T* v, long long ldv, const int*
         auto goc = [&](auto kern, int KW, int OY) -> cudaError_t {
             const int IH = OY + KW - 1, IWP = 256 + KW;
             const size_t smem = ((size_t)IH * IWP + (size_t)KW * KW) * sizeof(float);
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaError_t e = raise_smem(kern, (int)smem);
             if (e != cudaSuccess) return e;
             dim3 grid((W + 255) / 256, (H + OY - 1) / OY);
             kern<<<grid, 256, smem, s>>>(v, ldv, jp, (float*)w, H, W, op.psf, op.ph, op.pw);
@@ -475,7 +475,7 @@ cudaError_t conv_dispatch(const OpDev& op, const T* v, long long ldv, const int*
         auto goc2 = [&](auto kern, int KW, int OY) -> cudaError_t {
             const int IH = OY + KW - 1, IWP = 128 + KW;
             const size_t smem = (size_t)IH * IWP * sizeof(float);
-            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaError_t e = raise_smem(kern, (int)smem);
             if (e != cudaSuccess) return e;
             dim3 grid((W + 127) / 128, (H + OY - 1) / OY);
             kern<<<grid, 128, smem, s>>>(v, ldv, jp, (float*)w, H, W, op.psf_pairs);
@@ -506,7 +506,7 @@ cudaError_t sep_dispatch(const OpDev& op, const T* v, long long ldv, const int* 
     const size_t smem = ((size_t)A0 * A0 + (size_t)A0 * A1 + (size_t)A1 * A1 + 2 * op.slen +
                          (size_t)op.mlen * op.mlen) * sizeof(Acc);
     auto kern = k_sep_motion<T, Acc, TILE>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_smem(kern, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((op.cols + TILE - 1) / TILE, (op.rows + TILE - 1) / TILE);
     kern<<<grid, 256, smem, s>>>(v, ldv, jp, w, op.rows, op.cols, op.sep_row, op.sep_col, op.slen, op.motion, op.mlen);

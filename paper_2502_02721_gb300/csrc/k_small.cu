@@ -479,7 +479,7 @@ cudaError_t launch_solve_prepare(const Geom& g, const Bufs& bf, int zeta, int k,
     }
     const int njobs = g.B * (need_T ? 2 : 1);
     const size_t smem = 2 * sizeof(double) * (size_t)g.m_s;
-    e = cudaFuncSetAttribute(k_householder, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = raise_smem(k_householder, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_householder, 256, smem);
@@ -523,7 +523,7 @@ cudaError_t launch_solve_lambdas(int storage, const Geom& g, const Bufs& bf, int
         const int NLp = nlc <= 1 ? 1 : nlc <= 2 ? 2 : nlc <= 4 ? 4 : 8;
         auto launch = [&](auto kern, int vec) -> cudaError_t {
             const size_t smem = accsz * (size_t)NLp * g.B * (k > 0 ? k : 1);
-            cudaError_t ee = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaError_t ee = raise_smem(kern, (int)smem);
             if (ee != cudaSuccess) return ee;
             long long chunks = (g.N + 256LL * vec - 1) / (256LL * vec);
             long long blocks = (long long)num_sms * 4;
