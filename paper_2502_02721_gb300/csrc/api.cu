@@ -580,10 +580,8 @@ void ipf_config_default(ipf_config* cfg) {
 }
 
 // stride between basis vectors: N rounded up to 64 elements (16-byte
-// aligned columns for 128-bit loads and TMA) plus 128 elements, so that
-// columns of a power-of-two length do not all start at the same offset of
-// the same DRAM partitions (every step streams all columns side by side)
-static size_t ldv_for(long long N) { return (size_t)((N + 63) / 64 * 64 + 128); }
+// aligned columns for 128-bit loads and TMA)
+static size_t ldv_for(long long N) { return (size_t)((N + 63) / 64 * 64); }
 
 static int lam_chunk(int B) { return B >= kLamChunk ? 1 : kLamChunk / B; }
 static size_t solve_ws_for(const Geom& g) { return solve_workspace_bytes(g, lam_chunk(g.B)); }

@@ -160,7 +160,9 @@ struct BatchEngine {
     std::vector<unsigned char> maps;     // kMaxSlots tensor maps, host (passed by value at launch)
     SlotDesc* d_slots = nullptr;         // kMaxSlots entries
     SlotDesc* d_tune = nullptr;          // kMaxSlots entries, for the tuner's one-slot tables
-    int* d_groups = nullptr;             // kMaxSlots x (kCsrGroup + 1): CSR slots sharing one matrix
+    int* d_groups = nullptr;             // kMaxSlots x kCsrGroupRec: CSR slots sharing one matrix
+    unsigned char* d_stage = nullptr;    // the groups' staging rows of v_j
+    size_t stage_cap = 0;
     TileRef* d_tiles = nullptr;
     size_t tile_cap = 0;
     unsigned epoch = 1, uploaded_epoch = 0, ran_epoch = 0;
@@ -204,7 +206,8 @@ struct BatchEngine {
     // rows and the CSR tiles of slot groups sharing one matrix (each row's
     // nonzeros read once for up to kCsrGroup slots)
     static constexpr int kGroups = 3;
-    static constexpr int kTables = 8;        // op, tc16, tc32, piv, upd, norm, pivot-row products, CSR groups
+    static constexpr int kTables = 9;        // op, tc16, tc32, piv, upd, norm, pivot-row products, CSR groups,
+                                             // CSR staging
     struct Group {
         int storage = 0;
         int count[kTables] = {0};
@@ -217,7 +220,8 @@ struct BatchEngine {
         std::vector<SlotDesc> hs(kMaxSlots);
         memset(hs.data(), 0, hs.size() * sizeof(SlotDesc));
         std::vector<TileRef> tab[kGroups][kTables];
-        std::vector<int> hg((size_t)kMaxSlots * (kCsrGroup + 1), 0);
+        std::vector<int> hg((size_t)kMaxSlots * kCsrGroupRec, 0);
+        size_t stage_bytes = 0;
         int ngroups = 0;
         std::vector<int> csr[kGroups];
         for (int g = 0; g < kGroups; ++g) grp[g] = Group();
@@ -253,7 +257,7 @@ struct BatchEngine {
             for (size_t a = 0; a < c.size(); ++a) {
                 if (done[a]) continue;
                 const OpDev& oa = slots[c[a]].d.op;
-                int* gr = hg.data() + (size_t)ngroups * (kCsrGroup + 1);
+                int* gr = hg.data() + (size_t)ngroups * kCsrGroupRec;
                 gr[0] = 0;
                 for (size_t b = a; b < c.size() && gr[0] < kCsrGroup; ++b) {
                     const OpDev& ob = slots[c[b]].d.op;
@@ -264,6 +268,12 @@ struct BatchEngine {
                     gr[1 + gr[0]++] = c[b];
                 }
                 for (int q = 0, nq = cdiv(oa.rows, kBatchCsrRows); q < nq; ++q) tab[g][7].push_back({ngroups, q});
+                for (int q = 0, nq = cdiv(oa.cols, 1024); q < nq; ++q) tab[g][8].push_back({ngroups, q});
+                // staging rows: cols x kCsrGroup values, 256-byte aligned
+                const size_t es = grp[g].storage == IPF_STORE_F32 ? 4 : 2;
+                gr[kCsrGroup + 1] = (int)(unsigned)(stage_bytes & 0xFFFFFFFFu);
+                gr[kCsrGroup + 2] = (int)(unsigned)(stage_bytes >> 32);
+                stage_bytes += ((size_t)oa.cols * kCsrGroup * es + 255) / 256 * 256;
                 ++ngroups;
             }
         }
@@ -287,7 +297,16 @@ struct BatchEngine {
             tile_cap = cap;
         }
         if ((e = stage_copy(d_slots, hs.data(), hs.size() * sizeof(SlotDesc))) != cudaSuccess) return e;
-        if (ngroups && (e = stage_copy(d_groups, hg.data(), (size_t)ngroups * (kCsrGroup + 1) * sizeof(int))) !=
+        if (stage_bytes > stage_cap) {
+            // the old staging rows may still be read by launches in flight
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+            if (d_stage) cudaFree(d_stage);
+            d_stage = nullptr;
+            stage_cap = 0;
+            if ((e = cudaMalloc(&d_stage, stage_bytes * 2)) != cudaSuccess) return e;
+            stage_cap = stage_bytes * 2;
+        }
+        if (ngroups && (e = stage_copy(d_groups, hg.data(), (size_t)ngroups * kCsrGroupRec * sizeof(int))) !=
                            cudaSuccess)
             return e;
         if (total && (e = stage_copy(d_tiles, all.data(), total * sizeof(TileRef))) != cudaSuccess) return e;
@@ -318,8 +337,8 @@ struct BatchEngine {
             const int st = G.storage;
             TileRef* t = d_tiles;
             if ((e = launch_batch_operator(st, d_slots, t + G.off[0], G.count[0], num_sms, s)) != cudaSuccess) return e;
-            if ((e = launch_batch_csr_group(st, d_slots, d_groups, t + G.off[7], G.count[7], num_sms, s)) !=
-                cudaSuccess)
+            if ((e = launch_batch_csr_group(st, d_slots, d_groups, d_stage, t + G.off[8], G.count[8], t + G.off[7],
+                                            G.count[7], num_sms, s)) != cudaSuccess)
                 return e;
             if ((e = launch_batch_conv_tc(16, maps.data(), d_slots, t + G.off[1], G.count[1], s)) != cudaSuccess)
                 return e;
@@ -442,7 +461,7 @@ BatchEngine* batch_create() {
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev_t1);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_slots, sizeof(SlotDesc) * kMaxSlots);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_tune, sizeof(SlotDesc) * kMaxSlots);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_groups, sizeof(int) * kMaxSlots * (kCsrGroup + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_groups, sizeof(int) * kMaxSlots * kCsrGroupRec);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_slots, 0, sizeof(SlotDesc) * kMaxSlots, b->s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_tune, 0, sizeof(SlotDesc) * kMaxSlots, b->s);
     if (e != cudaSuccess) {
@@ -466,6 +485,7 @@ void batch_destroy(BatchEngine* b) {
     if (b->d_slots) cudaFree(b->d_slots);
     if (b->d_tune) cudaFree(b->d_tune);
     if (b->d_groups) cudaFree(b->d_groups);
+    if (b->d_stage) cudaFree(b->d_stage);
     if (b->ev_ready) cudaEventDestroy(b->ev_ready);
     if (b->ev_t0) cudaEventDestroy(b->ev_t0);
     if (b->ev_t1) cudaEventDestroy(b->ev_t1);

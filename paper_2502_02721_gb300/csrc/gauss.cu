@@ -282,6 +282,9 @@ __global__ void __launch_bounds__(kGmThreads, 1)
     if (warp == 0) {
         if (lane == 0) {
             const uint32_t bytes = (uint32_t)((R0 + R1 + Ntot) * kRow);
+            // S is read once: evict-first, so it does not push out the basis
+            // tile the other row groups of the slice read from L2 after us
+            const unsigned long long pol_s = l2_evict_first(), pol_v = l2_evict_last();
             int issued = 0;
             for (int kb = 0; kb < nkb; ++kb) {
                 const int s = kb % kGmStages;
@@ -298,21 +301,21 @@ __global__ void __launch_bounds__(kGmThreads, 1)
                     const int Rt = t ? R1 : R0;
                     const int xu = x & 63, zu = x >> 6;
                     if (Rt == 128) {
-                        tma_load_4d(st + t * kGmATile, &smaps.box[0], xu, 0, zu, y0 >> 4, full(s));
+                        tma_load_4d_hint(st + t * kGmATile, &smaps.box[0], xu, 0, zu, y0 >> 4, full(s), pol_s);
                     } else {
                         int done = 0;
 #pragma unroll
                         for (int b = 1; b < 4; ++b) {
                             const int h = 128 >> b;
                             if (Rt & h) {
-                                tma_load_4d(st + t * kGmATile + done * kRow, &smaps.box[b], xu, 0, zu,
-                                            (y0 + done) >> 4, full(s));
+                                tma_load_4d_hint(st + t * kGmATile + done * kRow, &smaps.box[b], xu, 0, zu,
+                                                 (y0 + done) >> 4, full(s), pol_s);
                                 done += h;
                             }
                         }
                     }
                 }
-                tma_load_2d(st + 2 * kGmATile, &vmap, x, 0, full(s));
+                tma_load_2d_hint(st + 2 * kGmATile, &vmap, x, 0, full(s), pol_v);
                 tma_load_2d(st + 2 * kGmATile + Nv * kRow, &bmap, x, 0, full(s));
                 issued = kb + 1;
             }
@@ -466,10 +469,9 @@ size_t part_bytes(int storage, int m, long long n, int K1max, int num_sms) {
 
 }  // namespace
 
-// row stride of S: n rounded up to 64 elements plus 128, so that the m_s rows
-// a contraction stage reads at the same column do not fall on the same DRAM
-// partitions when n is a power of two
-long long gauss_lds(long long n) { return (n + 63) / 64 * 64 + 128; }
+// row stride of the row-major S (FP32 / FP64) and of the b rows: n rounded
+// up to 64 elements
+long long gauss_lds(long long n) { return (n + 63) / 64 * 64; }
 
 size_t gauss_workspace_bytes(int storage, int m, long long n, int k_max, int num_sms) {
     const size_t sb = storage == IPF_STORE_F64 ? 8 : storage == IPF_STORE_F32 ? 4 : 2;

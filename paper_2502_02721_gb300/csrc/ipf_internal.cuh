@@ -297,6 +297,7 @@ constexpr int kBatchUpdTile = kFoldEvery;      // update tile: the split counter
 constexpr int kBatchNormTile = 4096;           // normalise tile (elements)
 constexpr int kBatchCsrRows = 16;              // CSR rows per operator tile
 constexpr int kCsrGroup = 8;                   // slots sharing one CSR matrix per pass over it
+constexpr int kCsrGroupRec = kCsrGroup + 3;    // group record: count, slots, staging byte offset (2 words)
 
 struct SlotDesc {
     Geom g;
@@ -437,9 +438,13 @@ cudaError_t launch_batch_normalize(int storage, const SlotDesc* slots, const Til
 cudaError_t launch_batch_pivot_rows(int storage, const SlotDesc* slots, const TileRef* tiles, int ntiles, int num_sms,
                                     cudaStream_t s);
 // CSR products of groups of slots sharing one matrix (groups: per group
-// kCsrGroup + 1 ints, the count then the slots; tile.slot = the group)
-cudaError_t launch_batch_csr_group(int storage, const SlotDesc* slots, const int* groups, const TileRef* tiles,
-                                   int ntiles, int num_sms, cudaStream_t s);
+// kCsrGroupRec ints, the count, the slots, the byte offset of its staging
+// rows: cols x kCsrGroup values of the storage type; tile.slot = the group):
+// the staging of each group's v_j (stage_tiles: 1024 columns each), then the
+// products (tiles: kBatchCsrRows rows each)
+cudaError_t launch_batch_csr_group(int storage, const SlotDesc* slots, const int* groups, unsigned char* stage,
+                                   const TileRef* stage_tiles, int nstage, const TileRef* tiles, int ntiles,
+                                   int num_sms, cudaStream_t s);
 // PSF (FMA column convolution, kw 7 / 15 / 31) and CSR products
 cudaError_t launch_batch_operator(int storage, const SlotDesc* slots, const TileRef* tiles, int ntiles, int num_sms,
                                   cudaStream_t s);

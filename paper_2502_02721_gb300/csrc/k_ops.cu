@@ -746,58 +746,130 @@ __global__ void __launch_bounds__(256) kb_pivot_rows(const SlotDesc* __restrict_
     }
 }
 
-// CSR products of up to kCsrGroup slots that share one matrix: tile t of a
-// group = its rows 16t .. 16t + 15, one warp per row; a row's nonzeros are
-// loaded once for all slots of the group, and each slot's sum runs over them
-// in the order of csr_rows (lane-strided, then the same shuffle tree), so a
-// slot gets the same bits as alone.  groups[g]: count, then the slots.
+// CSR products of up to kCsrGroup slots that share one matrix.  A group's
+// record (kCsrGroupRec ints): the count, the slots, and the byte offset of
+// its staging rows in the engine's staging buffer (low, high word).  Step 1,
+// kb_csr_stage: v_j of every slot of the group gathered into rows of
+// kCsrGroup values, row c = (v_{q}(c), q < kCsrGroup) (zero where a slot is
+// absent or idle), so that step 2 reads one 16-byte row (32 for FP32) per
+// nonzero for all slots instead of one scattered value per slot.
+struct CsrGroupView {
+    int count;
+    const int* slot;
+    size_t off;
+};
+__device__ __forceinline__ CsrGroupView csr_group(const int* groups, int g) {
+    const int* rec = groups + (size_t)g * kCsrGroupRec;
+    CsrGroupView v;
+    v.count = rec[0];
+    v.slot = rec + 1;
+    v.off = (size_t)(unsigned)rec[kCsrGroup + 1] | ((size_t)(unsigned)rec[kCsrGroup + 2] << 32);
+    return v;
+}
+
+// the step of each slot of a group, -1 where the slot does not step
+__device__ __forceinline__ void csr_group_steps(const SlotDesc* slots, const CsrGroupView& gv, int* s_j) {
+    if (threadIdx.x < kCsrGroup) {
+        int j = -1;
+        if ((int)threadIdx.x < gv.count) {
+            const SlotDesc* sd = slots + gv.slot[threadIdx.x];
+            if (sd->k_target > 0) {
+                const DevState* st = sd->bf.st;
+                j = st->j;
+                if (st->status[0] != IPF_OK || j >= sd->k_target || j >= sd->g.k_max) j = -1;
+            }
+        }
+        s_j[threadIdx.x] = j;
+    }
+}
+
+// tile t of a group: staging rows 1024 t .. 1024 t + 1023
+template <class T>
+__global__ void __launch_bounds__(256) kb_csr_stage(const SlotDesc* __restrict__ slots, const int* __restrict__ groups,
+                                                    unsigned char* __restrict__ stage,
+                                                    const TileRef* __restrict__ tiles, int ntiles) {
+    __shared__ int s_j[kCsrGroup];
+    for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
+        const TileRef tr = tiles[tt];
+        const CsrGroupView gv = csr_group(groups, tr.slot);
+        __syncthreads();
+        csr_group_steps(slots, gv, s_j);
+        __syncthreads();
+        const long long ncols = slots[gv.slot[0]].op.cols;
+        T* rows = (T*)(stage + gv.off);
+        const long long c0 = (long long)tr.tile * 1024;
+        const long long c1 = min(ncols, c0 + 1024);
+        for (long long c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+            T vals[kCsrGroup];
+#pragma unroll
+            for (int q = 0; q < kCsrGroup; ++q) {
+                vals[q] = from_acc<T>(0.f);
+                if (q < gv.count && s_j[q] >= 0) {
+                    const SlotDesc* sd = slots + gv.slot[q];
+                    vals[q] = ((const T*)sd->bf.V)[(size_t)s_j[q] * sd->g.ldv + c];
+                }
+            }
+            if constexpr (sizeof(T) == 2) {
+                union { uint4 u; T t[8]; } pk;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) pk.t[q] = vals[q];
+                reinterpret_cast<uint4*>(rows)[c] = pk.u;
+            } else {
+                float4* dst = reinterpret_cast<float4*>(rows) + 2 * c;
+                dst[0] = make_float4(to_acc(vals[0]), to_acc(vals[1]), to_acc(vals[2]), to_acc(vals[3]));
+                dst[1] = make_float4(to_acc(vals[4]), to_acc(vals[5]), to_acc(vals[6]), to_acc(vals[7]));
+            }
+        }
+    }
+}
+
+// tile t of a group = its rows 16t .. 16t + 15, one warp per row; a row's
+// nonzeros are loaded once for all slots of the group, each with one
+// staging row, and each slot's sum runs over them in the order of csr_rows
+// (lane-strided, then the same shuffle tree), so a slot gets the same bits
+// as alone
 template <class T>
 __global__ void __launch_bounds__(128) kb_csr_group(const SlotDesc* __restrict__ slots,
                                                     const int* __restrict__ groups,
+                                                    const unsigned char* __restrict__ stage,
                                                     const TileRef* __restrict__ tiles, int ntiles) {
     __shared__ int s_j[kCsrGroup];
-    __shared__ int s_n;
     for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
         const TileRef tr = tiles[tt];
-        const int* grp = groups + (size_t)tr.slot * (kCsrGroup + 1);
+        const CsrGroupView gv = csr_group(groups, tr.slot);
         __syncthreads();
-        if (threadIdx.x == 0) {
-            s_n = grp[0];
-            for (int q = 0; q < s_n; ++q) {
-                const SlotDesc* sd = slots + grp[1 + q];
-                int j = -1;
-                if (sd->k_target > 0) {
-                    const DevState* st = sd->bf.st;
-                    j = st->j;
-                    if (st->status[0] != IPF_OK || j >= sd->k_target || j >= sd->g.k_max) j = -1;
-                }
-                s_j[q] = j;
-            }
-        }
+        csr_group_steps(slots, gv, s_j);
         __syncthreads();
-        const int ng = s_n;
-        const OpDev& op = slots[grp[1]].op;
+        const int ng = gv.count;
+        const OpDev& op = slots[gv.slot[0]].op;
+        const T* rows = (const T*)(stage + gv.off);
         const long long r0 = (long long)tr.tile * kBatchCsrRows;
         const long long r1 = min((long long)op.rows, r0 + kBatchCsrRows);
         const int lane = threadIdx.x & 31;
         for (long long row = r0 + threadIdx.x / 32; row < r1; row += blockDim.x / 32) {
             const long long b0 = op.rowptr[row], b1 = op.rowptr[row + 1];
             float P[kCsrGroup];
-            const T* v[kCsrGroup];
 #pragma unroll
-            for (int q = 0; q < kCsrGroup; ++q) {
-                P[q] = 0.f;
-                const SlotDesc* sd = slots + grp[1 + (q < ng ? q : 0)];
-                v[q] = (q < ng && s_j[q] >= 0) ? (const T*)sd->bf.V + (size_t)s_j[q] * sd->g.ldv : nullptr;
-            }
+            for (int q = 0; q < kCsrGroup; ++q) P[q] = 0.f;
             for (long long base = b0; base < b1; base += 32) {
                 const long long pq = base + lane;
                 if (pq < b1) {
                     const float a = op.vals[pq];
                     const int c = op.colind[pq];
+                    T v[kCsrGroup];
+                    if constexpr (sizeof(T) == 2) {
+                        union { uint4 u; T t[8]; } pk;
+                        pk.u = reinterpret_cast<const uint4*>(rows)[c];
 #pragma unroll
-                    for (int q = 0; q < kCsrGroup; ++q)
-                        if (v[q]) P[q] = fmaf(a, to_acc(v[q][c]), P[q]);
+                        for (int q = 0; q < 8; ++q) v[q] = pk.t[q];
+                    } else {
+                        const float4 x0 = reinterpret_cast<const float4*>(rows)[2 * (size_t)c];
+                        const float4 x1 = reinterpret_cast<const float4*>(rows)[2 * (size_t)c + 1];
+                        v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
+                        v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
+                    }
+#pragma unroll
+                    for (int q = 0; q < kCsrGroup; ++q) P[q] = fmaf(a, to_acc(v[q]), P[q]);
                 }
             }
 #pragma unroll
@@ -806,7 +878,7 @@ __global__ void __launch_bounds__(128) kb_csr_group(const SlotDesc* __restrict__
                 float acc = P[q];
 #pragma unroll
                 for (int o = 16; o >= 1; o >>= 1) acc = acc + __shfl_xor_sync(0xffffffffu, acc, o);
-                if (lane == 0) ((float*)slots[grp[1 + q]].bf.w)[row] = acc;
+                if (lane == 0) ((float*)slots[gv.slot[q]].bf.w)[row] = acc;
             }
         }
     }
@@ -814,14 +886,25 @@ __global__ void __launch_bounds__(128) kb_csr_group(const SlotDesc* __restrict__
 
 }  // namespace
 
-cudaError_t launch_batch_csr_group(int storage, const SlotDesc* slots, const int* groups, const TileRef* tiles,
-                                   int ntiles, int num_sms, cudaStream_t s) {
+cudaError_t launch_batch_csr_group(int storage, const SlotDesc* slots, const int* groups, unsigned char* stage,
+                                   const TileRef* stage_tiles, int nstage, const TileRef* tiles, int ntiles,
+                                   int num_sms, cudaStream_t s) {
     if (ntiles <= 0) return cudaSuccess;
+    const int sb = nstage < num_sms * 8 ? nstage : num_sms * 8;
     const int blocks = ntiles < num_sms * 8 ? ntiles : num_sms * 8;
     switch (storage) {
-        case IPF_STORE_F32: kb_csr_group<float><<<blocks, 128, 0, s>>>(slots, groups, tiles, ntiles); break;
-        case IPF_STORE_BF16: kb_csr_group<__nv_bfloat16><<<blocks, 128, 0, s>>>(slots, groups, tiles, ntiles); break;
-        case IPF_STORE_F16: kb_csr_group<__half><<<blocks, 128, 0, s>>>(slots, groups, tiles, ntiles); break;
+        case IPF_STORE_F32:
+            kb_csr_stage<float><<<sb, 256, 0, s>>>(slots, groups, stage, stage_tiles, nstage);
+            kb_csr_group<float><<<blocks, 128, 0, s>>>(slots, groups, stage, tiles, ntiles);
+            break;
+        case IPF_STORE_BF16:
+            kb_csr_stage<__nv_bfloat16><<<sb, 256, 0, s>>>(slots, groups, stage, stage_tiles, nstage);
+            kb_csr_group<__nv_bfloat16><<<blocks, 128, 0, s>>>(slots, groups, stage, tiles, ntiles);
+            break;
+        case IPF_STORE_F16:
+            kb_csr_stage<__half><<<sb, 256, 0, s>>>(slots, groups, stage, stage_tiles, nstage);
+            kb_csr_group<__half><<<blocks, 128, 0, s>>>(slots, groups, stage, tiles, ntiles);
+            break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
