@@ -821,15 +821,18 @@ def run_small(storage: str):
     256 x 1024^2 BF16, 0.5 GB), whose solve runs the tensor-core
     contraction [S V_{k+1} | S b]; "gauss800": the Gaussian sketch with the
     shape of the 2048^2 workload's contraction (m_s = 800, k = 200: four row
-    groups of S, 201 basis columns) on the 1024^2 image (S 1.7 GB)."""
+    groups of S, 201 basis columns) on the 1024^2 image (S 1.7 GB);
+    "gauss2k256": the 2048^2 image with k = 200 and m_s = 256 (one row group,
+    S 2.1 GB, V_{k+1} 1.7 GB), the full-size basis in a capture of a few GB."""
     import torch
     from gen import problems as P
     from paper_2502_02721_gb300 import binding as bd, build as bl
     if not os.path.exists(bl.lib_path()):
         bl.build()
     torch.cuda.set_device(0)
-    kk, ms = (200, 800) if storage == "gauss800" else (64, 256)
-    p = P.deblur_moffat(side=1024, k=kk, m_s=ms)
+    kk, ms = (200, 800) if storage == "gauss800" else (200, 256) if storage == "gauss2k256" else (64, 256)
+    side = 2048 if storage == "gauss2k256" else 1024
+    p = P.deblur_moffat(side=side, k=kk, m_s=ms)
     keep = []
     op = bd.operator_from_problem(p, keep)
     gauss = storage.startswith("gauss")
@@ -839,7 +842,7 @@ def run_small(storage: str):
     ctx = bd.Context(op, p.b, cfg, keep)
     ctx.step(kk)
     x, info = ctx.solve(kk, [0.0, 1e-3])
-    print(json.dumps({"small_case": f"deblur1024 moffat31 k={kk} m_s={ms}", "storage": storage, "info": info,
+    print(json.dumps({"small_case": f"deblur{side} moffat31 k={kk} m_s={ms}", "storage": storage, "info": info,
                       "x_norm": float(np.linalg.norm(x[0, 0]))}))
     ctx.close()
 
@@ -863,7 +866,7 @@ def main():
                     help="serve without the batched step (each request on its own streams)")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the CT 32-RHS batch and the 5 s serving run on the default line")
-    ap.add_argument("--small", default=None, choices=["f32", "bf16", "f16", "f64", "gauss", "gauss800"],
+    ap.add_argument("--small", default=None, choices=["f32", "bf16", "f16", "f64", "gauss", "gauss800", "gauss2k256"],
                     help="run one small solve (profiling target) and exit")
     args = ap.parse_args()
     if args.small:

@@ -296,7 +296,7 @@ constexpr int kMaxSlots = 64;
 constexpr int kBatchUpdTile = kFoldEvery;      // update tile: the split counters' exact range
 constexpr int kBatchNormTile = 4096;           // normalise tile (elements)
 constexpr int kBatchCsrRows = 16;              // CSR rows per operator tile
-constexpr int kCsrGroup = 8;                   // slots sharing one CSR matrix per pass over it
+constexpr int kCsrGroup = 16;                  // slots sharing one CSR matrix per pass over it
 constexpr int kCsrGroupRec = kCsrGroup + 3;    // group record: count, slots, staging byte offset (2 words)
 
 struct SlotDesc {

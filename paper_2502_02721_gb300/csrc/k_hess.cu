@@ -272,16 +272,12 @@ __global__ void __launch_bounds__(256, 4) k_update_f(Geom g, Bufs bf, SketchPara
             }
         }
         const T* vb = V + base;
-        // the sketch's table entries are requested first, so that their
-        // latency passes behind the column stream; the sketched column is the
-        // newest one (csk == j), whose loaded words the scatter reuses after
-        // the last column's FMAs
+        // the sketch's table entries are prefetched into L2 first, so that
+        // their DRAM latency passes behind the column stream (no registers
+        // held across it); the sketched column is the newest one (csk == j),
+        // whose loaded words the scatter reuses after the last column's FMAs
         constexpr int NTE = B == 1 ? VEC / 2 : 1;          // the sketch is deferred for one RHS only
-        uint4 te[NTE];
-        if (B == 1 && csk >= 0) {
-#pragma unroll
-            for (int q = 0; q < NTE; ++q) te[q] = *(const uint4*)(tab + base + 2 * q);
-        }
+        if (B == 1 && csk >= 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(tab + base));
         const int nlead = csk >= 0 ? nc - 1 : nc;        // columns before the sketched one
         int c = 0;
         for (; c + 8 <= nlead; c += 8) {
@@ -303,6 +299,9 @@ __global__ void __launch_bounds__(256, 4) k_update_f(Geom g, Bufs bf, SketchPara
             for (int q = 0; q < VEC; ++q)
                 acc[q] = fmaf(-s_coef[c * B + ((base + q) & (B - 1))], to_acc(vv[q]), acc[q]);
             if (B == 1 && csk >= 0 && c == csk) {
+                uint4 te[NTE];
+#pragma unroll
+                for (int q = 0; q < NTE; ++q) te[q] = *(const uint4*)(tab + base + 2 * q);
 #pragma unroll
                 for (int q = 0; q < 2 * NTE; q += 2) {
                     if (base + q < N) {
@@ -1181,13 +1180,10 @@ __global__ void __launch_bounds__(256, 4) kb_update(const SlotDesc* __restrict__
                 }
             }
             const T* vb = V + base;
-            // table entries first, the scatter after the sketched (newest)
-            // column's FMAs from its loaded words, as in k_update_f
-            uint4 te[VEC / 2];
-            if (csk >= 0) {
-#pragma unroll
-                for (int q = 0; q < VEC / 2; ++q) te[q] = *(const uint4*)(tab + base + 2 * q);
-            }
+            // table entries prefetched into L2 first, the scatter after the
+            // sketched (newest) column's FMAs from its loaded words, as in
+            // k_update_f
+            if (csk >= 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(tab + base));
             const int nlead = csk >= 0 ? nc - 1 : nc;
             int c = 0;
             for (; c + 8 <= nlead; c += 8) {
@@ -1207,6 +1203,9 @@ __global__ void __launch_bounds__(256, 4) kb_update(const SlotDesc* __restrict__
 #pragma unroll
                 for (int q = 0; q < VEC; ++q) acc[q] = fmaf(-s_coef[c], to_acc(vv[q]), acc[q]);
                 if (csk >= 0 && c == csk) {
+                    uint4 te[VEC / 2];
+#pragma unroll
+                    for (int q = 0; q < VEC / 2; ++q) te[q] = *(const uint4*)(tab + base + 2 * q);
 #pragma unroll
                     for (int q = 0; q < VEC; q += 2) {
                         if (base + q < N) {

@@ -751,8 +751,9 @@ __global__ void __launch_bounds__(256) kb_pivot_rows(const SlotDesc* __restrict_
 // its staging rows in the engine's staging buffer (low, high word).  Step 1,
 // kb_csr_stage: v_j of every slot of the group gathered into rows of
 // kCsrGroup values, row c = (v_{q}(c), q < kCsrGroup) (zero where a slot is
-// absent or idle), so that step 2 reads one 16-byte row (32 for FP32) per
-// nonzero for all slots instead of one scattered value per slot.
+// absent or idle), so that step 2 reads one row of 2 kCsrGroup bytes (4
+// kCsrGroup for FP32) per nonzero for all slots instead of one scattered
+// value per slot.
 struct CsrGroupView {
     int count;
     const int* slot;
@@ -809,15 +810,15 @@ __global__ void __launch_bounds__(256) kb_csr_stage(const SlotDesc* __restrict__
                     vals[q] = ((const T*)sd->bf.V)[(size_t)s_j[q] * sd->g.ldv + c];
                 }
             }
-            if constexpr (sizeof(T) == 2) {
-                union { uint4 u; T t[8]; } pk;
+            // the row: kCsrGroup values, 16 bytes at a time
+            constexpr int PER = 16 / sizeof(T);
+            uint4* dst = reinterpret_cast<uint4*>(rows + (size_t)c * kCsrGroup);
 #pragma unroll
-                for (int q = 0; q < 8; ++q) pk.t[q] = vals[q];
-                reinterpret_cast<uint4*>(rows)[c] = pk.u;
-            } else {
-                float4* dst = reinterpret_cast<float4*>(rows) + 2 * c;
-                dst[0] = make_float4(to_acc(vals[0]), to_acc(vals[1]), to_acc(vals[2]), to_acc(vals[3]));
-                dst[1] = make_float4(to_acc(vals[4]), to_acc(vals[5]), to_acc(vals[6]), to_acc(vals[7]));
+            for (int h = 0; h < kCsrGroup / PER; ++h) {
+                union { uint4 u; T t[PER]; } pk;
+#pragma unroll
+                for (int q = 0; q < PER; ++q) pk.t[q] = vals[h * PER + q];
+                dst[h] = pk.u;
             }
         }
     }
@@ -856,20 +857,15 @@ __global__ void __launch_bounds__(128) kb_csr_group(const SlotDesc* __restrict__
                 if (pq < b1) {
                     const float a = op.vals[pq];
                     const int c = op.colind[pq];
-                    T v[kCsrGroup];
-                    if constexpr (sizeof(T) == 2) {
-                        union { uint4 u; T t[8]; } pk;
-                        pk.u = reinterpret_cast<const uint4*>(rows)[c];
+                    constexpr int PER = 16 / sizeof(T);
+                    const uint4* src = reinterpret_cast<const uint4*>(rows + (size_t)c * kCsrGroup);
 #pragma unroll
-                        for (int q = 0; q < 8; ++q) v[q] = pk.t[q];
-                    } else {
-                        const float4 x0 = reinterpret_cast<const float4*>(rows)[2 * (size_t)c];
-                        const float4 x1 = reinterpret_cast<const float4*>(rows)[2 * (size_t)c + 1];
-                        v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
-                        v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
+                    for (int h = 0; h < kCsrGroup / PER; ++h) {
+                        union { uint4 u; T t[PER]; } pk;
+                        pk.u = src[h];
+#pragma unroll
+                        for (int q = 0; q < PER; ++q) P[h * PER + q] = fmaf(a, to_acc(pk.t[q]), P[h * PER + q]);
                     }
-#pragma unroll
-                    for (int q = 0; q < kCsrGroup; ++q) P[q] = fmaf(a, to_acc(v[q]), P[q]);
                 }
             }
 #pragma unroll

@@ -139,7 +139,7 @@ def test_batched_fma_and_csr_equal_the_context():
 
 def test_batched_csr_requests_sharing_a_matrix():
     """CSR requests on one operator (one set of device arrays) share each
-    pass over its nonzeros in the batched step (groups of up to eight);
+    pass over its nonzeros in the batched step (groups of up to sixteen);
     each request's sums keep the one-request order, so every x equals the
     context's x bit for bit, whatever the group it ran in."""
     import torch
@@ -152,12 +152,12 @@ def test_batched_csr_requests_sharing_a_matrix():
     op = bd.make_operator("csr", n, n, rowptr=keep[0], colind=keep[1], vals=keep[2], keep=keep)
     rng = np.random.default_rng(5)
     reqs = []
-    for t in range(11):                       # one full group of eight and one of three
+    for t in range(20):                       # one full group of sixteen and one of four
         k = int(rng.integers(6, 20))
         b = (ct.b * (1.0 + 0.1 * rng.standard_normal(ct.b.shape))).astype(np.float32)
         reqs.append(dict(b=b, k=k, m_s=4 * k, lam=float(10 ** rng.uniform(-4, -2)),
                          storage=["bf16", "f32"][t % 3 == 2], seed=4000 + t))
-    srv = bd.Server(hbm_budget_bytes=2 << 30, max_inflight=16, steps_per_slice=4)
+    srv = bd.Server(hbm_budget_bytes=2 << 30, max_inflight=20, steps_per_slice=4)
     tickets = [srv.submit(op, r["b"], bd.default_config(k_max=r["k"], m_s=r["m_s"], zeta=8, seed=r["seed"],
                                                         storage=r["storage"]), r["k"], r["lam"]) for r in reqs]
     results = {}
