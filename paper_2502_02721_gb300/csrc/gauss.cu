@@ -19,6 +19,7 @@
 // slices in FP64 in a fixed order (so the result does not depend on
 // scheduling).  FP32 / FP64 storage use a CUDA-core kernel of the same
 // structure (k_gauss_simt; FP32 / FP64 accumulation).
+#include <atomic>
 #include <cstdio>
 #include <type_traits>
 
@@ -221,16 +222,22 @@ template <int BK> __device__ __forceinline__ unsigned long long gm_desc(uint32_t
 template <> __device__ __forceinline__ unsigned long long gm_desc<64>(uint32_t addr) { return smem_desc_sw128(addr); }
 template <> __device__ __forceinline__ unsigned long long gm_desc<32>(uint32_t addr) { return smem_desc_sw64(addr); }
 
-// S through four maps of box heights 128, 64, 32 and 16 rows
-struct GmSMaps {
-    CUtensorMap box[4];
+// The tensor maps: S through four box heights (128, 64, 32, 16 rows); V
+// through one box of all Nv rows (one CTA per row group), or, when the row
+// groups of a slice form a cluster, five box heights (128 .. 8 rows) from
+// which each CTA composes its share of V's rows, multicast to the cluster;
+// b (8 rows)
+struct GmMaps {
+    CUtensorMap s[4];
+    CUtensorMap v[5];
+    CUtensorMap vall;
+    CUtensorMap b;
 };
 
 template <bool BF16, int BK>
 __global__ void __launch_bounds__(kGmThreads, 1)
-    k_gauss_mma(const __grid_constant__ GmSMaps smaps, const __grid_constant__ CUtensorMap vmap,
-                const __grid_constant__ CUtensorMap bmap, long long n, int m, long long chunk, int mg, int rg,
-                int Nv, int Ntot, float* __restrict__ part, int m_pad, int* __restrict__ err) {
+    k_gauss_mma(const __grid_constant__ GmMaps maps, long long n, int m, long long chunk, int mg, int rg, int Nv,
+                int Ntot, int clustered, float* __restrict__ part, int m_pad, int* __restrict__ err) {
     using G = GmShape<BK>;
     constexpr int kGmBK = BK;
     constexpr int kGmStages = G::kStages;
@@ -250,7 +257,11 @@ __global__ void __launch_bounds__(kGmThreads, 1)
     volatile int* s_abort = (volatile int*)(sm + kGmOffMisc + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int slice = blockIdx.x / mg, q = blockIdx.x % mg;
+    const int slice = blockIdx.x / mg, q = blockIdx.x % mg;     // q = the cluster rank when clustered
+    // clustered: this CTA loads V's 8-row units [u0, u1) for every CTA of the
+    // cluster, and a stage slot is free again once all mg CTAs have consumed it
+    const uint16_t cmask = (uint16_t)((1u << mg) - 1u);
+    const int vu0 = q * (Nv / 8) / mg, vu1 = (q + 1) * (Nv / 8) / mg;
     const int row0 = q * rg;
     const int rows_q = min(rg, m - row0);                      // >= 1: q < mg, (mg - 1) rg < m
     const int ntile = (rows_q + 127) / 128;                    // 1 or 2
@@ -262,7 +273,7 @@ __global__ void __launch_bounds__(kGmThreads, 1)
     const int nkb = (int)((i1 - i0 + kGmBK - 1) / kGmBK);      // >= 1: slices = ceil(n / chunk)
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kGmStages; ++i) { mbar_init(full(i), 1); mbar_init(empty(i), 1); }
+        for (int i = 0; i < kGmStages; ++i) { mbar_init(full(i), 1); mbar_init(empty(i), clustered ? mg : 1); }
         mbar_init(done, 1);
         *s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -275,7 +286,11 @@ __global__ void __launch_bounds__(kGmThreads, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
-    __syncthreads();
+    __syncwarp();
+    // clustered: every CTA's barriers exist before any copy or commit of
+    // another CTA of the cluster can reach them
+    if (clustered) cluster_sync();
+    else __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *s_tmem;
 
@@ -301,27 +316,54 @@ __global__ void __launch_bounds__(kGmThreads, 1)
                     const int Rt = t ? R1 : R0;
                     const int xu = x & 63, zu = x >> 6;
                     if (Rt == 128) {
-                        tma_load_4d_hint(st + t * kGmATile, &smaps.box[0], xu, 0, zu, y0 >> 4, full(s), pol_s);
+                        tma_load_4d_hint(st + t * kGmATile, &maps.s[0], xu, 0, zu, y0 >> 4, full(s), pol_s);
                     } else {
-                        int done = 0;
+                        int dn = 0;
 #pragma unroll
                         for (int b = 1; b < 4; ++b) {
                             const int h = 128 >> b;
                             if (Rt & h) {
-                                tma_load_4d_hint(st + t * kGmATile + done * kRow, &smaps.box[b], xu, 0, zu,
-                                                 (y0 + done) >> 4, full(s), pol_s);
-                                done += h;
+                                tma_load_4d_hint(st + t * kGmATile + dn * kRow, &maps.s[b], xu, 0, zu,
+                                                 (y0 + dn) >> 4, full(s), pol_s);
+                                dn += h;
                             }
                         }
                     }
                 }
-                tma_load_2d_hint(st + 2 * kGmATile, &vmap, x, 0, full(s), pol_v);
-                tma_load_2d(st + 2 * kGmATile + Nv * kRow, &bmap, x, 0, full(s));
+                const uint32_t vst = st + 2 * kGmATile;
+                if (clustered) {
+                    // this CTA's rows of V (a multiple of 8, as boxes of 128 .. 8
+                    // rows at multiples of 8 rows: 1024-byte aligned), to every
+                    // CTA of the cluster; the full barrier of each receives them
+                    // (at most 128 rows: the launcher clusters only Nv <= 128 mg)
+                    int r = 8 * vu0;
+                    const int R = 8 * (vu1 - vu0);
+                    if (R == 128) {
+                        tma_load_2d_mc(vst + r * kRow, &maps.v[0], x, r, full(s), cmask, pol_v);
+                    } else {
+#pragma unroll
+                        for (int b = 1; b < 5; ++b) {
+                            const int h = 128 >> b;
+                            if (R & h) {
+                                tma_load_2d_mc(vst + r * kRow, &maps.v[b], x, r, full(s), cmask, pol_v);
+                                r += h;
+                            }
+                        }
+                    }
+                } else {
+                    tma_load_2d_hint(vst, &maps.vall, x, 0, full(s), pol_v);
+                }
+                tma_load_2d(vst + Nv * kRow, &maps.b, x, 0, full(s));
                 issued = kb + 1;
             }
             // every issued copy lands before the CTA may exit
             for (int kb = issued > kGmStages ? issued - kGmStages : 0; kb < issued; ++kb)
                 mbar_wait(full(kb % kGmStages), (kb / kGmStages) & 1, s_abort, err, false);
+            // clustered: the other CTAs' last arrivals on this CTA's empty
+            // barriers (their MMAs on the last stages) have come in
+            if (clustered)
+                for (int kb = nkb > kGmStages ? nkb - kGmStages : 0; kb < nkb; ++kb)
+                    mbar_wait(empty(kb % kGmStages), (kb / kGmStages) & 1, s_abort, err, false);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -337,7 +379,8 @@ __global__ void __launch_bounds__(kGmThreads, 1)
                         mma_bf16(tmem + (uint32_t)(t * Ntot), gm_desc<BK>(st + t * kGmATile + kk * 32),
                                  gm_desc<BK>(st + 2 * kGmATile + kk * 32), idesc, (kb > 0 || kk > 0) ? 1u : 0u);
                 }
-                mma_commit(empty(s));
+                if (clustered) mma_commit_mc(empty(s), cmask);
+                else mma_commit(empty(s));
             }
             // arrives once every MMA issued above has completed
             mma_commit(done);
@@ -368,7 +411,11 @@ __global__ void __launch_bounds__(kGmThreads, 1)
     }
 
     tc_fence_before();
-    __syncthreads();
+    __syncwarp();
+    // clustered: no CTA leaves while another may still write its shared
+    // memory or signal its barriers
+    if (clustered) cluster_sync();
+    else __syncthreads();
     if (warp == 1) {
         __syncwarp();
         tc_fence_after();
@@ -467,6 +514,42 @@ size_t part_bytes(int storage, int m, long long n, int K1max, int num_sms) {
     return (size_t)nsplit * m_pad * (K1max + 1) * sizeof(double);
 }
 
+// clusters of mg CTAs of the contraction (either pipeline, whichever allows
+// fewer) that fit on the GPU at once; 0 where the query fails.  Both
+// pipelines use the same slicing, so their results stay bit-identical.
+int gauss_max_clusters(bool bf16, int mg) {
+    static std::atomic<int> cache[2][9];              // 0: not asked yet; else the answer + 1
+    const int have = cache[bf16 ? 1 : 0][mg].load();
+    if (have > 0) return have - 1;
+    auto q = [&](auto kern, int smem) -> int {
+        if (raise_smem(kern, smem) != cudaSuccess) return 0;
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3((unsigned)(mg * 64));
+        lc.blockDim = dim3(kGmThreads);
+        lc.dynamicSmemBytes = (size_t)smem;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)mg;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        lc.attrs = at;
+        lc.numAttrs = 1;
+        int c = 0;
+        if (cudaOccupancyMaxActiveClusters(&c, kern, &lc) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return c;
+    };
+    const int a = bf16 ? q(k_gauss_mma<true, 64>, GmShape<64>::kSmemRequest)
+                       : q(k_gauss_mma<false, 64>, GmShape<64>::kSmemRequest);
+    const int b = bf16 ? q(k_gauss_mma<true, 32>, GmShape<32>::kSmemRequest)
+                       : q(k_gauss_mma<false, 32>, GmShape<32>::kSmemRequest);
+    const int r = a < b ? a : b;
+    cache[bf16 ? 1 : 0][mg].store(r + 1);
+    return r;
+}
+
 }  // namespace
 
 // row stride of the row-major S (FP32 / FP64) and of the b rows: n rounded
@@ -556,14 +639,19 @@ cudaError_t launch_gauss_sv(int storage, const void* S, int m, long long n, cons
         const int BK = variant == 32 ? 32 : 64;
         const int mg = m_pad / 256;
         const int rg = gauss_group_rows(m);
+        // the row groups of a slice as one cluster sharing V's tiles, when
+        // they are 2..8 and each CTA's share of V is at most 128 rows; the
+        // slices are then as many as clusters fit on the GPU at once
+        const bool bf = storage == IPF_STORE_BF16;
+        const int clusters = (mg >= 2 && mg <= 8 && Nv <= 128 * mg) ? gauss_max_clusters(bf, mg) : 0;
+        const bool clustered = clusters > 0;
         long long chunk;
         int nsplit;
-        split_plan(n, mg, num_sms, &chunk, &nsplit);
+        split_plan(n, mg, clustered ? clusters * mg : num_sms, &chunk, &nsplit);
         const CUtensorMapDataType dt =
             storage == IPF_STORE_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
         const cuuint32_t estr[2] = {1, 1};
-        GmSMaps smaps;
-        CUtensorMap vmap, bmap;
+        GmMaps maps;
         auto make = [&](CUtensorMap* map, const void* base, cuuint64_t rows, cuuint64_t ld, cuuint32_t box_rows) {
             const cuuint64_t dims[2] = {(cuuint64_t)n, rows};
             const cuuint64_t strides[1] = {ld * 2};
@@ -579,22 +667,35 @@ cudaError_t launch_gauss_sv(int storage, const void* S, int m, long long n, cons
             const cuuint64_t strides[3] = {128, 2048, nkb * 2048};
             const cuuint32_t box[4] = {(cuuint32_t)BK, 16, 1, (cuuint32_t)(8 >> b)};
             const cuuint32_t e4[4] = {1, 1, 1, 1};
-            if (enc(&smaps.box[b], dt, 4, const_cast<void*>(S), dims, strides, box, e4, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            if (enc(&maps.s[b], dt, 4, const_cast<void*>(S), dims, strides, box, e4, CU_TENSOR_MAP_INTERLEAVE_NONE,
                     BK == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
                 return cudaErrorInvalidValue;
         }
-        if (make(&vmap, V, (cuuint64_t)kcols, (cuuint64_t)ldv, (cuuint32_t)Nv) != CUDA_SUCCESS ||
-            make(&bmap, bpart, (cuuint64_t)kGmBRows, (cuuint64_t)lds, kGmBRows) != CUDA_SUCCESS)
+        if (make(&maps.vall, V, (cuuint64_t)kcols, (cuuint64_t)ldv, (cuuint32_t)Nv) != CUDA_SUCCESS ||
+            make(&maps.b, bpart, (cuuint64_t)kGmBRows, (cuuint64_t)lds, kGmBRows) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
+        for (int b = 0; clustered && b < 5; ++b)
+            if (make(&maps.v[b], V, (cuuint64_t)kcols, (cuuint64_t)ldv, (cuuint32_t)(128 >> b)) != CUDA_SUCCESS)
+                return cudaErrorInvalidValue;
         auto go = [&](auto kern, int smem) -> cudaError_t {
             cudaError_t e = raise_smem(kern, smem);
             if (e != cudaSuccess) return e;
-            kern<<<nsplit * mg, kGmThreads, smem, s>>>(smaps, vmap, bmap, n, m, chunk, mg, rg, Nv, Ntot,
-                                                      (float*)part, m_pad, err);
-            return cudaGetLastError();
+            cudaLaunchConfig_t lc = {};
+            lc.gridDim = dim3((unsigned)(nsplit * mg));
+            lc.blockDim = dim3(kGmThreads);
+            lc.dynamicSmemBytes = (size_t)smem;
+            lc.stream = s;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = clustered ? (unsigned)mg : 1u;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            lc.attrs = at;
+            lc.numAttrs = clustered ? 1 : 0;
+            return cudaLaunchKernelEx(&lc, kern, maps, n, m, chunk, mg, rg, Nv, Ntot, clustered ? 1 : 0,
+                                      (float*)part, m_pad, err);
         };
-        const bool bf = storage == IPF_STORE_BF16;
         cudaError_t e;
         if (BK == 64) e = bf ? go(k_gauss_mma<true, 64>, GmShape<64>::kSmemRequest)
                              : go(k_gauss_mma<false, 64>, GmShape<64>::kSmemRequest);

@@ -272,15 +272,24 @@ __global__ void __launch_bounds__(256, 4) k_update_f(Geom g, Bufs bf, SketchPara
             }
         }
         const T* vb = V + base;
-        // the sketch's table entries are prefetched into L2 first, so that
-        // their DRAM latency passes behind the column stream (no registers
-        // held across it); the sketched column is the newest one (csk == j),
-        // whose loaded words the scatter reuses after the last column's FMAs
-        constexpr int NTE = B == 1 ? VEC / 2 : 1;          // the sketch is deferred for one RHS only
-        if (B == 1 && csk >= 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(tab + base));
-        const int nlead = csk >= 0 ? nc - 1 : nc;        // columns before the sketched one
+        if (csk >= 0) {
+            const uint4 rv = *(const uint4*)(vb + (size_t)csk * ldv);
+            const T* vv = (const T*)&rv;
+#pragma unroll
+            for (int q = 0; q < VEC; q += 2) {
+                const uint4 te = *(const uint4*)(tab + base + q);
+                if (base + q < N) {
+                    const long long qv = fixed_from(to_acc(vv[q]), Ssk);
+                    if (qv) scatter8(s_hi, s_lo, sp, qv, make_uint2(te.x, te.y));
+                }
+                if (base + q + 1 < N) {
+                    const long long qv = fixed_from(to_acc(vv[q + 1]), Ssk);
+                    if (qv) scatter8(s_hi, s_lo, sp, qv, make_uint2(te.z, te.w));
+                }
+            }
+        }
         int c = 0;
-        for (; c + 8 <= nlead; c += 8) {
+        for (; c + 8 <= nc; c += 8) {
             uint4 raw[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) raw[u] = __ldcs((const uint4*)(vb + (size_t)(c + u) * ldv));
@@ -298,22 +307,6 @@ __global__ void __launch_bounds__(256, 4) k_update_f(Geom g, Bufs bf, SketchPara
 #pragma unroll
             for (int q = 0; q < VEC; ++q)
                 acc[q] = fmaf(-s_coef[c * B + ((base + q) & (B - 1))], to_acc(vv[q]), acc[q]);
-            if (B == 1 && csk >= 0 && c == csk) {
-                uint4 te[NTE];
-#pragma unroll
-                for (int q = 0; q < NTE; ++q) te[q] = *(const uint4*)(tab + base + 2 * q);
-#pragma unroll
-                for (int q = 0; q < 2 * NTE; q += 2) {
-                    if (base + q < N) {
-                        const long long qv = fixed_from(to_acc(vv[q]), Ssk);
-                        if (qv) scatter8(s_hi, s_lo, sp, qv, make_uint2(te[q / 2].x, te[q / 2].y));
-                    }
-                    if (base + q + 1 < N) {
-                        const long long qv = fixed_from(to_acc(vv[q + 1]), Ssk);
-                        if (qv) scatter8(s_hi, s_lo, sp, qv, make_uint2(te[q / 2].z, te[q / 2].w));
-                    }
-                }
-            }
         }
         const unsigned bits = bf.ispiv[base >> 5] >> (base & 31);
 #pragma unroll
@@ -1180,13 +1173,24 @@ __global__ void __launch_bounds__(256, 4) kb_update(const SlotDesc* __restrict__
                 }
             }
             const T* vb = V + base;
-            // table entries prefetched into L2 first, the scatter after the
-            // sketched (newest) column's FMAs from its loaded words, as in
-            // k_update_f
-            if (csk >= 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(tab + base));
-            const int nlead = csk >= 0 ? nc - 1 : nc;
+            if (csk >= 0) {
+                const uint4 rv = *(const uint4*)(vb + (size_t)csk * ldv);
+                const T* vv = (const T*)&rv;
+#pragma unroll
+                for (int q = 0; q < VEC; q += 2) {
+                    const uint4 te = *(const uint4*)(tab + base + q);
+                    if (base + q < N) {
+                        const long long qv = fixed_from(to_acc(vv[q]), Ssk);
+                        if (qv) scatter8(s_hi, s_lo, sp, qv, make_uint2(te.x, te.y));
+                    }
+                    if (base + q + 1 < N) {
+                        const long long qv = fixed_from(to_acc(vv[q + 1]), Ssk);
+                        if (qv) scatter8(s_hi, s_lo, sp, qv, make_uint2(te.z, te.w));
+                    }
+                }
+            }
             int c = 0;
-            for (; c + 8 <= nlead; c += 8) {
+            for (; c + 8 <= nc; c += 8) {
                 uint4 raw[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) raw[u] = __ldcs((const uint4*)(vb + (size_t)(c + u) * ldv));
@@ -1202,22 +1206,6 @@ __global__ void __launch_bounds__(256, 4) kb_update(const SlotDesc* __restrict__
                 const T* vv = (const T*)&r1;
 #pragma unroll
                 for (int q = 0; q < VEC; ++q) acc[q] = fmaf(-s_coef[c], to_acc(vv[q]), acc[q]);
-                if (csk >= 0 && c == csk) {
-                    uint4 te[VEC / 2];
-#pragma unroll
-                    for (int q = 0; q < VEC / 2; ++q) te[q] = *(const uint4*)(tab + base + 2 * q);
-#pragma unroll
-                    for (int q = 0; q < VEC; q += 2) {
-                        if (base + q < N) {
-                            const long long qv = fixed_from(to_acc(vv[q]), Ssk);
-                            if (qv) scatter8(s_hi, s_lo, sp, qv, make_uint2(te[q / 2].x, te[q / 2].y));
-                        }
-                        if (base + q + 1 < N) {
-                            const long long qv = fixed_from(to_acc(vv[q + 1]), Ssk);
-                            if (qv) scatter8(s_hi, s_lo, sp, qv, make_uint2(te[q / 2].z, te[q / 2].w));
-                        }
-                    }
-                }
             }
             const unsigned bits = bf.ispiv[base >> 5] >> (base & 31);
 #pragma unroll

@@ -57,7 +57,8 @@ def test_gaussian_sketch_odd_rows(storage):
 
 def test_gaussian_contraction_rows_and_slices():
     """The contraction against a direct FP64 product on a case with several
-    row groups (m_s = 600: groups of 256, 256 and 88 rows) and many slices:
+    row groups (m_s = 600: groups of 208, 208 and 184 rows, one cluster of
+    three CTAs per slice sharing V's tiles) and many slices:
     ragged image 72 x 88 (n = 6336, not a multiple of 64), BF16 basis; S V
     and c = S b read back through the solve's projected problem are checked
     via x_k against the oracle at every k to 40."""
@@ -74,6 +75,24 @@ def test_gaussian_contraction_rows_and_slices():
     ctx.step(p.k)
     verify_scmrh(ctx, p, "bf16", [1, 3, 10, 25, 40], p.lambdas, sketch=S, sketch64=S64, contraction_terms=p.n,
                  name="gauss_ragged_bf16")
+    ctx.close()
+
+
+def test_gaussian_cluster_with_idle_loaders():
+    """m_s = 1100 and k = 12: five row groups (224 x 4 + 204 rows) per slice
+    form one cluster, but V_{k+1} has only three 8-row units (N_v = 24), so
+    two CTAs of each cluster load no part of V and receive all of it from
+    the others; x_k against the oracle at every k to 12."""
+    p = P.make("deblur64")
+    m_s, k = 1100, 12
+    S = sk.GaussianSketch(p.sketch_seed, p.n, m_s, "bf16")
+    S64 = sk.GaussianSketch(p.sketch_seed, p.n, m_s, "f64")
+    ctx = gpu_context(p, "bf16", k=k, m_s=m_s, sketch="gaussian")
+    ctx.step(k)
+    status, kd = ctx.sync()
+    assert kd == [k]
+    verify_scmrh(ctx, p, "bf16", [1, 4, 12], [0.0, 1e-3], k=k, sketch=S, sketch64=S64, m_s=m_s,
+                 contraction_terms=p.n, name="gauss_cluster_idle_bf16")
     ctx.close()
 
 
@@ -142,12 +161,15 @@ def test_gaussian_sketch_full_size_samples():
     torch.cuda.empty_cache()
 
 
-def test_gaussian_contraction_pipelines_agree(tmp_path, monkeypatch):
+@pytest.mark.parametrize("m_s", [200, 600])
+def test_gaussian_contraction_pipelines_agree(tmp_path, monkeypatch, m_s):
     """The two pipelines of the tensor-core contraction (64-element stages,
     3 in flight; 32-element stages, 7 in flight) issue the same MMAs in the
     same K order, only grouped differently per stage: with each pinned in
-    turn through the autotuner cache, the solves give the same bits."""
+    turn through the autotuner cache, the solves give the same bits (m_s =
+    200: one CTA per slice; 600: clusters of three sharing V's tiles)."""
     p = P.make("deblur64")
+    p.m_s = m_s
     xs = []
     for bk in (64, 32):
         cache = tmp_path / f"tune{bk}.json"

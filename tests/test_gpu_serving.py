@@ -224,3 +224,56 @@ def test_server_rejects_what_can_never_fit():
         srv.submit(op, np.ones(512 * 512, np.float32), cfg, 100)
     assert ei.value.code == bd.IPF_ERR_REJECTED
     srv.close()
+
+
+def test_requests_wait_for_memory_to_free():
+    """An HBM budget that holds two requests at a time: six are submitted at
+    once with eight slots free, so four wait for memory (not for a slot);
+    the server never holds more than two, the budget is never exceeded, and
+    every result equals the same request served alone."""
+    import ctypes as C
+    ensure_lib()
+    from paper_2502_02721_gb300 import binding as bd
+    lib = bd.load()
+    rng = np.random.default_rng(31)
+    side, k = 96, 20
+    keep = []
+    psf = P.gaussian_psf(9, 1.5)
+    reqs = []
+    for t in range(6):
+        x = P.ellipse_phantom(side, side, 6, rng)
+        b = P.add_noise(P.blur_fft(x, psf), 0.01, rng).astype(np.float32)
+        reqs.append(dict(kind="psf2d", rows=side, cols=side, psf=psf, b=b.reshape(1, -1), k=k, m_s=4 * k,
+                         lam=1e-3, storage="bf16", seed=5000 + t))
+    cfg0 = bd.default_config(k_max=k, m_s=4 * k, zeta=8, seed=1, storage="bf16")
+    op0 = _op(bd, reqs[0], keep)
+    need = lib.ipf_footprint(C.byref(op0), C.byref(cfg0)) + 4 * side * side + (64 << 10)
+    budget = int(2.5 * need)
+    srv = bd.Server(hbm_budget_bytes=budget, max_inflight=8, steps_per_slice=2)
+    tickets = []
+    for r in reqs:
+        cfg = bd.default_config(k_max=r["k"], m_s=r["m_s"], zeta=8, seed=r["seed"], storage=r["storage"])
+        tickets.append(srv.submit(_op(bd, r, keep), r["b"], cfg, r["k"], r["lam"]))
+    results, most, queued_seen = {}, 0, 0
+    t0 = time.time()
+    while len(results) < len(tickets) and time.time() - t0 < 120:
+        active, queued, used = srv.stats()
+        most = max(most, active)
+        queued_seen = max(queued_seen, queued)
+        assert used <= budget
+        for t in tickets:
+            if t not in results:
+                out = srv.poll(t)
+                if out is not None:
+                    results[t] = out
+        time.sleep(0.001)
+    srv.close()
+    assert len(results) == len(tickets)
+    assert most <= 2 and queued_seen >= 1
+    spans = sorted((results[t][2][1], results[t][2][2]) for t in tickets)
+    for i, (a0, _) in enumerate(spans):
+        assert sum(1 for b0, b1 in spans if b0 <= a0 < b1) <= 2, i       # never three admitted at once
+    for r, t in zip(reqs, tickets):
+        assert results[t][0] == bd.IPF_OK and results[t][1] == r["k"]
+        (one,), _ = _serve(bd, [r], keep, max_inflight=1)
+        assert np.array_equal(results[t][3], one[3])
