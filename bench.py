@@ -785,6 +785,7 @@ def run_serving(args, duration=None):
         bstats = srv.batch_stats()
         srv.close()
         lat = np.array([r[0][2][2] - r[0][2][0] for r in results.values()])
+        wait = np.array([r[0][2][1] - r[0][2][0] for r in results.values()])      # submit -> admitted
         ok = sum(1 for r in results.values() if r[0][0] in (0, 1))
         t_first = min(r[0][2][0] for r in results.values())
         span = float(max(r[0][2][2] for r in results.values()) - t_first)
@@ -795,6 +796,8 @@ def run_serving(args, duration=None):
                 "latency_ms": {"p50": float(np.percentile(lat, 50) * 1e3),
                                "p99": float(np.percentile(lat, 99) * 1e3), "mean": float(lat.mean() * 1e3)},
                 "latency_ms_by_kind_p50": {k2: float(np.percentile(v, 50) * 1e3) for k2, v in sorted(by.items())},
+                "latency_ms_by_kind_p99": {k2: float(np.percentile(v, 99) * 1e3) for k2, v in sorted(by.items())},
+                "queue_ms": {"p50": float(np.percentile(wait, 50) * 1e3), "p99": float(np.percentile(wait, 99) * 1e3)},
                 "span_s": span,
                 "batched_step": {"requests_batched": bstats[0], "graph_turns": bstats[1], "eager_turns": bstats[2],
                                  "graph_captures": bstats[3]}}

@@ -166,6 +166,8 @@ struct BatchEngine {
     TileRef* d_tiles = nullptr;
     size_t tile_cap = 0;
     unsigned epoch = 1, uploaded_epoch = 0, ran_epoch = 0;
+    int ran_turns = 0;                         // eager turns of the composition ran_epoch
+    static constexpr int kEagerTurnsBeforeCapture = 3;
     Stage stage[4];
     int stage_next = 0;
     cudaGraphExec_t gexec = nullptr;
@@ -547,8 +549,10 @@ cudaError_t batch_run(BatchEngine* b, int steps, cudaEvent_t done) {
         if (reuse) {
             if ((e = cudaGraphLaunch(b->gexec, b->s)) != cudaSuccess) return e;
             ++b->graph_turns;
-        } else if (b->ran_epoch == b->epoch) {
-            // the composition held for a turn: capture it
+        } else if (b->ran_epoch == b->epoch && b->ran_turns >= kEagerTurnsBeforeCapture) {
+            // the composition held for several turns: capture it (under
+            // churn, a capture and instantiation costs more host time than
+            // the eager turns it would replace)
             cudaGraph_t g = nullptr;
             if ((e = cudaStreamBeginCapture(b->s, cudaStreamCaptureModeRelaxed)) != cudaSuccess) return e;
             cudaError_t e1 = cudaSuccess;
@@ -569,6 +573,7 @@ cudaError_t batch_run(BatchEngine* b, int steps, cudaEvent_t done) {
         } else {
             for (int t = 0; t < steps; ++t)
                 if ((e = b->step_launches()) != cudaSuccess) return e;
+            b->ran_turns = b->ran_epoch == b->epoch ? b->ran_turns + 1 : 1;
             b->ran_epoch = b->epoch;
             ++b->eager_turns;
         }
