@@ -549,7 +549,7 @@ cudaError_t batch_run(BatchEngine* b, int steps, cudaEvent_t done) {
         if (reuse) {
             if ((e = cudaGraphLaunch(b->gexec, b->s)) != cudaSuccess) return e;
             ++b->graph_turns;
-        } else if (b->ran_epoch == b->epoch && b->ran_turns >= kEagerTurnsBeforeCapture) {
+        } else if (b->ran_epoch == b->epoch && b->ran_turns >= BatchEngine::kEagerTurnsBeforeCapture) {
             // the composition held for several turns: capture it (under
             // churn, a capture and instantiation costs more host time than
             // the eager turns it would replace)
