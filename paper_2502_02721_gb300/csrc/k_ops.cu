@@ -852,19 +852,38 @@ __global__ void __launch_bounds__(128) kb_csr_group(const SlotDesc* __restrict__
             float P[kCsrGroup];
 #pragma unroll
             for (int q = 0; q < kCsrGroup; ++q) P[q] = 0.f;
-            for (long long base = b0; base < b1; base += 32) {
-                const long long pq = base + lane;
-                if (pq < b1) {
-                    const float a = op.vals[pq];
-                    const int c = op.colind[pq];
-                    constexpr int PER = 16 / sizeof(T);
-                    const uint4* src = reinterpret_cast<const uint4*>(rows + (size_t)c * kCsrGroup);
+            // U chunks of 32 nonzeros per pass: every index, value and staged
+            // row of the pass is requested before the first FMA (the loads of
+            // a chunk depend on its column index), and each lane still adds
+            // its nonzeros b0 + lane, b0 + lane + 32, ... in that order
+            constexpr int PER = 16 / sizeof(T);
+            constexpr int NH = kCsrGroup / PER;
+            constexpr int U = 4;
+            for (long long base = b0; base < b1; base += 32 * U) {
+                float a[U];
+                int c[U];
 #pragma unroll
-                    for (int h = 0; h < kCsrGroup / PER; ++h) {
-                        union { uint4 u; T t[PER]; } pk;
-                        pk.u = src[h];
+                for (int u = 0; u < U; ++u) {
+                    const long long pq = base + 32 * u + lane;
+                    c[u] = pq < b1 ? op.colind[pq] : -1;
+                    a[u] = pq < b1 ? op.vals[pq] : 0.f;
+                }
+                uint4 rv[U][NH];
 #pragma unroll
-                        for (int q = 0; q < PER; ++q) P[h * PER + q] = fmaf(a, to_acc(pk.t[q]), P[h * PER + q]);
+                for (int u = 0; u < U; ++u) {
+                    const uint4* src = reinterpret_cast<const uint4*>(rows + (size_t)(c[u] < 0 ? 0 : c[u]) * kCsrGroup);
+#pragma unroll
+                    for (int h = 0; h < NH; ++h) rv[u][h] = c[u] >= 0 ? src[h] : make_uint4(0, 0, 0, 0);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (c[u] < 0) continue;
+#pragma unroll
+                    for (int h = 0; h < NH; ++h) {
+                        union { uint4 u4; T t[PER]; } pk;
+                        pk.u4 = rv[u][h];
+#pragma unroll
+                        for (int q = 0; q < PER; ++q) P[h * PER + q] = fmaf(a[u], to_acc(pk.t[q]), P[h * PER + q]);
                     }
                 }
             }
