@@ -80,9 +80,13 @@ __global__ void k_form(Geom g, Bufs bf, int k, int zeta, int use_sw, int need_T,
     double* T = Tw ? Tw + (size_t)r * m * k : nullptr;
     const double beta = bf.st->beta[r];
     const long long total = (long long)m * (kb + 1);
+    // the work of column col grows with col (a sum over col + 2 terms):
+    // the first blocks take the last columns, so the heaviest blocks start
+    // first and the light ones fill the SMs behind them
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
-        const int col = (int)(t / m), row = (int)(t - (long long)col * m);
+        const int cr = (int)(t / m), row = (int)(t - (long long)cr * m);
+        const int col = kb - cr;
         double val;
         if (qmr) {
             if (col < kb) val = row <= col + 1 ? H[(size_t)K1 * col + row] : 0.0;
@@ -204,13 +208,25 @@ __device__ __forceinline__ void apply_block(const double* v, double tau, double*
 }
 
 // Householder QR (R only), pipelined by columns instead of a grid barrier
-// per column.  Column j belongs to CTA j mod cpj of its job.  Reflector i is
+// per column.  Columns are dealt to the job's CTAs in blocks of kHhBlock
+// (column j to CTA (j / kHhBlock) mod cpj), so a CTA forms the reflectors of
+// a block one after the other with no hand-off between them: one flag wait
+// on the critical path per block instead of per column.  Reflector i is
 // published by its owner (vector in the column below the diagonal, tau in
 // the diagonal slot, then a flag); a CTA waits only for the flag of the
 // reflector it applies next, and applies reflectors in order.  The owner of
 // column i+1 applies reflector i to that column first and publishes
 // reflector i+1 at once (lookahead), before its other columns; two shared
 // buffers hold v_i and v_{i+1}.  Cooperative launch: all CTAs co-resident.
+constexpr int kHhBlock = 4;
+
+// the first column >= j that CTA q of cpj owns
+__device__ __forceinline__ int hh_next_owned(int j, int q, int cpj) {
+    const int b = j / kHhBlock;
+    const int d = ((q - b % cpj) % cpj + cpj) % cpj;       // blocks to skip to reach one of q's
+    return d == 0 ? j : (b + d) * kHhBlock;
+}
+
 __global__ void __launch_bounds__(256) k_householder(Geom g, const DevState* st, int k, int need_T, int cpj,
                                                       double* Mw, double* Tw, double* dM, double* dT,
                                                       unsigned* flags, int* err) {
@@ -239,7 +255,7 @@ __global__ void __launch_bounds__(256) k_householder(Geom g, const DevState* st,
         double* v = s_buf + (size_t)(i & 1) * m;
         double* ci = A + (size_t)i * m;
         double tau;
-        if (i % cpj == q) {
+        if ((i / kHhBlock) % cpj == q) {
             if (have != i) make_reflector(ci, i, m, v, diag + i, flag + i, s_red, &s_tau[i & 1]);
             tau = s_tau[i & 1];
         } else {
@@ -250,9 +266,8 @@ __global__ void __launch_bounds__(256) k_householder(Geom g, const DevState* st,
             __syncthreads();
             tau = s_tau[i & 1];
         }
-        // owned columns j > i: j = q, q + cpj, ...
-        int j0 = q;
-        if (j0 <= i) j0 += ((i - q) / cpj + 1) * cpj;
+        // owned columns j > i, in blocks of kHhBlock every cpj blocks
+        const int j0 = hh_next_owned(i + 1, q, cpj);
         if (j0 >= ncols) break;                // no column (and no reflector) left here
         int jrest = j0;
         if (j0 == i + 1) {
@@ -264,11 +279,11 @@ __global__ void __launch_bounds__(256) k_householder(Geom g, const DevState* st,
                                &s_tau[(i + 1) & 1]);
                 have = i + 1;
             }
-            jrest = j0 + cpj;
+            jrest = hh_next_owned(j0 + 1, q, cpj);
         }
         if (tau != 0.0) {
             int idx = 0;
-            for (int jc = jrest; jc < ncols; jc += cpj, ++idx) {
+            for (int jc = jrest; jc < ncols; jc = hh_next_owned(jc + 1, q, cpj), ++idx) {
                 if ((idx % nw) != warp) continue;
                 double* cj = A + (size_t)jc * m;
                 double d = 0.0;
@@ -356,24 +371,40 @@ __global__ void __launch_bounds__(256) k_small_solve(Geom g, const DevState* st,
             __syncthreads();
         }
     }
-    // back substitution top(0:kb, 0:kb) y = top(0:kb, kb) by columns: y_i
-    // from the right-hand side column (which already has columns > i
-    // applied), then column i applied to rows < i by all threads
-    // (one thread divides: FP64 division is scarce on this GPU)
-    __shared__ double s_yi;
+    // back substitution top(0:kb, 0:kb) y = top(0:kb, kb) in blocks of 32
+    // rows from the bottom: warp 0 solves a block's diagonal triangle alone
+    // (y_i by a shuffle from the lane holding row i; the reciprocals of the
+    // diagonal are formed in parallel first: FP64 division is scarce on
+    // this GPU), one barrier publishes the block's y, and every thread
+    // applies the block's columns to the rows above it.  Each row still
+    // takes its updates in decreasing column order.
+    __shared__ double s_inv[kSmallMaxK];
     double* rhs = S + (size_t)kb * ld;
-    for (int i = kb - 1; i >= 0; --i) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const double d = S[(size_t)i * ld + i];
-            const double yi = d != 0.0 ? rhs[i] / d : 0.0;
-            y[i] = yi;
-            s_yi = yi;
+    for (int i = threadIdx.x; i < kb; i += blockDim.x) {
+        const double d = S[(size_t)i * ld + i];
+        s_inv[i] = d != 0.0 ? 1.0 / d : 0.0;
+    }
+    __syncthreads();
+    for (int hi = kb; hi > 0; hi -= 32) {
+        const int lo = hi > 32 ? hi - 32 : 0;
+        if (warp == 0) {
+            const int row = lo + lane;                       // this lane's row of the block
+            double b = row < hi ? rhs[row] : 0.0;
+            for (int i = hi - 1; i >= lo; --i) {
+                const double yi = __shfl_sync(0xffffffffu, b * s_inv[i < 0 ? 0 : i], i - lo);
+                if (lane == 0) y[i] = yi;
+                if (row < i) b = fma(-S[(size_t)i * ld + row], yi, b);
+                if (lane == i - lo) b = yi;                  // row i now holds y_i
+            }
+            if (row < hi) rhs[row] = b;                      // y of the block, for the rows above
         }
         __syncthreads();
-        const double yi = s_yi;
-        const double* ci = S + (size_t)i * ld;
-        for (int row = threadIdx.x; row < i; row += blockDim.x) rhs[row] = fma(-ci[row], yi, rhs[row]);
+        for (int row = threadIdx.x; row < lo; row += blockDim.x) {
+            double b = rhs[row];
+            for (int i = hi - 1; i >= lo; --i) b = fma(-S[(size_t)i * ld + row], rhs[i], b);
+            rhs[row] = b;
+        }
+        __syncthreads();
     }
 }
 
@@ -382,7 +413,7 @@ __global__ void __launch_bounds__(256) k_small_solve(Geom g, const DevState* st,
 // Each thread owns 16 bytes of every basis column per pass and keeps eight
 // 128-bit column loads in flight.
 // ------------------------------------------------------------------------
-template <class T, int NL>
+template <class T, int NL, bool ONE>
 __global__ void __launch_bounds__(256) k_reconstruct(Geom g, Bufs bf, const DevState* st, int k, int nl,
                                                       const double* Yw, int l0, int nlc, float* x) {
     using Acc = typename AccOf<T>::type;
@@ -420,7 +451,9 @@ __global__ void __launch_bounds__(256) k_reconstruct(Geom g, Bufs bf, const DevS
                 const T* vv = (const T*)&raw[u];
 #pragma unroll
                 for (int q = 0; q < VEC; ++q) {
-                    const int rr = (int)((base + q) & (B - 1));
+                    // one RHS (ONE): the coefficient is the same for the VEC
+                    // elements, read once per column
+                    const int rr = ONE ? 0 : (int)((base + q) & (B - 1));
                     const Acc vq = to_acc(vv[q]);
 #pragma unroll
                     for (int l = 0; l < NL; ++l) acc[l][q] = fma(s_y[((size_t)l * B + rr) * k + c + u], vq, acc[l][q]);
@@ -432,7 +465,7 @@ __global__ void __launch_bounds__(256) k_reconstruct(Geom g, Bufs bf, const DevS
             const T* vv = (const T*)&r1;
 #pragma unroll
             for (int q = 0; q < VEC; ++q) {
-                const int rr = (int)((base + q) & (B - 1));
+                const int rr = ONE ? 0 : (int)((base + q) & (B - 1));
                 const Acc vq = to_acc(vv[q]);
 #pragma unroll
                 for (int l = 0; l < NL; ++l) acc[l][q] = fma(s_y[((size_t)l * B + rr) * k + c], vq, acc[l][q]);
@@ -487,7 +520,8 @@ cudaError_t launch_solve_prepare(const Geom& g, const Bufs& bf, int zeta, int k,
     if (occ < 1) occ = 1;
     const int maxblocks = occ * num_sms;
     int cpj = maxblocks / njobs;
-    if (cpj > (k + 2) / 2) cpj = (k + 2) / 2;
+    const int nblk = (k + 2 + kHhBlock - 1) / kHhBlock;   // column blocks of the widest matrix
+    if (cpj > nblk) cpj = nblk;
     if (cpj < 1) cpj = 1;
     if (cpj * njobs > maxblocks) return cudaErrorInvalidConfiguration;   // cannot co-reside
     const int nb = cpj * njobs;
@@ -533,11 +567,19 @@ cudaError_t launch_solve_lambdas(int storage, const Geom& g, const Bufs& bf, int
         };
         auto byNL = [&](auto tag, int vec) -> cudaError_t {
             using T = decltype(tag);
+            if (g.B == 1) {
+                switch (NLp) {
+                    case 1: return launch(k_reconstruct<T, 1, true>, vec);
+                    case 2: return launch(k_reconstruct<T, 2, true>, vec);
+                    case 4: return launch(k_reconstruct<T, 4, true>, vec);
+                    default: return launch(k_reconstruct<T, 8, true>, vec);
+                }
+            }
             switch (NLp) {
-                case 1: return launch(k_reconstruct<T, 1>, vec);
-                case 2: return launch(k_reconstruct<T, 2>, vec);
-                case 4: return launch(k_reconstruct<T, 4>, vec);
-                default: return launch(k_reconstruct<T, 8>, vec);
+                case 1: return launch(k_reconstruct<T, 1, false>, vec);
+                case 2: return launch(k_reconstruct<T, 2, false>, vec);
+                case 4: return launch(k_reconstruct<T, 4, false>, vec);
+                default: return launch(k_reconstruct<T, 8, false>, vec);
             }
         };
         switch (storage) {
