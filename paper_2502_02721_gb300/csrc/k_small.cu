@@ -22,7 +22,7 @@ namespace ipf {
 namespace {
 
 struct SolveLayout {
-    size_t bar_off, err_off, M_off, T_off, dM_off, dT_off, Y_off, S_off, total;
+    size_t bar_off, err_off, M_off, T_off, dM_off, dT_off, Y_off, S_off, W_off, total;
 };
 
 // workspace for k <= g.k_max and nl_max lambdas; the barrier counters and
@@ -40,6 +40,7 @@ SolveLayout layout_for(const Geom& g, int nl_max) {
     L.dT_off = take(sizeof(double) * (size_t)g.B * (k + 1));
     L.Y_off = take(sizeof(double) * (size_t)g.B * nl_max * (k + 1));
     L.S_off = take(sizeof(double) * (size_t)g.B * nl_max * (2 * k + 1) * (k + 1));
+    L.W_off = take(sizeof(double) * (size_t)g.B * g.m_s * (k + 2));
     L.total = off;
     return L;
 }
@@ -62,7 +63,27 @@ __device__ __forceinline__ double col_scale(double scale, int e) { return e ? ld
 // Hessenber_LS): column col < kb is H(:, col) (rows 0..col+1, zero below)
 // and column kb is beta e_1, so the same QR and per-lambda solves give
 // y = argmin ||beta e_1 - H y||^2 + lambda^2 ||y||^2.
-__global__ void k_form(Geom g, Bufs bf, int k, int zeta, int use_sw, int need_T, double* Mw, double* Tw, int qmr) {
+// W = S V_{kb+1} in FP64, column i scaled by its exponent: the factors of
+// k_form's sums, formed once per entry instead of once per use
+__global__ void k_scale_sv(Geom g, Bufs bf, int k, int zeta, double* Ww) {
+    const int r = blockIdx.y;
+    const int kb = kuse_of(bf.st, r, k);
+    const int K1 = g.k_max + 1;
+    const int m = g.m_s;
+    const double scale = ldexp(1.0, -g.F) / sqrt((double)zeta);
+    const long long* sv = bf.accSV + (size_t)r * K1 * m;
+    const int* ce = bf.colE + (size_t)r * K1;
+    double* W = Ww + (size_t)r * m * (k + 2);
+    const long long total = (long long)m * (kb + 2 < K1 ? kb + 2 : K1);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(t / m);
+        W[t] = (double)sv[t] * col_scale(scale, ce[i]);
+    }
+}
+
+__global__ void k_form(Geom g, Bufs bf, int k, int zeta, int use_sw, int need_T, double* Mw, double* Tw, int qmr,
+                       const double* Ww) {
     const int r = blockIdx.y;
     const int kb = kuse_of(bf.st, r, k);
     const int K1 = g.k_max + 1;
@@ -107,9 +128,12 @@ __global__ void k_form(Geom g, Bufs bf, int k, int zeta, int use_sw, int need_T,
                 val = bf.cvec[row];
             }
         } else if (col < kb) {
+            // Ww holds (double)sv * col_scale for every column: the same
+            // factors, so the same bits as forming them here
             double s = 0.0;
             const double* Hc = H + (size_t)K1 * col;
-            for (int i = 0; i <= col; ++i) s = fma((double)sv[(size_t)i * m + row] * col_scale(scale, ce[i]), Hc[i], s);
+            const double* W = Ww + (size_t)r * m * (k + 2) + row;
+            for (int i = 0; i <= col; ++i) s = fma(W[(size_t)i * m], Hc[i], s);
             const long long* last = use_sw ? sw : sv;
             val = fma((double)last[(size_t)(col + 1) * m + row] * col_scale(scale, ce[col + 1]), Hc[col + 1], s);
             if (need_T) T[(size_t)col * m + row] = (double)pv[(size_t)col * m + row] * col_scale(pscale, pe[col]);
@@ -208,25 +232,13 @@ __device__ __forceinline__ void apply_block(const double* v, double tau, double*
 }
 
 // Householder QR (R only), pipelined by columns instead of a grid barrier
-// per column.  Columns are dealt to the job's CTAs in blocks of kHhBlock
-// (column j to CTA (j / kHhBlock) mod cpj), so a CTA forms the reflectors of
-// a block one after the other with no hand-off between them: one flag wait
-// on the critical path per block instead of per column.  Reflector i is
+// per column.  Column j belongs to CTA j mod cpj of its job.  Reflector i is
 // published by its owner (vector in the column below the diagonal, tau in
 // the diagonal slot, then a flag); a CTA waits only for the flag of the
 // reflector it applies next, and applies reflectors in order.  The owner of
 // column i+1 applies reflector i to that column first and publishes
 // reflector i+1 at once (lookahead), before its other columns; two shared
 // buffers hold v_i and v_{i+1}.  Cooperative launch: all CTAs co-resident.
-constexpr int kHhBlock = 4;
-
-// the first column >= j that CTA q of cpj owns
-__device__ __forceinline__ int hh_next_owned(int j, int q, int cpj) {
-    const int b = j / kHhBlock;
-    const int d = ((q - b % cpj) % cpj + cpj) % cpj;       // blocks to skip to reach one of q's
-    return d == 0 ? j : (b + d) * kHhBlock;
-}
-
 __global__ void __launch_bounds__(256) k_householder(Geom g, const DevState* st, int k, int need_T, int cpj,
                                                       double* Mw, double* Tw, double* dM, double* dT,
                                                       unsigned* flags, int* err) {
@@ -255,7 +267,7 @@ __global__ void __launch_bounds__(256) k_householder(Geom g, const DevState* st,
         double* v = s_buf + (size_t)(i & 1) * m;
         double* ci = A + (size_t)i * m;
         double tau;
-        if ((i / kHhBlock) % cpj == q) {
+        if (i % cpj == q) {
             if (have != i) make_reflector(ci, i, m, v, diag + i, flag + i, s_red, &s_tau[i & 1]);
             tau = s_tau[i & 1];
         } else {
@@ -266,8 +278,9 @@ __global__ void __launch_bounds__(256) k_householder(Geom g, const DevState* st,
             __syncthreads();
             tau = s_tau[i & 1];
         }
-        // owned columns j > i, in blocks of kHhBlock every cpj blocks
-        const int j0 = hh_next_owned(i + 1, q, cpj);
+        // owned columns j > i: j = q, q + cpj, ...
+        int j0 = q;
+        if (j0 <= i) j0 += ((i - q) / cpj + 1) * cpj;
         if (j0 >= ncols) break;                // no column (and no reflector) left here
         int jrest = j0;
         if (j0 == i + 1) {
@@ -279,11 +292,11 @@ __global__ void __launch_bounds__(256) k_householder(Geom g, const DevState* st,
                                &s_tau[(i + 1) & 1]);
                 have = i + 1;
             }
-            jrest = hh_next_owned(j0 + 1, q, cpj);
+            jrest = j0 + cpj;
         }
         if (tau != 0.0) {
             int idx = 0;
-            for (int jc = jrest; jc < ncols; jc = hh_next_owned(jc + 1, q, cpj), ++idx) {
+            for (int jc = jrest; jc < ncols; jc += cpj, ++idx) {
                 if ((idx % nw) != warp) continue;
                 double* cj = A + (size_t)jc * m;
                 double d = 0.0;
@@ -316,7 +329,9 @@ __global__ void __launch_bounds__(256) k_small_solve(Geom g, const DevState* st,
     const int ld = 2 * kb + 1;
     double* S = Sw + ((size_t)r * nl + l) * (size_t)(2 * k + 1) * (k + 1);
     // top rows 0..kb: R_M restricted to columns 0..kb-1 plus rhs column kb
-    for (int t = threadIdx.x; t < (kb + 1) * ld; t += blockDim.x) {
+    // (lambda = 0: the back substitution reads R_M in place, only the rhs
+    // column is copied)
+    for (int t = lam == 0.0 ? kb * ld + threadIdx.x : threadIdx.x; t < (kb + 1) * ld; t += blockDim.x) {
         const int col = t / ld, row = t - col * ld;
         double v = 0.0;
         if (row <= kb) {
@@ -380,8 +395,13 @@ __global__ void __launch_bounds__(256) k_small_solve(Geom g, const DevState* st,
     // takes its updates in decreasing column order.
     __shared__ double s_inv[kSmallMaxK];
     double* rhs = S + (size_t)kb * ld;
+    // R(row, i), row <= i: from R_M itself (lambda = 0) or the stacked QR
+    auto Rv = [&](int row, int i) -> double {
+        if (lam == 0.0) return row < i ? M[(size_t)i * m + row] : dm[i];
+        return S[(size_t)i * ld + row];
+    };
     for (int i = threadIdx.x; i < kb; i += blockDim.x) {
-        const double d = S[(size_t)i * ld + i];
+        const double d = Rv(i, i);
         s_inv[i] = d != 0.0 ? 1.0 / d : 0.0;
     }
     __syncthreads();
@@ -393,7 +413,7 @@ __global__ void __launch_bounds__(256) k_small_solve(Geom g, const DevState* st,
             for (int i = hi - 1; i >= lo; --i) {
                 const double yi = __shfl_sync(0xffffffffu, b * s_inv[i < 0 ? 0 : i], i - lo);
                 if (lane == 0) y[i] = yi;
-                if (row < i) b = fma(-S[(size_t)i * ld + row], yi, b);
+                if (row < i) b = fma(-Rv(row, i), yi, b);
                 if (lane == i - lo) b = yi;                  // row i now holds y_i
             }
             if (row < hi) rhs[row] = b;                      // y of the block, for the rows above
@@ -401,7 +421,7 @@ __global__ void __launch_bounds__(256) k_small_solve(Geom g, const DevState* st,
         __syncthreads();
         for (int row = threadIdx.x; row < lo; row += blockDim.x) {
             double b = rhs[row];
-            for (int i = hi - 1; i >= lo; --i) b = fma(-S[(size_t)i * ld + row], rhs[i], b);
+            for (int i = hi - 1; i >= lo; --i) b = fma(-Rv(row, i), rhs[i], b);
             rhs[row] = b;
         }
         __syncthreads();
@@ -413,7 +433,7 @@ __global__ void __launch_bounds__(256) k_small_solve(Geom g, const DevState* st,
 // Each thread owns 16 bytes of every basis column per pass and keeps eight
 // 128-bit column loads in flight.
 // ------------------------------------------------------------------------
-template <class T, int NL, bool ONE>
+template <class T, int NL>
 __global__ void __launch_bounds__(256) k_reconstruct(Geom g, Bufs bf, const DevState* st, int k, int nl,
                                                       const double* Yw, int l0, int nlc, float* x) {
     using Acc = typename AccOf<T>::type;
@@ -451,9 +471,7 @@ __global__ void __launch_bounds__(256) k_reconstruct(Geom g, Bufs bf, const DevS
                 const T* vv = (const T*)&raw[u];
 #pragma unroll
                 for (int q = 0; q < VEC; ++q) {
-                    // one RHS (ONE): the coefficient is the same for the VEC
-                    // elements, read once per column
-                    const int rr = ONE ? 0 : (int)((base + q) & (B - 1));
+                    const int rr = (int)((base + q) & (B - 1));
                     const Acc vq = to_acc(vv[q]);
 #pragma unroll
                     for (int l = 0; l < NL; ++l) acc[l][q] = fma(s_y[((size_t)l * B + rr) * k + c + u], vq, acc[l][q]);
@@ -465,7 +483,7 @@ __global__ void __launch_bounds__(256) k_reconstruct(Geom g, Bufs bf, const DevS
             const T* vv = (const T*)&r1;
 #pragma unroll
             for (int q = 0; q < VEC; ++q) {
-                const int rr = ONE ? 0 : (int)((base + q) & (B - 1));
+                const int rr = (int)((base + q) & (B - 1));
                 const Acc vq = to_acc(vv[q]);
 #pragma unroll
                 for (int l = 0; l < NL; ++l) acc[l][q] = fma(s_y[((size_t)l * B + rr) * k + c], vq, acc[l][q]);
@@ -503,11 +521,13 @@ cudaError_t launch_solve_prepare(const Geom& g, const Bufs& bf, int zeta, int k,
     double* dT = (double*)(base + L.dT_off);
     unsigned* bars = (unsigned*)(base + L.bar_off);
     int* err = (int*)(base + L.err_off);
+    double* Ww = (double*)(base + L.W_off);
     cudaError_t e = cudaMemsetAsync(base, 0, L.M_off, s);
     if (e != cudaSuccess) return e;
     {
         dim3 grid((unsigned)((g.m_s * (k + 1) + 255) / 256), (unsigned)g.B);
-        k_form<<<grid, 256, 0, s>>>(g, bf, k, zeta, use_sw ? 1 : 0, need_T ? 1 : 0, Mw, Tw, qmr ? 1 : 0);
+        if (!qmr && !bf.svd) k_scale_sv<<<grid, 256, 0, s>>>(g, bf, k, zeta, Ww);
+        k_form<<<grid, 256, 0, s>>>(g, bf, k, zeta, use_sw ? 1 : 0, need_T ? 1 : 0, Mw, Tw, qmr ? 1 : 0, Ww);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int njobs = g.B * (need_T ? 2 : 1);
@@ -520,8 +540,7 @@ cudaError_t launch_solve_prepare(const Geom& g, const Bufs& bf, int zeta, int k,
     if (occ < 1) occ = 1;
     const int maxblocks = occ * num_sms;
     int cpj = maxblocks / njobs;
-    const int nblk = (k + 2 + kHhBlock - 1) / kHhBlock;   // column blocks of the widest matrix
-    if (cpj > nblk) cpj = nblk;
+    if (cpj > (k + 2) / 2) cpj = (k + 2) / 2;
     if (cpj < 1) cpj = 1;
     if (cpj * njobs > maxblocks) return cudaErrorInvalidConfiguration;   // cannot co-reside
     const int nb = cpj * njobs;
@@ -567,19 +586,11 @@ cudaError_t launch_solve_lambdas(int storage, const Geom& g, const Bufs& bf, int
         };
         auto byNL = [&](auto tag, int vec) -> cudaError_t {
             using T = decltype(tag);
-            if (g.B == 1) {
-                switch (NLp) {
-                    case 1: return launch(k_reconstruct<T, 1, true>, vec);
-                    case 2: return launch(k_reconstruct<T, 2, true>, vec);
-                    case 4: return launch(k_reconstruct<T, 4, true>, vec);
-                    default: return launch(k_reconstruct<T, 8, true>, vec);
-                }
-            }
             switch (NLp) {
-                case 1: return launch(k_reconstruct<T, 1, false>, vec);
-                case 2: return launch(k_reconstruct<T, 2, false>, vec);
-                case 4: return launch(k_reconstruct<T, 4, false>, vec);
-                default: return launch(k_reconstruct<T, 8, false>, vec);
+                case 1: return launch(k_reconstruct<T, 1>, vec);
+                case 2: return launch(k_reconstruct<T, 2>, vec);
+                case 4: return launch(k_reconstruct<T, 4>, vec);
+                default: return launch(k_reconstruct<T, 8>, vec);
             }
         };
         switch (storage) {
