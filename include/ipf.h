@@ -139,8 +139,10 @@ typedef void* (*ipf_alloc_fn)(size_t bytes, void* user);
 typedef void (*ipf_free_fn)(void* ptr, void* user);
 
 typedef struct ipf_config {
-    int k_max;                   /* maximum Hessenberg steps, 1..224 (basis has k_max+1
-                                    vectors; the FP64 pivot block lives in shared memory)  */
+    int k_max;                   /* maximum Hessenberg steps, 1..480 (basis has k_max+1
+                                    vectors; the FP64 pivot block is staged in shared
+                                    memory up to 224, read from L2 beyond); with the
+                                    Gaussian sketch 1..247                                 */
     int m_s;                     /* sketch rows (l in Sec. 2); m_s >= zeta                  */
     int zeta;                    /* nonzeros per sketch column, 1..16                       */
     unsigned long long seed;     /* sketch seed (SplitMix64 state)                          */

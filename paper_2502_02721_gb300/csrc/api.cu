@@ -642,7 +642,9 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     if (cfg.zform != IPF_Z_DIRECT && cfg.zform != IPF_Z_HESSENBERG && cfg.zform != IPF_Z_AUTO) return IPF_ERR_ARG;
     const bool z_ok = cfg.storage != IPF_STORE_F64;
     if (cfg.zform == IPF_Z_DIRECT && !z_ok) return IPF_ERR_UNSUPPORTED;
-    if (cfg.k_max > kMaxK) return IPF_ERR_UNSUPPORTED;    // pivot block (FP64) fits shared memory
+    if (cfg.k_max > kMaxK) return IPF_ERR_UNSUPPORTED;    // the pivot solve's rows (512) in registers
+    // the Gaussian contraction's B tile: V_{k+1} rounded up, plus 8 rows of b, at most 256 rows
+    if (gauss && (cfg.k_max + 1 + 8 + 15) / 16 * 16 > 256) return IPF_ERR_UNSUPPORTED;
     if (b_mem != IPF_MEM_HOST && b_mem != IPF_MEM_DEVICE) return IPF_ERR_ARG;
     const size_t accb = cfg.storage == IPF_STORE_F64 ? 8 : 4;
 

@@ -293,8 +293,9 @@ struct OpDev {
 // its status is IPF_OK and its step counter is below k_target.
 // ---------------------------------------------------------------------------
 constexpr int kMaxSlots = 64;
-constexpr int kMaxK = 224;                     // k_max: the FP64 pivot block fits in shared memory
-constexpr int kSmallMaxK = 256;                // the projected solve's per-column shared arrays
+constexpr int kPivSmemK = 224;                 // k_max up to which the FP64 pivot block is staged in shared memory
+constexpr int kMaxK = 480;                     // k_max (the pivot solve's registers hold 512 rows)
+constexpr int kSmallMaxK = 512;                // the projected solve's per-column shared arrays
 static_assert(kMaxK <= kSmallMaxK, "projected solve arrays");
 constexpr int kBatchUpdTile = kFoldEvery;      // update tile: the split counters' exact range
 constexpr int kBatchNormTile = 4096;           // normalise tile (elements)

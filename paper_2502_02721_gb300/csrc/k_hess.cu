@@ -42,14 +42,17 @@ __global__ void k_load_rhs(const float* __restrict__ b, Acc* __restrict__ w, lon
 // the whole block is one flat copy into shared memory.  Warp 0 then solves
 // L_p h = u(p) in FP64 with lane l holding rows l, l+32, ..., l+224 in
 // registers: x_c is broadcast by a shuffle and every lane updates its rows
-// below c, with no block-wide barrier per column.  j < 256.
+// below c, with no block-wide barrier per column.  j < 128 NG (NG row
+// groups of 32 per warp).  SM: L_p staged in shared memory (k_max up to
+// kPivSmemK); otherwise the rows are read from L_p in global memory (L2:
+// k_max^2 / 2 doubles, 0.9 MB at k_max = 480).
 // ------------------------------------------------------------------------
 // doubles per RHS for the packed L_p, rounded up to whole 16-byte chunks
 __host__ __device__ constexpr size_t lp_stride(int k_max) { return ((size_t)(k_max + 1) * k_max / 2 + 2) & ~(size_t)1; }
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
-template <class T, class Acc>
+template <class T, class Acc, int NG, bool SM>
 __device__ __forceinline__ void pivot_solve_body(const Geom& g, const Bufs& bf, int r) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long s_bar;
@@ -57,20 +60,20 @@ __device__ __forceinline__ void pivot_solve_body(const Geom& g, const Bufs& bf, 
     DevState* st = bf.st;
     if (st->status[r] != IPF_OK) return;
     const int j = st->j;
-    if (j < 0 || j >= g.k_max || j >= 256) return;
+    if (j < 0 || j >= g.k_max || j >= 128 * NG) return;
     const int K1 = g.k_max + 1;
     const int B = g.B;
     const T* V = (const T*)bf.V;
     const Acc* w = (const Acc*)bf.w;
     double* Lp = (double*)bf.LpT + (size_t)r * lp_stride(g.k_max);
     const int* piv = bf.piv + (size_t)r * K1;
-    double* s_L = (double*)smem_raw;                      // rows 1..j, packed (16-byte aligned)
-    double* s_g = s_L + lp_stride(g.k_max);
+    double* s_L = (double*)smem_raw;                      // rows 1..j, packed (16-byte aligned; SM only)
+    double* s_g = SM ? s_L + lp_stride(g.k_max) : (double*)smem_raw;
     const size_t rowj = (size_t)j * (j - 1) / 2;          // doubles in rows 1..j-1
     const unsigned bytes = (unsigned)(((rowj + 1) & ~(size_t)1) * sizeof(double));   // whole 16-byte chunks
     if (threadIdx.x == 0) {
         s_timeout = 0;
-        if (bytes) {
+        if (SM && bytes) {
             // one bulk copy of the stored rows into shared memory, completion on an mbarrier
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar)));
             asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -94,7 +97,7 @@ __device__ __forceinline__ void pivot_solve_body(const Geom& g, const Bufs& bf, 
     } else {
         for (int i = threadIdx.x; i <= j; i += blockDim.x) s_g[i] = (double)w[(size_t)piv[i] * B + r];
     }
-    if (threadIdx.x == 0 && bytes) {
+    if (SM && threadIdx.x == 0 && bytes) {
         // bounded wait on the copy: gives up after ~2^22 polls and reports a timeout
         unsigned done = 0;
         for (long long it = 0; it < (1ll << 22) && !done; ++it) {
@@ -118,8 +121,10 @@ __device__ __forceinline__ void pivot_solve_body(const Geom& g, const Bufs& bf, 
     }
     __syncthreads();
     // row j goes to shared memory after the bulk copy has landed (it is not part of it)
-    for (int c = threadIdx.x; c < j; c += blockDim.x) s_L[rowj + c] = Lp[rowj + c];
+    if (SM)
+        for (int c = threadIdx.x; c < j; c += blockDim.x) s_L[rowj + c] = Lp[rowj + c];
     __syncthreads();
+    const double* Lr = SM ? s_L : Lp;                      // the rows of L_p, where this CTA reads them
     if (s_timeout) {
         if (threadIdx.x == 0) st->status[r] = IPF_ERR_TIMEOUT;
         return;
@@ -136,10 +141,10 @@ __device__ __forceinline__ void pivot_solve_body(const Geom& g, const Bufs& bf, 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int qmax = j >> 5;                               // last row group holding a row <= j
     double* s_x = s_g + ((j + 2) & ~1);                    // x_c per column, after g
-    double x[2];
-    int off[2];
+    double x[NG];
+    int off[NG];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < NG; ++h) {
         const int i = (warp + 4 * h) * 32 + lane;
         x[h] = (i <= j) ? s_g[i] : 0.0;
         off[h] = i * (i - 1) / 2;
@@ -149,26 +154,31 @@ __device__ __forceinline__ void pivot_solve_body(const Geom& g, const Bufs& bf, 
         const int cend = j - c0 < 32 ? j - c0 : 32;            // columns c = c0 + cc < j
         if (warp == (cb & 3)) {
             const int oh = cb >> 2;
-            double xv = oh ? x[1] : x[0];
-            const int offr = oh ? off[1] : off[0];
+            double xv = x[0];
+            int offr = off[0];
+#pragma unroll
+            for (int h = 1; h < NG; ++h)
+                if (h == oh) { xv = x[h]; offr = off[h]; }
             const bool row_ok = c0 + lane <= j;
 #pragma unroll 1
             for (int cc = 0; cc < cend; ++cc) {
                 const double xc = __shfl_sync(0xffffffffu, xv, cc);
-                if (row_ok && lane > cc) xv = fma(-s_L[offr + c0 + cc], xc, xv);
+                if (row_ok && lane > cc) xv = fma(-Lr[offr + c0 + cc], xc, xv);
             }
-            if (oh) x[1] = xv; else x[0] = xv;
+#pragma unroll
+            for (int h = 0; h < NG; ++h)
+                if (h == oh) x[h] = xv;
             if (c0 + lane < j) s_x[c0 + lane] = xv;
         }
         asm volatile("bar.sync 1, 128;" ::: "memory");
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < NG; ++h) {
             const int q = warp + 4 * h;
             // rows i > c with i <= j only: s_L holds rows 1..j and nothing beyond
             if (q > cb && q <= qmax && q * 32 + lane <= j) {
                 double xv = x[h];
 #pragma unroll 4
-                for (int cc = 0; cc < cend; ++cc) xv = fma(-s_L[off[h] + c0 + cc], s_x[c0 + cc], xv);
+                for (int cc = 0; cc < cend; ++cc) xv = fma(-Lr[off[h] + c0 + cc], s_x[c0 + cc], xv);
                 x[h] = xv;
             }
         }
@@ -176,7 +186,7 @@ __device__ __forceinline__ void pivot_solve_body(const Geom& g, const Bufs& bf, 
     double* Hc = bf.H + (size_t)r * K1 * g.k_max + (size_t)K1 * j;
     Acc* coef = (Acc*)bf.coef;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < NG; ++h) {
         const int i = (warp + 4 * h) * 32 + lane;
         if (i <= j) {
             Hc[i] = x[h];
@@ -185,9 +195,9 @@ __device__ __forceinline__ void pivot_solve_body(const Geom& g, const Bufs& bf, 
     }
 }
 
-template <class T, class Acc>
+template <class T, class Acc, int NG, bool SM>
 __global__ void __launch_bounds__(256) k_pivot_solve(Geom g, Bufs bf) {
-    pivot_solve_body<T, Acc>(g, bf, blockIdx.x);
+    pivot_solve_body<T, Acc, NG, SM>(g, bf, blockIdx.x);
 }
 
 // ------------------------------------------------------------------------
@@ -1346,7 +1356,7 @@ __global__ void __launch_bounds__(256) kb_normalize(const SlotDesc* __restrict__
     }
 }
 
-template <class T, class Acc>
+template <class T, class Acc, int NG, bool SM>
 __global__ void __launch_bounds__(256) kb_pivot_solve(const SlotDesc* __restrict__ slots,
                                                       const TileRef* __restrict__ list) {
     const SlotDesc* sd = slots + list[blockIdx.x].slot;
@@ -1355,7 +1365,7 @@ __global__ void __launch_bounds__(256) kb_pivot_solve(const SlotDesc* __restrict
     if (st->j >= sd->k_target) return;
     const Geom g = sd->g;
     const Bufs bf = sd->bf;
-    pivot_solve_body<T, Acc>(g, bf, 0);
+    pivot_solve_body<T, Acc, NG, SM>(g, bf, 0);
 }
 
 // ------------------------------------------------------------------------
@@ -1382,9 +1392,12 @@ cudaError_t launch_pivot_solve(int storage, const Geom& g, const Bufs& bf, cudaS
     const int K1 = g.k_max + 1;
     IPF_DISPATCH_STORAGE(storage, {
         using Acc = typename AccOf<T>::type;
-        // packed L_p, then g (K1, rounded to even) and the column values x_c (K1)
-        const size_t smem = lp_stride(g.k_max) * sizeof(double) + (size_t)(((K1 + 1) & ~1) + K1 + 1) * sizeof(double);
-        auto fn = k_pivot_solve<T, Acc>;
+        // packed L_p (up to kPivSmemK), then g (K1, rounded to even) and the
+        // column values x_c (K1)
+        const bool sm = g.k_max <= kPivSmemK;
+        const size_t small = (size_t)(((K1 + 1) & ~1) + K1 + 1) * sizeof(double);
+        const size_t smem = (sm ? lp_stride(g.k_max) * sizeof(double) : 0) + small;
+        auto fn = sm ? k_pivot_solve<T, Acc, 2, true> : k_pivot_solve<T, Acc, 4, false>;
         cudaError_t e = raise_smem(fn, (int)smem);
         if (e != cudaSuccess) return e;
         fn<<<g.B, 256, smem, s>>>(g, bf);
@@ -1593,7 +1606,9 @@ cudaError_t launch_batch_pivot_solve(int storage, const SlotDesc* slots, const T
                                      cudaStream_t s) {
     if (nslots <= 0) return cudaSuccess;
     const int K1 = k_max + 1;
-    const size_t smem = lp_stride(k_max) * sizeof(double) + (size_t)(((K1 + 1) & ~1) + K1 + 1) * sizeof(double);
+    const bool sm = k_max <= kPivSmemK;                   // the group's largest k_max
+    const size_t smem = (sm ? lp_stride(k_max) * sizeof(double) : 0) +
+                        (size_t)(((K1 + 1) & ~1) + K1 + 1) * sizeof(double);
     auto go = [&](auto fn) -> cudaError_t {
         cudaError_t e = raise_smem(fn, (int)smem);
         if (e != cudaSuccess) return e;
@@ -1601,9 +1616,11 @@ cudaError_t launch_batch_pivot_solve(int storage, const SlotDesc* slots, const T
         return cudaGetLastError();
     };
     switch (storage) {
-        case IPF_STORE_F32: return go(kb_pivot_solve<float, float>);
-        case IPF_STORE_BF16: return go(kb_pivot_solve<__nv_bfloat16, float>);
-        case IPF_STORE_F16: return go(kb_pivot_solve<__half, float>);
+        case IPF_STORE_F32: return sm ? go(kb_pivot_solve<float, float, 2, true>) : go(kb_pivot_solve<float, float, 4, false>);
+        case IPF_STORE_BF16:
+            return sm ? go(kb_pivot_solve<__nv_bfloat16, float, 2, true>)
+                      : go(kb_pivot_solve<__nv_bfloat16, float, 4, false>);
+        case IPF_STORE_F16: return sm ? go(kb_pivot_solve<__half, float, 2, true>) : go(kb_pivot_solve<__half, float, 4, false>);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -69,6 +69,12 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.ipf_create(C.byref(op), bb.ctypes.data, 0, C.byref(cfg), C.byref(h)) == b.IPF_ERR_UNSUPPORTED
     cfg = b.default_config(m_s=4, zeta=8)
     assert lib.ipf_create(C.byref(op), bb.ctypes.data, 0, C.byref(cfg), C.byref(h)) == b.IPF_ERR_ARG
+    # k_max: at most 480 (512 pivot rows in registers), 247 with the Gaussian
+    # sketch (its contraction's B tile holds 256 rows)
+    cfg = b.default_config(k_max=481, m_s=2000)
+    assert lib.ipf_create(C.byref(op), bb.ctypes.data, 0, C.byref(cfg), C.byref(h)) == b.IPF_ERR_UNSUPPORTED
+    cfg = b.default_config(k_max=248, m_s=1000, sketch="gaussian")
+    assert lib.ipf_create(C.byref(op), bb.ctypes.data, 0, C.byref(cfg), C.byref(h)) == b.IPF_ERR_UNSUPPORTED
     assert lib.ipf_step(None, 1, None) == b.IPF_ERR_ARG
     assert lib.ipf_footprint(C.byref(op), C.byref(b.default_config())) > 64 * 51 * 4
 

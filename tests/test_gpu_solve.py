@@ -218,6 +218,23 @@ def test_interleaved_solves_and_exports_keep_sketch_exact(deblur64, storage, ove
     assert np.array_equal(x12, x_ref12)
 
 
+@pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
+def test_large_k_pivot_block_from_l2(storage):
+    """k = 300, m_s = 1200: beyond the 224 columns whose FP64 pivot block is
+    staged in shared memory, the pivot-block solve reads L_p from global
+    memory with four row groups per warp (up to 512 rows); pivots and x_k
+    against the oracle up to the full k."""
+    p = P.make("deblur64")
+    k, m_s = 300, 1200
+    ctx = gpu_context(p, storage, k=k, m_s=m_s)
+    ctx.step(k)
+    status, kd = ctx.sync()
+    assert kd == [k]
+    verify_scmrh(ctx, p, storage, [50, 150, 225, 300], [0.0, 1e-3], k=k, m_s=m_s,
+                 require_all_pivots=storage == "f64", name=f"large_k300_{storage}")
+    ctx.close()
+
+
 def test_ragged_psf_image():
     rng = np.random.default_rng(7)
     H, W = 100, 130
