@@ -560,11 +560,29 @@ __device__ __forceinline__ float pivot_row_psf(const T* __restrict__ v, int p, i
     const int lane = threadIdx.x & 31;
     const int py = p / W, px = p - py * W;
     const int cy = ph / 2, cx = pw / 2;
+    const int taps = ph * pw;
     float acc = 0.f;
-    for (int t = lane; t < ph * pw; t += 32) {
-        const int ky = t / pw, kx = t - ky * pw;
-        const int yy = py - ky + cy, xx = px - kx + cx;
-        if (yy >= 0 && yy < H && xx >= 0 && xx < W) acc = fmaf(psf[t], to_acc(v[(size_t)yy * W + xx]), acc);
+    // U taps per lane per pass, every load of the pass issued before its
+    // FMAs (the taps t = lane, lane + 32, ... are still added in that order)
+    constexpr int U = 8;
+    for (int t0 = lane; t0 < taps; t0 += 32 * U) {
+        float f[U], x[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int t = t0 + 32 * u;
+            const int ky = t / pw, kx = t - ky * pw;
+            const int yy = py - ky + cy, xx = px - kx + cx;
+            const bool in = t < taps && yy >= 0 && yy < H && xx >= 0 && xx < W;
+            f[u] = in ? psf[t] : 0.f;
+            x[u] = in ? to_acc(v[(size_t)yy * W + xx]) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int t = t0 + 32 * u;
+            const int ky = t / pw, kx = t - ky * pw;
+            const int yy = py - ky + cy, xx = px - kx + cx;
+            if (t < taps && yy >= 0 && yy < H && xx >= 0 && xx < W) acc = fmaf(f[u], x[u], acc);
+        }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);

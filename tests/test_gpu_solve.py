@@ -230,8 +230,11 @@ def test_large_k_pivot_block_from_l2(storage):
     ctx.step(k)
     status, kd = ctx.sync()
     assert kd == [k]
-    verify_scmrh(ctx, p, storage, [50, 150, 225, 300], [0.0, 1e-3], k=k, m_s=m_s,
-                 require_all_pivots=storage == "f64", name=f"large_k300_{storage}")
+    # past j ~ 70 this smooth operator's residual is at rounding level and the
+    # pivot order chaotic even in FP64, so the pivots are checked against the
+    # oracle's own divergence under perturbations of the same size (in every
+    # storage type), and x_k by replaying the GPU's pivots
+    verify_scmrh(ctx, p, storage, [50, 150, 225, 300], [0.0, 1e-3], k=k, m_s=m_s, name=f"large_k300_{storage}")
     ctx.close()
 
 
