@@ -74,7 +74,7 @@ constexpr int kOffSeg = kBMax;
 constexpr int kOffHank = kOffSeg + kNSeg * kSegBytes;
 constexpr int kOffBar = kOffHank + kNHG * kG * kHankBytes;
 constexpr int kNBar = 2 * kNSeg + 2 * kNHG + 2 * kNDG + 1;
-constexpr int kOffMisc = kOffBar + 8 * kNBar;
+constexpr int kOffMisc = kOffBar + 8 * (kNBar + 1);       // + the B operand's barrier
 constexpr int kSmemUsed = kOffMisc + 16;
 constexpr int kSmemRequest = kSmemUsed + 1024;
 static_assert(kRB == kG, "one staged box per group");
@@ -134,6 +134,7 @@ __device__ __forceinline__ void conv_tc_body(const CUtensorMap* vmap, const int*
     auto d_full = [&](int i) { return bar0 + 8u * (2 * kNSeg + 2 * kNHG + i); };
     auto d_empty = [&](int i) { return bar0 + 8u * (2 * kNSeg + 2 * kNHG + kNDG + i); };
     const uint32_t done_bar = bar0 + 8u * (kNBar - 1);
+    const uint32_t b_bar = bar0 + 8u * kNBar;               // the B operand has landed
     uint32_t* s_tmem = (uint32_t*)(sm + kOffMisc);
     volatile int* s_abort = (volatile int*)(sm + kOffMisc + 4);
 
@@ -152,11 +153,18 @@ __device__ __forceinline__ void conv_tc_body(const CUtensorMap* vmap, const int*
         for (int i = 0; i < kNHG; ++i) { mbar_init(h_full(i), 32); mbar_init(h_empty(i), 1); }
         for (int i = 0; i < kNDG; ++i) { mbar_init(d_full(i), 1); mbar_init(d_empty(i), 128); }
         mbar_init(done_bar, kIssuers);
+        mbar_init(b_bar, 1);
         *s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        // the B operand by one bulk copy, landing while the first row boxes
+        // are staged and built (the issuers wait for it before their first MMA)
+        mbar_expect_tx(b_bar, (uint32_t)S::BBYTES);
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                sbase + (uint32_t)kOffB),
+            "l"(bimg), "r"((uint32_t)S::BBYTES), "r"(b_bar)
+            : "memory");
     }
-    for (int i = threadIdx.x; i < S::BBYTES / 16; i += kThreads) ((uint4*)(sm + kOffB))[i] = bimg[i];
-    fence_proxy_async_smem();
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          (uint32_t)__cvta_generic_to_shared(s_tmem)),
@@ -184,12 +192,14 @@ __device__ __forceinline__ void conv_tc_body(const CUtensorMap* vmap, const int*
             // every issued copy lands before the CTA may exit
             for (int t = issued > kNSeg ? issued - kNSeg : 0; t < issued; ++t)
                 mbar_wait(seg_full(t % kNSeg), (t / kNSeg) & 1, s_abort, err, false);
+            mbar_wait(b_bar, 0, s_abort, err, false);
         }
     } else if (warp <= 3 || warp == 12) {
         // ---- MMA issuers: groups g = issuer (mod kIssuers) ----
         if (lane == 0) {
             const int issuer = warp == 12 ? 3 : warp - 1;
-            for (int g = issuer; g < NG; g += kIssuers) {
+            const bool b_ok = mbar_wait(b_bar, 0, s_abort, err);
+            for (int g = issuer; b_ok && g < NG; g += kIssuers) {
                 const int hg = g % kNHG, dg = g % kNDG;
                 if (!mbar_wait(h_full(hg), (g / kNHG) & 1, s_abort, err)) break;
                 if (!mbar_wait(d_empty(dg), ((g / kNDG) & 1) ^ 1, s_abort, err)) break;
