@@ -233,41 +233,50 @@ __device__ __forceinline__ void conv_tc_body(const CUtensorMap* vmap, const int*
             if (!mbar_wait(seg_full(sl), (g / kNSeg) & 1, s_abort, err)) break;
             if (!mbar_wait(h_empty(hg), ((g / kNHG) & 1) ^ 1, s_abort, err)) break;
             const int rows = min(kG, NR - g * kG);
-            constexpr int NIT = (NQ * 8 + 31) / 32;
+            // two image rows per pass; a lane takes the core-matrix rows s = 2t
+            // and 2t + 1 of block q of one of them: both 16-byte rows lie in
+            // the five source words from (OFF + 8q + 2t) / 2 on, so the loads
+            // per stored byte are half those of one row per lane (the staged
+            // segment's reads and the block stores are the shared-memory
+            // traffic the convolution is bound by)
+            constexpr int JOBS = NQ * 4;                        // (q, t) per image row
+            constexpr int NIT = (2 * JOBS + 31) / 32;
             for (int r0 = 0; r0 < rows; r0 += 2) {
-                // two image rows: all their source words first (independent
-                // loads in flight together), then the byte permutes and stores
-                uint32_t wv[2][NIT][5];
+                uint32_t wv[NIT][5];
 #pragma unroll
-                for (int p = 0; p < 2; ++p) {
+                for (int it = 0; it < NIT; ++it) {
+                    const int jb = it * 32 + lane;
+                    const int p = jb >= JOBS ? 1 : 0, rem = jb - p * JOBS;
                     const int r = min(r0 + p, rows - 1);
                     const uint32_t* src = (const uint32_t*)(sm + kOffSeg + sl * kSegBytes + r * kSegW * 2);
+                    const int e0 = OFF + 8 * (rem >> 2) + 2 * (rem & 3);
+                    const int wb = jb < 2 * JOBS ? (e0 >> 1) : 0;
 #pragma unroll
-                    for (int it = 0; it < NIT; ++it) {
-                        const int row = it * 32 + lane;
-                        const int e0 = OFF + 8 * (row >> 3) + (row & 7);
-                        const int wb = row < NQ * 8 ? (e0 >> 1) : 0;
-#pragma unroll
-                        for (int k = 0; k < 5; ++k) wv[p][it][k] = src[wb + k];
-                    }
+                    for (int k = 0; k < 5; ++k) wv[it][k] = src[wb + k];
                 }
 #pragma unroll
-                for (int p = 0; p < 2; ++p) {
-                    if (r0 + p < rows) {
+                for (int it = 0; it < NIT; ++it) {
+                    const int jb = it * 32 + lane;
+                    const int p = jb >= JOBS ? 1 : 0, rem = jb - p * JOBS;
+                    if (jb < 2 * JOBS && r0 + p < rows) {
                         unsigned char* dst = sm + kOffHank + (hg * kG + r0 + p) * kHankBytes;
+                        const int q = rem >> 2, t = rem & 3;
+                        const int e0 = OFF + 8 * q + 2 * t;
+                        (void)e0;
 #pragma unroll
-                        for (int it = 0; it < NIT; ++it) {
-                            const int row = it * 32 + lane;
-                            if (row < NQ * 8) {
-                                const int q = row >> 3, s = row & 7;
-                                const uint32_t sel = ((OFF + s) & 1) ? 0x5432u : 0x3210u;
-                                uint4 o;
-                                o.x = __byte_perm(wv[p][it][0], wv[p][it][1], sel);
-                                o.y = __byte_perm(wv[p][it][1], wv[p][it][2], sel);
-                                o.z = __byte_perm(wv[p][it][2], wv[p][it][3], sel);
-                                o.w = __byte_perm(wv[p][it][3], wv[p][it][4], sel);
-                                *(uint4*)(dst + q * 128 + s * 16) = o;
-                            }
+                        for (int u = 0; u < 2; ++u) {
+                            // e = e0 + u has the parity of OFF + u (8q + 2t is even):
+                            // d words into wv, and a two-byte shift when e is odd
+                            constexpr bool kOdd = (OFF & 1) != 0;
+                            const int d = (kOdd && u == 1) ? 1 : 0;
+                            const uint32_t sel = ((OFF + u) & 1) ? 0x5432u : 0x3210u;
+                            const uint32_t w4 = d == 0 ? wv[it][4] : 0u;      // unused (aligned) when d = 1
+                            uint4 o;
+                            o.x = __byte_perm(wv[it][d], wv[it][d + 1], sel);
+                            o.y = __byte_perm(wv[it][d + 1], wv[it][d + 2], sel);
+                            o.z = __byte_perm(wv[it][d + 2], wv[it][d + 3], sel);
+                            o.w = __byte_perm(wv[it][d + 3], w4, sel);
+                            *(uint4*)(dst + q * 128 + (2 * t + u) * 16) = o;
                         }
                     }
                 }
