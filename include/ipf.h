@@ -104,7 +104,8 @@ enum ipf_method { IPF_METHOD_SCMRH = 0, IPF_METHOD_SLSLU = 1 };
  *              of the generator started at config.seed; u = ((out >> 11) + 1)
  *              2^-53; z = sqrt(-2 ln u1) cos(2 pi u2); S = z / sqrt(m_s)),
  *              rounded to the storage type and kept in device memory
- *              (m_s x n elements, row-major, see ipf_sketch_gaussian).  No
+ *              (m_s x n elements; ipf_sketch_gaussian writes the same values
+ *              row-major, the context keeps them in its own tiling).  No
  *              per-step sketch: at solve time one contraction forms
  *              [S V_{k+1} | S b] (the library's own kernels: tensor cores for
  *              BF16 / FP16 storage, with b entering as three exact parts of

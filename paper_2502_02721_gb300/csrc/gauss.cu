@@ -4,9 +4,11 @@
 // entry (r, i) takes outputs 2c and 2c+1, c = r*n + i, of the generator
 // started at the seed; u = ((out >> 11) + 1) * 2^-53 in (0, 1];
 // z = sqrt(-2 ln u1) cos(2 pi u2); S[r, i] = z / sqrt(m_s), rounded to the
-// storage type of the basis.  S is kept row-major (entry (r, i) at
-// r*lds + i), so both S and the basis V (column j at j*ldv) are K-major
-// operands of the one contraction the method needs at solve time:
+// storage type of the basis.  A context keeps S K-major (row-major for
+// FP32 / FP64, entry (r, i) at r*lds + i; for BF16 / FP16 in units of 16
+// rows x 64 elements, see k_gauss_fill_tiled), so S and the basis V (column
+// j at j*ldv) are both K-major operands of the one contraction the method
+// needs at solve time:
 //
 //     [S V_{k+1} | S b] = S [V_{k+1} | b]      (m_s x (k+2), K = n).
 //

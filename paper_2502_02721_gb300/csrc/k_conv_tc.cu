@@ -31,6 +31,11 @@
 //
 // One barrier wait, commit and arrive per group (each tcgen05 instruction
 // and barrier test costs tens of cycles of issue latency in its thread).
+// What bounds a group is shared-memory bandwidth: each MMA reads its A tile
+// (4 KB) and B tile (N x 32 bytes) from shared memory, and the builders read
+// the staged rows and store the Hankel blocks, about 1,000 128-byte
+// wavefronts per group of 8 image rows; the B image therefore arrives by one
+// bulk copy, and a builder lane writes two block rows from one set of loads.
 // Warp roles (416 threads, one CTA per SM): warp 0 issues the TMA loads;
 // warp 1 owns TMEM; one lane each of warps 1-3 and 12 issues the MMAs of
 // every fourth group; warps 8-11 build A (every fourth group, two image rows
@@ -227,7 +232,8 @@ __device__ __forceinline__ void conv_tc_body(const CUtensorMap* vmap, const int*
             mbar_wait(done_bar, 0, s_abort, err, false);
         }
     } else if (warp >= 8 && warp < 12) {
-        // ---- A builders: Hankel blocks from the staged box, one group per warp ----
+        // ---- A builders: Hankel blocks from the staged box, one group per warp
+        // (every fourth group), two image rows per pass ----
         for (int g = warp - 8; g < NG; g += kBuilders) {
             const int sl = g % kNSeg, hg = g % kNHG;
             if (!mbar_wait(seg_full(sl), (g / kNSeg) & 1, s_abort, err)) break;
