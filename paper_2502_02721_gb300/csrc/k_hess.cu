@@ -231,6 +231,9 @@ __device__ __forceinline__ void scatter8(int* s_hi, int* s_lo, const SketchParam
 // ------------------------------------------------------------------------
 template <class T, int B>
 __global__ void __launch_bounds__(256, 4) k_update_f(Geom g, Bufs bf, SketchParams sp) {
+    // the normaliser that follows may be placed as these CTAs finish; it
+    // waits for the whole grid (griddepcontrol.wait) before it reads anything
+    asm volatile("griddepcontrol.launch_dependents;");
     constexpr int VEC = Vec16<T>::n;
     constexpr int LB = (B == 1) ? 0 : (B == 2) ? 1 : (B == 4) ? 2 : (B == 8) ? 3 : (B == 16) ? 4 : 5;
     constexpr int NK = (B == 1) ? 1 : VEC;           // argmax keys kept per thread
@@ -552,6 +555,10 @@ __global__ void k_argmin_d(Geom g, Bufs bf) {
 template <class T, class Acc>
 __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams sp, int want_sw, int Bg, int lbg,
                                                    int lb) {
+    // launched as a programmatic dependent of the update: its CTAs may be
+    // placed while the update's last CTAs finish, and wait here until the
+    // update has completed and its writes are visible (a no-op otherwise)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     extern __shared__ unsigned char smem_raw[];
     constexpr bool f64 = sizeof(Acc) == 8;
     const int nacc = want_sw ? 2 : 1;
@@ -1533,7 +1540,20 @@ cudaError_t launch_normalize(int storage, const Geom& g, const Bufs& bf, const S
         auto fn = k_normalize<T, Acc>;
         cudaError_t e = raise_smem(fn, (int)smem);
         if (e != cudaSuccess) return e;
-        fn<<<grid, 256, smem, s>>>(g, bf, sp, want_sw ? 1 : 0, Bg, lbg, lb);
+        // programmatic dependent launch: overlaps this launch with the end of
+        // the kernel before it in the stream (the kernel waits for it first)
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = grid;
+        lc.blockDim = dim3(256);
+        lc.dynamicSmemBytes = smem;
+        lc.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        lc.attrs = at;
+        lc.numAttrs = 1;
+        e = cudaLaunchKernelEx(&lc, fn, g, bf, sp, want_sw ? 1 : 0, Bg, lbg, lb);
+        if (e != cudaSuccess) return e;
     });
     return cudaGetLastError();
 }
