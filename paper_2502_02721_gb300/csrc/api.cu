@@ -472,26 +472,23 @@ cudaError_t one_step(ipf_ctx* c, int j) {
                      [&] { return launch_normalize(c->storage, c->g, c->bf, c->sp, sw_on(c), c->num_sms, c->s); });
     }
     if (c->fork_piv) {
-        // the pivot-row products and the FP64 pivot-block solve (which need
-        // only v_j and the pivots) on s2 beside the operator on s, joined
-        // before the update that consumes both; the operator follows the
-        // normaliser on s as its programmatic dependent (placed while the
-        // normaliser's CTAs finish)
+        // the operator on s2 beside the pivot-row products and the FP64
+        // pivot-block solve on s (which need only v_j and the pivots), joined
+        // before the update that consumes both
         if ((e = cudaEventRecord(c->ev_fork, c->s)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(c->s2, c->ev_fork, 0)) != cudaSuccess) return e;
-        if ((e = timed_on(c, c->s2, 7, 0.0, [&] {
-                 return launch_pivot_rows(c->op, c->storage, c->bf.V, c->g.ldv, c->bf.st, c->bf.piv, c->B, c->g.k_max,
-                                          c->bf.gpiv, c->s2);
+        if ((e = timed_on(c, c->s2, 0, op_bytes(c), [&] {
+                 return launch_op_apply(c->op, c->storage, c->bf.V, c->g.ldv, c->g.k_max + 1, &c->bf.st->j, c->B,
+                                        c->bf.w, c->bf.st->status, c->s2);
              })) != cudaSuccess)
-            return e;
-        if ((e = timed_on(c, c->s2, 1, 0.0, [&] { return launch_pivot_solve(c->storage, c->g, c->bf, c->s2); })) !=
-            cudaSuccess)
             return e;
         if ((e = cudaEventRecord(c->ev_join, c->s2)) != cudaSuccess) return e;
-        if ((e = timed(c, 0, op_bytes(c), [&] {
-                 return launch_op_apply(c->op, c->storage, c->bf.V, c->g.ldv, c->g.k_max + 1, &c->bf.st->j, c->B,
-                                        c->bf.w, c->bf.st->status, c->s, true);
+        if ((e = timed(c, 7, 0.0, [&] {
+                 return launch_pivot_rows(c->op, c->storage, c->bf.V, c->g.ldv, c->bf.st, c->bf.piv, c->B, c->g.k_max,
+                                          c->bf.gpiv, c->s);
              })) != cudaSuccess)
+            return e;
+        if ((e = timed(c, 1, 0.0, [&] { return launch_pivot_solve(c->storage, c->g, c->bf, c->s); })) != cudaSuccess)
             return e;
         if ((e = cudaStreamWaitEvent(c->s, c->ev_join, 0)) != cudaSuccess) return e;
         if ((e = timed(c, 2, (double)(j + 1) * N * sv + 2.0 * N * ab + N / 8.0 + (c->defer_sketch ? 8.0 * N : 0.0),
@@ -503,7 +500,7 @@ cudaError_t one_step(ipf_ctx* c, int j) {
     }
     if ((e = timed(c, 0, op_bytes(c), [&] {
              return launch_op_apply(c->op, c->storage, c->bf.V, c->g.ldv, c->g.k_max + 1, &c->bf.st->j, c->B, c->bf.w,
-                                    c->bf.st->status, c->s, true);
+                                    c->bf.st->status, c->s);
          })) != cudaSuccess)
         return e;
     if ((e = timed(c, 1, 0.0, [&] { return launch_pivot_solve(c->storage, c->g, c->bf, c->s); })) != cudaSuccess)

@@ -363,16 +363,13 @@ float bf16_bits_to_float(unsigned short h);
 int conv_tc_operand(int kw, const std::function<float(int, int)>& F, std::vector<unsigned short>* img);
 bool conv_tc_eligible(const OpDev& op, const void* vbase, long long ldv);
 cudaError_t launch_conv_tc(const OpDev& op, const void* vbase, long long ldv, long long vcols, const int* jptr,
-                           float* w, int* err, cudaStream_t s, bool pdl = false);
+                           float* w, int* err, cudaStream_t s);
 
 // w = A v_j: vbase/ldv/vcols describe the basis (vcols columns), j read from
 // jptr (column 0 when NULL); err receives IPF_ERR_TIMEOUT if a bounded wait
-// inside the tensor-core convolution gives up (may be NULL).  pdl: the
-// tensor-core convolution is launched as a programmatic dependent of the
-// kernel before it in the stream (it waits for that grid before it reads
-// v_j or j); the other operator kernels are launched as usual.
+// inside the tensor-core convolution gives up (may be NULL)
 cudaError_t launch_op_apply(const OpDev& op, int storage, const void* vbase, long long ldv, long long vcols,
-                            const int* jptr, int B, void* w, int* err, cudaStream_t s, bool pdl = false);
+                            const int* jptr, int B, void* w, int* err, cudaStream_t s);
 // (A v_j)(p_i) for i <= j directly at the pivot rows (PSF2D and CSR); float accumulation
 cudaError_t launch_pivot_rows(const OpDev& op, int storage, const void* vbase, long long ldv, const DevState* st,
                               const int* piv, int B, int k_max, float* gout, cudaStream_t s);

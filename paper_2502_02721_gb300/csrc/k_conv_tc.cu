@@ -185,11 +185,6 @@ __device__ __forceinline__ void conv_tc_body(const CUtensorMap* vmap, const int*
     if (warp == 0) {
         // ---- TMA producer: one box of kRB = kG rows per group ----
         if (lane == 0) {
-            // launched as a programmatic dependent (the context's step): the
-            // normaliser that wrote v_j and j has completed past this point,
-            // and every other role follows this thread's copies (a no-op for
-            // an ordinary launch)
-            asm volatile("griddepcontrol.wait;" ::: "memory");
             const int z = jptr ? *jptr : 0;
             int issued = 0;
             for (int t = 0; t < NG; ++t) {
@@ -381,7 +376,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 template <int KP>
 cudaError_t launch_kp(const CUtensorMap& map, const int* jptr, float* w, int H, int W, const void* bimg, int* err,
-                      cudaStream_t s, bool pdl) {
+                      cudaStream_t s) {
     cudaError_t e = raise_smem(k_conv2d_tc<KP>, kSmemRequest);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 1;
@@ -395,17 +390,8 @@ cudaError_t launch_kp(const CUtensorMap& map, const int* jptr, float* w, int H, 
     if (S < 1) S = 1;
     const int R = (H + S - 1) / S;
     const int units = CT * ((H + R - 1) / R);
-    cudaLaunchConfig_t lc = {};
-    lc.gridDim = dim3((unsigned)units);
-    lc.blockDim = dim3(kThreads);
-    lc.dynamicSmemBytes = kSmemRequest;
-    lc.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    lc.attrs = at;
-    lc.numAttrs = pdl ? 1 : 0;
-    return cudaLaunchKernelEx(&lc, k_conv2d_tc<KP>, map, jptr, w, H, W, R, CT, (const uint4*)bimg, err);
+    k_conv2d_tc<KP><<<units, kThreads, kSmemRequest, s>>>(map, jptr, w, H, W, R, CT, (const uint4*)bimg, err);
+    return cudaGetLastError();
 }
 
 template <int KP>
@@ -456,7 +442,7 @@ bool conv_tc_eligible(const OpDev& op, const void* vbase, long long ldv) {
 }
 
 cudaError_t launch_conv_tc(const OpDev& op, const void* vbase, long long ldv, long long vcols, const int* jptr,
-                           float* w, int* err, cudaStream_t s, bool pdl) {
+                           float* w, int* err, cudaStream_t s) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     const int H = op.rows, W = op.cols;
@@ -470,8 +456,8 @@ cudaError_t launch_conv_tc(const OpDev& op, const void* vbase, long long ldv, lo
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    if (op.tc_kp == 32) return launch_kp<32>(map, jptr, w, H, W, op.psf_tc, err, s, pdl);
-    if (op.tc_kp == 16) return launch_kp<16>(map, jptr, w, H, W, op.psf_tc, err, s, pdl);
+    if (op.tc_kp == 32) return launch_kp<32>(map, jptr, w, H, W, op.psf_tc, err, s);
+    if (op.tc_kp == 16) return launch_kp<16>(map, jptr, w, H, W, op.psf_tc, err, s);
     return cudaErrorInvalidValue;
 }
 

@@ -559,8 +559,6 @@ __global__ void __launch_bounds__(256) k_normalize(Geom g, Bufs bf, SketchParams
     // placed while the update's last CTAs finish, and wait here until the
     // update has completed and its writes are visible (a no-op otherwise)
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    // and the operator of the next step may be placed as these CTAs finish
-    asm volatile("griddepcontrol.launch_dependents;");
     extern __shared__ unsigned char smem_raw[];
     constexpr bool f64 = sizeof(Acc) == 8;
     const int nacc = want_sw ? 2 : 1;

@@ -533,16 +533,15 @@ cudaError_t csr_dispatch(const OpDev& op, const T* v, long long ldv, const int* 
 
 template <class T>
 cudaError_t apply_T(const OpDev& op, const void* v, long long ldv, long long vcols, const int* jp, void* w, int B,
-                    int* err, cudaStream_t s, bool pdl) {
+                    int* err, cudaStream_t s) {
     using Acc = typename AccOf<T>::type;
     switch (op.kind) {
         case IPF_OP_PSF2D:
             if constexpr (std::is_same<T, __nv_bfloat16>::value) {
-                if (conv_tc_eligible(op, v, ldv)) return launch_conv_tc(op, v, ldv, vcols, jp, (float*)w, err, s, pdl);
+                if (conv_tc_eligible(op, v, ldv)) return launch_conv_tc(op, v, ldv, vcols, jp, (float*)w, err, s);
             }
             (void)vcols;
             (void)err;
-            (void)pdl;
             return conv_dispatch<T, Acc>(op, (const T*)v, ldv, jp, (Acc*)w, s);
         case IPF_OP_PSF2D_SEP_MOTION: return sep_dispatch<T, Acc>(op, (const T*)v, ldv, jp, (Acc*)w, s);
         case IPF_OP_CSR: return csr_dispatch<T, Acc>(op, (const T*)v, ldv, jp, (Acc*)w, B, s);
@@ -669,12 +668,12 @@ cudaError_t launch_pivot_rows(const OpDev& op, int storage, const void* vbase, l
 }
 
 cudaError_t launch_op_apply(const OpDev& op, int storage, const void* vbase, long long ldv, long long vcols,
-                            const int* jptr, int B, void* w, int* err, cudaStream_t s, bool pdl) {
+                            const int* jptr, int B, void* w, int* err, cudaStream_t s) {
     switch (storage) {
-        case IPF_STORE_F64: return apply_T<double>(op, vbase, ldv, vcols, jptr, w, B, err, s, false);
-        case IPF_STORE_F32: return apply_T<float>(op, vbase, ldv, vcols, jptr, w, B, err, s, false);
-        case IPF_STORE_BF16: return apply_T<__nv_bfloat16>(op, vbase, ldv, vcols, jptr, w, B, err, s, pdl);
-        case IPF_STORE_F16: return apply_T<__half>(op, vbase, ldv, vcols, jptr, w, B, err, s, false);
+        case IPF_STORE_F64: return apply_T<double>(op, vbase, ldv, vcols, jptr, w, B, err, s);
+        case IPF_STORE_F32: return apply_T<float>(op, vbase, ldv, vcols, jptr, w, B, err, s);
+        case IPF_STORE_BF16: return apply_T<__nv_bfloat16>(op, vbase, ldv, vcols, jptr, w, B, err, s);
+        case IPF_STORE_F16: return apply_T<__half>(op, vbase, ldv, vcols, jptr, w, B, err, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -687,7 +686,7 @@ cudaError_t launch_op_apply_f32_plain(const OpDev& op, const float* v, float* w,
     const long long m = csr ? (long long)op.rows : n;
     if (nrhs == 1 || !csr) {
         for (int r = 0; r < nrhs; ++r) {
-            cudaError_t e = apply_T<float>(op, v + (size_t)r * n, 0, 1, nullptr, w + (size_t)r * m, 1, nullptr, s, false);
+            cudaError_t e = apply_T<float>(op, v + (size_t)r * n, 0, 1, nullptr, w + (size_t)r * m, 1, nullptr, s);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -700,7 +699,7 @@ cudaError_t launch_op_apply_f32_plain(const OpDev& op, const float* v, float* w,
     float* wi = tmp + (size_t)n * nrhs;
     const int blocks = 1024;
     k_interleave<<<blocks, 256, 0, s>>>(v, vi, n, nrhs, 0);
-    e = apply_T<float>(op, vi, 0, 1, nullptr, wi, nrhs, nullptr, s, false);
+    e = apply_T<float>(op, vi, 0, 1, nullptr, wi, nrhs, nullptr, s);
     if (e == cudaSuccess) k_interleave<<<blocks, 256, 0, s>>>(wi, w, m, nrhs, 1);
     cudaError_t e2 = cudaFreeAsync(tmp, s);
     return e != cudaSuccess ? e : (e2 != cudaSuccess ? e2 : cudaGetLastError());
