@@ -141,9 +141,7 @@ typedef void (*ipf_free_fn)(void* ptr, void* user);
 
 typedef struct ipf_config {
     int k_max;                   /* maximum Hessenberg steps, 1..480 (basis has k_max+1
-                                    vectors; the FP64 pivot block is staged in shared
-                                    memory up to 224, read from L2 beyond); with the
-                                    Gaussian sketch 1..247                                 */
+                                    vectors); with the Gaussian sketch 1..247              */
     int m_s;                     /* sketch rows (l in Sec. 2); m_s >= zeta                  */
     int zeta;                    /* nonzeros per sketch column, 1..16                       */
     unsigned long long seed;     /* sketch seed (SplitMix64 state)                          */
@@ -180,6 +178,13 @@ typedef struct ipf_config {
     int conv_fma;                /* PSF2D with BF16 storage: 0 (default) runs the product on
                                     the tensor cores when the PSF pads to 15x15 or 31x31 and
                                     cols % 8 == 0; 1 keeps the FP32 FMA convolution         */
+    int pivot_fwd;               /* the FP64 pivot-block solve h = L_p^{-1} u(p) of each step:
+                                    0 (default) in inverse form: each step appends the row
+                                    of L_p^{-1} that matches the new row of L_p and forms h
+                                    as a product with independent rows, switching to forward
+                                    substitution for the rest of the solve if a row of the
+                                    inverse exceeds 2^20 in magnitude; 1 forward
+                                    substitution throughout (one CTA)                     */
     void* stream;                /* cudaStream_t of the caller (NULL: legacy default)      */
     ipf_alloc_fn alloc;          /* optional device allocator (e.g. a framework's pool)    */
     ipf_free_fn free;
@@ -255,7 +260,8 @@ ipf_status ipf_solve(ipf_ctx* ctx, int k, const double* lambdas, int nl,
  * failure of the solve is reported by the next ipf_sync.                  */
 
 /* Kernel timings of a context created with config.profile = 1: for each
- * kind (0 operator, 1 pivot-block solve, 2 update+argmax or V_j h,
+ * kind (0 operator, 1 pivot-block solve (two launches: the row of L_p^{-1},
+ * then h), 2 update+argmax or V_j h,
  * 3 normalise (+ sketch unless deferred), 4 initialisation, 5 projected-solve
  * QR, 6 per-lambda solve + x = V_k y, 7 operator at the pivot rows,
  * 8 u = A v_j - V_j h with argmax, 9 the Gaussian sketch's [S V_{k+1} | S b],

@@ -53,7 +53,7 @@ class ipf_config(C.Structure):
                 ("storage", C.c_int), ("penalty", C.c_int), ("zform", C.c_int), ("nrhs", C.c_int),
                 ("use_graphs", C.c_int), ("profile", C.c_int), ("overlap", C.c_int), ("method", C.c_int), ("sketch", C.c_int),
                 ("pivot_sample", C.c_int),
-                ("conv_fma", C.c_int),
+                ("conv_fma", C.c_int), ("pivot_fwd", C.c_int),
                 ("stream", C.c_void_p),
                 ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", C.c_void_p)]
 

@@ -291,6 +291,8 @@ struct ipf_ctx {
     int j_host = 0;                    // Hessenberg steps enqueued
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph_run = nullptr;    // kGraphSteps consecutive steps in one graph
+    cudaGraphExec_t gexec_run = nullptr;
     ipf_status sticky = IPF_OK;
     std::string err;
     void* solve_ws = nullptr;
@@ -445,12 +447,16 @@ cudaError_t one_step(ipf_ctx* c, int j) {
         // h first (products at the pivot rows + FP64 pivot-block solve, small),
         // then the operator on s2 overlapped with V_j h on s, joined before the
         // combine
+        // the new rows of L_p and L_p^{-1} (pivots and basis only), the
+        // products at the pivot rows, then h
+        if ((e = timed(c, 1, 0.0, [&] { return launch_pivot_minv(c->storage, c->g, c->bf, c->s); })) != cudaSuccess)
+            return e;
         if ((e = timed(c, 7, 0.0, [&] {
                  return launch_pivot_rows(c->op, c->storage, c->bf.V, c->g.ldv, c->bf.st, c->bf.piv, c->B, c->g.k_max,
                                           c->bf.gpiv, c->s);
              })) != cudaSuccess)
             return e;
-        if ((e = timed(c, 1, 0.0, [&] { return launch_pivot_solve(c->storage, c->g, c->bf, c->s); })) != cudaSuccess)
+        if ((e = timed(c, 1, 0.0, [&] { return launch_pivot_apply(c->storage, c->g, c->bf, c->s); })) != cudaSuccess)
             return e;
         if ((e = cudaEventRecord(c->ev_fork, c->s)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(c->s2, c->ev_fork, 0)) != cudaSuccess) return e;
@@ -483,12 +489,16 @@ cudaError_t one_step(ipf_ctx* c, int j) {
              })) != cudaSuccess)
             return e;
         if ((e = cudaEventRecord(c->ev_join, c->s2)) != cudaSuccess) return e;
+        // the new rows of L_p and L_p^{-1} (pivots and basis only), the
+        // products at the pivot rows, then h
+        if ((e = timed(c, 1, 0.0, [&] { return launch_pivot_minv(c->storage, c->g, c->bf, c->s); })) != cudaSuccess)
+            return e;
         if ((e = timed(c, 7, 0.0, [&] {
                  return launch_pivot_rows(c->op, c->storage, c->bf.V, c->g.ldv, c->bf.st, c->bf.piv, c->B, c->g.k_max,
                                           c->bf.gpiv, c->s);
              })) != cudaSuccess)
             return e;
-        if ((e = timed(c, 1, 0.0, [&] { return launch_pivot_solve(c->storage, c->g, c->bf, c->s); })) != cudaSuccess)
+        if ((e = timed(c, 1, 0.0, [&] { return launch_pivot_apply(c->storage, c->g, c->bf, c->s); })) != cudaSuccess)
             return e;
         if ((e = cudaStreamWaitEvent(c->s, c->ev_join, 0)) != cudaSuccess) return e;
         if ((e = timed(c, 2, (double)(j + 1) * N * sv + 2.0 * N * ab + N / 8.0 + (c->defer_sketch ? 8.0 * N : 0.0),
@@ -534,10 +544,10 @@ cudaError_t init_solve(ipf_ctx* c, const float* bdev) {
         if ((e = cudaMemsetAsync(c->bf2.accSW, 0, B * K1 * g2.m_s * sizeof(long long), c->s)) != cudaSuccess)
             return e;
         if ((e = cudaMemsetAsync(c->bf2.colE, 0, B * K1 * sizeof(int), c->s)) != cudaSuccess) return e;
-        if ((e = launch_reset_state(c->bf2.st, c->s)) != cudaSuccess) return e;
+        if ((e = launch_reset_state(c->bf2.st, c->cfg.pivot_fwd != 0, c->s)) != cudaSuccess) return e;
     }
     e = timed(c, 4, 0.0, [&] {
-        cudaError_t ee = launch_reset_state(c->bf.st, c->s);
+        cudaError_t ee = launch_reset_state(c->bf.st, c->cfg.pivot_fwd != 0, c->s);
         if (ee != cudaSuccess) return ee;
         if ((ee = launch_load_rhs(c->storage, bdev, g, c->bf, c->s)) != cudaSuccess) return ee;
         if ((ee = launch_update(c->storage, g, c->bf, c->sp, c->num_sms, c->s)) != cudaSuccess) return ee;
@@ -597,7 +607,7 @@ size_t ipf_footprint(const ipf_operator* op, const ipf_config* cfg) {
     auto basis = [&](long long np) -> size_t {
         const size_t l = ldv_for(np * B);
         size_t b = K1 * l * sb + l * acc + l / 8 + 4096;
-        b += B * K1 * (2 * sizeof(int) + sizeof(double) * cfg->k_max + sizeof(double) * K1) + K1 * B * acc;
+        b += B * K1 * (2 * sizeof(int) + sizeof(double) * cfg->k_max + 2 * sizeof(double) * K1) + K1 * B * acc;
         return b + 2 * (size_t)B * K1 * cfg->m_s * 8 + l * 8;
     };
     const bool gh = cfg->method == IPF_METHOD_SLSLU;
@@ -642,7 +652,8 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     if (cfg.zform != IPF_Z_DIRECT && cfg.zform != IPF_Z_HESSENBERG && cfg.zform != IPF_Z_AUTO) return IPF_ERR_ARG;
     const bool z_ok = cfg.storage != IPF_STORE_F64;
     if (cfg.zform == IPF_Z_DIRECT && !z_ok) return IPF_ERR_UNSUPPORTED;
-    if (cfg.k_max > kMaxK) return IPF_ERR_UNSUPPORTED;    // the pivot solve's rows (512) in registers
+    if (cfg.k_max > kMaxK) return IPF_ERR_UNSUPPORTED;    // forward substitution's rows (512) in registers
+    if (cfg.pivot_fwd != 0 && cfg.pivot_fwd != 1) return IPF_ERR_ARG;
     // the Gaussian contraction's B tile: V_{k+1} rounded up, plus 8 rows of b, at most 256 rows
     if (gauss && (cfg.k_max + 1 + 8 + 15) / 16 * 16 > 256) return IPF_ERR_UNSUPPORTED;
     if (b_mem != IPF_MEM_HOST && b_mem != IPF_MEM_DEVICE) return IPF_ERR_ARG;
@@ -727,6 +738,7 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
         AK(c->al.get((void**)&bf.piv, B * K1 * sizeof(int)));
         AK(c->al.get((void**)&bf.H, B * K1 * cfg.k_max * sizeof(double)));
         AK(c->al.get(&bf.LpT, B * K1 * K1 * sizeof(double)));
+        AK(c->al.get((void**)&bf.Minv, B * K1 * K1 * sizeof(double)));
         AK(c->al.get(&bf.coef, K1 * B * accb));
         AK(c->al.get((void**)&bf.ispiv, (g.ldv / 32 + 1) * sizeof(unsigned)));
         AK(c->al.get((void**)&bf.accSV, B * K1 * cfg.m_s * sizeof(long long)));
@@ -753,6 +765,7 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
         AK(cudaMemsetAsync(bf.V, 0, K1 * g.ldv * sb, c->s));
         AK(cudaMemsetAsync(bf.w, 0, g.ldv * accb, c->s));
         AK(cudaMemsetAsync(bf.LpT, 0, B * K1 * K1 * sizeof(double), c->s));
+        AK(cudaMemsetAsync(bf.Minv, 0, B * K1 * K1 * sizeof(double), c->s));
         AK(cudaMemsetAsync(bf.piv, 0, B * K1 * sizeof(int), c->s));
         AK(cudaMemsetAsync(bf.coef, 0, K1 * B * accb, c->s));
 #undef AK
@@ -851,6 +864,10 @@ ipf_status ipf_profile_read(ipf_ctx* c, double* ms, long long* launches, double*
     return IPF_OK;
 }
 
+// steps per graph launch once the one-step graph exists: one launch for
+// kGraphSteps steps saves the gap between graph launches on the device
+constexpr int kGraphSteps = 8;
+
 ipf_status ipf_step(ipf_ctx* c, int nsteps, int* k_enqueued) {
     if (!c) return IPF_ERR_ARG;
     if (c->sticky != IPF_OK) return c->sticky;
@@ -877,12 +894,32 @@ ipf_status ipf_step(ipf_ctx* c, int nsteps, int* k_enqueued) {
                 return cuda_fail(c, "instantiate", e);
         }
     }
-    for (; t < todo; ++t) {
+    if (c->gexec && !c->gexec_run && todo - t >= kGraphSteps) {
+        // the same step kGraphSteps times in one capture (every kernel reads
+        // j from device memory, so the steps differ only in their data)
+        if ((e = cudaStreamBeginCapture(c->s, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+            return cuda_fail(c, "capture", e);
+        cudaError_t e1 = cudaSuccess;
+        for (int q = 0; q < kGraphSteps && e1 == cudaSuccess; ++q) e1 = one_step(c, 0);
+        cudaError_t e2 = cudaStreamEndCapture(c->s, &c->graph_run);
+        if (e1 != cudaSuccess) return cuda_fail(c, "capture steps", e1);
+        if (e2 != cudaSuccess) return cuda_fail(c, "end capture", e2);
+        if ((e = cudaGraphInstantiate(&c->gexec_run, c->graph_run, 0)) != cudaSuccess)
+            return cuda_fail(c, "instantiate", e);
+    }
+    while (t < todo) {
+        if (c->gexec_run && todo - t >= kGraphSteps) {
+            if ((e = cudaGraphLaunch(c->gexec_run, c->s)) != cudaSuccess) return cuda_fail(c, "graph launch", e);
+            t += kGraphSteps;
+            c->j_host += kGraphSteps;
+            continue;
+        }
         if (c->gexec && !c->cfg.profile) {
             if ((e = cudaGraphLaunch(c->gexec, c->s)) != cudaSuccess) return cuda_fail(c, "graph launch", e);
         } else {
             if ((e = one_step(c, c->j_host)) != cudaSuccess) return cuda_fail(c, "step", e);
         }
+        ++t;
         ++c->j_host;
     }
     if ((e = leave(c)) != cudaSuccess) return cuda_fail(c, "order", e);
@@ -1180,6 +1217,8 @@ void ipf_destroy(ipf_ctx* c) {
     for (auto ev : c->spare) cudaEventDestroy(ev);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->graph) cudaGraphDestroy(c->graph);
+    if (c->gexec_run) cudaGraphExecDestroy(c->gexec_run);
+    if (c->graph_run) cudaGraphDestroy(c->graph_run);
     c->al.release();
     if (c->ev) cudaEventDestroy(c->ev);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);

@@ -211,6 +211,9 @@ struct DevState {
     double wmax[kMaxRhs];          // sampled pivoting: max |w| over the candidates of this step
     int sk_pending;                // deferred sketch: column of V still to be sketched, or -1
     unsigned sk_ctr;               // last-CTA ticket for the deferred sketch kernel
+    int fwd[kMaxRhs];              // per RHS: 1 = pivot block by forward substitution (chosen
+                                   // at creation, or set when a row of L_p^{-1} grew past
+                                   // kMinvGrowth), 0 = by the product with L_p^{-1}
 };
 
 // everything a kernel needs about the context, passed by value
@@ -235,6 +238,7 @@ struct Bufs {
     int* piv;                      // [B][k_max+1]
     double* H;                     // [B][(k_max+1)*k_max], column-major
     void* LpT;                     // [B][lp_stride] FP64, L_p packed by rows (strictly lower)
+    double* Minv = nullptr;        // [B][lp_stride] FP64, L_p^{-1} packed the same way
     void* coef;                    // [(k_max+1)*B] Acc, h for the update
     unsigned* ispiv;               // bitmap over N elements
     long long* accSV;              // [B][k_max+1][m_s] fixed-point S V
@@ -293,8 +297,7 @@ struct OpDev {
 // its status is IPF_OK and its step counter is below k_target.
 // ---------------------------------------------------------------------------
 constexpr int kMaxSlots = 64;
-constexpr int kPivSmemK = 224;                 // k_max up to which the FP64 pivot block is staged in shared memory
-constexpr int kMaxK = 480;                     // k_max (the pivot solve's registers hold 512 rows)
+constexpr int kMaxK = 480;                     // k_max (forward substitution's registers hold 512 rows)
 constexpr int kSmallMaxK = 512;                // the projected solve's per-column shared arrays
 static_assert(kMaxK <= kSmallMaxK, "projected solve arrays");
 constexpr int kBatchUpdTile = kFoldEvery;      // update tile: the split counters' exact range
@@ -376,7 +379,8 @@ cudaError_t launch_pivot_rows(const OpDev& op, int storage, const void* vbase, l
 cudaError_t launch_op_apply_f32_plain(const OpDev& op, const float* v, float* w, int nrhs,
                                       cudaStream_t s);
 // k_hess.cu
-cudaError_t launch_reset_state(DevState* st, cudaStream_t s);
+// fwd: the pivot block is solved by forward substitution from the first step
+cudaError_t launch_reset_state(DevState* st, bool fwd, cudaStream_t s);
 // Gaussian sketch (gauss.cu).  A context's S (launch_gauss_fill_ctx,
 // gauss_s_bytes): for BF16 / FP16 storage tiled in units of 16 rows x 64
 // elements (unit (r / 16, i / 64) at ((r / 16) ceil(n / 64) + i / 64) 1024
@@ -408,6 +412,12 @@ int gauss_variant(int storage, const void* S, int m, long long n, const void* V,
 cudaError_t launch_sample_pivot(int storage, const Geom& g, const Bufs& bf, unsigned long long seed, int size,
                                 cudaStream_t s);
 cudaError_t launch_load_rhs(int storage, const float* b, const Geom& g, const Bufs& bf, cudaStream_t s);
+// the FP64 pivot-block solve h = L_p^{-1} u(p) in two launches: the new row
+// of L_p and of L_p^{-1} (needs only the pivots and the basis), then the
+// product with u(p) (or forward substitution where DevState::fwd is set);
+// launch_pivot_solve issues both
+cudaError_t launch_pivot_minv(int storage, const Geom& g, const Bufs& bf, cudaStream_t s);
+cudaError_t launch_pivot_apply(int storage, const Geom& g, const Bufs& bf, cudaStream_t s);
 cudaError_t launch_pivot_solve(int storage, const Geom& g, const Bufs& bf, cudaStream_t s);
 cudaError_t launch_update(int storage, const Geom& g, const Bufs& bf, const SketchParams& sp, int num_sms,
                           cudaStream_t s);
@@ -431,7 +441,7 @@ cudaError_t launch_sketch_finish(const long long* acc, int m, long long n, int z
                                  double* y, cudaStream_t s);
 // batched step (k_hess.cu, k_ops.cu, k_conv_tc.cu): one launch per phase for
 // the slots of one float storage type
-// one CTA per entry of list (its slot field)
+// per entry of list (its slot field): the row of L_p^{-1}, then the product
 cudaError_t launch_batch_pivot_solve(int storage, const SlotDesc* slots, const TileRef* list, int nslots, int k_max,
                                      cudaStream_t s);
 cudaError_t launch_batch_update(int storage, const SlotDesc* slots, const TileRef* tiles, int ntiles, int k_max,

@@ -2,10 +2,11 @@
 // Hessenberg_s; the loop of Algorithm 1 in the square form, applying A where
 // the algorithm, written for the generalized process, applies A^T):
 //
-//   k_pivot_solve   append row p_j of L_p; h = L_p^{-1} u(p_1..p_j) in FP64
-//                   (the sequential elimination H(i,j) = u(p_i),
-//                   u -= H(i,j) v_i is this forward substitution because
-//                   v_c(p_i) = 0 for c > i and v_i(p_i) = 1)
+//   k_pivot_minv    append row p_j of L_p and the matching row of L_p^{-1}
+//   k_pivot_apply   h = L_p^{-1} u(p_1..p_j) in FP64 (the sequential
+//                   elimination H(i,j) = u(p_i), u -= H(i,j) v_i is this
+//                   triangular solve because v_c(p_i) = 0 for c > i and
+//                   v_i(p_i) = 1)
 //   k_update        u -= V_j h, u(p_i) = 0, argmax |u| over the rest
 //   k_normalize     H(j+1,j) = u(p_{j+1}); v_{j+1} = u / H(j+1,j) rounded to
 //                   the storage type; S v_{j+1} (and S of the unrounded
@@ -36,115 +37,76 @@ __global__ void k_load_rhs(const float* __restrict__ b, Acc* __restrict__ w, lon
 }
 
 // ------------------------------------------------------------------------
-// pivot-block forward substitution, one CTA per RHS.  L_p is kept packed
+// The FP64 pivot-block solve h = L_p^{-1} u(p_1..p_{j+1}) of step j.  L_p is
+// unit lower triangular, L(i, c) = v_c(p_i) for c < i (the stored basis
+// values at the pivot rows), so the sequential elimination H(i,j) = u(p_i),
+// u -= H(i,j) v_i of Algorithm 1 is this triangular solve (v_c(p_i) = 0 for
+// c > i and v_i(p_i) = 1).  Both L_p and M = L_p^{-1} are kept packed
 // row-major, strictly lower (row i, entries c < i, at offset i(i-1)/2; the
-// unit diagonal is implicit), so each step appends one contiguous row and
-// the whole block is one flat copy into shared memory.  Warp 0 then solves
-// L_p h = u(p) in FP64 with lane l holding rows l, l+32, ..., l+224 in
-// registers: x_c is broadcast by a shuffle and every lane updates its rows
-// below c, with no block-wide barrier per column.  j < 128 NG (NG row
-// groups of 32 per warp).  SM: L_p staged in shared memory (k_max up to
-// kPivSmemK); otherwise the rows are read from L_p in global memory (L2:
-// k_max^2 / 2 doubles, 0.9 MB at k_max = 480).
+// unit diagonal is implicit), each step appending one row.
+//
+// Inverse form (default).  The block inverse of [L 0; l^T 1] is
+// [M 0; -l^T M 1], so appending row j of L_p (l = L(j, 0..j-1)) appends
+//     M(j, c) = -( l_c + sum_{c < i < j} l_i M(i, c) ),   c < j,
+// which needs only the pivots and the stored basis (k_pivot_minv: a warp
+// per column, lanes over the rows, a fixed shuffle tree), and then h(i) = u(p_i) + sum_{c < i} M(i, c) u(p_c), i <= j, is a
+// product with independent rows (k_pivot_apply: a warp per row, lanes over
+// c, a fixed shuffle tree).  Forward substitution is a chain of j dependent
+// columns on one SM; GB300's FP64 rate per SM (about two FMAs per clock)
+// makes that chain the longest part of a step at large j, where the inverse
+// form spreads the same j^2 FMAs over many SMs.
+// Growth: with max-|.| pivots |L| <= 1; a row of M larger than kMinvGrowth
+// in magnitude (or not finite) sets DevState::fwd and the RHS continues by
+// forward substitution (k_pivot_apply runs pivot_fwd_body in one CTA); the
+// configuration can also ask for forward substitution throughout.
+//
+// Forward substitution (pivot_fwd_body): warp 0..3 (one per SM partition)
+// hold the rows in registers, four row groups of 32 per warp (j < 512);
+// column blocks of 32 are solved by the warp holding their rows and applied
+// by all four, each row's updates in column order; L_p is read from global
+// memory (L2).
 // ------------------------------------------------------------------------
-// doubles per RHS for the packed L_p, rounded up to whole 16-byte chunks
+// doubles per RHS for the packed L_p (and M), rounded up to whole 16-byte chunks
 __host__ __device__ constexpr size_t lp_stride(int k_max) { return ((size_t)(k_max + 1) * k_max / 2 + 2) & ~(size_t)1; }
 
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+constexpr double kMinvGrowth = 1048576.0;      // 2^20
+constexpr int kMinvCols = 8;                   // columns of M per CTA of k_pivot_minv (a warp each)
+constexpr int kApplyRows = 8;                  // rows of h per CTA of k_pivot_apply
+constexpr int kFwdNG = 4;                      // row groups of 32 per warp in pivot_fwd_body
 
-template <class T, class Acc, int NG, bool SM>
-__device__ __forceinline__ void pivot_solve_body(const Geom& g, const Bufs& bf, int r) {
+template <class T, class Acc>
+__device__ __forceinline__ void pivot_fwd_body(const Geom& g, const Bufs& bf, int r) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long s_bar;
-    __shared__ int s_timeout;
     DevState* st = bf.st;
     if (st->status[r] != IPF_OK) return;
     const int j = st->j;
-    if (j < 0 || j >= g.k_max || j >= 128 * NG) return;
+    if (j < 0 || j >= g.k_max || j >= 128 * kFwdNG) return;
     const int K1 = g.k_max + 1;
     const int B = g.B;
     const T* V = (const T*)bf.V;
     const Acc* w = (const Acc*)bf.w;
     double* Lp = (double*)bf.LpT + (size_t)r * lp_stride(g.k_max);
     const int* piv = bf.piv + (size_t)r * K1;
-    double* s_L = (double*)smem_raw;                      // rows 1..j, packed (16-byte aligned; SM only)
-    double* s_g = SM ? s_L + lp_stride(g.k_max) : (double*)smem_raw;
+    double* s_g = (double*)smem_raw;                      // u(p), K1 rounded to even, then x_c
     const size_t rowj = (size_t)j * (j - 1) / 2;          // doubles in rows 1..j-1
-    const unsigned bytes = (unsigned)(((rowj + 1) & ~(size_t)1) * sizeof(double));   // whole 16-byte chunks
-    if (threadIdx.x == 0) {
-        s_timeout = 0;
-        if (SM && bytes) {
-            // one bulk copy of the stored rows into shared memory, completion on an mbarrier
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar)));
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&s_bar)), "r"(bytes)
-                         : "memory");
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    smem_u32(s_L)),
-                "l"(Lp), "r"(bytes), "r"(smem_u32(&s_bar))
-                : "memory");
-        }
-    }
-    // meanwhile: row j (exact copies of the stored values) and u at the pivot rows
+    // row j (exact copies of the stored values) and u at the pivot rows
     const size_t pj = (size_t)piv[j] * B + r;
-    for (int c = threadIdx.x; c < j; c += blockDim.x) {
-        const double val = (double)to_acc(V[(size_t)c * g.ldv + pj]);
-        Lp[rowj + c] = val;
-    }
+    for (int c = threadIdx.x; c < j; c += blockDim.x) Lp[rowj + c] = (double)to_acc(V[(size_t)c * g.ldv + pj]);
     if (bf.gpiv) {
         for (int i = threadIdx.x; i <= j; i += blockDim.x) s_g[i] = (double)bf.gpiv[(size_t)r * K1 + i];
     } else {
         for (int i = threadIdx.x; i <= j; i += blockDim.x) s_g[i] = (double)w[(size_t)piv[i] * B + r];
     }
-    if (SM && threadIdx.x == 0 && bytes) {
-        // bounded wait on the copy: gives up after ~2^22 polls and reports a timeout
-        unsigned done = 0;
-        for (long long it = 0; it < (1ll << 22) && !done; ++it) {
-            asm volatile(
-                "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
-                : "=r"(done)
-                : "r"(smem_u32(&s_bar))
-                : "memory");
-        }
-        if (!done) {
-            s_timeout = 1;
-            // the copy is still ours: wait for it once more (bounded) before the CTA may exit
-            for (long long it = 0; it < (1ll << 22) && !done; ++it) {
-                asm volatile(
-                    "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0; selp.u32 %0, 1, 0, p; }"
-                    : "=r"(done)
-                    : "r"(smem_u32(&s_bar))
-                    : "memory");
-            }
-        }
-    }
     __syncthreads();
-    // row j goes to shared memory after the bulk copy has landed (it is not part of it)
-    if (SM)
-        for (int c = threadIdx.x; c < j; c += blockDim.x) s_L[rowj + c] = Lp[rowj + c];
-    __syncthreads();
-    const double* Lr = SM ? s_L : Lp;                      // the rows of L_p, where this CTA reads them
-    if (s_timeout) {
-        if (threadIdx.x == 0) st->status[r] = IPF_ERR_TIMEOUT;
-        return;
-    }
-    // four warps (one per SM partition, so four FP64 pipes): warp w holds the
-    // row groups w and w + 4 (rows 32q + lane) in registers.  Column block cb
-    // (columns 32cb .. 32cb + 31): the warp holding row group cb solves its
-    // diagonal block alone (x_c by a shuffle, no barrier), publishes the 32
-    // final values through shared memory, one 128-thread named barrier
-    // orders them, and every warp applies the block's columns to its rows
-    // below.  Each row still takes its updates in column order (blocks in
-    // order, columns in order within a block), one barrier per 32 columns.
     if (threadIdx.x >= 128) return;
+    const double* Lr = Lp;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int qmax = j >> 5;                               // last row group holding a row <= j
     double* s_x = s_g + ((j + 2) & ~1);                    // x_c per column, after g
-    double x[NG];
-    int off[NG];
+    double x[kFwdNG];
+    int off[kFwdNG];
 #pragma unroll
-    for (int h = 0; h < NG; ++h) {
+    for (int h = 0; h < kFwdNG; ++h) {
         const int i = (warp + 4 * h) * 32 + lane;
         x[h] = (i <= j) ? s_g[i] : 0.0;
         off[h] = i * (i - 1) / 2;
@@ -157,7 +119,7 @@ __device__ __forceinline__ void pivot_solve_body(const Geom& g, const Bufs& bf, 
             double xv = x[0];
             int offr = off[0];
 #pragma unroll
-            for (int h = 1; h < NG; ++h)
+            for (int h = 1; h < kFwdNG; ++h)
                 if (h == oh) { xv = x[h]; offr = off[h]; }
             const bool row_ok = c0 + lane <= j;
 #pragma unroll 1
@@ -166,15 +128,15 @@ __device__ __forceinline__ void pivot_solve_body(const Geom& g, const Bufs& bf, 
                 if (row_ok && lane > cc) xv = fma(-Lr[offr + c0 + cc], xc, xv);
             }
 #pragma unroll
-            for (int h = 0; h < NG; ++h)
+            for (int h = 0; h < kFwdNG; ++h)
                 if (h == oh) x[h] = xv;
             if (c0 + lane < j) s_x[c0 + lane] = xv;
         }
         asm volatile("bar.sync 1, 128;" ::: "memory");
 #pragma unroll
-        for (int h = 0; h < NG; ++h) {
+        for (int h = 0; h < kFwdNG; ++h) {
             const int q = warp + 4 * h;
-            // rows i > c with i <= j only: s_L holds rows 1..j and nothing beyond
+            // rows i > c with i <= j only: L_p holds rows 1..j and nothing beyond
             if (q > cb && q <= qmax && q * 32 + lane <= j) {
                 double xv = x[h];
 #pragma unroll 4
@@ -186,7 +148,7 @@ __device__ __forceinline__ void pivot_solve_body(const Geom& g, const Bufs& bf, 
     double* Hc = bf.H + (size_t)r * K1 * g.k_max + (size_t)K1 * j;
     Acc* coef = (Acc*)bf.coef;
 #pragma unroll
-    for (int h = 0; h < NG; ++h) {
+    for (int h = 0; h < kFwdNG; ++h) {
         const int i = (warp + 4 * h) * 32 + lane;
         if (i <= j) {
             Hc[i] = x[h];
@@ -195,9 +157,105 @@ __device__ __forceinline__ void pivot_solve_body(const Geom& g, const Bufs& bf, 
     }
 }
 
-template <class T, class Acc, int NG, bool SM>
-__global__ void __launch_bounds__(256) k_pivot_solve(Geom g, Bufs bf) {
-    pivot_solve_body<T, Acc, NG, SM>(g, bf, blockIdx.x);
+// the dynamic shared memory of k_pivot_apply (pivot_fwd_body's u(p) and x_c)
+__host__ __device__ constexpr size_t pivot_apply_smem(int k_max) {
+    return (size_t)(((k_max + 2) & ~1) + k_max + 2) * sizeof(double);
+}
+
+// row j of L_p and of M = L_p^{-1}, columns 8 cb .. 8 cb + 7 (256 threads, a
+// warp per column, lanes over the rows i = c + 1 + lane, c + 33 + lane, ...
+// (at most (j - 1) / 32 + 1 dependent FMAs per lane), a fixed shuffle tree)
+template <class T>
+__device__ __forceinline__ void pivot_minv_body(const Geom& g, const Bufs& bf, int r, int cb) {
+    __shared__ double s_l[kMaxK];
+    DevState* st = bf.st;
+    if (st->status[r] != IPF_OK) return;
+    const int j = st->j;
+    if (j < 1 || j >= g.k_max) return;
+    const int c0 = cb * kMinvCols;
+    if (c0 >= j) return;
+    const int K1 = g.k_max + 1;
+    const T* V = (const T*)bf.V;
+    const size_t ls = lp_stride(g.k_max);
+    double* Lp = (double*)bf.LpT + (size_t)r * ls;
+    double* M = bf.Minv + (size_t)r * ls;
+    const size_t rowj = (size_t)j * (j - 1) / 2;
+    // l: the stored values at the pivot row p_j (exact copies) of the columns
+    // this CTA reads (c0 .. j - 1); the first column block also appends all
+    // of them to L_p (read by forward substitution)
+    const size_t pj = (size_t)bf.piv[(size_t)r * K1 + j] * g.B + r;
+    for (int c = (cb == 0 ? 0 : c0) + threadIdx.x; c < j; c += blockDim.x) {
+        const double v = (double)to_acc(V[(size_t)c * g.ldv + pj]);
+        s_l[c] = v;
+        if (cb == 0) Lp[rowj + c] = v;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = c0 + warp;
+    if (c >= j) return;
+    double acc = 0.0;
+#pragma unroll 4
+    for (int i = c + 1 + lane; i < j; i += 32) acc = fma(s_l[i], M[(size_t)i * (i - 1) / 2 + c], acc);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) {
+        const double m = -(s_l[c] + acc);
+        M[rowj + c] = m;
+        if (!(fabs(m) <= kMinvGrowth)) st->fwd[r] = 1;
+    }
+}
+
+// h(i) = u(p_i) + sum_{c < i} M(i, c) u(p_c) for the rows i = 8 rb .. 8 rb + 7
+// (<= j), a warp per row; writes column j of H and the update's coefficients
+template <class T, class Acc>
+__device__ __forceinline__ void pivot_apply_body(const Geom& g, const Bufs& bf, int r, int rb) {
+    __shared__ double s_u[kMaxK + 1];
+    const DevState* st = bf.st;
+    if (st->status[r] != IPF_OK) return;
+    const int j = st->j;
+    if (j < 0 || j >= g.k_max) return;
+    const int i0 = rb * kApplyRows;
+    if (i0 > j) return;
+    const int K1 = g.k_max + 1;
+    const int* piv = bf.piv + (size_t)r * K1;
+    const int cmax = min(j, i0 + kApplyRows - 1);        // the entries of u(p) these rows read
+    if (bf.gpiv) {
+        for (int c = threadIdx.x; c <= cmax; c += blockDim.x) s_u[c] = (double)bf.gpiv[(size_t)r * K1 + c];
+    } else {
+        const Acc* w = (const Acc*)bf.w;
+        for (int c = threadIdx.x; c <= cmax; c += blockDim.x) s_u[c] = (double)w[(size_t)piv[c] * g.B + r];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = i0 + warp;
+    if (i > j) return;
+    const double* Mi = bf.Minv + (size_t)r * lp_stride(g.k_max) + (size_t)i * (i - 1) / 2;
+    double acc = 0.0;
+    for (int c = lane; c < i; c += 32) acc = fma(Mi[c], s_u[c], acc);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) {
+        const double x = s_u[i] + acc;
+        bf.H[(size_t)r * K1 * g.k_max + (size_t)K1 * j + i] = x;
+        ((Acc*)bf.coef)[(size_t)i * g.B + r] = (Acc)x;
+    }
+}
+
+// grid (column blocks, RHS)
+template <class T>
+__global__ void __launch_bounds__(256) k_pivot_minv(Geom g, Bufs bf) {
+    pivot_minv_body<T>(g, bf, blockIdx.y, blockIdx.x);
+}
+
+// grid (row blocks, RHS); dynamic shared memory pivot_apply_smem(k_max)
+template <class T, class Acc>
+__global__ void __launch_bounds__(256) k_pivot_apply(Geom g, Bufs bf) {
+    const int r = blockIdx.y;
+    if (bf.st->fwd[r]) {
+        if (blockIdx.x == 0) pivot_fwd_body<T, Acc>(g, bf, r);
+        return;
+    }
+    pivot_apply_body<T, Acc>(g, bf, r, blockIdx.x);
 }
 
 // ------------------------------------------------------------------------
@@ -1095,9 +1153,10 @@ __global__ void k_sketch_table(SketchParams sp, long long n, unsigned long long*
 }
 
 // fresh DevState for a new solve (j = -1, all RHS OK, keys cleared)
-__global__ void k_reset_state(DevState* st) {
+__global__ void k_reset_state(DevState* st, int fwd) {
     const int t = threadIdx.x;
     if (t < kMaxRhs) {
+        st->fwd[t] = fwd;
         st->status[t] = IPF_OK;
         st->kdone[t] = 0;
         st->beta[t] = 0.0;
@@ -1130,8 +1189,8 @@ cudaError_t launch_sketch_table(const SketchParams& sp, long long n, unsigned lo
     return cudaGetLastError();
 }
 
-cudaError_t launch_reset_state(DevState* st, cudaStream_t s) {
-    k_reset_state<<<1, 64, 0, s>>>(st);
+cudaError_t launch_reset_state(DevState* st, bool fwd, cudaStream_t s) {
+    k_reset_state<<<1, 64, 0, s>>>(st, fwd ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -1139,9 +1198,9 @@ cudaError_t launch_reset_state(DevState* st, cudaStream_t s) {
 // batched step: the update, normalisation and pivot-block solve of every
 // active slot of the work list in one launch each (persistent CTAs over the
 // (slot, tile) tables).  Per element the arithmetic is that of k_update_f,
-// k_normalize and k_pivot_solve for one right-hand side with float storage
-// and the deferred sketch, so a solve gets the same bits whatever else is
-// in the batch and however its elements are tiled.
+// k_normalize, k_pivot_minv and k_pivot_apply for one right-hand side with
+// float storage and the deferred sketch, so a solve gets the same bits
+// whatever else is in the batch and however its elements are tiled.
 // ------------------------------------------------------------------------
 template <class T>
 __global__ void __launch_bounds__(256, 4) kb_update(const SlotDesc* __restrict__ slots,
@@ -1363,16 +1422,33 @@ __global__ void __launch_bounds__(256) kb_normalize(const SlotDesc* __restrict__
     }
 }
 
-template <class T, class Acc, int NG, bool SM>
-__global__ void __launch_bounds__(256) kb_pivot_solve(const SlotDesc* __restrict__ slots,
+// grid (column blocks, list entries)
+template <class T>
+__global__ void __launch_bounds__(256) kb_pivot_minv(const SlotDesc* __restrict__ slots,
+                                                     const TileRef* __restrict__ list) {
+    const SlotDesc* sd = slots + list[blockIdx.y].slot;
+    if (sd->k_target <= 0) return;
+    if (sd->bf.st->j >= sd->k_target) return;
+    const Geom g = sd->g;
+    const Bufs bf = sd->bf;
+    pivot_minv_body<T>(g, bf, 0, blockIdx.x);
+}
+
+// grid (row blocks, list entries); dynamic shared memory pivot_apply_smem
+template <class T>
+__global__ void __launch_bounds__(256) kb_pivot_apply(const SlotDesc* __restrict__ slots,
                                                       const TileRef* __restrict__ list) {
-    const SlotDesc* sd = slots + list[blockIdx.x].slot;
+    const SlotDesc* sd = slots + list[blockIdx.y].slot;
     if (sd->k_target <= 0) return;
     const DevState* st = sd->bf.st;
     if (st->j >= sd->k_target) return;
     const Geom g = sd->g;
     const Bufs bf = sd->bf;
-    pivot_solve_body<T, Acc, NG, SM>(g, bf, 0);
+    if (st->fwd[0]) {
+        if (blockIdx.x == 0) pivot_fwd_body<T, float>(g, bf, 0);
+        return;
+    }
+    pivot_apply_body<T, float>(g, bf, 0, blockIdx.x);
 }
 
 // ------------------------------------------------------------------------
@@ -1395,21 +1471,26 @@ cudaError_t launch_load_rhs(int storage, const float* b, const Geom& g, const Bu
     return cudaGetLastError();
 }
 
-cudaError_t launch_pivot_solve(int storage, const Geom& g, const Bufs& bf, cudaStream_t s) {
-    const int K1 = g.k_max + 1;
+cudaError_t launch_pivot_minv(int storage, const Geom& g, const Bufs& bf, cudaStream_t s) {
+    const dim3 grid((unsigned)((g.k_max + kMinvCols - 1) / kMinvCols), (unsigned)g.B);
+    IPF_DISPATCH_STORAGE(storage, { k_pivot_minv<T><<<grid, 256, 0, s>>>(g, bf); });
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pivot_apply(int storage, const Geom& g, const Bufs& bf, cudaStream_t s) {
+    const dim3 grid((unsigned)((g.k_max + kApplyRows - 1) / kApplyRows), (unsigned)g.B);   // rows 0 .. k_max - 1
+    const size_t smem = pivot_apply_smem(g.k_max);
     IPF_DISPATCH_STORAGE(storage, {
         using Acc = typename AccOf<T>::type;
-        // packed L_p (up to kPivSmemK), then g (K1, rounded to even) and the
-        // column values x_c (K1)
-        const bool sm = g.k_max <= kPivSmemK;
-        const size_t small = (size_t)(((K1 + 1) & ~1) + K1 + 1) * sizeof(double);
-        const size_t smem = (sm ? lp_stride(g.k_max) * sizeof(double) : 0) + small;
-        auto fn = sm ? k_pivot_solve<T, Acc, 2, true> : k_pivot_solve<T, Acc, 4, false>;
-        cudaError_t e = raise_smem(fn, (int)smem);
-        if (e != cudaSuccess) return e;
-        fn<<<g.B, 256, smem, s>>>(g, bf);
+        k_pivot_apply<T, Acc><<<grid, 256, smem, s>>>(g, bf);
     });
     return cudaGetLastError();
+}
+
+cudaError_t launch_pivot_solve(int storage, const Geom& g, const Bufs& bf, cudaStream_t s) {
+    cudaError_t e = launch_pivot_minv(storage, g, bf, s);
+    if (e != cudaSuccess) return e;
+    return launch_pivot_apply(storage, g, bf, s);
 }
 
 template <class T>
@@ -1625,22 +1706,21 @@ cudaError_t launch_sketch_finish(const long long* acc, int m, long long n, int z
 cudaError_t launch_batch_pivot_solve(int storage, const SlotDesc* slots, const TileRef* list, int nslots, int k_max,
                                      cudaStream_t s) {
     if (nslots <= 0) return cudaSuccess;
-    const int K1 = k_max + 1;
-    const bool sm = k_max <= kPivSmemK;                   // the group's largest k_max
-    const size_t smem = (sm ? lp_stride(k_max) * sizeof(double) : 0) +
-                        (size_t)(((K1 + 1) & ~1) + K1 + 1) * sizeof(double);
-    auto go = [&](auto fn) -> cudaError_t {
-        cudaError_t e = raise_smem(fn, (int)smem);
+    // k_max: the group's largest; blocks past a slot's own k_max return at once
+    const dim3 gm((unsigned)((k_max + kMinvCols - 1) / kMinvCols), (unsigned)nslots);
+    const dim3 ga((unsigned)((k_max + kApplyRows - 1) / kApplyRows), (unsigned)nslots);
+    const size_t smem = pivot_apply_smem(k_max);
+    auto go = [&](auto fm, auto fa) -> cudaError_t {
+        fm<<<gm, 256, 0, s>>>(slots, list);
+        cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        fn<<<nslots, 256, smem, s>>>(slots, list);
+        fa<<<ga, 256, smem, s>>>(slots, list);
         return cudaGetLastError();
     };
     switch (storage) {
-        case IPF_STORE_F32: return sm ? go(kb_pivot_solve<float, float, 2, true>) : go(kb_pivot_solve<float, float, 4, false>);
-        case IPF_STORE_BF16:
-            return sm ? go(kb_pivot_solve<__nv_bfloat16, float, 2, true>)
-                      : go(kb_pivot_solve<__nv_bfloat16, float, 4, false>);
-        case IPF_STORE_F16: return sm ? go(kb_pivot_solve<__half, float, 2, true>) : go(kb_pivot_solve<__half, float, 4, false>);
+        case IPF_STORE_F32: return go(kb_pivot_minv<float>, kb_pivot_apply<float>);
+        case IPF_STORE_BF16: return go(kb_pivot_minv<__nv_bfloat16>, kb_pivot_apply<__nv_bfloat16>);
+        case IPF_STORE_F16: return go(kb_pivot_minv<__half>, kb_pivot_apply<__half>);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -549,45 +549,51 @@ cudaError_t apply_T(const OpDev& op, const void* v, long long ldv, long long vco
     }
 }
 
-// (A v_j)(p_i), i <= j: one warp per (pivot, RHS), lanes over the stencil
-// taps or the row's nonzeros, a fixed-order shuffle reduction.
-// (A v)(p) for one pivot row p, one warp: the stencil taps (PSF) or the row's
-// nonzeros (CSR, RHS r of B interleaved) over the lanes, a fixed-order
-// shuffle reduction; every lane returns the sum
+// (A v_j)(p_i), i <= j, for the pivot-block solve.  PSF: four warps per
+// pivot row, warp q taking the stencil rows q ceil(ph/4) .. (q+1) ceil(ph/4)
+// - 1 with the lanes over the columns (every load of a warp issued before
+// its FMAs: one round of loads for a 31 x 31 stencil), a fixed-order shuffle
+// reduction in each warp and the four partial sums added in warp order.
+// CSR: one warp per (pivot, RHS), lanes over the row's nonzeros, a
+// fixed-order shuffle reduction.
+constexpr int kPivParts = 4;                 // warps per PSF pivot row
+
 template <class T>
-__device__ __forceinline__ float pivot_row_psf(const T* __restrict__ v, int p, int H, int W,
-                                               const float* __restrict__ psf, int ph, int pw) {
+__device__ __forceinline__ float pivot_row_psf_part(const T* __restrict__ v, int p, int H, int W,
+                                                    const float* __restrict__ psf, int ph, int pw, int part) {
     const int lane = threadIdx.x & 31;
     const int py = p / W, px = p - py * W;
     const int cy = ph / 2, cx = pw / 2;
-    const int taps = ph * pw;
+    const int per = (ph + kPivParts - 1) / kPivParts;
+    const int ky0 = part * per, ky1 = min(ph, ky0 + per);
     float acc = 0.f;
-    // U taps per lane per pass, every load of the pass issued before its
-    // FMAs (the taps t = lane, lane + 32, ... are still added in that order)
     constexpr int U = 8;
-    for (int t0 = lane; t0 < taps; t0 += 32 * U) {
-        float f[U], x[U];
+    for (int kx = lane; kx < pw; kx += 32) {
+        const int xx = px - kx + cx;
+        const bool xin = xx >= 0 && xx < W;
+        for (int ky = ky0; ky < ky1; ky += U) {
+            float f[U], x[U];
+            bool in[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int t = t0 + 32 * u;
-            const int ky = t / pw, kx = t - ky * pw;
-            const int yy = py - ky + cy, xx = px - kx + cx;
-            const bool in = t < taps && yy >= 0 && yy < H && xx >= 0 && xx < W;
-            f[u] = in ? psf[t] : 0.f;
-            x[u] = in ? to_acc(v[(size_t)yy * W + xx]) : 0.f;
-        }
+            for (int u = 0; u < U; ++u) {
+                const int k = ky + u;
+                const int yy = py - k + cy;
+                in[u] = k < ky1 && xin && yy >= 0 && yy < H;
+                f[u] = in[u] ? psf[k * pw + kx] : 0.f;
+                x[u] = in[u] ? to_acc(v[(size_t)yy * W + xx]) : 0.f;
+            }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int t = t0 + 32 * u;
-            const int ky = t / pw, kx = t - ky * pw;
-            const int yy = py - ky + cy, xx = px - kx + cx;
-            if (t < taps && yy >= 0 && yy < H && xx >= 0 && xx < W) acc = fmaf(f[u], x[u], acc);
+            for (int u = 0; u < U; ++u)
+                if (in[u]) acc = fmaf(f[u], x[u], acc);
         }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
     return acc;
 }
+
+// the four warps' partial sums of one pivot row, in warp order
+__device__ __forceinline__ float pivot_parts_sum(const float* s) { return ((s[0] + s[1]) + s[2]) + s[3]; }
 
 template <class T>
 __device__ __forceinline__ float pivot_row_csr(const T* __restrict__ v, long long row, int B, int r,
@@ -607,12 +613,19 @@ __global__ void __launch_bounds__(256) k_pivot_rows_psf(const T* __restrict__ vb
                                                          const DevState* __restrict__ st, const int* __restrict__ piv,
                                                          int H, int W, const float* __restrict__ psf, int ph, int pw,
                                                          float* __restrict__ gout) {
+    // two pivot rows per CTA (8 warps, kPivParts per row)
+    __shared__ float s_part[8];
     const int j = st->j;
-    const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-    if (j < 0 || i > j || st->status[0] != IPF_OK) return;
+    const int i0 = blockIdx.x * 2;
+    if (j < 0 || i0 > j || st->status[0] != IPF_OK) return;          // uniform
+    const int warp = threadIdx.x >> 5;
+    const int i = i0 + warp / kPivParts;
     const T* v = vbase + (size_t)j * ldv;
-    const float acc = pivot_row_psf<T>(v, piv[i], H, W, psf, ph, pw);
-    if ((threadIdx.x & 31) == 0) gout[i] = acc;
+    float acc = 0.f;
+    if (i <= j) acc = pivot_row_psf_part<T>(v, piv[i], H, W, psf, ph, pw, warp % kPivParts);
+    if ((threadIdx.x & 31) == 0) s_part[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x < 2 && i0 + (int)threadIdx.x <= j) gout[i0 + threadIdx.x] = pivot_parts_sum(s_part + kPivParts * threadIdx.x);
 }
 
 template <class T>
@@ -650,8 +663,8 @@ cudaError_t launch_pivot_rows(const OpDev& op, int storage, const void* vbase, l
     auto go = [&](auto tag) -> cudaError_t {
         using T = decltype(tag);
         if (op.kind == IPF_OP_PSF2D)
-            k_pivot_rows_psf<T><<<blocks, 256, 0, s>>>((const T*)vbase, ldv, st, piv, op.rows, op.cols, op.psf, op.ph,
-                                                       op.pw, gout);
+            k_pivot_rows_psf<T><<<(K1 + 1) / 2, 256, 0, s>>>((const T*)vbase, ldv, st, piv, op.rows, op.cols, op.psf,
+                                                             op.ph, op.pw, gout);
         else if (op.kind == IPF_OP_CSR)
             k_pivot_rows_csr<T><<<blocks, 256, 0, s>>>((const T*)vbase, ldv, st, piv, B, K1, op.rowptr, op.colind,
                                                        op.vals, gout);
@@ -742,25 +755,41 @@ __global__ void __launch_bounds__(128, 7) kb_operator(const SlotDesc* __restrict
 }
 
 // (A v_j)(p_i), i <= j, of every active slot: tile t of a slot holds the
-// pivots 8t .. 8t + 7, one warp each (the arithmetic of k_pivot_rows_*)
+// pivots 8t .. 8t + 7 (the arithmetic of k_pivot_rows_*): CSR one warp
+// each; PSF two per pass, kPivParts warps each
 template <class T>
 __global__ void __launch_bounds__(256) kb_pivot_rows(const SlotDesc* __restrict__ slots,
                                                      const TileRef* __restrict__ tiles, int ntiles) {
     __shared__ int s_j;
+    __shared__ float s_part[8];
+    const int warp = threadIdx.x >> 5;
     for (int tt = blockIdx.x; tt < ntiles; tt += gridDim.x) {
         const TileRef tr = tiles[tt];
         const SlotDesc* sd = slots + tr.slot;
         const int j = slot_step(sd, &s_j);
         if (j < 0) continue;
-        const int i = tr.tile * 8 + (int)(threadIdx.x >> 5);
-        if (i > j) continue;                               // uniform per warp
         const T* v = (const T*)sd->bf.V + (size_t)j * sd->g.ldv;
         const OpDev& op = sd->op;
-        const int p = sd->bf.piv[i];
-        const float acc = op.kind == IPF_OP_CSR
-                              ? pivot_row_csr<T>(v, p, 1, 0, op.rowptr, op.colind, op.vals)
-                              : pivot_row_psf<T>(v, p, op.rows, op.cols, op.psf, op.ph, op.pw);
-        if ((threadIdx.x & 31) == 0) sd->bf.gpiv[i] = acc;
+        if (op.kind == IPF_OP_CSR) {
+            const int i = tr.tile * 8 + warp;
+            if (i > j) continue;                           // uniform per warp
+            const float acc = pivot_row_csr<T>(v, sd->bf.piv[i], 1, 0, op.rowptr, op.colind, op.vals);
+            if ((threadIdx.x & 31) == 0) sd->bf.gpiv[i] = acc;
+            continue;
+        }
+        for (int pass = 0; pass < 4; ++pass) {
+            const int i0 = tr.tile * 8 + 2 * pass;
+            if (i0 > j) break;                             // uniform
+            const int i = i0 + warp / kPivParts;
+            float acc = 0.f;
+            if (i <= j) acc = pivot_row_psf_part<T>(v, sd->bf.piv[i], op.rows, op.cols, op.psf, op.ph, op.pw,
+                                                    warp % kPivParts);
+            if ((threadIdx.x & 31) == 0) s_part[warp] = acc;
+            __syncthreads();
+            if (threadIdx.x < 2 && i0 + (int)threadIdx.x <= j)
+                sd->bf.gpiv[i0 + threadIdx.x] = pivot_parts_sum(s_part + kPivParts * threadIdx.x);
+            __syncthreads();
+        }
     }
 }
 

@@ -7,7 +7,7 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
-from _gpu_common import TIE, compare_solution, ensure_lib, gpu_context, verify_scmrh  # noqa: E402
+from _gpu_common import TIE, compare_solution, ensure_lib, gpu_context, tolerance, verify_scmrh  # noqa: E402
 from gen import problems as P  # noqa: E402
 from oracle import operators as ops, scmrh, sketch as sk  # noqa: E402
 
@@ -82,3 +82,41 @@ def test_sampled_pivot_growth_keeps_sketch_exact(storage):
     if storage == "f64":
         compare_solution(ctx, st, storage, [1, 2, 3, 4, 5], [0.0])
     ctx.close()
+
+
+def test_inverse_growth_switches_to_forward_substitution():
+    """The pivot-block solve in inverse form keeps a row of L_p^{-1} per
+    step; a row larger than 2^20 in magnitude switches the solve to forward
+    substitution for the rest of the run.  Sampled pivoting with one-entry
+    samples and a right-hand side with one entry 1e6 gives |v_j| up to 4e9
+    and, in the oracle's L_p, rows of the inverse of 0.45, 0.81, 1.2e2 and
+    then 1.5e7 at step 4, so the switch happens inside this 8-step run.  In
+    FP64 the pivots are the oracle's and x_k follows it, both with the
+    default solve (inverse form, then the switch) and with forward
+    substitution throughout (pivot_fwd = 1), and the two runs agree to FP64
+    rounding."""
+    p = P.make("deblur64")
+    rng = np.random.default_rng(8)
+    b = rng.uniform(1e-3, 1e-2, p.n).astype(np.float32)
+    b[1234] = 1e6
+    k = 8
+    A = ops.make_apply(p)
+    S = sk.SparseSignSketch(p.sketch_seed, p.n, p.m_s, p.zeta)
+    st = scmrh.run(A, b.astype(np.float64), S, k, pivot_sample=1, pivot_seed=p.sketch_seed ^ PIVOT_SEED_XOR)
+    L = st.V[st.piv[:k + 1], :k + 1]
+    Minv = np.linalg.inv(L)
+    rows = [np.abs(Minv[j, :j]).max() for j in range(1, k + 1)]
+    assert max(rows[:3]) < 2.0 ** 20 < rows[3], rows           # the switch comes at step 4
+    xs = []
+    for fwd in (0, 1):
+        ctx = gpu_context(p, "f64", k=k, b=b.reshape(1, -1), pivot_sample=1, pivot_fwd=fwd)
+        ctx.step(k)
+        status, kd = ctx.sync()
+        assert kd == [k]
+        assert [int(v) for v in ctx.export(0)["piv"][:k + 1]] == list(st.piv)
+        compare_solution(ctx, st, "f64", list(range(1, k + 1)), [0.0], name=f"growth_switch_fwd{fwd}")
+        x, _ = ctx.solve(k, [0.0])
+        xs.append(x[0, 0].astype(np.float64))
+        ctx.close()
+    tol = tolerance("f64", np.linalg.cond(scmrh.projected_matrix(st, k, "hessenberg")))
+    assert np.linalg.norm(xs[0] - xs[1]) <= tol * np.linalg.norm(xs[1])

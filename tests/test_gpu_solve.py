@@ -169,14 +169,20 @@ def test_deblur256_sep_motion_lambda_sweep(deblur256, storage):
     ctx.close()
 
 
-def test_graph_and_eager_paths_give_identical_bits(deblur64):
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_graph_and_eager_paths_give_identical_bits(deblur64, storage):
+    """Steps launched eagerly, from the one-step graph and from the
+    eight-step graph (step(7): one eager step and six one-step replays;
+    step(13) and step(20): eight-step replays and one-step remainders) give
+    the same bits."""
     p, _ = deblur64
     outs = []
     for graphs in (0, 1):
-        ctx = gpu_context(p, "f32", k=20, graphs=graphs)
+        ctx = gpu_context(p, storage, k=40, graphs=graphs)
         ctx.step(7)
         ctx.step(13)
-        x, _ = ctx.solve(20, [0.0, 1e-3])
+        ctx.step(20)
+        x, _ = ctx.solve(40, [0.0, 1e-3])
         outs.append((x.copy(), ctx.export(0)))
         ctx.close()
     assert np.array_equal(outs[0][0], outs[1][0])
@@ -218,15 +224,16 @@ def test_interleaved_solves_and_exports_keep_sketch_exact(deblur64, storage, ove
     assert np.array_equal(x12, x_ref12)
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32", "bf16"])
-def test_large_k_pivot_block_from_l2(storage):
-    """k = 300, m_s = 1200: beyond the 224 columns whose FP64 pivot block is
-    staged in shared memory, the pivot-block solve reads L_p from global
-    memory with four row groups per warp (up to 512 rows); pivots and x_k
+@pytest.mark.parametrize("storage,pivot_fwd", [("f64", 0), ("f32", 0), ("bf16", 0), ("f64", 1), ("bf16", 1)])
+def test_large_k_pivot_block(storage, pivot_fwd):
+    """k = 300, m_s = 1200: the pivot-block solve in inverse form (rows of
+    L_p^{-1} over ten blocks of 32 columns, h as a product with 300
+    independent rows) and by forward substitution (pivot_fwd = 1: L_p read
+    from L2, four row groups per warp, up to 512 rows); pivots and x_k
     against the oracle up to the full k."""
     p = P.make("deblur64")
     k, m_s = 300, 1200
-    ctx = gpu_context(p, storage, k=k, m_s=m_s)
+    ctx = gpu_context(p, storage, k=k, m_s=m_s, pivot_fwd=pivot_fwd)
     ctx.step(k)
     status, kd = ctx.sync()
     assert kd == [k]
@@ -234,7 +241,8 @@ def test_large_k_pivot_block_from_l2(storage):
     # pivot order chaotic even in FP64, so the pivots are checked against the
     # oracle's own divergence under perturbations of the same size (in every
     # storage type), and x_k by replaying the GPU's pivots
-    verify_scmrh(ctx, p, storage, [50, 150, 225, 300], [0.0, 1e-3], k=k, m_s=m_s, name=f"large_k300_{storage}")
+    verify_scmrh(ctx, p, storage, [50, 150, 225, 300], [0.0, 1e-3], k=k, m_s=m_s,
+                 name=f"large_k300_{storage}_fwd{pivot_fwd}")
     ctx.close()
 
 
