@@ -39,7 +39,7 @@
 // Warp roles (416 threads, one CTA per SM): warp 0 issues the TMA loads;
 // warp 1 owns TMEM; one lane each of warps 1-3 and 12 issues the MMAs of
 // every fourth group; warps 8-11 build A (every fourth group, two image rows
-// at a time); warps 4-7 read the accumulators (warp w reads TMEM lanes
+// at a time; the first group together); warps 4-7 read the accumulators (warp w reads TMEM lanes
 // 32 (w % 4) ..) and finish the output rows.  Each ring slot is waited on by
 // one role instance only (the slot counts are multiples of 4 and group g goes
 // to instance g mod 4), so a parity wait can never match a phase two
@@ -233,67 +233,78 @@ __device__ __forceinline__ void conv_tc_body(const CUtensorMap* vmap, const int*
         }
     } else if (warp >= 8 && warp < 12) {
         // ---- A builders: Hankel blocks from the staged box, one group per warp
-        // (every fourth group), two image rows per pass ----
-        for (int g = warp - 8; g < NG; g += kBuilders) {
+        // (every fourth group), two image rows per pass; the first group is
+        // built by all four warps, two rows each, so the first MMAs start
+        // a quarter of a group's build time after the first box lands ----
+        // two image rows r0, r0 + 1 of the box in slot sl into A slot hg; a
+        // lane takes the core-matrix rows s = 2t and 2t + 1 of block q of one
+        // of them: both 16-byte rows lie in the five source words from
+        // (OFF + 8q + 2t) / 2 on, so the loads per stored byte are half those
+        // of one row per lane (the staged segment's reads and the block
+        // stores are the shared-memory traffic the convolution is bound by)
+        auto build_pair = [&](int sl, int hg, int rows, int r0) {
+            constexpr int JOBS = NQ * 4;                        // (q, t) per image row
+            constexpr int NIT = (2 * JOBS + 31) / 32;
+            uint32_t wv[NIT][5];
+#pragma unroll
+            for (int it = 0; it < NIT; ++it) {
+                const int jb = it * 32 + lane;
+                const int p = jb >= JOBS ? 1 : 0, rem = jb - p * JOBS;
+                const int r = min(r0 + p, rows - 1);
+                const uint32_t* src = (const uint32_t*)(sm + kOffSeg + sl * kSegBytes + r * kSegW * 2);
+                const int e0 = OFF + 8 * (rem >> 2) + 2 * (rem & 3);
+                const int wb = jb < 2 * JOBS ? (e0 >> 1) : 0;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) wv[it][k] = src[wb + k];
+            }
+#pragma unroll
+            for (int it = 0; it < NIT; ++it) {
+                const int jb = it * 32 + lane;
+                const int p = jb >= JOBS ? 1 : 0, rem = jb - p * JOBS;
+                if (jb < 2 * JOBS && r0 + p < rows) {
+                    unsigned char* dst = sm + kOffHank + (hg * kG + r0 + p) * kHankBytes;
+                    const int q = rem >> 2, t = rem & 3;
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        // e = OFF + 8q + 2t + u has the parity of OFF + u: d
+                        // words into wv, and a two-byte shift when e is odd
+                        constexpr bool kOdd = (OFF & 1) != 0;
+                        const int d = (kOdd && u == 1) ? 1 : 0;
+                        const uint32_t sel = ((OFF + u) & 1) ? 0x5432u : 0x3210u;
+                        const uint32_t w4 = d == 0 ? wv[it][4] : 0u;      // unused (aligned) when d = 1
+                        uint4 o;
+                        o.x = __byte_perm(wv[it][d], wv[it][d + 1], sel);
+                        o.y = __byte_perm(wv[it][d + 1], wv[it][d + 2], sel);
+                        o.z = __byte_perm(wv[it][d + 2], wv[it][d + 3], sel);
+                        o.w = __byte_perm(wv[it][d + 3], w4, sel);
+                        *(uint4*)(dst + q * 128 + (2 * t + u) * 16) = o;
+                    }
+                }
+            }
+            // every word read from the two staged rows has been consumed by a
+            // store: they may be overwritten by the next box
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(seg_empty(sl));
+                if (r0 + 1 < rows) mbar_arrive(seg_empty(sl));
+            }
+        };
+        {
+            // group 0 (box slot 0, A slot 0, both in their first phase)
+            const int rows = min(kG, NR);
+            const int r0 = 2 * (warp - 8);
+            const bool ok = mbar_wait(seg_full(0), 0, s_abort, err) && mbar_wait(h_empty(0), 1, s_abort, err);
+            if (ok && r0 < rows) build_pair(0, 0, rows, r0);
+            fence_proxy_async_smem();
+            asm volatile("bar.sync 1, 128;" ::: "memory");      // the four builder warps
+            if (warp == 8 && !*s_abort) mbar_arrive(h_full(0));
+        }
+        for (int g = warp - 8 == 0 ? kBuilders : warp - 8; g < NG; g += kBuilders) {
             const int sl = g % kNSeg, hg = g % kNHG;
             if (!mbar_wait(seg_full(sl), (g / kNSeg) & 1, s_abort, err)) break;
             if (!mbar_wait(h_empty(hg), ((g / kNHG) & 1) ^ 1, s_abort, err)) break;
             const int rows = min(kG, NR - g * kG);
-            // two image rows per pass; a lane takes the core-matrix rows s = 2t
-            // and 2t + 1 of block q of one of them: both 16-byte rows lie in
-            // the five source words from (OFF + 8q + 2t) / 2 on, so the loads
-            // per stored byte are half those of one row per lane (the staged
-            // segment's reads and the block stores are the shared-memory
-            // traffic the convolution is bound by)
-            constexpr int JOBS = NQ * 4;                        // (q, t) per image row
-            constexpr int NIT = (2 * JOBS + 31) / 32;
-            for (int r0 = 0; r0 < rows; r0 += 2) {
-                uint32_t wv[NIT][5];
-#pragma unroll
-                for (int it = 0; it < NIT; ++it) {
-                    const int jb = it * 32 + lane;
-                    const int p = jb >= JOBS ? 1 : 0, rem = jb - p * JOBS;
-                    const int r = min(r0 + p, rows - 1);
-                    const uint32_t* src = (const uint32_t*)(sm + kOffSeg + sl * kSegBytes + r * kSegW * 2);
-                    const int e0 = OFF + 8 * (rem >> 2) + 2 * (rem & 3);
-                    const int wb = jb < 2 * JOBS ? (e0 >> 1) : 0;
-#pragma unroll
-                    for (int k = 0; k < 5; ++k) wv[it][k] = src[wb + k];
-                }
-#pragma unroll
-                for (int it = 0; it < NIT; ++it) {
-                    const int jb = it * 32 + lane;
-                    const int p = jb >= JOBS ? 1 : 0, rem = jb - p * JOBS;
-                    if (jb < 2 * JOBS && r0 + p < rows) {
-                        unsigned char* dst = sm + kOffHank + (hg * kG + r0 + p) * kHankBytes;
-                        const int q = rem >> 2, t = rem & 3;
-                        const int e0 = OFF + 8 * q + 2 * t;
-                        (void)e0;
-#pragma unroll
-                        for (int u = 0; u < 2; ++u) {
-                            // e = e0 + u has the parity of OFF + u (8q + 2t is even):
-                            // d words into wv, and a two-byte shift when e is odd
-                            constexpr bool kOdd = (OFF & 1) != 0;
-                            const int d = (kOdd && u == 1) ? 1 : 0;
-                            const uint32_t sel = ((OFF + u) & 1) ? 0x5432u : 0x3210u;
-                            const uint32_t w4 = d == 0 ? wv[it][4] : 0u;      // unused (aligned) when d = 1
-                            uint4 o;
-                            o.x = __byte_perm(wv[it][d], wv[it][d + 1], sel);
-                            o.y = __byte_perm(wv[it][d + 1], wv[it][d + 2], sel);
-                            o.z = __byte_perm(wv[it][d + 2], wv[it][d + 3], sel);
-                            o.w = __byte_perm(wv[it][d + 3], w4, sel);
-                            *(uint4*)(dst + q * 128 + (2 * t + u) * 16) = o;
-                        }
-                    }
-                }
-                // every word read from the two staged rows has been consumed
-                // by a store: they may be overwritten by the next box
-                __syncwarp();
-                if (lane == 0) {
-                    mbar_arrive(seg_empty(sl));
-                    if (r0 + 1 < rows) mbar_arrive(seg_empty(sl));
-                }
-            }
+            for (int r0 = 0; r0 < rows; r0 += 2) build_pair(sl, hg, rows, r0);
             fence_proxy_async_smem();
             mbar_arrive(h_full(hg));
         }
