@@ -184,8 +184,10 @@ __device__ __forceinline__ bool wait_flag(const unsigned* flag, int* err) {
 // tau = (beta - alpha) / beta, R(i,i) = beta.  v goes to buf (rows i..m-1)
 // and back into the column below the diagonal, tau into the column's
 // diagonal slot (R(i,i) lives in diag), then the column's flag is raised.
-__device__ __forceinline__ void make_reflector(double* col, int i, int m, double* buf, double* diag, unsigned* flag, double* s_red,
-                               double* s_tau) {
+// col is the working copy (shared memory or the column itself); gcol, if
+// not col, is the column in global memory, where v and tau are published.
+__device__ __forceinline__ void make_reflector(double* col, double* gcol, int i, int m, double* buf, double* diag,
+                                               unsigned* flag, double* s_red, double* s_tau) {
     __shared__ double s_inv;
     double part = 0.0;
     for (int row = i + threadIdx.x; row < m; row += blockDim.x) {
@@ -209,6 +211,7 @@ __device__ __forceinline__ void make_reflector(double* col, int i, int m, double
         s_inv = inv;
         buf[i] = 1.0;
         col[i] = tau;
+        if (gcol != col) gcol[i] = tau;
     }
     __syncthreads();
     const double inv = s_inv;
@@ -216,6 +219,7 @@ __device__ __forceinline__ void make_reflector(double* col, int i, int m, double
         const double v = buf[row] * inv;
         buf[row] = v;
         col[row] = v;
+        if (gcol != col) gcol[row] = v;
     }
     __threadfence();                          // every writer orders its stores before the flag
     __syncthreads();
@@ -238,13 +242,18 @@ __device__ __forceinline__ void apply_block(const double* v, double tau, double*
 // reflector it applies next, and applies reflectors in order.  The owner of
 // column i+1 applies reflector i to that column first and publishes
 // reflector i+1 at once (lookahead), before its other columns; two shared
-// buffers hold v_i and v_{i+1}.  Cooperative launch: all CTAs co-resident.
-__global__ void __launch_bounds__(256) k_householder(Geom g, const DevState* st, int k, int need_T, int cpj,
+// buffers hold v_i and v_{i+1}.  csm: the CTA's own columns are worked on
+// in shared memory (after the two buffers, m doubles each) and written back
+// at the end, so the chain from one reflector to the next (apply it to the
+// next column, form that column's reflector) reads and writes no global
+// memory except the published reflector.  Cooperative launch: all CTAs
+// co-resident.
+__global__ void __launch_bounds__(256) k_householder(Geom g, const DevState* st, int k, int need_T, int cpj, int csm,
                                                       double* Mw, double* Tw, double* dM, double* dT,
                                                       unsigned* flags, int* err) {
     extern __shared__ unsigned char smem_raw[];
     const int m = g.m_s;
-    double* s_buf = (double*)smem_raw;        // 2 x m doubles
+    double* s_buf = (double*)smem_raw;        // 2 x m doubles, then the own columns (csm)
     __shared__ double s_red[32];
     __shared__ double s_tau[2];
     const int jobs_per_rhs = need_T ? 2 : 1;
@@ -262,13 +271,24 @@ __global__ void __launch_bounds__(256) k_householder(Geom g, const DevState* st,
     unsigned* flag = flags + (size_t)job * (g.k_max + 2);
     const int nsteps = ncols < m ? ncols : m;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    // own column jc (jc = q mod cpj): its working copy
+    double* s_cols = s_buf + 2 * (size_t)m;
+    auto colp = [&](int jc) -> double* { return csm ? s_cols + (size_t)((jc - q) / cpj) * m : A + (size_t)jc * m; };
+    if (csm) {
+        for (int jc = q; jc < ncols; jc += cpj) {
+            double* d = colp(jc);
+            const double* src = A + (size_t)jc * m;
+            for (int row = threadIdx.x; row < m; row += blockDim.x) d[row] = src[row];
+        }
+        __syncthreads();
+    }
     int have = -1;                            // reflector already made here by lookahead
     for (int i = 0; i < nsteps; ++i) {
         double* v = s_buf + (size_t)(i & 1) * m;
         double* ci = A + (size_t)i * m;
         double tau;
         if (i % cpj == q) {
-            if (have != i) make_reflector(ci, i, m, v, diag + i, flag + i, s_red, &s_tau[i & 1]);
+            if (have != i) make_reflector(colp(i), ci, i, m, v, diag + i, flag + i, s_red, &s_tau[i & 1]);
             tau = s_tau[i & 1];
         } else {
             if (!wait_flag(flag + i, err)) return;
@@ -285,10 +305,10 @@ __global__ void __launch_bounds__(256) k_householder(Geom g, const DevState* st,
         int jrest = j0;
         if (j0 == i + 1) {
             // lookahead: the next reflector's column first, then that reflector
-            if (tau != 0.0) apply_block(v, tau, A + (size_t)j0 * m, i, m, s_red);
+            if (tau != 0.0) apply_block(v, tau, colp(j0), i, m, s_red);
             if (i + 1 < nsteps) {
                 double* vn = s_buf + (size_t)((i + 1) & 1) * m;
-                make_reflector(A + (size_t)j0 * m, i + 1, m, vn, diag + i + 1, flag + i + 1, s_red,
+                make_reflector(colp(j0), A + (size_t)j0 * m, i + 1, m, vn, diag + i + 1, flag + i + 1, s_red,
                                &s_tau[(i + 1) & 1]);
                 have = i + 1;
             }
@@ -298,7 +318,7 @@ __global__ void __launch_bounds__(256) k_householder(Geom g, const DevState* st,
             int idx = 0;
             for (int jc = jrest; jc < ncols; jc += cpj, ++idx) {
                 if ((idx % nw) != warp) continue;
-                double* cj = A + (size_t)jc * m;
+                double* cj = colp(jc);
                 double d = 0.0;
                 for (int row = i + lane; row < m; row += 32) d = fma(v[row], cj[row], d);
 #pragma unroll
@@ -308,6 +328,16 @@ __global__ void __launch_bounds__(256) k_householder(Geom g, const DevState* st,
             }
         }
         __syncthreads();
+    }
+    // the own columns back to global memory: R above the diagonal (the
+    // reflectors below it and tau were published already, the same values)
+    if (csm) {
+        __syncthreads();
+        for (int jc = q; jc < ncols; jc += cpj) {
+            const double* src = colp(jc);
+            double* d = A + (size_t)jc * m;
+            for (int row = threadIdx.x; row < m; row += blockDim.x) d[row] = src[row];
+        }
     }
     // columns beyond m (never for m_s >= k+1) have no diagonal
 }
@@ -531,23 +561,39 @@ cudaError_t launch_solve_prepare(const Geom& g, const Bufs& bf, int zeta, int k,
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const int njobs = g.B * (need_T ? 2 : 1);
-    const size_t smem = 2 * sizeof(double) * (size_t)g.m_s;
-    e = raise_smem(k_householder, (int)smem);
-    if (e != cudaSuccess) return e;
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_householder, 256, smem);
-    if (e != cudaSuccess) return e;
-    if (occ < 1) occ = 1;
-    const int maxblocks = occ * num_sms;
+    // CTAs per job from the occupancy with the two reflector buffers, then
+    // the own columns in shared memory too if all CTAs still co-reside
+    size_t smem = 2 * sizeof(double) * (size_t)g.m_s;
+    auto blocks_for = [&](size_t bytes, int* out) -> cudaError_t {
+        cudaError_t ee = raise_smem(k_householder, (int)bytes);
+        if (ee != cudaSuccess) return ee;
+        int occ = 0;
+        ee = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_householder, 256, bytes);
+        *out = (occ < 1 ? 0 : occ) * num_sms;
+        return ee;
+    };
+    int maxblocks = 0;
+    if ((e = blocks_for(smem, &maxblocks)) != cudaSuccess) return e;
+    if (maxblocks < 1) maxblocks = num_sms;
     int cpj = maxblocks / njobs;
     if (cpj > (k + 2) / 2) cpj = (k + 2) / 2;
     if (cpj < 1) cpj = 1;
     if (cpj * njobs > maxblocks) return cudaErrorInvalidConfiguration;   // cannot co-reside
+    int csm = 0;
+    const size_t own = (size_t)(k + 1 + cpj - 1) / cpj;                    // columns per CTA, at most
+    const size_t smem_c = (2 + own) * sizeof(double) * (size_t)g.m_s;
+    if (smem_c <= 200 * 1024) {
+        int mb = 0;
+        if (blocks_for(smem_c, &mb) == cudaSuccess && cpj * njobs <= mb) {
+            csm = 1;
+            smem = smem_c;
+        }
+    }
     const int nb = cpj * njobs;
     Geom gg = g;
     const DevState* stp = bf.st;
-    int kk = k, nt = need_T ? 1 : 0, cp = cpj;
-    void* args[] = {&gg, (void*)&stp, &kk, &nt, &cp, &Mw, &Tw, &dM, &dT, &bars, &err};
+    int kk = k, nt = need_T ? 1 : 0, cp = cpj, cs = csm;
+    void* args[] = {&gg, (void*)&stp, &kk, &nt, &cp, &cs, &Mw, &Tw, &dM, &dT, &bars, &err};
     return cudaLaunchCooperativeKernel((void*)k_householder, dim3(nb), dim3(256), args, smem, s);
 }
 
