@@ -148,17 +148,27 @@ __global__ void k_form(Geom g, Bufs bf, int k, int zeta, int use_sw, int need_T,
 // cooperative Householder QR (R only).  job = 2*r + which (which 0: M with
 // kb+1 columns, 1: T with kb columns).  cpj CTAs per job.
 // ------------------------------------------------------------------------
+// every thread gets the same sum: a shuffle tree per warp, then warp 0 adds
+// the warps' sums by a second tree and shares the total (one warp doing
+// those adds instead of every thread: FP64 issue is the scarce resource)
 __device__ __forceinline__ double block_sum(double v, double* s_red) {
+    __shared__ double s_total;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nw = blockDim.x >> 5;
     __syncthreads();
     if (lane == 0) s_red[wid] = v;
     __syncthreads();
-    double t = 0.0;
-    const int nw = blockDim.x >> 5;
-    for (int q = 0; q < nw; ++q) t += s_red[q];
-    return t;
+    if (wid == 0) {
+        double t = lane < nw ? s_red[lane] : 0.0;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+            if (off < nw) t += __shfl_xor_sync(0xffffffffu, t, off);
+        if (lane == 0) s_total = t;
+    }
+    __syncthreads();
+    return s_total;
 }
 
 // bounded wait by thread 0 for a column flag set by another CTA of the job;
