@@ -150,7 +150,9 @@ typedef struct ipf_config {
     int zform;                   /* enum ipf_zform                                          */
     int nrhs;                    /* independent right-hand sides sharing A: 1, 2, 4 .. 32;
                                     PSF operators and F64 storage need nrhs == 1            */
-    int use_graphs;              /* capture each Hessenberg step in a CUDA graph            */
+    int use_graphs;              /* replay Hessenberg steps from CUDA graphs: one step and
+                                    eight consecutive steps are captured once, and ipf_step
+                                    launches the eight-step graph while 8 or more remain    */
     int profile;                 /* bracket every kernel with CUDA events on the context's
                                     stream (launches eagerly; read with ipf_profile_read)   */
     int overlap;                 /* PSF2D/CSR with float storage, second stream per step:

@@ -249,7 +249,9 @@ struct BatchEngine {
             t[3].push_back({i, 0});
             for (int q = 0, nq = cdiv(d.g.N, kBatchUpdTile); q < nq; ++q) t[4].push_back({i, q});
             for (int q = 0; q < d.norm_tiles; ++q) t[5].push_back({i, q});
-            for (int q = 0, nq = cdiv(d.g.k_max + 1, 8); q < nq; ++q) t[6].push_back({i, q});
+            // pivot-row tiles: 8 CSR rows (a warp each) or 2 PSF rows (four warps each)
+            for (int q = 0, nq = cdiv(d.g.k_max + 1, d.op.kind == IPF_OP_CSR ? 8 : 2); q < nq; ++q)
+                t[6].push_back({i, q});
         }
         // CSR slots of one storage type on the same matrix, in groups of up
         // to kCsrGroup (slot order), one tile list per group

@@ -755,8 +755,8 @@ __global__ void __launch_bounds__(128, 7) kb_operator(const SlotDesc* __restrict
 }
 
 // (A v_j)(p_i), i <= j, of every active slot: tile t of a slot holds the
-// pivots 8t .. 8t + 7 (the arithmetic of k_pivot_rows_*): CSR one warp
-// each; PSF two per pass, kPivParts warps each
+// the arithmetic of k_pivot_rows_*: tile t is CSR pivots 8t .. 8t + 7, a
+// warp each, or PSF pivots 2t, 2t + 1, kPivParts warps each
 template <class T>
 __global__ void __launch_bounds__(256) kb_pivot_rows(const SlotDesc* __restrict__ slots,
                                                      const TileRef* __restrict__ tiles, int ntiles) {
@@ -777,19 +777,17 @@ __global__ void __launch_bounds__(256) kb_pivot_rows(const SlotDesc* __restrict_
             if ((threadIdx.x & 31) == 0) sd->bf.gpiv[i] = acc;
             continue;
         }
-        for (int pass = 0; pass < 4; ++pass) {
-            const int i0 = tr.tile * 8 + 2 * pass;
-            if (i0 > j) break;                             // uniform
-            const int i = i0 + warp / kPivParts;
-            float acc = 0.f;
-            if (i <= j) acc = pivot_row_psf_part<T>(v, sd->bf.piv[i], op.rows, op.cols, op.psf, op.ph, op.pw,
-                                                    warp % kPivParts);
-            if ((threadIdx.x & 31) == 0) s_part[warp] = acc;
-            __syncthreads();
-            if (threadIdx.x < 2 && i0 + (int)threadIdx.x <= j)
-                sd->bf.gpiv[i0 + threadIdx.x] = pivot_parts_sum(s_part + kPivParts * threadIdx.x);
-            __syncthreads();
-        }
+        const int i0 = tr.tile * 2;
+        if (i0 > j) continue;                              // uniform
+        const int i = i0 + warp / kPivParts;
+        float acc = 0.f;
+        if (i <= j) acc = pivot_row_psf_part<T>(v, sd->bf.piv[i], op.rows, op.cols, op.psf, op.ph, op.pw,
+                                                warp % kPivParts);
+        if ((threadIdx.x & 31) == 0) s_part[warp] = acc;
+        __syncthreads();
+        if (threadIdx.x < 2 && i0 + (int)threadIdx.x <= j)
+            sd->bf.gpiv[i0 + threadIdx.x] = pivot_parts_sum(s_part + kPivParts * threadIdx.x);
+        // (the next tile's slot_step starts with a barrier before s_part is reused)
     }
 }
 
