@@ -178,12 +178,16 @@ __device__ __forceinline__ bool wait_flag(const unsigned* flag, int* err) {
     if (threadIdx.x == 0) {
         s_fail = 0;
         long long spins = 0;
-        while (*(volatile const unsigned*)flag == 0u) {
+        for (;;) {
+            // acquire: the reflector written before the flag's release is
+            // visible to this CTA once the barrier below has passed
+            unsigned f;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(flag) : "memory");
+            if (f != 0u) break;
             if (*(volatile int*)err) { s_fail = 1; break; }
             if (++spins > (1ll << 22)) { atomicExch(err, 1); s_fail = 1; break; }
             __nanosleep(32);
         }
-        __threadfence();
     }
     __syncthreads();
     return s_fail == 0;
@@ -231,9 +235,10 @@ __device__ __forceinline__ void make_reflector(double* col, double* gcol, int i,
         col[row] = v;
         if (gcol != col) gcol[row] = v;
     }
-    __threadfence();                          // every writer orders its stores before the flag
+    // the CTA's stores of v and tau, ordered before thread 0 by the barrier,
+    // are published by the flag's release (cumulative at GPU scope)
     __syncthreads();
-    if (threadIdx.x == 0) atomicExch(flag, 1u);
+    if (threadIdx.x == 0) asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(flag), "r"(1u) : "memory");
 }
 
 // col -= tau v (v^T col) over rows i..m-1, the whole CTA (latency path)
@@ -445,15 +450,24 @@ __global__ void __launch_bounds__(256) k_small_solve(Geom g, const DevState* st,
         s_inv[i] = d != 0.0 ? 1.0 / d : 0.0;
     }
     __syncthreads();
+    // the diagonal block's triangle, staged by the whole CTA (coalesced along
+    // columns) so that warp 0's chain of 32 dependent steps reads shared
+    // memory instead of waiting on a global load per step
+    __shared__ double s_blk[32][33];
     for (int hi = kb; hi > 0; hi -= 32) {
         const int lo = hi > 32 ? hi - 32 : 0;
+        for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+            const int c = t >> 5, r = t & 31;                // column lo + c, row lo + r
+            if (lo + c < hi && r < c) s_blk[r][c] = Rv(lo + r, lo + c);
+        }
+        __syncthreads();
         if (warp == 0) {
             const int row = lo + lane;                       // this lane's row of the block
             double b = row < hi ? rhs[row] : 0.0;
             for (int i = hi - 1; i >= lo; --i) {
                 const double yi = __shfl_sync(0xffffffffu, b * s_inv[i < 0 ? 0 : i], i - lo);
                 if (lane == 0) y[i] = yi;
-                if (row < i) b = fma(-Rv(row, i), yi, b);
+                if (row < i) b = fma(-s_blk[lane][i - lo], yi, b);
                 if (lane == i - lo) b = yi;                  // row i now holds y_i
             }
             if (row < hi) rhs[row] = b;                      // y of the block, for the rows above
