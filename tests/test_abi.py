@@ -75,6 +75,9 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.ipf_create(C.byref(op), bb.ctypes.data, 0, C.byref(cfg), C.byref(h)) == b.IPF_ERR_UNSUPPORTED
     cfg = b.default_config(k_max=248, m_s=1000, sketch="gaussian")
     assert lib.ipf_create(C.byref(op), bb.ctypes.data, 0, C.byref(cfg), C.byref(h)) == b.IPF_ERR_UNSUPPORTED
+    # pivot-block solve: 0 inverse form (default), 1 forward substitution
+    cfg = b.default_config(pivot_fwd=2)
+    assert lib.ipf_create(C.byref(op), bb.ctypes.data, 0, C.byref(cfg), C.byref(h)) == b.IPF_ERR_ARG
     assert lib.ipf_step(None, 1, None) == b.IPF_ERR_ARG
     assert lib.ipf_footprint(C.byref(op), C.byref(b.default_config())) > 64 * 51 * 4
 
@@ -84,7 +87,7 @@ def test_default_config_maps_string_options(lib):
     names for the enums of include/ipf.h."""
     from paper_2502_02721_gb300 import binding as bd
     d = bd.default_config()
-    assert d.overlap == 2 and d.pivot_sample == 0 and d.sketch == 0 and d.method == 0
+    assert d.overlap == 2 and d.pivot_sample == 0 and d.sketch == 0 and d.method == 0 and d.pivot_fwd == 0
     cfg = bd.default_config(storage="bf16", method="slslu", sketch="gaussian", pivot_sample=25)
     assert cfg.storage == bd.STORAGE["bf16"]
     assert cfg.method == bd.METHOD["slslu"] == 1
