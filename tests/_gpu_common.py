@@ -26,8 +26,8 @@ the record says so; the parity check still holds there.
 
 Every comparison is appended to RECORD (test, storage, k, lambda, the
 errors and bounds); conftest.py prints the worst cases at the end of the
-run and writes all of them to gpurun_out/parity_errors.json when that
-folder exists.
+run and writes all of them to parity_errors.json in the folder named by
+IPF_PARITY_RECORD_DIR when that is set.
 """
 import os
 

@@ -17,7 +17,8 @@ def pytest_terminal_summary(terminalreporter, exitstatus, config):
     """Errors reached by the GPU parity tests: the worst case per test
     against the storage-matched oracle (e_par / bound) and against the FP64
     oracle (e64 / stated, or why the stated bound is out of reach); the full
-    record goes to gpurun_out/parity_errors.json when that folder exists."""
+    record goes to parity_errors.json in the folder named by the environment
+    variable IPF_PARITY_RECORD_DIR, when it is set and exists."""
     try:
         import _gpu_common as gc
     except Exception:
@@ -26,8 +27,8 @@ def pytest_terminal_summary(terminalreporter, exitstatus, config):
     if not rec:
         return
     import json
-    out = os.path.join(ROOT, "gpurun_out")
-    if os.path.isdir(out):
+    out = os.environ.get("IPF_PARITY_RECORD_DIR", "")
+    if out and os.path.isdir(out):
         with open(os.path.join(out, "parity_errors.json"), "w") as f:
             json.dump(rec, f)
     by = {}
