@@ -142,7 +142,9 @@ typedef void (*ipf_free_fn)(void* ptr, void* user);
 typedef struct ipf_config {
     int k_max;                   /* maximum Hessenberg steps, 1..480 (basis has k_max+1
                                     vectors); with the Gaussian sketch 1..247              */
-    int m_s;                     /* sketch rows (l in Sec. 2); m_s >= zeta                  */
+    int m_s;                     /* sketch rows (l in Sec. 2); zeta <= m_s <= 7232 (the exact
+                                    sketch counters of a right-hand side live in shared
+                                    memory; larger: IPF_ERR_UNSUPPORTED)                    */
     int zeta;                    /* nonzeros per sketch column, 1..16                       */
     unsigned long long seed;     /* sketch seed (SplitMix64 state)                          */
     int storage;                 /* enum ipf_storage                                        */

@@ -654,6 +654,7 @@ ipf_status ipf_create(const ipf_operator* op, const float* b, int b_mem, const i
     if (cfg.zform == IPF_Z_DIRECT && !z_ok) return IPF_ERR_UNSUPPORTED;
     if (cfg.k_max > kMaxK) return IPF_ERR_UNSUPPORTED;    // forward substitution's rows (512) in registers
     if (cfg.pivot_fwd != 0 && cfg.pivot_fwd != 1) return IPF_ERR_ARG;
+    if (cfg.m_s > kMaxMs) return IPF_ERR_UNSUPPORTED;     // the normaliser's shared sketch counters
     // the Gaussian contraction's B tile: V_{k+1} rounded up, plus 8 rows of b, at most 256 rows
     if (gauss && (cfg.k_max + 1 + 8 + 15) / 16 * 16 > 256) return IPF_ERR_UNSUPPORTED;
     if (b_mem != IPF_MEM_HOST && b_mem != IPF_MEM_DEVICE) return IPF_ERR_ARG;

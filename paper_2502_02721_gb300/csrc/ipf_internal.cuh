@@ -298,6 +298,11 @@ struct OpDev {
 // ---------------------------------------------------------------------------
 constexpr int kMaxSlots = 64;
 constexpr int kMaxK = 480;                     // k_max (forward substitution's registers hold 512 rows)
+// m_s of a context: the initial normalisation keeps two sets of exact sketch
+// counters of one right-hand side (S v_1 and S b / beta; 8 + 4 + 4 bytes per
+// row each) in dynamic shared memory, at most 227 KB per CTA less 1 KB for
+// the kernel's static shared memory
+constexpr int kMaxMs = (227 * 1024 - 1024) / 32;
 constexpr int kSmallMaxK = 512;                // the projected solve's per-column shared arrays
 static_assert(kMaxK <= kSmallMaxK, "projected solve arrays");
 constexpr int kBatchUpdTile = kFoldEvery;      // update tile: the split counters' exact range

@@ -75,6 +75,9 @@ def test_argument_errors_need_no_gpu(lib):
     assert lib.ipf_create(C.byref(op), bb.ctypes.data, 0, C.byref(cfg), C.byref(h)) == b.IPF_ERR_UNSUPPORTED
     cfg = b.default_config(k_max=248, m_s=1000, sketch="gaussian")
     assert lib.ipf_create(C.byref(op), bb.ctypes.data, 0, C.byref(cfg), C.byref(h)) == b.IPF_ERR_UNSUPPORTED
+    # m_s: the normaliser's two sets of shared sketch counters fit 227 KB
+    cfg = b.default_config(m_s=7233)
+    assert lib.ipf_create(C.byref(op), bb.ctypes.data, 0, C.byref(cfg), C.byref(h)) == b.IPF_ERR_UNSUPPORTED
     # pivot-block solve: 0 inverse form (default), 1 forward substitution
     cfg = b.default_config(pivot_fwd=2)
     assert lib.ipf_create(C.byref(op), bb.ctypes.data, 0, C.byref(cfg), C.byref(h)) == b.IPF_ERR_ARG
